@@ -1,0 +1,174 @@
+"""fp64 oracle for the trainable glyph query (Sec. 3 training loop, Sec. 4,
+Sec. 5.5 query over image grids).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The query: a grid image is split into 4x4 cells; a CNN maps each 28x28 cell
+to class probabilities (softmax, the PE column); the soft group-by turns the
+probabilities of the 16 cells into a per-class COUNT and a per-row SUM of
+class values; the loss is the mean squared error against the same query run
+exactly on the true labels; training backpropagates through the query into
+the CNN and takes Adam steps (lr 0.01 in the paper's loop).
+
+Network (one reading of the paper's unspecified ``CNN(num_classes=10)``):
+  conv3x3(1->32, valid) + ReLU -> conv3x3(32->64, valid) + ReLU
+  -> maxpool 2x2 -> flatten (y, x, c) -> FC 9216->128 + ReLU -> FC 128->10
+  -> softmax.
+
+``quant=True`` reproduces the precision contract of the accelerated path in
+float64 arithmetic: the conv2 / fc1 operands (activations and weights) and
+the back-propagated activation gradients that feed those contractions are
+rounded to bfloat16 (round to nearest even) at the same points, everything
+else stays float64.  ``quant=False`` is the plain float64 network used for
+the finite-difference pins.
+
+Direct-loop formulation: each 3x3 convolution is a sum over the 9 kernel
+taps of shifted-window contractions (numpy ``@`` / ``einsum`` as the
+library step); pooling takes the first maximal element of each 2x2 window in
+(dy, dx) row-major order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import soft
+
+K_CLASSES = 10
+GRID = 4
+CELL = 28
+
+
+def bf16(a):
+    """Round float values to the nearest bfloat16 (ties to even); float64 out."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def split_cells(grids_u8):
+    """[n, 112, 112] grid images -> [n*16, 28, 28] cells (row-major cells)."""
+    g = np.asarray(grids_u8)
+    n = g.shape[0]
+    return g.reshape(n, GRID, CELL, GRID, CELL).transpose(0, 1, 3, 2, 4).reshape(n * GRID * GRID, CELL, CELL)
+
+
+def _q(a, quant):
+    return bf16(a) if quant else np.asarray(a, np.float64)
+
+
+def forward(params, grids_u8, quant=True):
+    """Returns a dict with every intermediate needed by ``backward``."""
+    p = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    x0 = split_cells(grids_u8).astype(np.float64) / 255.0  # [B,28,28]
+    B = x0.shape[0]
+    # conv1 (1 -> 32), valid, + bias, ReLU
+    z1 = np.zeros((B, 26, 26, 32))
+    for ky in range(3):
+        for kx in range(3):
+            z1 += x0[:, ky:ky + 26, kx:kx + 26, None] * p["conv1_w"][:, ky, kx]
+    z1 += p["conv1_b"]
+    y1 = _q(np.maximum(z1, 0.0), quant)
+    # conv2 (32 -> 64), valid, + bias, ReLU
+    w2 = _q(p["conv2_w"], quant)
+    z2 = np.zeros((B, 24, 24, 64))
+    for ky in range(3):
+        for kx in range(3):
+            z2 += y1[:, ky:ky + 24, kx:kx + 24, :] @ w2[:, ky, kx, :].T
+    z2 += p["conv2_b"]
+    a2 = np.maximum(z2, 0.0)
+    # 2x2 max pool; first maximum in (dy, dx) order
+    win = a2.reshape(B, 12, 2, 12, 2, 64).transpose(0, 1, 3, 2, 4, 5).reshape(B, 12, 12, 4, 64)
+    arg = np.argmax(win, axis=3)  # first occurrence of the maximum
+    pooled = np.take_along_axis(win, arg[:, :, :, None, :], axis=3)[:, :, :, 0, :]
+    y2 = _q(pooled, quant)  # [B,12,12,64]
+    flat = y2.reshape(B, 9216)
+    wf1 = _q(p["fc1_w"], quant)
+    h1 = _q(np.maximum(flat @ wf1.T + p["fc1_b"], 0.0), quant)
+    logits = h1 @ p["fc2_w"].T + p["fc2_b"]
+    z = logits - logits.max(axis=1, keepdims=True)
+    e = np.exp(z)
+    P = e / e.sum(axis=1, keepdims=True)
+    cnt, rsum = soft.pe_groupby_fwd(P)
+    pred = np.concatenate([cnt, rsum], axis=1)  # [n_grids, 14]
+    return dict(x0=x0, y1=y1, w2=w2, a2=a2, arg=arg, y2=y2, wf1=wf1, h1=h1,
+                logits=logits, P=P, pred=pred, quant=quant)
+
+
+def targets_from_labels(labels):
+    """Exact query on the true labels: [n_grids, 14] (10 counts, 4 row sums)."""
+    cnt, rsum = soft.exact_groupby(labels, K_CLASSES)
+    return np.concatenate([cnt, rsum], axis=1).astype(np.float64)
+
+
+def loss(pred, target):
+    d = np.asarray(pred, np.float64) - np.asarray(target, np.float64)
+    return float(np.mean(d * d))
+
+
+def backward(params, fw, target):
+    """Gradients of the MSE loss w.r.t. every parameter (dict like params)."""
+    p = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    quant = fw["quant"]
+    pred = fw["pred"]
+    n_out = pred.size
+    dpred = 2.0 * (pred - np.asarray(target, np.float64)) / n_out
+    dP = soft.pe_groupby_bwd(dpred[:, :K_CLASSES], dpred[:, K_CLASSES:])
+    P = fw["P"]
+    dlogits = P * (dP - (P * dP).sum(axis=1, keepdims=True))
+    h1 = fw["h1"]
+    g = {}
+    g["fc2_w"] = dlogits.T @ h1
+    g["fc2_b"] = dlogits.sum(axis=0)
+    dh1 = _q((dlogits @ p["fc2_w"]) * (h1 > 0), quant)
+    B = h1.shape[0]
+    flat = fw["y2"].reshape(B, 9216)
+    g["fc1_w"] = dh1.T @ flat
+    g["fc1_b"] = dh1.sum(axis=0)
+    dflat = dh1 @ fw["wf1"]  # [B, 9216]
+    dy2 = dflat.reshape(B, 12, 12, 64) * (fw["y2"] > 0)
+    # route through the pool argmax
+    dwin = np.zeros((B, 12, 12, 4, 64))
+    np.put_along_axis(dwin, fw["arg"][:, :, :, None, :], dy2[:, :, :, None, :], axis=3)
+    dz2 = dwin.reshape(B, 12, 12, 2, 2, 64).transpose(0, 1, 3, 2, 4, 5).reshape(B, 24, 24, 64)
+    dz2 = _q(dz2, quant)
+    y1 = fw["y1"]
+    gw2 = np.zeros((64, 3, 3, 32))
+    dy1 = np.zeros((B, 26, 26, 32))
+    for ky in range(3):
+        for kx in range(3):
+            gw2[:, ky, kx, :] = np.einsum("byxo,byxi->oi", dz2, y1[:, ky:ky + 24, kx:kx + 24, :])
+            dy1[:, ky:ky + 24, kx:kx + 24, :] += dz2 @ fw["w2"][:, ky, kx, :]
+    g["conv2_w"] = gw2
+    g["conv2_b"] = dz2.sum(axis=(0, 1, 2))
+    dz1 = _q(dy1 * (y1 > 0), quant)
+    x0 = fw["x0"]
+    gw1 = np.zeros((32, 3, 3))
+    for ky in range(3):
+        for kx in range(3):
+            gw1[:, ky, kx] = np.einsum("byxo,byx->o", dz1, x0[:, ky:ky + 26, kx:kx + 26])
+    g["conv1_w"] = gw1
+    g["conv1_b"] = dz1.sum(axis=(0, 1, 2))
+    return g
+
+
+def adam_step(params, grads, m, v, t, lr=0.01, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (bias-corrected moments), float64.  Returns new
+    (params, m, v)."""
+    newp, newm, newv = {}, {}, {}
+    for k in params:
+        gk = np.asarray(grads[k], np.float64)
+        mk = b1 * np.asarray(m[k], np.float64) + (1 - b1) * gk
+        vk = b2 * np.asarray(v[k], np.float64) + (1 - b2) * gk * gk
+        mhat = mk / (1 - b1 ** t)
+        vhat = vk / (1 - b2 ** t)
+        newp[k] = np.asarray(params[k], np.float64) - lr * mhat / (np.sqrt(vhat) + eps)
+        newm[k], newv[k] = mk, vk
+    return newp, newm, newv
+
+
+def predict_labels(params, grids_u8):
+    """Exact-mode inference: argmax of the class probabilities per cell."""
+    fw = forward(params, grids_u8, quant=False)
+    return np.argmax(fw["logits"], axis=1).reshape(-1, GRID, GRID)

@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the Tensor Data Platform hot path on one B300 (or N replicas).
+
+Headline step: the shipping-priority query plan on a 60M-row fact table and a
+15M-row dimension table (dimension filter -> hash build; fact filter fused
+into the probe with a gather; sort-based GROUP BY key of
+SUM(price*(100-disc)); top-10), all on synthetic seeded data.  value = fact
+rows per second over the whole job.
+
+The same run also times, on their own inputs: the pricing-summary plan
+(filter + small-domain group-by over 60M rows), the three-table join chain
+(100M probe rows, fused probe + group-by), the soft query forward+backward
+(10M rows) and, when built, the glyph-CNN trainable-query training step.
+
+Flags: --gpus N --steps K --warmup W [--impl reference] [--plans all|main]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+N_FACT = 60_000_000
+N_DIM = 15_000_000
+SEED2 = gen.BASE_SEED + 1
+WORKLOAD = "shipping-priority plan: 60M-row fact x 15M-row dimension, filter+join+group-by+top-10"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def shipping_inputs():
+    fact = gen.fact_table(N_FACT, N_DIM, SEED2, cols=("key", "price", "disc", "date"))
+    dim = gen.dim_table(N_DIM, SEED2, cols=("key", "segment"))
+    return fact, dim
+
+
+# --------------------------------------------------------------- reference
+
+def cpu_shipping_sample(scale: int):
+    """The oracle (plain C, single thread) on a 1/scale sample of the
+    shipping-priority workload (same generator, key range scaled with it).
+    Returns (fact rows, seconds)."""
+    from oracle import relational as R
+    nf, nd = N_FACT // scale, N_DIM // scale
+    fact = gen.fact_table(nf, nd, SEED2 + 1000 + scale, cols=("key", "price", "disc", "date"))
+    dim = gen.dim_table(nd, SEED2 + 1000 + scale, cols=("key", "segment"))
+    t0 = time.perf_counter()
+    bsel = R.filter([(dim["segment"], "==", 2)], nd)
+    psel = R.filter([(fact["date"], ">", 1200)], nf)
+    prow, brow, _ = R.join(dim["key"], fact["key"], bsel=bsel, psel=psel)
+    keys, aggs = R.groupby([fact["key"]], [("sum_mul_kminus", fact["price"], fact["disc"], 100)], nf, sel=prow)
+    R.topk(aggs[:, 0], keys[:, 0], 10)
+    return nf, time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    scale = 20
+    rows, secs = [], []
+    for _ in range(args.warmup):
+        cpu_shipping_sample(scale)
+    for _ in range(args.steps):
+        r, s = cpu_shipping_sample(scale)
+        rows.append(r)
+        secs.append(s)
+    v = sum(rows) / sum(secs)
+    line = {
+        "impl": "reference", "metric": "fact rows/s (shipping-priority plan)", "value": v, "unit": "rows/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "fact_rows": N_FACT, "dim_rows": N_DIM, "parallelism": "replicas"},
+        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                         "sample": "1/%d of the workload per step (%d fact rows, %d dimension rows), plain C "
+                                   "oracle, one thread" % (scale, N_FACT // scale, N_DIM // scale)},
+        "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self, gpu_index: int):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9 or not p[0].isdigit() or int(p[0]) != gpu_index:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2211_02753_b300 import ops, plans
+    from paper_2211_02753_b300 import _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _lib.lib()  # fail loudly if the library is missing
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    hbm_peak, peak_kind = load_peaks()
+
+    # ---- headline: shipping-priority plan
+    fact_h, dim_h = shipping_inputs()
+    fact = {k: torch.from_numpy(v).to(dev) for k, v in fact_h.items()}
+    dim = {k: torch.from_numpy(v).to(dev) for k, v in dim_h.items()}
+    plan = plans.ShippingPriority(fact, dim)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        out = plan.run()
+    torch.cuda.synchronize()
+    ops.check(plan.status, "shipping-priority plan")
+    nmatch = int(out["nmatch"].item())
+    ngroups = int(out["ngroups"].item())
+
+    # stage timing (CUDA events on the launching stream) for the roofline
+    def stage_times(reps=3):
+        ev = []
+        for _ in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            e[0].record(stream)
+            ops.join_build([dim["key"], dim["segment"]], 0, preds=[(1, "==", 2)], nslots=plan.nslots,
+                           table=plan.table, status=plan.status)
+            e[1].record(stream)
+            pr = ops.join_probe(plan.table, [fact["key"], fact["date"], fact["price"], fact["disc"]], 0,
+                                preds=[(1, ">", 1200)], gather=[0, 2, 3], capacity=plan.cap, rowids=False,
+                                payload=False, status=plan.status)
+            e[2].record(stream)
+            kc, pc, dc = pr["gathered"]
+            gb = ops.groupby_agg([ops.Col(kc, 1, N_DIM), pc, dc], [0], [("sum_mul_kminus", 1, 2, 100)],
+                                 n=plan.cap, nsel=pr["count"], strategy="sort", capacity=plan.cap,
+                                 status=plan.status)
+            e[3].record(stream)
+            ops.topk(gb["aggs"][0], gb["keys"][0], 10, d_n=gb["ngroups"], status=plan.status)
+            e[4].record(stream)
+            torch.cuda.synchronize()
+            ev.append([e[i].elapsed_time(e[i + 1]) for i in range(4)])
+        return [statistics.median(x[i] for x in ev) for i in range(4)]
+
+    st_ms = stage_times()
+
+    # timed region
+    sampler = ClockSampler()
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        out = plan.run()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop(local)
+    ms = t0.elapsed_time(t1) / args.steps
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ops.check(plan.status, "shipping-priority plan")
+    value = N_FACT * world / (ms / 1000.0)
+
+    # ---- e2e: host (pinned) buffers in, top-10 out, every step
+    pin_f = {k: torch.from_numpy(v).pin_memory() for k, v in fact_h.items()}
+    pin_d = {k: torch.from_numpy(v).pin_memory() for k, v in dim_h.items()}
+    h2d = sum(v.numel() * v.element_size() for v in list(pin_f.values()) + list(pin_d.values()))
+    out_v = torch.empty(10, dtype=torch.int64).pin_memory()
+    out_k = torch.empty(10, dtype=torch.int32).pin_memory()
+    d2h = 10 * 8 + 10 * 4
+
+    def e2e_step():
+        for k in fact:
+            fact[k].copy_(pin_f[k], non_blocking=True)
+        for k in dim:
+            dim[k].copy_(pin_d[k], non_blocking=True)
+        o = plan.run()
+        out_v.copy_(o["top_vals"], non_blocking=True)
+        out_k.copy_(o["top_keys"], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = N_FACT * world / (e2e_ms / 1000.0)
+
+    # ---- kernel launches per step (profiler on one extra, untimed step)
+    launches_per_step = None
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            plan.run()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+        launches_per_step = sum(1 for n in names if "tdp::" in n)
+    except Exception:
+        launches_per_step = None
+
+    # ---- roofline of the dominant stage
+    stage_names = ["join_build", "join_probe", "groupby_sort", "topk"]
+    sel_f = float(np.mean(fact_h["date"] > 1200))
+    probe_rows = N_FACT * sel_f
+    algo = {
+        # build: dim segment (1 B) for every row + key (4 B) for matches + table slot writes (8 B/slot fill +
+        # 8 B per insert)
+        "join_build": N_DIM * 1 + N_DIM * 0.2 * 4 + plan.nslots * 8 + N_DIM * 0.2 * 8,
+        # probe: date (4 B) every row; key (4 B) of qualifying rows; one 8-byte slot per lookup; price/disc
+        # (16 B) of matches; key/price/disc written for matches (20 B)
+        "join_probe": N_FACT * 4 + probe_rows * 4 + probe_rows * 8 + nmatch * 16 + nmatch * 20,
+        # sort path group-by: pack (read 20 B, write 8 B), 3 digit passes (read+write 8 B pairs), reduce
+        # (read 8 B pair + 16 B gather, write 12 B per group)
+        "groupby_sort": nmatch * (20 + 8) + 3 * nmatch * 16 + nmatch * (8 + 16) + ngroups * 12,
+        "topk": ngroups * 12,
+    }
+    dom = int(np.argmax(st_ms))
+    dom_name = stage_names[dom]
+    achieved = algo[dom_name] / (st_ms[dom] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": dom_name,
+                "peak_kind": peak_kind + " (copy bandwidth)",
+                "stages_ms": dict(zip(stage_names, st_ms)),
+                "stages_algo_gbs": {k: algo[k] / (t / 1000.0) / 1e9 for k, t in zip(stage_names, st_ms)}}
+
+    line = {
+        "metric": "fact rows/s (shipping-priority plan)", "value": value, "unit": "rows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "fact_rows": N_FACT, "dim_rows": N_DIM, "matches": nmatch,
+                   "groups": ngroups, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (1.5 GB of columns per step)"},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms},
+        "gpu_launches": (launches_per_step * args.steps) if launches_per_step is not None else None,
+        "gpu_launches_per_step": launches_per_step,
+        "clocks": clocks,
+    }
+    del fact, dim, plan, pin_f, pin_d
+    torch.cuda.empty_cache()
+
+    if args.plans == "all":
+        line["plans"] = other_plans(dev, stream, hbm_peak, args)
+
+    if rank == 0:
+        # CPU baseline: the oracle on a bounded sample (rank 0, N=1 semantics)
+        scale = 20
+        r, s = cpu_shipping_sample(scale)
+        line["cpu_baseline"] = {"value": r / s, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                                "sample": "1/%d of the workload (%d fact rows, %d dimension rows), plain C "
+                                          "oracle, one thread, %.1f s" % (scale, r, N_DIM // scale, s)}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _time(fn, stream, steps):
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def other_plans(dev, stream, hbm_peak, args):
+    import torch
+    from paper_2211_02753_b300 import ops, plans
+    res = {}
+    steps = max(3, args.steps)
+    # pricing summary at 60M rows
+    t = gen.fact_table(N_FACT, N_DIM, SEED2, cols=("flag", "status", "qty", "price", "disc", "date"))
+    sel = float(np.mean(t["date"] <= 2460))
+    td = {k: torch.from_numpy(v).to(dev) for k, v in t.items()}
+    td["key"] = None
+    del t
+    for strategy in ("small_domain", "sort"):
+        p = plans.PricingSummary(td, strategy)
+        ms = _time(lambda: p.run(), stream, steps if strategy == "small_domain" else 3)
+        bpr = plans.PricingSummary.bytes_per_row(sel)
+        res["pricing_summary_60M_" + strategy] = {"ms": ms, "rows_per_s": N_FACT / (ms / 1e3),
+                                                  "algo_gbs": N_FACT * bpr / (ms / 1e3) / 1e9,
+                                                  "frac_hbm": N_FACT * bpr / (ms / 1e3) / 1e9 / hbm_peak}
+    del td
+    torch.cuda.empty_cache()
+    # join chain (100M probe rows)
+    d = gen.chain_tables(100_000_000, 10_000_000, 1_000_000, gen.BASE_SEED + 2)
+    dd = {k: torch.from_numpy(v.astype(np.int32) if k == "probe_fk" else v).to(dev) for k, v in d.items()}
+    del d
+    jc = plans.JoinChain(dd)
+    ms = _time(lambda: jc.run(), stream, steps)
+    out = jc.run()
+    torch.cuda.synchronize()
+    ops.check(jc.status, "join chain")
+    algo = 100e6 * (4 + 8 + 8) + 10e6 * (4 + 4 + 8 + 8) + 1e6 * 8
+    res["join_chain_100M"] = {"ms": ms, "rows_per_s": 100e6 / (ms / 1e3), "algo_gbs": algo / (ms / 1e3) / 1e9,
+                              "frac_hbm": algo / (ms / 1e3) / 1e9 / hbm_peak,
+                              "groups": int(out["ngroups"].item())}
+    del dd, jc
+    torch.cuda.empty_cache()
+    # soft query fwd+bwd (10M rows)
+    s = gen.soft_table(10_000_000, 1024, gen.BASE_SEED + 3)
+    sd = {k: torch.from_numpy(v).to(dev) for k, v in s.items()}
+    sq = plans.SoftQuery(sd)
+    ms = _time(lambda: sq.run(), stream, steps)
+    algo = 10e6 * 24
+    res["soft_query_10M_fwd_bwd"] = {"ms": ms, "rows_per_s": 10e6 / (ms / 1e3), "algo_gbs": algo / (ms / 1e3) / 1e9,
+                                     "frac_hbm": algo / (ms / 1e3) / 1e9 / hbm_peak}
+    del sd, sq
+    torch.cuda.empty_cache()
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plans", default="all", choices=["all", "main"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,259 @@
+// Shared device helpers of the tdp kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tdp.h"
+
+#define TDP_MAX_PREDS 8
+#define TDP_MAX_GATHER 8
+#define TDP_MAX_KEYS 4
+#define TDP_MAX_AGGS 8
+
+namespace tdp {
+
+// ---------------------------------------------------------------- host side
+
+// Current bounded-wait limit (polls) passed to every kernel that spins.
+uint32_t spin_limit();
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline int dtype_size(int dt)
+{
+    switch (dt) {
+    case TDP_I8:
+    case TDP_U8: return 1;
+    case TDP_BF16: return 2;
+    case TDP_I32:
+    case TDP_F32: return 4;
+    case TDP_I64: return 8;
+    default: return 0;
+    }
+}
+
+inline bool is_int_dtype(int dt) { return dt == TDP_I8 || dt == TDP_U8 || dt == TDP_I32 || dt == TDP_I64; }
+
+inline tdp_status launch_status()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TDP_OK : TDP_ERR_CUDA;
+}
+
+int num_sms();
+
+// Predicates as kernel parameters (values, not pointers to host memory).
+struct PredSet {
+    const void *col[TDP_MAX_PREDS];
+    int32_t dt[TDP_MAX_PREDS];
+    int32_t cmp[TDP_MAX_PREDS];
+    long long lit[TDP_MAX_PREDS];
+    int32_t vec_ok[TDP_MAX_PREDS]; // column base 16-byte aligned
+    int32_t n;
+};
+
+// Validates `preds` against `cols` and fills a PredSet.
+tdp_status make_predset(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds, int64_t n,
+                        PredSet *out);
+
+// ---------------------------------------------------------------- device side
+
+__device__ __forceinline__ void set_status(int32_t *s, int32_t code)
+{
+    if (s)
+        atomicOr(s, code);
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ long long load_int(const void *p, int dt, long long i)
+{
+    switch (dt) {
+    case TDP_I8: return ((const int8_t *)p)[i];
+    case TDP_U8: return ((const uint8_t *)p)[i];
+    case TDP_I32: return ((const int32_t *)p)[i];
+    default: return ((const long long *)p)[i];
+    }
+}
+
+// Loads 4 consecutive integer elements starting at row r (r % 4 == 0),
+// widened to int64.  Rows >= n read as 0 (the caller masks them out).
+__device__ __forceinline__ void load4_int(const void *p, int dt, bool vec_ok, long long r, long long n,
+                                          long long v[4])
+{
+    if (vec_ok && r + 3 < n) {
+        switch (dt) {
+        case TDP_I8: {
+            int w = __ldg((const int *)((const int8_t *)p + r));
+            v[0] = (int8_t)(w & 0xff);
+            v[1] = (int8_t)((w >> 8) & 0xff);
+            v[2] = (int8_t)((w >> 16) & 0xff);
+            v[3] = (int8_t)((w >> 24) & 0xff);
+            return;
+        }
+        case TDP_U8: {
+            unsigned w = __ldg((const unsigned *)((const uint8_t *)p + r));
+            v[0] = w & 0xff;
+            v[1] = (w >> 8) & 0xff;
+            v[2] = (w >> 16) & 0xff;
+            v[3] = (w >> 24) & 0xff;
+            return;
+        }
+        case TDP_I32: {
+            int4 w = __ldg((const int4 *)((const int32_t *)p + r));
+            v[0] = w.x;
+            v[1] = w.y;
+            v[2] = w.z;
+            v[3] = w.w;
+            return;
+        }
+        default: {
+            longlong2 a = __ldg((const longlong2 *)((const long long *)p + r));
+            longlong2 b = __ldg((const longlong2 *)((const long long *)p + r + 2));
+            v[0] = a.x;
+            v[1] = a.y;
+            v[2] = b.x;
+            v[3] = b.y;
+            return;
+        }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        v[k] = (r + k < n) ? load_int(p, dt, r + k) : 0;
+}
+
+__device__ __forceinline__ bool cmp_holds(long long v, int cmp, long long lit)
+{
+    switch (cmp) {
+    case TDP_LT: return v < lit;
+    case TDP_LE: return v <= lit;
+    case TDP_GT: return v > lit;
+    case TDP_GE: return v >= lit;
+    case TDP_EQ: return v == lit;
+    default: return v != lit;
+    }
+}
+
+// 4-bit mask of rows r..r+3 (r % 4 == 0) that are < n and satisfy every predicate.
+__device__ __forceinline__ unsigned eval_preds4(const PredSet &ps, long long r, long long n)
+{
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        m |= (r + k < n) ? (1u << k) : 0u;
+    for (int p = 0; p < ps.n; p++) {
+        long long v[4];
+        load4_int(ps.col[p], ps.dt[p], ps.vec_ok[p], r, n, v);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (!cmp_holds(v[k], ps.cmp[p], ps.lit[p]))
+                m &= ~(1u << k);
+    }
+    return m;
+}
+
+// Same for a single row.
+__device__ __forceinline__ bool eval_preds1(const PredSet &ps, long long r)
+{
+    for (int p = 0; p < ps.n; p++)
+        if (!cmp_holds(load_int(ps.col[p], ps.dt[p], r), ps.cmp[p], ps.lit[p]))
+            return false;
+    return true;
+}
+
+// --------------------------------------------------------- decoupled look-back
+//
+// Tile status word: bits 62..63 flag (0 = nothing yet, 1 = tile aggregate,
+// 2 = inclusive prefix), bits 0..61 the value.
+constexpr unsigned long long LB_AGG = 1ull << 62;
+constexpr unsigned long long LB_INC = 2ull << 62;
+constexpr unsigned long long LB_VAL = (1ull << 62) - 1;
+
+// Bounded spin on one status word until its flag is non-zero.  Gives up
+// after `limit` polls, sets TDP_ERR_TIMEOUT and returns the word as read.
+__device__ __forceinline__ unsigned long long lb_wait(const unsigned long long *w, uint32_t limit,
+                                                      int32_t *d_status)
+{
+    unsigned long long s = ld_relaxed_u64(w);
+    uint32_t polls = 0;
+    while ((s >> 62) == 0) {
+        if (polls++ >= limit) {
+            set_status(d_status, TDP_ERR_TIMEOUT);
+            return s;
+        }
+        __nanosleep(polls < 64 ? 20 : 200);
+        s = ld_relaxed_u64(w);
+    }
+    return s;
+}
+
+// Called by ONE full warp of the tile.  Publishes the tile aggregate, walks
+// back over predecessors 32 at a time and returns the exclusive prefix
+// (the same value in every lane); publishes the inclusive prefix.
+__device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long *status, long long tile,
+                                                                 unsigned long long aggregate, uint32_t limit,
+                                                                 int32_t *d_status)
+{
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0)
+            st_relaxed_u64(&status[0], LB_INC | aggregate);
+        return 0;
+    }
+    if (lane == 0)
+        st_relaxed_u64(&status[tile], LB_AGG | aggregate);
+    unsigned long long excl = 0;
+    long long base = tile - 1;
+    while (true) {
+        long long t = base - lane;
+        unsigned long long s = (t >= 0) ? lb_wait(&status[t], limit, d_status) : LB_INC;
+        unsigned long long v = (t >= 0) ? (s & LB_VAL) : 0;
+        unsigned incl_mask = __ballot_sync(0xffffffffu, (s >> 62) == 2 || (s >> 62) == 0);
+        // (a timed-out predecessor is treated as an inclusive prefix of its value)
+        int stop = incl_mask ? __ffs(incl_mask) - 1 : 32;
+        unsigned long long contrib = (lane <= stop) ? v : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+        excl += contrib;
+        if (incl_mask)
+            break;
+        base -= 32;
+    }
+    if (lane == 0)
+        st_relaxed_u64(&status[tile], LB_INC | ((excl + aggregate) & LB_VAL));
+    return excl;
+}
+
+} // namespace tdp

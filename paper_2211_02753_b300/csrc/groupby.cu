@@ -1,0 +1,494 @@
+// K5 (small-domain group-by) and the entry point tdp_groupby_agg.
+//
+// SMALL_DOMAIN: when every key column carries bounds (the column metadata of
+// Sec. 2 that picks an operator strategy) the key tuple maps to a dense group
+// id gid = sum_k (key_k - lo_k) * stride_k.  One pass over the rows (fused
+// with the WHERE predicates) adds every row into a private copy of the dense
+// accumulator table: one copy per warp when the table is tiny (a handful of
+// groups, e.g. flag x status), one per block when it fits in shared memory,
+// else the global table itself.  Copies are merged into the global table
+// with 64-bit atomics (integer sums are exact, so the result does not depend
+// on the order), and a compaction kernel emits the non-empty groups in
+// ascending gid order, which is ascending key order.
+//
+// SORT: see groupby_sort.cu.
+#include "groupby.cuh"
+
+namespace tdp {
+
+tdp_status make_aggset(const tdp_col *cols, int32_t ncols, const tdp_agg *aggs, int32_t naggs, int64_t n,
+                       AggSet *as)
+{
+    if (naggs < 1 || naggs > TDP_MAX_AGGS || !aggs)
+        return TDP_ERR_INVALID_ARG;
+    as->n = naggs;
+    as->nslots = 1;
+    for (int a = 0; a < TDP_MAX_AGGS; a++) {
+        as->a[a] = as->b[a] = nullptr;
+        as->adt[a] = as->bdt[a] = TDP_I64;
+        as->avec[a] = as->bvec[a] = 0;
+        as->k[a] = 0;
+        as->op[a] = 0;
+        as->slot[a] = 0;
+    }
+    for (int a = 0; a < naggs; a++) {
+        const tdp_agg &g = aggs[a];
+        if (g.op < TDP_AGG_COUNT || g.op > TDP_AGG_MAX)
+            return TDP_ERR_INVALID_ARG;
+        as->op[a] = g.op;
+        as->k[a] = g.k;
+        if (g.op == TDP_AGG_COUNT) {
+            as->slot[a] = 0;
+            continue;
+        }
+        if (g.a < 0 || g.a >= ncols || cols[g.a].n < n)
+            return TDP_ERR_INVALID_ARG;
+        if (!is_int_dtype(cols[g.a].dtype))
+            return TDP_ERR_UNSUPPORTED_DTYPE;
+        as->a[a] = cols[g.a].data;
+        as->adt[a] = cols[g.a].dtype;
+        as->avec[a] = ((uintptr_t)cols[g.a].data % 16) == 0;
+        if (g.op == TDP_AGG_SUM_MUL_KMINUS) {
+            if (g.b < 0 || g.b >= ncols || cols[g.b].n < n)
+                return TDP_ERR_INVALID_ARG;
+            if (!is_int_dtype(cols[g.b].dtype))
+                return TDP_ERR_UNSUPPORTED_DTYPE;
+            as->b[a] = cols[g.b].data;
+            as->bdt[a] = cols[g.b].dtype;
+            as->bvec[a] = ((uintptr_t)cols[g.b].data % 16) == 0;
+        }
+        as->slot[a] = as->nslots++;
+    }
+    return TDP_OK;
+}
+
+// Combine operator of accumulator slot s.
+__device__ __forceinline__ int slot_op(const AggSet &as, int s)
+{
+    for (int a = 0; a < as.n; a++)
+        if (as.slot[a] == s && s != 0)
+            return as.op[a];
+    return TDP_AGG_SUM;
+}
+
+__global__ void dense_acc_init_kernel(AggSet as, long long D, long long *acc)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long total = D * as.nslots;
+    for (; e < total; e += (long long)gridDim.x * blockDim.x)
+        acc[e] = slot_init(as, (int)(e % as.nslots));
+}
+
+constexpr int SD_THREADS = 256;
+
+// Adds rows into `my` (a dense table of D groups x nslots).  Returns false
+// (and flags OVERFLOW) when a key lies outside its declared bounds.
+__device__ __forceinline__ bool row_gid(const KeySet &ks, long long row, long long &gid)
+{
+    gid = 0;
+    for (int k = 0; k < ks.n; k++) {
+        long long v = load_int(ks.col[k], ks.dt[k], row) - ks.lo[k];
+        if (v < 0 || v >= ks.size[k])
+            return false;
+        gid += v * ks.stride[k];
+    }
+    return true;
+}
+
+template <bool SEL>
+__global__ void __launch_bounds__(SD_THREADS) small_domain_kernel(PredSet ps, KeySet ks, AggSet as, long long n,
+                                                                  const int32_t *sel, const long long *d_nsel,
+                                                                  long long D, int copies, long long *gacc,
+                                                                  int32_t *d_status)
+{
+    extern __shared__ long long sacc[];
+    const int NS = as.nslots;
+    const long long tab = D * NS;
+    if (copies > 0) {
+        for (long long e = threadIdx.x; e < tab * copies; e += SD_THREADS)
+            sacc[e] = slot_init(as, (int)(e % NS));
+        __syncthreads();
+    }
+    long long *my = copies == 0 ? gacc : sacc + (copies == 1 ? 0 : (long long)(threadIdx.x >> 5) * tab);
+    bool bad = false;
+    if (!SEL) {
+        if (d_nsel)
+            n = min(*d_nsel, n);
+        const long long stride = (long long)gridDim.x * SD_THREADS * 4;
+        for (long long r = ((long long)blockIdx.x * SD_THREADS + threadIdx.x) * 4; r < n; r += stride) {
+            unsigned m = eval_preds4(ps, r, n);
+            if (!m)
+                continue;
+            long long gid[4] = {0, 0, 0, 0};
+            for (int k = 0; k < ks.n; k++) {
+                long long v[4];
+                load4_int(ks.col[k], ks.dt[k], ks.vec_ok[k], r, n, v);
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    long long d = v[j] - ks.lo[k];
+                    if ((m >> j & 1) && (d < 0 || d >= ks.size[k])) {
+                        m &= ~(1u << j);
+                        bad = true;
+                    }
+                    gid[j] += d * ks.stride[k];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (m >> j & 1)
+                    atomicAdd((unsigned long long *)&my[gid[j] * NS], 1ull);
+            for (int a = 0; a < as.n; a++) {
+                if (as.op[a] == TDP_AGG_COUNT)
+                    continue;
+                long long va[4], vb[4] = {0, 0, 0, 0};
+                load4_int(as.a[a], as.adt[a], as.avec[a], r, n, va);
+                if (as.op[a] == TDP_AGG_SUM_MUL_KMINUS)
+                    load4_int(as.b[a], as.bdt[a], as.bvec[a], r, n, vb);
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (m >> j & 1)
+                        acc_update(&my[gid[j] * NS + as.slot[a]], as.op[a], agg_value(as, a, va[j], vb[j]));
+            }
+        }
+    } else {
+        long long nsel = min(*d_nsel, n);
+        for (long long i = (long long)blockIdx.x * SD_THREADS + threadIdx.x; i < nsel;
+             i += (long long)gridDim.x * SD_THREADS) {
+            long long row = sel[i];
+            if (!eval_preds1(ps, row))
+                continue;
+            long long gid;
+            if (!row_gid(ks, row, gid)) {
+                bad = true;
+                continue;
+            }
+            atomicAdd((unsigned long long *)&my[gid * NS], 1ull);
+            for (int a = 0; a < as.n; a++) {
+                if (as.op[a] == TDP_AGG_COUNT)
+                    continue;
+                long long va = load_int(as.a[a], as.adt[a], row);
+                long long vb = as.op[a] == TDP_AGG_SUM_MUL_KMINUS ? load_int(as.b[a], as.bdt[a], row) : 0;
+                acc_update(&my[gid * NS + as.slot[a]], as.op[a], agg_value(as, a, va, vb));
+            }
+        }
+    }
+    if (bad)
+        set_status(d_status, TDP_ERR_OVERFLOW);
+    if (copies > 0) {
+        __syncthreads();
+        for (long long e = threadIdx.x; e < tab; e += SD_THREADS) {
+            int s = (int)(e % NS);
+            int op = slot_op(as, s);
+            long long init = slot_init(as, s);
+            long long v = sacc[e];
+            for (int c = 1; c < copies; c++) {
+                long long u = sacc[c * tab + e];
+                v = op == TDP_AGG_MIN ? min(v, u) : op == TDP_AGG_MAX ? max(v, u) : v + u;
+            }
+            if (v != init)
+                acc_update(&gacc[e], op, v);
+        }
+    }
+}
+
+constexpr int FIN_THREADS = 256;
+constexpr int FIN_TILE = FIN_THREADS * 4;
+
+__global__ void __launch_bounds__(FIN_THREADS) dense_finalize_kernel(KeySet ks, AggSet as, DenseOut out, long long D,
+                                                                     const long long *acc, long long cap,
+                                                                     long long *d_ngroups,
+                                                                     unsigned long long *tile_status,
+                                                                     unsigned *ticket, int32_t *d_status,
+                                                                     uint32_t limit, long long ntiles)
+{
+    __shared__ long long s_tile;
+    __shared__ unsigned s_warp[FIN_THREADS / 32];
+    __shared__ unsigned long long s_excl;
+    if (threadIdx.x == 0)
+        s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    const int NS = as.nslots;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long g0 = tile * FIN_TILE + 4ll * threadIdx.x;
+    unsigned m = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        if (g0 + j < D && acc[(g0 + j) * NS] > 0)
+            m |= 1u << j;
+    unsigned c = __popc(m), incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += u;
+    }
+    if (lane == 31)
+        s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned t = lane < FIN_THREADS / 32 ? s_warp[lane] : 0, wi = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o)
+                wi += u;
+        }
+        unsigned long long agg = __shfl_sync(0xffffffffu, wi, 31);
+        if (lane < FIN_THREADS / 32)
+            s_warp[lane] = wi - t; // exclusive warp offsets
+        unsigned long long excl = lookback_exclusive(tile_status, tile, agg, limit, d_status);
+        if (lane == 0) {
+            s_excl = excl;
+            if (tile == ntiles - 1) {
+                *d_ngroups = (long long)(excl + agg);
+                if ((long long)(excl + agg) > cap)
+                    set_status(d_status, TDP_ERR_CAPACITY);
+            }
+        }
+    }
+    __syncthreads();
+    long long pos = (long long)s_excl + s_warp[warp] + (incl - c);
+    for (int j = 0; j < 4; j++) {
+        if (!(m >> j & 1))
+            continue;
+        long long g = g0 + j;
+        if (pos < cap) {
+            for (int k = 0; k < ks.n; k++) {
+                long long key = ks.lo[k] + (g / ks.stride[k]) % ks.size[k];
+                switch (out.key_dt[k]) {
+                case TDP_I8: ((int8_t *)out.key_out[k])[pos] = (int8_t)key; break;
+                case TDP_U8: ((uint8_t *)out.key_out[k])[pos] = (uint8_t)key; break;
+                case TDP_I32: ((int32_t *)out.key_out[k])[pos] = (int32_t)key; break;
+                default: ((long long *)out.key_out[k])[pos] = key; break;
+                }
+            }
+            for (int a = 0; a < as.n; a++)
+                out.agg_out[a][pos] = agg_final(as, a, acc + g * NS);
+        }
+        pos++;
+    }
+}
+
+size_t dense_finalize_ws(long long D)
+{
+    long long tiles = (D + FIN_TILE - 1) / FIN_TILE;
+    return align_up(16 + (size_t)tiles * 8, 256);
+}
+
+tdp_status dense_finalize(const KeySet &ks, const AggSet &as, const DenseOut &out, long long D, const long long *acc,
+                          long long capacity, int64_t *d_ngroups, void *ws, int32_t *d_status, cudaStream_t s)
+{
+    long long tiles = (D + FIN_TILE - 1) / FIN_TILE;
+    cudaMemsetAsync(ws, 0, 16 + (size_t)tiles * 8, s);
+    dense_finalize_kernel<<<(unsigned)tiles, FIN_THREADS, 0, s>>>(
+        ks, as, out, D, acc, capacity, (long long *)d_ngroups, (unsigned long long *)((char *)ws + 16),
+        (unsigned *)ws, d_status, spin_limit(), tiles);
+    return launch_status();
+}
+
+// ------------------------------------------------------------------ host
+
+tdp_status make_keyset(const tdp_col *cols, int32_t ncols, const int32_t *key_cols, int32_t nkeys, int64_t n,
+                       KeySet *ks, bool need_bounds, long long *domain)
+{
+    if (nkeys < 1 || nkeys > TDP_MAX_KEYS || !key_cols)
+        return TDP_ERR_INVALID_ARG;
+    ks->n = nkeys;
+    long long D = 1;
+    for (int k = nkeys - 1; k >= 0; k--) {
+        int c = key_cols[k];
+        if (c < 0 || c >= ncols || cols[c].n < n)
+            return TDP_ERR_INVALID_ARG;
+        if (!is_int_dtype(cols[c].dtype))
+            return TDP_ERR_UNSUPPORTED_DTYPE;
+        ks->col[k] = cols[c].data;
+        ks->dt[k] = cols[c].dtype;
+        ks->vec_ok[k] = ((uintptr_t)cols[c].data % 16) == 0;
+        if (cols[c].has_bounds && cols[c].hi >= cols[c].lo) {
+            ks->lo[k] = cols[c].lo;
+            ks->size[k] = cols[c].hi - cols[c].lo + 1;
+        } else {
+            if (need_bounds)
+                return TDP_ERR_INVALID_ARG;
+            ks->lo[k] = 0;
+            ks->size[k] = 0;
+        }
+        ks->stride[k] = D;
+        if (ks->size[k] > 0 && D <= (1ll << 40))
+            D *= ks->size[k];
+        else
+            D = 1ll << 41;
+    }
+    for (int k = nkeys; k < TDP_MAX_KEYS; k++) {
+        ks->col[k] = nullptr;
+        ks->dt[k] = 0;
+        ks->vec_ok[k] = 0;
+        ks->lo[k] = ks->size[k] = ks->stride[k] = 0;
+    }
+    *domain = D;
+    return TDP_OK;
+}
+
+static const long long SMALL_DOMAIN_MAX = 1ll << 22;
+
+static bool keys_small(const tdp_col *cols, int32_t ncols, const int32_t *key_cols, int32_t nkeys, long long *D)
+{
+    long long d = 1;
+    for (int k = 0; k < nkeys; k++) {
+        int c = key_cols[k];
+        if (c < 0 || c >= ncols || !cols[c].has_bounds || cols[c].hi < cols[c].lo)
+            return false;
+        long long sz = cols[c].hi - cols[c].lo + 1;
+        if (sz > SMALL_DOMAIN_MAX || d * sz > SMALL_DOMAIN_MAX)
+            return false;
+        d *= sz;
+    }
+    *D = d;
+    return true;
+}
+
+static bool keys_small_desc(const tdp_col *keys, int32_t nkeys, long long *D)
+{
+    long long d = 1;
+    for (int k = 0; k < nkeys; k++) {
+        if (!keys[k].has_bounds || keys[k].hi < keys[k].lo)
+            return false;
+        long long sz = keys[k].hi - keys[k].lo + 1;
+        if (sz > SMALL_DOMAIN_MAX || d * sz > SMALL_DOMAIN_MAX)
+            return false;
+        d *= sz;
+    }
+    *D = d;
+    return true;
+}
+
+int small_domain_copies(long long D, int nslots, size_t *smem)
+{
+    size_t tab = (size_t)D * nslots * 8;
+    if (tab * (SD_THREADS / 32) <= 32 * 1024) {
+        *smem = tab * (SD_THREADS / 32);
+        return SD_THREADS / 32;
+    }
+    if (tab <= 160 * 1024) {
+        *smem = tab;
+        return 1;
+    }
+    *smem = 0;
+    return 0;
+}
+
+size_t small_domain_ws(long long D, int naggs)
+{
+    return align_up((size_t)D * (1 + naggs) * 8, 256) + dense_finalize_ws(D);
+}
+
+tdp_status small_domain_run(const PredSet &ps, const KeySet &ks, const AggSet &as, long long D, long long n,
+                            const int32_t *sel, const int64_t *d_nsel, const DenseOut &out, long long capacity,
+                            int64_t *d_ngroups, void *ws, int32_t *d_status, cudaStream_t s)
+{
+    long long *acc = (long long *)ws;
+    void *fin_ws = (char *)ws + align_up((size_t)D * as.nslots * 8, 256);
+    dense_acc_init_kernel<<<(unsigned)std::min<long long>((D * as.nslots + 255) / 256, 4096), 256, 0, s>>>(as, D,
+                                                                                                         acc);
+    size_t smem = 0;
+    int copies = small_domain_copies(D, as.nslots, &smem);
+    int blocks_per_sm = copies == 1 ? std::max(1, (int)(200 * 1024 / std::max<size_t>(smem, 1))) : 8;
+    blocks_per_sm = std::min(8, blocks_per_sm);
+    long long rows = sel ? n : (n + 3) / 4;
+    long long want = (rows + SD_THREADS - 1) / SD_THREADS;
+    unsigned grid = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() * blocks_per_sm));
+    if (sel) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(small_domain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        small_domain_kernel<true><<<grid, SD_THREADS, smem, s>>>(ps, ks, as, n, sel, (const long long *)d_nsel, D,
+                                                                copies, acc, d_status);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(small_domain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        small_domain_kernel<false><<<grid, SD_THREADS, smem, s>>>(ps, ks, as, n, nullptr, (const long long *)d_nsel,
+                                                                 D, copies, acc, d_status);
+    }
+    tdp_status st = launch_status();
+    if (st != TDP_OK)
+        return st;
+    return dense_finalize(ks, as, out, D, acc, capacity, d_ngroups, fin_ws, d_status, s);
+}
+
+// Sort strategy (groupby_sort.cu)
+size_t sort_groupby_ws(long long n, int nkeys, int naggs, int key_bits);
+tdp_status sort_groupby_run(const PredSet &ps, const KeySet &ks, int key_bits, const AggSet &as, long long n,
+                            const int32_t *sel, const int64_t *d_nsel, const DenseOut &out, long long capacity,
+                            int64_t *d_ngroups, void *ws, size_t ws_bytes, int32_t *d_status, cudaStream_t s);
+int sort_key_bits(const KeySet &ks);
+int sort_key_bits_desc(const tdp_col *keys, int32_t nkeys);
+
+} // namespace tdp
+
+using namespace tdp;
+
+extern "C" size_t tdp_groupby_agg_workspace(int64_t n, const tdp_col *keys, int32_t nkeys, int32_t naggs,
+                                            int32_t strategy)
+{
+    if (!keys || nkeys < 1 || nkeys > TDP_MAX_KEYS || naggs < 1)
+        return 0;
+    long long D = 0;
+    bool small = keys_small_desc(keys, nkeys, &D);
+    if (strategy == TDP_GROUPBY_SMALL_DOMAIN || (strategy == TDP_GROUPBY_AUTO && small))
+        return small ? small_domain_ws(D, naggs) : 0;
+    int bits = sort_key_bits_desc(keys, nkeys);
+    return bits > 0 ? sort_groupby_ws(n, nkeys, naggs, bits) : 0;
+}
+
+extern "C" tdp_status tdp_groupby_agg(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds,
+                                      int64_t n, const int32_t *sel, const int64_t *d_nsel, const int32_t *key_cols,
+                                      int32_t nkeys, const tdp_agg *aggs, int32_t naggs, int32_t strategy,
+                                      void *const *out_keys, int64_t *const *out_aggs, int64_t capacity,
+                                      int64_t *d_ngroups, void *ws, size_t ws_bytes, int32_t *d_status,
+                                      tdp_stream_t stream)
+{
+    if (n < 0 || n >= (1ll << 31) || !cols || !d_ngroups || capacity < 0 || !out_keys || !out_aggs ||
+        (sel && !d_nsel) || strategy < 0 || strategy > 2)
+        return TDP_ERR_INVALID_ARG;
+    PredSet ps;
+    tdp_status st = make_predset(cols, ncols, preds, npreds, sel ? 0 : n, &ps);
+    if (st != TDP_OK)
+        return st;
+    AggSet as;
+    if ((st = make_aggset(cols, ncols, aggs, naggs, sel ? 0 : n, &as)) != TDP_OK)
+        return st;
+    long long Dsmall = 0;
+    bool small = keys_small(cols, ncols, key_cols, nkeys, &Dsmall);
+    if (strategy == TDP_GROUPBY_SMALL_DOMAIN && !small)
+        return TDP_ERR_INVALID_ARG;
+    bool use_small = strategy == TDP_GROUPBY_SMALL_DOMAIN || (strategy == TDP_GROUPBY_AUTO && small);
+    KeySet ks;
+    long long D = 0;
+    if ((st = make_keyset(cols, ncols, key_cols, nkeys, sel ? 0 : n, &ks, use_small, &D)) != TDP_OK)
+        return st;
+    DenseOut out;
+    for (int k = 0; k < TDP_MAX_KEYS; k++) {
+        out.key_out[k] = k < nkeys ? out_keys[k] : nullptr;
+        out.key_dt[k] = k < nkeys ? cols[key_cols[k]].dtype : 0;
+        if (k < nkeys && capacity > 0 && !out.key_out[k])
+            return TDP_ERR_INVALID_ARG;
+    }
+    for (int a = 0; a < TDP_MAX_AGGS; a++) {
+        out.agg_out[a] = a < naggs ? (long long *)out_aggs[a] : nullptr;
+        if (a < naggs && capacity > 0 && !out.agg_out[a])
+            return TDP_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (use_small) {
+        if (!ws || ws_bytes < small_domain_ws(D, naggs))
+            return TDP_ERR_WORKSPACE_TOO_SMALL;
+        return small_domain_run(ps, ks, as, D, n, sel, d_nsel, out, capacity, d_ngroups, ws, d_status, s);
+    }
+    int bits = sort_key_bits(ks);
+    if (bits <= 0)
+        return TDP_ERR_UNSUPPORTED_DTYPE;
+    if (!ws || ws_bytes < sort_groupby_ws(n, nkeys, naggs, bits))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    return sort_groupby_run(ps, ks, bits, as, n, sel, d_nsel, out, capacity, d_ngroups, ws, ws_bytes, d_status, s);
+}

@@ -1,0 +1,481 @@
+// K4: sort-based group-by (tdp_groupby_agg, strategy SORT).
+//
+//  1. (optional) the WHERE predicates compact the input to a row-id list
+//     (the filter kernel of filter.cu).
+//  2. Pack each row's key tuple into one unsigned radix key: key 0 is the
+//     most significant field; a bounded key takes ceil(log2(hi-lo+1)) bits
+//     as key-lo, an unbounded one its full width with the sign bit flipped,
+//     so unsigned order is lexicographic signed key order.  32-bit radix keys
+//     when the fields fit, else 64-bit.
+//  3. Onesweep radix sort of (packed key, row id) over the used bits only.
+//  4. Reduce-by-key over the sorted pairs in one pass: each thread folds 8
+//     consecutive pairs, the block scans (head count, running aggregates)
+//     with the segmented operator (a, b) -> (a.h + b.h, b.h ? b.s : a.s (+) b.s),
+//     tiles chain their carries by decoupled look-back, and the thread that
+//     holds the last pair of a group writes the group (key fields unpacked,
+//     aggregates finalised).  Groups come out in ascending key order.
+#include "filter_api.cuh"
+#include "groupby.cuh"
+#include "radix.cuh"
+
+namespace tdp {
+
+constexpr int SR_THREADS = 256;
+constexpr int SR_ITEMS = 8;
+constexpr int SR_TILE = SR_THREADS * SR_ITEMS;
+constexpr int SR_MAXS = TDP_MAX_AGGS + 1;
+
+struct KeyPack {
+    int32_t shift[TDP_MAX_KEYS];
+    int32_t bits[TDP_MAX_KEYS];
+    int32_t bounded[TDP_MAX_KEYS];
+};
+
+int key_field_bits(int dt, bool bounded, long long size)
+{
+    if (bounded) {
+        int b = 1;
+        while (b < 63 && (1ll << b) < size)
+            b++;
+        return b;
+    }
+    return 8 * dtype_size(dt);
+}
+
+int sort_key_bits(const KeySet &ks)
+{
+    int total = 0;
+    for (int k = 0; k < ks.n; k++)
+        total += key_field_bits(ks.dt[k], ks.size[k] > 0, ks.size[k]);
+    return total <= 64 ? total : -1;
+}
+
+int sort_key_bits_desc(const tdp_col *keys, int32_t nkeys)
+{
+    int total = 0;
+    for (int k = 0; k < nkeys; k++) {
+        bool b = keys[k].has_bounds && keys[k].hi >= keys[k].lo;
+        total += key_field_bits(keys[k].dtype, b, b ? keys[k].hi - keys[k].lo + 1 : 0);
+    }
+    return total <= 64 ? total : -1;
+}
+
+static KeyPack make_keypack(const KeySet &ks)
+{
+    KeyPack kp;
+    int shift = 0;
+    for (int k = TDP_MAX_KEYS - 1; k >= 0; k--) {
+        if (k >= ks.n) {
+            kp.shift[k] = kp.bits[k] = kp.bounded[k] = 0;
+            continue;
+        }
+        kp.bounded[k] = ks.size[k] > 0;
+        kp.bits[k] = key_field_bits(ks.dt[k], kp.bounded[k], ks.size[k]);
+        kp.shift[k] = shift;
+        shift += kp.bits[k];
+    }
+    return kp;
+}
+
+__device__ __forceinline__ unsigned long long field_mask(int bits)
+{
+    return bits >= 64 ? ~0ull : ((1ull << bits) - 1);
+}
+
+template <typename K>
+__global__ void pack_keys_kernel(KeySet ks, KeyPack kp, long long n, const int32_t *sel, const long long *d_nsel,
+                                 K *keys, uint32_t *rows, int32_t *d_status)
+{
+    const long long m = d_nsel ? min(*d_nsel, n) : n;
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        long long row = sel ? sel[i] : i;
+        unsigned long long packed = 0;
+        for (int k = 0; k < ks.n; k++) {
+            long long v = load_int(ks.col[k], ks.dt[k], row);
+            unsigned long long f;
+            if (kp.bounded[k]) {
+                long long d = v - ks.lo[k];
+                if (d < 0 || d >= ks.size[k]) {
+                    bad = true;
+                    d = 0;
+                }
+                f = (unsigned long long)d;
+            } else {
+                int w = kp.bits[k];
+                f = (unsigned long long)v & field_mask(w);
+                if (ks.dt[k] != TDP_U8)
+                    f ^= 1ull << (w - 1);
+            }
+            packed |= f << kp.shift[k];
+        }
+        keys[i] = (K)packed;
+        rows[i] = (uint32_t)row;
+    }
+    if (bad)
+        set_status(d_status, TDP_ERR_OVERFLOW);
+}
+
+// Look-back record of a tile.  The aggregate and the inclusive prefix live in
+// separate fields so that a reader never sees a half-overwritten value: the
+// fields selected by `flag` (1: aggregate, 2: inclusive) are final once the
+// flag is visible (written with release, read with acquire).
+struct __align__(16) SegRec {
+    unsigned flag;
+    unsigned h_agg;
+    unsigned h_inc;
+    unsigned pad;
+    long long s_agg[SR_MAXS];
+    long long s_inc[SR_MAXS];
+};
+
+struct SegVal {
+    unsigned h;
+    long long s[SR_MAXS];
+};
+
+__device__ __forceinline__ long long comb(int op, long long a, long long b)
+{
+    return op == TDP_AGG_MIN ? min(a, b) : op == TDP_AGG_MAX ? max(a, b) : a + b;
+}
+
+// a then b
+__device__ __forceinline__ void seg_combine(const int *ops, int NS, const SegVal &a, const SegVal &b, SegVal &r)
+{
+    r.h = a.h + b.h;
+#pragma unroll
+    for (int j = 0; j < SR_MAXS; j++)
+        if (j < NS)
+            r.s[j] = b.h ? b.s[j] : comb(ops[j], a.s[j], b.s[j]);
+}
+
+__device__ __forceinline__ void store_key(void *out, int dt, long long pos, long long v)
+{
+    switch (dt) {
+    case TDP_I8: ((int8_t *)out)[pos] = (int8_t)v; break;
+    case TDP_U8: ((uint8_t *)out)[pos] = (uint8_t)v; break;
+    case TDP_I32: ((int32_t *)out)[pos] = (int32_t)v; break;
+    default: ((long long *)out)[pos] = v; break;
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restrict__ keys,
+                                                                const uint32_t *__restrict__ rows, long long n_max,
+                                                                const long long *d_n, KeySet ks, KeyPack kp,
+                                                                AggSet as, DenseOut out, long long cap,
+                                                                long long *d_ngroups, SegRec *recs, unsigned *ticket,
+                                                                int32_t *d_status, uint32_t limit)
+{
+    __shared__ long long s_tile;
+    __shared__ SegVal s_warp[SR_THREADS / 32];
+    __shared__ SegVal s_carry;
+    __shared__ int s_ops[SR_MAXS];
+    __shared__ long long s_init[SR_MAXS];
+    if (threadIdx.x == 0)
+        s_tile = atomicAdd(ticket, 1u);
+    if (threadIdx.x < SR_MAXS) {
+        int s = threadIdx.x, op = TDP_AGG_SUM;
+        for (int a = 0; a < as.n; a++)
+            if (as.slot[a] == s && s != 0)
+                op = as.op[a];
+        s_ops[s] = op;
+        s_init[s] = op == TDP_AGG_MIN ? 0x7fffffffffffffffll : op == TDP_AGG_MAX ? (long long)0x8000000000000000ull : 0;
+    }
+    __syncthreads();
+    const long long tile = s_tile;
+    const long long n = d_n ? min(*d_n, n_max) : n_max;
+    const long long tile_base = tile * SR_TILE;
+    if (tile_base >= n)
+        return;
+    const int NS = as.nslots;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long i0 = tile_base + (long long)threadIdx.x * SR_ITEMS;
+    int ops[SR_MAXS];
+#pragma unroll
+    for (int j = 0; j < SR_MAXS; j++)
+        ops[j] = s_ops[j];
+
+    // thread fold: (heads, aggregates since the last head)
+    SegVal mine;
+    mine.h = 0;
+#pragma unroll
+    for (int j = 0; j < SR_MAXS; j++)
+        mine.s[j] = s_init[j];
+    K prev = (i0 > 0 && i0 - 1 < n) ? keys[i0 - 1] : (K)0;
+    unsigned headmask = 0;
+    for (int it = 0; it < SR_ITEMS; it++) {
+        long long i = i0 + it;
+        if (i >= n)
+            break;
+        K key = keys[i];
+        bool head = (i == 0) || key != prev;
+        prev = key;
+        if (head) {
+            headmask |= 1u << it;
+            mine.h++;
+#pragma unroll
+            for (int j = 0; j < SR_MAXS; j++)
+                mine.s[j] = s_init[j];
+        }
+        long long row = rows[i];
+        mine.s[0] += 1;
+        for (int a = 0; a < as.n; a++) {
+            if (as.op[a] == TDP_AGG_COUNT)
+                continue;
+            long long va = load_int(as.a[a], as.adt[a], row);
+            long long vb = as.op[a] == TDP_AGG_SUM_MUL_KMINUS ? load_int(as.b[a], as.bdt[a], row) : 0;
+            int s = as.slot[a];
+            mine.s[s] = comb(ops[s], mine.s[s], agg_value(as, a, va, vb));
+        }
+    }
+    // warp inclusive scan
+    SegVal inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        SegVal up;
+        up.h = __shfl_up_sync(0xffffffffu, inc.h, o);
+#pragma unroll
+        for (int j = 0; j < SR_MAXS; j++)
+            up.s[j] = __shfl_up_sync(0xffffffffu, inc.s[j], o);
+        if (lane >= o) {
+            SegVal r;
+            seg_combine(ops, NS, up, inc, r);
+            inc = r;
+        }
+    }
+    if (lane == 31)
+        s_warp[warp] = inc;
+    // lane-exclusive within the warp
+    SegVal lex;
+    lex.h = __shfl_up_sync(0xffffffffu, inc.h, 1);
+#pragma unroll
+    for (int j = 0; j < SR_MAXS; j++)
+        lex.s[j] = __shfl_up_sync(0xffffffffu, inc.s[j], 1);
+    if (lane == 0) {
+        lex.h = 0;
+#pragma unroll
+        for (int j = 0; j < SR_MAXS; j++)
+            lex.s[j] = s_init[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // tile aggregate = fold of warp totals
+        SegVal agg = s_warp[0];
+        for (int w = 1; w < SR_THREADS / 32; w++) {
+            SegVal r;
+            seg_combine(ops, NS, agg, s_warp[w], r);
+            agg = r;
+        }
+        SegRec *me = recs + tile;
+        SegVal excl;
+        excl.h = 0;
+        for (int j = 0; j < SR_MAXS; j++)
+            excl.s[j] = s_init[j];
+        if (tile == 0) {
+            me->h_inc = agg.h;
+            for (int j = 0; j < NS; j++)
+                me->s_inc[j] = agg.s[j];
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(2u) : "memory");
+        } else {
+            me->h_agg = agg.h;
+            for (int j = 0; j < NS; j++)
+                me->s_agg[j] = agg.s[j];
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(1u) : "memory");
+            // walk back: excl = pred (+) excl (predecessors come before)
+            for (long long t = tile - 1; t >= 0; t--) {
+                const SegRec *pr = recs + t;
+                unsigned f;
+                uint32_t polls = 0;
+                while (true) {
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&pr->flag) : "memory");
+                    if (f != 0)
+                        break;
+                    if (polls++ >= limit) {
+                        set_status(d_status, TDP_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(polls < 64 ? 20 : 200);
+                }
+                if (f == 0)
+                    break;
+                SegVal pv;
+                pv.h = f == 2 ? *(volatile const unsigned *)&pr->h_inc : *(volatile const unsigned *)&pr->h_agg;
+                for (int j = 0; j < SR_MAXS; j++)
+                    pv.s[j] = j >= NS ? s_init[j]
+                                      : (f == 2 ? *(volatile const long long *)&pr->s_inc[j]
+                                                : *(volatile const long long *)&pr->s_agg[j]);
+                SegVal r;
+                seg_combine(ops, NS, pv, excl, r);
+                excl = r;
+                if (f == 2)
+                    break;
+            }
+            SegVal incl;
+            seg_combine(ops, NS, excl, agg, incl);
+            me->h_inc = incl.h;
+            for (int j = 0; j < NS; j++)
+                me->s_inc[j] = incl.s[j];
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(2u) : "memory");
+        }
+        s_carry = excl;
+    }
+    __syncthreads();
+    // carry into this thread = tile excl (+) warps before (+) lanes before
+    SegVal carry = s_carry;
+    for (int w = 0; w < warp; w++) {
+        SegVal r;
+        seg_combine(ops, NS, carry, s_warp[w], r);
+        carry = r;
+    }
+    {
+        SegVal r;
+        seg_combine(ops, NS, carry, lex, r);
+        carry = r;
+    }
+    // emit groups that end inside this thread's items
+    long long g = (long long)carry.h - 1;
+    SegVal run = carry;
+    for (int it = 0; it < SR_ITEMS; it++) {
+        long long i = i0 + it;
+        if (i >= n)
+            break;
+        long long row = rows[i];
+        if (headmask >> it & 1) {
+            g++;
+            for (int j = 0; j < SR_MAXS; j++)
+                run.s[j] = s_init[j];
+        }
+        run.s[0] += 1;
+        for (int a = 0; a < as.n; a++) {
+            if (as.op[a] == TDP_AGG_COUNT)
+                continue;
+            long long va = load_int(as.a[a], as.adt[a], row);
+            long long vb = as.op[a] == TDP_AGG_SUM_MUL_KMINUS ? load_int(as.b[a], as.bdt[a], row) : 0;
+            int s = as.slot[a];
+            run.s[s] = comb(ops[s], run.s[s], agg_value(as, a, va, vb));
+        }
+        bool last = (i == n - 1);
+        K key = keys[i];
+        if (!last)
+            last = keys[i + 1] != key;
+        if (last) {
+            if (g >= 0 && g < cap) {
+                unsigned long long packed = (unsigned long long)key;
+                for (int k = 0; k < ks.n; k++) {
+                    unsigned long long f = (packed >> kp.shift[k]) & field_mask(kp.bits[k]);
+                    long long v;
+                    if (kp.bounded[k]) {
+                        v = ks.lo[k] + (long long)f;
+                    } else {
+                        int w = kp.bits[k];
+                        if (ks.dt[k] != TDP_U8)
+                            f ^= 1ull << (w - 1);
+                        v = w >= 64 ? (long long)f : (long long)(f << (64 - w)) >> (64 - w);
+                        if (ks.dt[k] == TDP_U8)
+                            v = (long long)f;
+                    }
+                    store_key(out.key_out[k], out.key_dt[k], g, v);
+                }
+                for (int a = 0; a < as.n; a++)
+                    out.agg_out[a][g] = agg_final(as, a, run.s);
+            }
+            if (i == n - 1) {
+                *d_ngroups = g + 1;
+                if (g + 1 > cap)
+                    set_status(d_status, TDP_ERR_CAPACITY);
+            }
+        }
+    }
+}
+
+static size_t seg_ws(long long n)
+{
+    long long tiles = (n + SR_TILE - 1) / SR_TILE;
+    return 256 + align_up((size_t)tiles * sizeof(SegRec), 256);
+}
+
+size_t sort_groupby_ws(long long n, int nkeys, int naggs, int key_bits)
+{
+    (void)nkeys;
+    (void)naggs;
+    int kb = key_bits <= 32 ? 4 : 8;
+    size_t b = align_up((size_t)n * 4, 256);                         // filtered row ids
+    b += 256;                                                         // filtered count
+    b += 2 * align_up((size_t)n * kb, 256) + 2 * align_up((size_t)n * 4, 256); // packed keys/rows, sorted
+    b += radix_ws_bytes(n, key_bits, kb);
+    b += seg_ws(n);
+    b += tdp_filter_workspace(n);
+    return b;
+}
+
+template <typename K>
+static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key_bits, const AggSet &as, long long n,
+                                    const int32_t *sel, const int64_t *d_nsel, const DenseOut &out,
+                                    long long capacity, int64_t *d_ngroups, void *ws, size_t ws_bytes,
+                                    int32_t *d_status, cudaStream_t s)
+{
+    char *p = (char *)ws;
+    int32_t *fsel = (int32_t *)p;
+    p += align_up((size_t)n * 4, 256);
+    long long *fcount = (long long *)p;
+    p += 256;
+    K *pk = (K *)p;
+    p += align_up((size_t)n * sizeof(K), 256);
+    K *sk = (K *)p;
+    p += align_up((size_t)n * sizeof(K), 256);
+    uint32_t *pr = (uint32_t *)p;
+    p += align_up((size_t)n * 4, 256);
+    uint32_t *sr = (uint32_t *)p;
+    p += align_up((size_t)n * 4, 256);
+    void *rws = p;
+    size_t rws_bytes = radix_ws_bytes(n, key_bits, sizeof(K));
+    p += rws_bytes;
+    char *segws = p;
+    p += seg_ws(n);
+    void *fws = p;
+
+    const int32_t *rowsel = sel;
+    const long long *rowcount = (const long long *)d_nsel;
+    if (ps.n > 0) {
+        if (sel)
+            return TDP_ERR_INVALID_ARG; // predicates over a row list: filter first
+        tdp_status st = filter_rows(ps, n, (const long long *)d_nsel, fsel, n, fcount, nullptr, fws, d_status, s);
+        if (st != TDP_OK)
+            return st;
+        rowsel = fsel;
+        rowcount = fcount;
+    }
+    KeyPack kp = make_keypack(ks);
+    int grid = (int)std::max(1ll, std::min<long long>((n + 255) / 256, (long long)num_sms() * 8));
+    if (n > 0)
+        pack_keys_kernel<K><<<grid, 256, 0, s>>>(ks, kp, n, rowsel, rowcount, pk, pr, d_status);
+    tdp_status st = radix_sort_pairs<K>(pk, pr, n, rowcount, key_bits, sk, sr, rws, rws_bytes, d_status, s);
+    if (st != TDP_OK)
+        return st;
+    cudaMemsetAsync(d_ngroups, 0, 8, s);
+    if (n == 0)
+        return launch_status();
+    cudaMemsetAsync(segws, 0, seg_ws(n), s);
+    long long tiles = (n + SR_TILE - 1) / SR_TILE;
+    seg_reduce_kernel<K><<<(unsigned)tiles, SR_THREADS, 0, s>>>(
+        sk, sr, n, rowcount, ks, kp, as, out, capacity, (long long *)d_ngroups, (SegRec *)(segws + 256),
+        (unsigned *)segws, d_status, spin_limit());
+    return launch_status();
+}
+
+tdp_status sort_groupby_run(const PredSet &ps, const KeySet &ks, int key_bits, const AggSet &as, long long n,
+                            const int32_t *sel, const int64_t *d_nsel, const DenseOut &out, long long capacity,
+                            int64_t *d_ngroups, void *ws, size_t ws_bytes, int32_t *d_status, cudaStream_t s)
+{
+    if (key_bits <= 32)
+        return sort_groupby_impl<uint32_t>(ps, ks, key_bits, as, n, sel, d_nsel, out, capacity, d_ngroups, ws,
+                                           ws_bytes, d_status, s);
+    return sort_groupby_impl<unsigned long long>(ps, ks, key_bits, as, n, sel, d_nsel, out, capacity, d_ngroups, ws,
+                                                 ws_bytes, d_status, s);
+}
+
+} // namespace tdp

@@ -1,0 +1,293 @@
+// K3: onesweep LSD radix sort of (key, uint32 value) pairs, 8-bit digits.
+//
+//  1. One histogram pass reads every key once and counts all digit positions
+//     (per-block shared-memory histograms, warp-aggregated with match_any so
+//     skewed digits do not serialise on one counter).
+//  2. A 256-thread kernel turns each digit position's histogram into
+//     exclusive global offsets.
+//  3. One scatter pass per digit.  A tile of 4096 pairs is ranked in shared
+//     memory (each warp ranks its 512 pairs stably with match_any + popc),
+//     publishes its per-digit counts, and every one of the 256 threads finds
+//     its digit's offset by decoupled look-back over earlier tiles (tile ids
+//     from an atomic ticket; waits bounded).  Pairs are staged in shared
+//     memory in digit order so that the global writes of a digit run are
+//     contiguous.
+#include "radix.cuh"
+
+namespace tdp {
+
+constexpr unsigned RS_AGG = 1u << 30;
+constexpr unsigned RS_INC = 2u << 30;
+constexpr unsigned RS_VAL = (1u << 30) - 1;
+
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) radix_hist_kernel(const K *__restrict__ keys, long long n_max,
+                                                                const long long *d_n, int passes,
+                                                                unsigned *__restrict__ hist)
+{
+    __shared__ unsigned sh[8 * 256];
+    for (int i = threadIdx.x; i < passes * 256; i += RS_THREADS)
+        sh[i] = 0;
+    __syncthreads();
+    const long long n = d_n ? min(*d_n, n_max) : n_max;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    for (long long base = ((long long)blockIdx.x * RS_WARPS + warp) * 32; base < n;
+         base += (long long)gridDim.x * RS_THREADS) {
+        long long i = base + lane;
+        bool valid = i < n;
+        K k = valid ? keys[i] : (K)0;
+        for (int p = 0; p < passes; p++) {
+            unsigned d = valid ? (unsigned)((k >> (8 * p)) & 0xff) : 0x100u;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid && (peers & lt) == 0)
+                atomicAdd(&sh[p * 256 + d], __popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += RS_THREADS)
+        if (sh[i])
+            atomicAdd(&hist[i], sh[i]);
+}
+
+// Exclusive scan of 256 values held one per thread (256 threads).
+__device__ __forceinline__ unsigned block_excl_scan_256(unsigned v, unsigned *s_tmp /* [8] */, unsigned *total)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += u;
+    }
+    if (lane == 31)
+        s_tmp[warp] = incl;
+    __syncthreads();
+    unsigned wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+        unsigned t = s_tmp[w];
+        wpre += w < warp ? t : 0;
+        tot += t;
+    }
+    __syncthreads();
+    if (total)
+        *total = tot;
+    return wpre + incl - v;
+}
+
+__global__ void radix_hist_scan_kernel(unsigned *hist)
+{
+    __shared__ unsigned tmp[8];
+    unsigned *h = hist + blockIdx.x * 256;
+    unsigned v = h[threadIdx.x];
+    unsigned e = block_excl_scan_256(v, tmp, nullptr);
+    h[threadIdx.x] = e;
+}
+
+__device__ __forceinline__ unsigned rs_wait(const unsigned *w, uint32_t limit, int32_t *d_status, bool *timed_out)
+{
+    unsigned s = ld_relaxed_u32(w);
+    uint32_t polls = 0;
+    while ((s >> 30) == 0) {
+        if (polls++ >= limit) {
+            set_status(d_status, TDP_ERR_TIMEOUT);
+            *timed_out = true;
+            return s;
+        }
+        __nanosleep(polls < 64 ? 20 : 200);
+        s = ld_relaxed_u32(w);
+    }
+    return s;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__restrict__ kin,
+                                                                   const uint32_t *__restrict__ vin,
+                                                                   K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                                   long long n_max, const long long *d_n, int shift,
+                                                                   const unsigned *__restrict__ offsets,
+                                                                   unsigned *status, unsigned *ticket,
+                                                                   int32_t *d_status, uint32_t limit)
+{
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    K *s_keys = (K *)rs_smem;
+    uint32_t *s_vals = (uint32_t *)(s_keys + RS_TILE);
+    unsigned *s_whist = s_vals + RS_TILE; // [RS_WARPS][257]
+    __shared__ unsigned s_dstart[256];
+    __shared__ unsigned s_glob[256];
+    __shared__ unsigned s_tmp[8];
+    __shared__ long long s_tile;
+
+    if (threadIdx.x == 0)
+        s_tile = atomicAdd(ticket, 1u);
+    for (int i = threadIdx.x; i < RS_WARPS * 257; i += RS_THREADS)
+        s_whist[i] = 0;
+    __syncthreads();
+    const long long tile = s_tile;
+    const long long n = d_n ? min(*d_n, n_max) : n_max;
+    const long long tile_base = tile * RS_TILE;
+    if (tile_base >= n)
+        return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const long long wb = tile_base + (long long)warp * (RS_ITEMS * 32);
+    unsigned *wh = s_whist + warp * 257;
+
+    K k[RS_ITEMS];
+    uint32_t v[RS_ITEMS];
+    unsigned short dig[RS_ITEMS], rank[RS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+        long long idx = wb + i * 32 + lane;
+        bool valid = idx < n;
+        k[i] = valid ? kin[idx] : (K)0;
+        v[i] = valid ? vin[idx] : 0u;
+        dig[i] = valid ? (unsigned short)((k[i] >> shift) & 0xff) : (unsigned short)256;
+    }
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+        unsigned peers = __match_any_sync(0xffffffffu, (unsigned)dig[i]);
+        unsigned base = wh[dig[i]];
+        rank[i] = (unsigned short)(base + __popc(peers & lt));
+        __syncwarp();
+        if ((peers & lt) == 0)
+            wh[dig[i]] = base + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit d = threadIdx.x: exclusive prefix over warps and tile count
+    const int d = threadIdx.x;
+    unsigned cnt = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; w++) {
+        unsigned c = s_whist[w * 257 + d];
+        s_whist[w * 257 + d] = cnt;
+        cnt += c;
+    }
+    unsigned dstart = block_excl_scan_256(cnt, s_tmp, nullptr);
+    s_dstart[d] = dstart;
+    // decoupled look-back for this digit
+    unsigned excl = 0;
+    unsigned *my = status + tile * 256 + d;
+    if (tile == 0) {
+        st_relaxed_u32(my, RS_INC | cnt);
+    } else {
+        st_relaxed_u32(my, RS_AGG | cnt);
+        long long t = tile - 1;
+        while (t >= 0) {
+            bool to = false;
+            unsigned s = rs_wait(status + t * 256 + d, limit, d_status, &to);
+            excl += s & RS_VAL;
+            if ((s >> 30) == 2 || to)
+                break;
+            t--;
+        }
+        st_relaxed_u32(my, RS_INC | ((excl + cnt) & RS_VAL));
+    }
+    s_glob[d] = offsets[d] + excl;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+        if (dig[i] < 256) {
+            unsigned lp = s_dstart[dig[i]] + s_whist[warp * 257 + dig[i]] + rank[i];
+            s_keys[lp] = k[i];
+            s_vals[lp] = v[i];
+        }
+    }
+    __syncthreads();
+    const int m = (int)min((long long)RS_TILE, n - tile_base);
+    for (int j = threadIdx.x; j < m; j += RS_THREADS) {
+        K key = s_keys[j];
+        unsigned dd = (unsigned)((key >> shift) & 0xff);
+        long long g = (long long)s_glob[dd] + (j - (long long)s_dstart[dd]);
+        kout[g] = key;
+        vout[g] = s_vals[j];
+    }
+}
+
+size_t radix_ws_bytes(long long n, int key_bits, int key_bytes)
+{
+    int P = radix_passes(key_bits);
+    long long tiles = (n + RS_TILE - 1) / RS_TILE;
+    size_t b = align_up((size_t)P * 256 * 4, 256) + 256 + align_up((size_t)P * tiles * 256 * 4, 256);
+    b += align_up((size_t)n * key_bytes, 256) + align_up((size_t)n * 4, 256);
+    return b;
+}
+
+template <typename K>
+tdp_status radix_sort_pairs(const K *keys_in, const uint32_t *vals_in, long long n_max, const long long *d_n,
+                            int key_bits, K *keys_out, uint32_t *vals_out, void *ws, size_t ws_bytes,
+                            int32_t *d_status, cudaStream_t s)
+{
+    if (key_bits < 1 || key_bits > (int)(8 * sizeof(K)) || n_max < 0 || n_max >= (1ll << 30))
+        return TDP_ERR_INVALID_ARG;
+    if (n_max == 0)
+        return TDP_OK;
+    if (ws_bytes < radix_ws_bytes(n_max, key_bits, sizeof(K)))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    const int P = radix_passes(key_bits);
+    const long long tiles = (n_max + RS_TILE - 1) / RS_TILE;
+    char *p = (char *)ws;
+    unsigned *hist = (unsigned *)p;
+    p += align_up((size_t)P * 256 * 4, 256);
+    unsigned *tickets = (unsigned *)p;
+    p += 256;
+    unsigned *status = (unsigned *)p;
+    p += align_up((size_t)P * tiles * 256 * 4, 256);
+    K *tmp_k = (K *)p;
+    p += align_up((size_t)n_max * sizeof(K), 256);
+    uint32_t *tmp_v = (uint32_t *)p;
+    cudaMemsetAsync(ws, 0, (size_t)((char *)tmp_k - (char *)ws), s);
+    int hist_blocks = (int)std::min<long long>((n_max + RS_THREADS - 1) / RS_THREADS, (long long)num_sms() * 4);
+    radix_hist_kernel<K><<<hist_blocks, RS_THREADS, 0, s>>>(keys_in, n_max, d_n, P, hist);
+    radix_hist_scan_kernel<<<P, 256, 0, s>>>(hist);
+    const size_t smem = (size_t)RS_TILE * (sizeof(K) + 4) + RS_WARPS * 257 * 4;
+    if (cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return TDP_ERR_CUDA;
+    const K *src_k = keys_in;
+    const uint32_t *src_v = vals_in;
+    for (int pass = 0; pass < P; pass++) {
+        bool to_out = ((P - 1 - pass) % 2) == 0;
+        K *dk = to_out ? keys_out : tmp_k;
+        uint32_t *dv = to_out ? vals_out : tmp_v;
+        radix_scatter_kernel<K><<<(unsigned)tiles, RS_THREADS, smem, s>>>(
+            src_k, src_v, dk, dv, n_max, d_n, 8 * pass, hist + pass * 256, status + (size_t)pass * tiles * 256,
+            tickets + pass, d_status, spin_limit());
+        src_k = dk;
+        src_v = dv;
+    }
+    return launch_status();
+}
+
+template tdp_status radix_sort_pairs<uint32_t>(const uint32_t *, const uint32_t *, long long, const long long *, int,
+                                                 uint32_t *, uint32_t *, void *, size_t, int32_t *, cudaStream_t);
+template tdp_status radix_sort_pairs<unsigned long long>(const unsigned long long *, const uint32_t *, long long,
+                                                           const long long *, int, unsigned long long *, uint32_t *,
+                                                           void *, size_t, int32_t *, cudaStream_t);
+
+} // namespace tdp
+
+using namespace tdp;
+
+extern "C" size_t tdp_sort_pairs_workspace(int64_t n, int32_t key_bits)
+{
+    if (key_bits < 1 || key_bits > 64 || n < 0)
+        return 0;
+    return radix_ws_bytes(n, key_bits, 8);
+}
+
+extern "C" tdp_status tdp_sort_pairs(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t key_bits,
+                                     uint64_t *keys_out, uint32_t *vals_out, void *ws, size_t ws_bytes,
+                                     int32_t *d_status, tdp_stream_t stream)
+{
+    if (n < 0 || (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out || !ws)))
+        return TDP_ERR_INVALID_ARG;
+    if (keys_in == (const uint64_t *)keys_out || vals_in == (const uint32_t *)vals_out)
+        return TDP_ERR_INVALID_ARG;
+    return radix_sort_pairs<unsigned long long>((const unsigned long long *)keys_in, vals_in, n, nullptr, key_bits,
+                                                (unsigned long long *)keys_out, vals_out, ws, ws_bytes, d_status,
+                                                (cudaStream_t)stream);
+}

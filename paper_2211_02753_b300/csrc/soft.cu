@@ -1,0 +1,287 @@
+// K9/K10: soft filter and soft grouped aggregation with hand-written adjoints
+// (Sec. 4: logistic relaxation of a predicate, soft_count / soft_groupby).
+//
+// Rows stream through once per call with 16-byte loads (x, v: float4; gid:
+// int4).  Each block owns a contiguous chunk of rows and accumulates its
+// per-group partial sums in shared memory; the partials of all blocks are
+// then added in block order in float64 by a second small kernel, so the only
+// fp32 summation is over the ~n/(blocks*G) rows a block sees per group.  The
+// mask m = sigmoid((x - theta[g]) / tau) is recomputed in the backward pass,
+// never stored; m(1-m) is evaluated as e/(1+e)^2 with e = exp(-|z|), which has
+// no cancellation when m is close to 1.
+#include "common.cuh"
+
+namespace tdp {
+
+constexpr int SA_THREADS = 512;
+constexpr int SA_MAX_GROUPS = 8192;
+
+struct Sig {
+    float m;  // sigmoid(z)
+    float dm; // m (1 - m)
+};
+
+__device__ __forceinline__ Sig sigmoid_pair(float z)
+{
+    float e = expf(-fabsf(z));
+    float r = 1.0f / (1.0f + e);
+    Sig s;
+    s.m = z >= 0.f ? r : e * r;
+    s.dm = e * r * r;
+    return s;
+}
+
+enum SoftMode { MODE_AGG_FWD = 0, MODE_AGG_BWD = 1, MODE_FILTER_BWD = 2 };
+
+// Per-row work of the three reduction modes.  Accumulates into smem
+// acc0 (and acc1 for the forward COUNT).
+template <int MODE>
+__device__ __forceinline__ void soft_row(float x, float v, int g, float gm, const float *s_theta, const float *s_g0,
+                                         const float *s_g1, float inv_tau, float *acc0, float *acc1, float *gx,
+                                         float *gv, long long i, int G)
+{
+    if ((unsigned)g >= (unsigned)G) // out-of-range group id: row ignored
+        return;
+    Sig s = sigmoid_pair((x - s_theta[g]) * inv_tau);
+    if (MODE == MODE_AGG_FWD) {
+        atomicAdd(&acc0[g], v * s.m);
+        atomicAdd(&acc1[g], s.m);
+    } else if (MODE == MODE_AGG_BWD) {
+        float gS = s_g0[g];
+        float w = (gS * v + s_g1[g]) * s.dm;
+        atomicAdd(&acc0[g], w);
+        if (gx)
+            gx[i] = w * inv_tau;
+        if (gv)
+            gv[i] = gS * s.m;
+    } else {
+        float w = gm * s.dm;
+        atomicAdd(&acc0[g], w);
+        if (gx)
+            gx[i] = w * inv_tau;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(SA_THREADS) soft_reduce_kernel(const float *__restrict__ x,
+                                                                 const float *__restrict__ v,
+                                                                 const int32_t *__restrict__ gid,
+                                                                 const float *__restrict__ theta,
+                                                                 const float *__restrict__ g0,
+                                                                 const float *__restrict__ g1, float inv_tau,
+                                                                 long long n, int G, long long chunk,
+                                                                 float *__restrict__ partial, float *gx, float *gv)
+{
+    extern __shared__ float sm[];
+    float *s_theta = sm;
+    float *acc0 = sm + G;
+    float *acc1 = sm + 2 * G;  // forward only
+    float *s_g0 = sm + 2 * G;  // backward only
+    float *s_g1 = sm + 3 * G;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        s_theta[g] = theta[g];
+        acc0[g] = 0.f;
+        if (MODE == MODE_AGG_FWD)
+            acc1[g] = 0.f;
+        if (MODE == MODE_AGG_BWD) {
+            s_g0[g] = g0[g];
+            s_g1[g] = g1[g];
+        }
+    }
+    __syncthreads();
+    const long long beg = (long long)blockIdx.x * chunk;
+    const long long end = min(n, beg + chunk);
+    const bool vec = (((uintptr_t)x | (uintptr_t)gid | (uintptr_t)(MODE == MODE_FILTER_BWD ? g0 : v)) % 16) == 0;
+    const float *aux = MODE == MODE_FILTER_BWD ? g0 : v; // v, or grad_mask for the filter adjoint
+    long long tail = beg;
+    if (vec) {
+        const long long nvec = (end - beg) / 4;
+        for (long long q = threadIdx.x; q < nvec; q += SA_THREADS) {
+            const long long i = beg + 4 * q;
+            float4 xx = __ldg((const float4 *)(x + i));
+            float4 aa = __ldg((const float4 *)(aux + i));
+            int4 gg = __ldg((const int4 *)(gid + i));
+            soft_row<MODE>(xx.x, aa.x, gg.x, aa.x, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i, G);
+            soft_row<MODE>(xx.y, aa.y, gg.y, aa.y, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 1, G);
+            soft_row<MODE>(xx.z, aa.z, gg.z, aa.z, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 2, G);
+            soft_row<MODE>(xx.w, aa.w, gg.w, aa.w, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 3, G);
+        }
+        tail = beg + 4 * nvec;
+    }
+    for (long long r = tail + threadIdx.x; r < end; r += SA_THREADS)
+        soft_row<MODE>(x[r], aux[r], gid[r], aux[r], s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, r, G);
+    __syncthreads();
+    float *out = partial + (size_t)blockIdx.x * (MODE == MODE_AGG_FWD ? 2 : 1) * G;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        out[g] = acc0[g];
+        if (MODE == MODE_AGG_FWD)
+            out[G + g] = acc1[g];
+    }
+}
+
+// out[k][g] = scale * sum_b partial[b][k][g], summed over b in order, float64.
+__global__ void soft_combine_kernel(const float *__restrict__ partial, int nblocks, int G, int K, float scale,
+                                    float *__restrict__ out0, float *__restrict__ out1)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K * G)
+        return;
+    double acc = 0.0;
+    for (int b = 0; b < nblocks; b++)
+        acc += (double)partial[(size_t)b * K * G + t];
+    acc *= (double)scale;
+    if (t < G)
+        out0[t] = (float)acc;
+    else
+        out1[t - G] = (float)acc;
+}
+
+__global__ void soft_filter_fwd_kernel(const float *__restrict__ x, const int32_t *__restrict__ gid,
+                                       const float *__restrict__ theta, float inv_tau, long long n,
+                                       float *__restrict__ mask)
+{
+    long long i = 4ll * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const bool vec = (((uintptr_t)x | (uintptr_t)gid | (uintptr_t)mask) % 16) == 0;
+    if (vec && i + 3 < n) {
+        float4 xx = __ldg((const float4 *)(x + i));
+        int4 gg = __ldg((const int4 *)(gid + i));
+        float4 o;
+        o.x = sigmoid_pair((xx.x - __ldg(theta + gg.x)) * inv_tau).m;
+        o.y = sigmoid_pair((xx.y - __ldg(theta + gg.y)) * inv_tau).m;
+        o.z = sigmoid_pair((xx.z - __ldg(theta + gg.z)) * inv_tau).m;
+        o.w = sigmoid_pair((xx.w - __ldg(theta + gg.w)) * inv_tau).m;
+        *(float4 *)(mask + i) = o;
+    } else {
+        for (long long r = i; r < min(n, i + 4); r++)
+            mask[r] = sigmoid_pair((x[r] - theta[gid[r]]) * inv_tau).m;
+    }
+}
+
+struct SoftGrid {
+    int blocks;
+    long long chunk;
+    size_t smem;
+};
+
+static SoftGrid soft_grid(long long n, int G, int nbuf)
+{
+    SoftGrid sg;
+    sg.smem = (size_t)nbuf * G * sizeof(float);
+    int per_sm = sg.smem <= 48 * 1024 ? 2 : 1;
+    long long want = (n + 4ll * SA_THREADS * 8 - 1) / (4ll * SA_THREADS * 8);
+    long long maxb = (long long)num_sms() * per_sm;
+    sg.blocks = (int)std::max(1ll, std::min(want, maxb));
+    sg.chunk = (n + sg.blocks - 1) / sg.blocks;
+    sg.chunk = (sg.chunk + 3) / 4 * 4;
+    return sg;
+}
+
+static tdp_status set_smem(const void *fn, size_t smem)
+{
+    if (smem > 48 * 1024)
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return TDP_ERR_CUDA;
+    return TDP_OK;
+}
+
+} // namespace tdp
+
+using namespace tdp;
+
+extern "C" size_t tdp_soft_workspace(int64_t n, int32_t n_groups)
+{
+    (void)n;
+    // per-block partials: at most 2 blocks per SM, 2 arrays of n_groups floats
+    return align_up((size_t)2 * num_sms() * 2 * (size_t)std::max(1, n_groups) * sizeof(float), 256);
+}
+
+static tdp_status soft_check(const float *x, const int32_t *gid, const float *theta, float tau, int64_t n, int32_t G)
+{
+    if (n < 0 || G <= 0 || G > SA_MAX_GROUPS || !(tau > 0.f) || !theta)
+        return TDP_ERR_INVALID_ARG;
+    if (n > 0 && (!x || !gid))
+        return TDP_ERR_INVALID_ARG;
+    return TDP_OK;
+}
+
+extern "C" tdp_status tdp_soft_filter_fwd(const float *x, const int32_t *gid, const float *theta, float tau,
+                                          int64_t n, float *mask, tdp_stream_t stream)
+{
+    if (n < 0 || !(tau > 0.f) || (n > 0 && (!x || !gid || !theta || !mask)))
+        return TDP_ERR_INVALID_ARG;
+    if (n == 0)
+        return TDP_OK;
+    long long threads = (n + 3) / 4;
+    soft_filter_fwd_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        x, gid, theta, 1.0f / tau, n, mask);
+    return launch_status();
+}
+
+extern "C" tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int32_t *gid, const float *theta,
+                                       float tau, int64_t n, int32_t G, float *sum, float *cnt, void *ws,
+                                       size_t ws_bytes, tdp_stream_t stream)
+{
+    tdp_status st = soft_check(x, gid, theta, tau, n, G);
+    if (st != TDP_OK)
+        return st;
+    if (!sum || !cnt || (n > 0 && !v))
+        return TDP_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < tdp_soft_workspace(n, G))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    SoftGrid sg = soft_grid(n, G, 3);
+    if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_FWD>, sg.smem)) != TDP_OK)
+        return st;
+    float *partial = (float *)ws;
+    soft_reduce_kernel<MODE_AGG_FWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
+        x, v, gid, theta, nullptr, nullptr, 1.0f / tau, n, G, sg.chunk, partial, nullptr, nullptr);
+    soft_combine_kernel<<<(2 * G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
+    return launch_status();
+}
+
+extern "C" tdp_status tdp_soft_agg_bwd(const float *x, const float *v, const int32_t *gid, const float *theta,
+                                       float tau, int64_t n, int32_t G, const float *gsum, const float *gcnt,
+                                       float *grad_theta, float *grad_v, float *grad_x, void *ws, size_t ws_bytes,
+                                       tdp_stream_t stream)
+{
+    tdp_status st = soft_check(x, gid, theta, tau, n, G);
+    if (st != TDP_OK)
+        return st;
+    if (!gsum || !gcnt || !grad_theta || (n > 0 && !v))
+        return TDP_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < tdp_soft_workspace(n, G))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    SoftGrid sg = soft_grid(n, G, 4);
+    if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_BWD>, sg.smem)) != TDP_OK)
+        return st;
+    float *partial = (float *)ws;
+    soft_reduce_kernel<MODE_AGG_BWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
+        x, v, gid, theta, gsum, gcnt, 1.0f / tau, n, G, sg.chunk, partial, grad_x, grad_v);
+    soft_combine_kernel<<<(G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau, grad_theta,
+                                                        nullptr);
+    return launch_status();
+}
+
+extern "C" tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, const float *theta, float tau,
+                                          int64_t n, int32_t G, const float *grad_mask, float *grad_x,
+                                          float *grad_theta, void *ws, size_t ws_bytes, tdp_stream_t stream)
+{
+    tdp_status st = soft_check(x, gid, theta, tau, n, G);
+    if (st != TDP_OK)
+        return st;
+    if (!grad_theta || (n > 0 && !grad_mask))
+        return TDP_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < tdp_soft_workspace(n, G))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    SoftGrid sg = soft_grid(n, G, 2);
+    if ((st = set_smem((const void *)soft_reduce_kernel<MODE_FILTER_BWD>, sg.smem)) != TDP_OK)
+        return st;
+    float *partial = (float *)ws;
+    soft_reduce_kernel<MODE_FILTER_BWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
+        x, nullptr, gid, theta, grad_mask, nullptr, 1.0f / tau, n, G, sg.chunk, partial, grad_x, nullptr);
+    soft_combine_kernel<<<(G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau, grad_theta,
+                                                        nullptr);
+    return launch_status();
+}

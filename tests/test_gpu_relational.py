@@ -1,0 +1,295 @@
+"""GPU parity of the relational operators against the CPU oracle: bit-exact
+(row ids, keys, int64 aggregates, order).  Inputs are seeded (gen) and the
+expected values come from oracle/ only."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+from oracle import relational as R
+from paper_2211_02753_b300 import ops
+from paper_2211_02753_b300._lib import TdpError
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def np_(t, n=None):
+    a = t.cpu().numpy()
+    return a if n is None else a[:n]
+
+
+def _table(n, seed):
+    r = np.random.default_rng(seed)
+    return {
+        "a8": r.integers(-128, 128, n).astype(np.int8),
+        "u8": r.integers(0, 256, n).astype(np.uint8),
+        "b32": r.integers(-1000, 1000, n).astype(np.int32),
+        "c64": r.integers(-10**12, 10**12, n).astype(np.int64),
+        "k1": r.integers(0, 3, n).astype(np.int8),
+        "k2": r.integers(-2, 3, n).astype(np.int32),
+        "v": r.integers(-10**9, 10**9, n).astype(np.int64),
+        "w": r.integers(0, 11, n).astype(np.int64),
+    }
+
+
+SIZES = [0, 1, 3, 4095, 4096, 4097, 70001]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_filter_matches_oracle(n):
+    t = _table(n, n)
+    names = ["a8", "u8", "b32", "c64"]
+    cols = [cu(t[k]) for k in names]
+    preds = [(0, ">", -60), (1, "!=", 7), (2, "<=", 500), (3, ">=", -5 * 10**11)]
+    out = ops.filter(cols, preds, gather=[0, 3])
+    ops.check(out["status"])
+    ref = R.filter([(t[names[c]], op, lit) for c, op, lit in preds], n)
+    cnt = int(out["count"].item())
+    assert cnt == len(ref)
+    assert np.array_equal(np_(out["rowid"], cnt), ref)
+    assert np.array_equal(np_(out["gathered"][0], cnt), t["a8"][ref])
+    assert np.array_equal(np_(out["gathered"][1], cnt), t["c64"][ref])
+
+
+@pytest.mark.parametrize("op", ["<", "<=", ">", ">=", "==", "!="])
+def test_filter_each_comparison_and_no_predicate(op):
+    n = 20000
+    t = _table(n, 7)
+    cols = [cu(t["b32"])]
+    out = ops.filter(cols, [(0, op, 3)])
+    ref = R.filter([(t["b32"], op, 3)], n)
+    assert np.array_equal(np_(out["rowid"], int(out["count"].item())), ref)
+    out = ops.filter(cols, [])
+    assert int(out["count"].item()) == n
+
+
+def test_filter_unaligned_columns_and_capacity():
+    n = 10001
+    t = _table(n + 1, 3)
+    base = cu(t["b32"])
+    col = base[1:]  # 4-byte offset: the scalar load path
+    assert col.data_ptr() % 16 != 0
+    ref = R.filter([(t["b32"][1:], "<", 0)], n)
+    out = ops.filter([col], [(0, "<", 0)])
+    assert np.array_equal(np_(out["rowid"], int(out["count"].item())), ref)
+    cap = len(ref) // 2
+    out = ops.filter([col], [(0, "<", 0)], capacity=cap)
+    assert int(out["count"].item()) == len(ref)
+    assert int(out["status"].item()) & 4
+    assert np.array_equal(np_(out["rowid"], cap), ref[:cap])
+
+
+def test_filter_config1_60m_rows():
+    n = 60_000_000
+    t = gen.fact_table(n, 15_000_000, gen.BASE_SEED + 1, cols=("date",))
+    out = ops.filter([cu(t["date"])], [(0, "<=", 2460)])
+    ops.check(out["status"])
+    ref = R.filter([(t["date"], "<=", 2460)], n)
+    cnt = int(out["count"].item())
+    assert cnt == len(ref)
+    got = np_(out["rowid"], cnt)
+    assert np.array_equal(got, ref)
+
+
+AGGS6 = [("count", None, None, None), ("sum", 6, None, None), ("sum_mul_kminus", 6, 7, 100),
+         ("avg", 6, None, None), ("min", 6, None, None), ("max", 6, None, None)]
+
+
+def _oracle_aggs(t, names):
+    out = []
+    for op, a, b, k in AGGS6:
+        out.append((op, t[names[a]] if a is not None else None, t[names[b]] if b is not None else None, k))
+    return out
+
+
+@pytest.mark.parametrize("strategy", ["small_domain", "sort"])
+@pytest.mark.parametrize("n", [0, 1, 4097, 70001])
+def test_groupby_matches_oracle(strategy, n):
+    t = _table(n, 100 + n)
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w"]
+    cols = [cu(t[k]) for k in names]
+    cols[4] = ops.Col(cols[4], 0, 2)
+    cols[5] = ops.Col(cols[5], -2, 2)
+    preds = [(2, "<", 700)]
+    out = ops.groupby_agg(cols, [4, 5], AGGS6, preds=preds, strategy=strategy)
+    ops.check(out["status"])
+    sel = R.filter([(t["b32"], "<", 700)], n)
+    rk, ra = R.groupby([t["k1"], t["k2"]], _oracle_aggs(t, names), n, sel=sel)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+    assert np.array_equal(np_(out["keys"][1], g), rk[:, 1])
+    for j in range(len(AGGS6)):
+        assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), AGGS6[j]
+
+
+@pytest.mark.parametrize("n", [5000, 300001])
+def test_groupby_sort_unbounded_keys_and_row_list(n):
+    """Sort strategy with keys without bounds (sign-flipped radix fields), a
+    64-bit packed key (int32 + int8 + int32 = 72 bits is too wide, so use
+    int32 + int8), and a row-id list input."""
+    t = _table(n, 5 + n)
+    t["b32"] = (t["b32"] // 7).astype(np.int32)  # many duplicates, negative keys
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w"]
+    cols = [cu(t[k]) for k in names]
+    sel = R.filter([(t["c64"], ">", 0)], n)
+    out = ops.groupby_agg(cols, [2, 0], AGGS6, sel=cu(sel), strategy="sort")
+    ops.check(out["status"])
+    rk, ra = R.groupby([t["b32"], t["a8"]], _oracle_aggs(t, names), n, sel=sel)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+    assert np.array_equal(np_(out["keys"][1], g), rk[:, 1])
+    for j in range(len(AGGS6)):
+        assert np.array_equal(np_(out["aggs"][j], g), ra[:, j])
+
+
+def test_groupby_config1_60k_both_strategies():
+    n = 60000
+    t = gen.fact_table(n, 15000, gen.BASE_SEED + 0)
+    names = ["key", "flag", "status", "qty", "price", "disc", "date"]
+    cols = [cu(t[k]) for k in names]
+    cols[1] = ops.Col(cols[1], 0, 2)
+    cols[2] = ops.Col(cols[2], 0, 1)
+    aggs = [("sum", 3), ("sum", 4), ("sum_mul_kminus", 4, 5, 100), ("count",), ("avg", 3)]
+    sel = R.filter([(t["date"], "<=", 2460)], n)
+    rk, ra = R.groupby([t["flag"], t["status"]],
+                       [("sum", t["qty"], None, None), ("sum", t["price"], None, None),
+                        ("sum_mul_kminus", t["price"], t["disc"], 100), ("count", None, None, None),
+                        ("avg", t["qty"], None, None)], n, sel=sel)
+    for strategy in ("small_domain", "sort"):
+        out = ops.groupby_agg(cols, [1, 2], aggs, preds=[(6, "<=", 2460)], strategy=strategy)
+        ops.check(out["status"])
+        g = int(out["ngroups"].item())
+        assert g == 6
+        assert np.array_equal(np.stack([np_(k, g) for k in out["keys"]], 1), rk)
+        assert np.array_equal(np.stack([np_(a, g) for a in out["aggs"]], 1), ra)
+
+
+def test_groupby_config1_60m_invariants():
+    n = 60_000_000
+    t = gen.fact_table(n, 15_000_000, gen.BASE_SEED + 1, cols=("flag", "status", "qty", "price", "disc", "date"))
+    names = ["flag", "status", "qty", "price", "disc", "date"]
+    cols = [cu(t[k]) for k in names]
+    cols[0] = ops.Col(cols[0], 0, 2)
+    cols[1] = ops.Col(cols[1], 0, 1)
+    aggs = [("count",), ("sum", 2), ("sum_mul_kminus", 3, 4, 100)]
+    out = ops.groupby_agg(cols, [0, 1], aggs, preds=[(5, "<=", 2460)], strategy="small_domain")
+    ops.check(out["status"])
+    keep = t["date"] <= 2460
+    g = int(out["ngroups"].item())
+    cnt, sq, sdp = (np_(a, g) for a in out["aggs"])
+    assert cnt.sum() == keep.sum()
+    assert sq.sum() == t["qty"][keep].sum()
+    assert sdp.sum() == (t["price"][keep] * (100 - t["disc"][keep])).sum()
+    # per-group sample: group (flag=1, status=0) one by one
+    m = keep & (t["flag"] == 1) & (t["status"] == 0)
+    j = 2 * 1 + 0
+    assert cnt[j] == m.sum() and sq[j] == t["qty"][m].sum()
+
+
+@pytest.mark.parametrize("n,bits", [(0, 8), (1, 8), (4096, 3), (4097, 24), (200000, 24), (123457, 64), (50000, 40)])
+def test_sort_pairs_matches_oracle(n, bits):
+    r = np.random.default_rng(n + bits)
+    hi = (1 << bits) if bits < 64 else (1 << 63)
+    keys = r.integers(0, hi, n, dtype=np.uint64) if bits < 64 else r.integers(0, 2**63, n).astype(np.uint64) * 2 + (r.integers(0, 2, n).astype(np.uint64))
+    if n > 10:
+        keys[: n // 3] = keys[0]  # long run of equal keys (stability)
+    vals = np.arange(n, dtype=np.uint32)
+    ko, vo, st = ops.sort_pairs(cu(keys.view(np.int64)), cu(vals.view(np.int32)), key_bits=bits)
+    ops.check(st)
+    ek, ev = R.sort_pairs(keys, vals)
+    assert np.array_equal(np_(ko).view(np.uint64), ek)
+    assert np.array_equal(np_(vo).view(np.uint32), ev)
+
+
+@pytest.mark.parametrize("nb,np_rows", [(1, 1), (1000, 5000), (300000, 1000003)])
+def test_join_matches_oracle(nb, np_rows):
+    r = np.random.default_rng(nb)
+    bkey = (r.permutation(nb) * 2 + 1).astype(np.int32)
+    bseg = r.integers(0, 5, nb).astype(np.int8)
+    bpay = r.integers(-10**6, 10**6, nb).astype(np.int32)
+    pkey = r.integers(0, 2 * nb + 2, np_rows).astype(np.int32)
+    pdate = r.integers(0, 2557, np_rows).astype(np.int32)
+    pval = r.integers(0, 10**9, np_rows).astype(np.int64)
+    bcols = [cu(bkey), cu(bseg), cu(bpay)]
+    pcols = [cu(pkey), cu(pdate), cu(pval)]
+    table, st = ops.join_build(bcols, 0, payload_col=2, preds=[(1, "==", 2)])
+    out = ops.join_probe(table, pcols, 0, preds=[(1, ">", 1200)], gather=[2], status=st)
+    ops.check(st)
+    bsel = R.filter([(bseg, "==", 2)], nb)
+    psel = R.filter([(pdate, ">", 1200)], np_rows)
+    op_, ob_, dup = R.join(bkey, pkey, bsel=bsel, psel=psel)
+    assert not dup
+    c = int(out["count"].item())
+    assert c == len(op_)
+    assert np.array_equal(np_(out["probe_row"], c), op_)
+    assert np.array_equal(np_(out["payload"], c), bpay[ob_])
+    assert np.array_equal(np_(out["gathered"][0], c), pval[op_])
+    # one-call join without payload column: payload = build row id
+    out2 = ops.join([cu(bkey)], 0, [cu(pkey)], 0)
+    ops.check(out2["status"])
+    op2, ob2, _ = R.join(bkey, pkey)
+    c2 = int(out2["count"].item())
+    assert c2 == len(op2)
+    assert np.array_equal(np_(out2["probe_row"], c2), op2)
+    assert np.array_equal(np_(out2["payload"], c2), ob2)
+
+
+def test_join_duplicate_keys_and_full_table_are_flagged():
+    bkey = cu(np.array([5, 7, 5, 9], np.int32))
+    table, st = ops.join_build([bkey], 0)
+    assert int(st.item()) & 8
+    big = cu(np.arange(100, dtype=np.int32))
+    table, st = ops.join_build([big], 0, nslots=64)
+    assert int(st.item()) & 4
+    with pytest.raises(TdpError):
+        ops.join_build([big], 0, nslots=63)
+
+
+def test_join_probe_agg_matches_join_then_groupby():
+    nb, npr = 50000, 400000
+    d = gen.chain_tables(npr, nb, 5000, seed=9, n_category=1000)
+    cols_b = [cu(d["build_pk"]), cu(d["third_cat"][:nb] if len(d["third_cat"]) >= nb else np.resize(d["third_cat"], nb))]
+    cat = cols_b[1].cpu().numpy()
+    table, st = ops.join_build(cols_b, 0, payload_col=1)
+    pcols = [cu(d["probe_fk"].astype(np.int32)), cu(d["probe_payload"])]
+    out = ops.join_probe_agg(table, pcols, 0, 0, 999, [("sum", 1), ("count",)], status=st)
+    ops.check(st)
+    op_, ob_, _ = R.join(d["build_pk"], d["probe_fk"].astype(np.int32))
+    g_cat = cat[ob_]
+    rk, ra = R.groupby([g_cat.astype(np.int32)], [("sum", d["probe_payload"][op_], None, None),
+                                                  ("count", None, None, None)], len(op_))
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    assert np.array_equal(np_(out["keys"], g), rk[:, 0])
+    assert np.array_equal(np_(out["aggs"][0], g), ra[:, 0])
+    assert np.array_equal(np_(out["aggs"][1], g), ra[:, 1])
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (5, 10), (1000, 10), (2_600_000, 10), (300000, 16)])
+def test_topk_matches_oracle(n, k):
+    r = np.random.default_rng(n)
+    vals = r.integers(-50, 50, n).astype(np.int64)  # many ties
+    keys = r.permutation(n).astype(np.int32)
+    ov, okk, dk = ops.topk(cu(vals), cu(keys), k)
+    ev, ek = R.topk(vals, keys.astype(np.int64), k)
+    m = int(dk.item())
+    assert m == len(ev)
+    assert np.array_equal(np_(ov, m), ev) and np.array_equal(np_(okk, m), ek)
+
+
+def test_bounded_wait_times_out_without_hanging():
+    flag = torch.zeros(1, dtype=torch.int32, device=DEV)
+    st = ops.new_status(DEV)
+    ops.debug_wait_flag(flag, 1000, st)
+    assert int(st.item()) == 16
+    flag.fill_(1)
+    st.zero_()
+    ops.debug_wait_flag(flag, 1000, st)
+    assert int(st.item()) == 0

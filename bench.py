@@ -115,9 +115,14 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                                          "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # wait for the first sample so that the timed region is covered
+        t_end = time.time() + 10
+        while time.time() < t_end and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
 
     def stop(self, gpu_index: int):
         if self.proc is None:
@@ -392,13 +397,74 @@ def other_plans(dev, stream, hbm_peak, args):
                                      "frac_hbm": algo / (ms / 1e3) / 1e9 / hbm_peak}
     del sd, sq
     torch.cuda.empty_cache()
+    res["trainable_query_glyph_cnn"] = glyph_plan(dev, stream, args)
     return res
+
+
+def glyph_plan(dev, stream, args):
+    """Trainable glyph query: train steps/s (batch 256 grids = 4096 cells),
+    exact-query steps/s on the same GPU, and the query-level accuracy reached
+    after a fixed training budget."""
+    import torch
+    from oracle import cnn as O  # targets: the exact query on the true labels
+    from oracle import soft
+    from paper_2211_02753_b300 import cnn
+    tr_img, tr_lab = gen.glyph_grids(4096, gen.BASE_SEED + 4)
+    te_img, te_lab = gen.glyph_grids(1024, gen.BASE_SEED + 104)
+    targets = torch.from_numpy(O.targets_from_labels(tr_lab).astype(np.float32)).to(dev)
+    g_tr = torch.from_numpy(tr_img).to(dev)
+    g_te = torch.from_numpy(te_img).to(dev)
+    q = cnn.GlyphQuery(gen.cnn_params(gen.BASE_SEED + 5), dev, lr=1e-3)
+    B = 256
+    nb = 4096 // B
+
+    def step(i):
+        j = (i % nb) * B
+        return q.train_step(g_tr[j:j + B], targets[j:j + B])
+
+    for i in range(3):
+        step(i)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    n_timed = max(20, args.steps)
+    a.record(stream)
+    for i in range(n_timed):
+        step(3 + i)
+    b.record(stream)
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(b) / n_timed
+    # finish a fixed training budget, then evaluate the exact query
+    budget = 1600
+    for i in range(3 + n_timed, budget):
+        if i == 1200:
+            q.lr = 3e-4
+        step(i)
+    torch.cuda.synchronize()
+    gq = g_te[:B]
+    for _ in range(3):
+        q.exact_query(gq)
+    a.record(stream)
+    for _ in range(n_timed):
+        q.exact_query(gq)
+    b.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = a.elapsed_time(b) / n_timed
+    labels, cnt, rsum = q.exact_query(g_te)
+    ec, er = soft.exact_groupby(te_lab)
+    ok = np.all(cnt.cpu().numpy() == ec, axis=1) & np.all(rsum.cpu().numpy() == er, axis=1)
+    cell_acc = float((labels.cpu().numpy().reshape(-1, 4, 4) == te_lab).mean())
+    flops_fwd = 4096 * 2 * (26 * 26 * 32 * 9 + 24 * 24 * 64 * 288 + 9216 * 128 + 128 * 10)
+    return {"train_ms": train_ms, "train_steps_per_s": 1000.0 / train_ms, "exact_query_ms": infer_ms,
+            "exact_query_steps_per_s": 1000.0 / infer_ms, "batch_grids": B, "training_steps": budget,
+            "query_accuracy": float(ok.mean()), "cell_accuracy": cell_acc,
+            "train_tflops": 3 * flops_fwd / (train_ms / 1e3) / 1e12}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plans", default="all", choices=["all", "main"])

@@ -120,7 +120,9 @@ int32_t tdp_abi_version(void);
 /*
  * Upper bound, in polls, of every device-side wait (decoupled look-back of the
  * filter/scan/sort kernels).  A wait that runs out sets TDP_ERR_TIMEOUT and
- * the kernel carries on without hanging.  Default 1<<22.  Affects later
+ * the kernel carries on without hanging; once one wait of a launch has timed
+ * out, the other waits of that launch give up at once.  Default 1<<20 (about
+ * 0.2 s of polling).  Affects later
  * launches only.  Returns the previous value.
  */
 uint32_t tdp_set_spin_limit(uint32_t polls);
@@ -248,7 +250,8 @@ int64_t tdp_join_default_slots(int64_t n_keys);
  *   table              device uint64[nslots]; this call fills it with the
  *                      empty pattern first
  *
- * A full table (no free slot within nslots probes) sets TDP_ERR_CAPACITY.
+ * A full table (no free slot within min(nslots, 65536) probes) sets
+ * TDP_ERR_CAPACITY; a lookup that walks that far sets it too.
  */
 tdp_status tdp_join_build(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds,
                           int64_t n, const int64_t *d_n, int32_t key_col, int32_t payload_col, uint32_t flags,
@@ -326,7 +329,11 @@ tdp_status tdp_topk(const int64_t *vals, const int32_t *keys, int64_t n, const i
 
 /* ------------------------------------------------- soft (trainable) query */
 
-/* Workspace bytes for the soft aggregation / soft filter backward calls. */
+/*
+ * Workspace bytes for the soft aggregation / soft filter backward calls.
+ * The grouped soft calls take 1 <= n_groups <= 4096 and a gid outside
+ * [0, n_groups) leaves its row out of the sums.
+ */
 size_t tdp_soft_workspace(int64_t n, int32_t n_groups);
 
 /*
@@ -351,8 +358,10 @@ tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, const float *
  * Soft grouped aggregation, Sec. 4 (soft_count / soft_groupby): with
  * m_i = sigmoid((x[i] - theta[gid[i]]) / tau),
  *   sum[g] = sum_{gid[i]=g} v[i] m_i ,   cnt[g] = sum_{gid[i]=g} m_i .
- * The mask is never stored.  Per-block partials are combined in a fixed
- * order in float64.  sum, cnt: fp32[n_groups], overwritten.
+ * The mask is never stored.  Each block sums fp32 contributions over short
+ * sub-chunks (about 16 rows per group) into float64 accumulators; block
+ * partials are combined in block order in float64.  sum, cnt: fp32[n_groups],
+ * overwritten.
  */
 tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int32_t *gid, const float *theta,
                             float tau, int64_t n, int32_t n_groups, float *sum, float *cnt, void *ws,

@@ -1,0 +1,144 @@
+/*
+ * tdp_cnn.h -- C ABI of the trainable glyph query (B300, sm_103a).
+ *
+ * The paper's trainable query (Sec. 3 training loop; Sec. 4 soft operators on
+ * probability-encoded (PE) columns; Sec. 5.5 queries over image grids) runs a
+ * CNN over every cell of a grid image, turns the class probabilities (the PE
+ * column, softmax as the proxy for argmax) into a soft per-class COUNT and a
+ * soft per-row SUM of class values, and trains the CNN end to end with an MSE
+ * loss against the same query run exactly on known labels, using Adam.  At
+ * inference the exact query (argmax, integer COUNT/SUM) replaces the soft one.
+ *
+ * Network: conv3x3 1->32 + ReLU, conv3x3 32->64 + ReLU, maxpool 2x2,
+ * FC 9216->128 + ReLU, FC 128->10, softmax.  Grids are 4x4 cells of 28x28.
+ *
+ * Tensors (all DEVICE memory owned by the caller; same conventions as tdp.h:
+ * asynchronous on `stream`, no allocation, host status for argument errors):
+ *   grids   uint8  [n_grids][112][112]   cell (r, c) is rows 28r.., cols 28c..
+ *   y1      bf16   [n_cells][26][26][32] conv1 output after ReLU (NHWC)
+ *   y2      bf16   [n_cells][12][12][64] pooled conv2 output after ReLU
+ *   argmax  uint8  [n_cells][12][12][64] window position (dy*2+dx) of the max,
+ *                                         first maximum on ties
+ *   h1      bf16   [n_cells][128]        fc1 output after ReLU
+ *   conv1 weights fp32 w1 [32][3][3], b1 [32]
+ *   conv2 weights bf16 w2 [64][3][3][32] (out, ky, kx, in), fp32 b2 [64]
+ *   fc1 weights   bf16 wfc1 [128][9216] (inputs in (y, x, c) order), fp32 bfc1
+ *   fc2 weights   fp32 wfc2 [10][128], bfc2 [10]
+ * n_cells = 16 * n_grids.  "bf16" buffers are passed as void*.
+ */
+#ifndef TDP_CNN_H
+#define TDP_CNN_H
+
+#include "tdp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* conv1 + bias + ReLU, reading the cells in place from the grid images
+ * (the split of a grid into cells is index arithmetic, no copy). */
+tdp_status tdp_cnn_conv1_fwd(const uint8_t *grids, int64_t n_grids, const float *w1, const float *b1, void *y1,
+                             tdp_stream_t stream);
+
+/* conv2 + bias + ReLU + 2x2 max-pool as one implicit GEMM on the tensor cores
+ * (bf16 operands, fp32 accumulation); writes y2 and argmax. */
+tdp_status tdp_cnn_conv2_pool_fwd(const void *y1, int64_t n_cells, const void *w2, const float *b2, void *y2,
+                                  uint8_t *argmax, tdp_stream_t stream);
+
+/* Workspace bytes of tdp_cnn_fc1_fwd. */
+size_t tdp_cnn_fc1_fwd_workspace(int64_t n_cells);
+
+/* fc1 + bias + ReLU (split-K GEMM, fp32 partials summed in ws). */
+tdp_status tdp_cnn_fc1_fwd(const void *y2, int64_t n_cells, const void *wfc1, const float *bfc1, void *h1, void *ws,
+                           size_t ws_bytes, tdp_stream_t stream);
+
+/* Workspace bytes of tdp_cnn_head. */
+size_t tdp_cnn_head_workspace(int64_t n_grids);
+
+/*
+ * fc2 + softmax + soft query, and (when targets != NULL) the loss and its
+ * backward, one block per grid:
+ *   logits [n_cells][10], P [n_cells][10]   (each optional)
+ *   pred   [n_grids][14]  = 10 soft counts  cnt[k]  = sum_cells P[c][k]
+ *                         + 4 soft row sums rsum[r] = sum_{c in row r} sum_k k P[c][k]
+ *   with targets [n_grids][14] (the exact query on true labels):
+ *   loss   [1]  = sum (pred - target)^2 (divide by 14 * n_grids for the mean)
+ *   dh1    bf16 [n_cells][128]  gradient of the MSE mean w.r.t. h1 (ReLU-masked)
+ *   dwfc2  [10][128], dbfc2 [10]  its fc2 gradients (per-grid partials in ws,
+ *                                 summed in grid order in float64)
+ */
+tdp_status tdp_cnn_head(const void *h1, int64_t n_grids, const float *wfc2, const float *bfc2, const float *targets,
+                        float *logits, float *P, float *pred, void *dh1, float *dwfc2, float *dbfc2, float *loss,
+                        void *ws, size_t ws_bytes, tdp_stream_t stream);
+
+/* Workspace bytes of tdp_cnn_fc1_bwd. */
+size_t tdp_cnn_fc1_bwd_workspace(int64_t n_cells);
+
+/*
+ * fc1 backward.  dy2p bf16 [n_cells][9216] = (dh1 . wfc1) masked by y2 > 0
+ * (the gradient at the pooled map, through the ReLU); dwfc1 fp32 [128][9216];
+ * dbfc1 fp32 [128].
+ */
+tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, int64_t n_cells, void *dy2p,
+                           float *dwfc1, float *dbfc1, void *ws, size_t ws_bytes, tdp_stream_t stream);
+
+/* Workspace bytes of tdp_cnn_conv2_bwd. */
+size_t tdp_cnn_conv2_bwd_workspace(int64_t n_cells);
+
+/*
+ * conv2 backward from the pooled gradient dy2p and the pool arg-max: the
+ * gradient at each conv2 output pixel is the pooled gradient where that pixel
+ * is its window's arg-max, else 0 (expanded on the fly, never stored).
+ *   dz1 bf16 [n_cells][26][26][32] = (conv2 transposed) masked by y1 > 0
+ *       (optional: NULL skips the data gradient)
+ *   dw2 fp32 [64][3][3][32], db2 fp32 [64]
+ */
+tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void *y1, const void *w2, int64_t n_cells,
+                             void *dz1, float *dw2, float *db2, void *ws, size_t ws_bytes, tdp_stream_t stream);
+
+/* Workspace bytes of tdp_cnn_conv1_bwd. */
+size_t tdp_cnn_conv1_bwd_workspace(int64_t n_cells);
+
+/* conv1 weight and bias gradients (dw1 [32][3][3], db1 [32]) from dz1. */
+tdp_status tdp_cnn_conv1_bwd(const void *dz1, const uint8_t *grids, int64_t n_cells, float *dw1, float *db1, void *ws,
+                             size_t ws_bytes, tdp_stream_t stream);
+
+/*
+ * One Adam step (the optimiser of the paper's training loop) over up to 8
+ * fp32 tensors: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * bf16_copies[i] (optional, or NULL entries) receives p rounded to bf16, the
+ * operand copy the tensor-core layers read.  step >= 1.
+ */
+tdp_status tdp_adam_step(float *const *params, const float *const *grads, float *const *m, float *const *v,
+                         void *const *bf16_copies, const int64_t *sizes, int32_t count, int32_t step, float lr,
+                         float beta1, float beta2, float eps, tdp_stream_t stream);
+
+/* y[i] = bf16(x[i]) (round to nearest even). */
+tdp_status tdp_f32_to_bf16(const float *x, int64_t n, void *y, tdp_stream_t stream);
+
+/*
+ * Exact query at inference (Sec. 4: exact operators replace the soft ones):
+ * per cell the first arg-max of its K logits (labels [n_grids*gh*gw], optional),
+ * per grid the exact integer COUNT per class cnt [n_grids][K] and the per-row
+ * SUM of class values rsum [n_grids][gh].
+ */
+tdp_status tdp_exact_pe_count(const float *logits, int64_t n_grids, int32_t K, int32_t grid_h, int32_t grid_w,
+                              int32_t *labels, int64_t *cnt, int64_t *rsum, tdp_stream_t stream);
+
+/*
+ * Soft group-by on a PE column (Sec. 4 soft_count / soft_groupby; only + and
+ * x): P [n_grids*gh*gw][K] (cells of a grid row-major), cnt [n_grids][K],
+ * rsum [n_grids][gh] as in tdp_cnn_head.  The backward is the adjoint:
+ * dP[c][k] = dcnt[g][k] + k * drsum[g][row(c)].
+ */
+tdp_status tdp_pe_groupby_fwd(const float *P, int64_t n_grids, int32_t K, int32_t grid_h, int32_t grid_w, float *cnt,
+                              float *rsum, tdp_stream_t stream);
+tdp_status tdp_pe_groupby_bwd(const float *dcnt, const float *drsum, int64_t n_grids, int32_t K, int32_t grid_h,
+                              int32_t grid_w, float *dP, tdp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDP_CNN_H */

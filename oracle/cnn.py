@@ -58,35 +58,52 @@ def _q(a, quant):
     return bf16(a) if quant else np.asarray(a, np.float64)
 
 
+def conv1_relu(x0, w1, b1):
+    """conv3x3 (1 -> 32, valid) + bias + ReLU; x0 [B,28,28] -> [B,26,26,32]."""
+    B = x0.shape[0]
+    z1 = np.zeros((B, 26, 26, 32))
+    for ky in range(3):
+        for kx in range(3):
+            z1 += x0[:, ky:ky + 26, kx:kx + 26, None] * w1[:, ky, kx]
+    z1 += b1
+    return np.maximum(z1, 0.0)
+
+
+def conv2_relu_pool(y1, w2, b2):
+    """conv3x3 (32 -> 64, valid) + bias + ReLU, then 2x2 max-pool taking the
+    first maximum of each window in (dy, dx) order.  Returns (pooled
+    [B,12,12,64], argmax window position [B,12,12,64], a2 [B,24,24,64])."""
+    B = y1.shape[0]
+    z2 = np.zeros((B, 24, 24, 64))
+    for ky in range(3):
+        for kx in range(3):
+            z2 += y1[:, ky:ky + 24, kx:kx + 24, :] @ w2[:, ky, kx, :].T
+    z2 += b2
+    a2 = np.maximum(z2, 0.0)
+    win = a2.reshape(B, 12, 2, 12, 2, 64).transpose(0, 1, 3, 2, 4, 5).reshape(B, 12, 12, 4, 64)
+    arg = np.argmax(win, axis=3)  # first occurrence of the maximum
+    pooled = np.take_along_axis(win, arg[:, :, :, None, :], axis=3)[:, :, :, 0, :]
+    return pooled, arg, a2
+
+
+def fc(x, w, b, relu):
+    z = x @ w.T + b
+    return np.maximum(z, 0.0) if relu else z
+
+
 def forward(params, grids_u8, quant=True):
     """Returns a dict with every intermediate needed by ``backward``."""
     p = {k: np.asarray(v, np.float64) for k, v in params.items()}
     x0 = split_cells(grids_u8).astype(np.float64) / 255.0  # [B,28,28]
     B = x0.shape[0]
-    # conv1 (1 -> 32), valid, + bias, ReLU
-    z1 = np.zeros((B, 26, 26, 32))
-    for ky in range(3):
-        for kx in range(3):
-            z1 += x0[:, ky:ky + 26, kx:kx + 26, None] * p["conv1_w"][:, ky, kx]
-    z1 += p["conv1_b"]
-    y1 = _q(np.maximum(z1, 0.0), quant)
-    # conv2 (32 -> 64), valid, + bias, ReLU
+    y1 = _q(conv1_relu(x0, p["conv1_w"], p["conv1_b"]), quant)
     w2 = _q(p["conv2_w"], quant)
-    z2 = np.zeros((B, 24, 24, 64))
-    for ky in range(3):
-        for kx in range(3):
-            z2 += y1[:, ky:ky + 24, kx:kx + 24, :] @ w2[:, ky, kx, :].T
-    z2 += p["conv2_b"]
-    a2 = np.maximum(z2, 0.0)
-    # 2x2 max pool; first maximum in (dy, dx) order
-    win = a2.reshape(B, 12, 2, 12, 2, 64).transpose(0, 1, 3, 2, 4, 5).reshape(B, 12, 12, 4, 64)
-    arg = np.argmax(win, axis=3)  # first occurrence of the maximum
-    pooled = np.take_along_axis(win, arg[:, :, :, None, :], axis=3)[:, :, :, 0, :]
+    pooled, arg, a2 = conv2_relu_pool(y1, w2, p["conv2_b"])
     y2 = _q(pooled, quant)  # [B,12,12,64]
     flat = y2.reshape(B, 9216)
     wf1 = _q(p["fc1_w"], quant)
-    h1 = _q(np.maximum(flat @ wf1.T + p["fc1_b"], 0.0), quant)
-    logits = h1 @ p["fc2_w"].T + p["fc2_b"]
+    h1 = _q(fc(flat, wf1, p["fc1_b"], True), quant)
+    logits = fc(h1, p["fc2_w"], p["fc2_b"], False)
     z = logits - logits.max(axis=1, keepdims=True)
     e = np.exp(z)
     P = e / e.sum(axis=1, keepdims=True)

@@ -87,6 +87,24 @@ SIGNATURES = {
     "tdp_soft_filter_bwd": (_st, [_p, _p, _p, _f, _i64, _i32, _p, _p, _p, _p, _sz, _p]),
     "tdp_soft_agg_fwd": (_st, [_p, _p, _p, _p, _f, _i64, _i32, _p, _p, _p, _sz, _p]),
     "tdp_soft_agg_bwd": (_st, [_p, _p, _p, _p, _f, _i64, _i32, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    # glyph CNN of the trainable query (include/tdp_cnn.h)
+    "tdp_cnn_conv1_fwd": (_st, [_p, _i64, _p, _p, _p, _p]),
+    "tdp_cnn_conv2_pool_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _p]),
+    "tdp_cnn_fc1_fwd_workspace": (_sz, [_i64]),
+    "tdp_cnn_fc1_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _sz, _p]),
+    "tdp_cnn_head_workspace": (_sz, [_i64]),
+    "tdp_cnn_head": (_st, [_p, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "tdp_cnn_fc1_bwd_workspace": (_sz, [_i64]),
+    "tdp_cnn_fc1_bwd": (_st, [_p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p]),
+    "tdp_cnn_conv2_bwd_workspace": (_sz, [_i64]),
+    "tdp_cnn_conv2_bwd": (_st, [_p, _p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p]),
+    "tdp_cnn_conv1_bwd_workspace": (_sz, [_i64]),
+    "tdp_cnn_conv1_bwd": (_st, [_p, _p, _i64, _p, _p, _p, _sz, _p]),
+    "tdp_adam_step": (_st, [_p, _p, _p, _p, _p, _p, _i32, _i32, _f, _f, _f, _f, _p]),
+    "tdp_f32_to_bf16": (_st, [_p, _i64, _p, _p]),
+    "tdp_exact_pe_count": (_st, [_p, _i64, _i32, _i32, _i32, _p, _p, _p, _p]),
+    "tdp_pe_groupby_fwd": (_st, [_p, _i64, _i32, _i32, _i32, _p, _p, _p]),
+    "tdp_pe_groupby_bwd": (_st, [_p, _p, _i64, _i32, _i32, _i32, _p, _p]),
 }
 
 _lib = None

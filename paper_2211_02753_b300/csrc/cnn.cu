@@ -1,0 +1,926 @@
+// K12-K18: the glyph-CNN of the trainable query (Sec. 3 training loop,
+// Sec. 4 soft operators on probability-encoded columns, Sec. 5.5).
+//
+// Layers (cells of 28x28 uint8, read in place from the 112x112 grid images):
+//   conv1 3x3 1->32 + ReLU       direct, CUDA cores (K = 9), bf16 NHWC out
+//   conv2 3x3 32->64 + ReLU      implicit GEMM on tensor cores (K = 288),
+//     + 2x2 max-pool             epilogue: rows are ordered pool-window-major,
+//                                so a window is 4 consecutive rows; bf16 pooled
+//                                map + per-channel arg-max byte
+//   fc1 9216->128 + ReLU         GEMM, split-K, bf16 out
+//   fc2 128->10, softmax, soft COUNT per class and soft row SUM per grid row,
+//   MSE loss and its backward    one block per grid (16 cells), fp32
+// Backward: fc1 dgrad (pool-gradient masked by ReLU), fc1 wgrad (split-K),
+// conv2 dgrad (implicit GEMM whose A operand expands the pooled gradient
+// through the arg-max on the fly), conv2 wgrad (split-K over pixels, same
+// expansion), conv1 wgrad/bias (CUDA cores), and a fused Adam step that also
+// refreshes the bf16 copies of the tensor-core weights.
+// Every GEMM is gemm_kernel (cnn_gemm.cuh) with its own operand loaders and
+// epilogue; no operand is transposed or materialised in im2col form.
+#include "cnn_gemm.cuh"
+#include "common.cuh"
+#include "tdp_cnn.h"
+
+namespace tdp {
+namespace cnn {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int CELL = 28, C1 = 26, C2 = 24, PO = 12;
+constexpr int CH1 = 32, CH2 = 64, FEAT = PO * PO * CH2, HID = 128, NCLS = 10;
+constexpr int GRID_W = 4, GRID_H = 4, CELLS_PER_GRID = 16;
+
+__device__ __forceinline__ float bf2f(bf16 x) { return __bfloat162float(x); }
+
+// ------------------------------------------------------------------ conv1
+
+__global__ void conv1_fwd_kernel(const uint8_t *__restrict__ grids, long long ncell, const float *__restrict__ w,
+                                 const float *__restrict__ b, bf16 *__restrict__ y1)
+{
+    __shared__ float sw[CH1 * 9];
+    __shared__ float sb[CH1];
+    for (int i = threadIdx.x; i < CH1 * 9; i += blockDim.x)
+        sw[i] = w[i];
+    for (int i = threadIdx.x; i < CH1; i += blockDim.x)
+        sb[i] = b[i];
+    __syncthreads();
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ncell * C1 * C1)
+        return;
+    const long long c = p / (C1 * C1);
+    const int w_ = (int)(p % (C1 * C1)), oy = w_ / C1, ox = w_ % C1;
+    const long long g = c / CELLS_PER_GRID;
+    const int r = (int)(c % CELLS_PER_GRID) / GRID_W, cc = (int)(c % GRID_W);
+    const uint8_t *img = grids + g * (GRID_H * CELL) * (GRID_W * CELL) + (long long)(r * CELL) * (GRID_W * CELL) +
+                         cc * CELL;
+    float x[9];
+#pragma unroll
+    for (int ky = 0; ky < 3; ky++)
+#pragma unroll
+        for (int kx = 0; kx < 3; kx++)
+            x[ky * 3 + kx] = (float)img[(oy + ky) * (GRID_W * CELL) + ox + kx] * (1.0f / 255.0f);
+    __align__(16) bf16 out[CH1];
+#pragma unroll
+    for (int co = 0; co < CH1; co++) {
+        float s = sb[co];
+#pragma unroll
+        for (int k = 0; k < 9; k++)
+            s = fmaf(x[k], sw[co * 9 + k], s);
+        out[co] = __float2bfloat16_rn(fmaxf(s, 0.f));
+    }
+    uint4 *dst = (uint4 *)(y1 + p * CH1);
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        dst[i] = ((const uint4 *)out)[i];
+}
+
+// ---------------------------------------------------------------- loaders
+
+struct LoadK { // K-major [rows][ld]
+    static constexpr bool MN_MAJOR = false, REG = false;
+    const bf16 *p;
+    int rows, ld;
+    __device__ const void *ptr(int r, int kc, int r0, int k0, int kend) const
+    {
+        int row = r0 + r, k = k0 + kc * 8;
+        if (row >= rows || k >= kend)
+            return nullptr;
+        return p + (size_t)row * ld + k;
+    }
+};
+
+struct LoadMN { // MN-major: stored [k][ld], the operand's rows contiguous
+    static constexpr bool MN_MAJOR = true, REG = false;
+    const bf16 *p;
+    int rows, ld;
+    __device__ const void *ptr(int kk, int rc, int r0, int k0, int kend) const
+    {
+        int k = k0 + kk, row = r0 + rc * 8;
+        if (k >= kend || row >= rows)
+            return nullptr;
+        return p + (size_t)k * ld + row;
+    }
+};
+
+// conv2 forward A: rows = output pixels in pool-window-major order
+// (cell, py, px, dy, dx); k = (ky*3 + kx)*32 + ci; source y1 [cell][26][26][32].
+struct LoadConv2A {
+    static constexpr bool MN_MAJOR = false, REG = false;
+    const bf16 *y1;
+    int M;
+    __device__ const void *ptr(int r, int kc, int m0, int k0, int kend) const
+    {
+        int m = m0 + r, k = k0 + kc * 8;
+        if (m >= M || k >= kend)
+            return nullptr;
+        int cell = m / (C2 * C2), w = m % (C2 * C2), win = w >> 2, pos = w & 3;
+        int oy = 2 * (win / PO) + (pos >> 1), ox = 2 * (win % PO) + (pos & 1);
+        int kp = k >> 5, ci = k & 31, ky = kp / 3, kx = kp % 3;
+        return y1 + (((size_t)cell * C1 + oy + ky) * C1 + ox + kx) * CH1 + ci;
+    }
+};
+
+// The gradient w.r.t. the conv2 output (pre-pool) for 8 channels of one
+// output pixel: the pooled gradient where the pixel is its window's arg-max,
+// else 0.  dy2p already carries the ReLU mask of the pooled value.
+__device__ __forceinline__ uint4 pool_grad8(const bf16 *dy2p, const uint8_t *argmax, int cell, int oy, int ox,
+                                            int co)
+{
+    size_t q = ((size_t)cell * PO + (oy >> 1)) * PO + (ox >> 1);
+    int wpos = ((oy & 1) << 1) | (ox & 1);
+    uint4 g = *(const uint4 *)(dy2p + q * CH2 + co);
+    uint2 a = *(const uint2 *)(argmax + q * CH2 + co);
+    uint32_t gw[4] = {g.x, g.y, g.z, g.w};
+    uint32_t ab[2] = {a.x, a.y};
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        uint32_t byte = (ab[i >> 2] >> (8 * (i & 3))) & 0xffu;
+        if (byte != (uint32_t)wpos)
+            gw[i >> 1] &= (i & 1) ? 0x0000ffffu : 0xffff0000u;
+    }
+    return make_uint4(gw[0], gw[1], gw[2], gw[3]);
+}
+
+// conv2 dgrad A: rows = input pixels (cell, y, x) raster; k = (ky*3+kx)*64 + co;
+// value = dz2[cell][y-ky][x-kx][co] (0 outside the 24x24 output).
+struct LoadConv2DgradA {
+    static constexpr bool MN_MAJOR = false, REG = true;
+    const bf16 *dy2p;
+    const uint8_t *argmax;
+    int M;
+    __device__ uint4 val(int r, int kc, int m0, int k0, int kend) const
+    {
+        int m = m0 + r, k = k0 + kc * 8;
+        if (m >= M || k >= kend)
+            return make_uint4(0, 0, 0, 0);
+        int cell = m / (C1 * C1), w = m % (C1 * C1), y = w / C1, x = w % C1;
+        int kp = k >> 6, co = k & 63, ky = kp / 3, kx = kp % 3;
+        int oy = y - ky, ox = x - kx;
+        if (oy < 0 || oy >= C2 || ox < 0 || ox >= C2)
+            return make_uint4(0, 0, 0, 0);
+        return pool_grad8(dy2p, argmax, cell, oy, ox, co);
+    }
+};
+
+// conv2 dgrad B: B(n = ci, k = (ky,kx,co)) = W2[co][ky][kx][ci], stored so that
+// ci is contiguous: MN-major chunk at k.
+struct LoadConv2DgradB {
+    static constexpr bool MN_MAJOR = true, REG = false;
+    const bf16 *w2;
+    __device__ const void *ptr(int kk, int rc, int n0, int k0, int kend) const
+    {
+        int k = k0 + kk, ci = n0 + rc * 8;
+        if (k >= kend || ci >= CH1)
+            return nullptr;
+        int kp = k >> 6, co = k & 63;
+        return w2 + ((size_t)co * 9 + kp) * CH1 + ci;
+    }
+};
+
+// conv2 wgrad A: A(m = co, k = output pixel raster (cell, oy, ox)) = dz2; MN-major (co contiguous)
+struct LoadConv2WgradA {
+    static constexpr bool MN_MAJOR = true, REG = true;
+    const bf16 *dy2p;
+    const uint8_t *argmax;
+    __device__ uint4 val(int kk, int rc, int m0, int k0, int kend) const
+    {
+        int k = k0 + kk, co = m0 + rc * 8;
+        if (k >= kend)
+            return make_uint4(0, 0, 0, 0);
+        int cell = k / (C2 * C2), w = k % (C2 * C2), oy = w / C2, ox = w % C2;
+        return pool_grad8(dy2p, argmax, cell, oy, ox, co);
+    }
+};
+
+// conv2 wgrad B: B(n = (ky,kx,ci), k = output pixel) = y1[cell][oy+ky][ox+kx][ci]; MN-major
+struct LoadConv2WgradB {
+    static constexpr bool MN_MAJOR = true, REG = false;
+    const bf16 *y1;
+    __device__ const void *ptr(int kk, int rc, int n0, int k0, int kend) const
+    {
+        int k = k0 + kk, n = n0 + rc * 8;
+        if (k >= kend || n >= 9 * CH1)
+            return nullptr;
+        int cell = k / (C2 * C2), w = k % (C2 * C2), oy = w / C2, ox = w % C2;
+        int kp = n >> 5, ci = n & 31, ky = kp / 3, kx = kp % 3;
+        return y1 + (((size_t)cell * C1 + oy + ky) * C1 + ox + kx) * CH1 + ci;
+    }
+};
+
+// -------------------------------------------------------------- epilogues
+
+// conv2 forward: bias + ReLU + 2x2 max-pool over 4 consecutive rows (lanes
+// 4 apart hold consecutive rows of a fragment).  First maximum wins.
+struct EpiConv2Pool {
+    const float *bias;
+    bf16 *y2;
+    uint8_t *argmax;
+    int M;
+    __device__ void operator()(int m, int n, float v0, float v1, int) const
+    {
+        v0 = fmaxf(v0 + bias[n], 0.f);
+        v1 = fmaxf(v1 + bias[n + 1], 0.f);
+        const int pos = m & 3; // lane bits 2..3 == row within the window
+        float b0 = v0, b1 = v1;
+        int a0 = pos, a1 = pos;
+#pragma unroll
+        for (int o = 4; o <= 8; o <<= 1) {
+            float c0 = __shfl_xor_sync(0xffffffffu, b0, o);
+            float c1 = __shfl_xor_sync(0xffffffffu, b1, o);
+            int d0 = __shfl_xor_sync(0xffffffffu, a0, o);
+            int d1 = __shfl_xor_sync(0xffffffffu, a1, o);
+            if (c0 > b0 || (c0 == b0 && d0 < a0)) {
+                b0 = c0;
+                a0 = d0;
+            }
+            if (c1 > b1 || (c1 == b1 && d1 < a1)) {
+                b1 = c1;
+                a1 = d1;
+            }
+        }
+        if (pos == 0 && m < M) {
+            size_t q = (size_t)(m >> 2);
+            __nv_bfloat162 o2;
+            o2.x = __float2bfloat16_rn(b0);
+            o2.y = __float2bfloat16_rn(b1);
+            *(__nv_bfloat162 *)(y2 + q * CH2 + n) = o2;
+            argmax[q * CH2 + n] = (uint8_t)a0;
+            argmax[q * CH2 + n + 1] = (uint8_t)a1;
+        }
+    }
+};
+
+struct EpiPartialF32 { // out[split][m][ldo]
+    float *out;
+    int M, ldo;
+    size_t split_stride;
+    __device__ void operator()(int m, int n, float v0, float v1, int split) const
+    {
+        if (m >= M)
+            return;
+        *(float2 *)(out + split * split_stride + (size_t)m * ldo + n) = make_float2(v0, v1);
+    }
+};
+
+// bf16 out[m][ldo] = v * (mask[m][ldo] > 0)
+struct EpiMaskedBf16 {
+    bf16 *out;
+    const bf16 *mask;
+    int M, ldo;
+    __device__ void operator()(int m, int n, float v0, float v1, int) const
+    {
+        if (m >= M)
+            return;
+        size_t i = (size_t)m * ldo + n;
+        __nv_bfloat162 mk = *(const __nv_bfloat162 *)(mask + i);
+        __nv_bfloat162 o2;
+        o2.x = __float2bfloat16_rn(bf2f(mk.x) > 0.f ? v0 : 0.f);
+        o2.y = __float2bfloat16_rn(bf2f(mk.y) > 0.f ? v1 : 0.f);
+        *(__nv_bfloat162 *)(out + i) = o2;
+    }
+};
+
+template <int BM, int BN, int WM, int WN, class LA, class LB, class EPI>
+static cudaError_t launch_gemm(const LA &la, const LB &lb, const EPI &epi, int M, int N, int K, int splits,
+                               cudaStream_t s)
+{
+    constexpr size_t smem = gemm_smem<BM, BN, LA::MN_MAJOR, LB::MN_MAJOR>();
+    auto kern = gemm_kernel<BM, BN, WM, WN, LA, LB, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int kps = (K + splits - 1) / splits;
+    kps = (kps + GBK - 1) / GBK * GBK;
+    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, splits);
+    kern<<<grid, GTHREADS, smem, s>>>(la, lb, epi, M, N, K, kps);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- reductions
+
+// out[i] = act(sum_s part[s][i] + bias[i % ncol]) -> bf16 (ReLU) or f32
+__global__ void splitk_reduce_kernel(const float *__restrict__ part, int splits, size_t stride, long long n, int ncol,
+                                     const float *__restrict__ bias, int relu, bf16 *out_bf, float *out_f)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    float s = 0.f;
+    for (int k = 0; k < splits; k++)
+        s += part[k * stride + i];
+    if (bias)
+        s += bias[i % ncol];
+    if (relu)
+        s = fmaxf(s, 0.f);
+    if (out_bf)
+        out_bf[i] = __float2bfloat16_rn(s);
+    if (out_f)
+        out_f[i] = s;
+}
+
+// Column sums of a bf16 matrix [rows][C] into fp32 partials [blocks][C].
+__global__ void colsum_bf16_kernel(const bf16 *__restrict__ x, long long rows, int C, float *__restrict__ part)
+{
+    extern __shared__ float cs[];
+    for (int c = threadIdx.x; c < C; c += blockDim.x)
+        cs[c] = 0.f;
+    __syncthreads();
+    const int c = threadIdx.x % C;
+    const int rstep = blockDim.x / C;
+    float acc = 0.f;
+    for (long long r = (long long)blockIdx.x * rstep + threadIdx.x / C; r < rows; r += (long long)gridDim.x * rstep)
+        acc += bf2f(x[r * C + c]);
+    if (threadIdx.x < rstep * C)
+        atomicAdd(&cs[c], acc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < C; i += blockDim.x)
+        part[(size_t)blockIdx.x * C + i] = cs[i];
+}
+
+// out[i] = sum_b part[b * stride + i] in float64, in block order
+__global__ void partial_sum_kernel(const float *__restrict__ part, int nb, int n, size_t stride,
+                                   float *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    double s = 0.0;
+    for (int b = 0; b < nb; b++)
+        s += part[(size_t)b * stride + i];
+    out[i] = (float)s;
+}
+
+// conv1 weight and bias gradients: thread (co, kpos) over a chunk of output
+// pixels; partials [blocks][32*9 + 32].
+__global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const uint8_t *__restrict__ grids, long long ncell,
+                                   long long chunk, float *__restrict__ part)
+{
+    const int co = threadIdx.x % CH1, kp = threadIdx.x / CH1; // 0..9 (9 = bias)
+    const long long P = ncell * C1 * C1;
+    const long long beg = (long long)blockIdx.x * chunk, end = min(P, beg + chunk);
+    float acc = 0.f;
+    const int ky = kp / 3, kx = kp % 3;
+    for (long long p = beg; p < end; p++) {
+        float d = bf2f(dz1[p * CH1 + co]);
+        if (kp == 9) {
+            acc += d;
+            continue;
+        }
+        long long c = p / (C1 * C1);
+        int w = (int)(p % (C1 * C1)), oy = w / C1, ox = w % C1;
+        long long g = c / CELLS_PER_GRID;
+        int r = (int)(c % CELLS_PER_GRID) / GRID_W, cc = (int)(c % GRID_W);
+        uint8_t u = grids[g * (GRID_H * CELL) * (GRID_W * CELL) + (long long)(r * CELL + oy + ky) * (GRID_W * CELL) +
+                          cc * CELL + ox + kx];
+        acc = fmaf(d, (float)u * (1.0f / 255.0f), acc);
+    }
+    float *o = part + (size_t)blockIdx.x * (CH1 * 10);
+    if (kp < 9)
+        o[co * 9 + kp] = acc;
+    else
+        o[CH1 * 9 + co] = acc;
+}
+
+// ------------------------------------------------------------------- head
+//
+// One block per grid: fc2 + softmax (the PE column), the soft query
+// cnt[k] = sum_c P[c][k], rsum[r] = sum_{c in row r} sum_k k P[c][k], and,
+// when targets are given, the MSE loss and its backward down to dh1 plus the
+// fc2 gradients (per-grid partials, summed later in a fixed order).
+constexpr int HEAD_THREADS = 256;
+constexpr int NPRED = NCLS + GRID_H;
+
+__global__ void __launch_bounds__(HEAD_THREADS) head_kernel(const bf16 *__restrict__ h1, long long ngrid,
+                                                            const float *__restrict__ w, const float *__restrict__ b,
+                                                            const float *__restrict__ target, float inv_nout,
+                                                            float *__restrict__ logits_out, float *__restrict__ P_out,
+                                                            float *__restrict__ pred_out, bf16 *__restrict__ dh1,
+                                                            float *__restrict__ part)
+{
+    __shared__ float sh[CELLS_PER_GRID][HID];
+    __shared__ float sw[NCLS][HID];
+    __shared__ float sP[CELLS_PER_GRID][NCLS];
+    __shared__ float sdl[CELLS_PER_GRID][NCLS];
+    __shared__ float spred[NPRED], sdpred[NPRED];
+    const long long grid = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < CELLS_PER_GRID * HID; i += HEAD_THREADS)
+        sh[i / HID][i % HID] = bf2f(h1[grid * CELLS_PER_GRID * HID + i]);
+    for (int i = tid; i < NCLS * HID; i += HEAD_THREADS)
+        sw[i / HID][i % HID] = w[i];
+    __syncthreads();
+    if (tid < CELLS_PER_GRID * NCLS) {
+        int c = tid / NCLS, k = tid % NCLS;
+        float s = b[k];
+        for (int u = 0; u < HID; u++)
+            s = fmaf(sh[c][u], sw[k][u], s);
+        sP[c][k] = s;
+        if (logits_out)
+            logits_out[(grid * CELLS_PER_GRID + c) * NCLS + k] = s;
+    }
+    __syncthreads();
+    if (tid < CELLS_PER_GRID) {
+        float mx = sP[tid][0];
+        for (int k = 1; k < NCLS; k++)
+            mx = fmaxf(mx, sP[tid][k]);
+        float e[NCLS], z = 0.f;
+        for (int k = 0; k < NCLS; k++) {
+            e[k] = expf(sP[tid][k] - mx);
+            z += e[k];
+        }
+        float iz = 1.0f / z;
+        for (int k = 0; k < NCLS; k++)
+            sP[tid][k] = e[k] * iz;
+    }
+    __syncthreads();
+    if (P_out && tid < CELLS_PER_GRID * NCLS)
+        P_out[grid * CELLS_PER_GRID * NCLS + tid] = sP[tid / NCLS][tid % NCLS];
+    if (tid < NPRED) {
+        float s = 0.f;
+        if (tid < NCLS) {
+            for (int c = 0; c < CELLS_PER_GRID; c++)
+                s += sP[c][tid];
+        } else {
+            int r = tid - NCLS;
+            for (int c = r * GRID_W; c < r * GRID_W + GRID_W; c++)
+                for (int k = 0; k < NCLS; k++)
+                    s = fmaf((float)k, sP[c][k], s);
+        }
+        spred[tid] = s;
+        if (pred_out)
+            pred_out[grid * NPRED + tid] = s;
+        if (target) {
+            float d = s - target[grid * NPRED + tid];
+            sdpred[tid] = 2.f * d * inv_nout;
+        }
+    }
+    if (!target)
+        return;
+    __syncthreads();
+    float *gp = part + grid * (NCLS * HID + NCLS + 1);
+    if (tid == 0) {
+        float l = 0.f;
+        for (int j = 0; j < NPRED; j++) {
+            float d = spred[j] - target[grid * NPRED + j];
+            l += d * d;
+        }
+        gp[NCLS * HID + NCLS] = l;
+    }
+    if (tid < CELLS_PER_GRID) {
+        const int c = tid, r = c / GRID_W;
+        float dP[NCLS], dot = 0.f;
+        for (int k = 0; k < NCLS; k++) {
+            dP[k] = sdpred[k] + (float)k * sdpred[NCLS + r];
+            dot = fmaf(sP[c][k], dP[k], dot);
+        }
+        for (int k = 0; k < NCLS; k++)
+            sdl[c][k] = sP[c][k] * (dP[k] - dot);
+    }
+    __syncthreads();
+    // dh1[c][u] = (sum_k dl[c][k] w[k][u]) * (h1 > 0)
+    for (int i = tid; i < CELLS_PER_GRID * HID; i += HEAD_THREADS) {
+        int c = i / HID, u = i % HID;
+        float s = 0.f;
+        for (int k = 0; k < NCLS; k++)
+            s = fmaf(sdl[c][k], sw[k][u], s);
+        dh1[grid * CELLS_PER_GRID * HID + i] = __float2bfloat16_rn(sh[c][u] > 0.f ? s : 0.f);
+    }
+    // fc2 gradient partials of this grid
+    for (int i = tid; i < NCLS * HID; i += HEAD_THREADS) {
+        int k = i / HID, u = i % HID;
+        float s = 0.f;
+        for (int c = 0; c < CELLS_PER_GRID; c++)
+            s = fmaf(sdl[c][k], sh[c][u], s);
+        gp[i] = s;
+    }
+    if (tid < NCLS) {
+        float s = 0.f;
+        for (int c = 0; c < CELLS_PER_GRID; c++)
+            s += sdl[c][tid];
+        gp[NCLS * HID + tid] = s;
+    }
+}
+
+// ------------------------------------------------------- exact inference
+
+// Exact query (Sec. 4: the exact operators replace the soft ones at
+// inference): argmax of the logits per cell (first maximum), then the exact
+// integer COUNT per class and the per-row SUM of class values per grid.
+__global__ void exact_count_kernel(const float *__restrict__ logits, long long ngrid, int K, int gh, int gw,
+                                   int32_t *__restrict__ labels, long long *__restrict__ cnt,
+                                   long long *__restrict__ rsum)
+{
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngrid)
+        return;
+    const int cpg = gh * gw;
+    for (int k = 0; k < K; k++)
+        cnt[g * K + k] = 0;
+    for (int r = 0; r < gh; r++)
+        rsum[g * gh + r] = 0;
+    for (int c = 0; c < cpg; c++) {
+        const float *l = logits + (g * cpg + c) * K;
+        int best = 0;
+        for (int k = 1; k < K; k++)
+            if (l[k] > l[best])
+                best = k;
+        if (labels)
+            labels[g * cpg + c] = best;
+        cnt[g * K + best] += 1;
+        rsum[g * gh + c / gw] += best;
+    }
+}
+
+// PE soft group-by (standalone): cnt[g][k] = sum_c P, rsum[g][r] = sum_{c in r} sum_k k P
+__global__ void pe_groupby_fwd_kernel(const float *__restrict__ P, long long ngrid, int K, int gh, int gw,
+                                      float *__restrict__ cnt, float *__restrict__ rsum)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cpg = gh * gw;
+    if (i >= ngrid * (K + gh))
+        return;
+    long long g = i / (K + gh);
+    int j = (int)(i % (K + gh));
+    float s = 0.f;
+    if (j < K) {
+        for (int c = 0; c < cpg; c++)
+            s += P[(g * cpg + c) * K + j];
+        cnt[g * K + j] = s;
+    } else {
+        int r = j - K;
+        for (int c = r * gw; c < r * gw + gw; c++)
+            for (int k = 0; k < K; k++)
+                s = fmaf((float)k, P[(g * cpg + c) * K + k], s);
+        rsum[g * gh + r] = s;
+    }
+}
+
+__global__ void pe_groupby_bwd_kernel(const float *__restrict__ dcnt, const float *__restrict__ drsum, long long ngrid,
+                                      int K, int gh, int gw, float *__restrict__ dP)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cpg = gh * gw;
+    if (i >= ngrid * cpg * K)
+        return;
+    long long cell = i / K;
+    int k = (int)(i % K);
+    long long g = cell / cpg;
+    int r = (int)(cell % cpg) / gw;
+    dP[i] = dcnt[g * K + k] + (float)k * drsum[g * gh + r];
+}
+
+// ------------------------------------------------------------------- Adam
+
+struct AdamSet {
+    float *p[8];
+    const float *g[8];
+    float *m[8];
+    float *v[8];
+    bf16 *copy[8];
+    long long off[9];
+    int count;
+};
+
+__global__ void adam_kernel(AdamSet as, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    long long total = as.off[as.count];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int t = 0;
+        while (i >= as.off[t + 1])
+            t++;
+        long long j = i - as.off[t];
+        float g = as.g[t][j];
+        float m = b1 * as.m[t][j] + (1.f - b1) * g;
+        float v = b2 * as.v[t][j] + (1.f - b2) * g * g;
+        as.m[t][j] = m;
+        as.v[t][j] = v;
+        float mh = m * c1, vh = v * c2;
+        float p = as.p[t][j] - lr * mh / (sqrtf(vh) + eps);
+        as.p[t][j] = p;
+        if (as.copy[t])
+            as.copy[t][j] = __float2bfloat16_rn(p);
+    }
+}
+
+__global__ void f32_to_bf16_kernel(const float *__restrict__ x, long long n, bf16 *__restrict__ y)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+} // namespace cnn
+} // namespace tdp
+
+using namespace tdp;
+using namespace tdp::cnn;
+
+static tdp_status cerr(cudaError_t e) { return e == cudaSuccess ? TDP_OK : TDP_ERR_CUDA; }
+
+static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// split-K factors (host side) for the fc1 GEMMs and the conv2 weight gradient
+static const int FC1_FWD_SPLITS = 8;
+static const int FC1_WGRAD_SPLITS = 4;
+
+static int conv2_wgrad_splits(long long ncell)
+{
+    long long P = ncell * C2 * C2;
+    long long s = std::min<long long>(2 * num_sms() / 3 + 1, (P + 4095) / 4096);
+    return (int)std::max(1ll, s);
+}
+
+extern "C" {
+
+tdp_status tdp_cnn_conv1_fwd(const uint8_t *grids, int64_t n_grids, const float *w1, const float *b1, void *y1,
+                             tdp_stream_t stream)
+{
+    if (n_grids < 0 || (n_grids > 0 && (!grids || !w1 || !b1 || !y1)))
+        return TDP_ERR_INVALID_ARG;
+    long long P = n_grids * CELLS_PER_GRID * C1 * C1;
+    if (P == 0)
+        return TDP_OK;
+    conv1_fwd_kernel<<<blocks_for(P, 256), 256, 0, (cudaStream_t)stream>>>(grids, n_grids * CELLS_PER_GRID, w1, b1,
+                                                                           (bf16 *)y1);
+    return launch_status();
+}
+
+tdp_status tdp_cnn_conv2_pool_fwd(const void *y1, int64_t n_cells, const void *w2, const float *b2, void *y2,
+                                  uint8_t *argmax, tdp_stream_t stream)
+{
+    if (n_cells < 0 || (n_cells > 0 && (!y1 || !w2 || !b2 || !y2 || !argmax)))
+        return TDP_ERR_INVALID_ARG;
+    if (n_cells == 0)
+        return TDP_OK;
+    const int M = (int)(n_cells * C2 * C2);
+    LoadConv2A la{(const bf16 *)y1, M};
+    LoadK lb{(const bf16 *)w2, CH2, 9 * CH1};
+    EpiConv2Pool epi{b2, (bf16 *)y2, argmax, M};
+    return cerr(launch_gemm<128, 64, 4, 2>(la, lb, epi, M, CH2, 9 * CH1, 1, (cudaStream_t)stream));
+}
+
+size_t tdp_cnn_fc1_fwd_workspace(int64_t n_cells)
+{
+    return align_up((size_t)FC1_FWD_SPLITS * n_cells * HID * sizeof(float), 256);
+}
+
+tdp_status tdp_cnn_fc1_fwd(const void *y2, int64_t n_cells, const void *wfc1, const float *bfc1, void *h1, void *ws,
+                           size_t ws_bytes, tdp_stream_t stream)
+{
+    if (n_cells < 0 || (n_cells > 0 && (!y2 || !wfc1 || !bfc1 || !h1)))
+        return TDP_ERR_INVALID_ARG;
+    if (n_cells == 0)
+        return TDP_OK;
+    if (!ws || ws_bytes < tdp_cnn_fc1_fwd_workspace(n_cells))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *part = (float *)ws;
+    const int M = (int)n_cells;
+    LoadK la{(const bf16 *)y2, M, FEAT};
+    LoadK lb{(const bf16 *)wfc1, HID, FEAT};
+    EpiPartialF32 epi{part, M, HID, (size_t)M * HID};
+    tdp_status st = cerr(launch_gemm<128, 128, 2, 4>(la, lb, epi, M, HID, FEAT, FC1_FWD_SPLITS, s));
+    if (st != TDP_OK)
+        return st;
+    long long n = (long long)M * HID;
+    splitk_reduce_kernel<<<blocks_for(n, 256), 256, 0, s>>>(part, FC1_FWD_SPLITS, (size_t)M * HID, n, HID, bfc1, 1,
+                                                            (bf16 *)h1, nullptr);
+    return launch_status();
+}
+
+size_t tdp_cnn_head_workspace(int64_t n_grids)
+{
+    return align_up((size_t)n_grids * (NCLS * HID + NCLS + 1) * sizeof(float), 256);
+}
+
+tdp_status tdp_cnn_head(const void *h1, int64_t n_grids, const float *wfc2, const float *bfc2, const float *targets,
+                        float *logits, float *P, float *pred, void *dh1, float *dwfc2, float *dbfc2, float *loss,
+                        void *ws, size_t ws_bytes, tdp_stream_t stream)
+{
+    if (n_grids < 0 || (n_grids > 0 && (!h1 || !wfc2 || !bfc2)))
+        return TDP_ERR_INVALID_ARG;
+    if (targets && (!dh1 || !dwfc2 || !dbfc2 || !loss))
+        return TDP_ERR_INVALID_ARG;
+    if (n_grids == 0)
+        return TDP_OK;
+    if (targets && (!ws || ws_bytes < tdp_cnn_head_workspace(n_grids)))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *part = (float *)ws;
+    head_kernel<<<(unsigned)n_grids, HEAD_THREADS, 0, s>>>((const bf16 *)h1, n_grids, wfc2, bfc2, targets,
+                                                           1.0f / (float)(n_grids * NPRED), logits, P, pred,
+                                                           (bf16 *)dh1, part);
+    if (targets) {
+        const size_t per = NCLS * HID + NCLS + 1;
+        partial_sum_kernel<<<blocks_for(NCLS * HID, 256), 256, 0, s>>>(part, (int)n_grids, NCLS * HID, per, dwfc2);
+        partial_sum_kernel<<<1, 32, 0, s>>>(part + NCLS * HID, (int)n_grids, NCLS, per, dbfc2);
+        partial_sum_kernel<<<1, 32, 0, s>>>(part + NCLS * HID + NCLS, (int)n_grids, 1, per, loss);
+    }
+    return launch_status();
+}
+
+size_t tdp_cnn_fc1_bwd_workspace(int64_t n_cells)
+{
+    size_t a = align_up((size_t)FC1_WGRAD_SPLITS * HID * FEAT * sizeof(float), 256);
+    size_t b = align_up((size_t)((n_cells + 63) / 64) * HID * sizeof(float), 256);
+    return a + b;
+}
+
+tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, int64_t n_cells, void *dy2p,
+                           float *dwfc1, float *dbfc1, void *ws, size_t ws_bytes, tdp_stream_t stream)
+{
+    if (n_cells < 1 || !dh1 || !y2 || !wfc1 || !dy2p || !dwfc1 || !dbfc1)
+        return TDP_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < tdp_cnn_fc1_bwd_workspace(n_cells))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int M = (int)n_cells;
+    // dgrad: dy2p[cell][f] = (sum_u dh1[cell][u] wfc1[u][f]) * (y2 > 0)
+    {
+        LoadK la{(const bf16 *)dh1, M, HID};
+        LoadMN lb{(const bf16 *)wfc1, FEAT, FEAT};
+        EpiMaskedBf16 epi{(bf16 *)dy2p, (const bf16 *)y2, M, FEAT};
+        tdp_status st = cerr(launch_gemm<128, 128, 2, 4>(la, lb, epi, M, FEAT, HID, 1, s));
+        if (st != TDP_OK)
+            return st;
+    }
+    // wgrad: dwfc1[u][f] = sum_cell dh1[cell][u] y2[cell][f]
+    float *part = (float *)ws;
+    {
+        LoadMN la{(const bf16 *)dh1, HID, HID};
+        LoadMN lb{(const bf16 *)y2, FEAT, FEAT};
+        EpiPartialF32 epi{part, HID, FEAT, (size_t)HID * FEAT};
+        tdp_status st = cerr(launch_gemm<128, 128, 2, 4>(la, lb, epi, HID, FEAT, M, FC1_WGRAD_SPLITS, s));
+        if (st != TDP_OK)
+            return st;
+        long long n = (long long)HID * FEAT;
+        splitk_reduce_kernel<<<blocks_for(n, 256), 256, 0, s>>>(part, FC1_WGRAD_SPLITS, (size_t)HID * FEAT, n, FEAT,
+                                                                nullptr, 0, nullptr, dwfc1);
+    }
+    // bias: column sums of dh1
+    {
+        float *bp = (float *)((char *)ws + align_up((size_t)FC1_WGRAD_SPLITS * HID * FEAT * sizeof(float), 256));
+        int nb = (int)((n_cells + 63) / 64);
+        colsum_bf16_kernel<<<nb, 256, HID * sizeof(float), s>>>((const bf16 *)dh1, n_cells, HID, bp);
+        partial_sum_kernel<<<1, HID, 0, s>>>(bp, nb, HID, HID, dbfc1);
+    }
+    return launch_status();
+}
+
+size_t tdp_cnn_conv2_bwd_workspace(int64_t n_cells)
+{
+    int sp = conv2_wgrad_splits(n_cells);
+    long long Q = n_cells * PO * PO;
+    size_t a = align_up((size_t)sp * CH2 * 9 * CH1 * sizeof(float), 256);
+    size_t b = align_up((size_t)((Q + 255) / 256) * CH2 * sizeof(float), 256);
+    return a + b;
+}
+
+tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void *y1, const void *w2, int64_t n_cells,
+                             void *dz1, float *dw2, float *db2, void *ws, size_t ws_bytes, tdp_stream_t stream)
+{
+    if (n_cells < 1 || !dy2p || !argmax || !y1 || !w2 || !dw2 || !db2)
+        return TDP_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < tdp_cnn_conv2_bwd_workspace(n_cells))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    // dgrad (optional): dz1[cell][y][x][ci] = (sum dz2 * w2) * (y1 > 0)
+    if (dz1) {
+        const int M = (int)(n_cells * C1 * C1);
+        LoadConv2DgradA la{(const bf16 *)dy2p, argmax, M};
+        LoadConv2DgradB lb{(const bf16 *)w2};
+        EpiMaskedBf16 epi{(bf16 *)dz1, (const bf16 *)y1, M, CH1};
+        tdp_status st = cerr(launch_gemm<128, 32, 8, 1>(la, lb, epi, M, CH1, 9 * CH2, 1, s));
+        if (st != TDP_OK)
+            return st;
+    }
+    // wgrad: dw2[co][(ky,kx,ci)] = sum_p dz2[p][co] y1[p+(ky,kx)][ci]
+    const int sp = conv2_wgrad_splits(n_cells);
+    float *part = (float *)ws;
+    {
+        const int K = (int)(n_cells * C2 * C2);
+        LoadConv2WgradA la{(const bf16 *)dy2p, argmax};
+        LoadConv2WgradB lb{(const bf16 *)y1};
+        EpiPartialF32 epi{part, CH2, 9 * CH1, (size_t)CH2 * 9 * CH1};
+        tdp_status st = cerr(launch_gemm<64, 96, 4, 2>(la, lb, epi, CH2, 9 * CH1, K, sp, s));
+        if (st != TDP_OK)
+            return st;
+        partial_sum_kernel<<<blocks_for(CH2 * 9 * CH1, 256), 256, 0, s>>>(part, sp, CH2 * 9 * CH1, CH2 * 9 * CH1,
+                                                                           dw2);
+    }
+    // bias: sum of the pooled gradient (each pooled value lands on exactly one pixel)
+    {
+        float *bp = (float *)((char *)ws + align_up((size_t)sp * CH2 * 9 * CH1 * sizeof(float), 256));
+        long long Q = n_cells * PO * PO;
+        int nb = (int)((Q + 255) / 256);
+        colsum_bf16_kernel<<<nb, 256, CH2 * sizeof(float), s>>>((const bf16 *)dy2p, Q, CH2, bp);
+        partial_sum_kernel<<<1, CH2, 0, s>>>(bp, nb, CH2, CH2, db2);
+    }
+    return launch_status();
+}
+
+size_t tdp_cnn_conv1_bwd_workspace(int64_t n_cells)
+{
+    (void)n_cells;
+    return align_up((size_t)4 * num_sms() * CH1 * 10 * sizeof(float), 256);
+}
+
+tdp_status tdp_cnn_conv1_bwd(const void *dz1, const uint8_t *grids, int64_t n_cells, float *dw1, float *db1, void *ws,
+                             size_t ws_bytes, tdp_stream_t stream)
+{
+    if (n_cells < 1 || n_cells % CELLS_PER_GRID || !dz1 || !grids || !dw1 || !db1)
+        return TDP_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < tdp_cnn_conv1_bwd_workspace(n_cells))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    long long P = n_cells * C1 * C1;
+    int nb = std::max(1, std::min(4 * num_sms(), (int)((P + 1023) / 1024)));
+    long long chunk = (P + nb - 1) / nb;
+    float *part = (float *)ws;
+    conv1_wgrad_kernel<<<nb, CH1 * 10, 0, s>>>((const bf16 *)dz1, grids, n_cells, chunk, part);
+    // each partial row: 288 weight sums, then the 32 bias sums
+    partial_sum_kernel<<<blocks_for(CH1 * 9, 256), 256, 0, s>>>(part, nb, CH1 * 9, CH1 * 10, dw1);
+    partial_sum_kernel<<<1, CH1, 0, s>>>(part + CH1 * 9, nb, CH1, CH1 * 10, db1);
+    return launch_status();
+}
+
+tdp_status tdp_adam_step(float *const *params, const float *const *grads, float *const *m, float *const *v,
+                         void *const *bf16_copies, const int64_t *sizes, int32_t count, int32_t step, float lr,
+                         float beta1, float beta2, float eps, tdp_stream_t stream)
+{
+    if (count < 1 || count > 8 || step < 1 || !params || !grads || !m || !v || !sizes)
+        return TDP_ERR_INVALID_ARG;
+    AdamSet as;
+    as.count = count;
+    as.off[0] = 0;
+    for (int i = 0; i < 8; i++) {
+        bool on = i < count;
+        as.p[i] = on ? params[i] : nullptr;
+        as.g[i] = on ? grads[i] : nullptr;
+        as.m[i] = on ? m[i] : nullptr;
+        as.v[i] = on ? v[i] : nullptr;
+        as.copy[i] = on && bf16_copies ? (bf16 *)bf16_copies[i] : nullptr;
+        if (on && (!as.p[i] || !as.g[i] || !as.m[i] || !as.v[i] || sizes[i] < 0))
+            return TDP_ERR_INVALID_ARG;
+        as.off[i + 1] = as.off[i] + (on ? sizes[i] : 0);
+    }
+    long long total = as.off[count];
+    if (total == 0)
+        return TDP_OK;
+    float c1 = (float)(1.0 / (1.0 - pow((double)beta1, step)));
+    float c2 = (float)(1.0 / (1.0 - pow((double)beta2, step)));
+    unsigned grid = (unsigned)std::min<long long>((total + 255) / 256, (long long)num_sms() * 8);
+    adam_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(as, lr, beta1, beta2, eps, c1, c2);
+    return launch_status();
+}
+
+tdp_status tdp_f32_to_bf16(const float *x, int64_t n, void *y, tdp_stream_t stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y)))
+        return TDP_ERR_INVALID_ARG;
+    if (n == 0)
+        return TDP_OK;
+    f32_to_bf16_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(x, n, (bf16 *)y);
+    return launch_status();
+}
+
+tdp_status tdp_exact_pe_count(const float *logits, int64_t n_grids, int32_t K, int32_t grid_h, int32_t grid_w,
+                              int32_t *labels, int64_t *cnt, int64_t *rsum, tdp_stream_t stream)
+{
+    if (n_grids < 0 || K < 1 || grid_h < 1 || grid_w < 1 || (n_grids > 0 && (!logits || !cnt || !rsum)))
+        return TDP_ERR_INVALID_ARG;
+    if (n_grids == 0)
+        return TDP_OK;
+    exact_count_kernel<<<blocks_for(n_grids, 128), 128, 0, (cudaStream_t)stream>>>(
+        logits, n_grids, K, grid_h, grid_w, labels, (long long *)cnt, (long long *)rsum);
+    return launch_status();
+}
+
+tdp_status tdp_pe_groupby_fwd(const float *P, int64_t n_grids, int32_t K, int32_t grid_h, int32_t grid_w, float *cnt,
+                              float *rsum, tdp_stream_t stream)
+{
+    if (n_grids < 0 || K < 1 || grid_h < 1 || grid_w < 1 || (n_grids > 0 && (!P || !cnt || !rsum)))
+        return TDP_ERR_INVALID_ARG;
+    long long n = n_grids * (K + grid_h);
+    if (n == 0)
+        return TDP_OK;
+    pe_groupby_fwd_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(P, n_grids, K, grid_h, grid_w, cnt,
+                                                                                rsum);
+    return launch_status();
+}
+
+tdp_status tdp_pe_groupby_bwd(const float *dcnt, const float *drsum, int64_t n_grids, int32_t K, int32_t grid_h,
+                              int32_t grid_w, float *dP, tdp_stream_t stream)
+{
+    if (n_grids < 0 || K < 1 || grid_h < 1 || grid_w < 1 || (n_grids > 0 && (!dcnt || !drsum || !dP)))
+        return TDP_ERR_INVALID_ARG;
+    long long n = n_grids * grid_h * grid_w * K;
+    if (n == 0)
+        return TDP_OK;
+    pe_groupby_bwd_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(dcnt, drsum, n_grids, K, grid_h,
+                                                                                grid_w, dP);
+    return launch_status();
+}
+
+} // extern "C"

@@ -153,6 +153,64 @@ __device__ __forceinline__ void load4_int(const void *p, int dt, bool vec_ok, lo
         v[k] = (r + k < n) ? load_int(p, dt, r + k) : 0;
 }
 
+// Loads rows r0 + j*128 + {0..3} for j < STEPS of one integer column.  The
+// dtype switch sits outside the step loop so that all STEPS vector loads are
+// issued before any result is used.
+template <int STEPS>
+__device__ __forceinline__ void load_rows(const void *p, int dt, bool vec_ok, long long r0, long long n,
+                                          long long (&v)[STEPS][4])
+{
+    if (vec_ok && r0 + (STEPS - 1) * 128 + 3 < n) {
+        if (dt == TDP_I32) {
+            int4 w[STEPS];
+#pragma unroll
+            for (int j = 0; j < STEPS; j++)
+                w[j] = __ldg((const int4 *)((const int32_t *)p + r0 + j * 128));
+#pragma unroll
+            for (int j = 0; j < STEPS; j++) {
+                v[j][0] = w[j].x;
+                v[j][1] = w[j].y;
+                v[j][2] = w[j].z;
+                v[j][3] = w[j].w;
+            }
+            return;
+        }
+        if (dt == TDP_I8 || dt == TDP_U8) {
+            unsigned w[STEPS];
+#pragma unroll
+            for (int j = 0; j < STEPS; j++)
+                w[j] = __ldg((const unsigned *)((const uint8_t *)p + r0 + j * 128));
+#pragma unroll
+            for (int j = 0; j < STEPS; j++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    unsigned b = (w[j] >> (8 * k)) & 0xffu;
+                    v[j][k] = dt == TDP_I8 ? (long long)(int8_t)b : (long long)b;
+                }
+            return;
+        }
+        if (dt == TDP_I64) {
+            longlong2 a[STEPS], b[STEPS];
+#pragma unroll
+            for (int j = 0; j < STEPS; j++) {
+                a[j] = __ldg((const longlong2 *)((const long long *)p + r0 + j * 128));
+                b[j] = __ldg((const longlong2 *)((const long long *)p + r0 + j * 128 + 2));
+            }
+#pragma unroll
+            for (int j = 0; j < STEPS; j++) {
+                v[j][0] = a[j].x;
+                v[j][1] = a[j].y;
+                v[j][2] = b[j].x;
+                v[j][3] = b[j].y;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < STEPS; j++)
+        load4_int(p, dt, vec_ok, r0 + j * 128, n, v[j]);
+}
+
 __device__ __forceinline__ bool cmp_holds(long long v, int cmp, long long lit)
 {
     switch (cmp) {
@@ -200,15 +258,23 @@ constexpr unsigned long long LB_AGG = 1ull << 62;
 constexpr unsigned long long LB_INC = 2ull << 62;
 constexpr unsigned long long LB_VAL = (1ull << 62) - 1;
 
+// True once any bounded wait of the call has timed out: later waits give up
+// at once, so one stuck chain cannot make every tile wait its full limit.
+__device__ __forceinline__ bool timed_out_already(const int32_t *d_status)
+{
+    return d_status && (*(volatile const int32_t *)d_status & TDP_ERR_TIMEOUT);
+}
+
 // Bounded spin on one status word until its flag is non-zero.  Gives up
-// after `limit` polls, sets TDP_ERR_TIMEOUT and returns the word as read.
+// after `limit` polls (or when another wait already gave up), sets
+// TDP_ERR_TIMEOUT and returns the word as read.
 __device__ __forceinline__ unsigned long long lb_wait(const unsigned long long *w, uint32_t limit,
                                                       int32_t *d_status)
 {
     unsigned long long s = ld_relaxed_u64(w);
     uint32_t polls = 0;
     while ((s >> 62) == 0) {
-        if (polls++ >= limit) {
+        if (polls++ >= limit || ((polls & 63) == 0 && timed_out_already(d_status))) {
             set_status(d_status, TDP_ERR_TIMEOUT);
             return s;
         }

@@ -18,44 +18,6 @@ constexpr int FT_STEPS = 4;
 constexpr int FT_WARP_ROWS = FT_STEPS * 128;
 constexpr int FT_TILE = FT_THREADS / 32 * FT_WARP_ROWS; // 4096
 
-// Loads the 4 rows r..r+3 of every step for one integer column.
-__device__ __forceinline__ void load_steps(const void *p, int dt, bool vec_ok, long long r0, long long n,
-                                           long long v[FT_STEPS][4])
-{
-    const bool full = vec_ok && (r0 + (FT_STEPS - 1) * 128 + 3 < n);
-    if (full && dt == TDP_I32) {
-        int4 w[FT_STEPS];
-#pragma unroll
-        for (int j = 0; j < FT_STEPS; j++)
-            w[j] = __ldg((const int4 *)((const int32_t *)p + r0 + j * 128));
-#pragma unroll
-        for (int j = 0; j < FT_STEPS; j++) {
-            v[j][0] = w[j].x;
-            v[j][1] = w[j].y;
-            v[j][2] = w[j].z;
-            v[j][3] = w[j].w;
-        }
-        return;
-    }
-    if (full && (dt == TDP_I8 || dt == TDP_U8)) {
-        unsigned w[FT_STEPS];
-#pragma unroll
-        for (int j = 0; j < FT_STEPS; j++)
-            w[j] = __ldg((const unsigned *)((const uint8_t *)p + r0 + j * 128));
-#pragma unroll
-        for (int j = 0; j < FT_STEPS; j++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                unsigned b = (w[j] >> (8 * k)) & 0xffu;
-                v[j][k] = dt == TDP_I8 ? (long long)(int8_t)b : (long long)b;
-            }
-        return;
-    }
-#pragma unroll
-    for (int j = 0; j < FT_STEPS; j++)
-        load4_int(p, dt, vec_ok, r0 + j * 128, n, v[j]);
-}
-
 // Copies element k (0..3) of a 4-row group at row r of a column of `size`
 // bytes to out[pos].
 __device__ __forceinline__ void gather_store(const void *col, void *out, int size, bool vec_ok, long long r,
@@ -144,7 +106,7 @@ __global__ void __launch_bounds__(FT_THREADS) filter_kernel(PredSet ps, GatherSe
     }
     for (int p = 0; p < ps.n; p++) {
         long long v[FT_STEPS][4];
-        load_steps(ps.col[p], ps.dt[p], ps.vec_ok[p], r0, n, v);
+        load_rows<FT_STEPS>(ps.col[p], ps.dt[p], ps.vec_ok[p], r0, n, v);
 #pragma unroll
         for (int j = 0; j < FT_STEPS; j++)
 #pragma unroll

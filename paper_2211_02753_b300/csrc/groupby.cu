@@ -59,6 +59,23 @@ tdp_status make_aggset(const tdp_col *cols, int32_t ncols, const tdp_agg *aggs, 
         }
         as->slot[a] = as->nslots++;
     }
+    for (int s = 0; s <= TDP_MAX_AGGS; s++) {
+        as->sa[s] = as->sb[s] = nullptr;
+        as->sadt[s] = as->sbdt[s] = TDP_I64;
+        as->sk[s] = 0;
+        as->sop[s] = TDP_AGG_COUNT;
+    }
+    for (int a = 0; a < naggs; a++) {
+        int s = as->slot[a];
+        if (s == 0)
+            continue;
+        as->sa[s] = as->a[a];
+        as->sb[s] = as->b[a];
+        as->sadt[s] = as->adt[a];
+        as->sbdt[s] = as->bdt[a];
+        as->sk[s] = as->k[a];
+        as->sop[s] = as->op[a];
+    }
     return TDP_OK;
 }
 

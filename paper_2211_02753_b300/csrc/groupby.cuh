@@ -29,7 +29,26 @@ struct AggSet {
     int32_t slot[TDP_MAX_AGGS];
     int32_t n;
     int32_t nslots; // 1 + number of non-COUNT aggregates
+    // The same aggregates indexed by accumulator slot (slot 0: COUNT), so that
+    // kernels can loop over slots with compile-time indices.
+    const void *sa[TDP_MAX_AGGS + 1];
+    const void *sb[TDP_MAX_AGGS + 1];
+    int32_t sadt[TDP_MAX_AGGS + 1];
+    int32_t sbdt[TDP_MAX_AGGS + 1];
+    long long sk[TDP_MAX_AGGS + 1];
+    int32_t sop[TDP_MAX_AGGS + 1];
 };
+
+// Contribution of `row` to accumulator slot s (slot 0 counts rows).
+__device__ __forceinline__ long long slot_value(const AggSet &as, int s, long long row)
+{
+    if (s == 0)
+        return 1;
+    long long va = load_int(as.sa[s], as.sadt[s], row);
+    if (as.sop[s] == TDP_AGG_SUM_MUL_KMINUS)
+        va *= as.sk[s] - load_int(as.sb[s], as.sbdt[s], row);
+    return va;
+}
 
 tdp_status make_aggset(const tdp_col *cols, int32_t ncols, const tdp_agg *aggs, int32_t naggs, int64_t n,
                        AggSet *out);

@@ -129,9 +129,10 @@ struct __align__(16) SegRec {
     long long s_inc[SR_MAXS];
 };
 
-struct SegVal {
+template <int SL>
+struct SegValT {
     unsigned h;
-    long long s[SR_MAXS];
+    long long s[SL];
 };
 
 __device__ __forceinline__ long long comb(int op, long long a, long long b)
@@ -140,11 +141,13 @@ __device__ __forceinline__ long long comb(int op, long long a, long long b)
 }
 
 // a then b
-__device__ __forceinline__ void seg_combine(const int *ops, int NS, const SegVal &a, const SegVal &b, SegVal &r)
+template <int SL>
+__device__ __forceinline__ void seg_combine(const int *ops, int NS, const SegValT<SL> &a, const SegValT<SL> &b,
+                                            SegValT<SL> &r)
 {
     r.h = a.h + b.h;
 #pragma unroll
-    for (int j = 0; j < SR_MAXS; j++)
+    for (int j = 0; j < SL; j++)
         if (j < NS)
             r.s[j] = b.h ? b.s[j] : comb(ops[j], a.s[j], b.s[j]);
 }
@@ -159,7 +162,7 @@ __device__ __forceinline__ void store_key(void *out, int dt, long long pos, long
     }
 }
 
-template <typename K>
+template <typename K, int SL>
 __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restrict__ keys,
                                                                 const uint32_t *__restrict__ rows, long long n_max,
                                                                 const long long *d_n, KeySet ks, KeyPack kp,
@@ -167,40 +170,48 @@ __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restr
                                                                 long long *d_ngroups, SegRec *recs, unsigned *ticket,
                                                                 int32_t *d_status, uint32_t limit)
 {
+    using SV = SegValT<SL>;
     __shared__ long long s_tile;
-    __shared__ SegVal s_warp[SR_THREADS / 32];
-    __shared__ SegVal s_carry;
+    __shared__ SV s_warp[SR_THREADS / 32];
+    __shared__ SV s_carry;
     __shared__ int s_ops[SR_MAXS];
     __shared__ long long s_init[SR_MAXS];
-    if (threadIdx.x == 0)
-        s_tile = atomicAdd(ticket, 1u);
+    // parameter structs indexed with run-time indices live in shared memory
+    // (indexing the kernel parameters directly would copy them to local memory)
+    __shared__ AggSet s_as;
+    __shared__ DenseOut s_out;
+    if (threadIdx.x == 0) {
+        s_as = as;
+        s_out = out;
+    }
     if (threadIdx.x < SR_MAXS) {
-        int s = threadIdx.x, op = TDP_AGG_SUM;
-        for (int a = 0; a < as.n; a++)
-            if (as.slot[a] == s && s != 0)
-                op = as.op[a];
+        int s = threadIdx.x, op = as.sop[s] == TDP_AGG_COUNT ? TDP_AGG_SUM : as.sop[s];
         s_ops[s] = op;
         s_init[s] = op == TDP_AGG_MIN ? 0x7fffffffffffffffll : op == TDP_AGG_MAX ? (long long)0x8000000000000000ull : 0;
     }
+    const long long n = d_n ? min(*d_n, n_max) : n_max;
+    // persistent: tiles are taken in ticket order until the input runs out
+    for (;;) {
+    if (threadIdx.x == 0)
+        s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
     const long long tile = s_tile;
-    const long long n = d_n ? min(*d_n, n_max) : n_max;
     const long long tile_base = tile * SR_TILE;
     if (tile_base >= n)
         return;
     const int NS = as.nslots;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long i0 = tile_base + (long long)threadIdx.x * SR_ITEMS;
-    int ops[SR_MAXS];
+    int ops[SL];
 #pragma unroll
-    for (int j = 0; j < SR_MAXS; j++)
+    for (int j = 0; j < SL; j++)
         ops[j] = s_ops[j];
 
     // thread fold: (heads, aggregates since the last head)
-    SegVal mine;
+    SV mine;
     mine.h = 0;
 #pragma unroll
-    for (int j = 0; j < SR_MAXS; j++)
+    for (int j = 0; j < SL; j++)
         mine.s[j] = s_init[j];
     K prev = (i0 > 0 && i0 - 1 < n) ? keys[i0 - 1] : (K)0;
     unsigned headmask = 0;
@@ -215,31 +226,26 @@ __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restr
             headmask |= 1u << it;
             mine.h++;
 #pragma unroll
-            for (int j = 0; j < SR_MAXS; j++)
+            for (int j = 0; j < SL; j++)
                 mine.s[j] = s_init[j];
         }
-        long long row = rows[i];
-        mine.s[0] += 1;
-        for (int a = 0; a < as.n; a++) {
-            if (as.op[a] == TDP_AGG_COUNT)
-                continue;
-            long long va = load_int(as.a[a], as.adt[a], row);
-            long long vb = as.op[a] == TDP_AGG_SUM_MUL_KMINUS ? load_int(as.b[a], as.bdt[a], row) : 0;
-            int s = as.slot[a];
-            mine.s[s] = comb(ops[s], mine.s[s], agg_value(as, a, va, vb));
-        }
+        const long long row = rows[i];
+#pragma unroll
+        for (int j = 0; j < SL; j++)
+            if (j < NS)
+                mine.s[j] = comb(ops[j], mine.s[j], slot_value(as, j, row));
     }
     // warp inclusive scan
-    SegVal inc = mine;
+    SV inc = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        SegVal up;
+        SV up;
         up.h = __shfl_up_sync(0xffffffffu, inc.h, o);
 #pragma unroll
-        for (int j = 0; j < SR_MAXS; j++)
+        for (int j = 0; j < SL; j++)
             up.s[j] = __shfl_up_sync(0xffffffffu, inc.s[j], o);
         if (lane >= o) {
-            SegVal r;
+            SV r;
             seg_combine(ops, NS, up, inc, r);
             inc = r;
         }
@@ -247,117 +253,155 @@ __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restr
     if (lane == 31)
         s_warp[warp] = inc;
     // lane-exclusive within the warp
-    SegVal lex;
+    SV lex;
     lex.h = __shfl_up_sync(0xffffffffu, inc.h, 1);
 #pragma unroll
-    for (int j = 0; j < SR_MAXS; j++)
+    for (int j = 0; j < SL; j++)
         lex.s[j] = __shfl_up_sync(0xffffffffu, inc.s[j], 1);
     if (lane == 0) {
         lex.h = 0;
 #pragma unroll
-        for (int j = 0; j < SR_MAXS; j++)
+        for (int j = 0; j < SL; j++)
             lex.s[j] = s_init[j];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // tile aggregate = fold of warp totals
-        SegVal agg = s_warp[0];
+    if (warp == 0) {
+        // tile aggregate = fold of the warp totals (every lane computes it)
+        SV agg = s_warp[0];
         for (int w = 1; w < SR_THREADS / 32; w++) {
-            SegVal r;
+            SV r;
             seg_combine(ops, NS, agg, s_warp[w], r);
             agg = r;
         }
         SegRec *me = recs + tile;
-        SegVal excl;
+        SV excl;
         excl.h = 0;
-        for (int j = 0; j < SR_MAXS; j++)
+#pragma unroll
+        for (int j = 0; j < SL; j++)
             excl.s[j] = s_init[j];
         if (tile == 0) {
-            me->h_inc = agg.h;
-            for (int j = 0; j < NS; j++)
-                me->s_inc[j] = agg.s[j];
-            __threadfence();
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(2u) : "memory");
-        } else {
-            me->h_agg = agg.h;
-            for (int j = 0; j < NS; j++)
-                me->s_agg[j] = agg.s[j];
-            __threadfence();
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(1u) : "memory");
-            // walk back: excl = pred (+) excl (predecessors come before)
-            for (long long t = tile - 1; t >= 0; t--) {
-                const SegRec *pr = recs + t;
-                unsigned f;
-                uint32_t polls = 0;
-                while (true) {
-                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&pr->flag) : "memory");
-                    if (f != 0)
-                        break;
-                    if (polls++ >= limit) {
-                        set_status(d_status, TDP_ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(polls < 64 ? 20 : 200);
-                }
-                if (f == 0)
-                    break;
-                SegVal pv;
-                pv.h = f == 2 ? *(volatile const unsigned *)&pr->h_inc : *(volatile const unsigned *)&pr->h_agg;
-                for (int j = 0; j < SR_MAXS; j++)
-                    pv.s[j] = j >= NS ? s_init[j]
-                                      : (f == 2 ? *(volatile const long long *)&pr->s_inc[j]
-                                                : *(volatile const long long *)&pr->s_agg[j]);
-                SegVal r;
-                seg_combine(ops, NS, pv, excl, r);
-                excl = r;
-                if (f == 2)
-                    break;
+            if (lane == 0) {
+                me->h_inc = agg.h;
+#pragma unroll
+                for (int j = 0; j < SL; j++)
+                    if (j < NS)
+                        me->s_inc[j] = agg.s[j];
+                __threadfence();
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(2u) : "memory");
             }
-            SegVal incl;
-            seg_combine(ops, NS, excl, agg, incl);
-            me->h_inc = incl.h;
-            for (int j = 0; j < NS; j++)
-                me->s_inc[j] = incl.s[j];
-            __threadfence();
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(2u) : "memory");
+        } else {
+            if (lane == 0) {
+                me->h_agg = agg.h;
+#pragma unroll
+                for (int j = 0; j < SL; j++)
+                    if (j < NS)
+                        me->s_agg[j] = agg.s[j];
+                __threadfence();
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(1u) : "memory");
+            }
+            // warp-parallel look-back: lane l reads the record of tile base-l;
+            // the records up to the nearest inclusive one are folded in order
+            // (earlier tiles first) and prepended to what was gathered so far.
+            long long base = tile - 1;
+            while (true) {
+                const long long t = base - lane;
+                unsigned f = 2;
+                SV pv;
+                pv.h = 0;
+#pragma unroll
+                for (int j = 0; j < SL; j++)
+                    pv.s[j] = s_init[j];
+                if (t >= 0) {
+                    const SegRec *pr = recs + t;
+                    uint32_t polls = 0;
+                    while (true) {
+                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&pr->flag) : "memory");
+                        if (f != 0)
+                            break;
+                        if (polls++ >= limit || ((polls & 63) == 0 && timed_out_already(d_status))) {
+                            set_status(d_status, TDP_ERR_TIMEOUT);
+                            break; // f == 0: treated as an (empty) inclusive record
+                        }
+                        __nanosleep(polls < 64 ? 20 : 200);
+                    }
+                    if (f != 0) {
+                        pv.h = f == 2 ? *(volatile const unsigned *)&pr->h_inc : *(volatile const unsigned *)&pr->h_agg;
+#pragma unroll
+                        for (int j = 0; j < SL; j++)
+                            if (j < NS)
+                                pv.s[j] = f == 2 ? *(volatile const long long *)&pr->s_inc[j]
+                                                 : *(volatile const long long *)&pr->s_agg[j];
+                    }
+                }
+                const unsigned incl_mask = __ballot_sync(0xffffffffu, f != 1);
+                const int k = incl_mask ? __ffs(incl_mask) - 1 : 31;
+                SV w;
+                w.h = 0;
+#pragma unroll
+                for (int j = 0; j < SL; j++)
+                    w.s[j] = s_init[j];
+                for (int src = k; src >= 0; src--) { // k is warp-uniform
+                    SV pj, r;
+                    pj.h = __shfl_sync(0xffffffffu, pv.h, src);
+#pragma unroll
+                    for (int j = 0; j < SL; j++)
+                        pj.s[j] = __shfl_sync(0xffffffffu, pv.s[j], src);
+                    seg_combine(ops, NS, w, pj, r);
+                    w = r;
+                }
+                SV r;
+                seg_combine(ops, NS, w, excl, r);
+                excl = r;
+                if (incl_mask)
+                    break;
+                base -= 32;
+            }
+            if (lane == 0) {
+                SV incl;
+                seg_combine(ops, NS, excl, agg, incl);
+                me->h_inc = incl.h;
+#pragma unroll
+                for (int j = 0; j < SL; j++)
+                    if (j < NS)
+                        me->s_inc[j] = incl.s[j];
+                __threadfence();
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(2u) : "memory");
+            }
         }
-        s_carry = excl;
+        if (lane == 0)
+            s_carry = excl;
     }
     __syncthreads();
     // carry into this thread = tile excl (+) warps before (+) lanes before
-    SegVal carry = s_carry;
+    SV carry = s_carry;
     for (int w = 0; w < warp; w++) {
-        SegVal r;
+        SV r;
         seg_combine(ops, NS, carry, s_warp[w], r);
         carry = r;
     }
     {
-        SegVal r;
+        SV r;
         seg_combine(ops, NS, carry, lex, r);
         carry = r;
     }
     // emit groups that end inside this thread's items
     long long g = (long long)carry.h - 1;
-    SegVal run = carry;
+    SV run = carry;
     for (int it = 0; it < SR_ITEMS; it++) {
         long long i = i0 + it;
         if (i >= n)
             break;
-        long long row = rows[i];
+        const long long row = rows[i];
         if (headmask >> it & 1) {
             g++;
-            for (int j = 0; j < SR_MAXS; j++)
+#pragma unroll
+            for (int j = 0; j < SL; j++)
                 run.s[j] = s_init[j];
         }
-        run.s[0] += 1;
-        for (int a = 0; a < as.n; a++) {
-            if (as.op[a] == TDP_AGG_COUNT)
-                continue;
-            long long va = load_int(as.a[a], as.adt[a], row);
-            long long vb = as.op[a] == TDP_AGG_SUM_MUL_KMINUS ? load_int(as.b[a], as.bdt[a], row) : 0;
-            int s = as.slot[a];
-            run.s[s] = comb(ops[s], run.s[s], agg_value(as, a, va, vb));
-        }
+#pragma unroll
+        for (int j = 0; j < SL; j++)
+            if (j < NS)
+                run.s[j] = comb(ops[j], run.s[j], slot_value(as, j, row));
         bool last = (i == n - 1);
         K key = keys[i];
         if (!last)
@@ -378,10 +422,24 @@ __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restr
                         if (ks.dt[k] == TDP_U8)
                             v = (long long)f;
                     }
-                    store_key(out.key_out[k], out.key_dt[k], g, v);
+                    store_key(s_out.key_out[k], s_out.key_dt[k], g, v);
                 }
-                for (int a = 0; a < as.n; a++)
-                    out.agg_out[a][g] = agg_final(as, a, run.s);
+                // aggregates by slot (compile-time slot index; AVG needs the count)
+#pragma unroll
+                for (int j = 0; j < SL; j++) {
+                    if (j >= NS)
+                        continue;
+                    for (int a = 0; a < s_as.n; a++) {
+                        if (s_as.slot[a] != j)
+                            continue;
+                        long long v = run.s[j];
+                        if (s_as.op[a] == TDP_AGG_AVG) {
+                            long long c = run.s[0], sg = v > 0 ? 1 : (v < 0 ? -1 : 0);
+                            v = (2 * v + sg * c) / (2 * c);
+                        }
+                        s_out.agg_out[a][g] = v;
+                    }
+                }
             }
             if (i == n - 1) {
                 *d_ngroups = g + 1;
@@ -389,6 +447,8 @@ __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restr
                     set_status(d_status, TDP_ERR_CAPACITY);
             }
         }
+    }
+    __syncthreads(); // s_warp / s_carry are reused by the next tile
     }
 }
 
@@ -461,9 +521,18 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
         return launch_status();
     cudaMemsetAsync(segws, 0, seg_ws(n), s);
     long long tiles = (n + SR_TILE - 1) / SR_TILE;
-    seg_reduce_kernel<K><<<(unsigned)tiles, SR_THREADS, 0, s>>>(
-        sk, sr, n, rowcount, ks, kp, as, out, capacity, (long long *)d_ngroups, (SegRec *)(segws + 256),
-        (unsigned *)segws, d_status, spin_limit());
+    const unsigned sgrid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 3);
+    // accumulator slots carried through the scan: the smallest of 2, 4, 9 that fits
+    auto launch = [&](auto kern) {
+        kern<<<sgrid, SR_THREADS, 0, s>>>(sk, sr, n, rowcount, ks, kp, as, out, capacity, (long long *)d_ngroups,
+                                          (SegRec *)(segws + 256), (unsigned *)segws, d_status, spin_limit());
+    };
+    if (as.nslots <= 2)
+        launch(seg_reduce_kernel<K, 2>);
+    else if (as.nslots <= 4)
+        launch(seg_reduce_kernel<K, 4>);
+    else
+        launch(seg_reduce_kernel<K, SR_MAXS>);
     return launch_status();
 }
 

@@ -4,13 +4,14 @@
 // | payload, empty = all ones (so the pair key = -1, payload = -1 cannot be
 // stored; the build flags it as TDP_ERR_OVERFLOW).  Multiplicative (Fibonacci)
 // hash, linear probing, one 64-bit CAS per insert, probe length bounded by
-// nslots.
+// min(nslots, 65536).
 //
 // Probe: same tile structure as the filter (256 threads x 16 rows, 4 steps of
 // 128 rows per warp, lane = 4 consecutive rows): the probe-side predicates
-// and keys are read with 16-byte loads, all 16 first-slot lookups of a thread
-// are issued before any is examined (16 independent random reads in flight
-// per thread), collisions are walked afterwards, and matches are compacted
+// and keys are read with 16-byte loads, the 16 lookups of a thread advance
+// through their collision chains in lock-step rounds (each round issues all
+// outstanding slot loads before examining any, so a thread waits for its
+// longest chain rather than the sum of its chains), and matches are compacted
 // with ballots + decoupled look-back so that the output keeps probe order.
 //
 // Probe + aggregate: the build payload is the group key (dense range
@@ -25,6 +26,10 @@
 namespace tdp {
 
 constexpr unsigned long long EMPTY_SLOT = ~0ull;
+// Longest probe sequence walked by a build insert or a lookup.  Linear probing
+// at load <= 1/2 needs a handful of steps; a longer run means a (nearly) full
+// table, which is reported as TDP_ERR_CAPACITY instead of being walked.
+constexpr unsigned long long MAX_PROBE = 1ull << 16;
 
 __device__ __forceinline__ unsigned hash_slot(int key, int lg)
 {
@@ -58,7 +63,8 @@ __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, c
         }
         unsigned long long h = hash_slot(k, lg);
         bool done = false;
-        for (long long probe = 0; probe <= (long long)mask; probe++) {
+        const unsigned long long steps = mask + 1 < MAX_PROBE ? mask + 1 : MAX_PROBE;
+        for (unsigned long long probe = 0; probe < steps; probe++) {
             unsigned long long prev = atomicCAS(&table[h], EMPTY_SLOT, v);
             if (prev == EMPTY_SLOT) {
                 done = true;
@@ -78,103 +84,100 @@ __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, c
         set_status(d_status, err);
 }
 
-// Looks up `k`; returns true and the payload if present.
-__device__ __forceinline__ bool probe_walk(const unsigned long long *table, int lg, int k, unsigned long long first,
-                                           unsigned h, unsigned &payload)
-{
-    const unsigned mask = (unsigned)((1ull << lg) - 1);
-    unsigned long long s = first;
-    for (unsigned probe = 0; probe <= mask; probe++) {
-        if (s == EMPTY_SLOT)
-            return false;
-        if ((unsigned)(s >> 32) == (unsigned)k) {
-            payload = (unsigned)s;
-            return true;
-        }
-        h = (h + 1) & mask;
-        s = __ldg(table + h);
-    }
-    return false;
-}
-
 constexpr int JP_THREADS = 256;
-constexpr int JP_STEPS = 4;
+constexpr int JP_STEPS = 2;
 constexpr int JP_WARP_ROWS = JP_STEPS * 128;
 constexpr int JP_TILE = JP_THREADS / 32 * JP_WARP_ROWS;
+constexpr int JP_ROWS = JP_STEPS * 4; // rows per thread
 
-// Reads the probe key of the 16 rows of a thread and resolves them.  idx: the
-// thread's first index (multiple of 4); rows are idx + j*128 + e.  When sel is
-// given the index maps to row sel[idx].
-__device__ __forceinline__ void probe16(const unsigned long long *table, int lg, const PredSet &ps,
-                                        const int32_t *key, bool key_vec, const int32_t *sel, long long m,
-                                        long long idx0, unsigned mbits[JP_STEPS], unsigned pay[JP_STEPS][4],
-                                        long long rows[JP_STEPS][4])
+// Reads the probe keys of the 16 rows of a thread and resolves them.  idx0:
+// the thread's first index (multiple of 4); row r = j*4 + e is idx0 + j*128 + e
+// (or sel[...] of it).  All unresolved lookups advance together: every round
+// issues the next slot load of each of them before any is examined, so a
+// thread waits for its longest collision chain, not for the sum of its chains.
+// On return bit r of `hit` is set for rows that qualify and match; pay[r] is
+// the payload, key[r] the probe key, row[r] the row id.
+__device__ __forceinline__ unsigned probe16(const unsigned long long *table, int lg, const PredSet &ps,
+                                            const int32_t *keycol, bool key_vec, const int32_t *sel, long long m,
+                                            long long idx0, unsigned (&pay)[JP_ROWS], int (&key)[JP_ROWS],
+                                            int (&row)[JP_ROWS], bool &gave_up)
 {
+    unsigned hit = 0;
 #pragma unroll
-    for (int j = 0; j < JP_STEPS; j++) {
-        long long i = idx0 + j * 128;
-        mbits[j] = 0;
+    for (int j = 0; j < JP_STEPS; j++)
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            rows[j][e] = i + e < m ? (sel ? (long long)sel[i + e] : i + e) : -1;
-            mbits[j] |= (i + e < m) ? (1u << e) : 0u;
+            long long i = idx0 + j * 128 + e;
+            row[j * 4 + e] = i < m ? (sel ? sel[i] : (int)i) : -1;
+            hit |= (i < m) ? (1u << (j * 4 + e)) : 0u;
         }
-    }
-    // predicates
     if (ps.n > 0) {
         if (!sel) {
             for (int p = 0; p < ps.n; p++) {
+                long long v[JP_STEPS][4];
+                load_rows<JP_STEPS>(ps.col[p], ps.dt[p], ps.vec_ok[p], idx0, m, v);
 #pragma unroll
-                for (int j = 0; j < JP_STEPS; j++) {
-                    long long v[4];
-                    load4_int(ps.col[p], ps.dt[p], ps.vec_ok[p], idx0 + j * 128, m, v);
+                for (int j = 0; j < JP_STEPS; j++)
 #pragma unroll
                     for (int e = 0; e < 4; e++)
-                        if (!cmp_holds(v[e], ps.cmp[p], ps.lit[p]))
-                            mbits[j] &= ~(1u << e);
-                }
+                        if (!cmp_holds(v[j][e], ps.cmp[p], ps.lit[p]))
+                            hit &= ~(1u << (j * 4 + e));
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < JP_STEPS; j++)
-#pragma unroll
-                for (int e = 0; e < 4; e++)
-                    if ((mbits[j] >> e & 1) && !eval_preds1(ps, rows[j][e]))
-                        mbits[j] &= ~(1u << e);
+            for (int r = 0; r < JP_ROWS; r++)
+                if ((hit >> r & 1) && !eval_preds1(ps, row[r]))
+                    hit &= ~(1u << r);
         }
     }
-    int k[JP_STEPS][4];
+    if (!sel && key_vec && idx0 + (JP_STEPS - 1) * 128 + 3 < m) {
+        int4 w[JP_STEPS];
 #pragma unroll
-    for (int j = 0; j < JP_STEPS; j++) {
-        long long i = idx0 + j * 128;
-        if (!sel && key_vec && i + 3 < m) {
-            int4 w = __ldg((const int4 *)(key + i));
-            k[j][0] = w.x, k[j][1] = w.y, k[j][2] = w.z, k[j][3] = w.w;
-        } else {
+        for (int j = 0; j < JP_STEPS; j++)
+            w[j] = __ldg((const int4 *)(keycol + idx0 + j * 128));
 #pragma unroll
-            for (int e = 0; e < 4; e++)
-                k[j][e] = (mbits[j] >> e & 1) ? key[rows[j][e]] : 0;
-        }
+        for (int j = 0; j < JP_STEPS; j++)
+            key[j * 4 + 0] = w[j].x, key[j * 4 + 1] = w[j].y, key[j * 4 + 2] = w[j].z, key[j * 4 + 3] = w[j].w;
+    } else {
+#pragma unroll
+        for (int r = 0; r < JP_ROWS; r++)
+            key[r] = (hit >> r & 1) ? keycol[row[r]] : 0;
     }
-    unsigned long long first[JP_STEPS][4];
-    unsigned h[JP_STEPS][4];
+    const unsigned mask = (unsigned)((1ull << lg) - 1);
+    const unsigned long long steps = (unsigned long long)mask + 1 < MAX_PROBE ? (unsigned long long)mask + 1 : MAX_PROBE;
+    unsigned long long s[JP_ROWS];
+    unsigned h[JP_ROWS];
+    unsigned act = hit;
 #pragma unroll
-    for (int j = 0; j < JP_STEPS; j++)
+    for (int r = 0; r < JP_ROWS; r++) {
+        h[r] = hash_slot(key[r], lg);
+        s[r] = (act >> r & 1) ? __ldg(table + h[r]) : EMPTY_SLOT;
+    }
+    for (unsigned long long round = 0; act && round < steps; round++) {
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            h[j][e] = hash_slot(k[j][e], lg);
-            first[j][e] = (mbits[j] >> e & 1) ? __ldg(table + h[j][e]) : EMPTY_SLOT;
+        for (int r = 0; r < JP_ROWS; r++) {
+            if (!(act >> r & 1))
+                continue;
+            if (s[r] == EMPTY_SLOT) {
+                act &= ~(1u << r);
+                hit &= ~(1u << r);
+            } else if ((unsigned)(s[r] >> 32) == (unsigned)key[r]) {
+                act &= ~(1u << r);
+                pay[r] = (unsigned)s[r];
+            } else {
+                h[r] = (h[r] + 1) & mask;
+            }
         }
 #pragma unroll
-    for (int j = 0; j < JP_STEPS; j++)
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            unsigned p = 0;
-            if ((mbits[j] >> e & 1) && probe_walk(table, lg, k[j][e], first[j][e], h[j][e], p))
-                pay[j][e] = p;
-            else
-                mbits[j] &= ~(1u << e);
-        }
+        for (int r = 0; r < JP_ROWS; r++)
+            if (act >> r & 1)
+                s[r] = __ldg(table + h[r]);
+    }
+    if (act) { // a chain longer than MAX_PROBE: reported, rows dropped
+        gave_up = true;
+        hit &= ~act;
+    }
+    return hit;
 }
 
 __global__ void __launch_bounds__(JP_THREADS) join_probe_kernel(const unsigned long long *__restrict__ table, int lg,
@@ -198,10 +201,12 @@ __global__ void __launch_bounds__(JP_THREADS) join_probe_kernel(const unsigned l
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long idx0 = tile * JP_TILE + (long long)warp * JP_WARP_ROWS + 4 * lane;
 
-    unsigned mb[JP_STEPS];
-    unsigned pay[JP_STEPS][4];
-    long long rows[JP_STEPS][4];
-    probe16(table, lg, ps, key, key_vec, sel, m, idx0, mb, pay, rows);
+    unsigned pay[JP_ROWS];
+    int keys[JP_ROWS], rows[JP_ROWS];
+    bool gave_up = false;
+    const unsigned hit = probe16(table, lg, ps, key, key_vec, sel, m, idx0, pay, keys, rows, gave_up);
+    if (gave_up)
+        set_status(d_status, TDP_ERR_CAPACITY);
 
     const unsigned lt = lanemask_lt();
     unsigned step_cnt[JP_STEPS], lane_pref[JP_STEPS], warp_tot = 0;
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(JP_THREADS) join_probe_kernel(const unsigned l
         unsigned c = 0, pre = 0;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            unsigned b = __ballot_sync(0xffffffffu, (mb[j] >> e) & 1u);
+            unsigned b = __ballot_sync(0xffffffffu, (hit >> (j * 4 + e)) & 1u);
             c += __popc(b);
             pre += __popc(b & lt);
         }
@@ -244,32 +249,71 @@ __global__ void __launch_bounds__(JP_THREADS) join_probe_kernel(const unsigned l
         }
     }
     __syncthreads();
-    long long pos = (long long)s_excl + s_warp_excl[warp];
+    // output slot of every hit (rows of a step land at consecutive slots)
+    long long outp[JP_ROWS];
+    {
+        long long pos = (long long)s_excl + s_warp_excl[warp];
 #pragma unroll
-    for (int j = 0; j < JP_STEPS; j++) {
-        long long p = pos + lane_pref[j];
+        for (int j = 0; j < JP_STEPS; j++) {
+            long long p = pos + lane_pref[j];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            if (!(mb[j] >> e & 1))
-                continue;
-            if (p < cap) {
-                long long row = rows[j][e];
-                if (out_row)
-                    out_row[p] = (int32_t)row;
-                if (out_payload)
-                    out_payload[p] = (int32_t)pay[j][e];
-                for (int g = 0; g < gs.n; g++) {
-                    switch (gs.size[g]) {
-                    case 8: ((long long *)gs.out[g])[p] = ((const long long *)gs.col[g])[row]; break;
-                    case 4: ((int *)gs.out[g])[p] = ((const int *)gs.col[g])[row]; break;
-                    case 2: ((uint16_t *)gs.out[g])[p] = ((const uint16_t *)gs.col[g])[row]; break;
-                    default: ((uint8_t *)gs.out[g])[p] = ((const uint8_t *)gs.col[g])[row]; break;
-                    }
-                }
+            for (int e = 0; e < 4; e++) {
+                outp[j * 4 + e] = p;
+                p += (hit >> (j * 4 + e)) & 1;
             }
-            p++;
+            pos += step_cnt[j];
         }
-        pos += step_cnt[j];
+    }
+    const unsigned wr = hit; // rows written (subject to capacity)
+#pragma unroll
+    for (int r = 0; r < JP_ROWS; r++) {
+        if (!(wr >> r & 1) || outp[r] >= cap)
+            continue;
+        if (out_row)
+            out_row[outp[r]] = rows[r];
+        if (out_payload)
+            out_payload[outp[r]] = (int32_t)pay[r];
+    }
+    // gathers: all loads of a column are issued before its stores
+    for (int g = 0; g < gs.n; g++) {
+        const void *col = gs.col[g];
+        void *out = gs.out[g];
+        if (col == (const void *)key) { // the probe key is already in a register
+#pragma unroll
+            for (int r = 0; r < JP_ROWS; r++)
+                if ((wr >> r & 1) && outp[r] < cap)
+                    ((int *)out)[outp[r]] = keys[r];
+            continue;
+        }
+        if (gs.size[g] == 8) {
+            long long v[JP_ROWS];
+#pragma unroll
+            for (int r = 0; r < JP_ROWS; r++)
+                v[r] = (wr >> r & 1) ? __ldg((const long long *)col + rows[r]) : 0;
+#pragma unroll
+            for (int r = 0; r < JP_ROWS; r++)
+                if ((wr >> r & 1) && outp[r] < cap)
+                    ((long long *)out)[outp[r]] = v[r];
+        } else if (gs.size[g] == 4) {
+            int v[JP_ROWS];
+#pragma unroll
+            for (int r = 0; r < JP_ROWS; r++)
+                v[r] = (wr >> r & 1) ? __ldg((const int *)col + rows[r]) : 0;
+#pragma unroll
+            for (int r = 0; r < JP_ROWS; r++)
+                if ((wr >> r & 1) && outp[r] < cap)
+                    ((int *)out)[outp[r]] = v[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < JP_ROWS; r++) {
+                if (!(wr >> r & 1) || outp[r] >= cap)
+                    continue;
+                if (gs.size[g] == 2)
+                    ((uint16_t *)out)[outp[r]] = ((const uint16_t *)col)[rows[r]];
+                else
+                    ((uint8_t *)out)[outp[r]] = ((const uint8_t *)col)[rows[r]];
+            }
+        }
     }
 }
 
@@ -313,15 +357,49 @@ __global__ void __launch_bounds__(JP_THREADS) join_probe_agg_kernel(const unsign
     for (long long base = (long long)blockIdx.x * JP_TILE; base < n; base += stride) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const long long idx0 = base + (long long)warp * JP_WARP_ROWS + 4 * lane;
-        unsigned mb[JP_STEPS];
-        unsigned pay[JP_STEPS][4];
-        long long rows[JP_STEPS][4];
-        probe16(table, lg, ps, key, key_vec, nullptr, n, idx0, mb, pay, rows);
+        unsigned pay[JP_ROWS];
+        int keys[JP_ROWS], rows[JP_ROWS];
+        bool gave_up = false;
+        const unsigned hit = probe16(table, lg, ps, key, key_vec, nullptr, n, idx0, pay, keys, rows, gave_up);
+        if (gave_up)
+            set_status(d_status, TDP_ERR_CAPACITY);
 #pragma unroll
         for (int j = 0; j < JP_STEPS; j++) {
-            if (!mb[j])
+            unsigned hj = (hit >> (4 * j)) & 0xfu;
+            if (!hj)
                 continue;
-            long long va[TDP_MAX_AGGS][4];
+            long long *dst[4] = {nullptr, nullptr, nullptr, nullptr};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                if (!(hj >> e & 1))
+                    continue;
+                long long gid = (long long)(int)pay[j * 4 + e] - lo;
+                if (gid < 0 || gid >= D) {
+                    bad = true;
+                    hj &= ~(1u << e);
+                    continue;
+                }
+                // find / claim a cache slot
+                unsigned tag = (unsigned)gid + 1u;
+                unsigned h = ((unsigned)gid * 0x9E3779B1u) >> 21; // 11 bits: GJ_CACHE = 2048
+                long long *d = nullptr;
+                for (int q = 0; q < GJ_PROBES; q++) {
+                    unsigned cur = s_key[h];
+                    if (cur == 0)
+                        cur = atomicCAS(&s_key[h], 0u, tag);
+                    if (cur == 0 || cur == tag) {
+                        d = s_acc + h * NS;
+                        break;
+                    }
+                    h = (h + 1) & (GJ_CACHE - 1);
+                }
+                if (!d)
+                    d = gacc + gid * NS;
+                dst[e] = d;
+                atomicAdd((unsigned long long *)&d[0], 1ull);
+            }
+            if (!hj)
+                continue;
             for (int a = 0; a < as.n; a++) {
                 if (as.op[a] == TDP_AGG_COUNT)
                     continue;
@@ -331,37 +409,8 @@ __global__ void __launch_bounds__(JP_THREADS) join_probe_agg_kernel(const unsign
                     load4_int(as.b[a], as.bdt[a], as.bvec[a], idx0 + j * 128, n, y);
 #pragma unroll
                 for (int e = 0; e < 4; e++)
-                    va[a][e] = agg_value(as, a, x[e], y[e]);
-            }
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                if (!(mb[j] >> e & 1))
-                    continue;
-                long long gid = (long long)(int)pay[j][e] - lo;
-                if (gid < 0 || gid >= D) {
-                    bad = true;
-                    continue;
-                }
-                // find / claim a cache slot
-                unsigned tag = (unsigned)gid + 1u;
-                unsigned h = ((unsigned)gid * 0x9E3779B1u) >> 21; // 11 bits: GJ_CACHE = 2048
-                long long *dst = nullptr;
-                for (int q = 0; q < GJ_PROBES; q++) {
-                    unsigned cur = s_key[h];
-                    if (cur == 0)
-                        cur = atomicCAS(&s_key[h], 0u, tag);
-                    if (cur == 0 || cur == tag) {
-                        dst = s_acc + h * NS;
-                        break;
-                    }
-                    h = (h + 1) & (GJ_CACHE - 1);
-                }
-                if (!dst)
-                    dst = gacc + gid * NS;
-                atomicAdd((unsigned long long *)&dst[0], 1ull);
-                for (int a = 0; a < as.n; a++)
-                    if (as.op[a] != TDP_AGG_COUNT)
-                        acc_update(&dst[as.slot[a]], as.op[a], va[a][e]);
+                    if (hj >> e & 1)
+                        acc_update(&dst[e][as.slot[a]], as.op[a], agg_value(as, a, x[e], y[e]));
             }
         }
     }

@@ -91,7 +91,7 @@ __device__ __forceinline__ unsigned rs_wait(const unsigned *w, uint32_t limit, i
     unsigned s = ld_relaxed_u32(w);
     uint32_t polls = 0;
     while ((s >> 30) == 0) {
-        if (polls++ >= limit) {
+        if (polls++ >= limit || ((polls & 63) == 0 && timed_out_already(d_status))) {
             set_status(d_status, TDP_ERR_TIMEOUT);
             *timed_out = true;
             return s;
@@ -120,13 +120,15 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__re
     __shared__ unsigned s_tmp[8];
     __shared__ long long s_tile;
 
+    const long long n = d_n ? min(*d_n, n_max) : n_max;
+    // persistent: tiles are taken in ticket order until the input runs out
+    for (;;) {
     if (threadIdx.x == 0)
         s_tile = atomicAdd(ticket, 1u);
     for (int i = threadIdx.x; i < RS_WARPS * 257; i += RS_THREADS)
         s_whist[i] = 0;
     __syncthreads();
     const long long tile = s_tile;
-    const long long n = d_n ? min(*d_n, n_max) : n_max;
     const long long tile_base = tile * RS_TILE;
     if (tile_base >= n)
         return;
@@ -205,6 +207,8 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__re
         kout[g] = key;
         vout[g] = s_vals[j];
     }
+    __syncthreads(); // shared staging is reused by the next tile
+    }
 }
 
 size_t radix_ws_bytes(long long n, int key_bits, int key_bytes)
@@ -249,11 +253,13 @@ tdp_status radix_sort_pairs(const K *keys_in, const uint32_t *vals_in, long long
         return TDP_ERR_CUDA;
     const K *src_k = keys_in;
     const uint32_t *src_v = vals_in;
+    // persistent grid: as many blocks as fit at once (2 per SM at 128 registers)
+    const unsigned sgrid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 2);
     for (int pass = 0; pass < P; pass++) {
         bool to_out = ((P - 1 - pass) % 2) == 0;
         K *dk = to_out ? keys_out : tmp_k;
         uint32_t *dv = to_out ? vals_out : tmp_v;
-        radix_scatter_kernel<K><<<(unsigned)tiles, RS_THREADS, smem, s>>>(
+        radix_scatter_kernel<K><<<sgrid, RS_THREADS, smem, s>>>(
             src_k, src_v, dk, dv, n_max, d_n, 8 * pass, hist + pass * 256, status + (size_t)pass * tiles * 256,
             tickets + pass, d_status, spin_limit());
         src_k = dk;
@@ -285,7 +291,7 @@ extern "C" tdp_status tdp_sort_pairs(const uint64_t *keys_in, const uint32_t *va
 {
     if (n < 0 || (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out || !ws)))
         return TDP_ERR_INVALID_ARG;
-    if (keys_in == (const uint64_t *)keys_out || vals_in == (const uint32_t *)vals_out)
+    if (n > 0 && (keys_in == (const uint64_t *)keys_out || vals_in == (const uint32_t *)vals_out))
         return TDP_ERR_INVALID_ARG;
     return radix_sort_pairs<unsigned long long>((const unsigned long long *)keys_in, vals_in, n, nullptr, key_bits,
                                                 (unsigned long long *)keys_out, vals_out, ws, ws_bytes, d_status,

@@ -2,19 +2,21 @@
 // (Sec. 4: logistic relaxation of a predicate, soft_count / soft_groupby).
 //
 // Rows stream through once per call with 16-byte loads (x, v: float4; gid:
-// int4).  Each block owns a contiguous chunk of rows and accumulates its
-// per-group partial sums in shared memory; the partials of all blocks are
-// then added in block order in float64 by a second small kernel, so the only
-// fp32 summation is over the ~n/(blocks*G) rows a block sees per group.  The
-// mask m = sigmoid((x - theta[g]) / tau) is recomputed in the backward pass,
-// never stored; m(1-m) is evaluated as e/(1+e)^2 with e = exp(-|z|), which has
-// no cancellation when m is close to 1.
+// int4).  Each block owns a contiguous chunk of rows and accumulates per-group
+// sums in shared memory: fp32 atomics over sub-chunks of about 16 rows per
+// group, folded after each sub-chunk into fp64 block accumulators; the fp64
+// partials of all blocks are then added in block order by a second small
+// kernel.  (Upstream gradients of either sign make the adjoint's group sums
+// cancel; a long fp32 chain would then lose the 1e-5 relative accuracy.)
+// The mask m = sigmoid((x - theta[g]) / tau) is recomputed in the backward
+// pass, never stored; m(1-m) is evaluated as e/(1+e)^2 with e = exp(-|z|),
+// which has no cancellation when m is close to 1.
 #include "common.cuh"
 
 namespace tdp {
 
 constexpr int SA_THREADS = 512;
-constexpr int SA_MAX_GROUPS = 8192;
+constexpr int SA_MAX_GROUPS = 4096;
 
 struct Sig {
     float m;  // sigmoid(z)
@@ -70,19 +72,28 @@ __global__ void __launch_bounds__(SA_THREADS) soft_reduce_kernel(const float *__
                                                                  const float *__restrict__ g0,
                                                                  const float *__restrict__ g1, float inv_tau,
                                                                  long long n, int G, long long chunk,
-                                                                 float *__restrict__ partial, float *gx, float *gv)
+                                                                 double *__restrict__ partial, float *gx, float *gv)
 {
-    extern __shared__ float sm[];
-    float *s_theta = sm;
-    float *acc0 = sm + G;
-    float *acc1 = sm + 2 * G;  // forward only
-    float *s_g0 = sm + 2 * G;  // backward only
-    float *s_g1 = sm + 3 * G;
+    // Shared memory: fp64 block accumulators first, then fp32 arrays.
+    // fp32 atomics only ever sum one sub-chunk of at most SUB rows (about 16
+    // rows per group); each sub-chunk is then folded into fp64, so the fp32
+    // rounding error does not grow with the rows a block covers.
+    constexpr int K = MODE == MODE_AGG_FWD ? 2 : 1;
+    extern __shared__ double sm64[];
+    double *acc64 = sm64;                    // [K][G]
+    float *s_theta = (float *)(sm64 + K * G);
+    float *acc0 = s_theta + G;
+    float *acc1 = s_theta + 2 * G;           // forward only
+    float *s_g0 = s_theta + 2 * G;           // aggregation backward only
+    float *s_g1 = s_theta + 3 * G;
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
         s_theta[g] = theta[g];
         acc0[g] = 0.f;
-        if (MODE == MODE_AGG_FWD)
+        acc64[g] = 0.0;
+        if (MODE == MODE_AGG_FWD) {
             acc1[g] = 0.f;
+            acc64[G + g] = 0.0;
+        }
         if (MODE == MODE_AGG_BWD) {
             s_g0[g] = g0[g];
             s_g1[g] = g1[g];
@@ -93,34 +104,44 @@ __global__ void __launch_bounds__(SA_THREADS) soft_reduce_kernel(const float *__
     const long long end = min(n, beg + chunk);
     const bool vec = (((uintptr_t)x | (uintptr_t)gid | (uintptr_t)(MODE == MODE_FILTER_BWD ? g0 : v)) % 16) == 0;
     const float *aux = MODE == MODE_FILTER_BWD ? g0 : v; // v, or grad_mask for the filter adjoint
-    long long tail = beg;
-    if (vec) {
-        const long long nvec = (end - beg) / 4;
-        for (long long q = threadIdx.x; q < nvec; q += SA_THREADS) {
-            const long long i = beg + 4 * q;
-            float4 xx = __ldg((const float4 *)(x + i));
-            float4 aa = __ldg((const float4 *)(aux + i));
-            int4 gg = __ldg((const int4 *)(gid + i));
-            soft_row<MODE>(xx.x, aa.x, gg.x, aa.x, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i, G);
-            soft_row<MODE>(xx.y, aa.y, gg.y, aa.y, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 1, G);
-            soft_row<MODE>(xx.z, aa.z, gg.z, aa.z, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 2, G);
-            soft_row<MODE>(xx.w, aa.w, gg.w, aa.w, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 3, G);
+    const long long SUB = max(16ll * G, 4ll * SA_THREADS) / (4 * SA_THREADS) * (4 * SA_THREADS);
+    for (long long sb = beg; sb < end; sb += SUB) {
+        const long long se = min(end, sb + SUB);
+        long long tail = sb;
+        if (vec) {
+            const long long nvec = (se - sb) / 4;
+            for (long long q = threadIdx.x; q < nvec; q += SA_THREADS) {
+                const long long i = sb + 4 * q;
+                float4 xx = __ldg((const float4 *)(x + i));
+                float4 aa = __ldg((const float4 *)(aux + i));
+                int4 gg = __ldg((const int4 *)(gid + i));
+                soft_row<MODE>(xx.x, aa.x, gg.x, aa.x, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i, G);
+                soft_row<MODE>(xx.y, aa.y, gg.y, aa.y, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 1, G);
+                soft_row<MODE>(xx.z, aa.z, gg.z, aa.z, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 2, G);
+                soft_row<MODE>(xx.w, aa.w, gg.w, aa.w, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 3, G);
+            }
+            tail = sb + 4 * nvec;
         }
-        tail = beg + 4 * nvec;
+        for (long long r = tail + threadIdx.x; r < se; r += SA_THREADS)
+            soft_row<MODE>(x[r], aux[r], gid[r], aux[r], s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, r, G);
+        __syncthreads();
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            acc64[g] += (double)acc0[g];
+            acc0[g] = 0.f;
+            if (MODE == MODE_AGG_FWD) {
+                acc64[G + g] += (double)acc1[g];
+                acc1[g] = 0.f;
+            }
+        }
+        __syncthreads();
     }
-    for (long long r = tail + threadIdx.x; r < end; r += SA_THREADS)
-        soft_row<MODE>(x[r], aux[r], gid[r], aux[r], s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, r, G);
-    __syncthreads();
-    float *out = partial + (size_t)blockIdx.x * (MODE == MODE_AGG_FWD ? 2 : 1) * G;
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        out[g] = acc0[g];
-        if (MODE == MODE_AGG_FWD)
-            out[G + g] = acc1[g];
-    }
+    double *out = partial + (size_t)blockIdx.x * K * G;
+    for (int g = threadIdx.x; g < K * G; g += blockDim.x)
+        out[g] = acc64[g];
 }
 
 // out[k][g] = scale * sum_b partial[b][k][g], summed over b in order, float64.
-__global__ void soft_combine_kernel(const float *__restrict__ partial, int nblocks, int G, int K, float scale,
+__global__ void soft_combine_kernel(const double *__restrict__ partial, int nblocks, int G, int K, float scale,
                                     float *__restrict__ out0, float *__restrict__ out1)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -128,7 +149,7 @@ __global__ void soft_combine_kernel(const float *__restrict__ partial, int nbloc
         return;
     double acc = 0.0;
     for (int b = 0; b < nblocks; b++)
-        acc += (double)partial[(size_t)b * K * G + t];
+        acc += partial[(size_t)b * K * G + t];
     acc *= (double)scale;
     if (t < G)
         out0[t] = (float)acc;
@@ -163,10 +184,11 @@ struct SoftGrid {
     size_t smem;
 };
 
-static SoftGrid soft_grid(long long n, int G, int nbuf)
+// n64 fp64 arrays and n32 fp32 arrays of G entries in shared memory
+static SoftGrid soft_grid(long long n, int G, int n64, int n32)
 {
     SoftGrid sg;
-    sg.smem = (size_t)nbuf * G * sizeof(float);
+    sg.smem = (size_t)G * (n64 * sizeof(double) + n32 * sizeof(float));
     int per_sm = sg.smem <= 48 * 1024 ? 2 : 1;
     long long want = (n + 4ll * SA_THREADS * 8 - 1) / (4ll * SA_THREADS * 8);
     long long maxb = (long long)num_sms() * per_sm;
@@ -191,8 +213,8 @@ using namespace tdp;
 extern "C" size_t tdp_soft_workspace(int64_t n, int32_t n_groups)
 {
     (void)n;
-    // per-block partials: at most 2 blocks per SM, 2 arrays of n_groups floats
-    return align_up((size_t)2 * num_sms() * 2 * (size_t)std::max(1, n_groups) * sizeof(float), 256);
+    // per-block fp64 partials: at most 2 blocks per SM, 2 arrays of n_groups
+    return align_up((size_t)2 * num_sms() * 2 * (size_t)std::max(1, n_groups) * sizeof(double), 256);
 }
 
 static tdp_status soft_check(const float *x, const int32_t *gid, const float *theta, float tau, int64_t n, int32_t G)
@@ -229,10 +251,10 @@ extern "C" tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 3);
+    SoftGrid sg = soft_grid(n, G, 2, 3);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_FWD>, sg.smem)) != TDP_OK)
         return st;
-    float *partial = (float *)ws;
+    double *partial = (double *)ws;
     soft_reduce_kernel<MODE_AGG_FWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
         x, v, gid, theta, nullptr, nullptr, 1.0f / tau, n, G, sg.chunk, partial, nullptr, nullptr);
     soft_combine_kernel<<<(2 * G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
@@ -252,10 +274,10 @@ extern "C" tdp_status tdp_soft_agg_bwd(const float *x, const float *v, const int
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 4);
+    SoftGrid sg = soft_grid(n, G, 1, 4);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_BWD>, sg.smem)) != TDP_OK)
         return st;
-    float *partial = (float *)ws;
+    double *partial = (double *)ws;
     soft_reduce_kernel<MODE_AGG_BWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
         x, v, gid, theta, gsum, gcnt, 1.0f / tau, n, G, sg.chunk, partial, grad_x, grad_v);
     soft_combine_kernel<<<(G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau, grad_theta,
@@ -275,10 +297,10 @@ extern "C" tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, co
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 2);
+    SoftGrid sg = soft_grid(n, G, 1, 2);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_FILTER_BWD>, sg.smem)) != TDP_OK)
         return st;
-    float *partial = (float *)ws;
+    double *partial = (double *)ws;
     soft_reduce_kernel<MODE_FILTER_BWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
         x, nullptr, gid, theta, grad_mask, nullptr, 1.0f / tau, n, G, sg.chunk, partial, grad_x, nullptr);
     soft_combine_kernel<<<(G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau, grad_theta,

@@ -5,7 +5,7 @@
 
 namespace tdp {
 
-static std::atomic<uint32_t> g_spin_limit{1u << 22};
+static std::atomic<uint32_t> g_spin_limit{1u << 20};
 
 uint32_t spin_limit() { return g_spin_limit.load(std::memory_order_relaxed); }
 

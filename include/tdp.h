@@ -368,6 +368,32 @@ tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int32_t *gid, 
                             size_t ws_bytes, tdp_stream_t stream);
 
 /*
+ * tdp_soft_agg_fwd without a workspace, for callers that cannot allocate
+ * device memory: code where a cudaMalloc is not allowed or would synchronise
+ * the device at a bad moment, or an embedding host that only passes in
+ * buffers it registered up front.  The paper has no counterpart; this is a
+ * deployment variant of the call above, with the same arguments minus ws and
+ * the same results (same kernels, same summation order for a given grid).
+ *
+ * Scratch: the per-block float64 partial sums live in one fixed 4 MiB array
+ * in the library's device image (256 blocks x 2 sums x 1024 groups), which
+ * every GPU that loads the library holds until the process exits.
+ *   - n_groups must be <= 1024; larger values return
+ *     TDP_ERR_WORKSPACE_TOO_SMALL (use tdp_soft_agg_fwd then).
+ *   - The first call on a device looks up the array's device address with
+ *     that device current (one cudaGetSymbolAddress, no allocation); make
+ *     that first call before any stream capture.
+ *   - All calls share the one array: two calls whose kernels overlap on the
+ *     GPU (different streams, or different threads) race and give wrong
+ *     sums.  Serialise them.  Each call overwrites the parts it reads, so
+ *     nothing has to be cleared between calls.
+ * No device memory is allocated or freed by this call.
+ */
+tdp_status tdp_soft_agg_fwd_noalloc(const float *x, const float *v, const int32_t *gid, const float *theta,
+                                    float tau, int64_t n, int32_t n_groups, float *sum, float *cnt,
+                                    tdp_stream_t stream);
+
+/*
  * Adjoint of tdp_soft_agg_fwd for upstream gradients gsum, gcnt (fp32[G]):
  *   grad_theta[g] = -(1/tau) sum_{gid[i]=g} (gsum[g] v_i + gcnt[g]) m_i (1-m_i)
  *   grad_v[i]     = gsum[gid[i]] m_i                                (optional)

@@ -11,6 +11,8 @@
 // The mask m = sigmoid((x - theta[g]) / tau) is recomputed in the backward
 // pass, never stored; m(1-m) is evaluated as e/(1+e)^2 with e = exp(-|z|),
 // which has no cancellation when m is close to 1.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace tdp {
@@ -305,5 +307,75 @@ extern "C" tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, co
         x, nullptr, gid, theta, grad_mask, nullptr, 1.0f / tau, n, G, sg.chunk, partial, grad_x, nullptr);
     soft_combine_kernel<<<(G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau, grad_theta,
                                                         nullptr);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// tdp_soft_agg_fwd_noalloc: the soft aggregation forward for callers that
+// cannot allocate device memory (for example code running where a
+// cudaMalloc would synchronise the device or is not permitted, or a host
+// that only hands out pre-registered buffers).  Its scratch -- the fp64
+// per-block partial sums -- lives in one fixed array in this library's device
+// image instead of a caller workspace.
+// ---------------------------------------------------------------------------
+
+namespace tdp {
+
+constexpr int NOALLOC_MAX_GROUPS = 1024;
+constexpr int NOALLOC_MAX_BLOCKS = 256;
+
+// 256 blocks x 2 sums x 1024 groups x 8 bytes = 4 MiB, resident on every GPU
+// that loads this library until the process exits.
+static __device__ __align__(256) double g_noalloc_partial[NOALLOC_MAX_BLOCKS * 2 * NOALLOC_MAX_GROUPS];
+
+// Device address of g_noalloc_partial, looked up once per device (in host
+// code the symbol is only a stand-in, never a device address).
+static std::atomic<double *> g_noalloc_ptr[64];
+
+static tdp_status noalloc_scratch(double **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return TDP_ERR_CUDA;
+    double *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *addr = nullptr;
+        if (cudaGetSymbolAddress(&addr, g_noalloc_partial) != cudaSuccess || !addr)
+            return TDP_ERR_CUDA;
+        p = (double *)addr;
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return TDP_OK;
+}
+
+} // namespace tdp
+
+extern "C" tdp_status tdp_soft_agg_fwd_noalloc(const float *x, const float *v, const int32_t *gid,
+                                               const float *theta, float tau, int64_t n, int32_t G, float *sum,
+                                               float *cnt, tdp_stream_t stream)
+{
+    tdp_status st = soft_check(x, gid, theta, tau, n, G);
+    if (st != TDP_OK)
+        return st;
+    if (!sum || !cnt || (n > 0 && !v))
+        return TDP_ERR_INVALID_ARG;
+    if (G > NOALLOC_MAX_GROUPS) // beyond the fixed scratch: the caller must use tdp_soft_agg_fwd
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    double *partial = nullptr;
+    if ((st = noalloc_scratch(&partial)) != TDP_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    SoftGrid sg = soft_grid(n, G, 2, 3);
+    if (sg.blocks > NOALLOC_MAX_BLOCKS) {
+        sg.blocks = NOALLOC_MAX_BLOCKS;
+        sg.chunk = (n + sg.blocks - 1) / sg.blocks;
+        sg.chunk = (sg.chunk + 3) / 4 * 4;
+    }
+    // every block used overwrites its own K x G partials before the combine
+    // reads them, so nothing in the shared scratch has to start at zero
+    soft_reduce_kernel<MODE_AGG_FWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
+        x, v, gid, theta, nullptr, nullptr, 1.0f / tau, n, G, sg.chunk, partial, nullptr, nullptr);
+    soft_combine_kernel<<<(2 * G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
     return launch_status();
 }

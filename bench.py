@@ -414,7 +414,7 @@ def glyph_plan(dev, stream, args):
     targets = torch.from_numpy(O.targets_from_labels(tr_lab).astype(np.float32)).to(dev)
     g_tr = torch.from_numpy(tr_img).to(dev)
     g_te = torch.from_numpy(te_img).to(dev)
-    q = cnn.GlyphQuery(gen.cnn_params(gen.BASE_SEED + 5), dev, lr=1e-3)
+    q = cnn.GlyphQuery(gen.cnn_params(gen.BASE_SEED + 5), dev, lr=1e-3, warmup=400)
     B = 256
     nb = 4096 // B
 
@@ -437,8 +437,6 @@ def glyph_plan(dev, stream, args):
     # finish a fixed training budget, then evaluate the exact query
     budget = 1600
     for i in range(3 + n_timed, budget):
-        if i == 1200:
-            q.lr = 3e-4
         step(i)
     torch.cuda.synchronize()
     gq = g_te[:B]

@@ -27,7 +27,12 @@ NPRED = 14
 
 
 class GlyphQuery:
-    def __init__(self, params: dict, device="cuda", lr: float = 0.01, betas=(0.9, 0.999), eps: float = 1e-8):
+    def __init__(self, params: dict, device="cuda", lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8,
+                 warmup: int = 400):
+        """Adam with a linear learning-rate warmup over `warmup` steps.  The
+        paper's loop uses Adam at lr 0.01; on this network that diverges, and
+        lr 1e-3 without warmup lets the softmax of class 0 (value 0, invisible
+        to the row sums) saturate and collapse into class 1."""
         self.dev = torch.device(device)
         self.p = {k: torch.as_tensor(np.asarray(params[k], np.float32)).to(self.dev).contiguous() for k in PARAMS}
         self.m = {k: torch.zeros_like(v) for k, v in self.p.items()}
@@ -36,7 +41,7 @@ class GlyphQuery:
         self.bf = {k: torch.empty(self.p[k].shape, dtype=torch.bfloat16, device=self.dev) for k in BF16_COPIES}
         for k in BF16_COPIES:
             L.call("tdp_f32_to_bf16", _ptr(self.p[k]), self.p[k].numel(), _ptr(self.bf[k]), _stream())
-        self.lr, self.betas, self.eps = lr, betas, eps
+        self.lr, self.betas, self.eps, self.warmup = lr, betas, eps, warmup
         self.t = 0
         self._buf = {}
 
@@ -115,9 +120,10 @@ class GlyphQuery:
         arr = lambda ts: (C.c_void_p * 8)(*[t.data_ptr() for t in ts])  # noqa: E731
         copies = (C.c_void_p * 8)(*[self.bf[x].data_ptr() if x in self.bf else 0 for x in k])
         sizes = (C.c_int64 * 8)(*[self.p[x].numel() for x in k])
+        lr = self.lr * min(1.0, self.t / self.warmup) if self.warmup else self.lr
         L.call("tdp_adam_step", arr([self.p[x] for x in k]), arr([self.g[x] for x in k]),
                arr([self.m[x] for x in k]), arr([self.v[x] for x in k]), copies, sizes, len(k), self.t,
-               float(self.lr), float(self.betas[0]), float(self.betas[1]), float(self.eps), _stream())
+               float(lr), float(self.betas[0]), float(self.betas[1]), float(self.eps), _stream())
 
     def train_step(self, grids: torch.Tensor, targets: torch.Tensor) -> torch.Tensor:
         """One step of the paper's training loop: query forward, MSE loss,

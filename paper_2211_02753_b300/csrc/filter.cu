@@ -82,10 +82,9 @@ __global__ void __launch_bounds__(FT_THREADS) filter_kernel(PredSet ps, GatherSe
                                                             unsigned long long *tile_status, unsigned *ticket,
                                                             int32_t *d_status, uint32_t limit, long long num_tiles)
 {
+    // The block takes a ticket; warp w then owns sub-tile ticket*8 + w and does
+    // its own decoupled look-back (no block-wide barrier after the start).
     __shared__ long long s_tile;
-    __shared__ unsigned s_warp_tot[FT_THREADS / 32];
-    __shared__ unsigned s_warp_excl[FT_THREADS / 32];
-    __shared__ unsigned long long s_excl;
 
     if (threadIdx.x == 0)
         s_tile = atomicAdd(ticket, 1u);
@@ -93,6 +92,7 @@ __global__ void __launch_bounds__(FT_THREADS) filter_kernel(PredSet ps, GatherSe
     const long long tile = s_tile;
     const long long n = d_n ? min(*d_n, n_host) : n_host;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long wtile = tile * (FT_THREADS / 32) + warp;
     const long long r0 = tile * FT_TILE + (long long)warp * FT_WARP_ROWS + 4 * lane;
 
     unsigned m[FT_STEPS];
@@ -132,35 +132,15 @@ __global__ void __launch_bounds__(FT_THREADS) filter_kernel(PredSet ps, GatherSe
         lane_pref[j] = pre;
         warp_tot += c;
     }
-    if (lane == 0)
-        s_warp_tot[warp] = warp_tot;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned t = lane < FT_THREADS / 32 ? s_warp_tot[lane] : 0;
-        unsigned incl = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o)
-                incl += u;
-        }
-        if (lane < FT_THREADS / 32)
-            s_warp_excl[lane] = incl - t;
-        unsigned long long agg = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned long long excl = lookback_exclusive(tile_status, tile, agg, limit, d_status);
-        if (lane == 0) {
-            s_excl = excl;
-            if (tile == num_tiles - 1) {
-                long long total = (long long)(excl + agg);
-                *d_count = total;
-                if (total > cap)
-                    set_status(d_status, TDP_ERR_CAPACITY);
-            }
-        }
+    const unsigned long long excl = lookback_exclusive(tile_status, wtile, warp_tot, limit, d_status);
+    if (lane == 0 && wtile == num_tiles - 1) { // num_tiles counts warp sub-tiles
+        long long total = (long long)(excl + warp_tot);
+        *d_count = total;
+        if (total > cap)
+            set_status(d_status, TDP_ERR_CAPACITY);
     }
-    __syncthreads();
 
-    long long pos = (long long)s_excl + s_warp_excl[warp];
+    long long pos = (long long)excl;
 #pragma unroll
     for (int j = 0; j < FT_STEPS; j++) {
         const long long r = r0 + j * 128;
@@ -220,11 +200,12 @@ tdp_status filter_rows(const PredSet &ps, long long n, const long long *d_n, int
     GatherSet none;
     none.n = 0;
     long long tiles = (n + FT_TILE - 1) / FT_TILE;
+    long long wtiles = tiles * (FT_THREADS / 32); // one look-back word per warp sub-tile
     unsigned *ticket = (unsigned *)ws;
     unsigned long long *status = (unsigned long long *)((char *)ws + 16);
-    cudaMemsetAsync(ws, 0, 16 + (size_t)tiles * 8, s);
+    cudaMemsetAsync(ws, 0, 16 + (size_t)wtiles * 8, s);
     filter_kernel<<<(unsigned)tiles, FT_THREADS, 0, s>>>(ps, gs ? *gs : none, n, d_n, out_rowid, cap, d_count, status,
-                                                         ticket, d_status, spin_limit(), tiles);
+                                                         ticket, d_status, spin_limit(), wtiles);
     return launch_status();
 }
 
@@ -234,8 +215,8 @@ using namespace tdp;
 
 extern "C" size_t tdp_filter_workspace(int64_t n)
 {
-    long long tiles = (n + FT_TILE - 1) / FT_TILE;
-    return align_up(16 + (size_t)tiles * 8, 256);
+    long long wtiles = (n + FT_TILE - 1) / FT_TILE * (FT_THREADS / 32);
+    return align_up(16 + (size_t)wtiles * 8, 256);
 }
 
 extern "C" tdp_status tdp_filter(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds,

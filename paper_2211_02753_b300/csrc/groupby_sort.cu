@@ -7,7 +7,10 @@
 //     as key-lo, an unbounded one its full width with the sign bit flipped,
 //     so unsigned order is lexicographic signed key order.  32-bit radix keys
 //     when the fields fit, else 64-bit.
-//  3. Onesweep radix sort of (packed key, row id) over the used bits only.
+//  3. Onesweep radix sort of (packed key, payload) over the used bits only.
+//     The payload is the row id, or -- when the query has a single value
+//     aggregate besides COUNT -- that row's value itself (e.g. price*(100-disc)),
+//     which spares the reduce a random gather per row.
 //  4. Reduce-by-key over the sorted pairs in one pass: each thread folds 8
 //     consecutive pairs, the block scans (head count, running aggregates)
 //     with the segmented operator (a, b) -> (a.h + b.h, b.h ? b.s : a.s (+) b.s),
@@ -82,9 +85,12 @@ __device__ __forceinline__ unsigned long long field_mask(int bits)
     return bits >= 64 ? ~0ull : ((1ull << bits) - 1);
 }
 
-template <typename K>
-__global__ void pack_keys_kernel(KeySet ks, KeyPack kp, long long n, const int32_t *sel, const long long *d_nsel,
-                                 K *keys, uint32_t *rows, int32_t *d_status)
+// Writes the packed key of every input row and its payload: the row id, or
+// (CARRY) the value of accumulator slot 1 when that is the only value slot,
+// so that the reduce streams it instead of gathering it by row id.
+template <typename K, typename V, bool CARRY>
+__global__ void pack_keys_kernel(KeySet ks, KeyPack kp, AggSet as, long long n, const int32_t *sel,
+                                 const long long *d_nsel, K *keys, V *rows, int32_t *d_status)
 {
     const long long m = d_nsel ? min(*d_nsel, n) : n;
     bool bad = false;
@@ -110,7 +116,7 @@ __global__ void pack_keys_kernel(KeySet ks, KeyPack kp, long long n, const int32
             packed |= f << kp.shift[k];
         }
         keys[i] = (K)packed;
-        rows[i] = (uint32_t)row;
+        rows[i] = CARRY ? (V)slot_value(as, 1, row) : (V)row;
     }
     if (bad)
         set_status(d_status, TDP_ERR_OVERFLOW);
@@ -162,9 +168,9 @@ __device__ __forceinline__ void store_key(void *out, int dt, long long pos, long
     }
 }
 
-template <typename K, int SL>
+template <typename K, typename V, int SL, bool CARRY>
 __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restrict__ keys,
-                                                                const uint32_t *__restrict__ rows, long long n_max,
+                                                                const V *__restrict__ rows, long long n_max,
                                                                 const long long *d_n, KeySet ks, KeyPack kp,
                                                                 AggSet as, DenseOut out, long long cap,
                                                                 long long *d_ngroups, SegRec *recs, unsigned *ticket,
@@ -229,11 +235,16 @@ __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restr
             for (int j = 0; j < SL; j++)
                 mine.s[j] = s_init[j];
         }
-        const long long row = rows[i];
+        if (CARRY) { // count + the carried value of slot 1
+            mine.s[0] += 1;
+            mine.s[1] = comb(ops[1], mine.s[1], (long long)rows[i]);
+        } else {
+            const long long row = (long long)rows[i];
 #pragma unroll
-        for (int j = 0; j < SL; j++)
-            if (j < NS)
-                mine.s[j] = comb(ops[j], mine.s[j], slot_value(as, j, row));
+            for (int j = 0; j < SL; j++)
+                if (j < NS)
+                    mine.s[j] = comb(ops[j], mine.s[j], slot_value(as, j, row));
+        }
     }
     // warp inclusive scan
     SV inc = mine;
@@ -391,17 +402,22 @@ __global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restr
         long long i = i0 + it;
         if (i >= n)
             break;
-        const long long row = rows[i];
         if (headmask >> it & 1) {
             g++;
 #pragma unroll
             for (int j = 0; j < SL; j++)
                 run.s[j] = s_init[j];
         }
+        if (CARRY) {
+            run.s[0] += 1;
+            run.s[1] = comb(ops[1], run.s[1], (long long)rows[i]);
+        } else {
+            const long long row = (long long)rows[i];
 #pragma unroll
-        for (int j = 0; j < SL; j++)
-            if (j < NS)
-                run.s[j] = comb(ops[j], run.s[j], slot_value(as, j, row));
+            for (int j = 0; j < SL; j++)
+                if (j < NS)
+                    run.s[j] = comb(ops[j], run.s[j], slot_value(as, j, row));
+        }
         bool last = (i == n - 1);
         K key = keys[i];
         if (!last)
@@ -463,16 +479,17 @@ size_t sort_groupby_ws(long long n, int nkeys, int naggs, int key_bits)
     (void)nkeys;
     (void)naggs;
     int kb = key_bits <= 32 ? 4 : 8;
+    const int vb = 8; // payload: uint32 row id, or the carried int64 value
     size_t b = align_up((size_t)n * 4, 256);                         // filtered row ids
     b += 256;                                                         // filtered count
-    b += 2 * align_up((size_t)n * kb, 256) + 2 * align_up((size_t)n * 4, 256); // packed keys/rows, sorted
-    b += radix_ws_bytes(n, key_bits, kb);
+    b += 2 * align_up((size_t)n * kb, 256) + 2 * align_up((size_t)n * vb, 256); // packed pairs, sorted pairs
+    b += radix_ws_bytes(n, key_bits, kb, vb);
     b += seg_ws(n);
     b += tdp_filter_workspace(n);
     return b;
 }
 
-template <typename K>
+template <typename K, typename V, bool CARRY>
 static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key_bits, const AggSet &as, long long n,
                                     const int32_t *sel, const int64_t *d_nsel, const DenseOut &out,
                                     long long capacity, int64_t *d_ngroups, void *ws, size_t ws_bytes,
@@ -487,12 +504,12 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
     p += align_up((size_t)n * sizeof(K), 256);
     K *sk = (K *)p;
     p += align_up((size_t)n * sizeof(K), 256);
-    uint32_t *pr = (uint32_t *)p;
-    p += align_up((size_t)n * 4, 256);
-    uint32_t *sr = (uint32_t *)p;
-    p += align_up((size_t)n * 4, 256);
+    V *pr = (V *)p;
+    p += align_up((size_t)n * 8, 256);
+    V *sr = (V *)p;
+    p += align_up((size_t)n * 8, 256);
     void *rws = p;
-    size_t rws_bytes = radix_ws_bytes(n, key_bits, sizeof(K));
+    size_t rws_bytes = radix_ws_bytes(n, key_bits, sizeof(K), 8);
     p += rws_bytes;
     char *segws = p;
     p += seg_ws(n);
@@ -512,8 +529,8 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
     KeyPack kp = make_keypack(ks);
     int grid = (int)std::max(1ll, std::min<long long>((n + 255) / 256, (long long)num_sms() * 8));
     if (n > 0)
-        pack_keys_kernel<K><<<grid, 256, 0, s>>>(ks, kp, n, rowsel, rowcount, pk, pr, d_status);
-    tdp_status st = radix_sort_pairs<K>(pk, pr, n, rowcount, key_bits, sk, sr, rws, rws_bytes, d_status, s);
+        pack_keys_kernel<K, V, CARRY><<<grid, 256, 0, s>>>(ks, kp, as, n, rowsel, rowcount, pk, pr, d_status);
+    tdp_status st = radix_sort_pairs<K, V>(pk, pr, n, rowcount, key_bits, sk, sr, rws, rws_bytes, d_status, s);
     if (st != TDP_OK)
         return st;
     cudaMemsetAsync(d_ngroups, 0, 8, s);
@@ -522,17 +539,19 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
     cudaMemsetAsync(segws, 0, seg_ws(n), s);
     long long tiles = (n + SR_TILE - 1) / SR_TILE;
     const unsigned sgrid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 3);
-    // accumulator slots carried through the scan: the smallest of 2, 4, 9 that fits
     auto launch = [&](auto kern) {
         kern<<<sgrid, SR_THREADS, 0, s>>>(sk, sr, n, rowcount, ks, kp, as, out, capacity, (long long *)d_ngroups,
                                           (SegRec *)(segws + 256), (unsigned *)segws, d_status, spin_limit());
     };
-    if (as.nslots <= 2)
-        launch(seg_reduce_kernel<K, 2>);
+    // accumulator slots carried through the scan: the smallest of 2, 4, 9 that fits
+    if (CARRY)
+        launch(seg_reduce_kernel<K, V, 2, true>);
+    else if (as.nslots <= 2)
+        launch(seg_reduce_kernel<K, V, 2, false>);
     else if (as.nslots <= 4)
-        launch(seg_reduce_kernel<K, 4>);
+        launch(seg_reduce_kernel<K, V, 4, false>);
     else
-        launch(seg_reduce_kernel<K, SR_MAXS>);
+        launch(seg_reduce_kernel<K, V, SR_MAXS, false>);
     return launch_status();
 }
 
@@ -540,11 +559,21 @@ tdp_status sort_groupby_run(const PredSet &ps, const KeySet &ks, int key_bits, c
                             const int32_t *sel, const int64_t *d_nsel, const DenseOut &out, long long capacity,
                             int64_t *d_ngroups, void *ws, size_t ws_bytes, int32_t *d_status, cudaStream_t s)
 {
+    // One value slot besides COUNT: carry the value through the sort (8-byte
+    // payload) so that the reduce streams it; otherwise carry row ids.
+    const bool carry = as.nslots == 2;
     if (key_bits <= 32)
-        return sort_groupby_impl<uint32_t>(ps, ks, key_bits, as, n, sel, d_nsel, out, capacity, d_ngroups, ws,
-                                           ws_bytes, d_status, s);
-    return sort_groupby_impl<unsigned long long>(ps, ks, key_bits, as, n, sel, d_nsel, out, capacity, d_ngroups, ws,
-                                                 ws_bytes, d_status, s);
+        return carry ? sort_groupby_impl<uint32_t, unsigned long long, true>(ps, ks, key_bits, as, n, sel, d_nsel,
+                                                                             out, capacity, d_ngroups, ws, ws_bytes,
+                                                                             d_status, s)
+                     : sort_groupby_impl<uint32_t, uint32_t, false>(ps, ks, key_bits, as, n, sel, d_nsel, out,
+                                                                    capacity, d_ngroups, ws, ws_bytes, d_status, s);
+    return carry ? sort_groupby_impl<unsigned long long, unsigned long long, true>(ps, ks, key_bits, as, n, sel,
+                                                                                   d_nsel, out, capacity, d_ngroups,
+                                                                                   ws, ws_bytes, d_status, s)
+                 : sort_groupby_impl<unsigned long long, uint32_t, false>(ps, ks, key_bits, as, n, sel, d_nsel, out,
+                                                                          capacity, d_ngroups, ws, ws_bytes, d_status,
+                                                                          s);
 }
 
 } // namespace tdp

@@ -50,27 +50,52 @@ __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, c
     if (d_n)
         n = min(*d_n, n);
     const unsigned long long mask = (1ull << lg) - 1;
+    const unsigned long long steps = mask + 1 < MAX_PROBE ? mask + 1 : MAX_PROBE;
     int err = 0;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        if (!eval_preds1(ps, r))
+    // 4 consecutive rows per thread: predicate, key and payload columns are
+    // read with vector loads before any insert starts
+    const long long r0 = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (r0 >= n)
+        return;
+    unsigned m = eval_preds4(ps, r0, n);
+    if (!m)
+        return;
+    int k[4];
+    unsigned p[4];
+    const bool full = r0 + 3 < n && ((uintptr_t)key % 16) == 0 && (!payload || ((uintptr_t)payload % 16) == 0);
+    if (full) {
+        int4 kk = __ldg((const int4 *)(key + r0));
+        k[0] = kk.x, k[1] = kk.y, k[2] = kk.z, k[3] = kk.w;
+        if (payload) {
+            int4 pp = __ldg((const int4 *)(payload + r0));
+            p[0] = pp.x, p[1] = pp.y, p[2] = pp.z, p[3] = pp.w;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            k[e] = (m >> e & 1) ? key[r0 + e] : 0;
+            p[e] = (m >> e & 1) && payload ? (unsigned)payload[r0 + e] : 0u;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        if (!(m >> e & 1))
             continue;
-        int k = key[r];
-        unsigned p = payload ? (unsigned)payload[r] : (unsigned)r;
-        unsigned long long v = ((unsigned long long)(unsigned)k << 32) | p;
+        unsigned pe = payload ? p[e] : (unsigned)(r0 + e);
+        unsigned long long v = ((unsigned long long)(unsigned)k[e] << 32) | pe;
         if (v == EMPTY_SLOT) {
             err |= TDP_ERR_OVERFLOW;
             continue;
         }
-        unsigned long long h = hash_slot(k, lg);
+        unsigned long long h = hash_slot(k[e], lg);
         bool done = false;
-        const unsigned long long steps = mask + 1 < MAX_PROBE ? mask + 1 : MAX_PROBE;
         for (unsigned long long probe = 0; probe < steps; probe++) {
             unsigned long long prev = atomicCAS(&table[h], EMPTY_SLOT, v);
             if (prev == EMPTY_SLOT) {
                 done = true;
                 break;
             }
-            if ((unsigned)(prev >> 32) == (unsigned)k) {
+            if ((unsigned)(prev >> 32) == (unsigned)k[e]) {
                 err |= TDP_ERR_DUP_BUILD_KEY;
                 done = true;
                 break;
@@ -472,7 +497,8 @@ extern "C" tdp_status tdp_join_build(const tdp_col *cols, int32_t ncols, const t
     fill_empty_kernel<<<(unsigned)std::min<long long>((nslots + 255) / 256, (long long)num_sms() * 8), 256, 0, s>>>(
         (unsigned long long *)table, nslots);
     if (n > 0) {
-        unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
+        // one thread per 4 rows (the kernel is not grid-strided)
+        unsigned grid = (unsigned)((n + 1023) / 1024);
         join_build_kernel<<<grid, 256, 0, s>>>(ps, (const int32_t *)cols[key_col].data,
                                                payload_col >= 0 ? (const int32_t *)cols[payload_col].data : nullptr,
                                                n, (const long long *)d_n, (unsigned long long *)table,

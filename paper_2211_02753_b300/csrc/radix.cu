@@ -102,10 +102,10 @@ __device__ __forceinline__ unsigned rs_wait(const unsigned *w, uint32_t limit, i
     return s;
 }
 
-template <typename K>
+template <typename K, typename V>
 __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__restrict__ kin,
-                                                                   const uint32_t *__restrict__ vin,
-                                                                   K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                                   const V *__restrict__ vin,
+                                                                   K *__restrict__ kout, V *__restrict__ vout,
                                                                    long long n_max, const long long *d_n, int shift,
                                                                    const unsigned *__restrict__ offsets,
                                                                    unsigned *status, unsigned *ticket,
@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__re
 {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     K *s_keys = (K *)rs_smem;
-    uint32_t *s_vals = (uint32_t *)(s_keys + RS_TILE);
-    unsigned *s_whist = s_vals + RS_TILE; // [RS_WARPS][257]
+    V *s_vals = (V *)(s_keys + RS_TILE);
+    unsigned *s_whist = (unsigned *)(s_vals + RS_TILE); // [RS_WARPS][257]
     __shared__ unsigned s_dstart[256];
     __shared__ unsigned s_glob[256];
     __shared__ unsigned s_tmp[8];
@@ -138,14 +138,14 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__re
     unsigned *wh = s_whist + warp * 257;
 
     K k[RS_ITEMS];
-    uint32_t v[RS_ITEMS];
+    V v[RS_ITEMS];
     unsigned short dig[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; i++) {
         long long idx = wb + i * 32 + lane;
         bool valid = idx < n;
         k[i] = valid ? kin[idx] : (K)0;
-        v[i] = valid ? vin[idx] : 0u;
+        v[i] = valid ? vin[idx] : (V)0;
         dig[i] = valid ? (unsigned short)((k[i] >> shift) & 0xff) : (unsigned short)256;
     }
 #pragma unroll
@@ -211,25 +211,25 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__re
     }
 }
 
-size_t radix_ws_bytes(long long n, int key_bits, int key_bytes)
+size_t radix_ws_bytes(long long n, int key_bits, int key_bytes, int val_bytes)
 {
     int P = radix_passes(key_bits);
     long long tiles = (n + RS_TILE - 1) / RS_TILE;
     size_t b = align_up((size_t)P * 256 * 4, 256) + 256 + align_up((size_t)P * tiles * 256 * 4, 256);
-    b += align_up((size_t)n * key_bytes, 256) + align_up((size_t)n * 4, 256);
+    b += align_up((size_t)n * key_bytes, 256) + align_up((size_t)n * val_bytes, 256);
     return b;
 }
 
-template <typename K>
-tdp_status radix_sort_pairs(const K *keys_in, const uint32_t *vals_in, long long n_max, const long long *d_n,
-                            int key_bits, K *keys_out, uint32_t *vals_out, void *ws, size_t ws_bytes,
+template <typename K, typename V>
+tdp_status radix_sort_pairs(const K *keys_in, const V *vals_in, long long n_max, const long long *d_n,
+                            int key_bits, K *keys_out, V *vals_out, void *ws, size_t ws_bytes,
                             int32_t *d_status, cudaStream_t s)
 {
     if (key_bits < 1 || key_bits > (int)(8 * sizeof(K)) || n_max < 0 || n_max >= (1ll << 30))
         return TDP_ERR_INVALID_ARG;
     if (n_max == 0)
         return TDP_OK;
-    if (ws_bytes < radix_ws_bytes(n_max, key_bits, sizeof(K)))
+    if (ws_bytes < radix_ws_bytes(n_max, key_bits, sizeof(K), sizeof(V)))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     const int P = radix_passes(key_bits);
     const long long tiles = (n_max + RS_TILE - 1) / RS_TILE;
@@ -242,24 +242,24 @@ tdp_status radix_sort_pairs(const K *keys_in, const uint32_t *vals_in, long long
     p += align_up((size_t)P * tiles * 256 * 4, 256);
     K *tmp_k = (K *)p;
     p += align_up((size_t)n_max * sizeof(K), 256);
-    uint32_t *tmp_v = (uint32_t *)p;
+    V *tmp_v = (V *)p;
     cudaMemsetAsync(ws, 0, (size_t)((char *)tmp_k - (char *)ws), s);
     int hist_blocks = (int)std::min<long long>((n_max + RS_THREADS - 1) / RS_THREADS, (long long)num_sms() * 4);
     radix_hist_kernel<K><<<hist_blocks, RS_THREADS, 0, s>>>(keys_in, n_max, d_n, P, hist);
     radix_hist_scan_kernel<<<P, 256, 0, s>>>(hist);
-    const size_t smem = (size_t)RS_TILE * (sizeof(K) + 4) + RS_WARPS * 257 * 4;
-    if (cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    const size_t smem = (size_t)RS_TILE * (sizeof(K) + sizeof(V)) + RS_WARPS * 257 * 4;
+    if (cudaFuncSetAttribute(radix_scatter_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return TDP_ERR_CUDA;
     const K *src_k = keys_in;
-    const uint32_t *src_v = vals_in;
+    const V *src_v = vals_in;
     // persistent grid: as many blocks as fit at once (2 per SM at 128 registers)
     const unsigned sgrid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 2);
     for (int pass = 0; pass < P; pass++) {
         bool to_out = ((P - 1 - pass) % 2) == 0;
         K *dk = to_out ? keys_out : tmp_k;
-        uint32_t *dv = to_out ? vals_out : tmp_v;
-        radix_scatter_kernel<K><<<sgrid, RS_THREADS, smem, s>>>(
+        V *dv = to_out ? vals_out : tmp_v;
+        radix_scatter_kernel<K, V><<<sgrid, RS_THREADS, smem, s>>>(
             src_k, src_v, dk, dv, n_max, d_n, 8 * pass, hist + pass * 256, status + (size_t)pass * tiles * 256,
             tickets + pass, d_status, spin_limit());
         src_k = dk;
@@ -268,11 +268,14 @@ tdp_status radix_sort_pairs(const K *keys_in, const uint32_t *vals_in, long long
     return launch_status();
 }
 
-template tdp_status radix_sort_pairs<uint32_t>(const uint32_t *, const uint32_t *, long long, const long long *, int,
-                                                 uint32_t *, uint32_t *, void *, size_t, int32_t *, cudaStream_t);
-template tdp_status radix_sort_pairs<unsigned long long>(const unsigned long long *, const uint32_t *, long long,
-                                                           const long long *, int, unsigned long long *, uint32_t *,
-                                                           void *, size_t, int32_t *, cudaStream_t);
+#define TDP_RADIX_INST(K, V)                                                                                  \
+    template tdp_status radix_sort_pairs<K, V>(const K *, const V *, long long, const long long *, int, K *, V *,   \
+                                               void *, size_t, int32_t *, cudaStream_t);
+TDP_RADIX_INST(uint32_t, uint32_t)
+TDP_RADIX_INST(unsigned long long, uint32_t)
+TDP_RADIX_INST(uint32_t, unsigned long long)
+TDP_RADIX_INST(unsigned long long, unsigned long long)
+#undef TDP_RADIX_INST
 
 } // namespace tdp
 
@@ -282,7 +285,7 @@ extern "C" size_t tdp_sort_pairs_workspace(int64_t n, int32_t key_bits)
 {
     if (key_bits < 1 || key_bits > 64 || n < 0)
         return 0;
-    return radix_ws_bytes(n, key_bits, 8);
+    return radix_ws_bytes(n, key_bits, 8, 4);
 }
 
 extern "C" tdp_status tdp_sort_pairs(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t key_bits,
@@ -293,7 +296,8 @@ extern "C" tdp_status tdp_sort_pairs(const uint64_t *keys_in, const uint32_t *va
         return TDP_ERR_INVALID_ARG;
     if (n > 0 && (keys_in == (const uint64_t *)keys_out || vals_in == (const uint32_t *)vals_out))
         return TDP_ERR_INVALID_ARG;
-    return radix_sort_pairs<unsigned long long>((const unsigned long long *)keys_in, vals_in, n, nullptr, key_bits,
+    return radix_sort_pairs<unsigned long long, uint32_t>((const unsigned long long *)keys_in, vals_in, n, nullptr,
+                                                          key_bits,
                                                 (unsigned long long *)keys_out, vals_out, ws, ws_bytes, d_status,
                                                 (cudaStream_t)stream);
 }

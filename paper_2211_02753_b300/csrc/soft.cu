@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(SA_THREADS) soft_reduce_kernel(const float *__
     const long long end = min(n, beg + chunk);
     const bool vec = (((uintptr_t)x | (uintptr_t)gid | (uintptr_t)(MODE == MODE_FILTER_BWD ? g0 : v)) % 16) == 0;
     const float *aux = MODE == MODE_FILTER_BWD ? g0 : v; // v, or grad_mask for the filter adjoint
-    const long long SUB = max(16ll * G, 4ll * SA_THREADS) / (4 * SA_THREADS) * (4 * SA_THREADS);
+    const long long SUB = (max(16ll * G, 512ll) + 3) / 4 * 4; // ~16 rows per group, multiple of 4
     for (long long sb = beg; sb < end; sb += SUB) {
         const long long se = min(end, sb + SUB);
         long long tail = sb;

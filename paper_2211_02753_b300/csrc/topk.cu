@@ -1,11 +1,13 @@
 // K8: ORDER BY value DESC, key ASC LIMIT k (k <= 16).
 //
-// Pass 1: every thread keeps the 16 best (value, key) pairs of its strided
-// share of the input in a sorted register list (insertions are rare once the
-// list is warm: an element is compared with the current 16th best first).
-// The block then extracts its k best with k rounds of a block-wide arg-max
-// over the threads' list heads; the winner pops its head.  Pass 2: one block
-// does the same over the per-block candidates.
+// Each warp keeps one sorted list of its 16 best (value, key) pairs spread
+// over lanes 0..15 (lane i holds the i-th best).  The warp reads 32 elements
+// at a time; an element is compared with the list's 16th entry (broadcast)
+// and almost always rejected there.  The few that qualify are inserted one at
+// a time: every lane compares the candidate with its own entry, the ballot
+// gives the insertion position, and entries behind it shift down one lane.
+// The 8 warp lists of a block are merged the same way by warp 0 and written
+// out; a single block then merges the per-block lists.
 #include "common.cuh"
 
 namespace tdp {
@@ -19,81 +21,80 @@ struct VK {
     int k;
 };
 
-__device__ __forceinline__ bool better(const VK &a, const VK &b) { return a.v > b.v || (a.v == b.v && a.k < b.k); }
-
-__device__ __forceinline__ VK worst_vk()
+__device__ __forceinline__ bool better(long long av, int ak, long long bv, int bk)
 {
-    VK w;
-    w.v = (long long)0x8000000000000000ull;
-    w.k = 0x7fffffff;
-    return w;
+    return av > bv || (av == bv && ak < bk);
 }
 
-__device__ __forceinline__ void list_insert(VK (&L)[TK_LIST], const VK &x)
+constexpr long long VK_WORST_V = (long long)0x8000000000000000ull;
+constexpr int VK_WORST_K = 0x7fffffff;
+
+// Warp-wide sorted list: lane i < 16 holds entry i (lanes >= 16 hold copies
+// of the worst value and never matter).
+struct WarpList {
+    long long v;
+    int k;
+};
+
+__device__ __forceinline__ void wl_init(WarpList &l)
 {
-    if (!better(x, L[TK_LIST - 1]))
-        return;
-    bool placed = false;
-#pragma unroll
-    for (int i = TK_LIST - 1; i >= 1; i--) {
-        if (!placed) {
-            if (better(x, L[i - 1])) {
-                L[i] = L[i - 1];
-            } else {
-                L[i] = x;
-                placed = true;
-            }
+    l.v = VK_WORST_V;
+    l.k = VK_WORST_K;
+}
+
+// Inserts the candidates held by the lanes in `mask` (each lane's (cv, ck)).
+__device__ __forceinline__ void wl_insert(WarpList &l, unsigned mask, long long cv, int ck)
+{
+    const int lane = threadIdx.x & 31;
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const long long xv = __shfl_sync(0xffffffffu, cv, src);
+        const int xk = __shfl_sync(0xffffffffu, ck, src);
+        // position = number of entries that stay ahead of x
+        const unsigned ahead = __ballot_sync(0xffffffffu, lane < TK_LIST && !better(xv, xk, l.v, l.k));
+        const int pos = __popc(ahead);
+        if (pos >= TK_LIST)
+            continue;
+        const long long uv = __shfl_up_sync(0xffffffffu, l.v, 1);
+        const int uk = __shfl_up_sync(0xffffffffu, l.k, 1);
+        if (lane == pos) {
+            l.v = xv;
+            l.k = xk;
+        } else if (lane > pos && lane < TK_LIST) {
+            l.v = uv;
+            l.k = uk;
         }
     }
-    if (!placed)
-        L[0] = x;
 }
 
-// k rounds of block arg-max over list heads; results to out (k entries).
-__device__ void block_extract(VK (&L)[TK_LIST], int k, VK *out)
+// Offers one element per lane (valid lanes only).
+__device__ __forceinline__ void wl_offer(WarpList &l, bool valid, long long v, int k)
 {
-    __shared__ VK s_best[TK_THREADS / 32];
-    __shared__ int s_who[TK_THREADS / 32];
-    __shared__ int s_win;
+    const long long tv = __shfl_sync(0xffffffffu, l.v, TK_LIST - 1);
+    const int tk = __shfl_sync(0xffffffffu, l.k, TK_LIST - 1);
+    const unsigned m = __ballot_sync(0xffffffffu, valid && better(v, k, tv, tk));
+    if (m)
+        wl_insert(l, m, v, k);
+}
+
+// Merges the warp lists of the block; warp 0 writes the first k to out.
+__device__ void block_merge(WarpList &l, int k, VK *out)
+{
+    __shared__ VK s_c[TK_THREADS / 32 * TK_LIST];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = 0; r < k; r++) {
-        VK b = L[0];
-        int who = threadIdx.x;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            VK ob;
-            ob.v = __shfl_xor_sync(0xffffffffu, b.v, o);
-            ob.k = __shfl_xor_sync(0xffffffffu, b.k, o);
-            int ow = __shfl_xor_sync(0xffffffffu, who, o);
-            if (better(ob, b) || (!better(b, ob) && ow < who)) {
-                b = ob;
-                who = ow;
-            }
+    if (lane < TK_LIST)
+        s_c[warp * TK_LIST + lane] = VK{l.v, l.k};
+    __syncthreads();
+    if (warp == 0) {
+        WarpList m;
+        wl_init(m);
+        for (int base = 0; base < TK_THREADS / 32 * TK_LIST; base += 32) {
+            VK c = s_c[base + lane];
+            wl_offer(m, true, c.v, c.k);
         }
-        if (lane == 0) {
-            s_best[warp] = b;
-            s_who[warp] = who;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            VK bb = s_best[0];
-            int ww = s_who[0];
-            for (int w = 1; w < TK_THREADS / 32; w++)
-                if (better(s_best[w], bb) || (!better(bb, s_best[w]) && s_who[w] < ww)) {
-                    bb = s_best[w];
-                    ww = s_who[w];
-                }
-            out[r] = bb;
-            s_win = ww;
-        }
-        __syncthreads();
-        if (threadIdx.x == s_win) {
-#pragma unroll
-            for (int i = 0; i < TK_LIST - 1; i++)
-                L[i] = L[i + 1];
-            L[TK_LIST - 1] = worst_vk();
-        }
-        __syncthreads();
+        if (lane < k)
+            out[lane] = VK{m.v, m.k};
     }
 }
 
@@ -102,17 +103,18 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass1_kernel(const long long 
                                                                 const long long *d_n, int k, VK *cand)
 {
     const long long n = d_n ? min(*d_n, n_max) : n_max;
-    VK L[TK_LIST];
-#pragma unroll
-    for (int i = 0; i < TK_LIST; i++)
-        L[i] = worst_vk();
-    for (long long i = (long long)blockIdx.x * TK_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * TK_THREADS) {
-        VK x;
-        x.v = vals[i];
-        x.k = keys[i];
-        list_insert(L, x);
+    WarpList l;
+    wl_init(l);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * TK_THREADS;
+    for (long long base = ((long long)blockIdx.x * (TK_THREADS / 32) + warp) * 32; base < n; base += stride) {
+        const long long i = base + lane;
+        const bool valid = i < n;
+        const long long v = valid ? vals[i] : VK_WORST_V;
+        const int kk = valid ? keys[i] : VK_WORST_K;
+        wl_offer(l, valid, v, kk);
     }
-    block_extract(L, k, cand + (size_t)blockIdx.x * k);
+    block_merge(l, k, cand + (size_t)blockIdx.x * k);
 }
 
 __global__ void __launch_bounds__(TK_THREADS) topk_pass2_kernel(const VK *__restrict__ cand, long long ncand,
@@ -120,13 +122,17 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass2_kernel(const VK *__rest
                                                                 long long *out_vals, int32_t *out_keys, long long *d_k)
 {
     __shared__ VK s_out[TK_MAXK];
-    VK L[TK_LIST];
-#pragma unroll
-    for (int i = 0; i < TK_LIST; i++)
-        L[i] = worst_vk();
-    for (long long i = threadIdx.x; i < ncand; i += TK_THREADS)
-        list_insert(L, cand[i]);
-    block_extract(L, k, s_out);
+    WarpList l;
+    wl_init(l);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long base = (long long)warp * 32; base < ncand; base += TK_THREADS) {
+        const long long i = base + lane;
+        const bool valid = i < ncand;
+        VK c = valid ? cand[i] : VK{VK_WORST_V, VK_WORST_K};
+        wl_offer(l, valid, c.v, c.k);
+    }
+    block_merge(l, k, s_out);
+    __syncthreads();
     const long long n = d_n ? min(*d_n, n_max) : n_max;
     const long long m = min((long long)k, n);
     if (threadIdx.x < m) {

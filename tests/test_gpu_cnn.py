@@ -124,7 +124,7 @@ def test_train_step_gradients_match_oracle():
 
 def test_adam_step_matches_oracle():
     p = params(7)
-    q = cnn.GlyphQuery(p, DEV)
+    q = cnn.GlyphQuery(p, DEV, lr=0.01, warmup=0)  # the oracle's Adam defaults
     r = np.random.default_rng(7)
     grads = {k: r.standard_normal(v.shape).astype(np.float32) for k, v in p.items()}
     for k in cnn.PARAMS:
@@ -188,9 +188,10 @@ def test_learned_part_gain(glyph_data):
     predicts the training-mean answer."""
     tr_img, tr_lab, te_img, te_lab = glyph_data
     targets = O.targets_from_labels(tr_lab).astype(np.float32)
-    # Adam at the paper's lr 0.01 diverges on this network (loss 9.5 -> 54 in
-    # 400 steps); 1e-3 is the fallback reading of the training recipe.
-    q = cnn.GlyphQuery(gen.cnn_params(gen.BASE_SEED + 5), DEV, lr=1e-3)
+    # The training recipe: Adam, lr 1e-3 reached by a 400-step linear warmup.
+    # (The paper's lr 0.01 diverges here: loss 9.5 -> 54 in 400 steps; 1e-3
+    # without warmup stalls at 90% of cells, class 0 absorbed into class 1.)
+    q = cnn.GlyphQuery(gen.cnn_params(gen.BASE_SEED + 5), DEV, lr=1e-3, warmup=400)
     g_te = torch.from_numpy(te_img).to(DEV)
     _, c0, r0 = q.exact_query(g_te)
     acc_init = query_accuracy(c0.cpu().numpy(), r0.cpu().numpy(), te_lab)
@@ -199,8 +200,6 @@ def test_learned_part_gain(glyph_data):
     B = 256
     losses = []
     for step in range(1600):  # 100 epochs of the 4096 training grids
-        if step == 1200:
-            q.lr = 3e-4
         i = (step % (4096 // B)) * B
         losses.append(q.train_step(g_tr[i:i + B], t_tr[i:i + B]))
     losses = [float(x.item()) for x in losses]
@@ -212,5 +211,5 @@ def test_learned_part_gain(glyph_data):
     print("query acc: init %.3f prior %.3f trained %.3f; cell acc %.4f; loss %.3f -> %.4f"
           % (acc_init, acc_prior, acc, cell_acc, losses[0], losses[-1]))
     assert losses[-1] < 0.1 * losses[0]
-    assert acc >= 0.5
-    assert acc - max(acc_init, acc_prior) >= 0.4
+    assert acc >= 0.9
+    assert acc - max(acc_init, acc_prior) >= 0.8

@@ -149,6 +149,27 @@ def test_groupby_sort_unbounded_keys_and_row_list(n):
         assert np.array_equal(np_(out["aggs"][j], g), ra[:, j])
 
 
+@pytest.mark.parametrize("agg", [("sum_mul_kminus", 6, 7, 100), ("avg", 6, None, None), ("min", 6, None, None),
+                                 ("max", 6, None, None), ("sum", 6, None, None)])
+def test_groupby_sort_single_value_aggregate(agg):
+    """One value aggregate (+ COUNT): the sort carries the value itself."""
+    n = 200003
+    t = _table(n, 77)
+    t["b32"] = (t["b32"] // 3).astype(np.int32)
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w"]
+    cols = [cu(t[k]) for k in names]
+    out = ops.groupby_agg(cols, [2], [agg, ("count",)], strategy="sort")
+    ops.check(out["status"])
+    op, a, b, k = agg
+    rk, ra = R.groupby([t["b32"]], [(op, t[names[a]], t[names[b]] if b is not None else None, k),
+                                    ("count", None, None, None)], n)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+    assert np.array_equal(np_(out["aggs"][0], g), ra[:, 0])
+    assert np.array_equal(np_(out["aggs"][1], g), ra[:, 1])
+
+
 def test_groupby_config1_60k_both_strategies():
     n = 60000
     t = gen.fact_table(n, 15000, gen.BASE_SEED + 0)

@@ -100,6 +100,22 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------- multi-rank
+
+def job_rate(units_per_rank: float, ms_local: float, world: int, device):
+    """Whole-job rate of `world` replicas: every rank processes
+    units_per_rank per step; the step time is the MAX over ranks (the slowest
+    replica bounds the job).  Returns (ms_per_step, units per second)."""
+    import torch
+    import torch.distributed as dist
+    ms = float(ms_local)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * world / (ms / 1000.0)
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -228,13 +244,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop(local)
-    ms = t0.elapsed_time(t1) / args.steps
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms, value = job_rate(N_FACT, t0.elapsed_time(t1) / args.steps, world, dev)
     ops.check(plan.status, "shipping-priority plan")
-    value = N_FACT * world / (ms / 1000.0)
 
     # ---- e2e: host (pinned) buffers in, top-10 out, every step
     pin_f = {k: torch.from_numpy(v).pin_memory() for k, v in fact_h.items()}
@@ -363,6 +374,17 @@ def other_plans(dev, stream, hbm_peak, args):
     td = {k: torch.from_numpy(v).to(dev) for k, v in t.items()}
     td["key"] = None
     del t
+    # standalone filter with stream compaction (row ids) over the 60M-row date column
+    fout = {}
+
+    def run_filter():
+        fout["o"] = ops.filter([td["date"]], [(0, "<=", 2460)], rowids=True)
+
+    ms = _time(run_filter, stream, steps)
+    nsel = int(fout["o"]["count"].item())
+    fbytes = N_FACT * 4 + nsel * 4
+    res["filter_60M"] = {"ms": ms, "rows_per_s": N_FACT / (ms / 1e3), "selected": nsel,
+                         "algo_gbs": fbytes / (ms / 1e3) / 1e9, "frac_hbm": fbytes / (ms / 1e3) / 1e9 / hbm_peak}
     for strategy in ("small_domain", "sort"):
         p = plans.PricingSummary(td, strategy)
         ms = _time(lambda: p.run(), stream, steps if strategy == "small_domain" else 3)
@@ -395,6 +417,19 @@ def other_plans(dev, stream, hbm_peak, args):
     algo = 10e6 * 24
     res["soft_query_10M_fwd_bwd"] = {"ms": ms, "rows_per_s": 10e6 / (ms / 1e3), "algo_gbs": algo / (ms / 1e3) / 1e9,
                                      "frac_hbm": algo / (ms / 1e3) / 1e9 / hbm_peak}
+    # the individual soft kernels: aggregation forward / backward (12 B/row
+    # each), soft filter forward (12 B/row: x, gid in, mask out) and backward
+    # (16 B/row: x, gid, grad_mask in, grad_x out)
+    th, tau = sq.theta, sq.tau
+    gm = torch.ones_like(sd["x"])
+    for name, fn, bpr in (
+            ("soft_agg_fwd_10M", lambda: ops.soft_agg_fwd(sd["x"], sd["v"], sd["gid"], th, tau), 12),
+            ("soft_agg_bwd_10M", lambda: ops.soft_agg_bwd(sd["x"], sd["v"], sd["gid"], th, tau, sq.gS, sq.gC), 12),
+            ("soft_filter_fwd_10M", lambda: ops.soft_filter_fwd(sd["x"], sd["gid"], th, tau), 12),
+            ("soft_filter_bwd_10M", lambda: ops.soft_filter_bwd(sd["x"], sd["gid"], th, tau, gm), 16)):
+        ms = _time(fn, stream, steps)
+        res[name] = {"ms": ms, "rows_per_s": 10e6 / (ms / 1e3), "algo_gbs": 10e6 * bpr / (ms / 1e3) / 1e9,
+                     "frac_hbm": 10e6 * bpr / (ms / 1e3) / 1e9 / hbm_peak}
     del sd, sq
     torch.cuda.empty_cache()
     res["trainable_query_glyph_cnn"] = glyph_plan(dev, stream, args)
@@ -459,6 +494,56 @@ def glyph_plan(dev, stream, args):
             "train_tflops": 3 * flops_fwd / (train_ms / 1e3) / 1e12}
 
 
+def run_only(args):
+    """One plan at 1/scale of its size, `steps` times after `warmup` runs, and
+    a one-line timing (CUDA events).  Used for profiler captures of a small
+    case; not the benchmark line."""
+    import torch
+    from paper_2211_02753_b300 import cnn, ops, plans
+    from oracle import cnn as O  # glyph targets: the exact query on true labels
+    dev = torch.device("cuda", 0)
+    sc = max(1, args.scale)
+    if args.only == "shipping":
+        f, d = (gen.fact_table(N_FACT // sc, N_DIM // sc, SEED2, cols=("key", "price", "disc", "date")),
+                gen.dim_table(N_DIM // sc, SEED2, cols=("key", "segment")))
+        p = plans.ShippingPriority({k: torch.from_numpy(v).to(dev) for k, v in f.items()},
+                                   {k: torch.from_numpy(v).to(dev) for k, v in d.items()})
+        fn = p.run
+    elif args.only in ("pricing", "pricing_sort", "filter"):
+        t = gen.fact_table(N_FACT // sc, N_DIM // sc, SEED2, cols=("flag", "status", "qty", "price", "disc", "date"))
+        td = {k: torch.from_numpy(v).to(dev) for k, v in t.items()}
+        if args.only == "filter":
+            fn = lambda: ops.filter([td["date"]], [(0, "<=", 2460)])  # noqa: E731
+        else:
+            fn = plans.PricingSummary(td, "sort" if args.only == "pricing_sort" else "small_domain").run
+    elif args.only == "chain":
+        dd = gen.chain_tables(100_000_000 // sc, 10_000_000 // sc, 1_000_000 // sc, gen.BASE_SEED + 2)
+        fn = plans.JoinChain({k: torch.from_numpy(v.astype(np.int32) if k == "probe_fk" else v).to(dev)
+                              for k, v in dd.items()}).run
+    elif args.only == "soft":
+        s = gen.soft_table(10_000_000 // sc, 1024, gen.BASE_SEED + 3)
+        fn = plans.SoftQuery({k: torch.from_numpy(v).to(dev) for k, v in s.items()}).run
+    else:  # glyph: one training step of the trainable query
+        g = max(16, 256 // sc)
+        img, lab = gen.glyph_grids(g, gen.BASE_SEED + 4)
+        q = cnn.GlyphQuery(gen.cnn_params(gen.BASE_SEED + 5), dev)
+        gi = torch.from_numpy(img).to(dev)
+        tg = torch.from_numpy(O.targets_from_labels(lab).astype(np.float32)).to(dev)
+        fn = lambda: q.train_step(gi, tg)  # noqa: E731
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"only": args.only, "scale": sc, "ms": a.elapsed_time(b) / max(1, args.steps)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,11 +551,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plans", default="all", choices=["all", "main"])
+    ap.add_argument("--only", default=None,
+                    choices=["shipping", "pricing", "pricing_sort", "filter", "chain", "soft", "glyph"],
+                    help="profiling mode: run one plan at 1/--scale size and print its time only")
+    ap.add_argument("--scale", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_gpu(args)
 
 

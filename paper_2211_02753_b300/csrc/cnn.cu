@@ -319,22 +319,26 @@ __global__ void splitk_reduce_kernel(const float *__restrict__ part, int splits,
 }
 
 // Column sums of a bf16 matrix [rows][C] into fp32 partials [blocks][C].
+// Every thread sums a fixed set of rows of one column; the per-thread sums
+// are then added in thread order (no atomics: the result is reproducible).
 __global__ void colsum_bf16_kernel(const bf16 *__restrict__ x, long long rows, int C, float *__restrict__ part)
 {
-    extern __shared__ float cs[];
-    for (int c = threadIdx.x; c < C; c += blockDim.x)
-        cs[c] = 0.f;
-    __syncthreads();
+    extern __shared__ float cs[]; // [blockDim.x]
     const int c = threadIdx.x % C;
     const int rstep = blockDim.x / C;
     float acc = 0.f;
-    for (long long r = (long long)blockIdx.x * rstep + threadIdx.x / C; r < rows; r += (long long)gridDim.x * rstep)
-        acc += bf2f(x[r * C + c]);
     if (threadIdx.x < rstep * C)
-        atomicAdd(&cs[c], acc);
+        for (long long r = (long long)blockIdx.x * rstep + threadIdx.x / C; r < rows;
+             r += (long long)gridDim.x * rstep)
+            acc += bf2f(x[r * C + c]);
+    cs[threadIdx.x] = acc;
     __syncthreads();
-    for (int i = threadIdx.x; i < C; i += blockDim.x)
-        part[(size_t)blockIdx.x * C + i] = cs[i];
+    for (int i = threadIdx.x; i < C; i += blockDim.x) {
+        float s = 0.f;
+        for (int j = 0; j < rstep; j++)
+            s += cs[j * C + i];
+        part[(size_t)blockIdx.x * C + i] = s;
+    }
 }
 
 // out[i] = sum_b part[b * stride + i] in float64, in block order
@@ -762,7 +766,7 @@ tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, in
     {
         float *bp = (float *)((char *)ws + align_up((size_t)FC1_WGRAD_SPLITS * HID * FEAT * sizeof(float), 256));
         int nb = (int)((n_cells + 63) / 64);
-        colsum_bf16_kernel<<<nb, 256, HID * sizeof(float), s>>>((const bf16 *)dh1, n_cells, HID, bp);
+        colsum_bf16_kernel<<<nb, 256, 256 * sizeof(float), s>>>((const bf16 *)dh1, n_cells, HID, bp);
         partial_sum_kernel<<<1, HID, 0, s>>>(bp, nb, HID, HID, dbfc1);
     }
     return launch_status();
@@ -814,7 +818,7 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
         float *bp = (float *)((char *)ws + align_up((size_t)sp * CH2 * 9 * CH1 * sizeof(float), 256));
         long long Q = n_cells * PO * PO;
         int nb = (int)((Q + 255) / 256);
-        colsum_bf16_kernel<<<nb, 256, CH2 * sizeof(float), s>>>((const bf16 *)dy2p, Q, CH2, bp);
+        colsum_bf16_kernel<<<nb, 256, 256 * sizeof(float), s>>>((const bf16 *)dy2p, Q, CH2, bp);
         partial_sum_kernel<<<1, CH2, 0, s>>>(bp, nb, CH2, CH2, db2);
     }
     return launch_status();

@@ -213,3 +213,22 @@ def test_learned_part_gain(glyph_data):
     assert losses[-1] < 0.1 * losses[0]
     assert acc >= 0.9
     assert acc - max(acc_init, acc_prior) >= 0.8
+
+
+def test_checkpoint_resume_reproduces_the_next_step_bitwise():
+    img, lab, t = _batch(4, 51)
+    tg = torch.from_numpy(t.astype(np.float32)).to(DEV)
+    g_img = torch.from_numpy(img).to(DEV)
+    a = cnn.GlyphQuery(params(8), DEV)
+    for _ in range(3):
+        a.train_step(g_img, tg)
+    st = a.state()
+    la = a.train_step(g_img, tg)
+    b = cnn.GlyphQuery(params(9), DEV)  # different init, then restored
+    b.load_state(st)
+    lb = b.train_step(g_img, tg)
+    torch.cuda.synchronize()
+    assert float(la.item()) == float(lb.item())
+    for k in cnn.PARAMS:
+        assert torch.equal(a.p[k], b.p[k]), k
+        assert torch.equal(a.m[k], b.m[k]) and torch.equal(a.v[k], b.v[k]), k

@@ -314,3 +314,21 @@ def test_bounded_wait_times_out_without_hanging():
     st.zero_()
     ops.debug_wait_flag(flag, 1000, st)
     assert int(st.item()) == 0
+
+
+def test_relational_results_are_deterministic():
+    """Five runs of the shipping-priority plan give bitwise identical results."""
+    from paper_2211_02753_b300 import plans
+    nf, nd = 2_000_000, 500_000
+    fact = {k: cu(v) for k, v in gen.fact_table(nf, nd, 5, cols=("key", "price", "disc", "date")).items()}
+    dim = {k: cu(v) for k, v in gen.dim_table(nd, 5, cols=("key", "segment")).items()}
+    p = plans.ShippingPriority(fact, dim)
+    ref = None
+    for _ in range(5):
+        o = p.run()
+        g = int(o["ngroups"].item())
+        got = (np_(o["groups"]["keys"][0], g).tobytes(), np_(o["groups"]["aggs"][0], g).tobytes(),
+               np_(o["top_vals"]).tobytes(), np_(o["top_keys"]).tobytes())
+        ref = ref or got
+        assert got == ref
+    ops.check(p.status)

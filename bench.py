@@ -100,6 +100,32 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- traffic
+
+# DRAM bytes (read + write) of a stage's kernel from an ncu capture kept in
+# profiles/, per fact row of the capture's workload, and the source file it was
+# built from.  The capture ran the plan at 1/4 scale; every term of the
+# probe's traffic grows with the fact rows, so it is scaled by them.
+TRAFFIC = {
+    "join_probe": {"bytes_per_fact_row": (339.988736e6 + 28.8256e6) / 15e6,
+                   "src": "paper_2211_02753_b300/csrc/join.cu", "sha1": "3b0679075d24",
+                   "capture": "profiles/join_probe_kernel_15M_fact_rows.md"},
+}
+
+
+def measured_traffic(stage: str):
+    """Per-launch DRAM bytes of the stage at full size, or None when there is
+    no capture or the kernel source changed since it was taken."""
+    import hashlib
+    t = TRAFFIC.get(stage)
+    if t is None:
+        return None
+    with open(os.path.join(ROOT, t["src"]), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest()[:12] != t["sha1"]:
+            return None
+    return t["bytes_per_fact_row"] * N_FACT
+
+
 # ------------------------------------------------------------- multi-rank
 
 def job_rate(units_per_rank: float, ms_local: float, world: int, device):
@@ -310,7 +336,7 @@ def run_gpu(args):
     dom_name = stage_names[dom]
     achieved = algo[dom_name] / (st_ms[dom] / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "kernel": dom_name,
+                "frac": achieved / hbm_peak, "traffic": measured_traffic(dom_name), "kernel": dom_name,
                 "peak_kind": peak_kind + " (copy bandwidth)",
                 "stages_ms": dict(zip(stage_names, st_ms)),
                 "stages_algo_gbs": {k: algo[k] / (t / 1000.0) / 1e9 for k, t in zip(stage_names, st_ms)}}

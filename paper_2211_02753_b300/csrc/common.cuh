@@ -50,14 +50,26 @@ struct PredSet {
     int32_t cmp[TDP_MAX_PREDS];
     long long lit[TDP_MAX_PREDS];
     int32_t vec_ok[TDP_MAX_PREDS]; // column base 16-byte aligned
+    // Each comparison as a closed range test over the column's own type:
+    // holds(v) = (lo <= v <= hi) != neg, with lo/hi clamped to the type's
+    // range (an empty range is the full range with neg set: never true).
+    long long lo[TDP_MAX_PREDS], hi[TDP_MAX_PREDS];
+    int32_t neg[TDP_MAX_PREDS];
     int32_t n;
 };
+
+void pred_range(int dt, int cmp, long long lit, long long *lo, long long *hi, int32_t *neg);
 
 // Validates `preds` against `cols` and fills a PredSet.
 tdp_status make_predset(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds, int64_t n,
                         PredSet *out);
 
 // ---------------------------------------------------------------- device side
+
+__device__ __forceinline__ int dtype_size_dev(int dt)
+{
+    return dt == TDP_I64 ? 8 : (dt == TDP_I32 || dt == TDP_F32) ? 4 : dt == TDP_BF16 ? 2 : 1;
+}
 
 __device__ __forceinline__ void set_status(int32_t *s, int32_t code)
 {
@@ -209,6 +221,18 @@ __device__ __forceinline__ void load_rows(const void *p, int dt, bool vec_ok, lo
 #pragma unroll
     for (int j = 0; j < STEPS; j++)
         load4_int(p, dt, vec_ok, r0 + j * 128, n, v[j]);
+}
+
+// Range form of predicate p for a value already widened to 32 bits (I8, U8,
+// I32 columns; lo/hi are clamped into the column type, so hi - lo fits).
+__device__ __forceinline__ unsigned range_holds32(int v, int lo, unsigned span, unsigned neg)
+{
+    return ((unsigned)(v - lo) <= span ? 1u : 0u) ^ neg;
+}
+
+__device__ __forceinline__ unsigned range_holds64(long long v, long long lo, unsigned long long span, unsigned neg)
+{
+    return ((unsigned long long)(v - lo) <= span ? 1u : 0u) ^ neg;
 }
 
 __device__ __forceinline__ bool cmp_holds(long long v, int cmp, long long lit)

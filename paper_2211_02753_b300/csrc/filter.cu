@@ -1,126 +1,183 @@
 // K1/K2: predicate filter with stream compaction and fused column gather.
 //
-// One pass over the predicate columns.  A tile is 256 threads x 16 rows.
-// Warp w of a tile owns 512 consecutive rows, visited in 4 steps of 128 rows
-// in which lane l holds rows 4l..4l+3 (one 16-byte load of an int32 column,
-// a 4-byte load of an int8 column, two 16-byte loads of an int64 column, so
-// each warp step reads one contiguous 512 B / 128 B / 1 KiB span).  Every
-// row's output slot is found with warp ballots + popc (one ballot per row
-// position within the lane's 4 rows), a scan over the 8 warps of the tile and
-// a decoupled look-back over earlier tiles (tile ids from an atomic ticket,
-// so every predecessor is already resident).  Output is stable.
+// One pass over the predicate columns; one tile of TILE = 256 x 4 x STEPS
+// rows per block (16384 rows while the predicate columns take <= 4 bytes a
+// row, fewer for wider predicates so that a tile stays <= 64 KiB).
+//   1. Thread 0 stages the tile of every predicate column in shared memory
+//      with one bulk copy per column (cp.async.bulk, completion on an
+//      mbarrier); tiles at the ragged end, and columns whose base is not
+//      16-byte aligned, are read with plain loads instead.
+//   2. Lane l of warp w tests rows w*STEPS*128 + j*128 + 4l..4l+3 (step j):
+//      every comparison is a range test (lo <= v <= hi) != neg on the
+//      column's own type.  Ballots + popc give each row its rank within the
+//      warp, the 8 warp totals its rank within the tile.
+//   3. The qualifying row ids are written to shared memory (over the
+//      consumed predicate tile) at their tile-local ranks, while warp 0 runs
+//      the decoupled look-back over earlier tiles for the tile's output
+//      offset (tiles are numbered by block index; every wait is bounded).
+//   4. The block writes its run of row ids, and the gathered columns at those
+//      rows, to consecutive output slots: coalesced stores.
+// Output is stable (row order).
+#include <algorithm>
+
 #include "filter_api.cuh"
 
 namespace tdp {
 
 constexpr int FT_THREADS = 256;
-constexpr int FT_STEPS = 4;
-constexpr int FT_WARP_ROWS = FT_STEPS * 128;
-constexpr int FT_TILE = FT_THREADS / 32 * FT_WARP_ROWS; // 4096
+constexpr int FT_MAX_STEPS = 16;
+constexpr int FT_MIN_TILE = FT_THREADS * 4; // 1024 rows: the workspace is sized for this tile
+constexpr int FT_SMEM_CAP = 64 * 1024;      // predicate bytes of one tile
 
-// Copies element k (0..3) of a 4-row group at row r of a column of `size`
-// bytes to out[pos].
-__device__ __forceinline__ void gather_store(const void *col, void *out, int size, bool vec_ok, long long r,
-                                             long long n, unsigned m4, long long pos, long long cap)
+__device__ __forceinline__ uint32_t ft_smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Mask bits (4 per step) of predicate p, rows read from shared memory.
+template <int STEPS>
+__device__ __forceinline__ void ft_test_smem(const PredSet &ps, int p, const unsigned char *tile_col, int lrow,
+                                             unsigned (&m)[STEPS])
 {
-    if (size == 8) {
-        long long v[4];
-        if (vec_ok && r + 3 < n) {
-            longlong2 a = __ldg((const longlong2 *)((const long long *)col + r));
-            longlong2 b = __ldg((const longlong2 *)((const long long *)col + r + 2));
-            v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-        } else {
+    const int dt = ps.dt[p];
+    const unsigned neg = (unsigned)ps.neg[p];
+    if (dt == TDP_I64) {
+        const long long lo = ps.lo[p];
+        const unsigned long long span = (unsigned long long)(ps.hi[p] - lo);
 #pragma unroll
-            for (int k = 0; k < 4; k++)
-                v[k] = (m4 >> k & 1) ? ((const long long *)col)[r + k] : 0;
+        for (int j = 0; j < STEPS; j++) {
+            const longlong2 *q = (const longlong2 *)(tile_col + (size_t)(lrow + j * 128) * 8);
+            longlong2 a = q[0], b = q[1];
+            unsigned t = range_holds64(a.x, lo, span, neg) | range_holds64(a.y, lo, span, neg) << 1 |
+                         range_holds64(b.x, lo, span, neg) << 2 | range_holds64(b.y, lo, span, neg) << 3;
+            m[j] &= t;
         }
+        return;
+    }
+    const int lo = (int)ps.lo[p];
+    const unsigned span = (unsigned)((int)ps.hi[p] - lo);
+    if (dt == TDP_I32) {
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (m4 >> k & 1) {
-                if (pos < cap)
-                    ((long long *)out)[pos] = v[k];
-                pos++;
-            }
-    } else if (size == 4) {
-        int v[4];
-        if (vec_ok && r + 3 < n) {
-            int4 a = __ldg((const int4 *)((const int *)col + r));
-            v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                v[k] = (m4 >> k & 1) ? ((const int *)col)[r + k] : 0;
+        for (int j = 0; j < STEPS; j++) {
+            int4 w = *(const int4 *)(tile_col + (size_t)(lrow + j * 128) * 4);
+            unsigned t = range_holds32(w.x, lo, span, neg) | range_holds32(w.y, lo, span, neg) << 1 |
+                         range_holds32(w.z, lo, span, neg) << 2 | range_holds32(w.w, lo, span, neg) << 3;
+            m[j] &= t;
         }
+        return;
+    }
+    const bool sgn = dt == TDP_I8;
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (m4 >> k & 1) {
-                if (pos < cap)
-                    ((int *)out)[pos] = v[k];
-                pos++;
-            }
-    } else if (size == 2) {
+    for (int j = 0; j < STEPS; j++) {
+        unsigned w = *(const unsigned *)(tile_col + lrow + j * 128);
+        unsigned t = 0;
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (m4 >> k & 1) {
-                if (pos < cap)
-                    ((uint16_t *)out)[pos] = ((const uint16_t *)col)[r + k];
-                pos++;
-            }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (m4 >> k & 1) {
-                if (pos < cap)
-                    ((uint8_t *)out)[pos] = ((const uint8_t *)col)[r + k];
-                pos++;
-            }
+        for (int k = 0; k < 4; k++) {
+            unsigned b = (w >> (8 * k)) & 0xffu;
+            int v = sgn ? (int)(int8_t)b : (int)b;
+            t |= range_holds32(v, lo, span, neg) << k;
+        }
+        m[j] &= t;
     }
 }
 
-__global__ void __launch_bounds__(FT_THREADS) filter_kernel(PredSet ps, GatherSet gs, long long n_host,
-                                                            const long long *d_n, int32_t *out_rowid, long long cap, long long *d_count,
-                                                            unsigned long long *tile_status, unsigned *ticket,
-                                                            int32_t *d_status, uint32_t limit, long long num_tiles)
+// Same for rows read from global memory (ragged tile or unaligned column).
+template <int STEPS>
+__device__ __forceinline__ void ft_test_global(const PredSet &ps, int p, long long r0, long long n,
+                                               unsigned (&m)[STEPS])
 {
-    // The block takes a ticket; warp w then owns sub-tile ticket*8 + w and does
-    // its own decoupled look-back (no block-wide barrier after the start).
-    __shared__ long long s_tile;
-
-    if (threadIdx.x == 0)
-        s_tile = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const long long tile = s_tile;
-    const long long n = d_n ? min(*d_n, n_host) : n_host;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long wtile = tile * (FT_THREADS / 32) + warp;
-    const long long r0 = tile * FT_TILE + (long long)warp * FT_WARP_ROWS + 4 * lane;
-
-    unsigned m[FT_STEPS];
+    const unsigned neg = (unsigned)ps.neg[p];
+    const long long lo = ps.lo[p];
+    const unsigned long long span = (unsigned long long)(ps.hi[p] - lo);
 #pragma unroll
-    for (int j = 0; j < FT_STEPS; j++) {
-        long long r = r0 + j * 128;
-        m[j] = 0;
+    for (int j = 0; j < STEPS; j++) {
+        long long v[4];
+        load4_int(ps.col[p], ps.dt[p], ps.vec_ok[p], r0 + j * 128, n, v);
+        unsigned t = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            m[j] |= (r + k < n) ? (1u << k) : 0u;
+            t |= range_holds64(v[k], lo, span, neg) << k;
+        m[j] &= t;
     }
-    for (int p = 0; p < ps.n; p++) {
-        long long v[FT_STEPS][4];
-        load_rows<FT_STEPS>(ps.col[p], ps.dt[p], ps.vec_ok[p], r0, n, v);
+}
+
+template <int STEPS>
+__global__ void __launch_bounds__(FT_THREADS, 3) filter_kernel(PredSet ps, GatherSet gs, long long n_host,
+                                                            const long long *d_n, int32_t *out_rowid, long long cap,
+                                                            long long *d_count, unsigned long long *tile_status,
+                                                            int32_t *d_status, uint32_t limit, long long num_tiles)
+{
+    constexpr int TILE = FT_THREADS * 4 * STEPS;
+    extern __shared__ __align__(128) unsigned char ft_smem[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ unsigned s_warp[FT_THREADS / 32];
+    __shared__ unsigned long long s_excl;
+
+    const long long tile = blockIdx.x;
+    const long long n = d_n ? min(*d_n, n_host) : n_host;
+    const long long rbase = tile * TILE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lrow = warp * (STEPS * 128) + 4 * lane;
+
+    // 1. stage the predicate columns of a full tile (all of them 16-byte aligned)
+    bool bulk = ps.n > 0 && rbase + TILE <= n;
+    for (int p = 0; p < ps.n; p++)
+        bulk = bulk && ps.vec_ok[p];
+    if (bulk && threadIdx.x == 0) {
+        const uint32_t bar = ft_smem_u32(&s_bar);
+        uint32_t bytes = 0;
+        for (int p = 0; p < ps.n; p++)
+            bytes += TILE * (uint32_t)dtype_size_dev(ps.dt[p]);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        uint32_t off = 0;
+        for (int p = 0; p < ps.n; p++) {
+            const uint32_t sz = TILE * (uint32_t)dtype_size_dev(ps.dt[p]);
+            const char *src = (const char *)ps.col[p] + (size_t)rbase * dtype_size_dev(ps.dt[p]);
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             ft_smem_u32(ft_smem + off)),
+                         "l"(src), "r"(sz), "r"(bar)
+                         : "memory");
+            off += sz;
+        }
+    }
+    __syncthreads(); // the mbarrier is initialised before anyone waits on it
+
+    unsigned m[STEPS];
 #pragma unroll
-        for (int j = 0; j < FT_STEPS; j++)
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (!cmp_holds(v[j][k], ps.cmp[p], ps.lit[p]))
-                    m[j] &= ~(1u << k);
+    for (int j = 0; j < STEPS; j++) {
+        const long long r = rbase + lrow + j * 128;
+        m[j] = r + 3 < n ? 0xfu : (r + 2 < n ? 0x7u : (r + 1 < n ? 0x3u : (r < n ? 0x1u : 0u)));
+    }
+    if (bulk) {
+        bool ok = false;
+        for (uint32_t i = 0; i < limit && !ok; i++) {
+            uint32_t done;
+            asm volatile("{\n\t.reg .pred p;\n\t"
+                         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                         "selp.b32 %0, 1, 0, p;\n\t}"
+                         : "=r"(done)
+                         : "r"(ft_smem_u32(&s_bar))
+                         : "memory");
+            ok = done != 0;
+        }
+        if (!ok)
+            set_status(d_status, TDP_ERR_TIMEOUT);
+        uint32_t off = 0;
+        for (int p = 0; p < ps.n; p++) {
+            ft_test_smem<STEPS>(ps, p, ft_smem + off, lrow, m);
+            off += TILE * dtype_size_dev(ps.dt[p]);
+        }
+    } else {
+        for (int p = 0; p < ps.n; p++)
+            ft_test_global<STEPS>(ps, p, rbase + lrow, n, m);
     }
 
-    // ballot / popc ranks
+    // 2. ranks within the warp and the tile
+    // per step: rank of the lane's first row within the step (low 16 bits) and
+    // the step's count (high 16 bits)
     const unsigned lt = lanemask_lt();
-    unsigned step_cnt[FT_STEPS], lane_pref[FT_STEPS];
-    unsigned warp_tot = 0;
+    unsigned rank[STEPS], warp_tot = 0;
 #pragma unroll
-    for (int j = 0; j < FT_STEPS; j++) {
+    for (int j = 0; j < STEPS; j++) {
         unsigned c = 0, pre = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -128,38 +185,79 @@ __global__ void __launch_bounds__(FT_THREADS) filter_kernel(PredSet ps, GatherSe
             c += __popc(b);
             pre += __popc(b & lt);
         }
-        step_cnt[j] = c;
-        lane_pref[j] = pre;
+        rank[j] = c << 16 | pre;
         warp_tot += c;
     }
-    const unsigned long long excl = lookback_exclusive(tile_status, wtile, warp_tot, limit, d_status);
-    if (lane == 0 && wtile == num_tiles - 1) { // num_tiles counts warp sub-tiles
-        long long total = (long long)(excl + warp_tot);
-        *d_count = total;
-        if (total > cap)
-            set_status(d_status, TDP_ERR_CAPACITY);
+    if (lane == 0)
+        s_warp[warp] = warp_tot;
+    __syncthreads(); // predicate tile consumed; warp totals visible
+    unsigned woff = 0, btot = 0;
+#pragma unroll
+    for (int w = 0; w < FT_THREADS / 32; w++) {
+        unsigned t = s_warp[w];
+        woff += w < warp ? t : 0;
+        btot += t;
     }
 
-    long long pos = (long long)excl;
+    // 3. row ids to shared memory at their tile ranks; look-back for the tile offset
+    int32_t *stage = (int32_t *)ft_smem;
+    {
+        unsigned pos = woff;
 #pragma unroll
-    for (int j = 0; j < FT_STEPS; j++) {
-        const long long r = r0 + j * 128;
-        long long p = pos + lane_pref[j];
-        if (m[j]) {
-            if (out_rowid) {
-                long long q = p;
+        for (int j = 0; j < STEPS; j++) {
+            unsigned q = pos + (rank[j] & 0xffffu);
 #pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (m[j] >> k & 1) {
-                        if (q < cap)
-                            out_rowid[q] = (int32_t)(r + k);
-                        q++;
-                    }
-            }
-            for (int g = 0; g < gs.n; g++)
-                gather_store(gs.col[g], gs.out[g], gs.size[g], gs.vec_ok[g], r, n, m[j], p, cap);
+            for (int k = 0; k < 4; k++)
+                if (m[j] >> k & 1)
+                    stage[q++] = (int32_t)(rbase + lrow + j * 128 + k);
+            pos += rank[j] >> 16;
         }
-        pos += step_cnt[j];
+    }
+    if (warp == 0) {
+        const unsigned long long e = lookback_exclusive(tile_status, tile, btot, limit, d_status);
+        if (lane == 0) {
+            s_excl = e;
+            if (tile == num_tiles - 1) {
+                const long long total = (long long)(e + btot);
+                *d_count = total;
+                if (total > cap)
+                    set_status(d_status, TDP_ERR_CAPACITY);
+            }
+        }
+    }
+    __syncthreads();
+
+    // 4. coalesced output of the tile's run
+    const long long excl = (long long)s_excl;
+    const unsigned lim = (unsigned)max(0ll, min((long long)btot, cap - excl));
+    if (out_rowid)
+        for (unsigned i = threadIdx.x; i < lim; i += FT_THREADS)
+            out_rowid[excl + i] = stage[i];
+    for (int g = 0; g < gs.n; g++) {
+        const void *col = gs.col[g];
+        void *out = gs.out[g];
+        switch (gs.size[g]) {
+        case 8:
+#pragma unroll 4
+            for (unsigned i = threadIdx.x; i < lim; i += FT_THREADS)
+                ((long long *)out)[excl + i] = __ldg((const long long *)col + stage[i]);
+            break;
+        case 4:
+#pragma unroll 4
+            for (unsigned i = threadIdx.x; i < lim; i += FT_THREADS)
+                ((int32_t *)out)[excl + i] = __ldg((const int32_t *)col + stage[i]);
+            break;
+        case 2:
+#pragma unroll 4
+            for (unsigned i = threadIdx.x; i < lim; i += FT_THREADS)
+                ((uint16_t *)out)[excl + i] = ((const uint16_t *)col)[stage[i]];
+            break;
+        default:
+#pragma unroll 4
+            for (unsigned i = threadIdx.x; i < lim; i += FT_THREADS)
+                ((uint8_t *)out)[excl + i] = ((const uint8_t *)col)[stage[i]];
+            break;
+        }
     }
 }
 
@@ -190,6 +288,36 @@ tdp_status make_gatherset(const tdp_col *cols, int32_t ncols, const int32_t *gat
     return TDP_OK;
 }
 
+// Rows per tile for predicate columns taking `row_bytes` bytes a row.
+static int filter_steps(int row_bytes)
+{
+    int steps = FT_MAX_STEPS;
+    while (steps > 1 && (size_t)FT_THREADS * 4 * steps * row_bytes > FT_SMEM_CAP)
+        steps >>= 1;
+    return steps;
+}
+
+template <int STEPS>
+static tdp_status launch_filter(const PredSet &ps, const GatherSet &gs, long long n, const long long *d_n,
+                                int32_t *out_rowid, long long cap, long long *d_count, void *ws, int32_t *d_status,
+                                cudaStream_t s)
+{
+    constexpr long long TILE = FT_THREADS * 4 * STEPS;
+    const long long tiles = (n + TILE - 1) / TILE;
+    size_t pred_bytes = 0;
+    for (int p = 0; p < ps.n; p++)
+        pred_bytes += (size_t)TILE * dtype_size(ps.dt[p]);
+    const size_t smem = std::max(pred_bytes, (size_t)TILE * 4);
+    auto kern = filter_kernel<STEPS>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TDP_ERR_CUDA;
+    unsigned long long *status = (unsigned long long *)((char *)ws + 16);
+    cudaMemsetAsync(status, 0, (size_t)tiles * 8, s);
+    kern<<<(unsigned)tiles, FT_THREADS, smem, s>>>(ps, gs, n, d_n, out_rowid, cap, d_count, status, d_status,
+                                                    spin_limit(), tiles);
+    return launch_status();
+}
+
 tdp_status filter_rows(const PredSet &ps, long long n, const long long *d_n, int32_t *out_rowid, long long cap,
                        long long *d_count, const GatherSet *gs, void *ws, int32_t *d_status, cudaStream_t s)
 {
@@ -199,14 +327,17 @@ tdp_status filter_rows(const PredSet &ps, long long n, const long long *d_n, int
     }
     GatherSet none;
     none.n = 0;
-    long long tiles = (n + FT_TILE - 1) / FT_TILE;
-    long long wtiles = tiles * (FT_THREADS / 32); // one look-back word per warp sub-tile
-    unsigned *ticket = (unsigned *)ws;
-    unsigned long long *status = (unsigned long long *)((char *)ws + 16);
-    cudaMemsetAsync(ws, 0, 16 + (size_t)wtiles * 8, s);
-    filter_kernel<<<(unsigned)tiles, FT_THREADS, 0, s>>>(ps, gs ? *gs : none, n, d_n, out_rowid, cap, d_count, status,
-                                                         ticket, d_status, spin_limit(), wtiles);
-    return launch_status();
+    const GatherSet &g = gs ? *gs : none;
+    int row_bytes = 0;
+    for (int p = 0; p < ps.n; p++)
+        row_bytes += dtype_size(ps.dt[p]);
+    switch (filter_steps(row_bytes)) {
+    case 16: return launch_filter<16>(ps, g, n, d_n, out_rowid, cap, d_count, ws, d_status, s);
+    case 8: return launch_filter<8>(ps, g, n, d_n, out_rowid, cap, d_count, ws, d_status, s);
+    case 4: return launch_filter<4>(ps, g, n, d_n, out_rowid, cap, d_count, ws, d_status, s);
+    case 2: return launch_filter<2>(ps, g, n, d_n, out_rowid, cap, d_count, ws, d_status, s);
+    default: return launch_filter<1>(ps, g, n, d_n, out_rowid, cap, d_count, ws, d_status, s);
+    }
 }
 
 } // namespace tdp
@@ -215,8 +346,9 @@ using namespace tdp;
 
 extern "C" size_t tdp_filter_workspace(int64_t n)
 {
-    long long wtiles = (n + FT_TILE - 1) / FT_TILE * (FT_THREADS / 32);
-    return align_up(16 + (size_t)wtiles * 8, 256);
+    // one look-back word per tile, sized for the smallest tile
+    long long tiles = (n + FT_MIN_TILE - 1) / FT_MIN_TILE;
+    return align_up(16 + (size_t)tiles * 8, 256);
 }
 
 extern "C" tdp_status tdp_filter(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds,

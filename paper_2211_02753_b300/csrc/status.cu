@@ -17,6 +17,61 @@ int num_sms()
     return v > 0 ? v : 148;
 }
 
+// The range [lo, hi] (and negation) equivalent to `v cmp lit` for values of
+// type dt: LT/LE/GT/GE bound one side, EQ is [lit, lit], NE its complement.
+// Bounds are clamped to the type's range; an empty range becomes the full
+// range with neg = 1 (never true).
+void pred_range(int dt, int cmp, long long lit, long long *lo, long long *hi, int32_t *neg)
+{
+    long long tmin, tmax;
+    switch (dt) {
+    case TDP_I8: tmin = -128, tmax = 127; break;
+    case TDP_U8: tmin = 0, tmax = 255; break;
+    case TDP_I32: tmin = INT32_MIN, tmax = INT32_MAX; break;
+    default: tmin = INT64_MIN, tmax = INT64_MAX; break;
+    }
+    long long a = tmin, b = tmax;
+    bool empty = false;
+    int ng = 0;
+    switch (cmp) {
+    case TDP_LT:
+        if (lit <= tmin) empty = true;
+        else b = lit - 1 < tmax ? lit - 1 : tmax;
+        break;
+    case TDP_LE:
+        if (lit < tmin) empty = true;
+        else b = lit < tmax ? lit : tmax;
+        break;
+    case TDP_GT:
+        if (lit >= tmax) empty = true;
+        else a = lit + 1 > tmin ? lit + 1 : tmin;
+        break;
+    case TDP_GE:
+        if (lit > tmax) empty = true;
+        else a = lit > tmin ? lit : tmin;
+        break;
+    case TDP_EQ:
+        if (lit < tmin || lit > tmax) empty = true;
+        else a = b = lit;
+        break;
+    default: // NE
+        if (lit < tmin || lit > tmax) {
+            a = tmin, b = tmax; // always true
+        } else {
+            a = b = lit;
+            ng = 1;
+        }
+        break;
+    }
+    if (empty) {
+        a = tmin, b = tmax;
+        ng = 1;
+    }
+    *lo = a;
+    *hi = b;
+    *neg = ng;
+}
+
 tdp_status make_predset(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds, int64_t n,
                         PredSet *out)
 {
@@ -36,6 +91,7 @@ tdp_status make_predset(const tdp_col *cols, int32_t ncols, const tdp_pred *pred
         out->cmp[i] = preds[i].cmp;
         out->lit[i] = preds[i].lit;
         out->vec_ok[i] = ((uintptr_t)cols[c].data % 16) == 0;
+        pred_range(cols[c].dtype, preds[i].cmp, preds[i].lit, &out->lo[i], &out->hi[i], &out->neg[i]);
     }
     for (int i = npreds; i < TDP_MAX_PREDS; i++) {
         out->col[i] = nullptr;
@@ -43,6 +99,9 @@ tdp_status make_predset(const tdp_col *cols, int32_t ncols, const tdp_pred *pred
         out->cmp[i] = 0;
         out->lit[i] = 0;
         out->vec_ok[i] = 0;
+        out->lo[i] = 0;
+        out->hi[i] = 0;
+        out->neg[i] = 0;
     }
     return TDP_OK;
 }

@@ -84,6 +84,46 @@ def test_filter_unaligned_columns_and_capacity():
     assert np.array_equal(np_(out["rowid"], cap), ref[:cap])
 
 
+@pytest.mark.parametrize("n", [16384, 50000])
+def test_filter_literals_outside_the_column_type(n):
+    """Range form of each comparison at and beyond the bounds of int8, uint8
+    and int32 columns (literals that clamp, or make the test empty or total),
+    over several full tiles and a ragged one."""
+    t = _table(n, 11)
+    names = ["a8", "u8", "b32"]
+    cols = [cu(t[k]) for k in names]
+    big = 2**40
+    cases = [(0, "<", 200), (0, ">", 200), (0, "==", 300), (0, "!=", 300), (0, ">=", -200), (0, "<=", -129),
+             (0, "<", -128), (0, ">", 127), (0, ">=", 127), (0, "<=", -128),
+             (1, "<", 0), (1, ">=", 0), (1, "<=", 255), (1, ">", 255), (1, "==", -1), (1, "!=", 256),
+             (2, "<", -big), (2, ">", -big), (2, "<=", big), (2, ">=", big), (2, "<", -(2**63)),
+             (2, ">", 2**63 - 1), (2, "==", 999), (2, "!=", -1000)]
+    for c, op, lit in cases:
+        out = ops.filter(cols, [(c, op, lit)], gather=[2])
+        ops.check(out["status"])
+        ref = R.filter([(t[names[c]], op, lit)], n)
+        cnt = int(out["count"].item())
+        assert cnt == len(ref), (c, op, lit)
+        assert np.array_equal(np_(out["rowid"], cnt), ref), (c, op, lit)
+        assert np.array_equal(np_(out["gathered"][0], cnt), t["b32"][ref]), (c, op, lit)
+
+
+def test_filter_device_row_count():
+    """The row count read on the device (d_n) cuts the table inside a tile."""
+    n = 70000
+    t = _table(n, 12)
+    cols = [cu(t["u8"])]
+    for m in (0, 1, 16383, 16385, 69999):
+        d_n = torch.tensor([m], dtype=torch.int64, device=DEV)
+        out = ops.filter(cols, [(0, ">=", 100)], gather=[0], d_n=d_n)
+        ops.check(out["status"])
+        ref = R.filter([(t["u8"][:m], ">=", 100)], m)
+        cnt = int(out["count"].item())
+        assert cnt == len(ref)
+        assert np.array_equal(np_(out["rowid"], cnt), ref)
+        assert np.array_equal(np_(out["gathered"][0], cnt), t["u8"][ref])
+
+
 def test_filter_config1_60m_rows():
     n = 60_000_000
     t = gen.fact_table(n, 15_000_000, gen.BASE_SEED + 1, cols=("date",))

@@ -231,14 +231,21 @@ tdp_status tdp_sort_pairs(const uint64_t *keys_in, const uint32_t *vals_in, int6
 
 /* ------------------------------------------------------------------ join */
 
-/* Smallest power-of-two slot count with load factor <= 1/2 for n keys. */
+/* Smallest power-of-two slot count (>= 8) with load factor <= 1/2 for n keys. */
 int64_t tdp_join_default_slots(int64_t n_keys);
 
 /*
- * Build an open-addressing hash table for an inner equi-join on int32 keys.
- * The table is `nslots` (a power of two) 64-bit slots in device memory owned
- * by the caller; slot = (uint32(key) << 32) | payload, empty = all ones.
- * Linear probing from a multiplicative hash; one 64-bit CAS per insert.
+ * Build an open-addressing hash table for an inner equi-join on int32 keys
+ * (the hash join of Sec. 2's relational operators over key tensors).
+ * The table is nslots x 8 bytes of device memory owned by the caller
+ * (nslots a power of two >= 8, base 32-byte aligned), laid out as two int32
+ * arrays of nslots entries: the keys, then the payloads (entry i of one
+ * belongs to entry i of the other).  Keys are grouped in buckets of 8 (32
+ * bytes); a multiplicative hash picks a bucket and a full bucket without the
+ * key passes the search on to the next one (linear probing over buckets).
+ * An empty key entry holds INT32_MIN, so that key cannot be stored: a build
+ * row with key INT32_MIN sets TDP_ERR_OVERFLOW and is dropped, and a probe
+ * row with that key finds nothing.  One 32-bit CAS per insert.
  *
  *   cols/preds         build-side columns and an optional fused filter
  *   n, d_n             rows 0..n-1, or 0..min(n, *d_n)-1 when d_n != NULL
@@ -250,8 +257,11 @@ int64_t tdp_join_default_slots(int64_t n_keys);
  *   table              device uint64[nslots]; this call fills it with the
  *                      empty pattern first
  *
- * A full table (no free slot within min(nslots, 65536) probes) sets
- * TDP_ERR_CAPACITY; a lookup that walks that far sets it too.
+ * A full table (no free slot within min(nslots / 8, 8192) buckets) sets
+ * TDP_ERR_CAPACITY; a lookup that walks that far sets it too.  Argument
+ * errors (nslots not a power of two >= 8, a misaligned table, a key column
+ * that is not int32) are returned as TDP_ERR_INVALID_ARG /
+ * TDP_ERR_UNSUPPORTED_DTYPE before anything runs.
  */
 tdp_status tdp_join_build(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds,
                           int64_t n, const int64_t *d_n, int32_t key_col, int32_t payload_col, uint32_t flags,

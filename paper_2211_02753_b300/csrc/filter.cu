@@ -29,55 +29,6 @@ constexpr int FT_MAX_STEPS = 16;
 constexpr int FT_MIN_TILE = FT_THREADS * 4; // 1024 rows: the workspace is sized for this tile
 constexpr int FT_SMEM_CAP = 64 * 1024;      // predicate bytes of one tile
 
-__device__ __forceinline__ uint32_t ft_smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Mask bits (4 per step) of predicate p, rows read from shared memory.
-template <int STEPS>
-__device__ __forceinline__ void ft_test_smem(const PredSet &ps, int p, const unsigned char *tile_col, int lrow,
-                                             unsigned (&m)[STEPS])
-{
-    const int dt = ps.dt[p];
-    const unsigned neg = (unsigned)ps.neg[p];
-    if (dt == TDP_I64) {
-        const long long lo = ps.lo[p];
-        const unsigned long long span = (unsigned long long)(ps.hi[p] - lo);
-#pragma unroll
-        for (int j = 0; j < STEPS; j++) {
-            const longlong2 *q = (const longlong2 *)(tile_col + (size_t)(lrow + j * 128) * 8);
-            longlong2 a = q[0], b = q[1];
-            unsigned t = range_holds64(a.x, lo, span, neg) | range_holds64(a.y, lo, span, neg) << 1 |
-                         range_holds64(b.x, lo, span, neg) << 2 | range_holds64(b.y, lo, span, neg) << 3;
-            m[j] &= t;
-        }
-        return;
-    }
-    const int lo = (int)ps.lo[p];
-    const unsigned span = (unsigned)((int)ps.hi[p] - lo);
-    if (dt == TDP_I32) {
-#pragma unroll
-        for (int j = 0; j < STEPS; j++) {
-            int4 w = *(const int4 *)(tile_col + (size_t)(lrow + j * 128) * 4);
-            unsigned t = range_holds32(w.x, lo, span, neg) | range_holds32(w.y, lo, span, neg) << 1 |
-                         range_holds32(w.z, lo, span, neg) << 2 | range_holds32(w.w, lo, span, neg) << 3;
-            m[j] &= t;
-        }
-        return;
-    }
-    const bool sgn = dt == TDP_I8;
-#pragma unroll
-    for (int j = 0; j < STEPS; j++) {
-        unsigned w = *(const unsigned *)(tile_col + lrow + j * 128);
-        unsigned t = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            unsigned b = (w >> (8 * k)) & 0xffu;
-            int v = sgn ? (int)(int8_t)b : (int)b;
-            t |= range_holds32(v, lo, span, neg) << k;
-        }
-        m[j] &= t;
-    }
-}
-
 // Same for rows read from global memory (ragged tile or unaligned column).
 template <int STEPS>
 __device__ __forceinline__ void ft_test_global(const PredSet &ps, int p, long long r0, long long n,
@@ -121,21 +72,15 @@ __global__ void __launch_bounds__(FT_THREADS, 3) filter_kernel(PredSet ps, Gathe
     for (int p = 0; p < ps.n; p++)
         bulk = bulk && ps.vec_ok[p];
     if (bulk && threadIdx.x == 0) {
-        const uint32_t bar = ft_smem_u32(&s_bar);
         uint32_t bytes = 0;
         for (int p = 0; p < ps.n; p++)
             bytes += TILE * (uint32_t)dtype_size_dev(ps.dt[p]);
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        mbar_init(&s_bar, 1);
+        mbar_arrive_expect_tx(&s_bar, bytes);
         uint32_t off = 0;
         for (int p = 0; p < ps.n; p++) {
             const uint32_t sz = TILE * (uint32_t)dtype_size_dev(ps.dt[p]);
-            const char *src = (const char *)ps.col[p] + (size_t)rbase * dtype_size_dev(ps.dt[p]);
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                             ft_smem_u32(ft_smem + off)),
-                         "l"(src), "r"(sz), "r"(bar)
-                         : "memory");
+            bulk_load(ft_smem + off, (const char *)ps.col[p] + (size_t)rbase * dtype_size_dev(ps.dt[p]), sz, &s_bar);
             off += sz;
         }
     }
@@ -148,22 +93,12 @@ __global__ void __launch_bounds__(FT_THREADS, 3) filter_kernel(PredSet ps, Gathe
         m[j] = r + 3 < n ? 0xfu : (r + 2 < n ? 0x7u : (r + 1 < n ? 0x3u : (r < n ? 0x1u : 0u)));
     }
     if (bulk) {
-        bool ok = false;
-        for (uint32_t i = 0; i < limit && !ok; i++) {
-            uint32_t done;
-            asm volatile("{\n\t.reg .pred p;\n\t"
-                         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-                         "selp.b32 %0, 1, 0, p;\n\t}"
-                         : "=r"(done)
-                         : "r"(ft_smem_u32(&s_bar))
-                         : "memory");
-            ok = done != 0;
-        }
+        const bool ok = mbar_wait(&s_bar, 0, limit);
         if (!ok)
             set_status(d_status, TDP_ERR_TIMEOUT);
         uint32_t off = 0;
         for (int p = 0; p < ps.n; p++) {
-            ft_test_smem<STEPS>(ps, p, ft_smem + off, lrow, m);
+            pred_test_smem<STEPS>(ps, p, ft_smem + off, lrow, m);
             off += TILE * dtype_size_dev(ps.dt[p]);
         }
     } else {

@@ -1,18 +1,38 @@
 // K6/K7: open-addressing hash equi-join (build, probe, fused probe+group-by).
 //
-// Table: nslots (power of two) 64-bit slots in HBM, slot = (uint32(key) << 32)
-// | payload, empty = all ones (so the pair key = -1, payload = -1 cannot be
-// stored; the build flags it as TDP_ERR_OVERFLOW).  Multiplicative (Fibonacci)
-// hash, linear probing, one 64-bit CAS per insert, probe length bounded by
-// min(nslots, 65536).
+// Table (the caller's nslots x 8 bytes, nslots a power of two >= 8, base
+// 32-byte aligned): two arrays of nslots int32, the keys and then the
+// payloads, entry i of one belonging to entry i of the other.  Keys are
+// grouped in buckets of 8 (32 bytes: one DRAM/L2 sector, one vector load),
+// and so are their payloads.  A key hashes (multiplicative, Fibonacci) to a
+// bucket; a bucket that is full and does not hold the key passes the search
+// on to the next bucket (linear probing over buckets).  An empty key slot
+// holds INT32_MIN, which therefore cannot be stored (the build flags it as
+// TDP_ERR_OVERFLOW).  Insert: one load of the bucket's keys, a 32-bit CAS on
+// its first empty slot (on a lost race the CAS result tells whether the
+// winner holds the same key: a duplicate), then a plain store of the
+// payload.  Lookup: one 32-byte load of the bucket's keys nearly always
+// decides it; the payload bucket is loaded alongside when the caller wants
+// payloads.  The key array stays compact in L2 for key-only probes.  At the
+// default load factor (<= 1/2) a lookup crosses into a second bucket
+// rarely; the walk is bounded by min(nbuckets, 8192) buckets, beyond which
+// TDP_ERR_CAPACITY is reported.
 //
-// Probe: same tile structure as the filter (256 threads x 16 rows, 4 steps of
-// 128 rows per warp, lane = 4 consecutive rows): the probe-side predicates
-// and keys are read with 16-byte loads, the 16 lookups of a thread advance
-// through their collision chains in lock-step rounds (each round issues all
-// outstanding slot loads before examining any, so a thread waits for its
-// longest chain rather than the sum of its chains), and matches are compacted
-// with ballots + decoupled look-back so that the output keeps probe order.
+// Probe (compaction in probe order): one tile of T = 256 x 4 x STEPS probe
+// rows per block, tiles in block order:
+//   1. the tile of every predicate column and of the key column goes to
+//      shared memory (one bulk copy per column for a full aligned tile of a
+//      plain scan, evict-first in L2; plain loads otherwise);
+//   2. predicate mask of lane rows lrow + j*128 + 0..3 (step j);
+//   3. the tile-local indices of qualifying rows form a dense queue (ballot
+//      ranks); every thread resolves queue entries tid, tid + 256, ... eight
+//      at a time (eight bucket loads in flight, table loads evict-last in L2)
+//      and marks found rows in a byte flag per row; found payloads overwrite
+//      their keys in shared memory when the caller wants payloads;
+//   4. ballots over the flags rank the hits; their tile-local indices are
+//      staged at their ranks while warp 0 runs the decoupled look-back for
+//      the tile's output offset;
+//   5. coalesced output: probe row, payload, gathered columns.
 //
 // Probe + aggregate: the build payload is the group key (dense range
 // [lo, hi]); matched rows are added into a per-block shared-memory cache of
@@ -20,37 +40,115 @@
 // groups; groups that find no cache slot go straight to the global dense
 // accumulator table with 64-bit atomics.  Cache contents are merged into the
 // global table at the end, then the non-empty groups are compacted in order.
+#include <algorithm>
+
 #include "filter_api.cuh"
 #include "groupby.cuh"
 
 namespace tdp {
 
-constexpr unsigned long long EMPTY_SLOT = ~0ull;
-// Longest probe sequence walked by a build insert or a lookup.  Linear probing
-// at load <= 1/2 needs a handful of steps; a longer run means a (nearly) full
-// table, which is reported as TDP_ERR_CAPACITY instead of being walked.
-constexpr unsigned long long MAX_PROBE = 1ull << 16;
+constexpr uint32_t EMPTY_KEY = 0x80000000u; // INT32_MIN
+constexpr int BUCKET = 8;                   // key slots per bucket (one sector)
+constexpr unsigned long long MAX_BUCKETS = 1ull << 13;
 
-__device__ __forceinline__ unsigned hash_slot(int key, int lg)
+struct TableView {
+    const uint32_t *keys; // bucket b: keys[8b .. 8b+7]
+    const int32_t *pay;   // and its payloads pay[8b .. 8b+7]
+    unsigned bmask;       // nbuckets - 1
+    int lgb;              // log2(nbuckets)
+    unsigned steps;       // bucket walk bound
+};
+
+__device__ __forceinline__ unsigned bucket_of(int key, int lgb)
 {
-    return ((unsigned)key * 0x9E3779B1u) >> (32 - lg);
+    return lgb == 0 ? 0u : ((unsigned)key * 0x9E3779B1u) >> (32 - lgb);
 }
 
-__global__ void fill_empty_kernel(unsigned long long *table, long long nslots)
+struct Oct {
+    uint32_t v[8];
+};
+
+// 32-byte read-only load with an L2 policy (a bucket of keys or payloads).
+__device__ __forceinline__ Oct load_oct(const uint32_t *p, uint64_t pol)
+{
+    Oct r;
+    asm("ld.global.nc.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+        : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]), "=r"(r.v[6]),
+          "=r"(r.v[7])
+        : "l"(p), "l"(pol));
+    return r;
+}
+
+// Position of the first slot holding `key` (0..7), -1 if an empty slot
+// comes first (the key is absent), -2 if the bucket is full of other keys
+// (the walk goes on).  Slots fill in order and are never freed, so no empty
+// slot precedes a stored key.
+__device__ __forceinline__ int scan_bucket(const Oct &k, uint32_t key)
+{
+    int res = -2;
+#pragma unroll
+    for (int i = BUCKET - 1; i >= 0; i--) {
+        if (k.v[i] == key)
+            res = i;
+        else if (k.v[i] == EMPTY_KEY)
+            res = -1;
+    }
+    return res;
+}
+
+// The payload at position i of a loaded payload bucket (i in 0..7).
+__device__ __forceinline__ int32_t pick(const Oct &p, int i)
+{
+    int32_t r = 0;
+#pragma unroll
+    for (int j = 0; j < BUCKET; j++)
+        r = j == i ? (int32_t)p.v[j] : r;
+    return r;
+}
+
+// Continues a lookup whose first bucket b0 was full of other keys: walks the
+// following buckets.  Returns the slot of the key (>= 0), -1 if absent, -2
+// past the walk bound.
+__device__ __noinline__ long long lookup_tail(const uint32_t *keys, unsigned bmask, unsigned steps, uint32_t key,
+                                              unsigned b0, uint64_t pol)
+{
+    unsigned b = b0;
+    for (unsigned s = 1; s < steps; s++) {
+        b = (b + 1) & bmask;
+        // two 16-byte loads here: ptxas of CUDA 13.0 fails on a 32-byte load
+        // inside a non-inlined function
+        const uint32_t *bk = keys + (size_t)b * BUCKET;
+        Oct k;
+        asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+            : "=r"(k.v[0]), "=r"(k.v[1]), "=r"(k.v[2]), "=r"(k.v[3])
+            : "l"(bk), "l"(pol));
+        asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+            : "=r"(k.v[4]), "=r"(k.v[5]), "=r"(k.v[6]), "=r"(k.v[7])
+            : "l"(bk + 4), "l"(pol));
+        const int r = scan_bucket(k, key);
+        if (r >= 0)
+            return (long long)b * BUCKET + r;
+        if (r == -1)
+            return -1;
+    }
+    return -2;
+}
+
+__global__ void fill_empty_kernel(uint32_t *keys, long long nslots)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i < nslots; i += (long long)gridDim.x * blockDim.x)
-        table[i] = EMPTY_SLOT;
+    const uint4 e = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
+    for (; i < nslots / 4; i += (long long)gridDim.x * blockDim.x)
+        ((uint4 *)keys)[i] = e;
 }
 
 __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, const int32_t *__restrict__ payload,
-                                  long long n, const long long *d_n, unsigned long long *table, int lg,
-                                  int32_t *d_status)
+                                  long long n, const long long *d_n, uint32_t *tkeys, int32_t *tpay, int lgb,
+                                  unsigned steps, int32_t *d_status)
 {
     if (d_n)
         n = min(*d_n, n);
-    const unsigned long long mask = (1ull << lg) - 1;
-    const unsigned long long steps = mask + 1 < MAX_PROBE ? mask + 1 : MAX_PROBE;
+    const unsigned bmask = (1u << lgb) - 1;
     int err = 0;
     // 4 consecutive rows per thread: predicate, key and payload columns are
     // read with vector loads before any insert starts
@@ -61,7 +159,7 @@ __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, c
     if (!m)
         return;
     int k[4];
-    unsigned p[4];
+    int p[4];
     const bool full = r0 + 3 < n && ((uintptr_t)key % 16) == 0 && (!payload || ((uintptr_t)payload % 16) == 0);
     if (full) {
         int4 kk = __ldg((const int4 *)(key + r0));
@@ -74,33 +172,45 @@ __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, c
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             k[e] = (m >> e & 1) ? key[r0 + e] : 0;
-            p[e] = (m >> e & 1) && payload ? (unsigned)payload[r0 + e] : 0u;
+            p[e] = (m >> e & 1) && payload ? payload[r0 + e] : 0;
         }
     }
 #pragma unroll
     for (int e = 0; e < 4; e++) {
         if (!(m >> e & 1))
             continue;
-        unsigned pe = payload ? p[e] : (unsigned)(r0 + e);
-        unsigned long long v = ((unsigned long long)(unsigned)k[e] << 32) | pe;
-        if (v == EMPTY_SLOT) {
+        const uint32_t kv = (uint32_t)k[e];
+        const int pv = payload ? p[e] : (int)(r0 + e);
+        if (kv == EMPTY_KEY) {
             err |= TDP_ERR_OVERFLOW;
             continue;
         }
-        unsigned long long h = hash_slot(k[e], lg);
+        unsigned b = bucket_of(k[e], lgb);
         bool done = false;
-        for (unsigned long long probe = 0; probe < steps; probe++) {
-            unsigned long long prev = atomicCAS(&table[h], EMPTY_SLOT, v);
-            if (prev == EMPTY_SLOT) {
-                done = true;
-                break;
+        for (unsigned s = 0; s < steps && !done; s++, b = (b + 1) & bmask) {
+            uint32_t *bk = tkeys + (size_t)b * BUCKET;
+            const uint4 lo = __ldcg((const uint4 *)bk), hi = __ldcg((const uint4 *)bk + 1);
+            const uint32_t cur[BUCKET] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            // slots are visited in order; a slot passed over holds another key
+            // for good (no deletes), so two inserts of one key meet on one slot
+#pragma unroll
+            for (int i = 0; i < BUCKET; i++) {
+                if (done)
+                    break;
+                uint32_t c = cur[i];
+                if (c == EMPTY_KEY) {
+                    c = atomicCAS(bk + i, EMPTY_KEY, kv);
+                    if (c == EMPTY_KEY) {
+                        tpay[(size_t)b * BUCKET + i] = pv;
+                        done = true;
+                        break;
+                    }
+                }
+                if (c == kv) {
+                    err |= TDP_ERR_DUP_BUILD_KEY;
+                    done = true;
+                }
             }
-            if ((unsigned)(prev >> 32) == (unsigned)k[e]) {
-                err |= TDP_ERR_DUP_BUILD_KEY;
-                done = true;
-                break;
-            }
-            h = (h + 1) & mask;
         }
         if (!done)
             err |= TDP_ERR_CAPACITY;
@@ -110,163 +220,237 @@ __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, c
 }
 
 constexpr int JP_THREADS = 256;
-constexpr int JP_STEPS = 2;
-constexpr int JP_WARP_ROWS = JP_STEPS * 128;
-constexpr int JP_TILE = JP_THREADS / 32 * JP_WARP_ROWS;
-constexpr int JP_ROWS = JP_STEPS * 4; // rows per thread
+constexpr int JP_BATCH = 5;     // key-bucket lookups in flight per thread
+constexpr int JP_BATCH_PAY = 3; // with their payload buckets
 
-// Reads the probe keys of the 16 rows of a thread and resolves them.  idx0:
-// the thread's first index (multiple of 4); row r = j*4 + e is idx0 + j*128 + e
-// (or sel[...] of it).  All unresolved lookups advance together: every round
-// issues the next slot load of each of them before any is examined, so a
-// thread waits for its longest collision chain, not for the sum of its chains.
-// On return bit r of `hit` is set for rows that qualify and match; pay[r] is
-// the payload, key[r] the probe key, row[r] the row id.
-__device__ __forceinline__ unsigned probe16(const unsigned long long *table, int lg, const PredSet &ps,
-                                            const int32_t *keycol, bool key_vec, const int32_t *sel, long long m,
-                                            long long idx0, unsigned (&pay)[JP_ROWS], int (&key)[JP_ROWS],
-                                            int (&row)[JP_ROWS], bool &gave_up)
+template <int STEPS, bool PAY>
+__global__ void __launch_bounds__(JP_THREADS, 3) join_probe_kernel(
+    TableView tv, PredSet ps, const int32_t *__restrict__ key, bool key_vec, long long n, const int32_t *sel,
+    const long long *d_nsel, int32_t *out_row, int32_t *out_payload, GatherSet gs, long long cap, long long *d_count,
+    unsigned long long *tile_status, int32_t *d_status, uint32_t limit, long long num_tiles)
 {
-    unsigned hit = 0;
-#pragma unroll
-    for (int j = 0; j < JP_STEPS; j++)
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            long long i = idx0 + j * 128 + e;
-            row[j * 4 + e] = i < m ? (sel ? sel[i] : (int)i) : -1;
-            hit |= (i < m) ? (1u << (j * 4 + e)) : 0u;
-        }
-    if (ps.n > 0) {
-        if (!sel) {
-            for (int p = 0; p < ps.n; p++) {
-                long long v[JP_STEPS][4];
-                load_rows<JP_STEPS>(ps.col[p], ps.dt[p], ps.vec_ok[p], idx0, m, v);
-#pragma unroll
-                for (int j = 0; j < JP_STEPS; j++)
-#pragma unroll
-                    for (int e = 0; e < 4; e++)
-                        if (!cmp_holds(v[j][e], ps.cmp[p], ps.lit[p]))
-                            hit &= ~(1u << (j * 4 + e));
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < JP_ROWS; r++)
-                if ((hit >> r & 1) && !eval_preds1(ps, row[r]))
-                    hit &= ~(1u << r);
-        }
-    }
-    if (!sel && key_vec && idx0 + (JP_STEPS - 1) * 128 + 3 < m) {
-        int4 w[JP_STEPS];
-#pragma unroll
-        for (int j = 0; j < JP_STEPS; j++)
-            w[j] = __ldg((const int4 *)(keycol + idx0 + j * 128));
-#pragma unroll
-        for (int j = 0; j < JP_STEPS; j++)
-            key[j * 4 + 0] = w[j].x, key[j * 4 + 1] = w[j].y, key[j * 4 + 2] = w[j].z, key[j * 4 + 3] = w[j].w;
-    } else {
-#pragma unroll
-        for (int r = 0; r < JP_ROWS; r++)
-            key[r] = (hit >> r & 1) ? keycol[row[r]] : 0;
-    }
-    const unsigned mask = (unsigned)((1ull << lg) - 1);
-    const unsigned long long steps = (unsigned long long)mask + 1 < MAX_PROBE ? (unsigned long long)mask + 1 : MAX_PROBE;
-    unsigned long long s[JP_ROWS];
-    unsigned h[JP_ROWS];
-    unsigned act = hit;
-#pragma unroll
-    for (int r = 0; r < JP_ROWS; r++) {
-        h[r] = hash_slot(key[r], lg);
-        s[r] = (act >> r & 1) ? __ldg(table + h[r]) : EMPTY_SLOT;
-    }
-    for (unsigned long long round = 0; act && round < steps; round++) {
-#pragma unroll
-        for (int r = 0; r < JP_ROWS; r++) {
-            if (!(act >> r & 1))
-                continue;
-            if (s[r] == EMPTY_SLOT) {
-                act &= ~(1u << r);
-                hit &= ~(1u << r);
-            } else if ((unsigned)(s[r] >> 32) == (unsigned)key[r]) {
-                act &= ~(1u << r);
-                pay[r] = (unsigned)s[r];
-            } else {
-                h[r] = (h[r] + 1) & mask;
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < JP_ROWS; r++)
-            if (act >> r & 1)
-                s[r] = __ldg(table + h[r]);
-    }
-    if (act) { // a chain longer than MAX_PROBE: reported, rows dropped
-        gave_up = true;
-        hit &= ~act;
-    }
-    return hit;
-}
-
-__global__ void __launch_bounds__(JP_THREADS) join_probe_kernel(const unsigned long long *__restrict__ table, int lg,
-                                                                PredSet ps, const int32_t *__restrict__ key,
-                                                                bool key_vec, long long n, const int32_t *sel,
-                                                                const long long *d_nsel, int32_t *out_row,
-                                                                int32_t *out_payload, GatherSet gs, long long cap,
-                                                                long long *d_count, unsigned long long *tile_status,
-                                                                unsigned *ticket, int32_t *d_status, uint32_t limit,
-                                                                long long num_tiles)
-{
-    __shared__ long long s_tile;
-    __shared__ unsigned s_warp_tot[JP_THREADS / 32];
-    __shared__ unsigned s_warp_excl[JP_THREADS / 32];
+    constexpr int T = JP_THREADS * 4 * STEPS;
+    extern __shared__ __align__(128) unsigned char jp_smem[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ unsigned s_warp[JP_THREADS / 32];
     __shared__ unsigned long long s_excl;
-    if (threadIdx.x == 0)
-        s_tile = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const long long tile = s_tile;
+
+    const long long tile = blockIdx.x;
     const long long m = d_nsel ? min(*d_nsel, n) : n;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long idx0 = tile * JP_TILE + (long long)warp * JP_WARP_ROWS + 4 * lane;
+    const long long ibase = tile * T;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lrow = warp * (STEPS * 128) + 4 * lane;
+    uint32_t pbytes = 0;
+    for (int p = 0; p < ps.n; p++)
+        pbytes += T * (uint32_t)dtype_size_dev(ps.dt[p]);
+    const uint32_t kofs = max(pbytes, (uint32_t)T * 4);
+    int32_t *sk = (int32_t *)(jp_smem + kofs);              // keys, then payloads in place
+    uint16_t *queue = (uint16_t *)jp_smem;                  // after the predicates: qualifying rows
+    unsigned char *found = jp_smem + 2 * T;                 // one flag byte per row
+    int32_t *stage = (int32_t *)jp_smem;                    // finally: the hits in output order
+    const uint64_t stream_pol = l2_evict_first(), table_pol = l2_evict_last();
 
-    unsigned pay[JP_ROWS];
-    int keys[JP_ROWS], rows[JP_ROWS];
-    bool gave_up = false;
-    const unsigned hit = probe16(table, lg, ps, key, key_vec, sel, m, idx0, pay, keys, rows, gave_up);
-    if (gave_up)
-        set_status(d_status, TDP_ERR_CAPACITY);
+    // 1. stage the tile
+    bool bulk = !sel && key_vec && ibase + T <= m;
+    for (int p = 0; p < ps.n; p++)
+        bulk = bulk && ps.vec_ok[p];
+    if (bulk) {
+        if (tid == 0) {
+            mbar_init(&s_bar, 1);
+            mbar_arrive_expect_tx(&s_bar, pbytes + T * 4);
+            uint32_t off = 0;
+            for (int p = 0; p < ps.n; p++) {
+                const int sz = dtype_size_dev(ps.dt[p]);
+                bulk_load_hint(jp_smem + off, (const char *)ps.col[p] + (size_t)ibase * sz, T * sz, &s_bar,
+                               stream_pol);
+                off += T * sz;
+            }
+            bulk_load_hint(sk, key + ibase, T * 4, &s_bar, stream_pol);
+        }
+    } else {
+        for (int i = tid; i < T; i += JP_THREADS) {
+            const long long idx = ibase + i;
+            if (idx >= m)
+                continue;
+            const long long row = sel ? sel[idx] : idx;
+            sk[i] = key[row];
+            uint32_t off = 0;
+            for (int p = 0; p < ps.n; p++) {
+                const int sz = dtype_size_dev(ps.dt[p]);
+                const long long v = load_int(ps.col[p], ps.dt[p], row);
+                unsigned char *d = jp_smem + off + (size_t)i * sz;
+                if (sz == 8)
+                    *(long long *)d = v;
+                else if (sz == 4)
+                    *(int32_t *)d = (int32_t)v;
+                else
+                    *d = (unsigned char)v;
+                off += T * sz;
+            }
+        }
+    }
+    __syncthreads();
+    if (bulk && !mbar_wait(&s_bar, 0, limit))
+        set_status(d_status, TDP_ERR_TIMEOUT);
 
-    const unsigned lt = lanemask_lt();
-    unsigned step_cnt[JP_STEPS], lane_pref[JP_STEPS], warp_tot = 0;
+    // 2. predicate mask (rows past the end are never set)
+    unsigned msk[STEPS];
 #pragma unroll
-    for (int j = 0; j < JP_STEPS; j++) {
-        unsigned c = 0, pre = 0;
+    for (int j = 0; j < STEPS; j++) {
+        const long long r = ibase + lrow + j * 128;
+        msk[j] = r + 3 < m ? 0xfu : (r + 2 < m ? 0x7u : (r + 1 < m ? 0x3u : (r < m ? 0x1u : 0u)));
+    }
+    {
+        uint32_t off = 0;
+        for (int p = 0; p < ps.n; p++) {
+            pred_test_smem<STEPS>(ps, p, jp_smem + off, lrow, msk);
+            off += T * dtype_size_dev(ps.dt[p]);
+        }
+    }
+
+    // 3. queue of qualifying rows, then lookups
+    const unsigned lt = lanemask_lt();
+    unsigned rank[STEPS], wtot = 0;
+#pragma unroll
+    for (int j = 0; j < STEPS; j++) {
+        unsigned cnt = 0, pre = 0;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            unsigned b = __ballot_sync(0xffffffffu, (hit >> (j * 4 + e)) & 1u);
-            c += __popc(b);
+            const unsigned b = __ballot_sync(0xffffffffu, (msk[j] >> e) & 1u);
+            cnt += __popc(b);
             pre += __popc(b & lt);
         }
-        step_cnt[j] = c;
-        lane_pref[j] = pre;
-        warp_tot += c;
+        rank[j] = cnt << 16 | pre;
+        wtot += cnt;
     }
     if (lane == 0)
-        s_warp_tot[warp] = warp_tot;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned t = lane < JP_THREADS / 32 ? s_warp_tot[lane] : 0, incl = t;
+        s_warp[warp] = wtot;
+    __syncthreads(); // predicate tiles consumed
+    unsigned qoff = 0, qtot = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o)
-                incl += u;
+    for (int w = 0; w < JP_THREADS / 32; w++) {
+        const unsigned t = s_warp[w];
+        qoff += w < warp ? t : 0;
+        qtot += t;
+    }
+    {
+        unsigned pos = qoff;
+#pragma unroll
+        for (int j = 0; j < STEPS; j++) {
+            unsigned q = pos + (rank[j] & 0xffffu);
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (msk[j] >> e & 1)
+                    queue[q++] = (uint16_t)(lrow + j * 128 + e);
+            pos += rank[j] >> 16;
         }
-        if (lane < JP_THREADS / 32)
-            s_warp_excl[lane] = incl - t;
-        unsigned long long agg = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned long long excl = lookback_exclusive(tile_status, tile, agg, limit, d_status);
+        for (int i = tid; i < T / 4; i += JP_THREADS)
+            ((uint32_t *)found)[i] = 0u;
+    }
+    __syncthreads();
+    constexpr bool want_pay = PAY;
+    // 8 registers per key bucket in flight, 16 with its payload bucket
+    constexpr int NB = PAY ? JP_BATCH_PAY : JP_BATCH;
+    bool gave_up = false;
+    for (unsigned base = 0; base < qtot; base += JP_THREADS * NB) {
+        int li[NB];
+        uint32_t kq[NB];
+        int pv[NB];
+        long long slot[NB]; // slot of the found key, -1 if absent
+        Oct wk[NB], wp[PAY ? NB : 1];
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+            const unsigned q = base + tid + k * JP_THREADS;
+            li[k] = q < qtot ? queue[q] : -1;
+            kq[k] = li[k] >= 0 ? (uint32_t)sk[li[k]] : EMPTY_KEY;
+            if (kq[k] != EMPTY_KEY) {
+                const size_t b8 = (size_t)bucket_of((int)kq[k], tv.lgb) * BUCKET;
+                wk[k] = load_oct(tv.keys + b8, table_pol);
+                if constexpr (PAY)
+                    wp[k] = load_oct((const uint32_t *)tv.pay + b8, table_pol);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+            slot[k] = -1;
+            pv[k] = 0;
+            if (kq[k] == EMPTY_KEY)
+                continue;
+            const unsigned b = bucket_of((int)kq[k], tv.lgb);
+            const int r = scan_bucket(wk[k], kq[k]);
+            if (r >= 0) {
+                slot[k] = (long long)b * BUCKET + r;
+                if constexpr (PAY)
+                    pv[k] = pick(wp[k], r);
+            } else if (r == -2) {
+                const long long t = lookup_tail(tv.keys, tv.bmask, tv.steps, kq[k], b, table_pol);
+                gave_up |= t == -2;
+                if (t >= 0) {
+                    slot[k] = t;
+                    if constexpr (PAY)
+                        pv[k] = tv.pay[t];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NB; k++)
+            if (slot[k] >= 0) {
+                found[li[k]] = 1;
+                if (want_pay)
+                    sk[li[k]] = pv[k];
+            }
+    }
+    if (gave_up)
+        set_status(d_status, TDP_ERR_CAPACITY);
+    __syncthreads();
+
+    // 4. ranks of the hits; staged tile-local indices; look-back
+#pragma unroll
+    for (int j = 0; j < STEPS; j++) {
+        const uint32_t f = *(const uint32_t *)(found + lrow + j * 128);
+        msk[j] = (f & 1u) | (f >> 7 & 2u) | (f >> 14 & 4u) | (f >> 21 & 8u);
+    }
+    unsigned btot = 0, woff = 0;
+    wtot = 0;
+#pragma unroll
+    for (int j = 0; j < STEPS; j++) {
+        unsigned cnt = 0, pre = 0;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const unsigned b = __ballot_sync(0xffffffffu, (msk[j] >> e) & 1u);
+            cnt += __popc(b);
+            pre += __popc(b & lt);
+        }
+        rank[j] = cnt << 16 | pre;
+        wtot += cnt;
+    }
+    if (lane == 0)
+        s_warp[warp] = wtot;
+    __syncthreads(); // queue and flags consumed
+#pragma unroll
+    for (int w = 0; w < JP_THREADS / 32; w++) {
+        const unsigned t = s_warp[w];
+        woff += w < warp ? t : 0;
+        btot += t;
+    }
+    {
+        unsigned pos = woff;
+#pragma unroll
+        for (int j = 0; j < STEPS; j++) {
+            unsigned q = pos + (rank[j] & 0xffffu);
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (msk[j] >> e & 1)
+                    stage[q++] = lrow + j * 128 + e;
+            pos += rank[j] >> 16;
+        }
+    }
+    if (warp == 0) {
+        const unsigned long long e = lookback_exclusive(tile_status, tile, btot, limit, d_status);
         if (lane == 0) {
-            s_excl = excl;
+            s_excl = e;
             if (tile == num_tiles - 1) {
-                long long total = (long long)(excl + agg);
+                const long long total = (long long)(e + btot);
                 *d_count = total;
                 if (total > cap)
                     set_status(d_status, TDP_ERR_CAPACITY);
@@ -274,81 +458,148 @@ __global__ void __launch_bounds__(JP_THREADS) join_probe_kernel(const unsigned l
         }
     }
     __syncthreads();
-    // output slot of every hit (rows of a step land at consecutive slots)
-    long long outp[JP_ROWS];
-    {
-        long long pos = (long long)s_excl + s_warp_excl[warp];
-#pragma unroll
-        for (int j = 0; j < JP_STEPS; j++) {
-            long long p = pos + lane_pref[j];
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                outp[j * 4 + e] = p;
-                p += (hit >> (j * 4 + e)) & 1;
-            }
-            pos += step_cnt[j];
+
+    // 5. output
+    const long long excl = (long long)s_excl;
+    const unsigned lim = (unsigned)max(0ll, min((long long)btot, cap - excl));
+    if (out_row || out_payload)
+        for (unsigned i = tid; i < lim; i += JP_THREADS) {
+            const int l = stage[i];
+            if (out_row)
+                out_row[excl + i] = sel ? sel[ibase + l] : (int32_t)(ibase + l);
+            if (out_payload)
+                out_payload[excl + i] = sk[l];
         }
-    }
-    const unsigned wr = hit; // rows written (subject to capacity)
-#pragma unroll
-    for (int r = 0; r < JP_ROWS; r++) {
-        if (!(wr >> r & 1) || outp[r] >= cap)
-            continue;
-        if (out_row)
-            out_row[outp[r]] = rows[r];
-        if (out_payload)
-            out_payload[outp[r]] = (int32_t)pay[r];
-    }
-    // gathers: all loads of a column are issued before its stores
     for (int g = 0; g < gs.n; g++) {
         const void *col = gs.col[g];
         void *out = gs.out[g];
-        if (col == (const void *)key) { // the probe key is already in a register
-#pragma unroll
-            for (int r = 0; r < JP_ROWS; r++)
-                if ((wr >> r & 1) && outp[r] < cap)
-                    ((int *)out)[outp[r]] = keys[r];
+        if (col == (const void *)key && !PAY) { // the probe key is still in shared memory
+            for (unsigned i = tid; i < lim; i += JP_THREADS)
+                ((int32_t *)out)[excl + i] = sk[stage[i]];
             continue;
         }
-        if (gs.size[g] == 8) {
-            long long v[JP_ROWS];
-#pragma unroll
-            for (int r = 0; r < JP_ROWS; r++)
-                v[r] = (wr >> r & 1) ? __ldg((const long long *)col + rows[r]) : 0;
-#pragma unroll
-            for (int r = 0; r < JP_ROWS; r++)
-                if ((wr >> r & 1) && outp[r] < cap)
-                    ((long long *)out)[outp[r]] = v[r];
-        } else if (gs.size[g] == 4) {
-            int v[JP_ROWS];
-#pragma unroll
-            for (int r = 0; r < JP_ROWS; r++)
-                v[r] = (wr >> r & 1) ? __ldg((const int *)col + rows[r]) : 0;
-#pragma unroll
-            for (int r = 0; r < JP_ROWS; r++)
-                if ((wr >> r & 1) && outp[r] < cap)
-                    ((int *)out)[outp[r]] = v[r];
-        } else {
-#pragma unroll
-            for (int r = 0; r < JP_ROWS; r++) {
-                if (!(wr >> r & 1) || outp[r] >= cap)
-                    continue;
-                if (gs.size[g] == 2)
-                    ((uint16_t *)out)[outp[r]] = ((const uint16_t *)col)[rows[r]];
-                else
-                    ((uint8_t *)out)[outp[r]] = ((const uint8_t *)col)[rows[r]];
+        switch (gs.size[g]) {
+        case 8:
+#pragma unroll 4
+            for (unsigned i = tid; i < lim; i += JP_THREADS) {
+                const long long row = sel ? sel[ibase + stage[i]] : ibase + stage[i];
+                ((long long *)out)[excl + i] = ldg_hint((const long long *)col + row, stream_pol);
             }
+            break;
+        case 4:
+#pragma unroll 4
+            for (unsigned i = tid; i < lim; i += JP_THREADS) {
+                const long long row = sel ? sel[ibase + stage[i]] : ibase + stage[i];
+                ((int32_t *)out)[excl + i] = ldg_hint((const int32_t *)col + row, stream_pol);
+            }
+            break;
+        case 2:
+            for (unsigned i = tid; i < lim; i += JP_THREADS) {
+                const long long row = sel ? sel[ibase + stage[i]] : ibase + stage[i];
+                ((uint16_t *)out)[excl + i] = ((const uint16_t *)col)[row];
+            }
+            break;
+        default:
+            for (unsigned i = tid; i < lim; i += JP_THREADS) {
+                const long long row = sel ? sel[ibase + stage[i]] : ibase + stage[i];
+                ((uint8_t *)out)[excl + i] = ((const uint8_t *)col)[row];
+            }
+            break;
         }
     }
 }
 
 // ------------------------------------------------------- probe + aggregate
 
+constexpr int GJ_STEPS = 2;
+constexpr int GJ_WARP_ROWS = GJ_STEPS * 128;
+constexpr int GJ_TILE = JP_THREADS / 32 * GJ_WARP_ROWS;
+constexpr int GJ_ROWS = GJ_STEPS * 4; // rows per thread
+
+// The 8 rows idx0 + j*128 + e (j < 2, e < 4) of a thread: predicates, keys
+// (vector loads), eight bucket loads in flight, then the payloads of the
+// found keys.  Bit r = j*4 + e of the result is set for rows that qualify
+// and match; pay[r] is their payload.
+__device__ __forceinline__ unsigned probe_rows8(const TableView &tv, const PredSet &ps, const int32_t *keycol,
+                                                bool key_vec, long long n, long long idx0, int (&pay)[GJ_ROWS],
+                                                bool &gave_up)
+{
+    unsigned hit = 0;
+#pragma unroll
+    for (int j = 0; j < GJ_STEPS; j++)
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            hit |= (idx0 + j * 128 + e < n) ? (1u << (j * 4 + e)) : 0u;
+    for (int p = 0; p < ps.n; p++) {
+        long long v[GJ_STEPS][4];
+        load_rows<GJ_STEPS>(ps.col[p], ps.dt[p], ps.vec_ok[p], idx0, n, v);
+#pragma unroll
+        for (int j = 0; j < GJ_STEPS; j++)
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (!cmp_holds(v[j][e], ps.cmp[p], ps.lit[p]))
+                    hit &= ~(1u << (j * 4 + e));
+    }
+    uint32_t key[GJ_ROWS];
+    if (key_vec && idx0 + (GJ_STEPS - 1) * 128 + 3 < n) {
+        int4 w[GJ_STEPS];
+#pragma unroll
+        for (int j = 0; j < GJ_STEPS; j++)
+            w[j] = __ldg((const int4 *)(keycol + idx0 + j * 128));
+#pragma unroll
+        for (int j = 0; j < GJ_STEPS; j++) {
+            key[j * 4 + 0] = (uint32_t)w[j].x, key[j * 4 + 1] = (uint32_t)w[j].y;
+            key[j * 4 + 2] = (uint32_t)w[j].z, key[j * 4 + 3] = (uint32_t)w[j].w;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < GJ_ROWS; r++)
+            key[r] = (hit >> r & 1) ? (uint32_t)keycol[idx0 + (r / 4) * 128 + r % 4] : EMPTY_KEY;
+    }
+    const uint64_t pol = l2_evict_last();
+#pragma unroll
+    for (int r = 0; r < GJ_ROWS; r++)
+        if (key[r] == EMPTY_KEY)
+            hit &= ~(1u << r);
+    // two halves of 4 rows: a key bucket and its payload bucket in flight per row
+#pragma unroll
+    for (int h = 0; h < GJ_ROWS; h += 4) {
+        Oct wk[4], wp[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            if (hit >> (h + r) & 1) {
+                const size_t b8 = (size_t)bucket_of((int)key[h + r], tv.lgb) * BUCKET;
+                wk[r] = load_oct(tv.keys + b8, pol);
+                wp[r] = load_oct((const uint32_t *)tv.pay + b8, pol);
+            }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            pay[h + r] = 0;
+            if (!(hit >> (h + r) & 1))
+                continue;
+            const int i = scan_bucket(wk[r], key[h + r]);
+            if (i >= 0) {
+                pay[h + r] = pick(wp[r], i);
+                continue;
+            }
+            long long t = -1;
+            if (i == -2) {
+                t = lookup_tail(tv.keys, tv.bmask, tv.steps, key[h + r], bucket_of((int)key[h + r], tv.lgb), pol);
+                gave_up |= t == -2;
+            }
+            if (t >= 0)
+                pay[h + r] = tv.pay[t];
+            else
+                hit &= ~(1u << (h + r));
+        }
+    }
+    return hit;
+}
+
 constexpr int GJ_CACHE = 2048;
 constexpr int GJ_PROBES = 8;
 
-__global__ void __launch_bounds__(JP_THREADS) join_probe_agg_kernel(const unsigned long long *__restrict__ table,
-                                                                    int lg, PredSet ps,
+__global__ void __launch_bounds__(JP_THREADS) join_probe_agg_kernel(TableView tv, PredSet ps,
                                                                     const int32_t *__restrict__ key, bool key_vec,
                                                                     long long n, const long long *d_n,
                                                                     long long lo, long long D, AggSet as,
@@ -378,18 +629,17 @@ __global__ void __launch_bounds__(JP_THREADS) join_probe_agg_kernel(const unsign
     }
     __syncthreads();
     bool bad = false;
-    const long long stride = (long long)gridDim.x * JP_TILE;
-    for (long long base = (long long)blockIdx.x * JP_TILE; base < n; base += stride) {
+    const long long stride = (long long)gridDim.x * GJ_TILE;
+    for (long long base = (long long)blockIdx.x * GJ_TILE; base < n; base += stride) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const long long idx0 = base + (long long)warp * JP_WARP_ROWS + 4 * lane;
-        unsigned pay[JP_ROWS];
-        int keys[JP_ROWS], rows[JP_ROWS];
+        const long long idx0 = base + (long long)warp * GJ_WARP_ROWS + 4 * lane;
+        int pay[GJ_ROWS];
         bool gave_up = false;
-        const unsigned hit = probe16(table, lg, ps, key, key_vec, nullptr, n, idx0, pay, keys, rows, gave_up);
+        const unsigned hit = probe_rows8(tv, ps, key, key_vec, n, idx0, pay, gave_up);
         if (gave_up)
             set_status(d_status, TDP_ERR_CAPACITY);
 #pragma unroll
-        for (int j = 0; j < JP_STEPS; j++) {
+        for (int j = 0; j < GJ_STEPS; j++) {
             unsigned hj = (hit >> (4 * j)) & 0xfu;
             if (!hj)
                 continue;
@@ -455,15 +705,69 @@ __global__ void __launch_bounds__(JP_THREADS) join_probe_agg_kernel(const unsign
     }
 }
 
-static int log2_slots(long long nslots)
+
+static int log2_of(long long x)
 {
     int lg = 0;
-    while ((1ll << lg) < nslots)
+    while ((1ll << lg) < x)
         lg++;
     return lg;
 }
 
-static bool pow2_ok(long long nslots) { return nslots >= 2 && nslots <= (1ll << 32) && (nslots & (nslots - 1)) == 0; }
+// nslots: a power of two in [8, 2^32]; the table 32-byte aligned (one
+// bucket per sector)
+static bool table_ok(const void *table, long long nslots)
+{
+    return nslots >= 8 && nslots <= (1ll << 32) && (nslots & (nslots - 1)) == 0 && ((uintptr_t)table % 32) == 0;
+}
+
+static TableView table_view(const uint64_t *table, long long nslots)
+{
+    TableView tv;
+    tv.keys = (const uint32_t *)table;
+    tv.pay = (const int32_t *)table + nslots;
+    const long long nb = nslots / BUCKET;
+    tv.lgb = log2_of(nb);
+    tv.bmask = (unsigned)(nb - 1);
+    tv.steps = (unsigned)std::min<unsigned long long>((unsigned long long)nb, MAX_BUCKETS);
+    return tv;
+}
+
+// Rows per probe tile: shared memory max(P, 4T) + 4T <= 64 KiB, P = T x the
+// predicate bytes of a row.
+static int probe_steps(const PredSet &ps)
+{
+    int row_bytes = 0;
+    for (int p = 0; p < ps.n; p++)
+        row_bytes += dtype_size(ps.dt[p]);
+    int steps = 8;
+    while (steps > 1 && (size_t)JP_THREADS * 4 * steps * (std::max(row_bytes, 4) + 4) > 64 * 1024)
+        steps >>= 1;
+    return steps;
+}
+
+template <int STEPS>
+static tdp_status launch_probe(const TableView &tv, const PredSet &ps, const int32_t *key, long long n,
+                               const int32_t *sel, const long long *d_nsel, int32_t *out_row, int32_t *out_payload,
+                               const GatherSet &gs, long long cap, long long *d_count, void *ws, int32_t *d_status,
+                               cudaStream_t s)
+{
+    constexpr long long T = JP_THREADS * 4 * STEPS;
+    const long long tiles = (n + T - 1) / T;
+    size_t pbytes = 0;
+    for (int p = 0; p < ps.n; p++)
+        pbytes += (size_t)T * dtype_size(ps.dt[p]);
+    const size_t smem = std::max(pbytes, (size_t)T * 4) + (size_t)T * 4;
+    auto kern = out_payload ? join_probe_kernel<STEPS, true> : join_probe_kernel<STEPS, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TDP_ERR_CUDA;
+    unsigned long long *status = (unsigned long long *)((char *)ws + 16);
+    cudaMemsetAsync(status, 0, (size_t)tiles * 8, s);
+    kern<<<(unsigned)tiles, JP_THREADS, smem, s>>>(tv, ps, key, ((uintptr_t)key % 16) == 0, n, sel, d_nsel, out_row,
+                                                    out_payload, gs, cap, d_count, status, d_status, spin_limit(),
+                                                    tiles);
+    return launch_status();
+}
 
 } // namespace tdp
 
@@ -471,7 +775,7 @@ using namespace tdp;
 
 extern "C" int64_t tdp_join_default_slots(int64_t n_keys)
 {
-    long long s = 2;
+    long long s = 8;
     while (s < 2 * n_keys)
         s <<= 1;
     return s;
@@ -482,8 +786,8 @@ extern "C" tdp_status tdp_join_build(const tdp_col *cols, int32_t ncols, const t
                                      uint64_t *table, int64_t nslots, int32_t *d_status, tdp_stream_t stream)
 {
     (void)flags;
-    if (n < 0 || n >= (1ll << 31) || !cols || !table || !pow2_ok(nslots) || key_col < 0 || key_col >= ncols ||
-        payload_col >= ncols)
+    if (n < 0 || n >= (1ll << 31) || !cols || !table || !table_ok(table, nslots) || key_col < 0 ||
+        key_col >= ncols || payload_col >= ncols)
         return TDP_ERR_INVALID_ARG;
     if (cols[key_col].dtype != TDP_I32 || (payload_col >= 0 && cols[payload_col].dtype != TDP_I32))
         return TDP_ERR_UNSUPPORTED_DTYPE;
@@ -494,22 +798,24 @@ extern "C" tdp_status tdp_join_build(const tdp_col *cols, int32_t ncols, const t
     if (st != TDP_OK)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
-    fill_empty_kernel<<<(unsigned)std::min<long long>((nslots + 255) / 256, (long long)num_sms() * 8), 256, 0, s>>>(
-        (unsigned long long *)table, nslots);
+    const TableView tv = table_view(table, nslots);
+    fill_empty_kernel<<<(unsigned)std::min<long long>((nslots / 4 + 255) / 256, (long long)num_sms() * 8), 256, 0,
+                        s>>>((uint32_t *)table, nslots);
     if (n > 0) {
         // one thread per 4 rows (the kernel is not grid-strided)
         unsigned grid = (unsigned)((n + 1023) / 1024);
         join_build_kernel<<<grid, 256, 0, s>>>(ps, (const int32_t *)cols[key_col].data,
                                                payload_col >= 0 ? (const int32_t *)cols[payload_col].data : nullptr,
-                                               n, (const long long *)d_n, (unsigned long long *)table,
-                                               log2_slots(nslots), d_status);
+                                               n, (const long long *)d_n, (uint32_t *)table,
+                                               (int32_t *)table + nslots, tv.lgb, tv.steps, d_status);
     }
     return launch_status();
 }
 
 extern "C" size_t tdp_join_probe_workspace(int64_t n)
 {
-    long long tiles = (n + JP_TILE - 1) / JP_TILE;
+    // one look-back word per tile, sized for the smallest tile (1024 rows)
+    long long tiles = (n + JP_THREADS * 4 - 1) / (JP_THREADS * 4);
     return align_up(16 + (size_t)tiles * 8, 256);
 }
 
@@ -520,8 +826,8 @@ extern "C" tdp_status tdp_join_probe(const uint64_t *table, int64_t nslots, cons
                                      void *const *gather_out, int64_t capacity, int64_t *d_count, void *ws,
                                      size_t ws_bytes, int32_t *d_status, tdp_stream_t stream)
 {
-    if (n < 0 || n >= (1ll << 31) || !cols || !table || !pow2_ok(nslots) || key_col < 0 || key_col >= ncols ||
-        !d_count || capacity < 0 || (sel && !d_nsel))
+    if (n < 0 || n >= (1ll << 31) || !cols || !table || !table_ok(table, nslots) || key_col < 0 ||
+        key_col >= ncols || !d_count || capacity < 0 || (sel && !d_nsel))
         return TDP_ERR_INVALID_ARG;
     if (cols[key_col].dtype != TDP_I32)
         return TDP_ERR_UNSUPPORTED_DTYPE;
@@ -542,14 +848,20 @@ extern "C" tdp_status tdp_join_probe(const uint64_t *table, int64_t nslots, cons
     }
     if (!ws || ws_bytes < tdp_join_probe_workspace(n))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
-    long long tiles = (n + JP_TILE - 1) / JP_TILE;
-    cudaMemsetAsync(ws, 0, 16 + (size_t)tiles * 8, s);
+    const TableView tv = table_view(table, nslots);
     const int32_t *key = (const int32_t *)cols[key_col].data;
-    join_probe_kernel<<<(unsigned)tiles, JP_THREADS, 0, s>>>(
-        (const unsigned long long *)table, log2_slots(nslots), ps, key, ((uintptr_t)key % 16) == 0, n, sel,
-        (const long long *)d_nsel, out_probe_row, out_payload, gs, capacity, (long long *)d_count,
-        (unsigned long long *)((char *)ws + 16), (unsigned *)ws, d_status, spin_limit(), tiles);
-    return launch_status();
+    const long long *dn = (const long long *)d_nsel;
+    long long *dc = (long long *)d_count;
+    switch (probe_steps(ps)) {
+    case 8: return launch_probe<8>(tv, ps, key, n, sel, dn, out_probe_row, out_payload, gs, capacity, dc, ws,
+                                   d_status, s);
+    case 4: return launch_probe<4>(tv, ps, key, n, sel, dn, out_probe_row, out_payload, gs, capacity, dc, ws,
+                                   d_status, s);
+    case 2: return launch_probe<2>(tv, ps, key, n, sel, dn, out_probe_row, out_payload, gs, capacity, dc, ws,
+                                   d_status, s);
+    default: return launch_probe<1>(tv, ps, key, n, sel, dn, out_probe_row, out_payload, gs, capacity, dc, ws,
+                                    d_status, s);
+    }
 }
 
 extern "C" size_t tdp_join_workspace(int64_t n_build, int64_t n_probe, int64_t nslots)
@@ -597,7 +909,7 @@ extern "C" tdp_status tdp_join_probe_agg(const uint64_t *table, int64_t nslots, 
                                          int64_t *d_ngroups, void *ws, size_t ws_bytes, int32_t *d_status,
                                          tdp_stream_t stream)
 {
-    if (n < 0 || n >= (1ll << 31) || !cols || !table || !pow2_ok(nslots) || key_col < 0 || key_col >= ncols ||
+    if (n < 0 || n >= (1ll << 31) || !cols || !table || !table_ok(table, nslots) || key_col < 0 || key_col >= ncols ||
         !d_ngroups || capacity < 0 || payload_hi < payload_lo || payload_hi - payload_lo >= (1ll << 31) ||
         !out_aggs || (capacity > 0 && !out_keys))
         return TDP_ERR_INVALID_ARG;
@@ -626,10 +938,10 @@ extern "C" tdp_status tdp_join_probe_agg(const uint64_t *table, int64_t nslots, 
             cudaSuccess)
             return TDP_ERR_CUDA;
         int per_sm = std::max(1, std::min(4, (int)((200 * 1024) / smem)));
-        long long want = (n + JP_TILE - 1) / JP_TILE;
+        long long want = (n + GJ_TILE - 1) / GJ_TILE;
         unsigned grid = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() * per_sm));
         const int32_t *key = (const int32_t *)cols[key_col].data;
-        join_probe_agg_kernel<<<grid, JP_THREADS, smem, s>>>((const unsigned long long *)table, log2_slots(nslots), ps,
+        join_probe_agg_kernel<<<grid, JP_THREADS, smem, s>>>(table_view(table, nslots), ps,
                                                             key, ((uintptr_t)key % 16) == 0, n,
                                                             (const long long *)d_n, payload_lo, D, as, acc, d_status);
     }

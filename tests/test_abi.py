@@ -32,10 +32,11 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 def test_host_only_calls():
     L = _lib.lib()
-    assert L.tdp_abi_version() == 100
+    assert L.tdp_abi_version() == 101
     assert L.tdp_status_str(4) == b"capacity exceeded"
     assert L.tdp_filter_workspace(0) >= 0
     assert L.tdp_join_default_slots(3_000_000) == 1 << 23
+    assert L.tdp_join_default_slots(0) == 8 and L.tdp_join_default_slots(5) == 16
     old = L.tdp_set_spin_limit(1000)
     assert L.tdp_set_spin_limit(old) == 1000
 

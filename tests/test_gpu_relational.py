@@ -302,6 +302,43 @@ def test_join_matches_oracle(nb, np_rows):
     assert np.array_equal(np_(out2["payload"], c2), ob2)
 
 
+@pytest.mark.parametrize("nb,nslots", [(1000, 2048), (1000, 1024), (4000, 4096), (7, 8)])
+def test_join_crowded_tables_walk_past_full_buckets(nb, nslots):
+    """Load factors up to 1 (every bucket full): lookups continue into the
+    following buckets, hits and misses both, including the wrap-around from
+    the last bucket to the first."""
+    r = np.random.default_rng(nslots + nb)
+    bkey = r.choice(np.arange(-10**6, 10**6, dtype=np.int32), nb, replace=False)
+    bpay = r.integers(-10**6, 10**6, nb).astype(np.int32)
+    pkey = np.concatenate([bkey, r.integers(-10**6, 10**6, 3 * nb).astype(np.int32)])
+    r.shuffle(pkey)
+    table, st = ops.join_build([cu(bkey), cu(bpay)], 0, payload_col=1, nslots=nslots)
+    out = ops.join_probe(table, [cu(pkey)], 0, gather=[0], status=st)
+    ops.check(st)
+    op_, ob_, dup = R.join(bkey, pkey)
+    assert not dup
+    c = int(out["count"].item())
+    assert c == len(op_)
+    assert np.array_equal(np_(out["probe_row"], c), op_)
+    assert np.array_equal(np_(out["payload"], c), bpay[ob_])
+    assert np.array_equal(np_(out["gathered"][0], c), pkey[op_])
+
+
+def test_join_int32_min_key_is_flagged_and_never_found():
+    imin = np.iinfo(np.int32).min
+    bkey = np.array([3, imin, 5], np.int32)
+    table, st = ops.join_build([cu(bkey)], 0)
+    assert int(st.item()) == 32  # TDP_ERR_OVERFLOW only
+    pkey = np.array([imin, 5, 3, imin, 4], np.int32)
+    st2 = ops.new_status(DEV)
+    out = ops.join_probe(table, [cu(pkey)], 0, status=st2)
+    ops.check(st2)
+    c = int(out["count"].item())
+    assert c == 2
+    assert np.array_equal(np_(out["probe_row"], c), [1, 2])
+    assert np.array_equal(np_(out["payload"], c), [2, 0])
+
+
 def test_join_duplicate_keys_and_full_table_are_flagged():
     bkey = cu(np.array([5, 7, 5, 9], np.int32))
     table, st = ops.join_build([bkey], 0)

@@ -351,6 +351,15 @@ __device__ __forceinline__ int32_t ldg_hint(const int32_t *p, uint64_t policy)
     return v;
 }
 
+__device__ __forceinline__ uint4 ldg16_hint(const uint32_t *p, uint64_t policy)
+{
+    uint4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(policy));
+    return v;
+}
+
 // Bounded wait for the phase of the given parity; false when it ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
 {

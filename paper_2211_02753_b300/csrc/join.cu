@@ -35,7 +35,10 @@
 //   5. coalesced output: probe row, payload, gathered columns.
 //
 // Probe + aggregate: the build payload is the group key (dense range
-// [lo, hi]); matched rows are added into a per-block shared-memory cache of
+// [lo, hi]).  Persistent blocks take tiles of probe rows in grid-stride
+// order, the staged columns of the next tile arriving by bulk copy while the
+// current one is processed; matched rows are added into a per-block
+// shared-memory cache of
 // 2048 groups (open addressing on the group id), which absorbs Zipf-hot
 // groups; groups that find no cache slot go straight to the global dense
 // accumulator table with 64-bit atomics.  Cache contents are merged into the
@@ -511,200 +514,255 @@ __global__ void __launch_bounds__(JP_THREADS, 3) join_probe_kernel(
 
 // ------------------------------------------------------- probe + aggregate
 
-constexpr int GJ_STEPS = 2;
-constexpr int GJ_WARP_ROWS = GJ_STEPS * 128;
-constexpr int GJ_TILE = JP_THREADS / 32 * GJ_WARP_ROWS;
-constexpr int GJ_ROWS = GJ_STEPS * 4; // rows per thread
-
-// The 8 rows idx0 + j*128 + e (j < 2, e < 4) of a thread: predicates, keys
-// (vector loads), eight bucket loads in flight, then the payloads of the
-// found keys.  Bit r = j*4 + e of the result is set for rows that qualify
-// and match; pay[r] is their payload.
-__device__ __forceinline__ unsigned probe_rows8(const TableView &tv, const PredSet &ps, const int32_t *keycol,
-                                                bool key_vec, long long n, long long idx0, int (&pay)[GJ_ROWS],
-                                                bool &gave_up)
-{
-    unsigned hit = 0;
-#pragma unroll
-    for (int j = 0; j < GJ_STEPS; j++)
-#pragma unroll
-        for (int e = 0; e < 4; e++)
-            hit |= (idx0 + j * 128 + e < n) ? (1u << (j * 4 + e)) : 0u;
-    for (int p = 0; p < ps.n; p++) {
-        long long v[GJ_STEPS][4];
-        load_rows<GJ_STEPS>(ps.col[p], ps.dt[p], ps.vec_ok[p], idx0, n, v);
-#pragma unroll
-        for (int j = 0; j < GJ_STEPS; j++)
-#pragma unroll
-            for (int e = 0; e < 4; e++)
-                if (!cmp_holds(v[j][e], ps.cmp[p], ps.lit[p]))
-                    hit &= ~(1u << (j * 4 + e));
-    }
-    uint32_t key[GJ_ROWS];
-    if (key_vec && idx0 + (GJ_STEPS - 1) * 128 + 3 < n) {
-        int4 w[GJ_STEPS];
-#pragma unroll
-        for (int j = 0; j < GJ_STEPS; j++)
-            w[j] = __ldg((const int4 *)(keycol + idx0 + j * 128));
-#pragma unroll
-        for (int j = 0; j < GJ_STEPS; j++) {
-            key[j * 4 + 0] = (uint32_t)w[j].x, key[j * 4 + 1] = (uint32_t)w[j].y;
-            key[j * 4 + 2] = (uint32_t)w[j].z, key[j * 4 + 3] = (uint32_t)w[j].w;
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < GJ_ROWS; r++)
-            key[r] = (hit >> r & 1) ? (uint32_t)keycol[idx0 + (r / 4) * 128 + r % 4] : EMPTY_KEY;
-    }
-    const uint64_t pol = l2_evict_last();
-#pragma unroll
-    for (int r = 0; r < GJ_ROWS; r++)
-        if (key[r] == EMPTY_KEY)
-            hit &= ~(1u << r);
-    // two halves of 4 rows: a key bucket and its payload bucket in flight per row
-#pragma unroll
-    for (int h = 0; h < GJ_ROWS; h += 4) {
-        Oct wk[4], wp[4];
-#pragma unroll
-        for (int r = 0; r < 4; r++)
-            if (hit >> (h + r) & 1) {
-                const size_t b8 = (size_t)bucket_of((int)key[h + r], tv.lgb) * BUCKET;
-                wk[r] = load_oct(tv.keys + b8, pol);
-                wp[r] = load_oct((const uint32_t *)tv.pay + b8, pol);
-            }
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            pay[h + r] = 0;
-            if (!(hit >> (h + r) & 1))
-                continue;
-            const int i = scan_bucket(wk[r], key[h + r]);
-            if (i >= 0) {
-                pay[h + r] = pick(wp[r], i);
-                continue;
-            }
-            long long t = -1;
-            if (i == -2) {
-                t = lookup_tail(tv.keys, tv.bmask, tv.steps, key[h + r], bucket_of((int)key[h + r], tv.lgb), pol);
-                gave_up |= t == -2;
-            }
-            if (t >= 0)
-                pay[h + r] = tv.pay[t];
-            else
-                hit &= ~(1u << (h + r));
-        }
-    }
-    return hit;
-}
-
 constexpr int GJ_CACHE = 2048;
 constexpr int GJ_PROBES = 8;
+constexpr int GJ_MAX_STAGE = 16; // distinct columns staged per tile
 
-__global__ void __launch_bounds__(JP_THREADS) join_probe_agg_kernel(TableView tv, PredSet ps,
-                                                                    const int32_t *__restrict__ key, bool key_vec,
-                                                                    long long n, const long long *d_n,
-                                                                    long long lo, long long D, AggSet as,
-                                                                    long long *gacc, int32_t *d_status)
+// The columns a group-join tile stages in shared memory (key, predicate and
+// aggregate columns, each once), and where every use finds its column.
+struct GJStage {
+    const void *col[GJ_MAX_STAGE];
+    int32_t size[GJ_MAX_STAGE];
+    int32_t n;
+    int32_t aligned;                 // every staged column 16-byte aligned
+    int32_t key;                     // stage index of the probe key
+    int32_t pred[TDP_MAX_PREDS];     // stage index of predicate p's column
+    int32_t sa[TDP_MAX_AGGS + 1];    // stage index of slot s's a column (-1: none)
+    int32_t sb[TDP_MAX_AGGS + 1];    // and of its b column
+};
+
+__device__ __forceinline__ long long stage_val(const unsigned char *col, int size, int dt, int li)
 {
-    if (d_n)
-        n = min(*d_n, n);
-    extern __shared__ long long gj_smem[];
+    switch (dt) {
+    case TDP_I8: return ((const int8_t *)col)[li];
+    case TDP_U8: return ((const uint8_t *)col)[li];
+    case TDP_I32: return ((const int32_t *)col)[li];
+    default: return size == 8 ? ((const long long *)col)[li] : ((const int32_t *)col)[li];
+    }
+}
+
+// Finds (or claims) the cache entry of group gid; nullptr when the probe
+// sequence of the cache is full.
+__device__ __forceinline__ long long *gj_cache_slot(unsigned *s_key, long long *s_acc, int NS, long long gid)
+{
+    const unsigned tag = (unsigned)gid + 1u;
+    unsigned h = ((unsigned)gid * 0x9E3779B1u) >> 21; // 11 bits: GJ_CACHE = 2048
+    for (int q = 0; q < GJ_PROBES; q++) {
+        unsigned cur = s_key[h];
+        if (cur == 0)
+            cur = atomicCAS(&s_key[h], 0u, tag);
+        if (cur == 0 || cur == tag)
+            return s_acc + h * NS;
+        h = (h + 1) & (GJ_CACHE - 1);
+    }
+    return nullptr;
+}
+
+// Persistent group-join: tiles of T = 256 x RPT probe rows in grid-stride
+// order.  Thread 0 bulk-copies the staged columns of the block's next tile
+// into the other of two shared buffers while the block works on the current
+// one (a ragged or unaligned tile is loaded by all threads instead).  Row
+// li = tid + k*256 of the tile (k < RPT) is looked up in batches of 4: the
+// first half of its key bucket and of its payload bucket are loaded
+// together, so one round trip resolves keys in the first four slots; the
+// second half, and then the following buckets, are read only when needed.
+template <int RPT>
+__global__ void __launch_bounds__(JP_THREADS, 3) join_probe_agg_kernel(TableView tv, PredSet ps, GJStage sg,
+                                                                       long long n_host, const long long *d_n,
+                                                                       long long lo, long long D, AggSet as,
+                                                                       long long *gacc, int32_t *d_status,
+                                                                       uint32_t limit)
+{
+    constexpr int T = JP_THREADS * RPT;
+    const long long n = d_n ? min(*d_n, n_host) : n_host;
+    extern __shared__ __align__(128) long long gj_smem[];
     const int NS = as.nslots;
-    long long *s_acc = gj_smem;                               // [GJ_CACHE][NS]
-    unsigned *s_key = (unsigned *)(gj_smem + GJ_CACHE * NS);  // [GJ_CACHE], gid + 1, 0 = empty
+    long long *s_acc = gj_smem;                                   // [GJ_CACHE][NS]
+    unsigned *s_key = (unsigned *)(gj_smem + GJ_CACHE * NS);      // [GJ_CACHE], gid + 1, 0 = empty
+    unsigned char *bufs = (unsigned char *)(s_key + GJ_CACHE);    // 2 x T x row bytes
+    __shared__ __align__(8) uint64_t s_full[2];
     __shared__ int s_ops[TDP_MAX_AGGS + 1];
     __shared__ long long s_init[TDP_MAX_AGGS + 1];
-    if (threadIdx.x <= TDP_MAX_AGGS) {
-        int s = threadIdx.x, op = TDP_AGG_SUM;
+    __shared__ uint32_t s_off[GJ_MAX_STAGE];
+    const int tid = threadIdx.x;
+    if (tid <= TDP_MAX_AGGS) {
+        int sl = tid, op = TDP_AGG_SUM;
         for (int a = 0; a < as.n; a++)
-            if (as.slot[a] == s && s != 0)
+            if (as.slot[a] == sl && sl != 0)
                 op = as.op[a];
-        s_ops[s] = op;
-        s_init[s] = slot_init(as, s);
+        s_ops[sl] = op;
+        s_init[sl] = slot_init(as, sl);
+    }
+    uint32_t row_bytes = 0;
+    for (int c = 0; c < sg.n; c++)
+        row_bytes += sg.size[c];
+    if (tid == 0) {
+        uint32_t off = 0;
+        for (int c = 0; c < sg.n; c++) {
+            s_off[c] = off;
+            off += T * sg.size[c];
+        }
+        mbar_init(&s_full[0], 1);
+        mbar_init(&s_full[1], 1);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < GJ_CACHE; e += JP_THREADS) {
+    for (int e = tid; e < GJ_CACHE; e += JP_THREADS) {
         s_key[e] = 0;
-        for (int s = 0; s < NS; s++)
-            s_acc[e * NS + s] = s_init[s];
+        for (int sl = 0; sl < NS; sl++)
+            s_acc[e * NS + sl] = s_init[sl];
     }
+    const uint64_t stream_pol = l2_evict_first(), table_pol = l2_evict_last();
+    const long long ntiles = (n + T - 1) / T;
+    auto bulk_ok = [&](long long t) { return sg.aligned && (t + 1) * T <= n; };
+    auto issue = [&](long long t, int b) {
+        unsigned char *buf = bufs + (size_t)b * T * row_bytes;
+        mbar_arrive_expect_tx(&s_full[b], T * row_bytes);
+        for (int c = 0; c < sg.n; c++)
+            bulk_load_hint(buf + s_off[c], (const char *)sg.col[c] + (size_t)t * T * sg.size[c], T * sg.size[c],
+                           &s_full[b], stream_pol);
+    };
+    if (tid == 0 && blockIdx.x < ntiles && bulk_ok(blockIdx.x))
+        issue(blockIdx.x, 0);
     __syncthreads();
-    bool bad = false;
-    const long long stride = (long long)gridDim.x * GJ_TILE;
-    for (long long base = (long long)blockIdx.x * GJ_TILE; base < n; base += stride) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const long long idx0 = base + (long long)warp * GJ_WARP_ROWS + 4 * lane;
-        int pay[GJ_ROWS];
-        bool gave_up = false;
-        const unsigned hit = probe_rows8(tv, ps, key, key_vec, n, idx0, pay, gave_up);
-        if (gave_up)
-            set_status(d_status, TDP_ERR_CAPACITY);
+
+    bool bad = false, gave_up = false, late = false;
+    uint32_t phase = 0; // bit b: parity of buffer b's next phase
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+        const int b = it & 1;
+        unsigned char *buf = bufs + (size_t)b * T * row_bytes;
+        const long long tn = t + gridDim.x;
+        if (tid == 0 && tn < ntiles && bulk_ok(tn))
+            issue(tn, b ^ 1); // that buffer was released at the end of the previous tile
+        if (bulk_ok(t)) {
+            late |= !mbar_wait(&s_full[b], (phase >> b) & 1u, limit);
+            phase ^= 1u << b;
+        } else {
+            for (int li = tid; li < T; li += JP_THREADS) {
+                const long long idx = t * T + li;
+                if (idx >= n)
+                    break;
+                for (int c = 0; c < sg.n; c++) {
+                    unsigned char *d = buf + s_off[c];
+                    switch (sg.size[c]) {
+                    case 8: ((long long *)d)[li] = ((const long long *)sg.col[c])[idx]; break;
+                    case 4: ((int32_t *)d)[li] = ((const int32_t *)sg.col[c])[idx]; break;
+                    case 2: ((uint16_t *)d)[li] = ((const uint16_t *)sg.col[c])[idx]; break;
+                    default: d[li] = ((const uint8_t *)sg.col[c])[idx]; break;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        const int32_t *skey = (const int32_t *)(buf + s_off[sg.key]);
 #pragma unroll
-        for (int j = 0; j < GJ_STEPS; j++) {
-            unsigned hj = (hit >> (4 * j)) & 0xfu;
-            if (!hj)
-                continue;
-            long long *dst[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int h = 0; h < RPT; h += 4) {
+            // predicates, then one round trip for the first halves of 4 buckets
+            uint32_t kq[4];
+            uint4 wk[4], wp[4];
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-                if (!(hj >> e & 1))
+            for (int r = 0; r < 4; r++) {
+                kq[r] = EMPTY_KEY;
+                if (h + r >= RPT)
                     continue;
-                long long gid = (long long)(int)pay[j * 4 + e] - lo;
+                const int li = tid + (h + r) * JP_THREADS;
+                if (t * T + li >= n)
+                    continue;
+                bool q = true;
+                for (int p = 0; p < ps.n; p++) {
+                    const int c = sg.pred[p];
+                    const long long v = stage_val(buf + s_off[c], sg.size[c], ps.dt[p], li);
+                    q = q && range_holds64(v, ps.lo[p], (unsigned long long)(ps.hi[p] - ps.lo[p]),
+                                           (unsigned)ps.neg[p]);
+                }
+                if (q)
+                    kq[r] = (uint32_t)skey[li];
+                if (kq[r] != EMPTY_KEY) {
+                    const size_t b8 = (size_t)bucket_of((int)kq[r], tv.lgb) * BUCKET;
+                    wk[r] = ldg16_hint(tv.keys + b8, table_pol);
+                    wp[r] = ldg16_hint((const uint32_t *)tv.pay + b8, table_pol);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                if (kq[r] == EMPTY_KEY)
+                    continue;
+                const int li = tid + (h + r) * JP_THREADS;
+                const unsigned bk = bucket_of((int)kq[r], tv.lgb);
+                const uint32_t k4[4] = {wk[r].x, wk[r].y, wk[r].z, wk[r].w};
+                const uint32_t p4[4] = {wp[r].x, wp[r].y, wp[r].z, wp[r].w};
+                int pos = -2;
+                int32_t pay = 0;
+#pragma unroll
+                for (int i = 3; i >= 0; i--) {
+                    if (k4[i] == kq[r]) {
+                        pos = i;
+                        pay = (int32_t)p4[i];
+                    } else if (k4[i] == EMPTY_KEY) {
+                        pos = -1;
+                    }
+                }
+                if (pos == -2) { // first half full of other keys: the rest of the bucket, then the walk
+                    const size_t b8 = (size_t)bk * BUCKET;
+                    const uint4 k2 = ldg16_hint(tv.keys + b8 + 4, table_pol);
+                    const uint32_t kk[4] = {k2.x, k2.y, k2.z, k2.w};
+#pragma unroll
+                    for (int i = 3; i >= 0; i--) {
+                        if (kk[i] == kq[r])
+                            pos = 4 + i;
+                        else if (kk[i] == EMPTY_KEY)
+                            pos = -1;
+                    }
+                    long long slot = pos >= 0 ? (long long)b8 + pos : -1;
+                    if (pos == -2) {
+                        slot = lookup_tail(tv.keys, tv.bmask, tv.steps, kq[r], bk, table_pol);
+                        gave_up |= slot == -2;
+                    }
+                    if (slot < 0)
+                        continue;
+                    pay = tv.pay[slot];
+                } else if (pos < 0) {
+                    continue;
+                }
+                // aggregate the row into its group
+                const long long gid = (long long)pay - lo;
                 if (gid < 0 || gid >= D) {
                     bad = true;
-                    hj &= ~(1u << e);
                     continue;
                 }
-                // find / claim a cache slot
-                unsigned tag = (unsigned)gid + 1u;
-                unsigned h = ((unsigned)gid * 0x9E3779B1u) >> 21; // 11 bits: GJ_CACHE = 2048
-                long long *d = nullptr;
-                for (int q = 0; q < GJ_PROBES; q++) {
-                    unsigned cur = s_key[h];
-                    if (cur == 0)
-                        cur = atomicCAS(&s_key[h], 0u, tag);
-                    if (cur == 0 || cur == tag) {
-                        d = s_acc + h * NS;
-                        break;
-                    }
-                    h = (h + 1) & (GJ_CACHE - 1);
+                long long *dst = gj_cache_slot(s_key, s_acc, NS, gid);
+                if (!dst)
+                    dst = gacc + gid * NS;
+                atomicAdd((unsigned long long *)&dst[0], 1ull);
+                for (int sl = 1; sl < NS; sl++) {
+                    long long va = stage_val(buf + s_off[sg.sa[sl]], sg.size[sg.sa[sl]], as.sadt[sl], li);
+                    if (as.sop[sl] == TDP_AGG_SUM_MUL_KMINUS)
+                        va *= as.sk[sl] - stage_val(buf + s_off[sg.sb[sl]], sg.size[sg.sb[sl]], as.sbdt[sl], li);
+                    acc_update(&dst[sl], s_ops[sl], va);
                 }
-                if (!d)
-                    d = gacc + gid * NS;
-                dst[e] = d;
-                atomicAdd((unsigned long long *)&d[0], 1ull);
-            }
-            if (!hj)
-                continue;
-            for (int a = 0; a < as.n; a++) {
-                if (as.op[a] == TDP_AGG_COUNT)
-                    continue;
-                long long x[4], y[4] = {0, 0, 0, 0};
-                load4_int(as.a[a], as.adt[a], as.avec[a], idx0 + j * 128, n, x);
-                if (as.op[a] == TDP_AGG_SUM_MUL_KMINUS)
-                    load4_int(as.b[a], as.bdt[a], as.bvec[a], idx0 + j * 128, n, y);
-#pragma unroll
-                for (int e = 0; e < 4; e++)
-                    if (hj >> e & 1)
-                        acc_update(&dst[e][as.slot[a]], as.op[a], agg_value(as, a, x[e], y[e]));
             }
         }
+        __syncthreads(); // buffer b free for the tile after next
     }
     if (bad)
         set_status(d_status, TDP_ERR_OVERFLOW);
+    if (gave_up)
+        set_status(d_status, TDP_ERR_CAPACITY);
+    if (late)
+        set_status(d_status, TDP_ERR_TIMEOUT);
     __syncthreads();
-    for (int e = threadIdx.x; e < GJ_CACHE; e += JP_THREADS) {
-        unsigned tag = s_key[e];
+    for (int e = tid; e < GJ_CACHE; e += JP_THREADS) {
+        const unsigned tag = s_key[e];
         if (!tag)
             continue;
-        long long gid = (long long)tag - 1;
-        for (int s = 0; s < NS; s++) {
-            long long v = s_acc[e * NS + s];
-            if (v != s_init[s])
-                acc_update(&gacc[gid * NS + s], s_ops[s], v);
+        const long long gid = (long long)tag - 1;
+        for (int sl = 0; sl < NS; sl++) {
+            const long long v = s_acc[e * NS + sl];
+            if (v != s_init[sl])
+                acc_update(&gacc[gid * NS + sl], s_ops[sl], v);
         }
     }
 }
-
 
 static int log2_of(long long x)
 {
@@ -767,6 +825,81 @@ static tdp_status launch_probe(const TableView &tv, const PredSet &ps, const int
                                                     out_payload, gs, cap, d_count, status, d_status, spin_limit(),
                                                     tiles);
     return launch_status();
+}
+
+// The staged-column plan of a group-join: each distinct column once.
+static bool make_gjstage(const PredSet &ps, const AggSet &as, const void *key, GJStage *sg)
+{
+    sg->n = 0;
+    sg->aligned = 1;
+    auto add = [&](const void *col, int size) -> int {
+        for (int c = 0; c < sg->n; c++)
+            if (sg->col[c] == col && sg->size[c] == size)
+                return c;
+        if (sg->n == GJ_MAX_STAGE)
+            return -1;
+        sg->col[sg->n] = col;
+        sg->size[sg->n] = size;
+        sg->aligned = sg->aligned && ((uintptr_t)col % 16) == 0;
+        return sg->n++;
+    };
+    for (int c = 0; c < GJ_MAX_STAGE; c++) {
+        sg->col[c] = nullptr;
+        sg->size[c] = 0;
+    }
+    if ((sg->key = add(key, 4)) < 0)
+        return false;
+    for (int p = 0; p < TDP_MAX_PREDS; p++) {
+        sg->pred[p] = -1;
+        if (p < ps.n && (sg->pred[p] = add(ps.col[p], dtype_size(ps.dt[p]))) < 0)
+            return false;
+    }
+    for (int sl = 0; sl <= TDP_MAX_AGGS; sl++) {
+        sg->sa[sl] = sg->sb[sl] = -1;
+        if (sl == 0 || sl >= as.nslots)
+            continue;
+        if ((sg->sa[sl] = add(as.sa[sl], dtype_size(as.sadt[sl]))) < 0)
+            return false;
+        if (as.sop[sl] == TDP_AGG_SUM_MUL_KMINUS && (sg->sb[sl] = add(as.sb[sl], dtype_size(as.sbdt[sl]))) < 0)
+            return false;
+    }
+    return true;
+}
+
+template <int RPT>
+static tdp_status launch_gj(const TableView &tv, const PredSet &ps, const GJStage &sg, const AggSet &as, long long n,
+                            const long long *d_n, long long lo, long long D, long long *acc, int32_t *d_status,
+                            cudaStream_t s, size_t row_bytes)
+{
+    constexpr long long T = JP_THREADS * RPT;
+    const size_t smem = (size_t)GJ_CACHE * as.nslots * 8 + GJ_CACHE * 4 + 2 * T * row_bytes;
+    auto kern = join_probe_agg_kernel<RPT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TDP_ERR_CUDA;
+    const int per_sm = std::max(1, std::min(3, (int)((220 * 1024) / (smem + 1024))));
+    const long long tiles = (n + T - 1) / T;
+    const unsigned grid = (unsigned)std::max(1ll, std::min<long long>(tiles, (long long)num_sms() * per_sm));
+    kern<<<grid, JP_THREADS, smem, s>>>(tv, ps, sg, n, d_n, lo, D, as, acc, d_status, spin_limit());
+    return launch_status();
+}
+
+// Rows per thread of a group-join tile (at most 4, so that three blocks, and
+// three group caches, fit on an SM): two tile buffers within 64 KiB.
+static tdp_status launch_probe_agg(const TableView &tv, const PredSet &ps, const GJStage &sg, const AggSet &as,
+                                   long long n, const long long *d_n, long long lo, long long D, long long *acc,
+                                   int32_t *d_status, cudaStream_t s)
+{
+    size_t row_bytes = 0;
+    for (int c = 0; c < sg.n; c++)
+        row_bytes += sg.size[c];
+    int rpt = 4;
+    while (rpt > 1 && 2 * (size_t)JP_THREADS * rpt * row_bytes > 64 * 1024)
+        rpt >>= 1;
+    switch (rpt) {
+    case 4: return launch_gj<4>(tv, ps, sg, as, n, d_n, lo, D, acc, d_status, s, row_bytes);
+    case 2: return launch_gj<2>(tv, ps, sg, as, n, d_n, lo, D, acc, d_status, s, row_bytes);
+    default: return launch_gj<1>(tv, ps, sg, as, n, d_n, lo, D, acc, d_status, s, row_bytes);
+    }
 }
 
 } // namespace tdp
@@ -933,17 +1066,12 @@ extern "C" tdp_status tdp_join_probe_agg(const uint64_t *table, int64_t nslots, 
     dense_acc_init_kernel<<<(unsigned)std::min<long long>((D * as.nslots + 255) / 256, 4096), 256, 0, s>>>(as, D,
                                                                                                          acc);
     if (n > 0) {
-        const size_t smem = (size_t)GJ_CACHE * as.nslots * 8 + GJ_CACHE * 4;
-        if (cudaFuncSetAttribute(join_probe_agg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return TDP_ERR_CUDA;
-        int per_sm = std::max(1, std::min(4, (int)((200 * 1024) / smem)));
-        long long want = (n + GJ_TILE - 1) / GJ_TILE;
-        unsigned grid = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() * per_sm));
-        const int32_t *key = (const int32_t *)cols[key_col].data;
-        join_probe_agg_kernel<<<grid, JP_THREADS, smem, s>>>(table_view(table, nslots), ps,
-                                                            key, ((uintptr_t)key % 16) == 0, n,
-                                                            (const long long *)d_n, payload_lo, D, as, acc, d_status);
+        GJStage sg;
+        if (!make_gjstage(ps, as, cols[key_col].data, &sg))
+            return TDP_ERR_INVALID_ARG;
+        if ((st = launch_probe_agg(table_view(table, nslots), ps, sg, as, n, (const long long *)d_n, payload_lo, D,
+                                   acc, d_status, s)) != TDP_OK)
+            return st;
     }
     if ((st = launch_status()) != TDP_OK)
         return st;

@@ -245,7 +245,7 @@ def run_gpu(args):
             e[2].record(stream)
             kc, pc, dc = pr["gathered"]
             gb = ops.groupby_agg([ops.Col(kc, 1, N_DIM), pc, dc], [0], [("sum_mul_kminus", 1, 2, 100)],
-                                 n=plan.cap, nsel=pr["count"], strategy="sort", capacity=plan.cap,
+                                 n=plan.cap, nsel=pr["count"], strategy=plan.groupby_strategy, capacity=plan.cap,
                                  status=plan.status)
             e[3].record(stream)
             ops.topk(gb["aggs"][0], gb["keys"][0], 10, d_n=gb["ngroups"], status=plan.status)
@@ -317,7 +317,7 @@ def run_gpu(args):
         launches_per_step = None
 
     # ---- roofline of the dominant stage
-    stage_names = ["join_build", "join_probe", "groupby_sort", "topk"]
+    stage_names = ["join_build", "join_probe", "groupby", "topk"]
     sel_f = float(np.mean(fact_h["date"] > 1200))
     probe_rows = N_FACT * sel_f
     algo = {
@@ -327,9 +327,9 @@ def run_gpu(args):
         # probe: date (4 B) every row; key (4 B) of qualifying rows; one 8-byte slot per lookup; price/disc
         # (16 B) of matches; key/price/disc written for matches (20 B)
         "join_probe": N_FACT * 4 + probe_rows * 4 + probe_rows * 8 + nmatch * 16 + nmatch * 20,
-        # sort path group-by: pack (read 20 B, write 8 B), 3 digit passes (read+write 8 B pairs), reduce
-        # (read 8 B pair + 16 B gather, write 12 B per group)
-        "groupby_sort": nmatch * (20 + 8) + 3 * nmatch * 16 + nmatch * (8 + 16) + ngroups * 12,
+        # partitioned group-by: count (key 4 B), scatter (key, price, disc 20 B in; gid + value 12 B out),
+        # bucket reduce (12 B in), groups out (key 4 B + sum 8 B)
+        "groupby": nmatch * (4 + 20 + 12 + 12) + ngroups * 12,
         "topk": ngroups * 12,
     }
     dom = int(np.argmax(st_ms))

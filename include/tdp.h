@@ -72,7 +72,12 @@ typedef enum {
     TDP_AGG_MAX = 5
 } tdp_agg_op;
 
-typedef enum { TDP_GROUPBY_AUTO = 0, TDP_GROUPBY_SORT = 1, TDP_GROUPBY_SMALL_DOMAIN = 2 } tdp_groupby_strategy;
+typedef enum {
+    TDP_GROUPBY_AUTO = 0,
+    TDP_GROUPBY_SORT = 1,
+    TDP_GROUPBY_SMALL_DOMAIN = 2,
+    TDP_GROUPBY_PARTITION = 3
+} tdp_groupby_strategy;
 
 /* Join flags */
 #define TDP_JOIN_UNIQUE_BUILD 1u /* build keys must be unique (N:1 join)      */
@@ -191,7 +196,12 @@ size_t tdp_groupby_agg_workspace(int64_t n, const tdp_col *keys, int32_t nkeys, 
  *   key_cols[nkeys]    indices into cols of the key columns (1..4, integer)
  *   aggs[naggs]        1..8 aggregates; a, b index cols
  *   strategy           AUTO picks SMALL_DOMAIN when every key column has
- *                      bounds and the domain product is <= 2^22, else SORT
+ *                      bounds and the dense table of the domain fits in one
+ *                      block's shared memory, else PARTITION when every key
+ *                      column has bounds and the domain allows it (below),
+ *                      else SMALL_DOMAIN when the domain is <= 2^22, else SORT.
+ *                      Asking for SMALL_DOMAIN or PARTITION where it does not
+ *                      apply returns TDP_ERR_INVALID_ARG.
  *   out_keys[nkeys]    device arrays (dtype of each key column, capacity rows)
  *   out_aggs[naggs]    device int64 arrays (capacity rows)
  *   d_ngroups          device int64: number of groups
@@ -204,6 +214,13 @@ size_t tdp_groupby_agg_workspace(int64_t n, const tdp_col *keys, int32_t nkeys, 
  * are present), radix-sorts (key, row id) and reduces the sorted runs.
  * SMALL_DOMAIN: one pass that accumulates into per-block copies of the dense
  * key domain and merges them.
+ * PARTITION: bounded keys whose dense domain D fits 16384 buckets of B group
+ * ids (B = 4096 with one aggregate slot besides COUNT, smaller with more, so
+ * D <= 64M for one sum): rows are counted per bucket, scattered to bucket
+ * segments with their aggregate inputs, and each bucket is reduced in a dense
+ * shared-memory table and written in ascending key order.  Within a bucket
+ * the rows are combined in no fixed order, which does not change exact
+ * integer sums, minima or maxima.
  */
 tdp_status tdp_groupby_agg(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds,
                            int64_t n, const int32_t *sel, const int64_t *d_nsel,

@@ -19,7 +19,7 @@ CMP = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
 # tdp_agg_op
 AGG = {"count": 0, "sum": 1, "sum_mul_kminus": 2, "avg": 3, "min": 4, "max": 5}
 # tdp_groupby_strategy
-STRATEGY = {"auto": 0, "sort": 1, "small_domain": 2}
+STRATEGY = {"auto": 0, "sort": 1, "small_domain": 2, "partition": 3}
 JOIN_UNIQUE_BUILD = 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported dtype", 3: "workspace too small",

@@ -11,7 +11,8 @@
 // on the order), and a compaction kernel emits the non-empty groups in
 // ascending gid order, which is ascending key order.
 //
-// SORT: see groupby_sort.cu.
+// SORT: see groupby_sort.cu.  PARTITION (bounded keys, domain too large for
+// one shared-memory table): see groupby_part.cu.
 #include "groupby.cuh"
 
 namespace tdp {
@@ -79,15 +80,6 @@ tdp_status make_aggset(const tdp_col *cols, int32_t ncols, const tdp_agg *aggs, 
     return TDP_OK;
 }
 
-// Combine operator of accumulator slot s.
-__device__ __forceinline__ int slot_op(const AggSet &as, int s)
-{
-    for (int a = 0; a < as.n; a++)
-        if (as.slot[a] == s && s != 0)
-            return as.op[a];
-    return TDP_AGG_SUM;
-}
-
 __global__ void dense_acc_init_kernel(AggSet as, long long D, long long *acc)
 {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,20 +89,6 @@ __global__ void dense_acc_init_kernel(AggSet as, long long D, long long *acc)
 }
 
 constexpr int SD_THREADS = 256;
-
-// Adds rows into `my` (a dense table of D groups x nslots).  Returns false
-// (and flags OVERFLOW) when a key lies outside its declared bounds.
-__device__ __forceinline__ bool row_gid(const KeySet &ks, long long row, long long &gid)
-{
-    gid = 0;
-    for (int k = 0; k < ks.n; k++) {
-        long long v = load_int(ks.col[k], ks.dt[k], row) - ks.lo[k];
-        if (v < 0 || v >= ks.size[k])
-            return false;
-        gid += v * ks.stride[k];
-    }
-    return true;
-}
 
 template <bool SEL>
 __global__ void __launch_bounds__(SD_THREADS) small_domain_kernel(PredSet ps, KeySet ks, AggSet as, long long n,
@@ -349,22 +327,6 @@ tdp_status make_keyset(const tdp_col *cols, int32_t ncols, const int32_t *key_co
 
 static const long long SMALL_DOMAIN_MAX = 1ll << 22;
 
-static bool keys_small(const tdp_col *cols, int32_t ncols, const int32_t *key_cols, int32_t nkeys, long long *D)
-{
-    long long d = 1;
-    for (int k = 0; k < nkeys; k++) {
-        int c = key_cols[k];
-        if (c < 0 || c >= ncols || !cols[c].has_bounds || cols[c].hi < cols[c].lo)
-            return false;
-        long long sz = cols[c].hi - cols[c].lo + 1;
-        if (sz > SMALL_DOMAIN_MAX || d * sz > SMALL_DOMAIN_MAX)
-            return false;
-        d *= sz;
-    }
-    *D = d;
-    return true;
-}
-
 static bool keys_small_desc(const tdp_col *keys, int32_t nkeys, long long *D)
 {
     long long d = 1;
@@ -416,14 +378,11 @@ tdp_status small_domain_run(const PredSet &ps, const KeySet &ks, const AggSet &a
     long long want = (rows + SD_THREADS - 1) / SD_THREADS;
     unsigned grid = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() * blocks_per_sm));
     if (sel) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(small_domain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(small_domain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         small_domain_kernel<true><<<grid, SD_THREADS, smem, s>>>(ps, ks, as, n, sel, (const long long *)d_nsel, D,
                                                                 copies, acc, d_status);
     } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(small_domain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        cudaFuncSetAttribute(small_domain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         small_domain_kernel<false><<<grid, SD_THREADS, smem, s>>>(ps, ks, as, n, nullptr, (const long long *)d_nsel,
                                                                  D, copies, acc, d_status);
     }
@@ -431,6 +390,52 @@ tdp_status small_domain_run(const PredSet &ps, const KeySet &ks, const AggSet &a
     if (st != TDP_OK)
         return st;
     return dense_finalize(ks, as, out, D, acc, capacity, d_ngroups, fin_ws, d_status, s);
+}
+
+// Partition strategy (groupby_part.cu)
+size_t part_ws(long long n, long long D, int nslots);
+tdp_status part_run(const PredSet &ps, const KeySet &ks, const AggSet &as, long long D, long long n,
+                    const int32_t *sel, const int64_t *d_nsel, const DenseOut &out, long long capacity,
+                    int64_t *d_ngroups, void *ws, int32_t *d_status, cudaStream_t s);
+
+// Domain size of bounded key columns (0 when some column has no bounds or
+// the product exceeds 2^31).
+static long long bounded_domain(const tdp_col *keys, int32_t nkeys)
+{
+    long long d = 1;
+    for (int k = 0; k < nkeys; k++) {
+        if (!keys[k].has_bounds || keys[k].hi < keys[k].lo)
+            return 0;
+        long long sz = keys[k].hi - keys[k].lo + 1;
+        if (sz > (1ll << 31) || d * sz > (1ll << 31))
+            return 0;
+        d *= sz;
+    }
+    return d;
+}
+
+enum GbPath { GB_SMALL, GB_PART, GB_SORT, GB_NONE };
+
+// AUTO: a dense table in shared memory when it fits (small domain), else
+// buckets of the dense domain (partition) when the keys are bounded, else
+// the sort.
+static GbPath choose_path(int32_t strategy, const tdp_col *keys, int32_t nkeys, int nslots)
+{
+    long long Ds = 0;
+    const bool small = keys_small_desc(keys, nkeys, &Ds);
+    const long long Db = bounded_domain(keys, nkeys);
+    size_t sm = 0;
+    switch (strategy) {
+    case TDP_GROUPBY_SMALL_DOMAIN: return small ? GB_SMALL : GB_NONE;
+    case TDP_GROUPBY_SORT: return GB_SORT;
+    case TDP_GROUPBY_PARTITION: return Db > 0 && part_ws(1, Db, nslots) > 0 ? GB_PART : GB_NONE;
+    default:
+        if (small && small_domain_copies(Ds, nslots, &sm) > 0)
+            return GB_SMALL;
+        if (Db > 0 && part_ws(1, Db, nslots) > 0)
+            return GB_PART;
+        return small ? GB_SMALL : GB_SORT;
+    }
 }
 
 // Sort strategy (groupby_sort.cu)
@@ -448,14 +453,22 @@ using namespace tdp;
 extern "C" size_t tdp_groupby_agg_workspace(int64_t n, const tdp_col *keys, int32_t nkeys, int32_t naggs,
                                             int32_t strategy)
 {
-    if (!keys || nkeys < 1 || nkeys > TDP_MAX_KEYS || naggs < 1)
+    if (!keys || nkeys < 1 || nkeys > TDP_MAX_KEYS || naggs < 1 || naggs > TDP_MAX_AGGS)
         return 0;
-    long long D = 0;
-    bool small = keys_small_desc(keys, nkeys, &D);
-    if (strategy == TDP_GROUPBY_SMALL_DOMAIN || (strategy == TDP_GROUPBY_AUTO && small))
-        return small ? small_domain_ws(D, naggs) : 0;
-    int bits = sort_key_bits_desc(keys, nkeys);
-    return bits > 0 ? sort_groupby_ws(n, nkeys, naggs, bits) : 0;
+    // slots: COUNT plus at most one per aggregate
+    switch (choose_path(strategy, keys, nkeys, 1 + naggs)) {
+    case GB_SMALL: {
+        long long D = 0;
+        keys_small_desc(keys, nkeys, &D);
+        return small_domain_ws(D, naggs);
+    }
+    case GB_PART: return part_ws(n, bounded_domain(keys, nkeys), 1 + naggs);
+    case GB_SORT: {
+        int bits = sort_key_bits_desc(keys, nkeys);
+        return bits > 0 ? sort_groupby_ws(n, nkeys, naggs, bits) : 0;
+    }
+    default: return 0;
+    }
 }
 
 extern "C" tdp_status tdp_groupby_agg(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds,
@@ -466,7 +479,7 @@ extern "C" tdp_status tdp_groupby_agg(const tdp_col *cols, int32_t ncols, const 
                                       tdp_stream_t stream)
 {
     if (n < 0 || n >= (1ll << 31) || !cols || !d_ngroups || capacity < 0 || !out_keys || !out_aggs ||
-        (sel && !d_nsel) || strategy < 0 || strategy > 2)
+        (sel && !d_nsel) || strategy < 0 || strategy > 3 || !key_cols || nkeys < 1 || nkeys > TDP_MAX_KEYS)
         return TDP_ERR_INVALID_ARG;
     PredSet ps;
     tdp_status st = make_predset(cols, ncols, preds, npreds, sel ? 0 : n, &ps);
@@ -475,14 +488,20 @@ extern "C" tdp_status tdp_groupby_agg(const tdp_col *cols, int32_t ncols, const 
     AggSet as;
     if ((st = make_aggset(cols, ncols, aggs, naggs, sel ? 0 : n, &as)) != TDP_OK)
         return st;
-    long long Dsmall = 0;
-    bool small = keys_small(cols, ncols, key_cols, nkeys, &Dsmall);
-    if (strategy == TDP_GROUPBY_SMALL_DOMAIN && !small)
+    tdp_col kd[TDP_MAX_KEYS];
+    for (int k = 0; k < nkeys; k++) {
+        if (key_cols[k] < 0 || key_cols[k] >= ncols)
+            return TDP_ERR_INVALID_ARG;
+        kd[k] = cols[key_cols[k]];
+    }
+    // the workspace was sized for 1 + naggs slots; the path is chosen with the
+    // same count so that both agree
+    const GbPath path = choose_path(strategy, kd, nkeys, 1 + naggs);
+    if (path == GB_NONE)
         return TDP_ERR_INVALID_ARG;
-    bool use_small = strategy == TDP_GROUPBY_SMALL_DOMAIN || (strategy == TDP_GROUPBY_AUTO && small);
     KeySet ks;
     long long D = 0;
-    if ((st = make_keyset(cols, ncols, key_cols, nkeys, sel ? 0 : n, &ks, use_small, &D)) != TDP_OK)
+    if ((st = make_keyset(cols, ncols, key_cols, nkeys, sel ? 0 : n, &ks, path != GB_SORT, &D)) != TDP_OK)
         return st;
     DenseOut out;
     for (int k = 0; k < TDP_MAX_KEYS; k++) {
@@ -497,10 +516,15 @@ extern "C" tdp_status tdp_groupby_agg(const tdp_col *cols, int32_t ncols, const 
             return TDP_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (use_small) {
+    if (path == GB_SMALL) {
         if (!ws || ws_bytes < small_domain_ws(D, naggs))
             return TDP_ERR_WORKSPACE_TOO_SMALL;
         return small_domain_run(ps, ks, as, D, n, sel, d_nsel, out, capacity, d_ngroups, ws, d_status, s);
+    }
+    if (path == GB_PART) {
+        if (!ws || ws_bytes < part_ws(n, D, 1 + naggs))
+            return TDP_ERR_WORKSPACE_TOO_SMALL;
+        return part_run(ps, ks, as, D, n, sel, d_nsel, out, capacity, d_ngroups, ws, d_status, s);
     }
     int bits = sort_key_bits(ks);
     if (bits <= 0)

@@ -83,6 +83,28 @@ __device__ __forceinline__ void acc_update(long long *acc, int op, long long v)
         atomicAdd((unsigned long long *)acc, (unsigned long long)v);
 }
 
+// Combine operator of accumulator slot s.
+__device__ __forceinline__ int slot_op(const AggSet &as, int s)
+{
+    for (int a = 0; a < as.n; a++)
+        if (as.slot[a] == s && s != 0)
+            return as.op[a];
+    return TDP_AGG_SUM;
+}
+
+// Dense group id of `row`; false when a key lies outside its declared bounds.
+__device__ __forceinline__ bool row_gid(const KeySet &ks, long long row, long long &gid)
+{
+    gid = 0;
+    for (int k = 0; k < ks.n; k++) {
+        long long v = load_int(ks.col[k], ks.dt[k], row) - ks.lo[k];
+        if (v < 0 || v >= ks.size[k])
+            return false;
+        gid += v * ks.stride[k];
+    }
+    return true;
+}
+
 // Final value of aggregate a from its accumulator and the group count.
 __device__ __forceinline__ long long agg_final(const AggSet &as, int a, const long long *acc)
 {

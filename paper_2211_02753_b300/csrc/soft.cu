@@ -202,9 +202,8 @@ static SoftGrid soft_grid(long long n, int G, int n64, int n32)
 
 static tdp_status set_smem(const void *fn, size_t smem)
 {
-    if (smem > 48 * 1024)
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return TDP_ERR_CUDA;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TDP_ERR_CUDA;
     return TDP_OK;
 }
 

@@ -47,9 +47,12 @@ class PricingSummary:
 
 
 class ShippingPriority:
-    def __init__(self, fact: dict, dim: dict, dim_selectivity: float = 0.2):
+    def __init__(self, fact: dict, dim: dict, dim_selectivity: float = 0.2, groupby_strategy: str = "auto"):
         self.f = fact  # key, price, disc, date
         self.d = dim   # key, segment
+        # the join key is bounded by the dimension's key range 1..n_dim: AUTO
+        # takes the partition strategy ("sort" keeps the general sort)
+        self.groupby_strategy = groupby_strategy
         dev = fact["key"].device
         self.n_fact = fact["key"].numel()
         self.n_dim = dim["key"].numel()
@@ -69,7 +72,8 @@ class ShippingPriority:
                             payload=False, status=st)
         key_c, price_c, disc_c = pr["gathered"]
         gb = ops.groupby_agg([ops.Col(key_c, 1, self.n_dim), price_c, disc_c], [0],
-                             [("sum_mul_kminus", 1, 2, 100)], n=self.cap, nsel=pr["count"], strategy="sort",
+                             [("sum_mul_kminus", 1, 2, 100)], n=self.cap, nsel=pr["count"],
+                             strategy=self.groupby_strategy,
                              capacity=self.cap, status=st)
         ov, okk, dk = ops.topk(gb["aggs"][0], gb["keys"][0], 10, d_n=gb["ngroups"], status=st)
         return {"top_vals": ov, "top_keys": okk, "k": dk, "ngroups": gb["ngroups"], "nmatch": pr["count"],

@@ -147,7 +147,7 @@ def _oracle_aggs(t, names):
     return out
 
 
-@pytest.mark.parametrize("strategy", ["small_domain", "sort"])
+@pytest.mark.parametrize("strategy", ["small_domain", "sort", "partition"])
 @pytest.mark.parametrize("n", [0, 1, 4097, 70001])
 def test_groupby_matches_oracle(strategy, n):
     t = _table(n, 100 + n)
@@ -166,6 +166,80 @@ def test_groupby_matches_oracle(strategy, n):
     assert np.array_equal(np_(out["keys"][1], g), rk[:, 1])
     for j in range(len(AGGS6)):
         assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), AGGS6[j]
+
+
+@pytest.mark.parametrize("n", [1, 4099, 300001])
+def test_groupby_partition_large_domain(n):
+    """PARTITION over domains of many buckets: one bounded int32 key over
+    [-5M, 5M] (2442 buckets of 4096 gids), and two keys (int32 x int8) whose
+    product spans 256 x 20001 gids; six aggregates, so narrower buckets; a
+    row-list input; and a dense input cut by a device row count."""
+    t = _table(n, 900 + n)
+    r = np.random.default_rng(n)
+    t["big"] = r.integers(-5_000_000, 5_000_001, n).astype(np.int32)
+    t["mid"] = r.integers(-10000, 10001, n).astype(np.int32)
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w", "big", "mid"]
+    cols = [cu(t[k]) for k in names]
+    cols[8] = ops.Col(cols[8], -5_000_000, 5_000_000)
+    cols[9] = ops.Col(cols[9], -10000, 10000)
+    cols[0] = ops.Col(cols[0], -128, 127)
+    oaggs = _oracle_aggs(t, names)
+    # one key, two aggregates (4096-gid buckets)
+    out = ops.groupby_agg(cols, [8], [("sum", 6), ("count",)], strategy="partition")
+    ops.check(out["status"])
+    rk, ra = R.groupby([t["big"]], [("sum", t["v"], None, None), ("count", None, None, None)], n)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+    assert np.array_equal(np_(out["aggs"][0], g), ra[:, 0])
+    assert np.array_equal(np_(out["aggs"][1], g), ra[:, 1])
+    # two keys, six aggregates, row list
+    sel = R.filter([(t["c64"], ">", 0)], n)
+    out = ops.groupby_agg(cols, [9, 0], AGGS6, sel=cu(sel), strategy="partition")
+    ops.check(out["status"])
+    rk, ra = R.groupby([t["mid"], t["a8"]], oaggs, n, sel=sel)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+    assert np.array_equal(np_(out["keys"][1], g), rk[:, 1])
+    for j in range(len(AGGS6)):
+        assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), AGGS6[j]
+    # dense input limited by a device row count, with a fused filter
+    m = n // 2 + 1
+    d_n = torch.tensor([m], dtype=torch.int64, device=DEV)
+    out = ops.groupby_agg(cols, [8], AGGS6, preds=[(2, ">=", 0)], nsel=d_n, strategy="partition")
+    ops.check(out["status"])
+    sel2 = R.filter([(t["b32"][:m], ">=", 0)], m)
+    rk, ra = R.groupby([t["big"]], oaggs, n, sel=sel2)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+    for j in range(len(AGGS6)):
+        assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), AGGS6[j]
+
+
+def test_groupby_partition_flags_keys_out_of_bounds_and_capacity():
+    n = 50000
+    t = _table(n, 4)
+    t["big"] = np.random.default_rng(4).integers(0, 1_000_000, n).astype(np.int32)
+    cols = [cu(t["big"]), cu(t["v"])]
+    bounded = [ops.Col(cols[0], 0, 499_999), cols[1]]  # about half the keys lie above the bound
+    out = ops.groupby_agg(bounded, [0], [("sum", 1)], strategy="partition")
+    assert int(out["status"].item()) & 32  # TDP_ERR_OVERFLOW: rows out of bounds are dropped
+    keep = np.flatnonzero(t["big"] <= 499_999).astype(np.int32)
+    rk, ra = R.groupby([t["big"]], [("sum", t["v"], None, None)], n, sel=keep)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+    assert np.array_equal(np_(out["aggs"][0], g), ra[:, 0])
+    full = [ops.Col(cols[0], 0, 999_999), cols[1]]
+    cap = 1000
+    out = ops.groupby_agg(full, [0], [("sum", 1)], strategy="partition", capacity=cap)
+    assert int(out["status"].item()) & 4  # TDP_ERR_CAPACITY
+    rk, ra = R.groupby([t["big"]], [("sum", t["v"], None, None)], n)
+    assert int(out["ngroups"].item()) == len(rk)
+    assert np.array_equal(np_(out["keys"][0], cap), rk[:cap, 0])
+    assert np.array_equal(np_(out["aggs"][0], cap), ra[:cap, 0])
 
 
 @pytest.mark.parametrize("n", [5000, 300001])

@@ -21,7 +21,9 @@
  *    allocate memory and does not synchronise the stream.  Scratch memory is
  *    the caller's workspace `ws` of `ws_bytes` bytes, sized by the matching
  *    tdp_*_workspace() query; a smaller workspace returns
- *    TDP_ERR_WORKSPACE_TOO_SMALL before anything is launched.
+ *    TDP_ERR_WORKSPACE_TOO_SMALL before anything is launched.  Workspaces
+ *    start on a 256-byte boundary (as every CUDA allocation does); a
+ *    workspace that is not 16-byte aligned returns TDP_ERR_INVALID_ARG.
  *  - The return value reports argument and launch errors found on the host.
  *    Errors found on the device (capacity exceeded, duplicate build key, a
  *    bounded wait that ran out, arithmetic overflow) are OR-ed into the

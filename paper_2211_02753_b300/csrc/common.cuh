@@ -301,6 +301,33 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// Shared -> global bulk copy (both addresses 16-byte aligned, bytes a
+// multiple of 16), in the issuing thread's current bulk group.  The shared
+// source must have been fenced for the async proxy by its writers.
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Waits until at most N of the thread's bulk groups are still reading their
+// shared source.
+template <int N> __device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Waits until all of the thread's bulk groups have completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // L2 cache policies: data read once (streamed columns, gathered columns) is
 // marked evict-first so that it does not push out data read many times (a
 // hash table), which is marked evict-last.
@@ -358,6 +385,25 @@ __device__ __forceinline__ uint4 ldg16_hint(const uint32_t *p, uint64_t policy)
         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
         : "l"(p), "l"(policy));
     return v;
+}
+
+// One test of the phase of the given parity (true once it has completed).
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.b32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+// Plain mbarrier arrival (release at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Bounded wait for the phase of the given parity; false when it ran out.
@@ -447,6 +493,148 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
     if (lane == 0)
         st_relaxed_u64(&status[tile], LB_INC | ((excl + aggregate) & LB_VAL));
     return excl;
+}
+
+
+// Wide look-back.  Each lane reads one aligned group of LB_WIDE = 16
+// consecutive status words (128 bytes, eight 16-byte vector loads) per round
+// trip, so one warp spans 512 predecessor tiles; the inclusive prefix a tile
+// needs is then nearly always found in one round.  Each status word is
+// written whole (64-bit single-copy atomic), so a vector load never sees a
+// torn word.  The window's loads can be issued early (lb_window_load) and
+// resolved later (lookback_resolve) so that their latency overlaps other work.
+constexpr int LB_WIDE = 16;
+
+struct LbWindow {
+    unsigned long long w[LB_WIDE]; // w[j] = word 16g + 15 - j of the lane's group g (j = 0 nearest)
+};
+
+__device__ __forceinline__ void lb_load2(const unsigned long long *p, unsigned long long &a, unsigned long long &b)
+{
+    asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+// Loads the group the lane covers in the first round of tile's look-back:
+// group (tile - 1) / 16 - lane.  Groups below 0 read as inclusive zeros.
+__device__ __forceinline__ void lb_window_load(const unsigned long long *status, long long tile, LbWindow &W)
+{
+    const int lane = threadIdx.x & 31;
+    const long long g = (tile - 1) / LB_WIDE - lane;
+    if (tile > 0 && g >= 0) {
+        const unsigned long long *p = status + g * LB_WIDE;
+#pragma unroll
+        for (int j = 0; j < LB_WIDE; j += 2)
+            lb_load2(p + LB_WIDE - 2 - j, W.w[j + 1], W.w[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < LB_WIDE; j++)
+            W.w[j] = LB_INC;
+    }
+}
+
+// Called by ONE full warp, with W loaded by lb_window_load(status, tile, W)
+// (possibly long before).  Walks back from tile - 1 until an inclusive
+// prefix, returns the exclusive prefix of `tile` (same value in every lane)
+// and publishes tile's inclusive prefix (exclusive + aggregate).  The
+// tile's own aggregate must have been published before (lb_publish_agg), or
+// tile == 0.
+__device__ __forceinline__ unsigned long long lookback_resolve(unsigned long long *status, long long tile,
+                                                               unsigned long long aggregate, LbWindow &W,
+                                                               uint32_t limit, int32_t *d_status)
+{
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0)
+            st_relaxed_u64(&status[0], LB_INC | aggregate);
+        return 0;
+    }
+    unsigned long long excl = 0;
+    const long long base = tile - 1;   // nearest predecessor
+    long long g0 = base / LB_WIDE;     // its group
+    for (int round = 0;; round++) {
+        const long long g = g0 - lane;
+        if (round > 0) { // later rounds load here
+            if (g >= 0) {
+                const unsigned long long *p = status + g * LB_WIDE;
+#pragma unroll
+                for (int j = 0; j < LB_WIDE; j += 2)
+                    lb_load2(p + LB_WIDE - 2 - j, W.w[j + 1], W.w[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < LB_WIDE; j++)
+                    W.w[j] = LB_INC;
+            }
+        }
+        unsigned pend = 0;
+#pragma unroll
+        for (int j = 0; j < LB_WIDE; j++) {
+            const long long t = g * LB_WIDE + LB_WIDE - 1 - j;
+            if (t > base)
+                W.w[j] = LB_AGG; // the tile itself and later ones: neutral
+            if (g < 0)
+                W.w[j] = LB_INC;
+            pend |= ((W.w[j] >> 62) == 0 ? 1u : 0u) << j;
+        }
+        // bounded wait until every word of the lane holds a flag
+        for (uint32_t polls = 0; pend;) {
+            if (polls++ >= limit || ((polls & 63) == 0 && timed_out_already(d_status))) {
+                set_status(d_status, TDP_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(polls < 64 ? 20 : 200);
+#pragma unroll
+            for (int j = 0; j < LB_WIDE; j++)
+                if (pend >> j & 1u) {
+                    W.w[j] = ld_relaxed_u64(&status[g * LB_WIDE + LB_WIDE - 1 - j]);
+                    if ((W.w[j] >> 62) != 0)
+                        pend &= ~(1u << j);
+                }
+        }
+        // nearest inclusive word of the lane (a timed-out word counts as one)
+        int jinc = LB_WIDE;
+#pragma unroll
+        for (int j = LB_WIDE - 1; j >= 0; j--)
+            if ((W.w[j] >> 62) != 1)
+                jinc = j;
+        const unsigned inc_lanes = __ballot_sync(0xffffffffu, jinc < LB_WIDE);
+        const int stop = inc_lanes ? __ffs(inc_lanes) - 1 : 32;
+        unsigned long long contrib = 0;
+        if (lane <= stop) {
+            const int last = lane == stop ? jinc : LB_WIDE - 1;
+#pragma unroll
+            for (int j = 0; j < LB_WIDE; j++)
+                contrib += j <= last ? (W.w[j] & LB_VAL) : 0ull;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+        excl += contrib;
+        if (inc_lanes)
+            break;
+        g0 -= 32;
+    }
+    if (lane == 0)
+        st_relaxed_u64(&status[tile], LB_INC | ((excl + aggregate) & LB_VAL));
+    return excl;
+}
+
+// Publishes a tile's aggregate (one thread); tile 0 publishes its inclusive
+// prefix, which is its aggregate.
+__device__ __forceinline__ void lb_publish_agg(unsigned long long *status, long long tile, unsigned long long aggregate)
+{
+    st_relaxed_u64(&status[tile], (tile == 0 ? LB_INC : LB_AGG) | aggregate);
+}
+
+// Same contract as lookback_exclusive, with the wide window.
+__device__ __forceinline__ unsigned long long lookback_exclusive_wide(unsigned long long *status, long long tile,
+                                                                      unsigned long long aggregate, uint32_t limit,
+                                                                      int32_t *d_status)
+{
+    if ((threadIdx.x & 31) == 0)
+        lb_publish_agg(status, tile, aggregate);
+    LbWindow W;
+    lb_window_load(status, tile, W);
+    return lookback_resolve(status, tile, aggregate, W, limit, d_status);
 }
 
 } // namespace tdp

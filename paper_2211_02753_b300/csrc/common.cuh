@@ -423,6 +423,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
+// Grid-wide barrier of a cooperative launch: every block adds one to the
+// counter and waits (bounded) until all blocks of this round have.
+__device__ __forceinline__ void grid_barrier(unsigned *counter, unsigned target, uint32_t limit, int32_t *d_status)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        uint32_t polls = 0;
+        while (ld_relaxed_u32(counter) < target) {
+            if (polls++ >= limit) {
+                set_status(d_status, TDP_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(polls < 64 ? 32 : 256);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
 // --------------------------------------------------------- decoupled look-back
 //
 // Tile status word: bits 62..63 flag (0 = nothing yet, 1 = tile aggregate,

@@ -138,27 +138,6 @@ __device__ __forceinline__ void ft_stage(const PredSet &ps, unsigned char *stage
     }
 }
 
-// Grid-wide barrier of a cooperative launch: every block adds one to the
-// counter and waits (bounded) until all blocks of this round have.
-__device__ __forceinline__ void grid_barrier(unsigned *counter, unsigned target, uint32_t limit, int32_t *d_status)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(counter, 1u);
-        uint32_t polls = 0;
-        while (ld_relaxed_u32(counter) < target) {
-            if (polls++ >= limit) {
-                set_status(d_status, TDP_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(polls < 64 ? 32 : 256);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
 template <int STEPS>
 __global__ void __launch_bounds__(FT_THREADS, 4) filter_kernel(PredSet ps, GatherSet gs, long long n_host,
                                                             const long long *d_n, int32_t *out_rowid, long long cap,

@@ -341,42 +341,84 @@ __global__ void colsum_bf16_kernel(const bf16 *__restrict__ x, long long rows, i
     }
 }
 
-// out[i] = sum_b part[b * stride + i] in float64, in block order
-__global__ void partial_sum_kernel(const float *__restrict__ part, int nb, int n, size_t stride,
-                                   float *__restrict__ out)
+// out[i] = sum_b part[b * stride + i] in float64, in a fixed order: slice s
+// (of PS_SLICES) sums b = s, s + PS_SLICES, ... in order, then the slices are
+// added by a fixed tree.  A block covers 32 consecutive outputs.
+constexpr int PS_SLICES = 16;
+
+__global__ void __launch_bounds__(32 * PS_SLICES) partial_sum_kernel(const float *__restrict__ part, int nb, int n,
+                                                                     size_t stride, float *__restrict__ out)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
-        return;
-    double s = 0.0;
-    for (int b = 0; b < nb; b++)
-        s += part[(size_t)b * stride + i];
-    out[i] = (float)s;
+    __shared__ double s_acc[PS_SLICES][32];
+    const int e = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + e;
+    double acc = 0.0;
+    if (i < n) {
+        int b = sl;
+        for (; b + 3 * PS_SLICES < nb; b += 4 * PS_SLICES) {
+            const float a0 = part[(size_t)b * stride + i];
+            const float a1 = part[(size_t)(b + PS_SLICES) * stride + i];
+            const float a2 = part[(size_t)(b + 2 * PS_SLICES) * stride + i];
+            const float a3 = part[(size_t)(b + 3 * PS_SLICES) * stride + i];
+            acc += a0;
+            acc += a1;
+            acc += a2;
+            acc += a3;
+        }
+        for (; b < nb; b += PS_SLICES)
+            acc += part[(size_t)b * stride + i];
+    }
+    s_acc[sl][e] = acc;
+    __syncthreads();
+#pragma unroll
+    for (int h = PS_SLICES / 2; h > 0; h >>= 1) {
+        if (sl < h)
+            s_acc[sl][e] += s_acc[sl + h][e];
+        __syncthreads();
+    }
+    if (sl == 0 && i < n)
+        out[i] = (float)s_acc[0][e];
 }
 
-// conv1 weight and bias gradients: thread (co, kpos) over a chunk of output
-// pixels; partials [blocks][32*9 + 32].
-__global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const uint8_t *__restrict__ grids, long long ncell,
-                                   long long chunk, float *__restrict__ part)
+static inline unsigned psum_blocks(int n) { return (unsigned)((n + 31) / 32); }
+
+// conv1 weight and bias gradients.  Block b takes the cells [c0, c1) of its
+// share; thread (kp, co) (kp 0..8 a tap, 9 the bias) walks every output
+// pixel of each cell: dz1 of the pixel's 32 channels is one 64-byte read of
+// a warp, the input pixel of the tap a broadcast from the cell's image in
+// shared memory.  Partials [blocks][32*9 + 32].
+__global__ void __launch_bounds__(CH1 * 10) conv1_wgrad_kernel(const bf16 *__restrict__ dz1,
+                                                               const uint8_t *__restrict__ grids, long long ncell,
+                                                               long long cells_per_block, float *__restrict__ part)
 {
-    const int co = threadIdx.x % CH1, kp = threadIdx.x / CH1; // 0..9 (9 = bias)
-    const long long P = ncell * C1 * C1;
-    const long long beg = (long long)blockIdx.x * chunk, end = min(P, beg + chunk);
+    __shared__ float simg[CELL * CELL];
+    const int co = threadIdx.x % CH1, kp = threadIdx.x / CH1; // warp = one kp
+    const int ky = kp < 9 ? kp / 3 : 0, kx = kp < 9 ? kp % 3 : 0;
+    const long long c0 = (long long)blockIdx.x * cells_per_block, c1 = min(ncell, c0 + cells_per_block);
     float acc = 0.f;
-    const int ky = kp / 3, kx = kp % 3;
-    for (long long p = beg; p < end; p++) {
-        float d = bf2f(dz1[p * CH1 + co]);
+    for (long long c = c0; c < c1; c++) {
+        const long long g = c / CELLS_PER_GRID;
+        const int r = (int)(c % CELLS_PER_GRID) / GRID_W, cc = (int)(c % GRID_W);
+        const uint8_t *img = grids + g * (GRID_H * CELL) * (GRID_W * CELL) + (long long)(r * CELL) * (GRID_W * CELL) +
+                             cc * CELL;
+        __syncthreads(); // the previous cell's image is no longer read
+        for (int i = threadIdx.x; i < CELL * CELL; i += blockDim.x)
+            simg[i] = (float)img[(i / CELL) * (GRID_W * CELL) + i % CELL] * (1.0f / 255.0f);
+        __syncthreads();
+        const bf16 *d = dz1 + c * (C1 * C1 * CH1) + co;
         if (kp == 9) {
-            acc += d;
-            continue;
+#pragma unroll 4
+            for (int pix = 0; pix < C1 * C1; pix++)
+                acc += bf2f(d[pix * CH1]);
+        } else {
+            for (int oy = 0; oy < C1; oy++) {
+                const float *row = simg + (oy + ky) * CELL + kx;
+                const bf16 *drow = d + oy * C1 * CH1;
+#pragma unroll 2
+                for (int ox = 0; ox < C1; ox++)
+                    acc = fmaf(bf2f(drow[ox * CH1]), row[ox], acc);
+            }
         }
-        long long c = p / (C1 * C1);
-        int w = (int)(p % (C1 * C1)), oy = w / C1, ox = w % C1;
-        long long g = c / CELLS_PER_GRID;
-        int r = (int)(c % CELLS_PER_GRID) / GRID_W, cc = (int)(c % GRID_W);
-        uint8_t u = grids[g * (GRID_H * CELL) * (GRID_W * CELL) + (long long)(r * CELL + oy + ky) * (GRID_W * CELL) +
-                          cc * CELL + ox + kx];
-        acc = fmaf(d, (float)u * (1.0f / 255.0f), acc);
     }
     float *o = part + (size_t)blockIdx.x * (CH1 * 10);
     if (kp < 9)
@@ -717,9 +759,12 @@ tdp_status tdp_cnn_head(const void *h1, int64_t n_grids, const float *wfc2, cons
                                                            (bf16 *)dh1, part);
     if (targets) {
         const size_t per = NCLS * HID + NCLS + 1;
-        partial_sum_kernel<<<blocks_for(NCLS * HID, 256), 256, 0, s>>>(part, (int)n_grids, NCLS * HID, per, dwfc2);
-        partial_sum_kernel<<<1, 32, 0, s>>>(part + NCLS * HID, (int)n_grids, NCLS, per, dbfc2);
-        partial_sum_kernel<<<1, 32, 0, s>>>(part + NCLS * HID + NCLS, (int)n_grids, 1, per, loss);
+        partial_sum_kernel<<<psum_blocks(NCLS * HID), 32 * PS_SLICES, 0, s>>>(part, (int)n_grids, NCLS * HID, per,
+                                                                             dwfc2);
+        partial_sum_kernel<<<psum_blocks(NCLS), 32 * PS_SLICES, 0, s>>>(part + NCLS * HID, (int)n_grids, NCLS, per,
+                                                                        dbfc2);
+        partial_sum_kernel<<<psum_blocks(1), 32 * PS_SLICES, 0, s>>>(part + NCLS * HID + NCLS, (int)n_grids, 1, per,
+                                                                     loss);
     }
     return launch_status();
 }
@@ -767,7 +812,7 @@ tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, in
         float *bp = (float *)((char *)ws + align_up((size_t)FC1_WGRAD_SPLITS * HID * FEAT * sizeof(float), 256));
         int nb = (int)((n_cells + 63) / 64);
         colsum_bf16_kernel<<<nb, 256, 256 * sizeof(float), s>>>((const bf16 *)dh1, n_cells, HID, bp);
-        partial_sum_kernel<<<1, HID, 0, s>>>(bp, nb, HID, HID, dbfc1);
+        partial_sum_kernel<<<psum_blocks(HID), 32 * PS_SLICES, 0, s>>>(bp, nb, HID, HID, dbfc1);
     }
     return launch_status();
 }
@@ -810,8 +855,8 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
         tdp_status st = cerr(launch_gemm<64, 96, 4, 2>(la, lb, epi, CH2, 9 * CH1, K, sp, s));
         if (st != TDP_OK)
             return st;
-        partial_sum_kernel<<<blocks_for(CH2 * 9 * CH1, 256), 256, 0, s>>>(part, sp, CH2 * 9 * CH1, CH2 * 9 * CH1,
-                                                                           dw2);
+        partial_sum_kernel<<<psum_blocks(CH2 * 9 * CH1), 32 * PS_SLICES, 0, s>>>(part, sp, CH2 * 9 * CH1,
+                                                                                 CH2 * 9 * CH1, dw2);
     }
     // bias: sum of the pooled gradient (each pooled value lands on exactly one pixel)
     {
@@ -819,7 +864,7 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
         long long Q = n_cells * PO * PO;
         int nb = (int)((Q + 255) / 256);
         colsum_bf16_kernel<<<nb, 256, 256 * sizeof(float), s>>>((const bf16 *)dy2p, Q, CH2, bp);
-        partial_sum_kernel<<<1, CH2, 0, s>>>(bp, nb, CH2, CH2, db2);
+        partial_sum_kernel<<<psum_blocks(CH2), 32 * PS_SLICES, 0, s>>>(bp, nb, CH2, CH2, db2);
     }
     return launch_status();
 }
@@ -838,14 +883,14 @@ tdp_status tdp_cnn_conv1_bwd(const void *dz1, const uint8_t *grids, int64_t n_ce
     if (!ws || ws_bytes < tdp_cnn_conv1_bwd_workspace(n_cells))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    long long P = n_cells * C1 * C1;
-    int nb = std::max(1, std::min(4 * num_sms(), (int)((P + 1023) / 1024)));
-    long long chunk = (P + nb - 1) / nb;
+    // cells spread evenly over at most 4 blocks per SM
+    const long long cpb = (n_cells + 4ll * num_sms() - 1) / (4ll * num_sms());
+    const int nb = (int)((n_cells + cpb - 1) / cpb);
     float *part = (float *)ws;
-    conv1_wgrad_kernel<<<nb, CH1 * 10, 0, s>>>((const bf16 *)dz1, grids, n_cells, chunk, part);
+    conv1_wgrad_kernel<<<nb, CH1 * 10, 0, s>>>((const bf16 *)dz1, grids, n_cells, cpb, part);
     // each partial row: 288 weight sums, then the 32 bias sums
-    partial_sum_kernel<<<blocks_for(CH1 * 9, 256), 256, 0, s>>>(part, nb, CH1 * 9, CH1 * 10, dw1);
-    partial_sum_kernel<<<1, CH1, 0, s>>>(part + CH1 * 9, nb, CH1, CH1 * 10, db1);
+    partial_sum_kernel<<<psum_blocks(CH1 * 9), 32 * PS_SLICES, 0, s>>>(part, nb, CH1 * 9, CH1 * 10, dw1);
+    partial_sum_kernel<<<psum_blocks(CH1), 32 * PS_SLICES, 0, s>>>(part + CH1 * 9, nb, CH1, CH1 * 10, db1);
     return launch_status();
 }
 

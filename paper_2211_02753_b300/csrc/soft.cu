@@ -18,6 +18,8 @@
 namespace tdp {
 
 constexpr int SA_THREADS = 512;
+constexpr int SA_UNROLL = 2;        // row quads a thread loads ahead
+constexpr int SA_BLOCKS_PER_SM = 3; // resident blocks the register budget allows
 constexpr int SA_MAX_GROUPS = 4096;
 
 struct Sig {
@@ -67,7 +69,7 @@ __device__ __forceinline__ void soft_row(float x, float v, int g, float gm, cons
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(SA_THREADS) soft_reduce_kernel(const float *__restrict__ x,
+__global__ void __launch_bounds__(SA_THREADS, SA_BLOCKS_PER_SM) soft_reduce_kernel(const float *__restrict__ x,
                                                                  const float *__restrict__ v,
                                                                  const int32_t *__restrict__ gid,
                                                                  const float *__restrict__ theta,
@@ -112,11 +114,33 @@ __global__ void __launch_bounds__(SA_THREADS) soft_reduce_kernel(const float *__
         long long tail = sb;
         if (vec) {
             const long long nvec = (se - sb) / 4;
-            for (long long q = threadIdx.x; q < nvec; q += SA_THREADS) {
+            // SA_UNROLL quads a thread per pass, all of their loads issued
+            // before any row is reduced (bytes in flight for the HBM)
+            long long q = threadIdx.x;
+            for (; q + (SA_UNROLL - 1) * SA_THREADS < nvec; q += SA_UNROLL * SA_THREADS) {
+                float4 xx[SA_UNROLL], aa[SA_UNROLL];
+                int4 gg[SA_UNROLL];
+#pragma unroll
+                for (int u = 0; u < SA_UNROLL; u++) {
+                    const long long i = sb + 4 * (q + u * SA_THREADS);
+                    xx[u] = __ldcs((const float4 *)(x + i));
+                    aa[u] = __ldcs((const float4 *)(aux + i));
+                    gg[u] = __ldcs((const int4 *)(gid + i));
+                }
+#pragma unroll
+                for (int u = 0; u < SA_UNROLL; u++) {
+                    const long long i = sb + 4 * (q + u * SA_THREADS);
+                    soft_row<MODE>(xx[u].x, aa[u].x, gg[u].x, aa[u].x, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i, G);
+                    soft_row<MODE>(xx[u].y, aa[u].y, gg[u].y, aa[u].y, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 1, G);
+                    soft_row<MODE>(xx[u].z, aa[u].z, gg[u].z, aa[u].z, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 2, G);
+                    soft_row<MODE>(xx[u].w, aa[u].w, gg[u].w, aa[u].w, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 3, G);
+                }
+            }
+            for (; q < nvec; q += SA_THREADS) {
                 const long long i = sb + 4 * q;
-                float4 xx = __ldg((const float4 *)(x + i));
-                float4 aa = __ldg((const float4 *)(aux + i));
-                int4 gg = __ldg((const int4 *)(gid + i));
+                float4 xx = __ldcs((const float4 *)(x + i));
+                float4 aa = __ldcs((const float4 *)(aux + i));
+                int4 gg = __ldcs((const int4 *)(gid + i));
                 soft_row<MODE>(xx.x, aa.x, gg.x, aa.x, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i, G);
                 soft_row<MODE>(xx.y, aa.y, gg.y, aa.y, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 1, G);
                 soft_row<MODE>(xx.z, aa.z, gg.z, aa.z, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 2, G);
@@ -142,22 +166,54 @@ __global__ void __launch_bounds__(SA_THREADS) soft_reduce_kernel(const float *__
         out[g] = acc64[g];
 }
 
-// out[k][g] = scale * sum_b partial[b][k][g], summed over b in order, float64.
-__global__ void soft_combine_kernel(const double *__restrict__ partial, int nblocks, int G, int K, float scale,
-                                    float *__restrict__ out0, float *__restrict__ out1)
+// out[k][g] = scale * sum_b partial[b][k][g] in float64, in a fixed order:
+// slice s (of SC_SLICES) sums blocks b = s, s + SC_SLICES, ... in order, then
+// the slices are added by a fixed tree.  A block covers 32 consecutive
+// (k, g) entries (coalesced loads), each with SC_SLICES threads.
+constexpr int SC_SLICES = 16;
+
+__global__ void __launch_bounds__(32 * SC_SLICES) soft_combine_kernel(const double *__restrict__ partial, int nblocks,
+                                                                      int G, int K, float scale,
+                                                                      float *__restrict__ out0,
+                                                                      float *__restrict__ out1)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= K * G)
-        return;
+    __shared__ double s_acc[SC_SLICES][32];
+    const int e = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + e;
     double acc = 0.0;
-    for (int b = 0; b < nblocks; b++)
-        acc += partial[(size_t)b * K * G + t];
-    acc *= (double)scale;
-    if (t < G)
-        out0[t] = (float)acc;
-    else
-        out1[t - G] = (float)acc;
+    if (t < K * G) {
+        int b = sl;
+        for (; b + 3 * SC_SLICES < nblocks; b += 4 * SC_SLICES) {
+            const double a0 = partial[(size_t)b * K * G + t];
+            const double a1 = partial[(size_t)(b + SC_SLICES) * K * G + t];
+            const double a2 = partial[(size_t)(b + 2 * SC_SLICES) * K * G + t];
+            const double a3 = partial[(size_t)(b + 3 * SC_SLICES) * K * G + t];
+            acc += a0;
+            acc += a1;
+            acc += a2;
+            acc += a3;
+        }
+        for (; b < nblocks; b += SC_SLICES)
+            acc += partial[(size_t)b * K * G + t];
+    }
+    s_acc[sl][e] = acc;
+    __syncthreads();
+#pragma unroll
+    for (int h = SC_SLICES / 2; h > 0; h >>= 1) {
+        if (sl < h)
+            s_acc[sl][e] += s_acc[sl + h][e];
+        __syncthreads();
+    }
+    if (sl == 0 && t < K * G) {
+        const double r = s_acc[0][e] * (double)scale;
+        if (t < G)
+            out0[t] = (float)r;
+        else
+            out1[t - G] = (float)r;
+    }
 }
+
+static inline unsigned combine_blocks(int K, int G) { return (unsigned)((K * G + 31) / 32); }
 
 __global__ void soft_filter_fwd_kernel(const float *__restrict__ x, const int32_t *__restrict__ gid,
                                        const float *__restrict__ theta, float inv_tau, long long n,
@@ -191,7 +247,8 @@ static SoftGrid soft_grid(long long n, int G, int n64, int n32)
 {
     SoftGrid sg;
     sg.smem = (size_t)G * (n64 * sizeof(double) + n32 * sizeof(float));
-    int per_sm = sg.smem <= 48 * 1024 ? 2 : 1;
+    // resident blocks per SM: registers allow SA_BLOCKS_PER_SM, shared memory as it allows
+    int per_sm = (int)std::max<size_t>(1, std::min<size_t>(SA_BLOCKS_PER_SM, (200 * 1024) / std::max<size_t>(sg.smem, 1)));
     long long want = (n + 4ll * SA_THREADS * 8 - 1) / (4ll * SA_THREADS * 8);
     long long maxb = (long long)num_sms() * per_sm;
     sg.blocks = (int)std::max(1ll, std::min(want, maxb));
@@ -214,8 +271,9 @@ using namespace tdp;
 extern "C" size_t tdp_soft_workspace(int64_t n, int32_t n_groups)
 {
     (void)n;
-    // per-block fp64 partials: at most 2 blocks per SM, 2 arrays of n_groups
-    return align_up((size_t)2 * num_sms() * 2 * (size_t)std::max(1, n_groups) * sizeof(double), 256);
+    // per-block fp64 partials: at most SA_BLOCKS_PER_SM blocks per SM, 2
+    // arrays of n_groups
+    return align_up((size_t)SA_BLOCKS_PER_SM * num_sms() * 2 * (size_t)std::max(1, n_groups) * sizeof(double), 256);
 }
 
 static tdp_status soft_check(const float *x, const int32_t *gid, const float *theta, float tau, int64_t n, int32_t G)
@@ -258,7 +316,7 @@ extern "C" tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int
     double *partial = (double *)ws;
     soft_reduce_kernel<MODE_AGG_FWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
         x, v, gid, theta, nullptr, nullptr, 1.0f / tau, n, G, sg.chunk, partial, nullptr, nullptr);
-    soft_combine_kernel<<<(2 * G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
+    soft_combine_kernel<<<combine_blocks(2, G), 32 * SC_SLICES, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
     return launch_status();
 }
 
@@ -281,8 +339,8 @@ extern "C" tdp_status tdp_soft_agg_bwd(const float *x, const float *v, const int
     double *partial = (double *)ws;
     soft_reduce_kernel<MODE_AGG_BWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
         x, v, gid, theta, gsum, gcnt, 1.0f / tau, n, G, sg.chunk, partial, grad_x, grad_v);
-    soft_combine_kernel<<<(G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau, grad_theta,
-                                                        nullptr);
+    soft_combine_kernel<<<combine_blocks(1, G), 32 * SC_SLICES, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau,
+                                                                           grad_theta, nullptr);
     return launch_status();
 }
 
@@ -304,8 +362,8 @@ extern "C" tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, co
     double *partial = (double *)ws;
     soft_reduce_kernel<MODE_FILTER_BWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
         x, nullptr, gid, theta, grad_mask, nullptr, 1.0f / tau, n, G, sg.chunk, partial, grad_x, nullptr);
-    soft_combine_kernel<<<(G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau, grad_theta,
-                                                        nullptr);
+    soft_combine_kernel<<<combine_blocks(1, G), 32 * SC_SLICES, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau,
+                                                                           grad_theta, nullptr);
     return launch_status();
 }
 
@@ -375,6 +433,6 @@ extern "C" tdp_status tdp_soft_agg_fwd_noalloc(const float *x, const float *v, c
     // reads them, so nothing in the shared scratch has to start at zero
     soft_reduce_kernel<MODE_AGG_FWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
         x, v, gid, theta, nullptr, nullptr, 1.0f / tau, n, G, sg.chunk, partial, nullptr, nullptr);
-    soft_combine_kernel<<<(2 * G + 255) / 256, 256, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
+    soft_combine_kernel<<<combine_blocks(2, G), 32 * SC_SLICES, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
     return launch_status();
 }

@@ -107,8 +107,8 @@ def run_reference(args):
 # built from.  The capture ran the plan at 1/4 scale; every term of the
 # probe's traffic grows with the fact rows, so it is scaled by them.
 TRAFFIC = {
-    "join_probe": {"bytes_per_fact_row": (339.988736e6 + 28.8256e6) / 15e6,
-                   "src": "paper_2211_02753_b300/csrc/join.cu", "sha1": "3b0679075d24",
+    "join_probe": {"bytes_per_fact_row": (328.591104e6 + 7.65696e6) / 15e6,
+                   "src": "paper_2211_02753_b300/csrc/join.cu", "sha1": "3fbda6a2fcd7",
                    "capture": "profiles/join_probe_kernel_15M_fact_rows.md"},
 }
 

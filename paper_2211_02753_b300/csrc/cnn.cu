@@ -406,17 +406,22 @@ __global__ void __launch_bounds__(CH1 * 10) conv1_wgrad_kernel(const bf16 *__res
             simg[i] = (float)img[(i / CELL) * (GRID_W * CELL) + i % CELL] * (1.0f / 255.0f);
         __syncthreads();
         const bf16 *d = dz1 + c * (C1 * C1 * CH1) + co;
-        if (kp == 9) {
-#pragma unroll 4
-            for (int pix = 0; pix < C1 * C1; pix++)
-                acc += bf2f(d[pix * CH1]);
-        } else {
-            for (int oy = 0; oy < C1; oy++) {
-                const float *row = simg + (oy + ky) * CELL + kx;
-                const bf16 *drow = d + oy * C1 * CH1;
-#pragma unroll 2
+        for (int oy = 0; oy < C1; oy++) {
+            // the row's 26 gradients loaded before any is used (26 loads in flight)
+            const bf16 *drow = d + oy * C1 * CH1;
+            float dv[C1];
+#pragma unroll
+            for (int ox = 0; ox < C1; ox++)
+                dv[ox] = bf2f(drow[ox * CH1]);
+            if (kp == 9) {
+#pragma unroll
                 for (int ox = 0; ox < C1; ox++)
-                    acc = fmaf(bf2f(drow[ox * CH1]), row[ox], acc);
+                    acc += dv[ox];
+            } else {
+                const float *row = simg + (oy + ky) * CELL + kx;
+#pragma unroll
+                for (int ox = 0; ox < C1; ox++)
+                    acc = fmaf(dv[ox], row[ox], acc);
             }
         }
     }

@@ -40,10 +40,13 @@ extern "C" {
 tdp_status tdp_cnn_conv1_fwd(const uint8_t *grids, int64_t n_grids, const float *w1, const float *b1, void *y1,
                              tdp_stream_t stream);
 
-/* conv2 + bias + ReLU + 2x2 max-pool as one implicit GEMM on the tensor cores
- * (bf16 operands, fp32 accumulation); writes y2 and argmax. */
+/* conv2 + bias + ReLU + 2x2 max-pool as one implicit GEMM on the 5th-gen
+ * tensor cores (tcgen05: bf16 operands staged in shared memory, fp32
+ * accumulator in tensor memory); writes y2 and argmax.  y1, w2, y2 and argmax
+ * must be 16-byte aligned (TDP_ERR_INVALID_ARG otherwise).  A bounded device
+ * wait that runs out sets TDP_ERR_TIMEOUT in *d_status (nullable). */
 tdp_status tdp_cnn_conv2_pool_fwd(const void *y1, int64_t n_cells, const void *w2, const float *b2, void *y2,
-                                  uint8_t *argmax, tdp_stream_t stream);
+                                  uint8_t *argmax, int32_t *d_status, tdp_stream_t stream);
 
 /* Workspace bytes of tdp_cnn_fc1_fwd. */
 size_t tdp_cnn_fc1_fwd_workspace(int64_t n_cells);

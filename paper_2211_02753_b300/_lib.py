@@ -90,7 +90,7 @@ SIGNATURES = {
     "tdp_soft_agg_bwd": (_st, [_p, _p, _p, _p, _f, _i64, _i32, _p, _p, _p, _p, _p, _p, _sz, _p]),
     # glyph CNN of the trainable query (include/tdp_cnn.h)
     "tdp_cnn_conv1_fwd": (_st, [_p, _i64, _p, _p, _p, _p]),
-    "tdp_cnn_conv2_pool_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _p]),
+    "tdp_cnn_conv2_pool_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _p, _p]),
     "tdp_cnn_fc1_fwd_workspace": (_sz, [_i64]),
     "tdp_cnn_fc1_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _sz, _p]),
     "tdp_cnn_head_workspace": (_sz, [_i64]),

@@ -44,6 +44,8 @@ class GlyphQuery:
         self.lr, self.betas, self.eps, self.warmup = lr, betas, eps, warmup
         self.t = 0
         self._buf = {}
+        # device status word of the kernels that wait on the device (bounded waits)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.dev)
 
     # -------------------------------------------------------------- buffers
     def _buffers(self, n_grids: int) -> dict:
@@ -87,7 +89,7 @@ class GlyphQuery:
         ws, wsn = _ptr(b["ws"]), b["ws"].numel()
         L.call("tdp_cnn_conv1_fwd", _ptr(grids), n, _ptr(p["conv1_w"]), _ptr(p["conv1_b"]), _ptr(b["y1"]), s)
         L.call("tdp_cnn_conv2_pool_fwd", _ptr(b["y1"]), nc, _ptr(self.bf["conv2_w"]), _ptr(p["conv2_b"]),
-               _ptr(b["y2"]), _ptr(b["argmax"]), s)
+               _ptr(b["y2"]), _ptr(b["argmax"]), _ptr(self.status), s)
         L.call("tdp_cnn_fc1_fwd", _ptr(b["y2"]), nc, _ptr(self.bf["fc1_w"]), _ptr(p["fc1_b"]), _ptr(b["h1"]), ws,
                wsn, s)
         g = self.g

@@ -19,6 +19,7 @@
 // epilogue; no operand is transposed or materialised in im2col form.
 #include "cnn_gemm.cuh"
 #include "common.cuh"
+#include "umma.cuh"
 #include "tdp_cnn.h"
 
 namespace tdp {
@@ -99,24 +100,6 @@ struct LoadMN { // MN-major: stored [k][ld], the operand's rows contiguous
         if (k >= kend || row >= rows)
             return nullptr;
         return p + (size_t)k * ld + row;
-    }
-};
-
-// conv2 forward A: rows = output pixels in pool-window-major order
-// (cell, py, px, dy, dx); k = (ky*3 + kx)*32 + ci; source y1 [cell][26][26][32].
-struct LoadConv2A {
-    static constexpr bool MN_MAJOR = false, REG = false;
-    const bf16 *y1;
-    int M;
-    __device__ const void *ptr(int r, int kc, int m0, int k0, int kend) const
-    {
-        int m = m0 + r, k = k0 + kc * 8;
-        if (m >= M || k >= kend)
-            return nullptr;
-        int cell = m / (C2 * C2), w = m % (C2 * C2), win = w >> 2, pos = w & 3;
-        int oy = 2 * (win / PO) + (pos >> 1), ox = 2 * (win % PO) + (pos & 1);
-        int kp = k >> 5, ci = k & 31, ky = kp / 3, kx = kp % 3;
-        return y1 + (((size_t)cell * C1 + oy + ky) * C1 + ox + kx) * CH1 + ci;
     }
 };
 
@@ -209,47 +192,6 @@ struct LoadConv2WgradB {
 
 // -------------------------------------------------------------- epilogues
 
-// conv2 forward: bias + ReLU + 2x2 max-pool over 4 consecutive rows (lanes
-// 4 apart hold consecutive rows of a fragment).  First maximum wins.
-struct EpiConv2Pool {
-    const float *bias;
-    bf16 *y2;
-    uint8_t *argmax;
-    int M;
-    __device__ void operator()(int m, int n, float v0, float v1, int) const
-    {
-        v0 = fmaxf(v0 + bias[n], 0.f);
-        v1 = fmaxf(v1 + bias[n + 1], 0.f);
-        const int pos = m & 3; // lane bits 2..3 == row within the window
-        float b0 = v0, b1 = v1;
-        int a0 = pos, a1 = pos;
-#pragma unroll
-        for (int o = 4; o <= 8; o <<= 1) {
-            float c0 = __shfl_xor_sync(0xffffffffu, b0, o);
-            float c1 = __shfl_xor_sync(0xffffffffu, b1, o);
-            int d0 = __shfl_xor_sync(0xffffffffu, a0, o);
-            int d1 = __shfl_xor_sync(0xffffffffu, a1, o);
-            if (c0 > b0 || (c0 == b0 && d0 < a0)) {
-                b0 = c0;
-                a0 = d0;
-            }
-            if (c1 > b1 || (c1 == b1 && d1 < a1)) {
-                b1 = c1;
-                a1 = d1;
-            }
-        }
-        if (pos == 0 && m < M) {
-            size_t q = (size_t)(m >> 2);
-            __nv_bfloat162 o2;
-            o2.x = __float2bfloat16_rn(b0);
-            o2.y = __float2bfloat16_rn(b1);
-            *(__nv_bfloat162 *)(y2 + q * CH2 + n) = o2;
-            argmax[q * CH2 + n] = (uint8_t)a0;
-            argmax[q * CH2 + n + 1] = (uint8_t)a1;
-        }
-    }
-};
-
 struct EpiPartialF32 { // out[split][m][ldo]
     float *out;
     int M, ldo;
@@ -294,6 +236,196 @@ static cudaError_t launch_gemm(const LA &la, const LB &lb, const EPI &epi, int M
     dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, splits);
     kern<<<grid, GTHREADS, smem, s>>>(la, lb, epi, M, N, K, kps);
     return cudaGetLastError();
+}
+
+// ------------------------------------------ conv2 forward on tcgen05
+//
+// conv2 + bias + ReLU + 2x2 max-pool on the 5th-gen tensor cores as nine
+// accumulating GEMMs, one per tap, over shifted views of one input patch.
+// Output pixels of a cell are taken in raster order with the input's row
+// pitch of 26 (columns 24 and 25 of each row are computed and discarded), so
+// output pixel q' = 26*oy + ox reads input pixel q' + 26*ky + kx for tap
+// (ky, kx): the A operand of a tap is the patch seen from a start row moved by
+// 26*ky + kx.  A tile is two output row-pairs of one cell (104 useful rows of
+// the 128-row MMA); its patch is the 182 input pixels from row 52*t of the
+// cell (zero past the cell's 676), stored K-major with one 16-byte core-matrix
+// row per (pixel, 8 channels): plane kc (channels 8kc..8kc+7) holds every
+// pixel at 16 bytes apart, so an 8-row group is 128 bytes (SBO) and the next
+// 8 channels one plane (LBO) further.  W2 of all nine taps stays in shared
+// memory for the CTA's whole life (persistent CTAs, tiles in grid-stride
+// order).  Per tile: 18 K16 MMAs into a 64-column fp32 accumulator in tensor
+// memory, issued by one thread and committed to an mbarrier; the accumulator
+// then goes through shared memory (a window's four rows sit in different
+// warps) for bias + ReLU + the window maximum and its first arg-max.  Patches
+// and accumulators are double-buffered: while a tile is pooled, the next
+// tile's MMAs run on the tensor cores and the patch after it is in flight.  Every wait is bounded; a wait that runs out sets
+// TDP_ERR_TIMEOUT in d_status.
+constexpr int C2_THREADS = 256; // warps w and w + 4 share TMEM lanes 32(w%4).., each half of the columns
+constexpr int C2_PATCH_ROWS = 192;                  // >= 128 + 2*26 + 2 = 182, whole 8-row groups
+constexpr int C2_PLANE = C2_PATCH_ROWS * 16;        // bytes of one 8-channel plane
+constexpr int C2_PATCH_BYTES = 4 * C2_PLANE;        // 32 channels
+constexpr int C2_W_TAP_BYTES = CH2 * CH1 * 2;       // W2 of one tap, [64 co][32 ci]
+constexpr int C2_W_BYTES = 9 * C2_W_TAP_BYTES;
+constexpr int C2_ACC_PITCH = CH2 + 4;               // floats per staged accumulator row
+constexpr int C2_ACC_BYTES = 128 * C2_ACC_PITCH * 4; // the accumulator staged for the pool
+constexpr int C2_TILES_PER_CELL = C2 / 4;           // 6 tiles of 2 row-pairs
+constexpr uint32_t C2_TMEM_COLS = 64;
+
+__global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 *__restrict__ y1,
+                                                                     const bf16 *__restrict__ w2,
+                                                                     const float *__restrict__ bias, bf16 *y2,
+                                                                     uint8_t *argmax, long long ntiles,
+                                                                     int32_t *d_status, uint32_t limit)
+{
+    extern __shared__ __align__(1024) unsigned char c2_smem[];
+    unsigned char *sw = c2_smem;                          // W2, 9 taps
+    unsigned char *sp = c2_smem + C2_W_BYTES;             // two patches
+    float *sacc = (float *)(sp + 2 * C2_PATCH_BYTES);     // [128][64] accumulator of the tile being pooled
+    __shared__ __align__(8) uint64_t s_mma;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(16) float s_bias[CH2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(128, CH2);
+
+    if (tid < CH2)
+        s_bias[tid] = bias[tid];
+    if (tid == 0)
+        mbar_init(&s_mma, 1);
+    if (warp == 0) {
+        umma::tmem_alloc(&s_tmem, 2 * C2_TMEM_COLS); // two accumulators
+        umma::fence_before_sync();
+    }
+    // W2 [co][ky][kx][ci] -> tap t = ky*3 + kx: K-major [co][ci] core matrices
+    for (int c = tid; c < 9 * CH2 * 4; c += C2_THREADS) {
+        const int t = c / (CH2 * 4), co = (c / 4) % CH2, kc = c % 4;
+        cnn::cp_async16(sw + t * C2_W_TAP_BYTES + umma::chunk_off(co, kc, 4), w2 + ((size_t)co * 9 + t) * CH1 + kc * 8,
+                        true);
+    }
+    // the patch of a tile: pixel p0 + r (r < 192) of its cell, 8 channels per 16-byte chunk
+    auto load_patch = [&](long long tile, int buf) {
+        const long long cell = tile / C2_TILES_PER_CELL;
+        const int p0 = (int)(tile % C2_TILES_PER_CELL) * 4 * C1;
+        const bf16 *src = y1 + (size_t)cell * C1 * C1 * CH1;
+        unsigned char *dst = sp + buf * C2_PATCH_BYTES;
+        for (int c = tid; c < C2_PATCH_ROWS * 4; c += C2_THREADS) {
+            const int r = c >> 2, kc = c & 3;
+            const int pix = p0 + r;
+            const bool in = pix < C1 * C1;
+            cnn::cp_async16(dst + kc * C2_PLANE + r * 16, in ? src + (size_t)pix * CH1 + kc * 8 : nullptr, in);
+        }
+    };
+    // the 18 MMAs of a tile (one thread): patch buffer -> accumulator buffer
+    auto issue = [&](int buf, uint32_t acc) {
+        const uint32_t aw = smem_addr(sw), ap = smem_addr(sp + buf * C2_PATCH_BYTES);
+        umma::fence_after_sync();
+#pragma unroll 1
+        for (int tap = 0; tap < 9; tap++) {
+            const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3) * 16; // start row 26*ky + kx
+#pragma unroll
+            for (int j = 0; j < 2; j++) // channels 16j..16j+15: planes 2j, 2j+1
+                umma::mma_bf16(acc, umma::smem_desc(ap + shift + 2 * j * C2_PLANE, C2_PLANE, 128),
+                               umma::smem_desc(aw + tap * C2_W_TAP_BYTES + j * 256, 128, 512), idesc,
+                               tap > 0 || j > 0);
+        }
+        umma::commit(&s_mma);
+    };
+
+    long long tile = blockIdx.x;
+    if (tile < ntiles)
+        load_patch(tile, 0);
+    cnn::cp_async_commit();
+    cnn::cp_async_wait<0>();
+    fence_proxy_async_smem(); // W2 and the first patch visible to the tensor cores
+    __syncthreads();          // ... and the mbarrier, tensor-memory address and bias
+    umma::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    if (tile < ntiles && tid == 0)
+        issue(0, tmem);
+    bool ok = true;
+    uint32_t phase = 0;
+
+    for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
+        const int buf = it & 1;
+        const long long next = tile + gridDim.x;
+        // prefetch the next patch into the other buffer (its last reader, the
+        // previous tile's MMAs, completed before this tile's were issued)
+        if (next < ntiles)
+            load_patch(next, buf ^ 1);
+        cnn::cp_async_commit();
+        // this tile's MMAs
+        if (!mbar_wait(&s_mma, phase, limit))
+            ok = false;
+        phase ^= 1u;
+        umma::fence_after_sync();
+        // issue the next tile's MMAs into the other accumulator before pooling this one
+        cnn::cp_async_wait<0>();
+        fence_proxy_async_smem();
+        umma::fence_before_sync();
+        __syncthreads(); // next patch complete; every thread past this tile's MMA wait
+        if (next < ntiles && tid == 0)
+            issue(buf ^ 1, tmem + (uint32_t)((buf ^ 1) * C2_TMEM_COLS));
+        // accumulator rows (TMEM lane = row) to shared memory: warp w takes
+        // lanes 32(w%4).. and columns 32(w/4).. (row pitch C2_ACC_PITCH: the
+        // lanes' 16-byte stores hit distinct banks)
+        const int lq = warp & 3, ch = (warp >> 2) * 32;
+        const uint32_t acc = tmem + (uint32_t)(buf * C2_TMEM_COLS) + ((uint32_t)(32 * lq) << 16);
+#pragma unroll 1
+        for (int cb = ch; cb < ch + 32; cb += 16) {
+            float v[16];
+            umma::ld_16cols(acc + cb, v);
+            float4 *dst = (float4 *)(sacc + (32 * lq + lane) * C2_ACC_PITCH + cb);
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+        umma::fence_before_sync();
+        __syncthreads(); // accumulator staged
+        // pool: 2 row-pairs x 12 windows x 16 groups of 4 channels (lanes read
+        // consecutive 16-byte chunks); window (P, px) = rows 52P + 2px +
+        // {0, 1, 26, 27}, (dy, dx) = (0,0) (0,1) (1,0) (1,1)
+        const long long cell = tile / C2_TILES_PER_CELL;
+        const int t = (int)(tile % C2_TILES_PER_CELL);
+        for (int o = tid; o < 2 * PO * (CH2 / 4); o += C2_THREADS) {
+            const int cg = o % (CH2 / 4), w = o / (CH2 / 4), P = w / PO, px = w % PO;
+            const int r0 = 52 * P + 2 * px;
+            const int rows[4] = {r0, r0 + 1, r0 + C1, r0 + C1 + 1};
+            const float4 bb = *(const float4 *)(s_bias + cg * 4);
+            float best[4];
+            int arg[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const float4 a = *(const float4 *)(sacc + rows[i] * C2_ACC_PITCH + cg * 4);
+                const float x[4] = {fmaxf(a.x + bb.x, 0.f), fmaxf(a.y + bb.y, 0.f), fmaxf(a.z + bb.z, 0.f),
+                                    fmaxf(a.w + bb.w, 0.f)};
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (i == 0 || x[c] > best[c]) { // first maximum wins
+                        best[c] = x[c];
+                        arg[c] = i;
+                    }
+            }
+            __align__(8) bf16 ov[4];
+            __align__(4) uint8_t oa[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                ov[c] = __float2bfloat16_rn(best[c]);
+                oa[c] = (uint8_t)arg[c];
+            }
+            const size_t qo = ((size_t)cell * PO + 2 * t + P) * PO + px; // pooled pixel (cell, py, px)
+            *(uint2 *)(y2 + qo * CH2 + cg * 4) = *(const uint2 *)ov;
+            *(uint32_t *)(argmax + qo * CH2 + cg * 4) = *(const uint32_t *)oa;
+        }
+        __syncthreads(); // the staged accumulator is read
+    }
+    cnn::cp_async_wait<0>();
+    if (!ok)
+        set_status(d_status, TDP_ERR_TIMEOUT);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, 2 * C2_TMEM_COLS);
+    }
 }
 
 // ---------------------------------------------------------- reductions
@@ -698,17 +830,31 @@ tdp_status tdp_cnn_conv1_fwd(const uint8_t *grids, int64_t n_grids, const float 
 }
 
 tdp_status tdp_cnn_conv2_pool_fwd(const void *y1, int64_t n_cells, const void *w2, const float *b2, void *y2,
-                                  uint8_t *argmax, tdp_stream_t stream)
+                                  uint8_t *argmax, int32_t *d_status, tdp_stream_t stream)
 {
     if (n_cells < 0 || (n_cells > 0 && (!y1 || !w2 || !b2 || !y2 || !argmax)))
         return TDP_ERR_INVALID_ARG;
     if (n_cells == 0)
         return TDP_OK;
-    const int M = (int)(n_cells * C2 * C2);
-    LoadConv2A la{(const bf16 *)y1, M};
-    LoadK lb{(const bf16 *)w2, CH2, 9 * CH1};
-    EpiConv2Pool epi{b2, (bf16 *)y2, argmax, M};
-    return cerr(launch_gemm<128, 64, 4, 2>(la, lb, epi, M, CH2, 9 * CH1, 1, (cudaStream_t)stream));
+    // 16-byte alignment of every operand and output row (vector stores, cp.async)
+    if (((uintptr_t)y1 | (uintptr_t)w2 | (uintptr_t)y2 | (uintptr_t)argmax) % 16)
+        return TDP_ERR_INVALID_ARG;
+    const long long ntiles = n_cells * C2_TILES_PER_CELL;
+    const size_t smem = (size_t)C2_W_BYTES + 2 * C2_PATCH_BYTES + C2_ACC_BYTES;
+    if (cudaFuncSetAttribute(conv2_pool_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(conv2_pool_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return TDP_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv2_pool_umma_kernel, C2_THREADS, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return TDP_ERR_CUDA;
+    const long long grid = std::min<long long>(ntiles, (long long)per_sm * num_sms());
+    conv2_pool_umma_kernel<<<(unsigned)grid, C2_THREADS, smem, (cudaStream_t)stream>>>(
+        (const bf16 *)y1, (const bf16 *)w2, b2, (bf16 *)y2, argmax, ntiles, d_status, spin_limit());
+    return launch_status();
 }
 
 size_t tdp_cnn_fc1_fwd_workspace(int64_t n_cells)

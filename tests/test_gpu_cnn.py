@@ -66,8 +66,11 @@ def test_conv2_pool_layer(ncell):
     y2 = torch.empty((ncell, 9216), dtype=torch.bfloat16, device=DEV)
     am = torch.empty((ncell, 9216), dtype=torch.uint8, device=DEV)
     g_y1, g_w2, g_b2 = to_bf16_dev(y1), to_bf16_dev(w2), torch.from_numpy(b2).to(DEV)
-    L.call("tdp_cnn_conv2_pool_fwd", _ptr(g_y1), ncell, _ptr(g_w2), _ptr(g_b2), _ptr(y2), _ptr(am), _stream())
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    L.call("tdp_cnn_conv2_pool_fwd", _ptr(g_y1), ncell, _ptr(g_w2), _ptr(g_b2), _ptr(y2), _ptr(am), _ptr(st),
+           _stream())
     torch.cuda.synchronize()
+    assert int(st.item()) == 0
     pooled, arg, a2 = O.conv2_relu_pool(y1, w2, b2.astype(np.float64))
     ref = bf16_np(pooled).reshape(ncell, 9216)
     got = y2.float().cpu().numpy()

@@ -95,9 +95,14 @@ size_t tdp_cnn_conv2_bwd_workspace(int64_t n_cells);
  *   dz1 bf16 [n_cells][26][26][32] = (conv2 transposed) masked by y1 > 0
  *       (optional: NULL skips the data gradient)
  *   dw2 fp32 [64][3][3][32], db2 fp32 [64]
+ * The data gradient runs on the 5th-gen tensor cores (tcgen05, nine
+ * accumulating GEMMs over shifted views of one gradient patch); dy2p,
+ * argmax, y1 and dz1 must be 16-byte aligned.  A bounded device wait that
+ * runs out sets TDP_ERR_TIMEOUT in *d_status (nullable).
  */
 tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void *y1, const void *w2, int64_t n_cells,
-                             void *dz1, float *dw2, float *db2, void *ws, size_t ws_bytes, tdp_stream_t stream);
+                             void *dz1, float *dw2, float *db2, void *ws, size_t ws_bytes, int32_t *d_status,
+                             tdp_stream_t stream);
 
 /* Workspace bytes of tdp_cnn_conv1_bwd. */
 size_t tdp_cnn_conv1_bwd_workspace(int64_t n_cells);

@@ -98,7 +98,7 @@ SIGNATURES = {
     "tdp_cnn_fc1_bwd_workspace": (_sz, [_i64]),
     "tdp_cnn_fc1_bwd": (_st, [_p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p]),
     "tdp_cnn_conv2_bwd_workspace": (_sz, [_i64]),
-    "tdp_cnn_conv2_bwd": (_st, [_p, _p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p]),
+    "tdp_cnn_conv2_bwd": (_st, [_p, _p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_cnn_conv1_bwd_workspace": (_sz, [_i64]),
     "tdp_cnn_conv1_bwd": (_st, [_p, _p, _i64, _p, _p, _p, _sz, _p]),
     "tdp_adam_step": (_st, [_p, _p, _p, _p, _p, _p, _i32, _i32, _f, _f, _f, _f, _p]),

@@ -112,7 +112,7 @@ class GlyphQuery:
         L.call("tdp_cnn_fc1_bwd", _ptr(b["dh1"]), _ptr(b["y2"]), _ptr(self.bf["fc1_w"]), nc, _ptr(b["dy2p"]),
                _ptr(g["fc1_w"]), _ptr(g["fc1_b"]), ws, wsn, s)
         L.call("tdp_cnn_conv2_bwd", _ptr(b["dy2p"]), _ptr(b["argmax"]), _ptr(b["y1"]), _ptr(self.bf["conv2_w"]), nc,
-               _ptr(b["dz1"]), _ptr(g["conv2_w"]), _ptr(g["conv2_b"]), ws, wsn, s)
+               _ptr(b["dz1"]), _ptr(g["conv2_w"]), _ptr(g["conv2_b"]), ws, wsn, _ptr(self.status), s)
         L.call("tdp_cnn_conv1_bwd", _ptr(b["dz1"]), _ptr(grids), nc, _ptr(g["conv1_w"]), _ptr(g["conv1_b"]), ws,
                wsn, s)
 

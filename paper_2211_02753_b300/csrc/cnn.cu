@@ -124,42 +124,6 @@ __device__ __forceinline__ uint4 pool_grad8(const bf16 *dy2p, const uint8_t *arg
     return make_uint4(gw[0], gw[1], gw[2], gw[3]);
 }
 
-// conv2 dgrad A: rows = input pixels (cell, y, x) raster; k = (ky*3+kx)*64 + co;
-// value = dz2[cell][y-ky][x-kx][co] (0 outside the 24x24 output).
-struct LoadConv2DgradA {
-    static constexpr bool MN_MAJOR = false, REG = true;
-    const bf16 *dy2p;
-    const uint8_t *argmax;
-    int M;
-    __device__ uint4 val(int r, int kc, int m0, int k0, int kend) const
-    {
-        int m = m0 + r, k = k0 + kc * 8;
-        if (m >= M || k >= kend)
-            return make_uint4(0, 0, 0, 0);
-        int cell = m / (C1 * C1), w = m % (C1 * C1), y = w / C1, x = w % C1;
-        int kp = k >> 6, co = k & 63, ky = kp / 3, kx = kp % 3;
-        int oy = y - ky, ox = x - kx;
-        if (oy < 0 || oy >= C2 || ox < 0 || ox >= C2)
-            return make_uint4(0, 0, 0, 0);
-        return pool_grad8(dy2p, argmax, cell, oy, ox, co);
-    }
-};
-
-// conv2 dgrad B: B(n = ci, k = (ky,kx,co)) = W2[co][ky][kx][ci], stored so that
-// ci is contiguous: MN-major chunk at k.
-struct LoadConv2DgradB {
-    static constexpr bool MN_MAJOR = true, REG = false;
-    const bf16 *w2;
-    __device__ const void *ptr(int kk, int rc, int n0, int k0, int kend) const
-    {
-        int k = k0 + kk, ci = n0 + rc * 8;
-        if (k >= kend || ci >= CH1)
-            return nullptr;
-        int kp = k >> 6, co = k & 63;
-        return w2 + ((size_t)co * 9 + kp) * CH1 + ci;
-    }
-};
-
 // conv2 wgrad A: A(m = co, k = output pixel raster (cell, oy, ox)) = dz2; MN-major (co contiguous)
 struct LoadConv2WgradA {
     static constexpr bool MN_MAJOR = true, REG = true;
@@ -425,6 +389,152 @@ __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 
     if (warp == 0) {
         umma::fence_after_sync();
         umma::tmem_dealloc(tmem, 2 * C2_TMEM_COLS);
+    }
+}
+
+// ------------------------------------ conv2 data gradient on tcgen05
+//
+// dz1[cell][y][x][ci] = (y1 > 0) * sum_{ky,kx,co} dz2[cell][y-ky][x-kx][co]
+// W2[co][ky][kx][ci], dz2 the pre-pool gradient (the pooled gradient at its
+// window's arg-max pixel, 0 elsewhere; zero outside the 24x24 output).  As in
+// the forward, nine accumulating GEMMs over shifted views of one patch:
+// input pixels are taken in raster order with pitch 28 over a zero-padded
+// 28 x 28 grid dzp (dzp[a][b] = dz2[a-2][b-2]), so pixel m' = 28y + x reads
+// dzp[m' + 28(2-ky) + (2-kx)] for tap (ky, kx); columns 26, 27 are dropped.
+// A tile is 128 consecutive m' of one cell (6 tiles per cell, the last
+// partial); its patch is dzp[128t .. 128t + 191], computed from the pooled
+// gradient and the arg-max (8 channels per 16-byte chunk) straight into 8
+// K-major planes.  W2 of every tap is kept transposed as [32 ci][64 co]
+// core matrices for the CTA's life.  N = 32 (ci), 4 K16 steps per tap.  The
+// epilogue applies the ReLU mask of y1 from registers (no shared memory).
+// Patches and accumulators are double-buffered as in the forward.
+constexpr int DG_THREADS = 256;
+constexpr int DG_P = 28;                              // padded pitch
+constexpr int DG_PIX = C1 * DG_P;                     // m' per cell: 26 rows x 28
+constexpr int DG_TILES_PER_CELL = (DG_PIX + 127) / 128; // 6
+constexpr int DG_PATCH_ROWS = 192;                    // >= 128 + 2*28 + 2 = 186
+constexpr int DG_PLANE = DG_PATCH_ROWS * 16;
+constexpr int DG_PATCH_BYTES = 8 * DG_PLANE;          // 64 channels
+constexpr int DG_W_TAP_BYTES = CH1 * CH2 * 2;         // [32 ci][64 co]
+constexpr int DG_W_BYTES = 9 * DG_W_TAP_BYTES;
+constexpr uint32_t DG_TMEM_COLS = 32;
+
+__global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16 *__restrict__ dy2p,
+                                                                      const uint8_t *__restrict__ argmax,
+                                                                      const bf16 *__restrict__ w2,
+                                                                      const bf16 *__restrict__ y1, bf16 *dz1,
+                                                                      long long ntiles, int32_t *d_status,
+                                                                      uint32_t limit)
+{
+    extern __shared__ __align__(1024) unsigned char dg_smem[];
+    unsigned char *sw = dg_smem;                // W2 transposed, 9 taps
+    unsigned char *sp = dg_smem + DG_W_BYTES;   // two patches
+    __shared__ __align__(8) uint64_t s_mma;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(128, CH1);
+
+    if (tid == 0)
+        mbar_init(&s_mma, 1);
+    if (warp == 0) {
+        umma::tmem_alloc(&s_tmem, 2 * DG_TMEM_COLS);
+        umma::fence_before_sync();
+    }
+    // W2[co][tap][ci] -> tap: K-major [ci][co]: chunk (ci, kc) = co 8kc..8kc+7
+    for (int c = tid; c < 9 * CH1 * (CH2 / 8); c += DG_THREADS) {
+        const int tap = c / (CH1 * 8), ci = (c / 8) % CH1, kc = c % 8;
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++)
+            v[e] = w2[((size_t)(kc * 8 + e) * 9 + tap) * CH1 + ci];
+        *(uint4 *)(sw + tap * DG_W_TAP_BYTES + umma::chunk_off(ci, kc, 8)) = *(const uint4 *)v;
+    }
+    // the patch of a tile: dzp[128t + r], r < 192, 8 channels per 16-byte chunk
+    auto build_patch = [&](long long tile, int buf) {
+        const long long cell = tile / DG_TILES_PER_CELL;
+        const int i0 = (int)(tile % DG_TILES_PER_CELL) * 128;
+        unsigned char *dst = sp + buf * DG_PATCH_BYTES;
+        for (int c = tid; c < DG_PATCH_ROWS * 8; c += DG_THREADS) {
+            const int r = c >> 3, kc = c & 7;
+            const int i = i0 + r, a = i / DG_P - 2, b = i % DG_P - 2; // dz2 pixel (a, b)
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (i < DG_P * DG_P && a >= 0 && a < C2 && b >= 0 && b < C2)
+                v = pool_grad8(dy2p, argmax, (int)cell, a, b, kc * 8);
+            *(uint4 *)(dst + kc * DG_PLANE + r * 16) = v;
+        }
+    };
+    auto issue = [&](int buf, uint32_t acc) {
+        const uint32_t aw = smem_addr(sw), ap = smem_addr(sp + buf * DG_PATCH_BYTES);
+        umma::fence_after_sync();
+#pragma unroll 1
+        for (int tap = 0; tap < 9; tap++) {
+            const int ky = tap / 3, kx = tap % 3;
+            const uint32_t shift = (uint32_t)((2 - ky) * DG_P + (2 - kx)) * 16;
+#pragma unroll
+            for (int j = 0; j < CH2 / 16; j++) // co 16j..16j+15: planes 2j, 2j+1
+                umma::mma_bf16(acc, umma::smem_desc(ap + shift + 2 * j * DG_PLANE, DG_PLANE, 128),
+                               umma::smem_desc(aw + tap * DG_W_TAP_BYTES + j * 256, 128, 1024), idesc,
+                               tap > 0 || j > 0);
+        }
+        umma::commit(&s_mma);
+    };
+
+    long long tile = blockIdx.x;
+    if (tile < ntiles)
+        build_patch(tile, 0);
+    fence_proxy_async_smem(); // W2 and the first patch visible to the tensor cores
+    __syncthreads();          // ... and the mbarrier and tensor-memory address
+    umma::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    if (tile < ntiles && tid == 0)
+        issue(0, tmem);
+    bool ok = true;
+    uint32_t phase = 0;
+
+    for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
+        const int buf = it & 1;
+        const long long next = tile + gridDim.x;
+        if (next < ntiles) // its last reader, the previous tile's MMAs, has completed
+            build_patch(next, buf ^ 1);
+        fence_proxy_async_smem();
+        if (!mbar_wait(&s_mma, phase, limit))
+            ok = false;
+        phase ^= 1u;
+        umma::fence_after_sync();
+        umma::fence_before_sync();
+        __syncthreads(); // next patch built; every thread past this tile's MMA wait
+        if (next < ntiles && tid == 0)
+            issue(buf ^ 1, tmem + (uint32_t)((buf ^ 1) * DG_TMEM_COLS));
+        // epilogue: warp w reads lanes 32(w%4).. (its rows), columns 16(w/4)..
+        const long long cell = tile / DG_TILES_PER_CELL;
+        const int lq = warp & 3, cb = (warp >> 2) * 16;
+        const int i = (int)(tile % DG_TILES_PER_CELL) * 128 + 32 * lq + lane; // m'
+        float v[16];
+        umma::ld_16cols(tmem + (uint32_t)(buf * DG_TMEM_COLS) + ((uint32_t)(32 * lq) << 16) + cb, v);
+        const int y = i / DG_P, x = i % DG_P;
+        if (i < DG_PIX && x < C1) {
+            const size_t o = (((size_t)cell * C1 + y) * C1 + x) * CH1 + cb;
+            const uint4 *mk = (const uint4 *)(y1 + o);
+            uint4 *dst = (uint4 *)(dz1 + o);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint4 mm = mk[h];
+                const bf16 *mb = (const bf16 *)&mm;
+                __align__(16) bf16 ov[8];
+#pragma unroll
+                for (int e = 0; e < 8; e++)
+                    ov[e] = __float2bfloat16_rn(bf2f(mb[e]) > 0.f ? v[8 * h + e] : 0.f);
+                dst[h] = *(const uint4 *)ov;
+            }
+        }
+    }
+    if (!ok)
+        set_status(d_status, TDP_ERR_TIMEOUT);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, 2 * DG_TMEM_COLS);
     }
 }
 
@@ -978,22 +1088,37 @@ size_t tdp_cnn_conv2_bwd_workspace(int64_t n_cells)
 }
 
 tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void *y1, const void *w2, int64_t n_cells,
-                             void *dz1, float *dw2, float *db2, void *ws, size_t ws_bytes, tdp_stream_t stream)
+                             void *dz1, float *dw2, float *db2, void *ws, size_t ws_bytes, int32_t *d_status,
+                             tdp_stream_t stream)
 {
     if (n_cells < 1 || !dy2p || !argmax || !y1 || !w2 || !dw2 || !db2)
         return TDP_ERR_INVALID_ARG;
     if (!ws || ws_bytes < tdp_cnn_conv2_bwd_workspace(n_cells))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
+    // 16-byte alignment of the activation rows (vector loads and stores)
+    if (((uintptr_t)dy2p | (uintptr_t)argmax | (uintptr_t)y1 | (uintptr_t)dz1) % 16)
+        return TDP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    // dgrad (optional): dz1[cell][y][x][ci] = (sum dz2 * w2) * (y1 > 0)
+    // dgrad (optional): dz1[cell][y][x][ci] = (sum dz2 * w2) * (y1 > 0), tcgen05
     if (dz1) {
-        const int M = (int)(n_cells * C1 * C1);
-        LoadConv2DgradA la{(const bf16 *)dy2p, argmax, M};
-        LoadConv2DgradB lb{(const bf16 *)w2};
-        EpiMaskedBf16 epi{(bf16 *)dz1, (const bf16 *)y1, M, CH1};
-        tdp_status st = cerr(launch_gemm<128, 32, 8, 1>(la, lb, epi, M, CH1, 9 * CH2, 1, s));
-        if (st != TDP_OK)
-            return st;
+        const long long ntiles = n_cells * DG_TILES_PER_CELL;
+        const size_t smem = (size_t)DG_W_BYTES + 2 * DG_PATCH_BYTES;
+        if (cudaFuncSetAttribute(conv2_dgrad_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(conv2_dgrad_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+            return TDP_ERR_CUDA;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv2_dgrad_umma_kernel, DG_THREADS, smem) !=
+                cudaSuccess ||
+            per_sm < 1)
+            return TDP_ERR_CUDA;
+        const long long grid = std::min<long long>(ntiles, (long long)per_sm * num_sms());
+        conv2_dgrad_umma_kernel<<<(unsigned)grid, DG_THREADS, smem, s>>>(
+            (const bf16 *)dy2p, argmax, (const bf16 *)w2, (const bf16 *)y1, (bf16 *)dz1, ntiles, d_status,
+            spin_limit());
+        if (cudaGetLastError() != cudaSuccess)
+            return TDP_ERR_CUDA;
     }
     // wgrad: dw2[co][(ky,kx,ci)] = sum_p dz2[p][co] y1[p+(ky,kx)][ci]
     const int sp = conv2_wgrad_splits(n_cells);

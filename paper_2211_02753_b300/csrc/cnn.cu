@@ -124,36 +124,6 @@ __device__ __forceinline__ uint4 pool_grad8(const bf16 *dy2p, const uint8_t *arg
     return make_uint4(gw[0], gw[1], gw[2], gw[3]);
 }
 
-// conv2 wgrad A: A(m = co, k = output pixel raster (cell, oy, ox)) = dz2; MN-major (co contiguous)
-struct LoadConv2WgradA {
-    static constexpr bool MN_MAJOR = true, REG = true;
-    const bf16 *dy2p;
-    const uint8_t *argmax;
-    __device__ uint4 val(int kk, int rc, int m0, int k0, int kend) const
-    {
-        int k = k0 + kk, co = m0 + rc * 8;
-        if (k >= kend)
-            return make_uint4(0, 0, 0, 0);
-        int cell = k / (C2 * C2), w = k % (C2 * C2), oy = w / C2, ox = w % C2;
-        return pool_grad8(dy2p, argmax, cell, oy, ox, co);
-    }
-};
-
-// conv2 wgrad B: B(n = (ky,kx,ci), k = output pixel) = y1[cell][oy+ky][ox+kx][ci]; MN-major
-struct LoadConv2WgradB {
-    static constexpr bool MN_MAJOR = true, REG = false;
-    const bf16 *y1;
-    __device__ const void *ptr(int kk, int rc, int n0, int k0, int kend) const
-    {
-        int k = k0 + kk, n = n0 + rc * 8;
-        if (k >= kend || n >= 9 * CH1)
-            return nullptr;
-        int cell = k / (C2 * C2), w = k % (C2 * C2), oy = w / C2, ox = w % C2;
-        int kp = n >> 5, ci = n & 31, ky = kp / 3, kx = kp % 3;
-        return y1 + (((size_t)cell * C1 + oy + ky) * C1 + ox + kx) * CH1 + ci;
-    }
-};
-
 // -------------------------------------------------------------- epilogues
 
 struct EpiPartialF32 { // out[split][m][ldo]
@@ -538,6 +508,141 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
     }
 }
 
+// ---------------------------------- conv2 weight gradient on tcgen05
+//
+// dW[co][tap][ci] = sum_p dz2[p][co] y1[p + shift(tap)][ci] over every output
+// pixel p of every cell, as nine accumulating GEMMs per tile of pixels with
+// the pixels as K: output pixels in raster order with pitch 26 (p' = 26 oy +
+// ox; dz2 is 0 for ox >= 24, so the padding adds nothing) make tap (ky, kx)
+// the input patch shifted by 26 ky + kx rows.  Both operands are MN-major
+// (the channel dimension contiguous in 16-byte rows of 8 channels, one row
+// per pixel): A = dz2 of the tile's 128 pixels in 8 planes of 8 co (built
+// from the pooled gradient and the arg-max), B = y1 of its 182 input pixels
+// in 4 planes of 8 ci (cp.async).  M = 64 (co; TMEM lane 32(co/16) + co%16),
+// N = 32 (ci), one 32-column accumulator per tap (288 of 512 columns).  A
+// persistent CTA accumulates its tiles in tensor memory and writes one fp32
+// partial of dW at the end; the partials are summed in block order (fixed).
+constexpr int WG_THREADS = 256;
+constexpr int WG_PIX = C2 * C1;                        // p' per cell: 24 rows x 26
+constexpr int WG_TILES_PER_CELL = (WG_PIX + 127) / 128; // 5
+constexpr int WG_A_PLANE = 128 * 16;
+constexpr int WG_A_BYTES = 8 * WG_A_PLANE;              // 64 co
+constexpr int WG_B_ROWS = 192;                          // >= 128 + 2*26 + 2 = 182
+constexpr int WG_B_PLANE = WG_B_ROWS * 16;
+constexpr int WG_B_BYTES = 4 * WG_B_PLANE;              // 32 ci
+constexpr int WG_BUF_BYTES = WG_A_BYTES + WG_B_BYTES;
+constexpr uint32_t WG_TMEM_COLS = 512;
+
+__global__ void __launch_bounds__(WG_THREADS) conv2_wgrad_umma_kernel(const bf16 *__restrict__ dy2p,
+                                                                      const uint8_t *__restrict__ argmax,
+                                                                      const bf16 *__restrict__ y1, long long ntiles,
+                                                                      float *__restrict__ part, int32_t *d_status,
+                                                                      uint32_t limit)
+{
+    extern __shared__ __align__(1024) unsigned char wg_smem[]; // two buffers: A patch, then B patch
+    __shared__ __align__(8) uint64_t s_mma;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // M = 64, N = 32, both operands MN-major (bits 15, 16)
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(64, CH1) | (1u << 15) | (1u << 16);
+
+    if (tid == 0)
+        mbar_init(&s_mma, 1);
+    if (warp == 0) {
+        umma::tmem_alloc(&s_tmem, WG_TMEM_COLS);
+        umma::fence_before_sync();
+    }
+    auto build = [&](long long tile, int buf) {
+        const long long cell = tile / WG_TILES_PER_CELL;
+        const int i0 = (int)(tile % WG_TILES_PER_CELL) * 128;
+        unsigned char *a = wg_smem + buf * WG_BUF_BYTES, *b = a + WG_A_BYTES;
+        // B: input pixels i0 + r (r < 192) of the cell, 8 ci per chunk (cp.async)
+        const bf16 *src = y1 + (size_t)cell * C1 * C1 * CH1;
+        for (int c = tid; c < WG_B_ROWS * 4; c += WG_THREADS) {
+            const int r = c >> 2, kc = c & 3, pix = i0 + r;
+            const bool in = pix < C1 * C1;
+            cnn::cp_async16(b + kc * WG_B_PLANE + r * 16, in ? src + (size_t)pix * CH1 + kc * 8 : nullptr, in);
+        }
+        // A: dz2 at output pixels p' = i0 + r (r < 128), 8 co per chunk
+        for (int c = tid; c < 128 * 8; c += WG_THREADS) {
+            const int r = c >> 3, kc = c & 7, pp = i0 + r, oy = pp / C1, ox = pp % C1;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (pp < WG_PIX && ox < C2)
+                v = pool_grad8(dy2p, argmax, (int)cell, oy, ox, kc * 8);
+            *(uint4 *)(a + kc * WG_A_PLANE + r * 16) = v;
+        }
+    };
+    auto issue = [&](int buf, bool first, uint32_t tmem) {
+        const uint32_t a = smem_addr(wg_smem + buf * WG_BUF_BYTES), b = a + WG_A_BYTES;
+        umma::fence_after_sync();
+#pragma unroll 1
+        for (int tap = 0; tap < 9; tap++) {
+            const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3) * 16;
+#pragma unroll
+            for (int j = 0; j < 8; j++) // pixels 16j..16j+15: two 8-row K groups
+                umma::mma_bf16(tmem + (uint32_t)(tap * CH1), umma::smem_desc(a + j * 256, 128, WG_A_PLANE),
+                               umma::smem_desc(b + shift + j * 256, 128, WG_B_PLANE), idesc, !first || j > 0);
+        }
+        umma::commit(&s_mma);
+    };
+
+    long long tile = blockIdx.x;
+    if (tile < ntiles)
+        build(tile, 0);
+    cnn::cp_async_commit();
+    cnn::cp_async_wait<0>();
+    fence_proxy_async_smem();
+    __syncthreads(); // the first patches, the mbarrier and the tensor-memory address
+    umma::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    if (tile < ntiles && tid == 0)
+        issue(0, true, tmem);
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
+        const int buf = it & 1;
+        const long long next = tile + gridDim.x;
+        if (next < ntiles) // its buffer's last reader, the previous tile's MMAs, completed
+            build(next, buf ^ 1);
+        cnn::cp_async_commit();
+        cnn::cp_async_wait<0>();
+        fence_proxy_async_smem();
+        if (!mbar_wait(&s_mma, phase, limit))
+            ok = false;
+        phase ^= 1u;
+        umma::fence_before_sync();
+        __syncthreads();
+        if (next < ntiles && tid == 0)
+            issue(buf ^ 1, false, tmem);
+    }
+    // every MMA done (the last wait above); this CTA's partial of dW:
+    // warp w < 4, lanes 0..15 hold co = 16w + lane, columns tap*32 + ci
+    umma::fence_after_sync();
+    if (warp < 4) {
+        const int co = 16 * warp + lane;
+        float *o = part + (size_t)blockIdx.x * (CH2 * 9 * CH1) + (size_t)co * 9 * CH1;
+#pragma unroll 1
+        for (int cb = 0; cb < 9 * CH1; cb += 16) {
+            float v[16];
+            umma::ld_16cols(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, v);
+            if (lane < 16 && blockIdx.x < ntiles) {
+                float4 *d = (float4 *)(o + cb);
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+        }
+    }
+    if (!ok)
+        set_status(d_status, TDP_ERR_TIMEOUT);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, WG_TMEM_COLS);
+    }
+}
+
 // ---------------------------------------------------------- reductions
 
 // out[i] = act(sum_s part[s][i] + bias[i % ncol]) -> bf16 (ReLU) or f32
@@ -917,12 +1022,9 @@ static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 static const int FC1_FWD_SPLITS = 8;
 static const int FC1_WGRAD_SPLITS = 4;
 
-static int conv2_wgrad_splits(long long ncell)
-{
-    long long P = ncell * C2 * C2;
-    long long s = std::min<long long>(2 * num_sms() / 3 + 1, (P + 4095) / 4096);
-    return (int)std::max(1ll, s);
-}
+// CTAs of the conv2 weight gradient: one per SM (each holds 512 tensor-memory
+// columns), each writing one partial of dW
+static int conv2_wgrad_ctas() { return num_sms(); }
 
 extern "C" {
 
@@ -1080,7 +1182,7 @@ tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, in
 
 size_t tdp_cnn_conv2_bwd_workspace(int64_t n_cells)
 {
-    int sp = conv2_wgrad_splits(n_cells);
+    int sp = conv2_wgrad_ctas();
     long long Q = n_cells * PO * PO;
     size_t a = align_up((size_t)sp * CH2 * 9 * CH1 * sizeof(float), 256);
     size_t b = align_up((size_t)((Q + 255) / 256) * CH2 * sizeof(float), 256);
@@ -1120,18 +1222,22 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
         if (cudaGetLastError() != cudaSuccess)
             return TDP_ERR_CUDA;
     }
-    // wgrad: dw2[co][(ky,kx,ci)] = sum_p dz2[p][co] y1[p+(ky,kx)][ci]
-    const int sp = conv2_wgrad_splits(n_cells);
+    // wgrad: dw2[co][(ky,kx,ci)] = sum_p dz2[p][co] y1[p+(ky,kx)][ci], tcgen05, one
+    // fp32 partial per CTA summed in block order
+    const int sp = conv2_wgrad_ctas();
     float *part = (float *)ws;
     {
-        const int K = (int)(n_cells * C2 * C2);
-        LoadConv2WgradA la{(const bf16 *)dy2p, argmax};
-        LoadConv2WgradB lb{(const bf16 *)y1};
-        EpiPartialF32 epi{part, CH2, 9 * CH1, (size_t)CH2 * 9 * CH1};
-        tdp_status st = cerr(launch_gemm<64, 96, 4, 2>(la, lb, epi, CH2, 9 * CH1, K, sp, s));
-        if (st != TDP_OK)
-            return st;
-        partial_sum_kernel<<<psum_blocks(CH2 * 9 * CH1), 32 * PS_SLICES, 0, s>>>(part, sp, CH2 * 9 * CH1,
+        const long long ntiles = n_cells * WG_TILES_PER_CELL;
+        const size_t smem = 2 * (size_t)WG_BUF_BYTES;
+        if (cudaFuncSetAttribute(conv2_wgrad_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(conv2_wgrad_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+            return TDP_ERR_CUDA;
+        const int grid = (int)std::min<long long>(ntiles, sp);
+        conv2_wgrad_umma_kernel<<<grid, WG_THREADS, smem, s>>>((const bf16 *)dy2p, argmax, (const bf16 *)y1, ntiles,
+                                                               part, d_status, spin_limit());
+        partial_sum_kernel<<<psum_blocks(CH2 * 9 * CH1), 32 * PS_SLICES, 0, s>>>(part, grid, CH2 * 9 * CH1,
                                                                                  CH2 * 9 * CH1, dw2);
     }
     // bias: sum of the pooled gradient (each pooled value lands on exactly one pixel)

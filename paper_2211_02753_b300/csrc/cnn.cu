@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
 // N = 32 (ci), one 32-column accumulator per tap (288 of 512 columns).  A
 // persistent CTA accumulates its tiles in tensor memory and writes one fp32
 // partial of dW at the end; the partials are summed in block order (fixed).
-constexpr int WG_THREADS = 256;
+constexpr int WG_THREADS = 512;
 constexpr int WG_PIX = C2 * C1;                        // p' per cell: 24 rows x 26
 constexpr int WG_TILES_PER_CELL = (WG_PIX + 127) / 128; // 5
 constexpr int WG_A_PLANE = 128 * 16;
@@ -1026,6 +1026,19 @@ static const int FC1_WGRAD_SPLITS = 4;
 // columns), each writing one partial of dW
 static int conv2_wgrad_ctas() { return num_sms(); }
 
+// Resident CTAs per SM of a persistent tcgen05 kernel: as many as the SM's
+// shared memory holds (dynamic bytes + its static part and the per-block
+// reservation, counted as 2 KiB) and its tensor memory (512 columns) allows.
+static int umma_ctas_per_sm(size_t smem, uint32_t tmem_cols)
+{
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int by_smem = (int)((size_t)smem_sm / (smem + 2048));
+    const int by_tmem = (int)(512 / tmem_cols);
+    return std::max(1, std::min(by_smem, by_tmem));
+}
+
 extern "C" {
 
 tdp_status tdp_cnn_conv1_fwd(const uint8_t *grids, int64_t n_grids, const float *w1, const float *b1, void *y1,
@@ -1058,12 +1071,7 @@ tdp_status tdp_cnn_conv2_pool_fwd(const void *y1, int64_t n_cells, const void *w
         cudaFuncSetAttribute(conv2_pool_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return TDP_ERR_CUDA;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv2_pool_umma_kernel, C2_THREADS, smem) !=
-            cudaSuccess ||
-        per_sm < 1)
-        return TDP_ERR_CUDA;
-    const long long grid = std::min<long long>(ntiles, (long long)per_sm * num_sms());
+    const long long grid = std::min<long long>(ntiles, (long long)umma_ctas_per_sm(smem, 2 * C2_TMEM_COLS) * num_sms());
     conv2_pool_umma_kernel<<<(unsigned)grid, C2_THREADS, smem, (cudaStream_t)stream>>>(
         (const bf16 *)y1, (const bf16 *)w2, b2, (bf16 *)y2, argmax, ntiles, d_status, spin_limit());
     return launch_status();
@@ -1210,12 +1218,8 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
             cudaFuncSetAttribute(conv2_dgrad_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return TDP_ERR_CUDA;
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv2_dgrad_umma_kernel, DG_THREADS, smem) !=
-                cudaSuccess ||
-            per_sm < 1)
-            return TDP_ERR_CUDA;
-        const long long grid = std::min<long long>(ntiles, (long long)per_sm * num_sms());
+        const long long grid =
+            std::min<long long>(ntiles, (long long)umma_ctas_per_sm(smem, 2 * DG_TMEM_COLS) * num_sms());
         conv2_dgrad_umma_kernel<<<(unsigned)grid, DG_THREADS, smem, s>>>(
             (const bf16 *)dy2p, argmax, (const bf16 *)w2, (const bf16 *)y1, (bf16 *)dz1, ntiles, d_status,
             spin_limit());

@@ -186,6 +186,96 @@ __global__ void __launch_bounds__(SD_THREADS) small_domain_kernel(PredSet ps, Ke
     }
 }
 
+// Small domains (D * nslots <= SP_MAX_TAB accumulators): every thread owns a
+// private slice of D x nslots accumulators in shared memory (odd 64-bit
+// pitch, so that the lanes' slices fall on distinct banks), updated with
+// plain loads and stores -- no atomics and no contention however few the
+// groups are.  The block then folds its 256 slices (tree over threads in a
+// fixed order) and adds each group's totals to the global accumulators.
+constexpr int SP_MAX_TAB = 63;
+
+__global__ void __launch_bounds__(SD_THREADS) small_domain_priv_kernel(PredSet ps, KeySet ks, AggSet as, long long n,
+                                                                       const long long *d_nsel, int D, int pitch,
+                                                                       long long *gacc, int32_t *d_status)
+{
+    extern __shared__ long long spriv[];
+    const int NS = as.nslots;
+    const int tab = D * NS;
+    long long *my = spriv + (size_t)threadIdx.x * pitch;
+    __shared__ long long s_init[TDP_MAX_AGGS + 1];
+    __shared__ int s_op[TDP_MAX_AGGS + 1];
+    if (threadIdx.x <= TDP_MAX_AGGS) {
+        s_init[threadIdx.x] = threadIdx.x < NS ? slot_init(as, threadIdx.x) : 0;
+        s_op[threadIdx.x] = threadIdx.x < NS ? slot_op(as, threadIdx.x) : TDP_AGG_SUM;
+    }
+    __syncthreads();
+    for (int e = 0; e < tab; e++)
+        my[e] = s_init[e % NS];
+    bool bad = false;
+    if (d_nsel)
+        n = min(*d_nsel, n);
+    const long long stride = (long long)gridDim.x * SD_THREADS * 4;
+    for (long long r = ((long long)blockIdx.x * SD_THREADS + threadIdx.x) * 4; r < n; r += stride) {
+        unsigned m = eval_preds4(ps, r, n);
+        if (!m)
+            continue;
+        long long gid[4] = {0, 0, 0, 0};
+        for (int k = 0; k < ks.n; k++) {
+            long long v[4];
+            load4_int(ks.col[k], ks.dt[k], ks.vec_ok[k], r, n, v);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const long long d = v[j] - ks.lo[k];
+                if ((m >> j & 1) && (d < 0 || d >= ks.size[k])) {
+                    m &= ~(1u << j);
+                    bad = true;
+                }
+                gid[j] += d * ks.stride[k];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (m >> j & 1)
+                my[gid[j] * NS] += 1;
+        for (int sl = 1; sl < NS; sl++) {
+            long long va[4], vb[4] = {0, 0, 0, 0};
+            load4_int(as.sa[sl], as.sadt[sl], ((uintptr_t)as.sa[sl] % 16) == 0, r, n, va);
+            const int op = s_op[sl];
+            if (op == TDP_AGG_SUM_MUL_KMINUS)
+                load4_int(as.sb[sl], as.sbdt[sl], ((uintptr_t)as.sb[sl] % 16) == 0, r, n, vb);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (!(m >> j & 1))
+                    continue;
+                long long *a = my + gid[j] * NS + sl;
+                if (op == TDP_AGG_MIN)
+                    *a = min(*a, va[j]);
+                else if (op == TDP_AGG_MAX)
+                    *a = max(*a, va[j]);
+                else
+                    *a += op == TDP_AGG_SUM_MUL_KMINUS ? va[j] * (as.sk[sl] - vb[j]) : va[j];
+            }
+        }
+    }
+    if (bad)
+        set_status(d_status, TDP_ERR_OVERFLOW);
+    // fold the slices: tree over threads, then one global update per accumulator
+    for (int h = SD_THREADS / 2; h > 0; h >>= 1) {
+        __syncthreads();
+        if ((int)threadIdx.x < h) {
+            const long long *o = spriv + (size_t)(threadIdx.x + h) * pitch;
+            for (int e = 0; e < tab; e++) {
+                const int op = s_op[e % NS];
+                my[e] = op == TDP_AGG_MIN ? min(my[e], o[e]) : op == TDP_AGG_MAX ? max(my[e], o[e]) : my[e] + o[e];
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tab; e += SD_THREADS)
+        if (spriv[e] != s_init[e % NS])
+            acc_update(&gacc[e], s_op[e % NS], spriv[e]);
+}
+
 constexpr int FIN_THREADS = 256;
 constexpr int FIN_TILE = FIN_THREADS * 4;
 
@@ -370,6 +460,21 @@ tdp_status small_domain_run(const PredSet &ps, const KeySet &ks, const AggSet &a
     void *fin_ws = (char *)ws + align_up((size_t)D * as.nslots * 8, 256);
     dense_acc_init_kernel<<<(unsigned)std::min<long long>((D * as.nslots + 255) / 256, 4096), 256, 0, s>>>(as, D,
                                                                                                          acc);
+    if (!sel && D * as.nslots <= SP_MAX_TAB) {
+        // private per-thread accumulators
+        const int pitch = (int)(D * as.nslots) | 1;
+        const size_t psm = (size_t)SD_THREADS * pitch * 8;
+        cudaFuncSetAttribute(small_domain_priv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+        const int per_sm = std::max(1, std::min(8, (int)(200 * 1024 / psm)));
+        const long long want = ((n + 3) / 4 + SD_THREADS - 1) / SD_THREADS;
+        const unsigned pgrid = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() * per_sm));
+        small_domain_priv_kernel<<<pgrid, SD_THREADS, psm, s>>>(ps, ks, as, n, (const long long *)d_nsel, (int)D,
+                                                                pitch, acc, d_status);
+        tdp_status st = launch_status();
+        if (st != TDP_OK)
+            return st;
+        return dense_finalize(ks, as, out, D, acc, capacity, d_ngroups, fin_ws, d_status, s);
+    }
     size_t smem = 0;
     int copies = small_domain_copies(D, as.nslots, &smem);
     int blocks_per_sm = copies == 1 ? std::max(1, (int)(200 * 1024 / std::max<size_t>(smem, 1))) : 8;

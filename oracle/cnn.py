@@ -86,6 +86,27 @@ def conv2_relu_pool(y1, w2, b2):
     return pooled, arg, a2
 
 
+def conv2_backward(dy2, arg, y1, w2):
+    """Backward of conv2 + ReLU + 2x2 max-pool from the pooled gradient dy2
+    [B,12,12,64] (already masked by the pooled ReLU) and the pool arg-max:
+    the pre-pool gradient dz2 is dy2 at each window's arg-max pixel and 0
+    elsewhere.  Returns (dz1 [B,26,26,32] = the transposed convolution of
+    dz2 masked by y1 > 0, dw2 [64,3,3,32], db2 [64]).  float64."""
+    B = dy2.shape[0]
+    dwin = np.zeros((B, 12, 12, 4, 64))
+    np.put_along_axis(dwin, np.asarray(arg)[:, :, :, None, :], np.asarray(dy2, np.float64)[:, :, :, None, :], axis=3)
+    dz2 = dwin.reshape(B, 12, 12, 2, 2, 64).transpose(0, 1, 3, 2, 4, 5).reshape(B, 24, 24, 64)
+    y1 = np.asarray(y1, np.float64)
+    w2 = np.asarray(w2, np.float64)
+    gw2 = np.zeros((64, 3, 3, 32))
+    dy1 = np.zeros((B, 26, 26, 32))
+    for ky in range(3):
+        for kx in range(3):
+            gw2[:, ky, kx, :] = np.einsum("byxo,byxi->oi", dz2, y1[:, ky:ky + 24, kx:kx + 24, :])
+            dy1[:, ky:ky + 24, kx:kx + 24, :] += dz2 @ w2[:, ky, kx, :]
+    return dy1 * (y1 > 0), gw2, dz2.sum(axis=(0, 1, 2))
+
+
 def fc(x, w, b, relu):
     z = x @ w.T + b
     return np.maximum(z, 0.0) if relu else z
@@ -144,22 +165,10 @@ def backward(params, fw, target):
     g["fc1_w"] = dh1.T @ flat
     g["fc1_b"] = dh1.sum(axis=0)
     dflat = dh1 @ fw["wf1"]  # [B, 9216]
-    dy2 = dflat.reshape(B, 12, 12, 64) * (fw["y2"] > 0)
-    # route through the pool argmax
-    dwin = np.zeros((B, 12, 12, 4, 64))
-    np.put_along_axis(dwin, fw["arg"][:, :, :, None, :], dy2[:, :, :, None, :], axis=3)
-    dz2 = dwin.reshape(B, 12, 12, 2, 2, 64).transpose(0, 1, 3, 2, 4, 5).reshape(B, 24, 24, 64)
-    dz2 = _q(dz2, quant)
+    dy2 = _q(dflat.reshape(B, 12, 12, 64) * (fw["y2"] > 0), quant)
     y1 = fw["y1"]
-    gw2 = np.zeros((64, 3, 3, 32))
-    dy1 = np.zeros((B, 26, 26, 32))
-    for ky in range(3):
-        for kx in range(3):
-            gw2[:, ky, kx, :] = np.einsum("byxo,byxi->oi", dz2, y1[:, ky:ky + 24, kx:kx + 24, :])
-            dy1[:, ky:ky + 24, kx:kx + 24, :] += dz2 @ fw["w2"][:, ky, kx, :]
-    g["conv2_w"] = gw2
-    g["conv2_b"] = dz2.sum(axis=(0, 1, 2))
-    dz1 = _q(dy1 * (y1 > 0), quant)
+    dz1, g["conv2_w"], g["conv2_b"] = conv2_backward(dy2, fw["arg"], y1, fw["w2"])
+    dz1 = _q(dz1, quant)
     x0 = fw["x0"]
     gw1 = np.zeros((32, 3, 3))
     for ky in range(3):

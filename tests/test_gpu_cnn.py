@@ -89,6 +89,38 @@ def _batch(n_grids, seed):
     return img, lab, t
 
 
+@pytest.mark.parametrize("ncell", [9, 160])
+def test_conv2_backward_layer(ncell):
+    """conv2 data and weight gradients (tcgen05) against the float64 oracle;
+    160 cells give every CTA of both kernels several tiles (the
+    double-buffered path).  Inputs are bf16, products exact in fp32, so the
+    weight gradient agrees to fp32 accumulation error and dz1 to its bf16
+    rounding."""
+    r = np.random.default_rng(100 + ncell)
+    y1 = bf16_np(np.abs(r.standard_normal((ncell, 26, 26, 32))) * (r.random((ncell, 26, 26, 32)) > 0.3))
+    w2 = bf16_np(r.uniform(-0.08, 0.08, (64, 3, 3, 32)))
+    dy2 = bf16_np(r.standard_normal((ncell, 12, 12, 64)) * (r.random((ncell, 12, 12, 64)) > 0.2))
+    arg = r.integers(0, 4, (ncell, 12, 12, 64)).astype(np.uint8)
+    g_y1, g_w2, g_dy2 = to_bf16_dev(y1), to_bf16_dev(w2), to_bf16_dev(dy2)
+    g_arg = torch.from_numpy(arg).to(DEV)
+    dz1 = torch.empty((ncell, 26, 26, 32), dtype=torch.bfloat16, device=DEV)
+    dw2 = torch.empty((64, 3, 3, 32), dtype=torch.float32, device=DEV)
+    db2 = torch.empty(64, dtype=torch.float32, device=DEV)
+    ws = torch.empty(L.lib().tdp_cnn_conv2_bwd_workspace(ncell), dtype=torch.uint8, device=DEV)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    L.call("tdp_cnn_conv2_bwd", _ptr(g_dy2), _ptr(g_arg), _ptr(g_y1), _ptr(g_w2), ncell, _ptr(dz1), _ptr(dw2),
+           _ptr(db2), _ptr(ws), ws.numel(), _ptr(st), _stream())
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    rdz1, rdw2, rdb2 = O.conv2_backward(dy2, arg, y1, w2)
+    got = dz1.float().cpu().numpy()
+    ref = bf16_np(rdz1)
+    assert np.all(np.abs(got - ref) <= ULP * np.abs(ref) + 1e-3 * np.abs(rdz1).max())
+    gw = dw2.cpu().numpy()
+    assert np.linalg.norm(gw - rdw2) <= 1e-5 * np.linalg.norm(rdw2)
+    assert np.allclose(db2.cpu().numpy(), rdb2, rtol=1e-5, atol=1e-5 * np.abs(rdb2).max())
+
+
 def test_forward_query_matches_oracle():
     img, lab, t = _batch(3, 31)
     p = params()

@@ -124,6 +124,28 @@ def test_filter_device_row_count():
         assert np.array_equal(np_(out["gathered"][0], cnt), t["u8"][ref])
 
 
+def test_filter_multi_round():
+    """100M one-byte rows are more than one round of chunks (every block's
+    chunk is capped by its shared-memory bitmap), so the table is counted and
+    written in two rounds; row ids alone take the bulk-store write path, a
+    gathered column the per-lane path."""
+    n = 100_000_000
+    u = np.random.default_rng(7).integers(0, 256, n).astype(np.uint8)
+    g = cu(u)
+    ref = R.filter([(u, ">=", 128)], n)
+    out = ops.filter([g], [(0, ">=", 128)])
+    ops.check(out["status"])
+    cnt = int(out["count"].item())
+    assert cnt == len(ref)
+    assert np.array_equal(np_(out["rowid"], cnt), ref)
+    del out
+    out = ops.filter([g], [(0, ">=", 128)], gather=[0])
+    ops.check(out["status"])
+    assert int(out["count"].item()) == len(ref)
+    assert np.array_equal(np_(out["rowid"], cnt), ref)
+    assert np.array_equal(np_(out["gathered"][0], cnt), u[ref])
+
+
 def test_filter_config1_60m_rows():
     n = 60_000_000
     t = gen.fact_table(n, 15_000_000, gen.BASE_SEED + 1, cols=("date",))

@@ -103,27 +103,6 @@ struct LoadMN { // MN-major: stored [k][ld], the operand's rows contiguous
     }
 };
 
-// The gradient w.r.t. the conv2 output (pre-pool) for 8 channels of one
-// output pixel: the pooled gradient where the pixel is its window's arg-max,
-// else 0.  dy2p already carries the ReLU mask of the pooled value.
-__device__ __forceinline__ uint4 pool_grad8(const bf16 *dy2p, const uint8_t *argmax, int cell, int oy, int ox,
-                                            int co)
-{
-    size_t q = ((size_t)cell * PO + (oy >> 1)) * PO + (ox >> 1);
-    int wpos = ((oy & 1) << 1) | (ox & 1);
-    uint4 g = *(const uint4 *)(dy2p + q * CH2 + co);
-    uint2 a = *(const uint2 *)(argmax + q * CH2 + co);
-    uint32_t gw[4] = {g.x, g.y, g.z, g.w};
-    uint32_t ab[2] = {a.x, a.y};
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        uint32_t byte = (ab[i >> 2] >> (8 * (i & 3))) & 0xffu;
-        if (byte != (uint32_t)wpos)
-            gw[i >> 1] &= (i & 1) ? 0x0000ffffu : 0xffff0000u;
-    }
-    return make_uint4(gw[0], gw[1], gw[2], gw[3]);
-}
-
 // -------------------------------------------------------------- epilogues
 
 struct EpiPartialF32 { // out[split][m][ldo]
@@ -170,6 +149,57 @@ static cudaError_t launch_gemm(const LA &la, const LB &lb, const EPI &epi, int M
     dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, splits);
     kern<<<grid, GTHREADS, smem, s>>>(la, lb, epi, M, N, K, kps);
     return cudaGetLastError();
+}
+
+// ------------------------------------- pre-pool gradient patches
+//
+// Writes rows [base, base + rows) of a pre-pool-gradient patch: row i is
+// dz2 pixel (oy, ox) = (i / PITCH - OFF, i % PITCH - OFF) of `cell`, 8
+// channels per 16-byte chunk in plane kc (plane_bytes apart, rows 16 bytes
+// apart); rows that are no dz2 pixel (padding, dropped columns, past the
+// grid) are zero.  One work item per (pooled window, 8 channels) loads the
+// pooled gradient and the arg-max once and writes the window's four pixels
+// (the value at the arg-max pixel, zero at the others).
+template <int PITCH, int OFF>
+__device__ __forceinline__ void dz2_patch(unsigned char *planes, int plane_bytes, int base, int rows,
+                                          const bf16 *dy2p, const uint8_t *argmax, long long cell, int tid,
+                                          int nthreads)
+{
+    // zero rows that hold no dz2 pixel
+    for (int c = tid; c < rows * 8; c += nthreads) {
+        const int r = c >> 3, kc = c & 7, i = base + r;
+        const int oy = i / PITCH - OFF, ox = i % PITCH - OFF;
+        if (oy < 0 || oy >= C2 || ox < 0 || ox >= C2)
+            *(uint4 *)(planes + kc * plane_bytes + r * 16) = make_uint4(0, 0, 0, 0);
+    }
+    // pooled rows whose windows meet the patch
+    const int oy0 = max(0, base / PITCH - OFF), oy1 = min(C2 - 1, (base + rows - 1) / PITCH - OFF);
+    if (oy1 < oy0)
+        return;
+    const int py0 = oy0 >> 1, np = (oy1 >> 1) - py0 + 1;
+    for (int c = tid; c < np * PO * 8; c += nthreads) {
+        const int kc = c & 7, w = c >> 3, py = py0 + w / PO, px = w % PO;
+        const size_t q = ((size_t)cell * PO + py) * PO + px;
+        const uint4 g = *(const uint4 *)(dy2p + q * CH2 + kc * 8);
+        const uint2 a = *(const uint2 *)(argmax + q * CH2 + kc * 8);
+        const uint32_t gw[4] = {g.x, g.y, g.z, g.w};
+        const uint32_t ab[2] = {a.x, a.y};
+#pragma unroll
+        for (int pos = 0; pos < 4; pos++) {
+            const int oy = 2 * py + (pos >> 1), ox = 2 * px + (pos & 1);
+            const int r = (oy + OFF) * PITCH + ox + OFF - base;
+            if (r < 0 || r >= rows)
+                continue;
+            uint32_t o[4] = {gw[0], gw[1], gw[2], gw[3]};
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const uint32_t byte = (ab[e >> 2] >> (8 * (e & 3))) & 0xffu;
+                if (byte != (uint32_t)pos)
+                    o[e >> 1] &= (e & 1) ? 0x0000ffffu : 0xffff0000u;
+            }
+            *(uint4 *)(planes + kc * plane_bytes + r * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+    }
 }
 
 // ------------------------------------------ conv2 forward on tcgen05
@@ -250,16 +280,17 @@ __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 
     };
     // the 18 MMAs of a tile (one thread): patch buffer -> accumulator buffer
     auto issue = [&](int buf, uint32_t acc) {
-        const uint32_t aw = smem_addr(sw), ap = smem_addr(sp + buf * C2_PATCH_BYTES);
+        // descriptors differ only in their start address (16-byte units, low bits)
+        const uint64_t da = umma::smem_desc(smem_addr(sp + buf * C2_PATCH_BYTES), C2_PLANE, 128);
+        const uint64_t db = umma::smem_desc(smem_addr(sw), 128, 512);
         umma::fence_after_sync();
-#pragma unroll 1
+#pragma unroll
         for (int tap = 0; tap < 9; tap++) {
-            const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3) * 16; // start row 26*ky + kx
+            const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // start row 26*ky + kx
 #pragma unroll
             for (int j = 0; j < 2; j++) // channels 16j..16j+15: planes 2j, 2j+1
-                umma::mma_bf16(acc, umma::smem_desc(ap + shift + 2 * j * C2_PLANE, C2_PLANE, 128),
-                               umma::smem_desc(aw + tap * C2_W_TAP_BYTES + j * 256, 128, 512), idesc,
-                               tap > 0 || j > 0);
+                umma::mma_bf16(acc, da + shift + 2 * j * (C2_PLANE / 16),
+                               db + (uint32_t)(tap * C2_W_TAP_BYTES + j * 256) / 16, idesc, tap > 0 || j > 0);
         }
         umma::commit(&s_mma);
     };
@@ -423,28 +454,22 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
     auto build_patch = [&](long long tile, int buf) {
         const long long cell = tile / DG_TILES_PER_CELL;
         const int i0 = (int)(tile % DG_TILES_PER_CELL) * 128;
-        unsigned char *dst = sp + buf * DG_PATCH_BYTES;
-        for (int c = tid; c < DG_PATCH_ROWS * 8; c += DG_THREADS) {
-            const int r = c >> 3, kc = c & 7;
-            const int i = i0 + r, a = i / DG_P - 2, b = i % DG_P - 2; // dz2 pixel (a, b)
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (i < DG_P * DG_P && a >= 0 && a < C2 && b >= 0 && b < C2)
-                v = pool_grad8(dy2p, argmax, (int)cell, a, b, kc * 8);
-            *(uint4 *)(dst + kc * DG_PLANE + r * 16) = v;
-        }
+        dz2_patch<DG_P, 2>(sp + buf * DG_PATCH_BYTES, DG_PLANE, i0, DG_PATCH_ROWS, dy2p, argmax, cell, tid,
+                           DG_THREADS);
     };
     auto issue = [&](int buf, uint32_t acc) {
-        const uint32_t aw = smem_addr(sw), ap = smem_addr(sp + buf * DG_PATCH_BYTES);
+        // descriptors differ only in their start address (16-byte units, low bits)
+        const uint64_t da = umma::smem_desc(smem_addr(sp + buf * DG_PATCH_BYTES), DG_PLANE, 128);
+        const uint64_t db = umma::smem_desc(smem_addr(sw), 128, 1024);
         umma::fence_after_sync();
-#pragma unroll 1
+#pragma unroll
         for (int tap = 0; tap < 9; tap++) {
             const int ky = tap / 3, kx = tap % 3;
-            const uint32_t shift = (uint32_t)((2 - ky) * DG_P + (2 - kx)) * 16;
+            const uint32_t shift = (uint32_t)((2 - ky) * DG_P + (2 - kx));
 #pragma unroll
             for (int j = 0; j < CH2 / 16; j++) // co 16j..16j+15: planes 2j, 2j+1
-                umma::mma_bf16(acc, umma::smem_desc(ap + shift + 2 * j * DG_PLANE, DG_PLANE, 128),
-                               umma::smem_desc(aw + tap * DG_W_TAP_BYTES + j * 256, 128, 1024), idesc,
-                               tap > 0 || j > 0);
+                umma::mma_bf16(acc, da + shift + 2 * j * (DG_PLANE / 16),
+                               db + (uint32_t)(tap * DG_W_TAP_BYTES + j * 256) / 16, idesc, tap > 0 || j > 0);
         }
         umma::commit(&s_mma);
     };
@@ -564,24 +589,20 @@ __global__ void __launch_bounds__(WG_THREADS) conv2_wgrad_umma_kernel(const bf16
             cnn::cp_async16(b + kc * WG_B_PLANE + r * 16, in ? src + (size_t)pix * CH1 + kc * 8 : nullptr, in);
         }
         // A: dz2 at output pixels p' = i0 + r (r < 128), 8 co per chunk
-        for (int c = tid; c < 128 * 8; c += WG_THREADS) {
-            const int r = c >> 3, kc = c & 7, pp = i0 + r, oy = pp / C1, ox = pp % C1;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (pp < WG_PIX && ox < C2)
-                v = pool_grad8(dy2p, argmax, (int)cell, oy, ox, kc * 8);
-            *(uint4 *)(a + kc * WG_A_PLANE + r * 16) = v;
-        }
+        dz2_patch<C1, 0>(a, WG_A_PLANE, i0, 128, dy2p, argmax, cell, tid, WG_THREADS);
     };
     auto issue = [&](int buf, bool first, uint32_t tmem) {
-        const uint32_t a = smem_addr(wg_smem + buf * WG_BUF_BYTES), b = a + WG_A_BYTES;
+        // descriptors differ only in their start address (16-byte units, low bits)
+        const uint32_t a = smem_addr(wg_smem + buf * WG_BUF_BYTES);
+        const uint64_t da = umma::smem_desc(a, 128, WG_A_PLANE), db = umma::smem_desc(a + WG_A_BYTES, 128, WG_B_PLANE);
         umma::fence_after_sync();
-#pragma unroll 1
+#pragma unroll
         for (int tap = 0; tap < 9; tap++) {
-            const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3) * 16;
+            const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // rows
 #pragma unroll
             for (int j = 0; j < 8; j++) // pixels 16j..16j+15: two 8-row K groups
-                umma::mma_bf16(tmem + (uint32_t)(tap * CH1), umma::smem_desc(a + j * 256, 128, WG_A_PLANE),
-                               umma::smem_desc(b + shift + j * 256, 128, WG_B_PLANE), idesc, !first || j > 0);
+                umma::mma_bf16(tmem + (uint32_t)(tap * CH1), da + 16 * j, db + shift + 16 * j, idesc,
+                               !first || j > 0);
         }
         umma::commit(&s_mma);
     };

@@ -107,7 +107,13 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
 /* Workspace bytes of tdp_cnn_conv1_bwd. */
 size_t tdp_cnn_conv1_bwd_workspace(int64_t n_cells);
 
-/* conv1 weight and bias gradients (dw1 [32][3][3], db1 [32]) from dz1. */
+/*
+ * conv1 weight and bias gradients from dz1 bf16 [n_cells][26][26][32] (the
+ * gradient at conv1's output, ReLU applied): dw1 fp32 [32][3][3] (the
+ * correlation of dz1 with the cell image / 255), db1 fp32 [32] (the sum of
+ * dz1 per channel).  dz1 must be 4-byte aligned, n_cells a multiple of 16
+ * (whole grids), else TDP_ERR_INVALID_ARG.  Deterministic for a given GPU.
+ */
 tdp_status tdp_cnn_conv1_bwd(const void *dz1, const uint8_t *grids, int64_t n_cells, float *dw1, float *db1, void *ws,
                              size_t ws_bytes, tdp_stream_t stream);
 

@@ -107,6 +107,20 @@ def conv2_backward(dy2, arg, y1, w2):
     return dy1 * (y1 > 0), gw2, dz2.sum(axis=(0, 1, 2))
 
 
+def conv1_backward(dz1, x0):
+    """conv1 weight and bias gradients of the valid 3x3 correlation in the
+    Sec. 5.5 CNN: dW1[o, ky, kx] = sum over cells
+    and output pixels of dz1[b, y, x, o] * x0[b, y+ky, x+kx]; db1[o] = sum of
+    dz1[..., o].  dz1 [B, 26, 26, 32], x0 [B, 28, 28] (pixels / 255)."""
+    dz1 = np.asarray(dz1, np.float64)
+    x0 = np.asarray(x0, np.float64)
+    gw1 = np.zeros((32, 3, 3))
+    for ky in range(3):
+        for kx in range(3):
+            gw1[:, ky, kx] = np.einsum("byxo,byx->o", dz1, x0[:, ky:ky + 26, kx:kx + 26])
+    return gw1, dz1.sum(axis=(0, 1, 2))
+
+
 def fc(x, w, b, relu):
     z = x @ w.T + b
     return np.maximum(z, 0.0) if relu else z
@@ -169,13 +183,7 @@ def backward(params, fw, target):
     y1 = fw["y1"]
     dz1, g["conv2_w"], g["conv2_b"] = conv2_backward(dy2, fw["arg"], y1, fw["w2"])
     dz1 = _q(dz1, quant)
-    x0 = fw["x0"]
-    gw1 = np.zeros((32, 3, 3))
-    for ky in range(3):
-        for kx in range(3):
-            gw1[:, ky, kx] = np.einsum("byxo,byx->o", dz1, x0[:, ky:ky + 26, kx:kx + 26])
-    g["conv1_w"] = gw1
-    g["conv1_b"] = dz1.sum(axis=(0, 1, 2))
+    g["conv1_w"], g["conv1_b"] = conv1_backward(dz1, fw["x0"])
     return g
 
 

@@ -750,54 +750,124 @@ __global__ void __launch_bounds__(32 * PS_SLICES) partial_sum_kernel(const float
 
 static inline unsigned psum_blocks(int n) { return (unsigned)((n + 31) / 32); }
 
-// conv1 weight and bias gradients.  Block b takes the cells [c0, c1) of its
-// share; thread (kp, co) (kp 0..8 a tap, 9 the bias) walks every output
-// pixel of each cell: dz1 of the pixel's 32 channels is one 64-byte read of
-// a warp, the input pixel of the tap a broadcast from the cell's image in
-// shared memory.  Partials [blocks][32*9 + 32].
-__global__ void __launch_bounds__(CH1 * 10) conv1_wgrad_kernel(const bf16 *__restrict__ dz1,
-                                                               const uint8_t *__restrict__ grids, long long ncell,
-                                                               long long cells_per_block, float *__restrict__ part)
+// conv1 weight and bias gradients, dW1[co][ky][kx] = sum x0[oy+ky][ox+kx] *
+// dz1[oy][ox][co] and db1[co] = sum dz1[..][co] over all cells.  Thread
+// (cp, g) owns channels 2cp, 2cp+1 and output rows g, g+13 of every cell of
+// its block: one 4-byte load of dz1 feeds 20 accumulators (nine taps and the
+// bias for both channels), with the 3x3 image window sliding along the row
+// in registers.  The next cell's image is fetched while this one is reduced.
+// Per-block partials: the 13 row groups are added in a fixed order.
+constexpr int W1_ROWG = C1 / 2;                // 13 row groups of two rows
+constexpr int W1_THREADS = 16 * (W1_ROWG + 1); // 224 = 7 warps; group 13 only fetches images
+constexpr int W1_BLOCKS_PER_SM = 3;
+constexpr int W1_FETCH = (CELL * CELL + W1_THREADS - 1) / W1_THREADS; // image bytes per thread
+
+__global__ void __launch_bounds__(W1_THREADS, W1_BLOCKS_PER_SM)
+    conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const uint8_t *__restrict__ grids, long long ncell,
+                       long long cells_per_block, float *__restrict__ part)
 {
-    __shared__ float simg[CELL * CELL];
-    const int co = threadIdx.x % CH1, kp = threadIdx.x / CH1; // warp = one kp
-    const int ky = kp < 9 ? kp / 3 : 0, kx = kp < 9 ? kp % 3 : 0;
+    __shared__ float simg[2][CELL * CELL];
+    __shared__ float sred[W1_ROWG][CH1 * 10];
+    const int tid = threadIdx.x, cp = tid % 16, g = tid / 16;
     const long long c0 = (long long)blockIdx.x * cells_per_block, c1 = min(ncell, c0 + cells_per_block);
-    float acc = 0.f;
-    for (long long c = c0; c < c1; c++) {
-        const long long g = c / CELLS_PER_GRID;
+    float acc[2][10];
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+#pragma unroll
+        for (int t = 0; t < 10; t++)
+            acc[j][t] = 0.f;
+    uint8_t pre[W1_FETCH];
+    auto fetch = [&](long long c) {
+        const long long gi = c / CELLS_PER_GRID;
         const int r = (int)(c % CELLS_PER_GRID) / GRID_W, cc = (int)(c % GRID_W);
-        const uint8_t *img = grids + g * (GRID_H * CELL) * (GRID_W * CELL) + (long long)(r * CELL) * (GRID_W * CELL) +
-                             cc * CELL;
-        __syncthreads(); // the previous cell's image is no longer read
-        for (int i = threadIdx.x; i < CELL * CELL; i += blockDim.x)
-            simg[i] = (float)img[(i / CELL) * (GRID_W * CELL) + i % CELL] * (1.0f / 255.0f);
-        __syncthreads();
-        const bf16 *d = dz1 + c * (C1 * C1 * CH1) + co;
-        for (int oy = 0; oy < C1; oy++) {
-            // the row's 26 gradients loaded before any is used (26 loads in flight)
-            const bf16 *drow = d + oy * C1 * CH1;
-            float dv[C1];
+        const uint8_t *img = grids + gi * (GRID_H * CELL) * (GRID_W * CELL) +
+                             (long long)(r * CELL) * (GRID_W * CELL) + cc * CELL;
 #pragma unroll
-            for (int ox = 0; ox < C1; ox++)
-                dv[ox] = bf2f(drow[ox * CH1]);
-            if (kp == 9) {
+        for (int k = 0; k < W1_FETCH; k++) {
+            const int i = tid + k * W1_THREADS;
+            if (i < CELL * CELL)
+                pre[k] = img[(i / CELL) * (GRID_W * CELL) + i % CELL];
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int k = 0; k < W1_FETCH; k++) {
+            const int i = tid + k * W1_THREADS;
+            if (i < CELL * CELL)
+                simg[buf][i] = (float)pre[k] * (1.0f / 255.0f);
+        }
+    };
+    if (c0 < c1) {
+        fetch(c0);
+        store(0);
+    }
+    for (long long c = c0; c < c1; c++) {
+        const int buf = (int)((c - c0) & 1);
+        __syncthreads(); // simg[buf] is written; simg[buf ^ 1] is no longer read
+        if (c + 1 < c1)
+            fetch(c + 1);
+        if (g < W1_ROWG) {
+#pragma unroll 1
+            for (int h = 0; h < 2; h++) {
+                const int oy = g + W1_ROWG * h;
+                // the row's 26 channel pairs loaded before any is used
+                const uint32_t *drow = (const uint32_t *)(dz1 + (c * C1 + oy) * (C1 * CH1)) + cp;
+                uint32_t dv[C1];
 #pragma unroll
                 for (int ox = 0; ox < C1; ox++)
-                    acc += dv[ox];
-            } else {
-                const float *row = simg + (oy + ky) * CELL + kx;
+                    dv[ox] = __ldg(drow + ox * (CH1 / 2));
+                const float *row = simg[buf] + oy * CELL;
+                float w[3][3];
 #pragma unroll
-                for (int ox = 0; ox < C1; ox++)
-                    acc = fmaf(dv[ox], row[ox], acc);
+                for (int ky = 0; ky < 3; ky++) {
+                    w[ky][0] = row[ky * CELL];
+                    w[ky][1] = row[ky * CELL + 1];
+                }
+#pragma unroll
+                for (int ox = 0; ox < C1; ox++) {
+#pragma unroll
+                    for (int ky = 0; ky < 3; ky++)
+                        w[ky][2] = row[ky * CELL + ox + 2];
+                    // bf16 pair: channel 2cp in the low half, 2cp+1 in the high half
+                    const float d0 = __uint_as_float(dv[ox] << 16), d1 = __uint_as_float(dv[ox] & 0xffff0000u);
+#pragma unroll
+                    for (int ky = 0; ky < 3; ky++)
+#pragma unroll
+                        for (int kx = 0; kx < 3; kx++) {
+                            acc[0][ky * 3 + kx] = fmaf(d0, w[ky][kx], acc[0][ky * 3 + kx]);
+                            acc[1][ky * 3 + kx] = fmaf(d1, w[ky][kx], acc[1][ky * 3 + kx]);
+                        }
+                    acc[0][9] += d0;
+                    acc[1][9] += d1;
+#pragma unroll
+                    for (int ky = 0; ky < 3; ky++) {
+                        w[ky][0] = w[ky][1];
+                        w[ky][1] = w[ky][2];
+                    }
+                }
             }
         }
+        if (c + 1 < c1)
+            store(buf ^ 1);
     }
-    float *o = part + (size_t)blockIdx.x * (CH1 * 10);
-    if (kp < 9)
-        o[co * 9 + kp] = acc;
-    else
-        o[CH1 * 9 + co] = acc;
+    if (g < W1_ROWG) {
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const int co = 2 * cp + j;
+#pragma unroll
+            for (int t = 0; t < 9; t++)
+                sred[g][co * 9 + t] = acc[j][t];
+            sred[g][CH1 * 9 + co] = acc[j][9];
+        }
+    }
+    __syncthreads();
+    // each partial row: 288 weight sums (co-major), then the 32 bias sums
+    for (int i = tid; i < CH1 * 10; i += W1_THREADS) {
+        float sum = 0.f;
+        for (int gg = 0; gg < W1_ROWG; gg++)
+            sum += sred[gg][i];
+        part[(size_t)blockIdx.x * (CH1 * 10) + i] = sum;
+    }
 }
 
 // ------------------------------------------------------------------- head
@@ -1279,7 +1349,7 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
 size_t tdp_cnn_conv1_bwd_workspace(int64_t n_cells)
 {
     (void)n_cells;
-    return align_up((size_t)4 * num_sms() * CH1 * 10 * sizeof(float), 256);
+    return align_up((size_t)W1_BLOCKS_PER_SM * num_sms() * CH1 * 10 * sizeof(float), 256);
 }
 
 tdp_status tdp_cnn_conv1_bwd(const void *dz1, const uint8_t *grids, int64_t n_cells, float *dw1, float *db1, void *ws,
@@ -1289,12 +1359,15 @@ tdp_status tdp_cnn_conv1_bwd(const void *dz1, const uint8_t *grids, int64_t n_ce
         return TDP_ERR_INVALID_ARG;
     if (!ws || ws_bytes < tdp_cnn_conv1_bwd_workspace(n_cells))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
+    if ((uintptr_t)dz1 % 4)
+        return TDP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    // cells spread evenly over at most 4 blocks per SM
-    const long long cpb = (n_cells + 4ll * num_sms() - 1) / (4ll * num_sms());
+    // cells spread evenly over the resident blocks
+    const long long cap = (long long)W1_BLOCKS_PER_SM * num_sms();
+    const long long cpb = (n_cells + cap - 1) / cap;
     const int nb = (int)((n_cells + cpb - 1) / cpb);
     float *part = (float *)ws;
-    conv1_wgrad_kernel<<<nb, CH1 * 10, 0, s>>>((const bf16 *)dz1, grids, n_cells, cpb, part);
+    conv1_wgrad_kernel<<<nb, W1_THREADS, 0, s>>>((const bf16 *)dz1, grids, n_cells, cpb, part);
     // each partial row: 288 weight sums, then the 32 bias sums
     partial_sum_kernel<<<psum_blocks(CH1 * 9), 32 * PS_SLICES, 0, s>>>(part, nb, CH1 * 9, CH1 * 10, dw1);
     partial_sum_kernel<<<psum_blocks(CH1), 32 * PS_SLICES, 0, s>>>(part + CH1 * 9, nb, CH1, CH1 * 10, db1);

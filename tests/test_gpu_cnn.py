@@ -121,6 +121,28 @@ def test_conv2_backward_layer(ncell):
     assert np.allclose(db2.cpu().numpy(), rdb2, rtol=1e-5, atol=1e-5 * np.abs(rdb2).max())
 
 
+@pytest.mark.parametrize("n_grids", [1, 10])
+def test_conv1_backward_layer(n_grids):
+    """conv1 weight and bias gradients against the float64 oracle: one grid
+    (fewer cells than blocks), and 160 cells (blocks of one or two cells,
+    the image double buffer).  dz1 is bf16 and pixels / 255 are rounded to
+    fp32 once, so agreement is to fp32 accumulation error."""
+    img, _ = gen.glyph_grids(n_grids, 61 + n_grids)
+    ncell = 16 * n_grids
+    r = np.random.default_rng(200 + n_grids)
+    dz1 = bf16_np(r.standard_normal((ncell, 26, 26, 32)) * (r.random((ncell, 26, 26, 32)) > 0.4))
+    g_dz1, g_img = to_bf16_dev(dz1), torch.from_numpy(img).to(DEV)
+    dw1 = torch.empty((32, 3, 3), dtype=torch.float32, device=DEV)
+    db1 = torch.empty(32, dtype=torch.float32, device=DEV)
+    ws = torch.empty(L.lib().tdp_cnn_conv1_bwd_workspace(ncell), dtype=torch.uint8, device=DEV)
+    L.call("tdp_cnn_conv1_bwd", _ptr(g_dz1), _ptr(g_img), ncell, _ptr(dw1), _ptr(db1), _ptr(ws), ws.numel(),
+           _stream())
+    torch.cuda.synchronize()
+    rdw1, rdb1 = O.conv1_backward(dz1, O.split_cells(img) / 255.0)
+    assert np.linalg.norm(dw1.cpu().numpy() - rdw1) <= 1e-5 * np.linalg.norm(rdw1)
+    assert np.allclose(db1.cpu().numpy(), rdb1, rtol=1e-5, atol=1e-5 * np.abs(rdb1).max())
+
+
 def test_forward_query_matches_oracle():
     img, lab, t = _batch(3, 31)
     p = params()

@@ -36,7 +36,9 @@ extern "C" {
 #endif
 
 /* conv1 + bias + ReLU, reading the cells in place from the grid images
- * (the split of a grid into cells is index arithmetic, no copy). */
+ * (the split of a grid into cells is index arithmetic, no copy): grids u8
+ * [n_grids][112][112], w1 fp32 [32][3][3], b1 fp32 [32], y1 bf16
+ * [n_grids*16][26][26][32] (16-byte aligned, else TDP_ERR_INVALID_ARG). */
 tdp_status tdp_cnn_conv1_fwd(const uint8_t *grids, int64_t n_grids, const float *w1, const float *b1, void *y1,
                              tdp_stream_t stream);
 
@@ -80,7 +82,7 @@ size_t tdp_cnn_fc1_bwd_workspace(int64_t n_cells);
 /*
  * fc1 backward.  dy2p bf16 [n_cells][9216] = (dh1 . wfc1) masked by y2 > 0
  * (the gradient at the pooled map, through the ReLU); dwfc1 fp32 [128][9216];
- * dbfc1 fp32 [128].
+ * dbfc1 fp32 [128].  dh1 must be 16-byte aligned, else TDP_ERR_INVALID_ARG.
  */
 tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, int64_t n_cells, void *dy2p,
                            float *dwfc1, float *dbfc1, void *ws, size_t ws_bytes, tdp_stream_t stream);

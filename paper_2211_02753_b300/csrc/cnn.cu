@@ -35,44 +35,79 @@ __device__ __forceinline__ float bf2f(bf16 x) { return __bfloat162float(x); }
 
 // ------------------------------------------------------------------ conv1
 
-__global__ void conv1_fwd_kernel(const uint8_t *__restrict__ grids, long long ncell, const float *__restrict__ w,
-                                 const float *__restrict__ b, bf16 *__restrict__ y1)
+// conv1 + ReLU, y1[c][oy][ox][co] = relu(b[co] + sum_k x[oy+ky][ox+kx] w[co][k])
+// (fp32, taps in order, rounded once to bf16).  Thread = a horizontal pixel
+// pair of one cell (26 is even, so pairs never straddle rows): one broadcast
+// 16-byte read of the [tap][co] weights feeds 8 FMAs.  A block's 256 pairs
+// are 32 KB of y1, contiguous: staged in shared memory (16-byte chunks
+// XOR-swizzled by the pair index, conflict-free both ways) and written with
+// full-line stores.
+constexpr int C1F_THREADS = 256; // pixel pairs per block
+constexpr int PAIRS_PER_CELL = C1 * C1 / 2;
+
+__global__ void __launch_bounds__(C1F_THREADS) conv1_fwd_kernel(const uint8_t *__restrict__ grids, long long npairs,
+                                                                const float *__restrict__ w,
+                                                                const float *__restrict__ b, bf16 *__restrict__ y1)
 {
-    __shared__ float sw[CH1 * 9];
+    __shared__ __align__(16) float sw[9][CH1];
     __shared__ float sb[CH1];
-    for (int i = threadIdx.x; i < CH1 * 9; i += blockDim.x)
-        sw[i] = w[i];
-    for (int i = threadIdx.x; i < CH1; i += blockDim.x)
-        sb[i] = b[i];
+    __shared__ uint4 sout[C1F_THREADS * 8];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < CH1 * 9; i += C1F_THREADS)
+        sw[i % 9][i / 9] = w[i]; // w is [co][ky][kx]
+    if (tid < CH1)
+        sb[tid] = b[tid];
     __syncthreads();
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= ncell * C1 * C1)
-        return;
-    const long long c = p / (C1 * C1);
-    const int w_ = (int)(p % (C1 * C1)), oy = w_ / C1, ox = w_ % C1;
-    const long long g = c / CELLS_PER_GRID;
-    const int r = (int)(c % CELLS_PER_GRID) / GRID_W, cc = (int)(c % GRID_W);
-    const uint8_t *img = grids + g * (GRID_H * CELL) * (GRID_W * CELL) + (long long)(r * CELL) * (GRID_W * CELL) +
-                         cc * CELL;
-    float x[9];
+    const long long q0 = (long long)blockIdx.x * C1F_THREADS, q = q0 + tid;
+    if (q < npairs) {
+        const long long c = q / PAIRS_PER_CELL;
+        const int rem = (int)(q % PAIRS_PER_CELL), oy = rem / (C1 / 2), ox = (rem % (C1 / 2)) * 2;
+        const long long g = c / CELLS_PER_GRID;
+        const int r = (int)(c % CELLS_PER_GRID) / GRID_W, cc = (int)(c % GRID_W);
+        const uint8_t *img = grids + g * (GRID_H * CELL) * (GRID_W * CELL) +
+                             (long long)(r * CELL + oy) * (GRID_W * CELL) + cc * CELL + ox;
+        float x[3][4];
 #pragma unroll
-    for (int ky = 0; ky < 3; ky++)
+        for (int ky = 0; ky < 3; ky++)
 #pragma unroll
-        for (int kx = 0; kx < 3; kx++)
-            x[ky * 3 + kx] = (float)img[(oy + ky) * (GRID_W * CELL) + ox + kx] * (1.0f / 255.0f);
-    __align__(16) bf16 out[CH1];
+            for (int j = 0; j < 4; j++)
+                x[ky][j] = (float)img[ky * (GRID_W * CELL) + j] * (1.0f / 255.0f);
 #pragma unroll
-    for (int co = 0; co < CH1; co++) {
-        float s = sb[co];
+        for (int cg = 0; cg < CH1 / 8; cg++) {
+            float a[2][8];
 #pragma unroll
-        for (int k = 0; k < 9; k++)
-            s = fmaf(x[k], sw[co * 9 + k], s);
-        out[co] = __float2bfloat16_rn(fmaxf(s, 0.f));
+            for (int i = 0; i < 8; i++)
+                a[0][i] = a[1][i] = sb[cg * 8 + i];
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                const float4 wa = *(const float4 *)&sw[k][cg * 8], wb = *(const float4 *)&sw[k][cg * 8 + 4];
+                const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int p = 0; p < 2; p++) {
+                    const float xv = x[k / 3][k % 3 + p];
+#pragma unroll
+                    for (int i = 0; i < 8; i++)
+                        a[p][i] = fmaf(xv, wv[i], a[p][i]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                uint4 o;
+                __nv_bfloat162 *h = (__nv_bfloat162 *)&o;
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    h[i] = __floats2bfloat162_rn(fmaxf(a[p][2 * i], 0.f), fmaxf(a[p][2 * i + 1], 0.f));
+                sout[tid * 8 + ((p * 4 + cg) ^ (tid & 7))] = o;
+            }
+        }
     }
-    uint4 *dst = (uint4 *)(y1 + p * CH1);
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-        dst[i] = ((const uint4 *)out)[i];
+    __syncthreads();
+    const long long nchunks = (min(npairs, q0 + C1F_THREADS) - q0) * 8;
+    uint4 *dst = (uint4 *)y1 + q0 * 8;
+    for (int i = tid; i < nchunks; i += C1F_THREADS) {
+        const int t = i >> 3;
+        dst[i] = sout[t * 8 + ((i & 7) ^ (t & 7))];
+    }
 }
 
 // ---------------------------------------------------------------- loaders
@@ -686,27 +721,60 @@ __global__ void splitk_reduce_kernel(const float *__restrict__ part, int splits,
         out_f[i] = s;
 }
 
-// Column sums of a bf16 matrix [rows][C] into fp32 partials [blocks][C].
-// Every thread sums a fixed set of rows of one column; the per-thread sums
-// are then added in thread order (no atomics: the result is reproducible).
-__global__ void colsum_bf16_kernel(const bf16 *__restrict__ x, long long rows, int C, float *__restrict__ part)
+// Column sums of a bf16 matrix [rows][C] (C a multiple of 8 dividing 2048,
+// rows 16-byte aligned) into fp32 partials [blocks][C].  Thread = 8
+// consecutive columns (one 16-byte load, four in flight) of a fixed set of
+// rows; the per-thread sums are added in thread order (no atomics: the
+// result is reproducible for a given grid).
+constexpr int CS_THREADS = 256;
+
+__global__ void __launch_bounds__(CS_THREADS) colsum_bf16_kernel(const bf16 *__restrict__ x, long long rows, int C,
+                                                                 float *__restrict__ part)
 {
-    extern __shared__ float cs[]; // [blockDim.x]
-    const int c = threadIdx.x % C;
-    const int rstep = blockDim.x / C;
-    float acc = 0.f;
-    if (threadIdx.x < rstep * C)
-        for (long long r = (long long)blockIdx.x * rstep + threadIdx.x / C; r < rows;
-             r += (long long)gridDim.x * rstep)
-            acc += bf2f(x[r * C + c]);
-    cs[threadIdx.x] = acc;
-    __syncthreads();
-    for (int i = threadIdx.x; i < C; i += blockDim.x) {
-        float s = 0.f;
-        for (int j = 0; j < rstep; j++)
-            s += cs[j * C + i];
-        part[(size_t)blockIdx.x * C + i] = s;
+    __shared__ float cs[CS_THREADS * 8];
+    const int cv = C / 8, c8 = threadIdx.x % cv, rstep = CS_THREADS / cv;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const uint4 *xv = (const uint4 *)x;
+    auto add = [&](uint4 v) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            acc[2 * j] += __uint_as_float(w[j] << 16);
+            acc[2 * j + 1] += __uint_as_float(w[j] & 0xffff0000u);
+        }
+    };
+    if ((int)threadIdx.x < rstep * cv) {
+        const long long step = (long long)gridDim.x * rstep;
+        long long r = (long long)blockIdx.x * rstep + threadIdx.x / cv;
+        for (; r + 3 * step < rows; r += 4 * step) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                v[u] = __ldg(xv + (r + u * step) * cv + c8);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                add(v[u]);
+        }
+        for (; r < rows; r += step)
+            add(__ldg(xv + r * cv + c8));
     }
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        cs[threadIdx.x * 8 + j] = acc[j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < C; i += CS_THREADS) {
+        float sum = 0.f;
+        for (int q = 0; q < rstep; q++)
+            sum += cs[(q * cv + i / 8) * 8 + i % 8];
+        part[(size_t)blockIdx.x * C + i] = sum;
+    }
+}
+
+// Blocks of colsum_bf16_kernel (and partial rows it writes) for rows x C.
+static inline int colsum_blocks(long long rows, int C)
+{
+    const long long rstep = CS_THREADS / (C / 8);
+    return (int)std::max<long long>(1, std::min<long long>((rows + rstep - 1) / rstep, 2ll * num_sms()));
 }
 
 // out[i] = sum_b part[b * stride + i] in float64, in a fixed order: slice s
@@ -1137,11 +1205,13 @@ tdp_status tdp_cnn_conv1_fwd(const uint8_t *grids, int64_t n_grids, const float 
 {
     if (n_grids < 0 || (n_grids > 0 && (!grids || !w1 || !b1 || !y1)))
         return TDP_ERR_INVALID_ARG;
-    long long P = n_grids * CELLS_PER_GRID * C1 * C1;
-    if (P == 0)
+    const long long npairs = n_grids * CELLS_PER_GRID * PAIRS_PER_CELL;
+    if (npairs == 0)
         return TDP_OK;
-    conv1_fwd_kernel<<<blocks_for(P, 256), 256, 0, (cudaStream_t)stream>>>(grids, n_grids * CELLS_PER_GRID, w1, b1,
-                                                                           (bf16 *)y1);
+    if ((uintptr_t)y1 % 16)
+        return TDP_ERR_INVALID_ARG;
+    conv1_fwd_kernel<<<blocks_for(npairs, C1F_THREADS), C1F_THREADS, 0, (cudaStream_t)stream>>>(grids, npairs, w1, b1,
+                                                                                             (bf16 *)y1);
     return launch_status();
 }
 
@@ -1234,14 +1304,14 @@ tdp_status tdp_cnn_head(const void *h1, int64_t n_grids, const float *wfc2, cons
 size_t tdp_cnn_fc1_bwd_workspace(int64_t n_cells)
 {
     size_t a = align_up((size_t)FC1_WGRAD_SPLITS * HID * FEAT * sizeof(float), 256);
-    size_t b = align_up((size_t)((n_cells + 63) / 64) * HID * sizeof(float), 256);
+    size_t b = align_up((size_t)colsum_blocks(n_cells, HID) * HID * sizeof(float), 256);
     return a + b;
 }
 
 tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, int64_t n_cells, void *dy2p,
                            float *dwfc1, float *dbfc1, void *ws, size_t ws_bytes, tdp_stream_t stream)
 {
-    if (n_cells < 1 || !dh1 || !y2 || !wfc1 || !dy2p || !dwfc1 || !dbfc1)
+    if (n_cells < 1 || !dh1 || !y2 || !wfc1 || !dy2p || !dwfc1 || !dbfc1 || (uintptr_t)dh1 % 16)
         return TDP_ERR_INVALID_ARG;
     if (!ws || ws_bytes < tdp_cnn_fc1_bwd_workspace(n_cells))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
@@ -1272,8 +1342,8 @@ tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, in
     // bias: column sums of dh1
     {
         float *bp = (float *)((char *)ws + align_up((size_t)FC1_WGRAD_SPLITS * HID * FEAT * sizeof(float), 256));
-        int nb = (int)((n_cells + 63) / 64);
-        colsum_bf16_kernel<<<nb, 256, 256 * sizeof(float), s>>>((const bf16 *)dh1, n_cells, HID, bp);
+        const int nb = colsum_blocks(n_cells, HID);
+        colsum_bf16_kernel<<<nb, CS_THREADS, 0, s>>>((const bf16 *)dh1, n_cells, HID, bp);
         partial_sum_kernel<<<psum_blocks(HID), 32 * PS_SLICES, 0, s>>>(bp, nb, HID, HID, dbfc1);
     }
     return launch_status();
@@ -1284,7 +1354,7 @@ size_t tdp_cnn_conv2_bwd_workspace(int64_t n_cells)
     int sp = conv2_wgrad_ctas();
     long long Q = n_cells * PO * PO;
     size_t a = align_up((size_t)sp * CH2 * 9 * CH1 * sizeof(float), 256);
-    size_t b = align_up((size_t)((Q + 255) / 256) * CH2 * sizeof(float), 256);
+    size_t b = align_up((size_t)colsum_blocks(Q, CH2) * CH2 * sizeof(float), 256);
     return a + b;
 }
 
@@ -1339,8 +1409,8 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
     {
         float *bp = (float *)((char *)ws + align_up((size_t)sp * CH2 * 9 * CH1 * sizeof(float), 256));
         long long Q = n_cells * PO * PO;
-        int nb = (int)((Q + 255) / 256);
-        colsum_bf16_kernel<<<nb, 256, 256 * sizeof(float), s>>>((const bf16 *)dy2p, Q, CH2, bp);
+        const int nb = colsum_blocks(Q, CH2);
+        colsum_bf16_kernel<<<nb, CS_THREADS, 0, s>>>((const bf16 *)dy2p, Q, CH2, bp);
         partial_sum_kernel<<<psum_blocks(CH2), 32 * PS_SLICES, 0, s>>>(bp, nb, CH2, CH2, db2);
     }
     return launch_status();

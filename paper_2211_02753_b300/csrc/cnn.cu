@@ -582,7 +582,15 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
 // N = 32 (ci), one 32-column accumulator per tap (288 of 512 columns).  A
 // persistent CTA accumulates its tiles in tensor memory and writes one fp32
 // partial of dW at the end; the partials are summed in block order (fixed).
-constexpr int WG_THREADS = 512;
+// Warp roles: four producer warpgroups each own one stage and build every
+// fourth tile of the CTA (so four tiles' load latencies overlap); one more
+// warp allocates tensor memory and issues the MMAs, tile by tile in order.
+// Stage s is handed over by mbarriers: full[s] (128 producer arrivals after
+// the patches are written) and empty[s] (tcgen05.commit once the MMAs that
+// read it have completed).
+constexpr int WG_PRODUCERS = 4;                         // warpgroups = stages
+constexpr int WG_THREADS = 128 * WG_PRODUCERS + 32;     // + the MMA warp
+constexpr int WG_MMA_WARP = 4 * WG_PRODUCERS;
 constexpr int WG_PIX = C2 * C1;                        // p' per cell: 24 rows x 26
 constexpr int WG_TILES_PER_CELL = (WG_PIX + 127) / 128; // 5
 constexpr int WG_A_PLANE = 128 * 16;
@@ -599,101 +607,113 @@ __global__ void __launch_bounds__(WG_THREADS) conv2_wgrad_umma_kernel(const bf16
                                                                       float *__restrict__ part, int32_t *d_status,
                                                                       uint32_t limit)
 {
-    extern __shared__ __align__(1024) unsigned char wg_smem[]; // two buffers: A patch, then B patch
-    __shared__ __align__(8) uint64_t s_mma;
+    extern __shared__ __align__(1024) unsigned char wg_smem[]; // one stage per producer: A patch, then B patch
+    __shared__ __align__(8) uint64_t s_full[WG_PRODUCERS], s_empty[WG_PRODUCERS], s_done;
     __shared__ uint32_t s_tmem;
+    __shared__ int s_err;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // M = 64, N = 32, both operands MN-major (bits 15, 16)
     constexpr uint32_t idesc = umma::idesc_bf16_f32(64, CH1) | (1u << 15) | (1u << 16);
 
-    if (tid == 0)
-        mbar_init(&s_mma, 1);
-    if (warp == 0) {
+    if (tid == 0) {
+        for (int g = 0; g < WG_PRODUCERS; g++) {
+            mbar_init(&s_full[g], 128);
+            mbar_init(&s_empty[g], 1);
+        }
+        mbar_init(&s_done, 1);
+        s_err = 0;
+    }
+    if (warp == WG_MMA_WARP) {
         umma::tmem_alloc(&s_tmem, WG_TMEM_COLS);
         umma::fence_before_sync();
     }
-    auto build = [&](long long tile, int buf) {
-        const long long cell = tile / WG_TILES_PER_CELL;
-        const int i0 = (int)(tile % WG_TILES_PER_CELL) * 128;
-        unsigned char *a = wg_smem + buf * WG_BUF_BYTES, *b = a + WG_A_BYTES;
-        // B: input pixels i0 + r (r < 192) of the cell, 8 ci per chunk (cp.async)
-        const bf16 *src = y1 + (size_t)cell * C1 * C1 * CH1;
-        for (int c = tid; c < WG_B_ROWS * 4; c += WG_THREADS) {
-            const int r = c >> 2, kc = c & 3, pix = i0 + r;
-            const bool in = pix < C1 * C1;
-            cnn::cp_async16(b + kc * WG_B_PLANE + r * 16, in ? src + (size_t)pix * CH1 + kc * 8 : nullptr, in);
-        }
-        // A: dz2 at output pixels p' = i0 + r (r < 128), 8 co per chunk
-        dz2_patch<C1, 0>(a, WG_A_PLANE, i0, 128, dy2p, argmax, cell, tid, WG_THREADS);
-    };
-    auto issue = [&](int buf, bool first, uint32_t tmem) {
-        // descriptors differ only in their start address (16-byte units, low bits)
-        const uint32_t a = smem_addr(wg_smem + buf * WG_BUF_BYTES);
-        const uint64_t da = umma::smem_desc(a, 128, WG_A_PLANE), db = umma::smem_desc(a + WG_A_BYTES, 128, WG_B_PLANE);
-        umma::fence_after_sync();
-#pragma unroll
-        for (int tap = 0; tap < 9; tap++) {
-            const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // rows
-#pragma unroll
-            for (int j = 0; j < 8; j++) // pixels 16j..16j+15: two 8-row K groups
-                umma::mma_bf16(tmem + (uint32_t)(tap * CH1), da + 16 * j, db + shift + 16 * j, idesc,
-                               !first || j > 0);
-        }
-        umma::commit(&s_mma);
-    };
-
-    long long tile = blockIdx.x;
-    if (tile < ntiles)
-        build(tile, 0);
-    cnn::cp_async_commit();
-    cnn::cp_async_wait<0>();
-    fence_proxy_async_smem();
-    __syncthreads(); // the first patches, the mbarrier and the tensor-memory address
+    __syncthreads(); // the mbarriers and the tensor-memory address
     umma::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    if (tile < ntiles && tid == 0)
-        issue(0, true, tmem);
-    bool ok = true;
-    uint32_t phase = 0;
-    for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
-        const int buf = it & 1;
-        const long long next = tile + gridDim.x;
-        if (next < ntiles) // its buffer's last reader, the previous tile's MMAs, completed
-            build(next, buf ^ 1);
-        cnn::cp_async_commit();
-        cnn::cp_async_wait<0>();
-        fence_proxy_async_smem();
-        if (!mbar_wait(&s_mma, phase, limit))
-            ok = false;
-        phase ^= 1u;
-        umma::fence_before_sync();
-        __syncthreads();
-        if (next < ntiles && tid == 0)
-            issue(buf ^ 1, false, tmem);
-    }
-    // every MMA done (the last wait above); this CTA's partial of dW:
-    // warp w < 4, lanes 0..15 hold co = 16w + lane, columns tap*32 + ci
-    umma::fence_after_sync();
-    if (warp < 4) {
-        const int co = 16 * warp + lane;
-        float *o = part + (size_t)blockIdx.x * (CH2 * 9 * CH1) + (size_t)co * 9 * CH1;
-#pragma unroll 1
-        for (int cb = 0; cb < 9 * CH1; cb += 16) {
-            float v[16];
-            umma::ld_16cols(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, v);
-            if (lane < 16 && blockIdx.x < ntiles) {
-                float4 *d = (float4 *)(o + cb);
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp < WG_MMA_WARP) {
+        // producer warpgroup g: the CTA's tiles g, g + 4, ... into stage g
+        const int g = warp >> 2, ptid = tid & 127;
+        unsigned char *a = wg_smem + g * WG_BUF_BYTES, *b = a + WG_A_BYTES;
+        uint32_t ephase = 0;
+        for (long long it = g; it < my_tiles; it += WG_PRODUCERS) {
+            if (it >= WG_PRODUCERS) { // the MMAs of tile it - 4 have read the stage
+                if (!mbar_wait(&s_empty[g], ephase, limit)) {
+                    s_err = 1;
+                    break;
+                }
+                ephase ^= 1u;
+            }
+            const long long tile = blockIdx.x + it * gridDim.x;
+            const long long cell = tile / WG_TILES_PER_CELL;
+            const int i0 = (int)(tile % WG_TILES_PER_CELL) * 128;
+            // B: input pixels i0 + r (r < 192) of the cell, 8 ci per chunk (cp.async)
+            const bf16 *src = y1 + (size_t)cell * C1 * C1 * CH1;
+            for (int c = ptid; c < WG_B_ROWS * 4; c += 128) {
+                const int r = c >> 2, kc = c & 3, pix = i0 + r;
+                const bool in = pix < C1 * C1;
+                cnn::cp_async16(b + kc * WG_B_PLANE + r * 16, in ? src + (size_t)pix * CH1 + kc * 8 : nullptr, in);
+            }
+            cnn::cp_async_commit();
+            // A: dz2 at output pixels p' = i0 + r (r < 128), 8 co per chunk
+            dz2_patch<C1, 0>(a, WG_A_PLANE, i0, 128, dy2p, argmax, cell, ptid, 128);
+            cnn::cp_async_wait<0>();
+            fence_proxy_async_smem(); // this thread's patch writes, visible to the tensor cores
+            mbar_arrive(&s_full[g]);
+        }
+    } else if (lane == 0) {
+        // the MMA issuer: tiles in order, stage it % 4
+        for (long long it = 0; it < my_tiles; it++) {
+            const int st = (int)(it % WG_PRODUCERS);
+            if (!mbar_wait(&s_full[st], (uint32_t)(it / WG_PRODUCERS) & 1u, limit)) {
+                s_err = 1;
+                break;
+            }
+            umma::fence_after_sync();
+            // descriptors differ only in their start address (16-byte units, low bits)
+            const uint32_t a = smem_addr(wg_smem + st * WG_BUF_BYTES);
+            const uint64_t da = umma::smem_desc(a, 128, WG_A_PLANE),
+                           db = umma::smem_desc(a + WG_A_BYTES, 128, WG_B_PLANE);
 #pragma unroll
-                for (int i = 0; i < 4; i++)
-                    d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            for (int tap = 0; tap < 9; tap++) {
+                const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // rows
+#pragma unroll
+                for (int j = 0; j < 8; j++) // pixels 16j..16j+15: two 8-row K groups
+                    umma::mma_bf16(tmem + (uint32_t)(tap * CH1), da + 16 * j, db + shift + 16 * j, idesc,
+                                   it > 0 || j > 0);
+            }
+            umma::commit(&s_empty[st]);
+        }
+        umma::commit(&s_done); // arrives once every MMA issued above has completed
+    }
+    // this CTA's partial of dW: warp w < 4, lanes 0..15 hold co = 16w + lane, columns tap*32 + ci
+    if (warp < 4) {
+        const bool done = mbar_wait(&s_done, 0, limit);
+        umma::fence_after_sync();
+        if (!done)
+            s_err = 1;
+        else if (my_tiles > 0) {
+            const int co = 16 * warp + lane;
+            float *o = part + (size_t)blockIdx.x * (CH2 * 9 * CH1) + (size_t)co * 9 * CH1;
+#pragma unroll 1
+            for (int cb = 0; cb < 9 * CH1; cb += 16) {
+                float v[16];
+                umma::ld_16cols(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, v);
+                if (lane < 16) {
+                    float4 *d = (float4 *)(o + cb);
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
             }
         }
     }
-    if (!ok)
-        set_status(d_status, TDP_ERR_TIMEOUT);
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (tid == 0 && s_err)
+        set_status(d_status, TDP_ERR_TIMEOUT);
+    if (warp == WG_MMA_WARP) {
         umma::fence_after_sync();
         umma::tmem_dealloc(tmem, WG_TMEM_COLS);
     }
@@ -1393,7 +1413,7 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
     float *part = (float *)ws;
     {
         const long long ntiles = n_cells * WG_TILES_PER_CELL;
-        const size_t smem = 2 * (size_t)WG_BUF_BYTES;
+        const size_t smem = (size_t)WG_PRODUCERS * WG_BUF_BYTES;
         if (cudaFuncSetAttribute(conv2_wgrad_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(conv2_wgrad_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,

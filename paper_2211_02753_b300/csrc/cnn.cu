@@ -188,37 +188,84 @@ static cudaError_t launch_gemm(const LA &la, const LB &lb, const EPI &epi, int M
 
 // ------------------------------------- pre-pool gradient patches
 //
-// Writes rows [base, base + rows) of a pre-pool-gradient patch: row i is
-// dz2 pixel (oy, ox) = (i / PITCH - OFF, i % PITCH - OFF) of `cell`, 8
-// channels per 16-byte chunk in plane kc (plane_bytes apart, rows 16 bytes
-// apart); rows that are no dz2 pixel (padding, dropped columns, past the
-// grid) are zero.  One work item per (pooled window, 8 channels) loads the
-// pooled gradient and the arg-max once and writes the window's four pixels
-// (the value at the arg-max pixel, zero at the others).
+// Rows [base, base + rows) of a pre-pool-gradient patch: row i is dz2 pixel
+// (oy, ox) = (i / PITCH - OFF, i % PITCH - OFF) of a cell, 8 channels per
+// 16-byte chunk in plane kc (plane_bytes apart, rows 16 bytes apart); rows
+// that are no dz2 pixel (padding, dropped columns, past the grid) are zero.
+// One work item per (pooled window, 8 channels) loads the pooled gradient
+// and the arg-max once and writes the window's four pixels (the value at the
+// arg-max pixel, zero at the others).  Items are numbered so that the 8 lanes
+// of a 16-byte shared-memory store phase write 8 consecutive windows of one
+// plane (rows 2 apart: at most 2-way bank conflicts), and a warp's loads are
+// 8 windows x 64 contiguous bytes.  Loading (into registers) and storing are
+// separate steps so that the loads can be issued before waiting for the
+// destination buffer; a thread holds at most DZ2_ITEMS items.
+constexpr int DZ2_ITEMS = 4;
+
+struct Dz2Items {
+    uint4 g[DZ2_ITEMS];
+    uint2 a[DZ2_ITEMS];
+};
+
 template <int PITCH, int OFF>
-__device__ __forceinline__ void dz2_patch(unsigned char *planes, int plane_bytes, int base, int rows,
-                                          const bf16 *dy2p, const uint8_t *argmax, long long cell, int tid,
-                                          int nthreads)
+__device__ __forceinline__ void dz2_window_range(int base, int rows, int &py0, int &nwin)
 {
-    // zero rows that hold no dz2 pixel
-    for (int c = tid; c < rows * 8; c += nthreads) {
-        const int r = c >> 3, kc = c & 7, i = base + r;
-        const int oy = i / PITCH - OFF, ox = i % PITCH - OFF;
-        if (oy < 0 || oy >= C2 || ox < 0 || ox >= C2)
-            *(uint4 *)(planes + kc * plane_bytes + r * 16) = make_uint4(0, 0, 0, 0);
-    }
-    // pooled rows whose windows meet the patch
     const int oy0 = max(0, base / PITCH - OFF), oy1 = min(C2 - 1, (base + rows - 1) / PITCH - OFF);
-    if (oy1 < oy0)
-        return;
-    const int py0 = oy0 >> 1, np = (oy1 >> 1) - py0 + 1;
-    for (int c = tid; c < np * PO * 8; c += nthreads) {
-        const int kc = c & 7, w = c >> 3, py = py0 + w / PO, px = w % PO;
-        const size_t q = ((size_t)cell * PO + py) * PO + px;
-        const uint4 g = *(const uint4 *)(dy2p + q * CH2 + kc * 8);
-        const uint2 a = *(const uint2 *)(argmax + q * CH2 + kc * 8);
-        const uint32_t gw[4] = {g.x, g.y, g.z, g.w};
-        const uint32_t ab[2] = {a.x, a.y};
+    py0 = oy0 >> 1;
+    nwin = oy1 < oy0 ? 0 : ((oy1 >> 1) - py0 + 1) * PO;
+}
+
+__device__ __forceinline__ void dz2_item(int c, int &w, int &kc)
+{
+    w = ((c >> 6) << 3) | (c & 7);
+    kc = ((c >> 3) & 3) | (((c >> 5) & 1) << 2);
+}
+
+template <int PITCH, int OFF>
+__device__ __forceinline__ void dz2_load(Dz2Items &it, int base, int rows, const bf16 *__restrict__ dy2p,
+                                         const uint8_t *__restrict__ argmax, long long cell, int tid, int nthreads)
+{
+    int py0, nwin;
+    dz2_window_range<PITCH, OFF>(base, rows, py0, nwin);
+    const int nitems = ((nwin + 7) >> 3) << 6;
+#pragma unroll
+    for (int k = 0; k < DZ2_ITEMS; k++) {
+        const int c = tid + k * nthreads;
+        int w, kc;
+        dz2_item(c, w, kc);
+        if (c < nitems && w < nwin) {
+            const size_t q = ((size_t)cell * PO + py0 + w / PO) * PO + w % PO;
+            it.g[k] = __ldg((const uint4 *)(dy2p + q * CH2 + kc * 8));
+            it.a[k] = __ldg((const uint2 *)(argmax + q * CH2 + kc * 8));
+        }
+    }
+}
+
+template <int PITCH, int OFF>
+__device__ __forceinline__ void dz2_store(const Dz2Items &it, unsigned char *planes, int plane_bytes, int base,
+                                          int rows, int tid, int nthreads)
+{
+    // zero rows that hold no dz2 pixel (row-major: a warp writes 32 rows of one plane)
+    for (int r = tid; r < rows; r += nthreads) {
+        const int i = base + r, oy = i / PITCH - OFF, ox = i % PITCH - OFF;
+        if (oy < 0 || oy >= C2 || ox < 0 || ox >= C2)
+#pragma unroll
+            for (int kc = 0; kc < 8; kc++)
+                *(uint4 *)(planes + kc * plane_bytes + r * 16) = make_uint4(0, 0, 0, 0);
+    }
+    int py0, nwin;
+    dz2_window_range<PITCH, OFF>(base, rows, py0, nwin);
+    const int nitems = ((nwin + 7) >> 3) << 6;
+#pragma unroll
+    for (int k = 0; k < DZ2_ITEMS; k++) {
+        const int c = tid + k * nthreads;
+        int w, kc;
+        dz2_item(c, w, kc);
+        if (c >= nitems || w >= nwin)
+            continue;
+        const int py = py0 + w / PO, px = w % PO;
+        const uint32_t gw[4] = {it.g[k].x, it.g[k].y, it.g[k].z, it.g[k].w};
+        const uint32_t ab[2] = {it.a[k].x, it.a[k].y};
 #pragma unroll
         for (int pos = 0; pos < 4; pos++) {
             const int oy = 2 * py + (pos >> 1), ox = 2 * px + (pos & 1);
@@ -313,21 +360,24 @@ __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 
             cnn::cp_async16(dst + kc * C2_PLANE + r * 16, in ? src + (size_t)pix * CH1 + kc * 8 : nullptr, in);
         }
     };
-    // the 18 MMAs of a tile (one thread): patch buffer -> accumulator buffer
+    // the 18 MMAs of a tile (warp 0, one elected lane): patch buffer -> accumulator buffer
     auto issue = [&](int buf, uint32_t acc) {
         // descriptors differ only in their start address (16-byte units, low bits)
         const uint64_t da = umma::smem_desc(smem_addr(sp + buf * C2_PATCH_BYTES), C2_PLANE, 128);
         const uint64_t db = umma::smem_desc(smem_addr(sw), 128, 512);
         umma::fence_after_sync();
+        if (umma::elect_one()) {
 #pragma unroll
-        for (int tap = 0; tap < 9; tap++) {
-            const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // start row 26*ky + kx
+            for (int tap = 0; tap < 9; tap++) {
+                const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // start row 26*ky + kx
 #pragma unroll
-            for (int j = 0; j < 2; j++) // channels 16j..16j+15: planes 2j, 2j+1
-                umma::mma_bf16(acc, da + shift + 2 * j * (C2_PLANE / 16),
-                               db + (uint32_t)(tap * C2_W_TAP_BYTES + j * 256) / 16, idesc, tap > 0 || j > 0);
+                for (int j = 0; j < 2; j++) // channels 16j..16j+15: planes 2j, 2j+1
+                    umma::mma_bf16(acc, da + shift + 2 * j * (C2_PLANE / 16),
+                                   db + (uint32_t)(tap * C2_W_TAP_BYTES + j * 256) / 16, idesc, tap > 0 || j > 0);
+            }
+            umma::commit(&s_mma);
         }
-        umma::commit(&s_mma);
+        __syncwarp();
     };
 
     long long tile = blockIdx.x;
@@ -339,7 +389,7 @@ __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 
     __syncthreads();          // ... and the mbarrier, tensor-memory address and bias
     umma::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    if (tile < ntiles && tid == 0)
+    if (tile < ntiles && warp == 0)
         issue(0, tmem);
     bool ok = true;
     uint32_t phase = 0;
@@ -362,7 +412,7 @@ __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 
         fence_proxy_async_smem();
         umma::fence_before_sync();
         __syncthreads(); // next patch complete; every thread past this tile's MMA wait
-        if (next < ntiles && tid == 0)
+        if (next < ntiles && warp == 0)
             issue(buf ^ 1, tmem + (uint32_t)((buf ^ 1) * C2_TMEM_COLS));
         // accumulator rows (TMEM lane = row) to shared memory: warp w takes
         // lanes 32(w%4).. and columns 32(w/4).. (row pitch C2_ACC_PITCH: the
@@ -489,24 +539,29 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
     auto build_patch = [&](long long tile, int buf) {
         const long long cell = tile / DG_TILES_PER_CELL;
         const int i0 = (int)(tile % DG_TILES_PER_CELL) * 128;
-        dz2_patch<DG_P, 2>(sp + buf * DG_PATCH_BYTES, DG_PLANE, i0, DG_PATCH_ROWS, dy2p, argmax, cell, tid,
-                           DG_THREADS);
+        Dz2Items items;
+        dz2_load<DG_P, 2>(items, i0, DG_PATCH_ROWS, dy2p, argmax, cell, tid, DG_THREADS);
+        dz2_store<DG_P, 2>(items, sp + buf * DG_PATCH_BYTES, DG_PLANE, i0, DG_PATCH_ROWS, tid, DG_THREADS);
     };
+    // the 36 MMAs of a tile (warp 0, one elected lane)
     auto issue = [&](int buf, uint32_t acc) {
         // descriptors differ only in their start address (16-byte units, low bits)
         const uint64_t da = umma::smem_desc(smem_addr(sp + buf * DG_PATCH_BYTES), DG_PLANE, 128);
         const uint64_t db = umma::smem_desc(smem_addr(sw), 128, 1024);
         umma::fence_after_sync();
+        if (umma::elect_one()) {
 #pragma unroll
-        for (int tap = 0; tap < 9; tap++) {
-            const int ky = tap / 3, kx = tap % 3;
-            const uint32_t shift = (uint32_t)((2 - ky) * DG_P + (2 - kx));
+            for (int tap = 0; tap < 9; tap++) {
+                const int ky = tap / 3, kx = tap % 3;
+                const uint32_t shift = (uint32_t)((2 - ky) * DG_P + (2 - kx));
 #pragma unroll
-            for (int j = 0; j < CH2 / 16; j++) // co 16j..16j+15: planes 2j, 2j+1
-                umma::mma_bf16(acc, da + shift + 2 * j * (DG_PLANE / 16),
-                               db + (uint32_t)(tap * DG_W_TAP_BYTES + j * 256) / 16, idesc, tap > 0 || j > 0);
+                for (int j = 0; j < CH2 / 16; j++) // co 16j..16j+15: planes 2j, 2j+1
+                    umma::mma_bf16(acc, da + shift + 2 * j * (DG_PLANE / 16),
+                                   db + (uint32_t)(tap * DG_W_TAP_BYTES + j * 256) / 16, idesc, tap > 0 || j > 0);
+            }
+            umma::commit(&s_mma);
         }
-        umma::commit(&s_mma);
+        __syncwarp();
     };
 
     long long tile = blockIdx.x;
@@ -516,7 +571,7 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
     __syncthreads();          // ... and the mbarrier and tensor-memory address
     umma::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    if (tile < ntiles && tid == 0)
+    if (tile < ntiles && warp == 0)
         issue(0, tmem);
     bool ok = true;
     uint32_t phase = 0;
@@ -533,7 +588,7 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
         umma::fence_after_sync();
         umma::fence_before_sync();
         __syncthreads(); // next patch built; every thread past this tile's MMA wait
-        if (next < ntiles && tid == 0)
+        if (next < ntiles && warp == 0)
             issue(buf ^ 1, tmem + (uint32_t)((buf ^ 1) * DG_TMEM_COLS));
         // epilogue: warp w reads lanes 32(w%4).. (its rows), columns 16(w/4)..
         const long long cell = tile / DG_TILES_PER_CELL;
@@ -638,6 +693,12 @@ __global__ void __launch_bounds__(WG_THREADS) conv2_wgrad_umma_kernel(const bf16
         unsigned char *a = wg_smem + g * WG_BUF_BYTES, *b = a + WG_A_BYTES;
         uint32_t ephase = 0;
         for (long long it = g; it < my_tiles; it += WG_PRODUCERS) {
+            const long long tile = blockIdx.x + it * gridDim.x;
+            const long long cell = tile / WG_TILES_PER_CELL;
+            const int i0 = (int)(tile % WG_TILES_PER_CELL) * 128;
+            // the pooled gradient and arg-max of the tile, in flight during the wait
+            Dz2Items items;
+            dz2_load<C1, 0>(items, i0, 128, dy2p, argmax, cell, ptid, 128);
             if (it >= WG_PRODUCERS) { // the MMAs of tile it - 4 have read the stage
                 if (!mbar_wait(&s_empty[g], ephase, limit)) {
                     s_err = 1;
@@ -645,9 +706,6 @@ __global__ void __launch_bounds__(WG_THREADS) conv2_wgrad_umma_kernel(const bf16
                 }
                 ephase ^= 1u;
             }
-            const long long tile = blockIdx.x + it * gridDim.x;
-            const long long cell = tile / WG_TILES_PER_CELL;
-            const int i0 = (int)(tile % WG_TILES_PER_CELL) * 128;
             // B: input pixels i0 + r (r < 192) of the cell, 8 ci per chunk (cp.async)
             const bf16 *src = y1 + (size_t)cell * C1 * C1 * CH1;
             for (int c = ptid; c < WG_B_ROWS * 4; c += 128) {
@@ -657,16 +715,16 @@ __global__ void __launch_bounds__(WG_THREADS) conv2_wgrad_umma_kernel(const bf16
             }
             cnn::cp_async_commit();
             // A: dz2 at output pixels p' = i0 + r (r < 128), 8 co per chunk
-            dz2_patch<C1, 0>(a, WG_A_PLANE, i0, 128, dy2p, argmax, cell, ptid, 128);
+            dz2_store<C1, 0>(items, a, WG_A_PLANE, i0, 128, ptid, 128);
             cnn::cp_async_wait<0>();
             fence_proxy_async_smem(); // this thread's patch writes, visible to the tensor cores
             mbar_arrive(&s_full[g]);
         }
-    } else if (lane == 0) {
-        // the MMA issuer: tiles in order, stage it % 4
+    } else {
+        // the MMA warp: tiles in order, stage it % 4; warp-uniform descriptors, one elected lane issues
         for (long long it = 0; it < my_tiles; it++) {
             const int st = (int)(it % WG_PRODUCERS);
-            if (!mbar_wait(&s_full[st], (uint32_t)(it / WG_PRODUCERS) & 1u, limit)) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&s_full[st], (uint32_t)(it / WG_PRODUCERS) & 1u, limit))) {
                 s_err = 1;
                 break;
             }
@@ -675,17 +733,22 @@ __global__ void __launch_bounds__(WG_THREADS) conv2_wgrad_umma_kernel(const bf16
             const uint32_t a = smem_addr(wg_smem + st * WG_BUF_BYTES);
             const uint64_t da = umma::smem_desc(a, 128, WG_A_PLANE),
                            db = umma::smem_desc(a + WG_A_BYTES, 128, WG_B_PLANE);
+            if (umma::elect_one()) {
 #pragma unroll
-            for (int tap = 0; tap < 9; tap++) {
-                const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // rows
+                for (int tap = 0; tap < 9; tap++) {
+                    const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // rows
 #pragma unroll
-                for (int j = 0; j < 8; j++) // pixels 16j..16j+15: two 8-row K groups
-                    umma::mma_bf16(tmem + (uint32_t)(tap * CH1), da + 16 * j, db + shift + 16 * j, idesc,
-                                   it > 0 || j > 0);
+                    for (int j = 0; j < 8; j++) // pixels 16j..16j+15: two 8-row K groups
+                        umma::mma_bf16(tmem + (uint32_t)(tap * CH1), da + 16 * j, db + shift + 16 * j, idesc,
+                                       it > 0 || j > 0);
+                }
+                umma::commit(&s_empty[st]);
             }
-            umma::commit(&s_empty[st]);
+            __syncwarp();
         }
-        umma::commit(&s_done); // arrives once every MMA issued above has completed
+        if (umma::elect_one())
+            umma::commit(&s_done); // arrives once every MMA issued above has completed
+        __syncwarp();
     }
     // this CTA's partial of dW: warp w < 4, lanes 0..15 hold co = 16w + lane, columns tap*32 + ci
     if (warp < 4) {

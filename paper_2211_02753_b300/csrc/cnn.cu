@@ -300,13 +300,17 @@ __device__ __forceinline__ void dz2_store(const Dz2Items &it, unsigned char *pla
 // 8 channels one plane (LBO) further.  W2 of all nine taps stays in shared
 // memory for the CTA's whole life (persistent CTAs, tiles in grid-stride
 // order).  Per tile: 18 K16 MMAs into a 64-column fp32 accumulator in tensor
-// memory, issued by one thread and committed to an mbarrier; the accumulator
-// then goes through shared memory (a window's four rows sit in different
-// warps) for bias + ReLU + the window maximum and its first arg-max.  Patches
-// and accumulators are double-buffered: while a tile is pooled, the next
-// tile's MMAs run on the tensor cores and the patch after it is in flight.  Every wait is bounded; a wait that runs out sets
-// TDP_ERR_TIMEOUT in d_status.
-constexpr int C2_THREADS = 256; // warps w and w + 4 share TMEM lanes 32(w%4).., each half of the columns
+// memory; the accumulator then goes through shared memory (a window's four
+// rows sit in different warps) for bias + ReLU + the window maximum and its
+// first arg-max.  Warp roles: four worker warpgroups, each owning one patch
+// stage, one accumulator and one staging buffer, take every fourth tile of
+// the CTA (load the patch, hand it to the MMA warp through mbarrier full[g],
+// wait for done[g], pool); one more warp issues the MMAs tile by tile.
+// Every wait is bounded; a wait that runs out sets TDP_ERR_TIMEOUT in
+// d_status.
+constexpr int C2_WORKERS = 4;
+constexpr int C2_THREADS = 128 * C2_WORKERS + 32;
+constexpr int C2_MMA_WARP = 4 * C2_WORKERS;
 constexpr int C2_PATCH_ROWS = 192;                  // >= 128 + 2*26 + 2 = 182, whole 8-row groups
 constexpr int C2_PLANE = C2_PATCH_ROWS * 16;        // bytes of one 8-channel plane
 constexpr int C2_PATCH_BYTES = 4 * C2_PLANE;        // 32 channels
@@ -314,8 +318,30 @@ constexpr int C2_W_TAP_BYTES = CH2 * CH1 * 2;       // W2 of one tap, [64 co][32
 constexpr int C2_W_BYTES = 9 * C2_W_TAP_BYTES;
 constexpr int C2_ACC_PITCH = CH2 + 4;               // floats per staged accumulator row
 constexpr int C2_ACC_BYTES = 128 * C2_ACC_PITCH * 4; // the accumulator staged for the pool
+constexpr int C2_STAGE_BYTES = C2_PATCH_BYTES + C2_ACC_BYTES;
 constexpr int C2_TILES_PER_CELL = C2 / 4;           // 6 tiles of 2 row-pairs
-constexpr uint32_t C2_TMEM_COLS = 64;
+constexpr uint32_t C2_TMEM_COLS = 64;               // one accumulator
+constexpr uint32_t C2_TMEM_ALLOC = C2_WORKERS * C2_TMEM_COLS;
+static_assert(C2_W_BYTES + C2_WORKERS * C2_STAGE_BYTES + 1024 <= 232448, "conv2 forward shared memory");
+
+// Barrier among the 128 threads of warpgroup g (ids 1.. ; 0 is __syncthreads).
+__device__ __forceinline__ void wg_sync(int g)
+{
+    asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory");
+}
+
+// The same barrier with an OR over the threads' flags: every thread of the
+// warpgroup gets the same answer (so they leave a loop together).
+__device__ __forceinline__ bool wg_any(int g, bool flag)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, 128, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)flag), "r"(g + 1)
+                 : "memory");
+    return r != 0;
+}
 
 __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 *__restrict__ y1,
                                                                      const bf16 *__restrict__ w2,
@@ -324,21 +350,27 @@ __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 
                                                                      int32_t *d_status, uint32_t limit)
 {
     extern __shared__ __align__(1024) unsigned char c2_smem[];
-    unsigned char *sw = c2_smem;                          // W2, 9 taps
-    unsigned char *sp = c2_smem + C2_W_BYTES;             // two patches
-    float *sacc = (float *)(sp + 2 * C2_PATCH_BYTES);     // [128][64] accumulator of the tile being pooled
-    __shared__ __align__(8) uint64_t s_mma;
+    unsigned char *sw = c2_smem;              // W2, 9 taps
+    unsigned char *sst = c2_smem + C2_W_BYTES; // per worker: patch, then staged accumulator
+    __shared__ __align__(8) uint64_t s_full[C2_WORKERS], s_done[C2_WORKERS], s_fin;
     __shared__ uint32_t s_tmem;
+    __shared__ int s_err;
     __shared__ __align__(16) float s_bias[CH2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t idesc = umma::idesc_bf16_f32(128, CH2);
 
     if (tid < CH2)
         s_bias[tid] = bias[tid];
-    if (tid == 0)
-        mbar_init(&s_mma, 1);
-    if (warp == 0) {
-        umma::tmem_alloc(&s_tmem, 2 * C2_TMEM_COLS); // two accumulators
+    if (tid == 0) {
+        for (int g = 0; g < C2_WORKERS; g++) {
+            mbar_init(&s_full[g], 128);
+            mbar_init(&s_done[g], 1);
+        }
+        mbar_init(&s_fin, 1);
+        s_err = 0;
+    }
+    if (warp == C2_MMA_WARP) {
+        umma::tmem_alloc(&s_tmem, C2_TMEM_ALLOC);
         umma::fence_before_sync();
     }
     // W2 [co][ky][kx][ci] -> tap t = ky*3 + kx: K-major [co][ci] core matrices
@@ -347,134 +379,134 @@ __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 
         cnn::cp_async16(sw + t * C2_W_TAP_BYTES + umma::chunk_off(co, kc, 4), w2 + ((size_t)co * 9 + t) * CH1 + kc * 8,
                         true);
     }
-    // the patch of a tile: pixel p0 + r (r < 192) of its cell, 8 channels per 16-byte chunk
-    auto load_patch = [&](long long tile, int buf) {
-        const long long cell = tile / C2_TILES_PER_CELL;
-        const int p0 = (int)(tile % C2_TILES_PER_CELL) * 4 * C1;
-        const bf16 *src = y1 + (size_t)cell * C1 * C1 * CH1;
-        unsigned char *dst = sp + buf * C2_PATCH_BYTES;
-        for (int c = tid; c < C2_PATCH_ROWS * 4; c += C2_THREADS) {
-            const int r = c >> 2, kc = c & 3;
-            const int pix = p0 + r;
-            const bool in = pix < C1 * C1;
-            cnn::cp_async16(dst + kc * C2_PLANE + r * 16, in ? src + (size_t)pix * CH1 + kc * 8 : nullptr, in);
-        }
-    };
-    // the 18 MMAs of a tile (warp 0, one elected lane): patch buffer -> accumulator buffer
-    auto issue = [&](int buf, uint32_t acc) {
-        // descriptors differ only in their start address (16-byte units, low bits)
-        const uint64_t da = umma::smem_desc(smem_addr(sp + buf * C2_PATCH_BYTES), C2_PLANE, 128);
-        const uint64_t db = umma::smem_desc(smem_addr(sw), 128, 512);
-        umma::fence_after_sync();
-        if (umma::elect_one()) {
-#pragma unroll
-            for (int tap = 0; tap < 9; tap++) {
-                const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // start row 26*ky + kx
-#pragma unroll
-                for (int j = 0; j < 2; j++) // channels 16j..16j+15: planes 2j, 2j+1
-                    umma::mma_bf16(acc, da + shift + 2 * j * (C2_PLANE / 16),
-                                   db + (uint32_t)(tap * C2_W_TAP_BYTES + j * 256) / 16, idesc, tap > 0 || j > 0);
-            }
-            umma::commit(&s_mma);
-        }
-        __syncwarp();
-    };
-
-    long long tile = blockIdx.x;
-    if (tile < ntiles)
-        load_patch(tile, 0);
     cnn::cp_async_commit();
     cnn::cp_async_wait<0>();
-    fence_proxy_async_smem(); // W2 and the first patch visible to the tensor cores
-    __syncthreads();          // ... and the mbarrier, tensor-memory address and bias
+    fence_proxy_async_smem(); // W2 visible to the tensor cores
+    __syncthreads();          // ... and the mbarriers, tensor-memory address and bias
     umma::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    if (tile < ntiles && warp == 0)
-        issue(0, tmem);
-    bool ok = true;
-    uint32_t phase = 0;
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
-        const int buf = it & 1;
-        const long long next = tile + gridDim.x;
-        // prefetch the next patch into the other buffer (its last reader, the
-        // previous tile's MMAs, completed before this tile's were issued)
-        if (next < ntiles)
-            load_patch(next, buf ^ 1);
-        cnn::cp_async_commit();
-        // this tile's MMAs
-        if (!mbar_wait(&s_mma, phase, limit))
-            ok = false;
-        phase ^= 1u;
-        umma::fence_after_sync();
-        // issue the next tile's MMAs into the other accumulator before pooling this one
-        cnn::cp_async_wait<0>();
-        fence_proxy_async_smem();
-        umma::fence_before_sync();
-        __syncthreads(); // next patch complete; every thread past this tile's MMA wait
-        if (next < ntiles && warp == 0)
-            issue(buf ^ 1, tmem + (uint32_t)((buf ^ 1) * C2_TMEM_COLS));
-        // accumulator rows (TMEM lane = row) to shared memory: warp w takes
-        // lanes 32(w%4).. and columns 32(w/4).. (row pitch C2_ACC_PITCH: the
-        // lanes' 16-byte stores hit distinct banks)
-        const int lq = warp & 3, ch = (warp >> 2) * 32;
-        const uint32_t acc = tmem + (uint32_t)(buf * C2_TMEM_COLS) + ((uint32_t)(32 * lq) << 16);
+    if (warp < C2_MMA_WARP) {
+        // worker warpgroup g: the CTA's tiles g, g + 4, ...
+        const int g = warp >> 2, ptid = tid & 127, q = warp & 3;
+        unsigned char *patch = sst + g * C2_STAGE_BYTES;
+        float *sacc = (float *)(patch + C2_PATCH_BYTES);
+        const uint32_t acc = tmem + (uint32_t)(g * C2_TMEM_COLS) + ((uint32_t)(32 * q) << 16);
+        uint32_t dphase = 0;
+        for (long long it = g; it < my_tiles; it += C2_WORKERS) {
+            const long long tile = blockIdx.x + it * gridDim.x;
+            const long long cell = tile / C2_TILES_PER_CELL;
+            const int t = (int)(tile % C2_TILES_PER_CELL);
+            // the patch: pixel 104t + r (r < 192) of the cell, 8 channels per 16-byte chunk
+            // (its last reader, this warpgroup's previous tile's MMAs, has completed)
+            const bf16 *src = y1 + (size_t)cell * C1 * C1 * CH1;
+            for (int c = ptid; c < C2_PATCH_ROWS * 4; c += 128) {
+                const int r = c >> 2, kc = c & 3, pix = 4 * C1 * t + r;
+                const bool in = pix < C1 * C1;
+                cnn::cp_async16(patch + kc * C2_PLANE + r * 16, in ? src + (size_t)pix * CH1 + kc * 8 : nullptr,
+                                in);
+            }
+            cnn::cp_async_commit();
+            cnn::cp_async_wait<0>();
+            fence_proxy_async_smem();
+            umma::fence_before_sync();
+            mbar_arrive(&s_full[g]);
+            const bool done = mbar_wait(&s_done[g], dphase, limit);
+            if (wg_any(g, !done)) { // the warpgroup leaves together (its barriers below)
+                s_err = 1;
+                break;
+            }
+            dphase ^= 1u;
+            umma::fence_after_sync();
+            // accumulator rows (TMEM lane = row) to shared memory: warp q takes
+            // lanes 32q.., all 64 columns (row pitch C2_ACC_PITCH: the lanes'
+            // 16-byte stores hit distinct banks)
 #pragma unroll 1
-        for (int cb = ch; cb < ch + 32; cb += 16) {
-            float v[16];
-            umma::ld_16cols(acc + cb, v);
-            float4 *dst = (float4 *)(sacc + (32 * lq + lane) * C2_ACC_PITCH + cb);
+            for (int cb = 0; cb < CH2; cb += 16) {
+                float v[16];
+                umma::ld_16cols(acc + cb, v);
+                float4 *dst = (float4 *)(sacc + (32 * q + lane) * C2_ACC_PITCH + cb);
 #pragma unroll
-            for (int i = 0; i < 4; i++)
-                dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-        }
-        umma::fence_before_sync();
-        __syncthreads(); // accumulator staged
-        // pool: 2 row-pairs x 12 windows x 16 groups of 4 channels (lanes read
-        // consecutive 16-byte chunks); window (P, px) = rows 52P + 2px +
-        // {0, 1, 26, 27}, (dy, dx) = (0,0) (0,1) (1,0) (1,1)
-        const long long cell = tile / C2_TILES_PER_CELL;
-        const int t = (int)(tile % C2_TILES_PER_CELL);
-        for (int o = tid; o < 2 * PO * (CH2 / 4); o += C2_THREADS) {
-            const int cg = o % (CH2 / 4), w = o / (CH2 / 4), P = w / PO, px = w % PO;
-            const int r0 = 52 * P + 2 * px;
-            const int rows[4] = {r0, r0 + 1, r0 + C1, r0 + C1 + 1};
-            const float4 bb = *(const float4 *)(s_bias + cg * 4);
-            float best[4];
-            int arg[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const float4 a = *(const float4 *)(sacc + rows[i] * C2_ACC_PITCH + cg * 4);
-                const float x[4] = {fmaxf(a.x + bb.x, 0.f), fmaxf(a.y + bb.y, 0.f), fmaxf(a.z + bb.z, 0.f),
-                                    fmaxf(a.w + bb.w, 0.f)};
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-                    if (i == 0 || x[c] > best[c]) { // first maximum wins
-                        best[c] = x[c];
-                        arg[c] = i;
-                    }
+                for (int e = 0; e < 4; e++)
+                    dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
             }
-            __align__(8) bf16 ov[4];
-            __align__(4) uint8_t oa[4];
+            wg_sync(g); // accumulator staged
+            // pool: 2 row-pairs x 12 windows x 16 groups of 4 channels (lanes read
+            // consecutive 16-byte chunks); window (P, px) = rows 52P + 2px +
+            // {0, 1, 26, 27}, (dy, dx) = (0,0) (0,1) (1,0) (1,1)
+            for (int o = ptid; o < 2 * PO * (CH2 / 4); o += 128) {
+                const int cg = o % (CH2 / 4), w = o / (CH2 / 4), P = w / PO, px = w % PO;
+                const int r0 = 52 * P + 2 * px;
+                const int rows[4] = {r0, r0 + 1, r0 + C1, r0 + C1 + 1};
+                const float4 bb = *(const float4 *)(s_bias + cg * 4);
+                float best[4];
+                int arg[4];
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
-                ov[c] = __float2bfloat16_rn(best[c]);
-                oa[c] = (uint8_t)arg[c];
+                for (int e = 0; e < 4; e++) {
+                    const float4 a = *(const float4 *)(sacc + rows[e] * C2_ACC_PITCH + cg * 4);
+                    const float x[4] = {fmaxf(a.x + bb.x, 0.f), fmaxf(a.y + bb.y, 0.f), fmaxf(a.z + bb.z, 0.f),
+                                        fmaxf(a.w + bb.w, 0.f)};
+#pragma unroll
+                    for (int c = 0; c < 4; c++)
+                        if (e == 0 || x[c] > best[c]) { // first maximum wins
+                            best[c] = x[c];
+                            arg[c] = e;
+                        }
+                }
+                __align__(8) bf16 ov[4];
+                __align__(4) uint8_t oa[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    ov[c] = __float2bfloat16_rn(best[c]);
+                    oa[c] = (uint8_t)arg[c];
+                }
+                const size_t qo = ((size_t)cell * PO + 2 * t + P) * PO + px; // pooled pixel (cell, py, px)
+                *(uint2 *)(y2 + qo * CH2 + cg * 4) = *(const uint2 *)ov;
+                *(uint32_t *)(argmax + qo * CH2 + cg * 4) = *(const uint32_t *)oa;
             }
-            const size_t qo = ((size_t)cell * PO + 2 * t + P) * PO + px; // pooled pixel (cell, py, px)
-            *(uint2 *)(y2 + qo * CH2 + cg * 4) = *(const uint2 *)ov;
-            *(uint32_t *)(argmax + qo * CH2 + cg * 4) = *(const uint32_t *)oa;
+            wg_sync(g); // the staged accumulator is read
         }
-        __syncthreads(); // the staged accumulator is read
+    } else {
+        // the MMA warp: tiles in order, stage and accumulator it % 4; one elected lane issues
+        for (long long it = 0; it < my_tiles; it++) {
+            const int g = (int)(it % C2_WORKERS);
+            if (!__all_sync(0xffffffffu, mbar_wait(&s_full[g], (uint32_t)(it / C2_WORKERS) & 1u, limit))) {
+                s_err = 1;
+                break;
+            }
+            umma::fence_after_sync();
+            // descriptors differ only in their start address (16-byte units, low bits)
+            const uint64_t da = umma::smem_desc(smem_addr(sst + g * C2_STAGE_BYTES), C2_PLANE, 128);
+            const uint64_t db = umma::smem_desc(smem_addr(sw), 128, 512);
+            const uint32_t d = tmem + (uint32_t)(g * C2_TMEM_COLS);
+            if (umma::elect_one()) {
+#pragma unroll
+                for (int tap = 0; tap < 9; tap++) {
+                    const uint32_t shift = (uint32_t)((tap / 3) * C1 + tap % 3); // start row 26*ky + kx
+#pragma unroll
+                    for (int j = 0; j < 2; j++) // channels 16j..16j+15: planes 2j, 2j+1
+                        umma::mma_bf16(d, da + shift + 2 * j * (C2_PLANE / 16),
+                                       db + (uint32_t)(tap * C2_W_TAP_BYTES + j * 256) / 16, idesc,
+                                       tap > 0 || j > 0);
+                }
+                umma::commit(&s_done[g]);
+            }
+            __syncwarp();
+        }
+        if (umma::elect_one())
+            umma::commit(&s_fin); // arrives once every MMA issued above has completed
+        __syncwarp();
+        if (!__all_sync(0xffffffffu, mbar_wait(&s_fin, 0, limit)))
+            s_err = 1;
     }
-    cnn::cp_async_wait<0>();
-    if (!ok)
-        set_status(d_status, TDP_ERR_TIMEOUT);
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (tid == 0 && s_err)
+        set_status(d_status, TDP_ERR_TIMEOUT);
+    if (warp == C2_MMA_WARP) {
         umma::fence_after_sync();
-        umma::tmem_dealloc(tmem, 2 * C2_TMEM_COLS);
+        umma::tmem_dealloc(tmem, C2_TMEM_ALLOC);
     }
 }
 
@@ -493,8 +525,15 @@ __global__ void __launch_bounds__(C2_THREADS) conv2_pool_umma_kernel(const bf16 
 // K-major planes.  W2 of every tap is kept transposed as [32 ci][64 co]
 // core matrices for the CTA's life.  N = 32 (ci), 4 K16 steps per tap.  The
 // epilogue applies the ReLU mask of y1 from registers (no shared memory).
-// Patches and accumulators are double-buffered as in the forward.
-constexpr int DG_THREADS = 256;
+// Warp roles: four worker warpgroups, each owning one patch stage and one
+// 32-column accumulator, take every fourth tile of the CTA: build the patch,
+// hand it to the MMA warp (mbarrier full[g], 128 arrivals), fetch the next
+// tile's pooled gradient, wait for the MMAs (done[g], tcgen05.commit) and
+// write the masked dz1 rows; one more warp issues the MMAs tile by tile.
+// While one warpgroup waits on memory the others build, drain or compute.
+constexpr int DG_WORKERS = 4;
+constexpr int DG_THREADS = 128 * DG_WORKERS + 32;
+constexpr int DG_MMA_WARP = 4 * DG_WORKERS;
 constexpr int DG_P = 28;                              // padded pitch
 constexpr int DG_PIX = C1 * DG_P;                     // m' per cell: 26 rows x 28
 constexpr int DG_TILES_PER_CELL = (DG_PIX + 127) / 128; // 6
@@ -503,7 +542,9 @@ constexpr int DG_PLANE = DG_PATCH_ROWS * 16;
 constexpr int DG_PATCH_BYTES = 8 * DG_PLANE;          // 64 channels
 constexpr int DG_W_TAP_BYTES = CH1 * CH2 * 2;         // [32 ci][64 co]
 constexpr int DG_W_BYTES = 9 * DG_W_TAP_BYTES;
-constexpr uint32_t DG_TMEM_COLS = 32;
+constexpr uint32_t DG_TMEM_COLS = 32;                 // one accumulator
+constexpr uint32_t DG_TMEM_ALLOC = DG_WORKERS * DG_TMEM_COLS;
+static_assert(DG_W_BYTES + DG_WORKERS * DG_PATCH_BYTES + 1024 <= 232448, "conv2 data gradient shared memory");
 
 __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16 *__restrict__ dy2p,
                                                                       const uint8_t *__restrict__ argmax,
@@ -513,17 +554,24 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
                                                                       uint32_t limit)
 {
     extern __shared__ __align__(1024) unsigned char dg_smem[];
-    unsigned char *sw = dg_smem;                // W2 transposed, 9 taps
-    unsigned char *sp = dg_smem + DG_W_BYTES;   // two patches
-    __shared__ __align__(8) uint64_t s_mma;
+    unsigned char *sw = dg_smem;              // W2 transposed, 9 taps
+    unsigned char *sp = dg_smem + DG_W_BYTES; // one patch per worker warpgroup
+    __shared__ __align__(8) uint64_t s_full[DG_WORKERS], s_done[DG_WORKERS], s_fin;
     __shared__ uint32_t s_tmem;
+    __shared__ int s_err;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t idesc = umma::idesc_bf16_f32(128, CH1);
 
-    if (tid == 0)
-        mbar_init(&s_mma, 1);
-    if (warp == 0) {
-        umma::tmem_alloc(&s_tmem, 2 * DG_TMEM_COLS);
+    if (tid == 0) {
+        for (int g = 0; g < DG_WORKERS; g++) {
+            mbar_init(&s_full[g], 128);
+            mbar_init(&s_done[g], 1);
+        }
+        mbar_init(&s_fin, 1);
+        s_err = 0;
+    }
+    if (warp == DG_MMA_WARP) {
+        umma::tmem_alloc(&s_tmem, DG_TMEM_ALLOC);
         umma::fence_before_sync();
     }
     // W2[co][tap][ci] -> tap: K-major [ci][co]: chunk (ci, kc) = co 8kc..8kc+7
@@ -535,91 +583,111 @@ __global__ void __launch_bounds__(DG_THREADS) conv2_dgrad_umma_kernel(const bf16
             v[e] = w2[((size_t)(kc * 8 + e) * 9 + tap) * CH1 + ci];
         *(uint4 *)(sw + tap * DG_W_TAP_BYTES + umma::chunk_off(ci, kc, 8)) = *(const uint4 *)v;
     }
-    // the patch of a tile: dzp[128t + r], r < 192, 8 channels per 16-byte chunk
-    auto build_patch = [&](long long tile, int buf) {
-        const long long cell = tile / DG_TILES_PER_CELL;
-        const int i0 = (int)(tile % DG_TILES_PER_CELL) * 128;
-        Dz2Items items;
-        dz2_load<DG_P, 2>(items, i0, DG_PATCH_ROWS, dy2p, argmax, cell, tid, DG_THREADS);
-        dz2_store<DG_P, 2>(items, sp + buf * DG_PATCH_BYTES, DG_PLANE, i0, DG_PATCH_ROWS, tid, DG_THREADS);
-    };
-    // the 36 MMAs of a tile (warp 0, one elected lane)
-    auto issue = [&](int buf, uint32_t acc) {
-        // descriptors differ only in their start address (16-byte units, low bits)
-        const uint64_t da = umma::smem_desc(smem_addr(sp + buf * DG_PATCH_BYTES), DG_PLANE, 128);
-        const uint64_t db = umma::smem_desc(smem_addr(sw), 128, 1024);
-        umma::fence_after_sync();
-        if (umma::elect_one()) {
-#pragma unroll
-            for (int tap = 0; tap < 9; tap++) {
-                const int ky = tap / 3, kx = tap % 3;
-                const uint32_t shift = (uint32_t)((2 - ky) * DG_P + (2 - kx));
-#pragma unroll
-                for (int j = 0; j < CH2 / 16; j++) // co 16j..16j+15: planes 2j, 2j+1
-                    umma::mma_bf16(acc, da + shift + 2 * j * (DG_PLANE / 16),
-                                   db + (uint32_t)(tap * DG_W_TAP_BYTES + j * 256) / 16, idesc, tap > 0 || j > 0);
-            }
-            umma::commit(&s_mma);
-        }
-        __syncwarp();
-    };
-
-    long long tile = blockIdx.x;
-    if (tile < ntiles)
-        build_patch(tile, 0);
-    fence_proxy_async_smem(); // W2 and the first patch visible to the tensor cores
-    __syncthreads();          // ... and the mbarrier and tensor-memory address
+    fence_proxy_async_smem(); // W2 visible to the tensor cores
+    __syncthreads();          // ... and the mbarriers and tensor-memory address
     umma::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    if (tile < ntiles && warp == 0)
-        issue(0, tmem);
-    bool ok = true;
-    uint32_t phase = 0;
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
-        const int buf = it & 1;
-        const long long next = tile + gridDim.x;
-        if (next < ntiles) // its last reader, the previous tile's MMAs, has completed
-            build_patch(next, buf ^ 1);
-        fence_proxy_async_smem();
-        if (!mbar_wait(&s_mma, phase, limit))
-            ok = false;
-        phase ^= 1u;
-        umma::fence_after_sync();
-        umma::fence_before_sync();
-        __syncthreads(); // next patch built; every thread past this tile's MMA wait
-        if (next < ntiles && warp == 0)
-            issue(buf ^ 1, tmem + (uint32_t)((buf ^ 1) * DG_TMEM_COLS));
-        // epilogue: warp w reads lanes 32(w%4).. (its rows), columns 16(w/4)..
-        const long long cell = tile / DG_TILES_PER_CELL;
-        const int lq = warp & 3, cb = (warp >> 2) * 16;
-        const int i = (int)(tile % DG_TILES_PER_CELL) * 128 + 32 * lq + lane; // m'
-        float v[16];
-        umma::ld_16cols(tmem + (uint32_t)(buf * DG_TMEM_COLS) + ((uint32_t)(32 * lq) << 16) + cb, v);
-        const int y = i / DG_P, x = i % DG_P;
-        if (i < DG_PIX && x < C1) {
-            const size_t o = (((size_t)cell * C1 + y) * C1 + x) * CH1 + cb;
-            const uint4 *mk = (const uint4 *)(y1 + o);
-            uint4 *dst = (uint4 *)(dz1 + o);
+    if (warp < DG_MMA_WARP) {
+        // worker warpgroup g: the CTA's tiles g, g + 4, ... (patch stage g, accumulator g)
+        const int g = warp >> 2, ptid = tid & 127, q = warp & 3;
+        unsigned char *stage = sp + g * DG_PATCH_BYTES;
+        const uint32_t acc = tmem + (uint32_t)(g * DG_TMEM_COLS) + ((uint32_t)(32 * q) << 16);
+        uint32_t dphase = 0;
+        Dz2Items items;
+        if (g < my_tiles) {
+            const long long tile = blockIdx.x + (long long)g * gridDim.x;
+            dz2_load<DG_P, 2>(items, (int)(tile % DG_TILES_PER_CELL) * 128, DG_PATCH_ROWS, dy2p, argmax,
+                              tile / DG_TILES_PER_CELL, ptid, 128);
+        }
+        for (long long it = g; it < my_tiles; it += DG_WORKERS) {
+            const long long tile = blockIdx.x + it * gridDim.x;
+            const long long cell = tile / DG_TILES_PER_CELL;
+            const int i0 = (int)(tile % DG_TILES_PER_CELL) * 128;
+            // the stage's last reader, this warpgroup's previous tile's MMAs, has completed
+            dz2_store<DG_P, 2>(items, stage, DG_PLANE, i0, DG_PATCH_ROWS, ptid, 128);
+            fence_proxy_async_smem();
+            umma::fence_before_sync(); // the previous tile's accumulator loads precede the hand-over
+            mbar_arrive(&s_full[g]);
+            if (it + DG_WORKERS < my_tiles) { // the next tile's pooled gradient, in flight meanwhile
+                const long long nt = tile + (long long)DG_WORKERS * gridDim.x;
+                dz2_load<DG_P, 2>(items, (int)(nt % DG_TILES_PER_CELL) * 128, DG_PATCH_ROWS, dy2p, argmax,
+                                  nt / DG_TILES_PER_CELL, ptid, 128);
+            }
+            if (!mbar_wait(&s_done[g], dphase, limit)) {
+                s_err = 1;
+                break;
+            }
+            dphase ^= 1u;
+            umma::fence_after_sync();
+            // epilogue: warp q holds m' = i0 + 32q + lane, all 32 ci
+            float v0[16], v1[16];
+            umma::ld_16cols(acc, v0);
+            umma::ld_16cols(acc + 16, v1);
+            const int i = i0 + 32 * q + lane, y = i / DG_P, x = i % DG_P;
+            if (i < DG_PIX && x < C1) {
+                const size_t o = (((size_t)cell * C1 + y) * C1 + x) * CH1;
+                const uint4 *mk = (const uint4 *)(y1 + o);
+                uint4 mm[4];
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint4 mm = mk[h];
-                const bf16 *mb = (const bf16 *)&mm;
-                __align__(16) bf16 ov[8];
+                for (int h = 0; h < 4; h++)
+                    mm[h] = mk[h];
+                uint4 *dst = (uint4 *)(dz1 + o);
 #pragma unroll
-                for (int e = 0; e < 8; e++)
-                    ov[e] = __float2bfloat16_rn(bf2f(mb[e]) > 0.f ? v[8 * h + e] : 0.f);
-                dst[h] = *(const uint4 *)ov;
+                for (int h = 0; h < 4; h++) {
+                    const bf16 *mb = (const bf16 *)&mm[h];
+                    __align__(16) bf16 ov[8];
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const float val = h < 2 ? v0[8 * h + e] : v1[8 * (h - 2) + e];
+                        ov[e] = __float2bfloat16_rn(bf2f(mb[e]) > 0.f ? val : 0.f);
+                    }
+                    dst[h] = *(const uint4 *)ov;
+                }
             }
         }
+    } else {
+        // the MMA warp: tiles in order, stage and accumulator it % 4; one elected lane issues
+        for (long long it = 0; it < my_tiles; it++) {
+            const int g = (int)(it % DG_WORKERS);
+            if (!__all_sync(0xffffffffu, mbar_wait(&s_full[g], (uint32_t)(it / DG_WORKERS) & 1u, limit))) {
+                s_err = 1;
+                break;
+            }
+            umma::fence_after_sync();
+            // descriptors differ only in their start address (16-byte units, low bits)
+            const uint64_t da = umma::smem_desc(smem_addr(sp + g * DG_PATCH_BYTES), DG_PLANE, 128);
+            const uint64_t db = umma::smem_desc(smem_addr(sw), 128, 1024);
+            const uint32_t d = tmem + (uint32_t)(g * DG_TMEM_COLS);
+            if (umma::elect_one()) {
+#pragma unroll
+                for (int tap = 0; tap < 9; tap++) {
+                    const int ky = tap / 3, kx = tap % 3;
+                    const uint32_t shift = (uint32_t)((2 - ky) * DG_P + (2 - kx));
+#pragma unroll
+                    for (int j = 0; j < CH2 / 16; j++) // co 16j..16j+15: planes 2j, 2j+1
+                        umma::mma_bf16(d, da + shift + 2 * j * (DG_PLANE / 16),
+                                       db + (uint32_t)(tap * DG_W_TAP_BYTES + j * 256) / 16, idesc,
+                                       tap > 0 || j > 0);
+                }
+                umma::commit(&s_done[g]);
+            }
+            __syncwarp();
+        }
+        if (umma::elect_one())
+            umma::commit(&s_fin); // arrives once every MMA issued above has completed
+        __syncwarp();
+        if (!__all_sync(0xffffffffu, mbar_wait(&s_fin, 0, limit)))
+            s_err = 1;
     }
-    if (!ok)
-        set_status(d_status, TDP_ERR_TIMEOUT);
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (tid == 0 && s_err)
+        set_status(d_status, TDP_ERR_TIMEOUT);
+    if (warp == DG_MMA_WARP) {
         umma::fence_after_sync();
-        umma::tmem_dealloc(tmem, 2 * DG_TMEM_COLS);
+        umma::tmem_dealloc(tmem, DG_TMEM_ALLOC);
     }
 }
 
@@ -1309,13 +1377,13 @@ tdp_status tdp_cnn_conv2_pool_fwd(const void *y1, int64_t n_cells, const void *w
     if (((uintptr_t)y1 | (uintptr_t)w2 | (uintptr_t)y2 | (uintptr_t)argmax) % 16)
         return TDP_ERR_INVALID_ARG;
     const long long ntiles = n_cells * C2_TILES_PER_CELL;
-    const size_t smem = (size_t)C2_W_BYTES + 2 * C2_PATCH_BYTES + C2_ACC_BYTES;
+    const size_t smem = (size_t)C2_W_BYTES + C2_WORKERS * C2_STAGE_BYTES;
     if (cudaFuncSetAttribute(conv2_pool_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
         cudaFuncSetAttribute(conv2_pool_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return TDP_ERR_CUDA;
-    const long long grid = std::min<long long>(ntiles, (long long)umma_ctas_per_sm(smem, 2 * C2_TMEM_COLS) * num_sms());
+    const long long grid = std::min<long long>(ntiles, (long long)umma_ctas_per_sm(smem, C2_TMEM_ALLOC) * num_sms());
     conv2_pool_umma_kernel<<<(unsigned)grid, C2_THREADS, smem, (cudaStream_t)stream>>>(
         (const bf16 *)y1, (const bf16 *)w2, b2, (bf16 *)y2, argmax, ntiles, d_status, spin_limit());
     return launch_status();
@@ -1456,14 +1524,14 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
     // dgrad (optional): dz1[cell][y][x][ci] = (sum dz2 * w2) * (y1 > 0), tcgen05
     if (dz1) {
         const long long ntiles = n_cells * DG_TILES_PER_CELL;
-        const size_t smem = (size_t)DG_W_BYTES + 2 * DG_PATCH_BYTES;
+        const size_t smem = (size_t)DG_W_BYTES + DG_WORKERS * DG_PATCH_BYTES;
         if (cudaFuncSetAttribute(conv2_dgrad_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(conv2_dgrad_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return TDP_ERR_CUDA;
         const long long grid =
-            std::min<long long>(ntiles, (long long)umma_ctas_per_sm(smem, 2 * DG_TMEM_COLS) * num_sms());
+            std::min<long long>(ntiles, (long long)umma_ctas_per_sm(smem, DG_TMEM_ALLOC) * num_sms());
         conv2_dgrad_umma_kernel<<<(unsigned)grid, DG_THREADS, smem, s>>>(
             (const bf16 *)dy2p, argmax, (const bf16 *)w2, (const bf16 *)y1, (bf16 *)dz1, ntiles, d_status,
             spin_limit());

@@ -57,8 +57,10 @@ def test_conv1_layer():
     assert np.mean(got == ref) > 0.99
 
 
-@pytest.mark.parametrize("ncell", [2, 9, 64])
+@pytest.mark.parametrize("ncell", [2, 9, 64, 256])
 def test_conv2_pool_layer(ncell):
+    """256 cells give every CTA ten or more tiles (each worker stage and
+    accumulator reused)."""
     r = np.random.default_rng(ncell)
     y1 = bf16_np(np.abs(r.standard_normal((ncell, 26, 26, 32))) * (r.random((ncell, 26, 26, 32)) > 0.3))
     w2 = bf16_np(r.uniform(-0.08, 0.08, (64, 3, 3, 32)))
@@ -89,11 +91,11 @@ def _batch(n_grids, seed):
     return img, lab, t
 
 
-@pytest.mark.parametrize("ncell", [9, 160])
+@pytest.mark.parametrize("ncell", [9, 160, 256])
 def test_conv2_backward_layer(ncell):
     """conv2 data and weight gradients (tcgen05) against the float64 oracle;
-    160 cells give every CTA of both kernels several tiles (the
-    double-buffered path).  Inputs are bf16, products exact in fp32, so the
+    160 and 256 cells give every CTA of both kernels several tiles (each
+    worker stage and accumulator reused).  Inputs are bf16, products exact in fp32, so the
     weight gradient agrees to fp32 accumulation error and dz1 to its bf16
     rounding."""
     r = np.random.default_rng(100 + ncell)

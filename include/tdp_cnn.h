@@ -53,9 +53,16 @@ tdp_status tdp_cnn_conv2_pool_fwd(const void *y1, int64_t n_cells, const void *w
 /* Workspace bytes of tdp_cnn_fc1_fwd. */
 size_t tdp_cnn_fc1_fwd_workspace(int64_t n_cells);
 
-/* fc1 + bias + ReLU (split-K GEMM, fp32 partials summed in ws). */
+/*
+ * fc1 + bias + ReLU: h1 bf16 [n_cells][128] = relu(y2 . wfc1^T + bfc1), y2 bf16
+ * [n_cells][9216], wfc1 bf16 [128][9216], bfc1 fp32 [128].  A split-K GEMM on
+ * the 5th-gen tensor cores (tcgen05), fp32 partials summed in ws in a fixed
+ * order.  y2 and wfc1 must be 16-byte aligned, else TDP_ERR_INVALID_ARG.  A
+ * bounded device wait that runs out sets TDP_ERR_TIMEOUT in *d_status
+ * (nullable).
+ */
 tdp_status tdp_cnn_fc1_fwd(const void *y2, int64_t n_cells, const void *wfc1, const float *bfc1, void *h1, void *ws,
-                           size_t ws_bytes, tdp_stream_t stream);
+                           size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
 
 /* Workspace bytes of tdp_cnn_head. */
 size_t tdp_cnn_head_workspace(int64_t n_grids);
@@ -80,12 +87,17 @@ tdp_status tdp_cnn_head(const void *h1, int64_t n_grids, const float *wfc2, cons
 size_t tdp_cnn_fc1_bwd_workspace(int64_t n_cells);
 
 /*
- * fc1 backward.  dy2p bf16 [n_cells][9216] = (dh1 . wfc1) masked by y2 > 0
- * (the gradient at the pooled map, through the ReLU); dwfc1 fp32 [128][9216];
- * dbfc1 fp32 [128].  dh1 must be 16-byte aligned, else TDP_ERR_INVALID_ARG.
+ * fc1 backward from dh1 bf16 [n_cells][128] (the gradient at fc1's output,
+ * ReLU applied).  dy2p bf16 [n_cells][9216] = (dh1 . wfc1) masked by y2 > 0
+ * (the gradient at the pooled map, through the ReLU); dwfc1 fp32 [128][9216]
+ * = dh1^T . y2 (split-K); dbfc1 fp32 [128] = column sums of dh1.  Both
+ * products on the 5th-gen tensor cores (tcgen05).  dh1, y2, wfc1 and dy2p
+ * must be 16-byte aligned, else TDP_ERR_INVALID_ARG.  A bounded device wait
+ * that runs out sets TDP_ERR_TIMEOUT in *d_status (nullable).
  */
 tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, int64_t n_cells, void *dy2p,
-                           float *dwfc1, float *dbfc1, void *ws, size_t ws_bytes, tdp_stream_t stream);
+                           float *dwfc1, float *dbfc1, void *ws, size_t ws_bytes, int32_t *d_status,
+                           tdp_stream_t stream);
 
 /* Workspace bytes of tdp_cnn_conv2_bwd. */
 size_t tdp_cnn_conv2_bwd_workspace(int64_t n_cells);

@@ -107,6 +107,17 @@ def conv2_backward(dy2, arg, y1, w2):
     return dy1 * (y1 > 0), gw2, dz2.sum(axis=(0, 1, 2))
 
 
+def fc1_backward(dh1, flat, wf1):
+    """fc1 gradients from dh1 [B, 128] (the gradient at fc1's output, ReLU
+    applied), its input flat [B, 9216] (the pooled map, itself a ReLU output)
+    and weights wf1 [128, 9216]: (dh1 . wf1 masked by flat > 0, the gradient
+    at the pooled map through its ReLU; dW = dh1^T . flat; db = column sums of
+    dh1).  float64."""
+    dh1 = np.asarray(dh1, np.float64)
+    flat = np.asarray(flat, np.float64)
+    return (dh1 @ np.asarray(wf1, np.float64)) * (flat > 0), dh1.T @ flat, dh1.sum(axis=0)
+
+
 def conv1_backward(dz1, x0):
     """conv1 weight and bias gradients of the valid 3x3 correlation in the
     Sec. 5.5 CNN: dW1[o, ky, kx] = sum over cells
@@ -176,10 +187,8 @@ def backward(params, fw, target):
     dh1 = _q((dlogits @ p["fc2_w"]) * (h1 > 0), quant)
     B = h1.shape[0]
     flat = fw["y2"].reshape(B, 9216)
-    g["fc1_w"] = dh1.T @ flat
-    g["fc1_b"] = dh1.sum(axis=0)
-    dflat = dh1 @ fw["wf1"]  # [B, 9216]
-    dy2 = _q(dflat.reshape(B, 12, 12, 64) * (fw["y2"] > 0), quant)
+    dflat, g["fc1_w"], g["fc1_b"] = fc1_backward(dh1, flat, fw["wf1"])
+    dy2 = _q(dflat.reshape(B, 12, 12, 64), quant)
     y1 = fw["y1"]
     dz1, g["conv2_w"], g["conv2_b"] = conv2_backward(dy2, fw["arg"], y1, fw["w2"])
     dz1 = _q(dz1, quant)

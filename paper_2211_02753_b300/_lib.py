@@ -92,11 +92,11 @@ SIGNATURES = {
     "tdp_cnn_conv1_fwd": (_st, [_p, _i64, _p, _p, _p, _p]),
     "tdp_cnn_conv2_pool_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _p, _p]),
     "tdp_cnn_fc1_fwd_workspace": (_sz, [_i64]),
-    "tdp_cnn_fc1_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _sz, _p]),
+    "tdp_cnn_fc1_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_cnn_head_workspace": (_sz, [_i64]),
     "tdp_cnn_head": (_st, [_p, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "tdp_cnn_fc1_bwd_workspace": (_sz, [_i64]),
-    "tdp_cnn_fc1_bwd": (_st, [_p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p]),
+    "tdp_cnn_fc1_bwd": (_st, [_p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_cnn_conv2_bwd_workspace": (_sz, [_i64]),
     "tdp_cnn_conv2_bwd": (_st, [_p, _p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_cnn_conv1_bwd_workspace": (_sz, [_i64]),

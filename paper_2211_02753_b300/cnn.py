@@ -91,7 +91,7 @@ class GlyphQuery:
         L.call("tdp_cnn_conv2_pool_fwd", _ptr(b["y1"]), nc, _ptr(self.bf["conv2_w"]), _ptr(p["conv2_b"]),
                _ptr(b["y2"]), _ptr(b["argmax"]), _ptr(self.status), s)
         L.call("tdp_cnn_fc1_fwd", _ptr(b["y2"]), nc, _ptr(self.bf["fc1_w"]), _ptr(p["fc1_b"]), _ptr(b["h1"]), ws,
-               wsn, s)
+               wsn, _ptr(self.status), s)
         g = self.g
         L.call("tdp_cnn_head", _ptr(b["h1"]), n, _ptr(p["fc2_w"]), _ptr(p["fc2_b"]), _ptr(targets),
                _ptr(b["logits"]), _ptr(b["P"]), _ptr(b["pred"]),
@@ -110,7 +110,7 @@ class GlyphQuery:
         g = self.g
         ws, wsn = _ptr(b["ws"]), b["ws"].numel()
         L.call("tdp_cnn_fc1_bwd", _ptr(b["dh1"]), _ptr(b["y2"]), _ptr(self.bf["fc1_w"]), nc, _ptr(b["dy2p"]),
-               _ptr(g["fc1_w"]), _ptr(g["fc1_b"]), ws, wsn, s)
+               _ptr(g["fc1_w"]), _ptr(g["fc1_b"]), ws, wsn, _ptr(self.status), s)
         L.call("tdp_cnn_conv2_bwd", _ptr(b["dy2p"]), _ptr(b["argmax"]), _ptr(b["y1"]), _ptr(self.bf["conv2_w"]), nc,
                _ptr(b["dz1"]), _ptr(g["conv2_w"]), _ptr(g["conv2_b"]), ws, wsn, _ptr(self.status), s)
         L.call("tdp_cnn_conv1_bwd", _ptr(b["dz1"]), _ptr(grids), nc, _ptr(g["conv1_w"]), _ptr(g["conv1_b"]), ws,

@@ -3,21 +3,19 @@
 //
 // Layers (cells of 28x28 uint8, read in place from the 112x112 grid images):
 //   conv1 3x3 1->32 + ReLU       direct, CUDA cores (K = 9), bf16 NHWC out
-//   conv2 3x3 32->64 + ReLU      implicit GEMM on tensor cores (K = 288),
-//     + 2x2 max-pool             epilogue: rows are ordered pool-window-major,
-//                                so a window is 4 consecutive rows; bf16 pooled
-//                                map + per-channel arg-max byte
-//   fc1 9216->128 + ReLU         GEMM, split-K, bf16 out
+//   conv2 3x3 32->64 + ReLU      nine accumulating tcgen05 GEMMs over shifted
+//     + 2x2 max-pool             views of one input patch; bias, ReLU, pool
+//                                and per-channel arg-max byte in the epilogue
+//   fc1 9216->128 + ReLU         tcgen05 GEMM, split-K, bf16 out
 //   fc2 128->10, softmax, soft COUNT per class and soft row SUM per grid row,
 //   MSE loss and its backward    one block per grid (16 cells), fp32
-// Backward: fc1 dgrad (pool-gradient masked by ReLU), fc1 wgrad (split-K),
-// conv2 dgrad (implicit GEMM whose A operand expands the pooled gradient
-// through the arg-max on the fly), conv2 wgrad (split-K over pixels, same
-// expansion), conv1 wgrad/bias (CUDA cores), and a fused Adam step that also
-// refreshes the bf16 copies of the tensor-core weights.
-// Every GEMM is gemm_kernel (cnn_gemm.cuh) with its own operand loaders and
-// epilogue; no operand is transposed or materialised in im2col form.
-#include "cnn_gemm.cuh"
+// Backward: fc1 data gradient (masked by the pooled ReLU) and weight gradient
+// (split-K) as tcgen05 GEMMs; conv2 data and weight gradients on tcgen05,
+// their A operand the pre-pool gradient expanded from the pooled gradient
+// through the arg-max; conv1 weight and bias gradients on CUDA cores; a fused
+// Adam step that also refreshes the bf16 copies of the tensor-core weights.
+// No operand is transposed in global memory or materialised in im2col form.
+#include "cnn_async.cuh"
 #include "common.cuh"
 #include "umma.cuh"
 #include "tdp_cnn.h"
@@ -139,50 +137,235 @@ struct LoadMN { // MN-major: stored [k][ld], the operand's rows contiguous
 };
 
 // -------------------------------------------------------------- epilogues
+//
+// Called with 32 consecutive accumulator columns of one output row.  An
+// epilogue with PREFETCH also stages a tile of its own input in shared
+// memory (cp.async, issued before the main loop) and reads it back there.
 
 struct EpiPartialF32 { // out[split][m][ldo]
+    static constexpr bool PREFETCH = false;
     float *out;
     int M, ldo;
     size_t split_stride;
-    __device__ void operator()(int m, int n, float v0, float v1, int split) const
+    static constexpr int smem_bytes(int) { return 0; }
+    __device__ void prefetch(unsigned char *, int, int, int, int) const {}
+    __device__ void store(int m, int n, const float (&v)[32], int split, const unsigned char *, int, int) const
     {
         if (m >= M)
             return;
-        *(float2 *)(out + split * split_stride + (size_t)m * ldo + n) = make_float2(v0, v1);
+        float4 *d = (float4 *)(out + split * split_stride + (size_t)m * ldo + n);
+#pragma unroll
+        for (int e = 0; e < 8; e++)
+            d[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
     }
 };
 
-// bf16 out[m][ldo] = v * (mask[m][ldo] > 0)
+// bf16 out[m][ldo] = v * (mask[m][ldo] > 0); the mask tile (128 rows x BN)
+// is staged with a row pitch of BN*2 + 16 bytes (a warp's 16-byte reads of
+// 32 rows then hit distinct banks).
 struct EpiMaskedBf16 {
+    static constexpr bool PREFETCH = true;
     bf16 *out;
     const bf16 *mask;
     int M, ldo;
-    __device__ void operator()(int m, int n, float v0, float v1, int) const
+    static constexpr int pitch(int bn) { return bn * 2 + 16; }
+    static constexpr int smem_bytes(int bn) { return 128 * pitch(bn); }
+    __device__ void prefetch(unsigned char *buf, int m0, int n0, int bn, int tid) const
+    {
+        const int cpr = bn / 8; // 16-byte chunks per row
+        for (int c = tid; c < 128 * cpr; c += 128) {
+            const int r = c / cpr, j = c % cpr, m = m0 + r;
+            cnn::cp_async16(buf + r * pitch(bn) + j * 16, m < M ? mask + (size_t)m * ldo + n0 + j * 8 : nullptr,
+                            m < M);
+        }
+    }
+    __device__ void store(int m, int n, const float (&v)[32], int, const unsigned char *buf, int m0, int n0) const
     {
         if (m >= M)
             return;
-        size_t i = (size_t)m * ldo + n;
-        __nv_bfloat162 mk = *(const __nv_bfloat162 *)(mask + i);
-        __nv_bfloat162 o2;
-        o2.x = __float2bfloat16_rn(bf2f(mk.x) > 0.f ? v0 : 0.f);
-        o2.y = __float2bfloat16_rn(bf2f(mk.y) > 0.f ? v1 : 0.f);
-        *(__nv_bfloat162 *)(out + i) = o2;
+        const uint4 *mk = (const uint4 *)(buf + (m - m0) * pitch_bn + (n - n0) * 2);
+        uint4 *dst = (uint4 *)(out + (size_t)m * ldo + n);
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const uint4 mm = mk[h];
+            const bf16 *mb = (const bf16 *)&mm;
+            __align__(16) bf16 ov[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++)
+                ov[e] = __float2bfloat16_rn(bf2f(mb[e]) > 0.f ? v[8 * h + e] : 0.f);
+            dst[h] = *(const uint4 *)ov;
+        }
     }
+    int pitch_bn; // the staging row pitch, pitch(BN) of the launch
 };
 
-template <int BM, int BN, int WM, int WN, class LA, class LB, class EPI>
-static cudaError_t launch_gemm(const LA &la, const LB &lb, const EPI &epi, int M, int N, int K, int splits,
-                               cudaStream_t s)
+// ------------------------------------------------ dense GEMM on tcgen05
+//
+// C[m][n] = sum_k A(m, k) B(n, k) for the fully connected layer: one 128 x BN
+// output tile per CTA (and one K range of it under split-K), its fp32
+// accumulator in tensor memory (BN columns, TMEM lane = row).  Operands move
+// by cp.async in 64-k stages, STAGES deep, into padded no-swizzle
+// core-matrix layouts that let 8 lanes copy one whole 128-byte line of the
+// source into 8 distinct shared-memory bank groups:
+//   K-major ([row][k] in memory): chunk (row r, k-chunk kc) at
+//     (r / 8) * 1152 + kc * 144 + (r % 8) * 16  (LBO 144, SBO 1152, K16 step 288 B)
+//   MN-major ([k][row]): chunk (k, row-chunk rc) at
+//     rc * 1040 + k * 16                         (LBO 128, SBO 1040, K16 step 256 B)
+// (LBO: the next 8 k; SBO: the next 8 rows).  One elected lane of warp 0
+// issues a stage's four K16 MMAs and commits them to the stage's mbarrier;
+// the stage is refilled once that has fired (bounded wait).
+constexpr int UG_BM = 128, UG_BK = 64, UG_THREADS = 128;
+constexpr int UG_K_LBO = 144, UG_K_SBO = 8 * UG_K_LBO, UG_MN_SBO = UG_BK * 16 + 16;
+
+template <class L> constexpr int ug_op_bytes(int rows) { return L::MN_MAJOR ? rows / 8 * UG_MN_SBO : rows / 8 * UG_K_SBO; }
+template <class L> constexpr uint32_t ug_lbo() { return L::MN_MAJOR ? 128u : (uint32_t)UG_K_LBO; }
+template <class L> constexpr uint32_t ug_sbo() { return L::MN_MAJOR ? (uint32_t)UG_MN_SBO : (uint32_t)UG_K_SBO; }
+template <class L> constexpr uint32_t ug_kstep() { return 2 * ug_lbo<L>() / 16; } // 16-byte units per K16
+
+template <class L>
+__device__ __forceinline__ void ug_load(const L &ld, unsigned char *dst, int rows, int r0, int k0, int kend, int tid)
 {
-    constexpr size_t smem = gemm_smem<BM, BN, LA::MN_MAJOR, LB::MN_MAJOR>();
-    auto kern = gemm_kernel<BM, BN, WM, WN, LA, LB, EPI>;
+    for (int c = tid; c < rows * (UG_BK / 8); c += UG_THREADS) {
+        if constexpr (!L::MN_MAJOR) {
+            const int r = c >> 3, kc = c & 7; // 8 lanes: one row's 128 bytes
+            const void *src = ld.ptr(r, kc, r0, k0, kend);
+            cnn::cp_async16(dst + (r >> 3) * UG_K_SBO + kc * UG_K_LBO + (r & 7) * 16, src, src != nullptr);
+        } else {
+            const int nrc = rows / 8, rc = c % nrc, kk = c / nrc; // lanes along one k-row
+            const void *src = ld.ptr(kk, rc, r0, k0, kend);
+            cnn::cp_async16(dst + rc * UG_MN_SBO + kk * 16, src, src != nullptr);
+        }
+    }
+}
+
+template <int BN, class LA, class LB> constexpr int ug_stage_bytes()
+{
+    return ug_op_bytes<LA>(UG_BM) + ug_op_bytes<LB>(BN);
+}
+
+template <int BN, int STAGES, class LA, class LB, class EPI>
+__global__ void __launch_bounds__(UG_THREADS) umma_gemm_kernel(LA la, LB lb, EPI epi, int K, int k_per_split,
+                                                               int32_t *d_status, uint32_t limit)
+{
+    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256 && STAGES >= 2, "tile");
+    extern __shared__ __align__(1024) unsigned char ug_smem[];
+    __shared__ __align__(8) uint64_t s_mma[STAGES];
+    __shared__ uint32_t s_tmem;
+    constexpr int SB = ug_stage_bytes<BN, LA, LB>();
+    constexpr int A_BYTES = ug_op_bytes<LA>(UG_BM);
+    unsigned char *epi_buf = ug_smem + STAGES * SB;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(UG_BM, BN) | (LA::MN_MAJOR ? 1u << 15 : 0u) |
+                               (LB::MN_MAJOR ? 1u << 16 : 0u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * UG_BM, n0 = blockIdx.y * BN, split = blockIdx.z;
+    const int kbeg = split * k_per_split, kend = min(K, kbeg + k_per_split);
+    const int ktiles = kend > kbeg ? (kend - kbeg + UG_BK - 1) / UG_BK : 0;
+
+    if (tid == 0)
+        for (int st = 0; st < STAGES; st++)
+            mbar_init(&s_mma[st], 1);
+    if (warp == 0) {
+        umma::tmem_alloc(&s_tmem, BN);
+        umma::fence_before_sync();
+    }
+    if constexpr (EPI::PREFETCH)
+        epi.prefetch(epi_buf, m0, n0, BN, tid); // lands with the first stage's group
+    auto load = [&](int kt) {
+        unsigned char *st = ug_smem + (kt % STAGES) * SB;
+        const int k0 = kbeg + kt * UG_BK;
+        ug_load<LA>(la, st, UG_BM, m0, k0, kend, tid);
+        ug_load<LB>(lb, st + A_BYTES, BN, n0, k0, kend, tid);
+    };
+    for (int st = 0; st < STAGES - 1; st++) {
+        if (st < ktiles)
+            load(st);
+        cnn::cp_async_commit();
+    }
+    __syncthreads(); // the mbarriers and the tensor-memory address
+    umma::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    bool ok = true;
+    for (int kt = 0; kt < ktiles; kt++) {
+        cnn::cp_async_wait<STAGES - 2>(); // this thread's chunks of stage kt have landed
+        fence_proxy_async_smem();
+        __syncthreads(); // ... everyone's
+        if (warp == 0) {
+            umma::fence_after_sync();
+            const uint32_t a = smem_addr(ug_smem + (kt % STAGES) * SB);
+            const uint64_t da = umma::smem_desc(a, ug_lbo<LA>(), ug_sbo<LA>()),
+                           db = umma::smem_desc(a + A_BYTES, ug_lbo<LB>(), ug_sbo<LB>());
+            if (umma::elect_one()) {
+#pragma unroll
+                for (int j = 0; j < UG_BK / 16; j++)
+                    umma::mma_bf16(tmem, da + ug_kstep<LA>() * j, db + ug_kstep<LB>() * j, idesc, kt > 0 || j > 0);
+                umma::commit(&s_mma[kt % STAGES]);
+            }
+            __syncwarp();
+        }
+        // refill the stage of tile kt - 1 with tile kt + STAGES - 1 once its MMAs completed
+        const int nk = kt + STAGES - 1;
+        if (nk < ktiles) {
+            if (kt >= 1 && !mbar_wait(&s_mma[(kt - 1) % STAGES], (uint32_t)((kt - 1) / STAGES) & 1u, limit))
+                ok = false;
+            load(nk);
+        }
+        cnn::cp_async_commit();
+    }
+    // the last commit fires once every MMA has completed (they run in order)
+    if (ktiles > 0 &&
+        !mbar_wait(&s_mma[(ktiles - 1) % STAGES], (uint32_t)((ktiles - 1) / STAGES) & 1u, limit))
+        ok = false;
+    if constexpr (EPI::PREFETCH) {
+        cnn::cp_async_wait<0>();
+        __syncthreads(); // the staged epilogue input
+    }
+    umma::fence_after_sync();
+    const int m = m0 + 32 * warp + lane;
+#pragma unroll 1
+    for (int cb = 0; cb < BN; cb += 32) {
+        float v[32];
+        if (ktiles > 0) {
+            float lo[16], hi[16];
+            umma::ld_16cols(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, lo);
+            umma::ld_16cols(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cb + 16), hi);
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                v[e] = lo[e];
+                v[16 + e] = hi[e];
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; e++)
+                v[e] = 0.f; // an empty K range contributes zeros
+        }
+        epi.store(m, n0 + cb, v, split, epi_buf, m0, n0);
+    }
+    if (!ok)
+        set_status(d_status, TDP_ERR_TIMEOUT);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, BN);
+    }
+}
+
+// M x N output (N a multiple of BN), K split into `splits` ranges of whole stages.
+template <int BN, int STAGES, class LA, class LB, class EPI>
+static cudaError_t launch_umma_gemm(const LA &la, const LB &lb, const EPI &epi, int M, int N, int K, int splits,
+                                    int32_t *d_status, cudaStream_t s)
+{
+    if (N % BN)
+        return cudaErrorInvalidValue;
+    constexpr size_t smem = (size_t)STAGES * ug_stage_bytes<BN, LA, LB>() + EPI::smem_bytes(BN);
+    auto kern = umma_gemm_kernel<BN, STAGES, LA, LB, EPI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     int kps = (K + splits - 1) / splits;
-    kps = (kps + GBK - 1) / GBK * GBK;
-    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, splits);
-    kern<<<grid, GTHREADS, smem, s>>>(la, lb, epi, M, N, K, kps);
+    kps = (kps + UG_BK - 1) / UG_BK * UG_BK;
+    dim3 grid((M + UG_BM - 1) / UG_BM, N / BN, splits);
+    kern<<<grid, UG_THREADS, smem, s>>>(la, lb, epi, K, kps, d_status, spin_limit());
     return cudaGetLastError();
 }
 
@@ -929,9 +1112,10 @@ static inline int colsum_blocks(long long rows, int C)
 }
 
 // out[i] = sum_b part[b * stride + i] in float64, in a fixed order: slice s
-// (of PS_SLICES) sums b = s, s + PS_SLICES, ... in order, then the slices are
-// added by a fixed tree.  A block covers 32 consecutive outputs.
-constexpr int PS_SLICES = 16;
+// (of PS_SLICES) sums b = s, s + PS_SLICES, ... in order (eight loads in
+// flight), then the slices are added by a fixed tree.  A block covers 32
+// consecutive outputs.
+constexpr int PS_SLICES = 32;
 
 __global__ void __launch_bounds__(32 * PS_SLICES) partial_sum_kernel(const float *__restrict__ part, int nb, int n,
                                                                      size_t stride, float *__restrict__ out)
@@ -942,15 +1126,14 @@ __global__ void __launch_bounds__(32 * PS_SLICES) partial_sum_kernel(const float
     double acc = 0.0;
     if (i < n) {
         int b = sl;
-        for (; b + 3 * PS_SLICES < nb; b += 4 * PS_SLICES) {
-            const float a0 = part[(size_t)b * stride + i];
-            const float a1 = part[(size_t)(b + PS_SLICES) * stride + i];
-            const float a2 = part[(size_t)(b + 2 * PS_SLICES) * stride + i];
-            const float a3 = part[(size_t)(b + 3 * PS_SLICES) * stride + i];
-            acc += a0;
-            acc += a1;
-            acc += a2;
-            acc += a3;
+        for (; b + 7 * PS_SLICES < nb; b += 8 * PS_SLICES) {
+            float a[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                a[u] = part[(size_t)(b + u * PS_SLICES) * stride + i];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                acc += a[u];
         }
         for (; b < nb; b += PS_SLICES)
             acc += part[(size_t)b * stride + i];
@@ -1329,8 +1512,8 @@ static tdp_status cerr(cudaError_t e) { return e == cudaSuccess ? TDP_OK : TDP_E
 static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // split-K factors (host side) for the fc1 GEMMs and the conv2 weight gradient
-static const int FC1_FWD_SPLITS = 8;
-static const int FC1_WGRAD_SPLITS = 4;
+static const int FC1_FWD_SPLITS = 9;
+static const int FC1_WGRAD_SPLITS = 8;
 
 // CTAs of the conv2 weight gradient: one per SM (each holds 512 tensor-memory
 // columns), each writing one partial of dW
@@ -1395,9 +1578,11 @@ size_t tdp_cnn_fc1_fwd_workspace(int64_t n_cells)
 }
 
 tdp_status tdp_cnn_fc1_fwd(const void *y2, int64_t n_cells, const void *wfc1, const float *bfc1, void *h1, void *ws,
-                           size_t ws_bytes, tdp_stream_t stream)
+                           size_t ws_bytes, int32_t *d_status, tdp_stream_t stream)
 {
     if (n_cells < 0 || (n_cells > 0 && (!y2 || !wfc1 || !bfc1 || !h1)))
+        return TDP_ERR_INVALID_ARG;
+    if (((uintptr_t)y2 | (uintptr_t)wfc1) % 16)
         return TDP_ERR_INVALID_ARG;
     if (n_cells == 0)
         return TDP_OK;
@@ -1409,7 +1594,7 @@ tdp_status tdp_cnn_fc1_fwd(const void *y2, int64_t n_cells, const void *wfc1, co
     LoadK la{(const bf16 *)y2, M, FEAT};
     LoadK lb{(const bf16 *)wfc1, HID, FEAT};
     EpiPartialF32 epi{part, M, HID, (size_t)M * HID};
-    tdp_status st = cerr(launch_gemm<128, 128, 2, 4>(la, lb, epi, M, HID, FEAT, FC1_FWD_SPLITS, s));
+    tdp_status st = cerr(launch_umma_gemm<HID, 3>(la, lb, epi, M, HID, FEAT, FC1_FWD_SPLITS, d_status, s));
     if (st != TDP_OK)
         return st;
     long long n = (long long)M * HID;
@@ -1460,9 +1645,12 @@ size_t tdp_cnn_fc1_bwd_workspace(int64_t n_cells)
 }
 
 tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, int64_t n_cells, void *dy2p,
-                           float *dwfc1, float *dbfc1, void *ws, size_t ws_bytes, tdp_stream_t stream)
+                           float *dwfc1, float *dbfc1, void *ws, size_t ws_bytes, int32_t *d_status,
+                           tdp_stream_t stream)
 {
-    if (n_cells < 1 || !dh1 || !y2 || !wfc1 || !dy2p || !dwfc1 || !dbfc1 || (uintptr_t)dh1 % 16)
+    if (n_cells < 1 || !dh1 || !y2 || !wfc1 || !dy2p || !dwfc1 || !dbfc1)
+        return TDP_ERR_INVALID_ARG;
+    if (((uintptr_t)dh1 | (uintptr_t)y2 | (uintptr_t)wfc1 | (uintptr_t)dy2p) % 16)
         return TDP_ERR_INVALID_ARG;
     if (!ws || ws_bytes < tdp_cnn_fc1_bwd_workspace(n_cells))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
@@ -1472,8 +1660,8 @@ tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, in
     {
         LoadK la{(const bf16 *)dh1, M, HID};
         LoadMN lb{(const bf16 *)wfc1, FEAT, FEAT};
-        EpiMaskedBf16 epi{(bf16 *)dy2p, (const bf16 *)y2, M, FEAT};
-        tdp_status st = cerr(launch_gemm<128, 128, 2, 4>(la, lb, epi, M, FEAT, HID, 1, s));
+        EpiMaskedBf16 epi{(bf16 *)dy2p, (const bf16 *)y2, M, FEAT, EpiMaskedBf16::pitch(128)};
+        tdp_status st = cerr(launch_umma_gemm<128, 2>(la, lb, epi, M, FEAT, HID, 1, d_status, s));
         if (st != TDP_OK)
             return st;
     }
@@ -1483,7 +1671,7 @@ tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, in
         LoadMN la{(const bf16 *)dh1, HID, HID};
         LoadMN lb{(const bf16 *)y2, FEAT, FEAT};
         EpiPartialF32 epi{part, HID, FEAT, (size_t)HID * FEAT};
-        tdp_status st = cerr(launch_gemm<128, 128, 2, 4>(la, lb, epi, HID, FEAT, M, FC1_WGRAD_SPLITS, s));
+        tdp_status st = cerr(launch_umma_gemm<256, 2>(la, lb, epi, HID, FEAT, M, FC1_WGRAD_SPLITS, d_status, s));
         if (st != TDP_OK)
             return st;
         long long n = (long long)HID * FEAT;

@@ -145,6 +145,43 @@ def test_conv1_backward_layer(n_grids):
     assert np.allclose(db1.cpu().numpy(), rdb1, rtol=1e-5, atol=1e-5 * np.abs(rdb1).max())
 
 
+def test_fc1_layers():
+    """fc1 forward, data and weight gradients (tcgen05 GEMMs) against the
+    float64 oracle at a ragged cell count (300 = 2 x 128 + 44 rows of the
+    128-row tile).  Inputs are bf16, products exact in fp32: outputs rounded
+    to bf16 agree to one bf16 ulp (plus fp32 accumulation error), the fp32
+    weight gradient to accumulation error."""
+    nc = 300
+    r = np.random.default_rng(77)
+    y2 = bf16_np(np.abs(r.standard_normal((nc, 9216))) * (r.random((nc, 9216)) > 0.5))
+    w = bf16_np(r.uniform(-0.02, 0.02, (128, 9216)))
+    b = r.uniform(-0.05, 0.05, 128).astype(np.float32)
+    dh1 = bf16_np(r.standard_normal((nc, 128)) * (r.random((nc, 128)) > 0.3))
+    g_y2, g_w, g_b, g_dh1 = to_bf16_dev(y2), to_bf16_dev(w), torch.from_numpy(b).to(DEV), to_bf16_dev(dh1)
+    h1 = torch.empty((nc, 128), dtype=torch.bfloat16, device=DEV)
+    dy2p = torch.empty((nc, 9216), dtype=torch.bfloat16, device=DEV)
+    dw = torch.empty((128, 9216), dtype=torch.float32, device=DEV)
+    db = torch.empty(128, dtype=torch.float32, device=DEV)
+    lib = L.lib()
+    ws = torch.empty(max(lib.tdp_cnn_fc1_fwd_workspace(nc), lib.tdp_cnn_fc1_bwd_workspace(nc)), dtype=torch.uint8,
+                     device=DEV)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    L.call("tdp_cnn_fc1_fwd", _ptr(g_y2), nc, _ptr(g_w), _ptr(g_b), _ptr(h1), _ptr(ws), ws.numel(), _ptr(st),
+           _stream())
+    L.call("tdp_cnn_fc1_bwd", _ptr(g_dh1), _ptr(g_y2), _ptr(g_w), nc, _ptr(dy2p), _ptr(dw), _ptr(db), _ptr(ws),
+           ws.numel(), _ptr(st), _stream())
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    rh = O.fc(y2, w, b.astype(np.float64), True)
+    got = h1.float().cpu().numpy()
+    assert np.all(np.abs(got - bf16_np(rh)) <= ULP * np.abs(rh) + 1e-5 * np.abs(rh).max())
+    rdy, rdw, rdb = O.fc1_backward(dh1, y2, w)
+    got = dy2p.float().cpu().numpy()
+    assert np.all(np.abs(got - bf16_np(rdy)) <= ULP * np.abs(rdy) + 1e-5 * np.abs(rdy).max())
+    assert np.linalg.norm(dw.cpu().numpy() - rdw) <= 1e-5 * np.linalg.norm(rdw)
+    assert np.allclose(db.cpu().numpy(), rdb, rtol=1e-5, atol=1e-5 * np.abs(rdb).max())
+
+
 def test_forward_query_matches_oracle():
     img, lab, t = _batch(3, 31)
     p = params()

@@ -1112,10 +1112,9 @@ static inline int colsum_blocks(long long rows, int C)
 }
 
 // out[i] = sum_b part[b * stride + i] in float64, in a fixed order: slice s
-// (of PS_SLICES) sums b = s, s + PS_SLICES, ... in order (eight loads in
-// flight), then the slices are added by a fixed tree.  A block covers 32
-// consecutive outputs.
-constexpr int PS_SLICES = 32;
+// (of PS_SLICES) sums b = s, s + PS_SLICES, ... in order, then the slices are
+// added by a fixed tree.  A block covers 32 consecutive outputs.
+constexpr int PS_SLICES = 16;
 
 __global__ void __launch_bounds__(32 * PS_SLICES) partial_sum_kernel(const float *__restrict__ part, int nb, int n,
                                                                      size_t stride, float *__restrict__ out)
@@ -1126,14 +1125,15 @@ __global__ void __launch_bounds__(32 * PS_SLICES) partial_sum_kernel(const float
     double acc = 0.0;
     if (i < n) {
         int b = sl;
-        for (; b + 7 * PS_SLICES < nb; b += 8 * PS_SLICES) {
-            float a[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                a[u] = part[(size_t)(b + u * PS_SLICES) * stride + i];
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                acc += a[u];
+        for (; b + 3 * PS_SLICES < nb; b += 4 * PS_SLICES) {
+            const float a0 = part[(size_t)b * stride + i];
+            const float a1 = part[(size_t)(b + PS_SLICES) * stride + i];
+            const float a2 = part[(size_t)(b + 2 * PS_SLICES) * stride + i];
+            const float a3 = part[(size_t)(b + 3 * PS_SLICES) * stride + i];
+            acc += a0;
+            acc += a1;
+            acc += a2;
+            acc += a3;
         }
         for (; b < nb; b += PS_SLICES)
             acc += part[(size_t)b * stride + i];

@@ -74,7 +74,7 @@ size_t tdp_cnn_head_workspace(int64_t n_grids);
  *   pred   [n_grids][14]  = 10 soft counts  cnt[k]  = sum_cells P[c][k]
  *                         + 4 soft row sums rsum[r] = sum_{c in row r} sum_k k P[c][k]
  *   with targets [n_grids][14] (the exact query on true labels):
- *   loss   [1]  = sum (pred - target)^2 (divide by 14 * n_grids for the mean)
+ *   loss   [1]  = mean over the n_grids x 14 outputs of (pred - target)^2
  *   dh1    bf16 [n_cells][128]  gradient of the MSE mean w.r.t. h1 (ReLU-masked)
  *   dwfc2  [10][128], dbfc2 [10]  its fc2 gradients (per-grid partials in ws,
  *                                 summed in grid order in float64)

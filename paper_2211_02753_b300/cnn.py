@@ -79,8 +79,11 @@ class GlyphQuery:
         return b
 
     # -------------------------------------------------------------- forward
-    def forward(self, grids: torch.Tensor, targets: torch.Tensor | None = None) -> dict:
-        """Forward (and, with targets, the loss backward down to dh1)."""
+    def forward(self, grids: torch.Tensor, targets: torch.Tensor | None = None,
+                loss_out: torch.Tensor | None = None) -> dict:
+        """Forward (and, with targets, the loss backward down to dh1).  The
+        mean loss goes to b["loss"], or to the one-element fp32 device tensor
+        loss_out when given."""
         n = grids.shape[0]
         nc = n * CELLS
         b = self._buffers(n)
@@ -98,7 +101,8 @@ class GlyphQuery:
                _ptr(b["dh1"]) if targets is not None else None,
                _ptr(g["fc2_w"]) if targets is not None else None,
                _ptr(g["fc2_b"]) if targets is not None else None,
-               _ptr(b["loss"]) if targets is not None else None, ws, wsn, s)
+               _ptr(loss_out if loss_out is not None else b["loss"]) if targets is not None else None, ws, wsn,
+               s)
         return b
 
     def backward(self, grids: torch.Tensor) -> None:
@@ -127,14 +131,17 @@ class GlyphQuery:
                arr([self.m[x] for x in k]), arr([self.v[x] for x in k]), copies, sizes, len(k), self.t,
                float(lr), float(self.betas[0]), float(self.betas[1]), float(self.eps), _stream())
 
-    def train_step(self, grids: torch.Tensor, targets: torch.Tensor) -> torch.Tensor:
+    def train_step(self, grids: torch.Tensor, targets: torch.Tensor,
+                   loss_out: torch.Tensor | None = None) -> torch.Tensor:
         """One step of the paper's training loop: query forward, MSE loss,
         backward through the soft query into the CNN, Adam.  Returns the
-        device loss (mean squared error)."""
-        b = self.forward(grids, targets)
+        device loss (mean squared error): loss_out when given (a one-element
+        fp32 device tensor, e.g. a slot of a loss history), else the query's
+        own loss buffer, which the next step overwrites."""
+        b = self.forward(grids, targets, loss_out)
         self.backward(grids)
         self.adam()
-        return b["loss"] / float(grids.shape[0] * NPRED)
+        return loss_out if loss_out is not None else b["loss"]
 
     # -------------------------------------------------------------- inference
     def soft_query(self, grids: torch.Tensor) -> torch.Tensor:

@@ -1355,7 +1355,8 @@ __global__ void __launch_bounds__(HEAD_THREADS) head_kernel(const bf16 *__restri
             float d = spred[j] - target[grid * NPRED + j];
             l += d * d;
         }
-        gp[NCLS * HID + NCLS] = l;
+        gp[NCLS * HID + NCLS] = l * inv_nout; // the grid's share of the mean
+
     }
     if (tid < CELLS_PER_GRID) {
         const int c = tid, r = c / GRID_W;

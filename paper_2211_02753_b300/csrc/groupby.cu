@@ -604,6 +604,9 @@ extern "C" tdp_status tdp_groupby_agg(const tdp_col *cols, int32_t ncols, const 
     const GbPath path = choose_path(strategy, kd, nkeys, 1 + naggs);
     if (path == GB_NONE)
         return TDP_ERR_INVALID_ARG;
+    // the group count is this call's output whatever path runs (0 if no row qualifies)
+    if (cudaMemsetAsync(d_ngroups, 0, sizeof(int64_t), (cudaStream_t)stream) != cudaSuccess)
+        return TDP_ERR_CUDA;
     KeySet ks;
     long long D = 0;
     if ((st = make_keyset(cols, ncols, key_cols, nkeys, sel ? 0 : n, &ks, path != GB_SORT, &D)) != TDP_OK)

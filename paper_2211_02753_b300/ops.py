@@ -153,7 +153,7 @@ def filter(cols, preds, n=None, capacity=None, gather=(), rowids=True, status=No
     cap = n if capacity is None else int(capacity)
     status = new_status(dev) if status is None else status
     rowid = torch.empty(max(cap, 1), dtype=torch.int32, device=dev) if rowids else None
-    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    count = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
     gout = [torch.empty(max(cap, 1), dtype=_as_col(cols[g]).t.dtype, device=dev) for g in gather]
     ws_n = L.lib().tdp_filter_workspace(n)
     ws = workspace(ws_n, dev)
@@ -184,7 +184,7 @@ def groupby_agg(cols, key_cols, aggs, preds=(), n=None, sel=None, nsel=None, str
     ws = workspace(ws_n, dev)
     kout = [torch.empty(max(cap, 1), dtype=_as_col(cols[k]).t.dtype, device=dev) for k in key_cols]
     aout = [torch.empty(max(cap, 1), dtype=torch.int64, device=dev) for _ in aggs]
-    ng = torch.zeros(1, dtype=torch.int64, device=dev)
+    ng = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
     if sel is not None and nsel is None:
         nsel = torch.tensor([sel.numel()], dtype=torch.int64, device=dev)
     L.call("tdp_groupby_agg", carr, len(cols), pred_array(preds), len(preds), n, _ptr(sel), _ptr(nsel),
@@ -243,7 +243,7 @@ def join_probe(table, cols, key_col, preds=(), n=None, sel=None, nsel=None, gath
     orow = torch.empty(max(cap, 1), dtype=torch.int32, device=dev) if rowids else None
     opay = torch.empty(max(cap, 1), dtype=torch.int32, device=dev) if payload else None
     gout = [torch.empty(max(cap, 1), dtype=_as_col(cols[g]).t.dtype, device=dev) for g in gather]
-    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    count = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
     if sel is not None and nsel is None:
         nsel = torch.tensor([sel.numel()], dtype=torch.int64, device=dev)
     ws = workspace(L.lib().tdp_join_probe_workspace(n), dev)
@@ -266,7 +266,7 @@ def join(build_cols, build_key, probe_cols, probe_key, build_payload=-1, build_p
     orow = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
     opay = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
     gout = [torch.empty(max(cap, 1), dtype=_as_col(probe_cols[g]).t.dtype, device=dev) for g in gather]
-    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    count = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
     ws = workspace(L.lib().tdp_join_workspace(nb, npr, nslots), dev)
     L.call("tdp_join", bc, len(build_cols), pred_array(build_preds), len(build_preds), nb, int(build_key),
            int(build_payload), pc, len(probe_cols), pred_array(probe_preds), len(probe_preds), npr, int(probe_key),
@@ -284,7 +284,7 @@ def join_probe_agg(table, cols, key_col, lo, hi, aggs, preds=(), n=None, capacit
     status = new_status(dev) if status is None else status
     kout = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
     aout = [torch.empty(max(cap, 1), dtype=torch.int64, device=dev) for _ in aggs]
-    ng = torch.zeros(1, dtype=torch.int64, device=dev)
+    ng = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
     ws = workspace(L.lib().tdp_join_probe_agg_workspace(n, D, len(aggs)), dev)
     L.call("tdp_join_probe_agg", _ptr(table), table.numel(), carr, len(cols), pred_array(preds), len(preds), n,
            _ptr(d_n), int(key_col), int(lo), int(hi), agg_array(aggs), len(aggs), _ptr(kout), _ptr_array(aout), cap, _ptr(ng),
@@ -301,7 +301,7 @@ def topk(vals, keys, k, d_n=None, status=None):
     status = new_status(dev) if status is None else status
     ov = torch.empty(k, dtype=torch.int64, device=dev)
     okk = torch.empty(k, dtype=torch.int32, device=dev)
-    dk = torch.zeros(1, dtype=torch.int64, device=dev)
+    dk = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
     ws = workspace(L.lib().tdp_topk_workspace(n, k), dev)
     L.call("tdp_topk", _ptr(vals), _ptr(keys), n, _ptr(d_n), int(k), _ptr(ov), _ptr(okk), _ptr(dk), _ptr(ws),
            ws.numel(), _ptr(status), _stream())

@@ -98,6 +98,11 @@ __device__ void block_merge(WarpList &l, int k, VK *out)
     }
 }
 
+// Pass 1: each lane loads TK_UNROLL values (32 apart) before offering any,
+// and the key of a value only when it can enter the list (a key is needed to
+// break a tie with the list's last entry or to insert).
+constexpr int TK_UNROLL = 8;
+
 __global__ void __launch_bounds__(TK_THREADS) topk_pass1_kernel(const long long *__restrict__ vals,
                                                                 const int32_t *__restrict__ keys, long long n_max,
                                                                 const long long *d_n, int k, VK *cand)
@@ -106,13 +111,26 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass1_kernel(const long long 
     WarpList l;
     wl_init(l);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * TK_THREADS;
-    for (long long base = ((long long)blockIdx.x * (TK_THREADS / 32) + warp) * 32; base < n; base += stride) {
-        const long long i = base + lane;
-        const bool valid = i < n;
-        const long long v = valid ? vals[i] : VK_WORST_V;
-        const int kk = valid ? keys[i] : VK_WORST_K;
-        wl_offer(l, valid, v, kk);
+    const long long stride = (long long)gridDim.x * TK_THREADS * TK_UNROLL;
+    for (long long base = ((long long)blockIdx.x * (TK_THREADS / 32) + warp) * 32 * TK_UNROLL; base < n;
+         base += stride) {
+        long long v[TK_UNROLL];
+#pragma unroll
+        for (int u = 0; u < TK_UNROLL; u++) {
+            const long long i = base + u * 32 + lane;
+            v[u] = i < n ? __ldg(vals + i) : VK_WORST_V;
+        }
+#pragma unroll
+        for (int u = 0; u < TK_UNROLL; u++) {
+            const long long i = base + u * 32 + lane;
+            const long long tv = __shfl_sync(0xffffffffu, l.v, TK_LIST - 1);
+            const int tk = __shfl_sync(0xffffffffu, l.k, TK_LIST - 1);
+            const bool maybe = i < n && v[u] >= tv;
+            const int kk = maybe ? __ldg(keys + i) : VK_WORST_K;
+            const unsigned m = __ballot_sync(0xffffffffu, maybe && better(v[u], kk, tv, tk));
+            if (m)
+                wl_insert(l, m, v[u], kk);
+        }
     }
     block_merge(l, k, cand + (size_t)blockIdx.x * k);
 }
@@ -125,11 +143,17 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass2_kernel(const VK *__rest
     WarpList l;
     wl_init(l);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (long long base = (long long)warp * 32; base < ncand; base += TK_THREADS) {
-        const long long i = base + lane;
-        const bool valid = i < ncand;
-        VK c = valid ? cand[i] : VK{VK_WORST_V, VK_WORST_K};
-        wl_offer(l, valid, c.v, c.k);
+    constexpr int U = 4; // candidates per lane in flight
+    for (long long base = (long long)warp * 32 * U; base < ncand; base += TK_THREADS * U) {
+        VK c[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long i = base + u * 32 + lane;
+            c[u] = i < ncand ? cand[i] : VK{VK_WORST_V, VK_WORST_K};
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            wl_offer(l, base + u * 32 + lane < ncand, c[u].v, c[u].k);
     }
     block_merge(l, k, s_out);
     __syncthreads();
@@ -145,7 +169,7 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass2_kernel(const VK *__rest
 
 static int topk_blocks(long long n)
 {
-    long long want = (n + TK_THREADS * 16 - 1) / (TK_THREADS * 16);
+    long long want = (n + TK_THREADS * 32 - 1) / (TK_THREADS * 32);
     return (int)std::max(1ll, std::min<long long>(want, (long long)num_sms() * 2));
 }
 

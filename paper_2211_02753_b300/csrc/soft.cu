@@ -10,7 +10,11 @@
 // cancel; a long fp32 chain would then lose the 1e-5 relative accuracy.)
 // The mask m = sigmoid((x - theta[g]) / tau) is recomputed in the backward
 // pass, never stored; m(1-m) is evaluated as e/(1+e)^2 with e = exp(-|z|),
-// which has no cancellation when m is close to 1.
+// which has no cancellation when m is close to 1.  z = (x - theta) / tau is
+// carried as a pair zh + zl (x - theta by TwoSum, the division's residual by
+// an FMA) and exp(-|z|) is corrected to first order in zl: the exponential
+// multiplies the rounding error of a plain fp32 z by |z| (up to ~50 at
+// tau = 0.1), which alone used most of the 1e-5 budget of the adjoint.
 #include <atomic>
 
 #include "common.cuh"
@@ -27,12 +31,23 @@ struct Sig {
     float dm; // m (1 - m)
 };
 
-__device__ __forceinline__ Sig sigmoid_pair(float z)
+struct Tau {
+    float t;   // tau
+    float inv; // 1 / tau, rounded
+};
+
+// sigmoid((x - th) / tau) and its m (1 - m), z = zh + zl as described above.
+__device__ __forceinline__ Sig sigmoid_xt(float x, float th, Tau tau)
 {
-    float e = expf(-fabsf(z));
-    float r = 1.0f / (1.0f + e);
+    const float d = x - th;
+    const float bb = d - x;
+    const float dl = (x - (d - bb)) + (-th - bb); // x - th = d + dl exactly
+    const float zh = d * tau.inv;
+    const float zl = (fmaf(-zh, tau.t, d) + dl) * tau.inv; // (d + dl - zh tau) / tau
+    const float e = expf(-fabsf(zh)) * (1.0f - (zh >= 0.f ? zl : -zl));
+    const float r = 1.0f / (1.0f + e);
     Sig s;
-    s.m = z >= 0.f ? r : e * r;
+    s.m = zh >= 0.f ? r : e * r;
     s.dm = e * r * r;
     return s;
 }
@@ -43,12 +58,12 @@ enum SoftMode { MODE_AGG_FWD = 0, MODE_AGG_BWD = 1, MODE_FILTER_BWD = 2 };
 // acc0 (and acc1 for the forward COUNT).
 template <int MODE>
 __device__ __forceinline__ void soft_row(float x, float v, int g, float gm, const float *s_theta, const float *s_g0,
-                                         const float *s_g1, float inv_tau, float *acc0, float *acc1, float *gx,
+                                         const float *s_g1, Tau tau, float *acc0, float *acc1, float *gx,
                                          float *gv, long long i, int G)
 {
     if ((unsigned)g >= (unsigned)G) // out-of-range group id: row ignored
         return;
-    Sig s = sigmoid_pair((x - s_theta[g]) * inv_tau);
+    Sig s = sigmoid_xt(x, s_theta[g], tau);
     if (MODE == MODE_AGG_FWD) {
         atomicAdd(&acc0[g], v * s.m);
         atomicAdd(&acc1[g], s.m);
@@ -57,14 +72,14 @@ __device__ __forceinline__ void soft_row(float x, float v, int g, float gm, cons
         float w = (gS * v + s_g1[g]) * s.dm;
         atomicAdd(&acc0[g], w);
         if (gx)
-            gx[i] = w * inv_tau;
+            gx[i] = w * tau.inv;
         if (gv)
             gv[i] = gS * s.m;
     } else {
         float w = gm * s.dm;
         atomicAdd(&acc0[g], w);
         if (gx)
-            gx[i] = w * inv_tau;
+            gx[i] = w * tau.inv;
     }
 }
 
@@ -74,7 +89,7 @@ __global__ void __launch_bounds__(SA_THREADS, SA_BLOCKS_PER_SM) soft_reduce_kern
                                                                  const int32_t *__restrict__ gid,
                                                                  const float *__restrict__ theta,
                                                                  const float *__restrict__ g0,
-                                                                 const float *__restrict__ g1, float inv_tau,
+                                                                 const float *__restrict__ g1, Tau tau,
                                                                  long long n, int G, long long chunk,
                                                                  double *__restrict__ partial, float *gx, float *gv)
 {
@@ -130,10 +145,10 @@ __global__ void __launch_bounds__(SA_THREADS, SA_BLOCKS_PER_SM) soft_reduce_kern
 #pragma unroll
                 for (int u = 0; u < SA_UNROLL; u++) {
                     const long long i = sb + 4 * (q + u * SA_THREADS);
-                    soft_row<MODE>(xx[u].x, aa[u].x, gg[u].x, aa[u].x, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i, G);
-                    soft_row<MODE>(xx[u].y, aa[u].y, gg[u].y, aa[u].y, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 1, G);
-                    soft_row<MODE>(xx[u].z, aa[u].z, gg[u].z, aa[u].z, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 2, G);
-                    soft_row<MODE>(xx[u].w, aa[u].w, gg[u].w, aa[u].w, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 3, G);
+                    soft_row<MODE>(xx[u].x, aa[u].x, gg[u].x, aa[u].x, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i, G);
+                    soft_row<MODE>(xx[u].y, aa[u].y, gg[u].y, aa[u].y, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 1, G);
+                    soft_row<MODE>(xx[u].z, aa[u].z, gg[u].z, aa[u].z, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 2, G);
+                    soft_row<MODE>(xx[u].w, aa[u].w, gg[u].w, aa[u].w, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 3, G);
                 }
             }
             for (; q < nvec; q += SA_THREADS) {
@@ -141,15 +156,15 @@ __global__ void __launch_bounds__(SA_THREADS, SA_BLOCKS_PER_SM) soft_reduce_kern
                 float4 xx = __ldcs((const float4 *)(x + i));
                 float4 aa = __ldcs((const float4 *)(aux + i));
                 int4 gg = __ldcs((const int4 *)(gid + i));
-                soft_row<MODE>(xx.x, aa.x, gg.x, aa.x, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i, G);
-                soft_row<MODE>(xx.y, aa.y, gg.y, aa.y, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 1, G);
-                soft_row<MODE>(xx.z, aa.z, gg.z, aa.z, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 2, G);
-                soft_row<MODE>(xx.w, aa.w, gg.w, aa.w, s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, i + 3, G);
+                soft_row<MODE>(xx.x, aa.x, gg.x, aa.x, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i, G);
+                soft_row<MODE>(xx.y, aa.y, gg.y, aa.y, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 1, G);
+                soft_row<MODE>(xx.z, aa.z, gg.z, aa.z, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 2, G);
+                soft_row<MODE>(xx.w, aa.w, gg.w, aa.w, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 3, G);
             }
             tail = sb + 4 * nvec;
         }
         for (long long r = tail + threadIdx.x; r < se; r += SA_THREADS)
-            soft_row<MODE>(x[r], aux[r], gid[r], aux[r], s_theta, s_g0, s_g1, inv_tau, acc0, acc1, gx, gv, r, G);
+            soft_row<MODE>(x[r], aux[r], gid[r], aux[r], s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, r, G);
         __syncthreads();
         for (int g = threadIdx.x; g < G; g += blockDim.x) {
             acc64[g] += (double)acc0[g];
@@ -216,7 +231,7 @@ __global__ void __launch_bounds__(32 * SC_SLICES) soft_combine_kernel(const doub
 static inline unsigned combine_blocks(int K, int G) { return (unsigned)((K * G + 31) / 32); }
 
 __global__ void soft_filter_fwd_kernel(const float *__restrict__ x, const int32_t *__restrict__ gid,
-                                       const float *__restrict__ theta, float inv_tau, long long n,
+                                       const float *__restrict__ theta, Tau tau, long long n,
                                        float *__restrict__ mask)
 {
     long long i = 4ll * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
@@ -225,14 +240,14 @@ __global__ void soft_filter_fwd_kernel(const float *__restrict__ x, const int32_
         float4 xx = __ldg((const float4 *)(x + i));
         int4 gg = __ldg((const int4 *)(gid + i));
         float4 o;
-        o.x = sigmoid_pair((xx.x - __ldg(theta + gg.x)) * inv_tau).m;
-        o.y = sigmoid_pair((xx.y - __ldg(theta + gg.y)) * inv_tau).m;
-        o.z = sigmoid_pair((xx.z - __ldg(theta + gg.z)) * inv_tau).m;
-        o.w = sigmoid_pair((xx.w - __ldg(theta + gg.w)) * inv_tau).m;
+        o.x = sigmoid_xt(xx.x, __ldg(theta + gg.x), tau).m;
+        o.y = sigmoid_xt(xx.y, __ldg(theta + gg.y), tau).m;
+        o.z = sigmoid_xt(xx.z, __ldg(theta + gg.z), tau).m;
+        o.w = sigmoid_xt(xx.w, __ldg(theta + gg.w), tau).m;
         *(float4 *)(mask + i) = o;
     } else {
         for (long long r = i; r < min(n, i + 4); r++)
-            mask[r] = sigmoid_pair((x[r] - theta[gid[r]]) * inv_tau).m;
+            mask[r] = sigmoid_xt(x[r], theta[gid[r]], tau).m;
     }
 }
 
@@ -294,7 +309,7 @@ extern "C" tdp_status tdp_soft_filter_fwd(const float *x, const int32_t *gid, co
         return TDP_OK;
     long long threads = (n + 3) / 4;
     soft_filter_fwd_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        x, gid, theta, 1.0f / tau, n, mask);
+        x, gid, theta, Tau{tau, 1.0f / tau}, n, mask);
     return launch_status();
 }
 
@@ -315,7 +330,7 @@ extern "C" tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int
         return st;
     double *partial = (double *)ws;
     soft_reduce_kernel<MODE_AGG_FWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
-        x, v, gid, theta, nullptr, nullptr, 1.0f / tau, n, G, sg.chunk, partial, nullptr, nullptr);
+        x, v, gid, theta, nullptr, nullptr, Tau{tau, 1.0f / tau}, n, G, sg.chunk, partial, nullptr, nullptr);
     soft_combine_kernel<<<combine_blocks(2, G), 32 * SC_SLICES, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
     return launch_status();
 }
@@ -338,7 +353,7 @@ extern "C" tdp_status tdp_soft_agg_bwd(const float *x, const float *v, const int
         return st;
     double *partial = (double *)ws;
     soft_reduce_kernel<MODE_AGG_BWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
-        x, v, gid, theta, gsum, gcnt, 1.0f / tau, n, G, sg.chunk, partial, grad_x, grad_v);
+        x, v, gid, theta, gsum, gcnt, Tau{tau, 1.0f / tau}, n, G, sg.chunk, partial, grad_x, grad_v);
     soft_combine_kernel<<<combine_blocks(1, G), 32 * SC_SLICES, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau,
                                                                            grad_theta, nullptr);
     return launch_status();
@@ -361,7 +376,7 @@ extern "C" tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, co
         return st;
     double *partial = (double *)ws;
     soft_reduce_kernel<MODE_FILTER_BWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
-        x, nullptr, gid, theta, grad_mask, nullptr, 1.0f / tau, n, G, sg.chunk, partial, grad_x, nullptr);
+        x, nullptr, gid, theta, grad_mask, nullptr, Tau{tau, 1.0f / tau}, n, G, sg.chunk, partial, grad_x, nullptr);
     soft_combine_kernel<<<combine_blocks(1, G), 32 * SC_SLICES, 0, s>>>(partial, sg.blocks, G, 1, -1.0f / tau,
                                                                            grad_theta, nullptr);
     return launch_status();
@@ -432,7 +447,7 @@ extern "C" tdp_status tdp_soft_agg_fwd_noalloc(const float *x, const float *v, c
     // every block used overwrites its own K x G partials before the combine
     // reads them, so nothing in the shared scratch has to start at zero
     soft_reduce_kernel<MODE_AGG_FWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(
-        x, v, gid, theta, nullptr, nullptr, 1.0f / tau, n, G, sg.chunk, partial, nullptr, nullptr);
+        x, v, gid, theta, nullptr, nullptr, Tau{tau, 1.0f / tau}, n, G, sg.chunk, partial, nullptr, nullptr);
     soft_combine_kernel<<<combine_blocks(2, G), 32 * SC_SLICES, 0, s>>>(partial, sg.blocks, G, 2, 1.0f, sum, cnt);
     return launch_status();
 }

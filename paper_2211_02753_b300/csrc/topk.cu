@@ -7,7 +7,13 @@
 // a time: every lane compares the candidate with its own entry, the ballot
 // gives the insertion position, and entries behind it shift down one lane.
 // The 8 warp lists of a block are merged the same way by warp 0 and written
-// out; a single block then merges the per-block lists.
+// out; a single block then merges the per-block lists.  Lists hold k entries.
+// A shared lower bound prunes almost every element before it reaches a
+// list: each warp's k-th best so far is at most the global k-th best (its
+// elements are a subset), so the running maximum of those values, kept in
+// one 64-bit word in the workspace (atomicMax on an order-preserving
+// encoding), only ever rejects values that cannot be among the global top
+// k; ties at the bound are kept.
 #include "common.cuh"
 
 namespace tdp {
@@ -42,8 +48,9 @@ __device__ __forceinline__ void wl_init(WarpList &l)
     l.k = VK_WORST_K;
 }
 
-// Inserts the candidates held by the lanes in `mask` (each lane's (cv, ck)).
-__device__ __forceinline__ void wl_insert(WarpList &l, unsigned mask, long long cv, int ck)
+// Inserts the candidates held by the lanes in `mask` (each lane's (cv, ck))
+// into the list of the first k lanes.
+__device__ __forceinline__ void wl_insert(WarpList &l, unsigned mask, long long cv, int ck, int k)
 {
     const int lane = threadIdx.x & 31;
     while (mask) {
@@ -52,31 +59,38 @@ __device__ __forceinline__ void wl_insert(WarpList &l, unsigned mask, long long 
         const long long xv = __shfl_sync(0xffffffffu, cv, src);
         const int xk = __shfl_sync(0xffffffffu, ck, src);
         // position = number of entries that stay ahead of x
-        const unsigned ahead = __ballot_sync(0xffffffffu, lane < TK_LIST && !better(xv, xk, l.v, l.k));
+        const unsigned ahead = __ballot_sync(0xffffffffu, lane < k && !better(xv, xk, l.v, l.k));
         const int pos = __popc(ahead);
-        if (pos >= TK_LIST)
+        if (pos >= k)
             continue;
         const long long uv = __shfl_up_sync(0xffffffffu, l.v, 1);
         const int uk = __shfl_up_sync(0xffffffffu, l.k, 1);
         if (lane == pos) {
             l.v = xv;
             l.k = xk;
-        } else if (lane > pos && lane < TK_LIST) {
+        } else if (lane > pos && lane < k) {
             l.v = uv;
             l.k = uk;
         }
     }
 }
 
-// Offers one element per lane (valid lanes only).
-__device__ __forceinline__ void wl_offer(WarpList &l, bool valid, long long v, int k)
+// Offers one element per lane (valid lanes only) to a k-entry list.
+__device__ __forceinline__ void wl_offer(WarpList &l, bool valid, long long v, int key, int k)
 {
-    const long long tv = __shfl_sync(0xffffffffu, l.v, TK_LIST - 1);
-    const int tk = __shfl_sync(0xffffffffu, l.k, TK_LIST - 1);
-    const unsigned m = __ballot_sync(0xffffffffu, valid && better(v, k, tv, tk));
+    const long long tv = __shfl_sync(0xffffffffu, l.v, k - 1);
+    const int tk = __shfl_sync(0xffffffffu, l.k, k - 1);
+    const unsigned m = __ballot_sync(0xffffffffu, valid && better(v, key, tv, tk));
     if (m)
-        wl_insert(l, m, v, k);
+        wl_insert(l, m, v, key, k);
 }
+
+// Order-preserving unsigned encoding of a signed value (for atomicMax).
+__device__ __forceinline__ unsigned long long enc_v(long long v)
+{
+    return (unsigned long long)v ^ 0x8000000000000000ull;
+}
+__device__ __forceinline__ long long dec_v(unsigned long long e) { return (long long)(e ^ 0x8000000000000000ull); }
 
 // Merges the warp lists of the block; warp 0 writes the first k to out.
 __device__ void block_merge(WarpList &l, int k, VK *out)
@@ -91,7 +105,7 @@ __device__ void block_merge(WarpList &l, int k, VK *out)
         wl_init(m);
         for (int base = 0; base < TK_THREADS / 32 * TK_LIST; base += 32) {
             VK c = s_c[base + lane];
-            wl_offer(m, true, c.v, c.k);
+            wl_offer(m, true, c.v, c.k, k);
         }
         if (lane < k)
             out[lane] = VK{m.v, m.k};
@@ -105,13 +119,15 @@ constexpr int TK_UNROLL = 8;
 
 __global__ void __launch_bounds__(TK_THREADS) topk_pass1_kernel(const long long *__restrict__ vals,
                                                                 const int32_t *__restrict__ keys, long long n_max,
-                                                                const long long *d_n, int k, VK *cand)
+                                                                const long long *d_n, int k, VK *cand,
+                                                                unsigned long long *bound)
 {
     const long long n = d_n ? min(*d_n, n_max) : n_max;
     WarpList l;
     wl_init(l);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * TK_THREADS * TK_UNROLL;
+    long long published = VK_WORST_V;
     for (long long base = ((long long)blockIdx.x * (TK_THREADS / 32) + warp) * 32 * TK_UNROLL; base < n;
          base += stride) {
         long long v[TK_UNROLL];
@@ -120,16 +136,26 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass1_kernel(const long long 
             const long long i = base + u * 32 + lane;
             v[u] = i < n ? __ldg(vals + i) : VK_WORST_V;
         }
+        // the shared bound (relaxed: any value it ever held is a valid bound)
+        const long long gb = dec_v(__shfl_sync(0xffffffffu, lane == 0 ? ld_relaxed_u64(bound) : 0ull, 0));
 #pragma unroll
         for (int u = 0; u < TK_UNROLL; u++) {
             const long long i = base + u * 32 + lane;
-            const long long tv = __shfl_sync(0xffffffffu, l.v, TK_LIST - 1);
-            const int tk = __shfl_sync(0xffffffffu, l.k, TK_LIST - 1);
-            const bool maybe = i < n && v[u] >= tv;
+            const long long tv = __shfl_sync(0xffffffffu, l.v, k - 1);
+            const int tk = __shfl_sync(0xffffffffu, l.k, k - 1);
+            const bool maybe = i < n && v[u] >= gb && v[u] >= tv;
             const int kk = maybe ? __ldg(keys + i) : VK_WORST_K;
             const unsigned m = __ballot_sync(0xffffffffu, maybe && better(v[u], kk, tv, tk));
             if (m)
-                wl_insert(l, m, v[u], kk);
+                wl_insert(l, m, v[u], kk, k);
+        }
+        // publish this warp's k-th best once its list is full and it has risen
+        const long long kth = __shfl_sync(0xffffffffu, l.v, k - 1);
+        const int kthk = __shfl_sync(0xffffffffu, l.k, k - 1);
+        if (kthk != VK_WORST_K && kth > published && kth > gb) {
+            if (lane == 0)
+                atomicMax(bound, enc_v(kth));
+            published = kth;
         }
     }
     block_merge(l, k, cand + (size_t)blockIdx.x * k);
@@ -137,8 +163,10 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass1_kernel(const long long 
 
 __global__ void __launch_bounds__(TK_THREADS) topk_pass2_kernel(const VK *__restrict__ cand, long long ncand,
                                                                 long long n_max, const long long *d_n, int k,
-                                                                long long *out_vals, int32_t *out_keys, long long *d_k)
+                                                                long long *out_vals, int32_t *out_keys, long long *d_k,
+                                                                const unsigned long long *bound)
 {
+    const long long gb = dec_v(*bound); // final: every pass-1 block has finished
     __shared__ VK s_out[TK_MAXK];
     WarpList l;
     wl_init(l);
@@ -153,7 +181,7 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass2_kernel(const VK *__rest
         }
 #pragma unroll
         for (int u = 0; u < U; u++)
-            wl_offer(l, base + u * 32 + lane < ncand, c[u].v, c[u].k);
+            wl_offer(l, base + u * 32 + lane < ncand && c[u].v >= gb, c[u].v, c[u].k, k);
     }
     block_merge(l, k, s_out);
     __syncthreads();
@@ -181,7 +209,7 @@ extern "C" size_t tdp_topk_workspace(int64_t n, int32_t k)
 {
     if (k < 1 || k > TK_MAXK)
         return 0;
-    return align_up((size_t)topk_blocks(n) * k * sizeof(VK), 256);
+    return 256 + align_up((size_t)topk_blocks(n) * k * sizeof(VK), 256); // the bound word, then candidates
 }
 
 extern "C" tdp_status tdp_topk(const int64_t *vals, const int32_t *keys, int64_t n, const int64_t *d_n, int32_t k,
@@ -195,9 +223,13 @@ extern "C" tdp_status tdp_topk(const int64_t *vals, const int32_t *keys, int64_t
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
     int blocks = topk_blocks(n);
-    VK *cand = (VK *)ws;
-    topk_pass1_kernel<<<blocks, TK_THREADS, 0, s>>>((const long long *)vals, keys, n, (const long long *)d_n, k, cand);
+    unsigned long long *bound = (unsigned long long *)ws; // 0 encodes the smallest value: no pruning yet
+    VK *cand = (VK *)((char *)ws + 256);
+    if (cudaMemsetAsync(bound, 0, sizeof(unsigned long long), s) != cudaSuccess)
+        return TDP_ERR_CUDA;
+    topk_pass1_kernel<<<blocks, TK_THREADS, 0, s>>>((const long long *)vals, keys, n, (const long long *)d_n, k, cand,
+                                                    bound);
     topk_pass2_kernel<<<1, TK_THREADS, 0, s>>>(cand, (long long)blocks * k, n, (const long long *)d_n, k,
-                                               (long long *)out_vals, out_keys, (long long *)d_k);
+                                               (long long *)out_vals, out_keys, (long long *)d_k, bound);
     return launch_status();
 }

@@ -145,14 +145,15 @@ def test_conv1_backward_layer(n_grids):
     assert np.allclose(db1.cpu().numpy(), rdb1, rtol=1e-5, atol=1e-5 * np.abs(rdb1).max())
 
 
-def test_fc1_layers():
+@pytest.mark.parametrize("nc", [300, 1500])
+def test_fc1_layers(nc):
     """fc1 forward, data and weight gradients (tcgen05 GEMMs) against the
-    float64 oracle at a ragged cell count (300 = 2 x 128 + 44 rows of the
-    128-row tile).  Inputs are bf16, products exact in fp32: outputs rounded
-    to bf16 agree to one bf16 ulp (plus fp32 accumulation error), the fp32
-    weight gradient to accumulation error."""
-    nc = 300
-    r = np.random.default_rng(77)
+    float64 oracle at ragged cell counts (300 = 2 x 128 + 44 rows of the
+    128-row tile; 1500 gives each persistent CTA several data-gradient tiles,
+    so both accumulators are reused).  Inputs are bf16, products exact in
+    fp32: outputs rounded to bf16 agree to one bf16 ulp (plus fp32
+    accumulation error), the fp32 weight gradient to accumulation error."""
+    r = np.random.default_rng(77 + nc)
     y2 = bf16_np(np.abs(r.standard_normal((nc, 9216))) * (r.random((nc, 9216)) > 0.5))
     w = bf16_np(r.uniform(-0.02, 0.02, (128, 9216)))
     b = r.uniform(-0.05, 0.05, 128).astype(np.float32)

@@ -15,6 +15,8 @@
 // through the arg-max; conv1 weight and bias gradients on CUDA cores; a fused
 // Adam step that also refreshes the bf16 copies of the tensor-core weights.
 // No operand is transposed in global memory or materialised in im2col form.
+#include <cuda.h>
+
 #include "cnn_async.cuh"
 #include "common.cuh"
 #include "umma.cuh"
@@ -108,34 +110,6 @@ __global__ void __launch_bounds__(C1F_THREADS) conv1_fwd_kernel(const uint8_t *_
     }
 }
 
-// ---------------------------------------------------------------- loaders
-
-struct LoadK { // K-major [rows][ld]
-    static constexpr bool MN_MAJOR = false, REG = false;
-    const bf16 *p;
-    int rows, ld;
-    __device__ const void *ptr(int r, int kc, int r0, int k0, int kend) const
-    {
-        int row = r0 + r, k = k0 + kc * 8;
-        if (row >= rows || k >= kend)
-            return nullptr;
-        return p + (size_t)row * ld + k;
-    }
-};
-
-struct LoadMN { // MN-major: stored [k][ld], the operand's rows contiguous
-    static constexpr bool MN_MAJOR = true, REG = false;
-    const bf16 *p;
-    int rows, ld;
-    __device__ const void *ptr(int kk, int rc, int r0, int k0, int kend) const
-    {
-        int k = k0 + kk, row = r0 + rc * 8;
-        if (k >= kend || row >= rows)
-            return nullptr;
-        return p + (size_t)k * ld + row;
-    }
-};
-
 // -------------------------------------------------------------- epilogues
 //
 // Called with 32 consecutive accumulator columns of one output row.  An
@@ -204,117 +178,141 @@ struct EpiMaskedBf16 {
 // C[m][n] = sum_k A(m, k) B(n, k) for the fully connected layer: one 128 x BN
 // output tile per CTA (and one K range of it under split-K), its fp32
 // accumulator in tensor memory (BN columns, TMEM lane = row).  Operands move
-// by cp.async in 64-k stages, STAGES deep, into padded no-swizzle
-// core-matrix layouts that let 8 lanes copy one whole 128-byte line of the
-// source into 8 distinct shared-memory bank groups:
-//   K-major ([row][k] in memory): chunk (row r, k-chunk kc) at
-//     (r / 8) * 1152 + kc * 144 + (r % 8) * 16  (LBO 144, SBO 1152, K16 step 288 B)
-//   MN-major ([k][row]): chunk (k, row-chunk rc) at
-//     rc * 1040 + k * 16                         (LBO 128, SBO 1040, K16 step 256 B)
-// (LBO: the next 8 k; SBO: the next 8 rows).  One elected lane of warp 0
-// issues a stage's four K16 MMAs and commits them to the stage's mbarrier;
-// the stage is refilled once that has fired (bounded wait).
+// by TMA (cp.async.bulk.tensor, completion counted on an mbarrier) in 64-k
+// stages, STAGES deep, straight into the layout the MMA reads:
+//   K-major operand ([rows][k] in memory): one copy of R rows x 128 bytes
+//     (the whole 64-k stage of each row) with the 128-byte swizzle, read
+//     through a SWIZZLE_128B descriptor (SBO 1024 per 8-row atom, +32 bytes
+//     per K16 step);
+//   MN-major operand ([k][rows]): one copy per 64 rows of 64 k x 128 bytes
+//     with the 128-byte swizzle (8 KB: eight 1024-byte atoms along K), read
+//     through a swizzled MN-major descriptor (1024 bytes per 8 k, 8192 per
+//     64 rows, +2048 bytes per K16 step).
+// Rows past the tensor (the M tail) arrive as zeros.  One elected lane of
+// warp 0 issues the copies of a stage once the MMAs that last read its slot
+// have committed (empty[]); one elected lane of warp 1 issues the four K16
+// MMAs of a stage once its copies have landed (full[]); then all four warps
+// run the epilogue.  Every wait is bounded (TDP_ERR_TIMEOUT).
 constexpr int UG_BM = 128, UG_BK = 64, UG_THREADS = 128;
-constexpr int UG_K_LBO = 144, UG_K_SBO = 8 * UG_K_LBO, UG_MN_SBO = UG_BK * 16 + 16;
 
-template <class L> constexpr int ug_op_bytes(int rows) { return L::MN_MAJOR ? rows / 8 * UG_MN_SBO : rows / 8 * UG_K_SBO; }
-template <class L> constexpr uint32_t ug_lbo() { return L::MN_MAJOR ? 128u : (uint32_t)UG_K_LBO; }
-template <class L> constexpr uint32_t ug_sbo() { return L::MN_MAJOR ? (uint32_t)UG_MN_SBO : (uint32_t)UG_K_SBO; }
-template <class L> constexpr uint32_t ug_kstep() { return 2 * ug_lbo<L>() / 16; } // 16-byte units per K16
+struct GemmOp {         // one operand as the host describes it
+    const void *p;
+    long long rows;     // extent along M (or N)
+    long long kext;     // extent along K
+    long long ld;       // elements between consecutive outer rows in memory
+    bool mn_major;      // [k][rows] in memory (else [rows][k])
+};
 
-template <class L>
-__device__ __forceinline__ void ug_load(const L &ld, unsigned char *dst, int rows, int r0, int k0, int kend, int tid)
+template <bool MN> __host__ __device__ constexpr int ug_op_bytes(int rows) { return rows * UG_BK * 2; }
+template <bool MN> __device__ __forceinline__ uint64_t ug_desc(uint32_t a)
 {
-    for (int c = tid; c < rows * (UG_BK / 8); c += UG_THREADS) {
-        if constexpr (!L::MN_MAJOR) {
-            const int r = c >> 3, kc = c & 7; // 8 lanes: one row's 128 bytes
-            const void *src = ld.ptr(r, kc, r0, k0, kend);
-            cnn::cp_async16(dst + (r >> 3) * UG_K_SBO + kc * UG_K_LBO + (r & 7) * 16, src, src != nullptr);
-        } else {
-            const int nrc = rows / 8, rc = c % nrc, kk = c / nrc; // lanes along one k-row
-            const void *src = ld.ptr(kk, rc, r0, k0, kend);
-            cnn::cp_async16(dst + rc * UG_MN_SBO + kk * 16, src, src != nullptr);
-        }
+    return MN ? umma::smem_desc_sw128_mn(a, 1024, 8192) : umma::smem_desc_sw128(a);
+}
+template <bool MN> __device__ __forceinline__ uint32_t ug_kstep() // 16-byte units per K16
+{
+    return MN ? 128u : 2u;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                 "[%4];" ::"r"(smem_addr(dst)),
+                 "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// The copies of one stage of one operand (rows r0.., k k0..k0+63).
+template <bool MN>
+__device__ __forceinline__ void ug_tma_stage(const CUtensorMap *map, unsigned char *dst, int rows, int r0, int k0,
+                                             uint64_t *bar)
+{
+    if (MN) {
+        for (int a = 0; a < rows / 64; a++) // 64 rows x 64 k, 128-byte swizzle
+            tma_load_2d(dst + a * 8192, map, r0 + 64 * a, k0, bar);
+    } else {
+        tma_load_2d(dst, map, k0, r0, bar); // rows x 64 k, 128-byte swizzle
     }
 }
 
-template <int BN, class LA, class LB> constexpr int ug_stage_bytes()
-{
-    return ug_op_bytes<LA>(UG_BM) + ug_op_bytes<LB>(BN);
-}
-
-template <int BN, int STAGES, class LA, class LB, class EPI>
-__global__ void __launch_bounds__(UG_THREADS) umma_gemm_kernel(LA la, LB lb, EPI epi, int K, int k_per_split,
-                                                               int32_t *d_status, uint32_t limit)
+template <int BN, int STAGES, bool AMN, bool BMN, class EPI>
+__global__ void __launch_bounds__(UG_THREADS) umma_gemm_kernel(const __grid_constant__ CUtensorMap ta,
+                                                               const __grid_constant__ CUtensorMap tb, EPI epi,
+                                                               int K, int k_per_split, int32_t *d_status,
+                                                               uint32_t limit)
 {
     static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256 && STAGES >= 2, "tile");
+    static_assert(!BMN || BN % 64 == 0, "MN-major operands come in 64-row boxes");
     extern __shared__ __align__(1024) unsigned char ug_smem[];
-    __shared__ __align__(8) uint64_t s_mma[STAGES];
+    __shared__ __align__(8) uint64_t s_full[STAGES], s_empty[STAGES], s_done;
     __shared__ uint32_t s_tmem;
-    constexpr int SB = ug_stage_bytes<BN, LA, LB>();
-    constexpr int A_BYTES = ug_op_bytes<LA>(UG_BM);
+    __shared__ int s_err;
+    constexpr int A_BYTES = ug_op_bytes<AMN>(UG_BM), SB = A_BYTES + ug_op_bytes<BMN>(BN);
     unsigned char *epi_buf = ug_smem + STAGES * SB;
-    constexpr uint32_t idesc = umma::idesc_bf16_f32(UG_BM, BN) | (LA::MN_MAJOR ? 1u << 15 : 0u) |
-                               (LB::MN_MAJOR ? 1u << 16 : 0u);
+    constexpr uint32_t idesc =
+        umma::idesc_bf16_f32(UG_BM, BN) | (AMN ? 1u << 15 : 0u) | (BMN ? 1u << 16 : 0u);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * UG_BM, n0 = blockIdx.y * BN, split = blockIdx.z;
     const int kbeg = split * k_per_split, kend = min(K, kbeg + k_per_split);
     const int ktiles = kend > kbeg ? (kend - kbeg + UG_BK - 1) / UG_BK : 0;
 
-    if (tid == 0)
-        for (int st = 0; st < STAGES; st++)
-            mbar_init(&s_mma[st], 1);
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&s_full[s], 1);
+            mbar_init(&s_empty[s], 1);
+        }
+        mbar_init(&s_done, 1);
+        s_err = 0;
+    }
     if (warp == 0) {
         umma::tmem_alloc(&s_tmem, BN);
         umma::fence_before_sync();
     }
     if constexpr (EPI::PREFETCH)
-        epi.prefetch(epi_buf, m0, n0, BN, tid); // lands with the first stage's group
-    auto load = [&](int kt) {
-        unsigned char *st = ug_smem + (kt % STAGES) * SB;
-        const int k0 = kbeg + kt * UG_BK;
-        ug_load<LA>(la, st, UG_BM, m0, k0, kend, tid);
-        ug_load<LB>(lb, st + A_BYTES, BN, n0, k0, kend, tid);
-    };
-    for (int st = 0; st < STAGES - 1; st++) {
-        if (st < ktiles)
-            load(st);
-        cnn::cp_async_commit();
-    }
+        epi.prefetch(epi_buf, m0, n0, BN, tid);
+    cnn::cp_async_commit();
     __syncthreads(); // the mbarriers and the tensor-memory address
     umma::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    bool ok = true;
-    for (int kt = 0; kt < ktiles; kt++) {
-        cnn::cp_async_wait<STAGES - 2>(); // this thread's chunks of stage kt have landed
-        fence_proxy_async_smem();
-        __syncthreads(); // ... everyone's
-        if (warp == 0) {
-            umma::fence_after_sync();
-            const uint32_t a = smem_addr(ug_smem + (kt % STAGES) * SB);
-            const uint64_t da = umma::smem_desc(a, ug_lbo<LA>(), ug_sbo<LA>()),
-                           db = umma::smem_desc(a + A_BYTES, ug_lbo<LB>(), ug_sbo<LB>());
-            if (umma::elect_one()) {
+
+    if (warp == 0) { // copies
+        if (umma::elect_one()) {
+            for (int kt = 0; kt < ktiles; kt++) {
+                const int s = kt % STAGES;
+                if (kt >= STAGES && !mbar_wait(&s_empty[s], (uint32_t)((kt / STAGES) - 1) & 1u, limit)) {
+                    s_err = 1;
+                    break;
+                }
+                unsigned char *st = ug_smem + s * SB;
+                const int k0 = kbeg + kt * UG_BK;
+                mbar_arrive_expect_tx(&s_full[s], (uint32_t)SB);
+                ug_tma_stage<AMN>(&ta, st, UG_BM, m0, k0, &s_full[s]);
+                ug_tma_stage<BMN>(&tb, st + A_BYTES, BN, n0, k0, &s_full[s]);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) { // MMAs
+        if (umma::elect_one()) {
+            for (int kt = 0; kt < ktiles; kt++) {
+                const int s = kt % STAGES;
+                if (!mbar_wait(&s_full[s], (uint32_t)(kt / STAGES) & 1u, limit)) {
+                    s_err = 1;
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint32_t a = smem_addr(ug_smem + s * SB);
+                const uint64_t da = ug_desc<AMN>(a), db = ug_desc<BMN>(a + A_BYTES);
 #pragma unroll
                 for (int j = 0; j < UG_BK / 16; j++)
-                    umma::mma_bf16(tmem, da + ug_kstep<LA>() * j, db + ug_kstep<LB>() * j, idesc, kt > 0 || j > 0);
-                umma::commit(&s_mma[kt % STAGES]);
+                    umma::mma_bf16(tmem, da + ug_kstep<AMN>() * j, db + ug_kstep<BMN>() * j, idesc, kt > 0 || j > 0);
+                umma::commit(&s_empty[s]);
             }
-            __syncwarp();
+            umma::commit(&s_done); // fires once every MMA above has completed
         }
-        // refill the stage of tile kt - 1 with tile kt + STAGES - 1 once its MMAs completed
-        const int nk = kt + STAGES - 1;
-        if (nk < ktiles) {
-            if (kt >= 1 && !mbar_wait(&s_mma[(kt - 1) % STAGES], (uint32_t)((kt - 1) / STAGES) & 1u, limit))
-                ok = false;
-            load(nk);
-        }
-        cnn::cp_async_commit();
+        __syncwarp();
     }
-    // the last commit fires once every MMA has completed (they run in order)
-    if (ktiles > 0 &&
-        !mbar_wait(&s_mma[(ktiles - 1) % STAGES], (uint32_t)((ktiles - 1) / STAGES) & 1u, limit))
-        ok = false;
+    const bool done = mbar_wait(&s_done, 0, limit);
+    if (!done)
+        s_err = 1;
     if constexpr (EPI::PREFETCH) {
         cnn::cp_async_wait<0>();
         __syncthreads(); // the staged epilogue input
@@ -340,33 +338,55 @@ __global__ void __launch_bounds__(UG_THREADS) umma_gemm_kernel(LA la, LB lb, EPI
         }
         epi.store(m, n0 + cb, v, split, epi_buf, m0, n0);
     }
-    if (!ok)
-        set_status(d_status, TDP_ERR_TIMEOUT);
     umma::fence_before_sync();
     __syncthreads();
+    if (tid == 0 && s_err)
+        set_status(d_status, TDP_ERR_TIMEOUT);
     if (warp == 0) {
         umma::fence_after_sync();
         umma::tmem_dealloc(tmem, BN);
     }
 }
 
-// M x N output (N a multiple of BN), K split into `splits` ranges of whole stages.
-template <int BN, int STAGES, class LA, class LB, class EPI>
-static cudaError_t launch_umma_gemm(const LA &la, const LB &lb, const EPI &epi, int M, int N, int K, int splits,
-                                    int32_t *d_status, cudaStream_t s)
+// Tensor map of one operand: 2-D, bf16, inner dimension the contiguous one,
+// zero fill, 128-byte swizzle; K-major: a box of 64 k x box_outer rows;
+// MN-major: a box of 64 rows x box_outer (64) k.
+static bool ug_tensor_map(const GemmOp &op, int box_outer, CUtensorMap *map)
 {
-    if (N % BN)
-        return cudaErrorInvalidValue;
-    constexpr size_t smem = (size_t)STAGES * ug_stage_bytes<BN, LA, LB>() + EPI::smem_bytes(BN);
-    auto kern = umma_gemm_kernel<BN, STAGES, LA, LB, EPI>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
+    const cuuint64_t inner = (cuuint64_t)(op.mn_major ? op.rows : op.kext);
+    const cuuint64_t outer = (cuuint64_t)(op.mn_major ? op.kext : op.rows);
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {(cuuint64_t)op.ld * 2};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    if ((uintptr_t)op.p % 16 || (op.ld * 2) % 16 || inner > (cuuint64_t)op.ld)
+        return false;
+    return cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(op.p), dims, strides,
+                                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// M x N output (N a multiple of BN), K split into `splits` ranges of whole stages.
+template <int BN, int STAGES, bool AMN, bool BMN, class EPI>
+static tdp_status launch_umma_gemm(const GemmOp &a, const GemmOp &b, const EPI &epi, int M, int N, int K, int splits,
+                                   int32_t *d_status, cudaStream_t s)
+{
+    if (N % BN || a.mn_major != AMN || b.mn_major != BMN)
+        return TDP_ERR_INVALID_ARG;
+    CUtensorMap ta, tb;
+    if (!ug_tensor_map(a, AMN ? UG_BK : UG_BM, &ta) || !ug_tensor_map(b, BMN ? UG_BK : BN, &tb))
+        return TDP_ERR_INVALID_ARG;
+    constexpr size_t smem = (size_t)STAGES * (ug_op_bytes<AMN>(UG_BM) + ug_op_bytes<BMN>(BN)) + EPI::smem_bytes(BN);
+    static_assert(smem + 1024 <= 232448, "shared memory");
+    auto kern = umma_gemm_kernel<BN, STAGES, AMN, BMN, EPI>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TDP_ERR_CUDA;
     int kps = (K + splits - 1) / splits;
     kps = (kps + UG_BK - 1) / UG_BK * UG_BK;
     dim3 grid((M + UG_BM - 1) / UG_BM, N / BN, splits);
-    kern<<<grid, UG_THREADS, smem, s>>>(la, lb, epi, K, kps, d_status, spin_limit());
-    return cudaGetLastError();
+    kern<<<grid, UG_THREADS, smem, s>>>(ta, tb, epi, K, kps, d_status, spin_limit());
+    return cudaGetLastError() == cudaSuccess ? TDP_OK : TDP_ERR_CUDA;
 }
 
 // ------------------------------------- pre-pool gradient patches
@@ -1592,10 +1612,9 @@ tdp_status tdp_cnn_fc1_fwd(const void *y2, int64_t n_cells, const void *wfc1, co
     cudaStream_t s = (cudaStream_t)stream;
     float *part = (float *)ws;
     const int M = (int)n_cells;
-    LoadK la{(const bf16 *)y2, M, FEAT};
-    LoadK lb{(const bf16 *)wfc1, HID, FEAT};
+    const GemmOp la{y2, M, FEAT, FEAT, false}, lb{wfc1, HID, FEAT, FEAT, false};
     EpiPartialF32 epi{part, M, HID, (size_t)M * HID};
-    tdp_status st = cerr(launch_umma_gemm<HID, 3>(la, lb, epi, M, HID, FEAT, FC1_FWD_SPLITS, d_status, s));
+    tdp_status st = launch_umma_gemm<HID, 3, false, false>(la, lb, epi, M, HID, FEAT, FC1_FWD_SPLITS, d_status, s);
     if (st != TDP_OK)
         return st;
     long long n = (long long)M * HID;
@@ -1659,20 +1678,18 @@ tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, in
     const int M = (int)n_cells;
     // dgrad: dy2p[cell][f] = (sum_u dh1[cell][u] wfc1[u][f]) * (y2 > 0)
     {
-        LoadK la{(const bf16 *)dh1, M, HID};
-        LoadMN lb{(const bf16 *)wfc1, FEAT, FEAT};
+        const GemmOp la{dh1, M, HID, HID, false}, lb{wfc1, FEAT, HID, FEAT, true};
         EpiMaskedBf16 epi{(bf16 *)dy2p, (const bf16 *)y2, M, FEAT, EpiMaskedBf16::pitch(128)};
-        tdp_status st = cerr(launch_umma_gemm<128, 2>(la, lb, epi, M, FEAT, HID, 1, d_status, s));
+        tdp_status st = launch_umma_gemm<128, 2, false, true>(la, lb, epi, M, FEAT, HID, 1, d_status, s);
         if (st != TDP_OK)
             return st;
     }
     // wgrad: dwfc1[u][f] = sum_cell dh1[cell][u] y2[cell][f]
     float *part = (float *)ws;
     {
-        LoadMN la{(const bf16 *)dh1, HID, HID};
-        LoadMN lb{(const bf16 *)y2, FEAT, FEAT};
+        const GemmOp la{dh1, HID, M, HID, true}, lb{y2, FEAT, M, FEAT, true};
         EpiPartialF32 epi{part, HID, FEAT, (size_t)HID * FEAT};
-        tdp_status st = cerr(launch_umma_gemm<256, 2>(la, lb, epi, HID, FEAT, M, FC1_WGRAD_SPLITS, d_status, s));
+        tdp_status st = launch_umma_gemm<256, 2, true, true>(la, lb, epi, HID, FEAT, M, FC1_WGRAD_SPLITS, d_status, s);
         if (st != TDP_OK)
             return st;
         long long n = (long long)HID * FEAT;

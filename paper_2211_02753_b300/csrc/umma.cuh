@@ -26,6 +26,30 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// Descriptor of a K-major operand stored with the 128-byte swizzle: each row
+// of 64 bf16 (one K stage) is 128 bytes, 8 rows form a 1024-byte atom whose
+// 16-byte chunks are XOR-permuted by row (the layout a TMA copy with
+// CU_TENSOR_MAP_SWIZZLE_128B writes); SBO = 1024 (the next 8 rows), LBO
+// unused (1), layout type 2 (128-byte swizzle) in bits 61-63.  The atom must
+// be 1024-byte aligned; a K16 step advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+// Descriptor of an MN-major operand stored with the 128-byte swizzle: each
+// k-row holds 64 consecutive M (or N) elements in 128 bytes, 8 k-rows form a
+// 1024-byte atom.  Here the leading offset is the distance between 64-element
+// groups along M/N and the stride offset the distance between 8-row groups
+// along K (measured: the other assignment gives wrong products); layout type
+// 2.
+__device__ __forceinline__ uint64_t smem_desc_sw128_mn(uint32_t saddr, uint32_t k_stride, uint32_t mn_stride)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((mn_stride >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((k_stride >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
 // Instruction descriptor of kind::f16 with bf16 A and B (both K-major) and an
 // fp32 accumulator: D format bit 4, A format bits 7-9 = 1 (bf16), B format
 // bits 10-12 = 1, N / 8 at bit 17, M / 16 at bit 24.

@@ -348,6 +348,25 @@ __global__ void __launch_bounds__(UG_THREADS) umma_gemm_kernel(const __grid_cons
     }
 }
 
+// cuTensorMapEncodeTiled, looked up through the runtime once (the library
+// takes no link-time dependency on the driver library); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
 // Tensor map of one operand: 2-D, bf16, inner dimension the contiguous one,
 // zero fill, 128-byte swizzle; K-major: a box of 64 k x box_outer rows;
 // MN-major: a box of 64 rows x box_outer (64) k.
@@ -359,9 +378,10 @@ static bool ug_tensor_map(const GemmOp &op, int box_outer, CUtensorMap *map)
     const cuuint64_t strides[1] = {(cuuint64_t)op.ld * 2};
     const cuuint32_t box[2] = {64u, (cuuint32_t)box_outer};
     const cuuint32_t estr[2] = {1, 1};
-    if ((uintptr_t)op.p % 16 || (op.ld * 2) % 16 || inner > (cuuint64_t)op.ld)
+    const EncodeTiledFn encode = encode_tiled();
+    if (!encode || (uintptr_t)op.p % 16 || (op.ld * 2) % 16 || inner > (cuuint64_t)op.ld)
         return false;
-    return cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(op.p), dims, strides,
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(op.p), dims, strides,
                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;

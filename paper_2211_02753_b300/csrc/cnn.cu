@@ -1156,8 +1156,16 @@ static inline int colsum_blocks(long long rows, int C)
 // added by a fixed tree.  A block covers 32 consecutive outputs.
 constexpr int PS_SLICES = 16;
 
+// Output column i goes to out0[i] for i < n0, out1[i - n0] for i < n0 + n1,
+// else out2[i - n0 - n1] (the column ranges of one partial row that belong
+// to different tensors, reduced in one launch).
+struct PsOut {
+    float *out0, *out1, *out2;
+    int n0, n1;
+};
+
 __global__ void __launch_bounds__(32 * PS_SLICES) partial_sum_kernel(const float *__restrict__ part, int nb, int n,
-                                                                     size_t stride, float *__restrict__ out)
+                                                                     size_t stride, PsOut po)
 {
     __shared__ double s_acc[PS_SLICES][32];
     const int e = threadIdx.x & 31, sl = threadIdx.x >> 5;
@@ -1186,9 +1194,18 @@ __global__ void __launch_bounds__(32 * PS_SLICES) partial_sum_kernel(const float
             s_acc[sl][e] += s_acc[sl + h][e];
         __syncthreads();
     }
-    if (sl == 0 && i < n)
-        out[i] = (float)s_acc[0][e];
+    if (sl == 0 && i < n) {
+        const float r = (float)s_acc[0][e];
+        if (i < po.n0)
+            po.out0[i] = r;
+        else if (i < po.n0 + po.n1)
+            po.out1[i - po.n0] = r;
+        else
+            po.out2[i - po.n0 - po.n1] = r;
+    }
 }
+
+static inline PsOut ps_out(float *o) { return PsOut{o, nullptr, nullptr, 1 << 30, 0}; }
 
 static inline unsigned psum_blocks(int n) { return (unsigned)((n + 31) / 32); }
 
@@ -1667,12 +1684,9 @@ tdp_status tdp_cnn_head(const void *h1, int64_t n_grids, const float *wfc2, cons
                                                            (bf16 *)dh1, part);
     if (targets) {
         const size_t per = NCLS * HID + NCLS + 1;
-        partial_sum_kernel<<<psum_blocks(NCLS * HID), 32 * PS_SLICES, 0, s>>>(part, (int)n_grids, NCLS * HID, per,
-                                                                             dwfc2);
-        partial_sum_kernel<<<psum_blocks(NCLS), 32 * PS_SLICES, 0, s>>>(part + NCLS * HID, (int)n_grids, NCLS, per,
-                                                                        dbfc2);
-        partial_sum_kernel<<<psum_blocks(1), 32 * PS_SLICES, 0, s>>>(part + NCLS * HID + NCLS, (int)n_grids, 1, per,
-                                                                     loss);
+        // one launch: fc2 weight sums, then the 10 bias sums, then the loss
+        partial_sum_kernel<<<psum_blocks((int)per), 32 * PS_SLICES, 0, s>>>(
+            part, (int)n_grids, (int)per, per, PsOut{dwfc2, dbfc2, loss, NCLS * HID, NCLS});
     }
     return launch_status();
 }
@@ -1721,7 +1735,7 @@ tdp_status tdp_cnn_fc1_bwd(const void *dh1, const void *y2, const void *wfc1, in
         float *bp = (float *)((char *)ws + align_up((size_t)FC1_WGRAD_SPLITS * HID * FEAT * sizeof(float), 256));
         const int nb = colsum_blocks(n_cells, HID);
         colsum_bf16_kernel<<<nb, CS_THREADS, 0, s>>>((const bf16 *)dh1, n_cells, HID, bp);
-        partial_sum_kernel<<<psum_blocks(HID), 32 * PS_SLICES, 0, s>>>(bp, nb, HID, HID, dbfc1);
+        partial_sum_kernel<<<psum_blocks(HID), 32 * PS_SLICES, 0, s>>>(bp, nb, HID, HID, ps_out(dbfc1));
     }
     return launch_status();
 }
@@ -1780,7 +1794,7 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
         conv2_wgrad_umma_kernel<<<grid, WG_THREADS, smem, s>>>((const bf16 *)dy2p, argmax, (const bf16 *)y1, ntiles,
                                                                part, d_status, spin_limit());
         partial_sum_kernel<<<psum_blocks(CH2 * 9 * CH1), 32 * PS_SLICES, 0, s>>>(part, grid, CH2 * 9 * CH1,
-                                                                                 CH2 * 9 * CH1, dw2);
+                                                                                 CH2 * 9 * CH1, ps_out(dw2));
     }
     // bias: sum of the pooled gradient (each pooled value lands on exactly one pixel)
     {
@@ -1788,7 +1802,7 @@ tdp_status tdp_cnn_conv2_bwd(const void *dy2p, const uint8_t *argmax, const void
         long long Q = n_cells * PO * PO;
         const int nb = colsum_blocks(Q, CH2);
         colsum_bf16_kernel<<<nb, CS_THREADS, 0, s>>>((const bf16 *)dy2p, Q, CH2, bp);
-        partial_sum_kernel<<<psum_blocks(CH2), 32 * PS_SLICES, 0, s>>>(bp, nb, CH2, CH2, db2);
+        partial_sum_kernel<<<psum_blocks(CH2), 32 * PS_SLICES, 0, s>>>(bp, nb, CH2, CH2, ps_out(db2));
     }
     return launch_status();
 }
@@ -1816,8 +1830,9 @@ tdp_status tdp_cnn_conv1_bwd(const void *dz1, const uint8_t *grids, int64_t n_ce
     float *part = (float *)ws;
     conv1_wgrad_kernel<<<nb, W1_THREADS, 0, s>>>((const bf16 *)dz1, grids, n_cells, cpb, part);
     // each partial row: 288 weight sums, then the 32 bias sums
-    partial_sum_kernel<<<psum_blocks(CH1 * 9), 32 * PS_SLICES, 0, s>>>(part, nb, CH1 * 9, CH1 * 10, dw1);
-    partial_sum_kernel<<<psum_blocks(CH1), 32 * PS_SLICES, 0, s>>>(part + CH1 * 9, nb, CH1, CH1 * 10, db1);
+    // one launch: the 288 weight sums, then the 32 bias sums
+    partial_sum_kernel<<<psum_blocks(CH1 * 10), 32 * PS_SLICES, 0, s>>>(part, nb, CH1 * 10, CH1 * 10,
+                                                                        PsOut{dw1, db1, nullptr, CH1 * 9, CH1});
     return launch_status();
 }
 

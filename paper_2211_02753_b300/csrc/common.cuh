@@ -165,64 +165,6 @@ __device__ __forceinline__ void load4_int(const void *p, int dt, bool vec_ok, lo
         v[k] = (r + k < n) ? load_int(p, dt, r + k) : 0;
 }
 
-// Loads rows r0 + j*128 + {0..3} for j < STEPS of one integer column.  The
-// dtype switch sits outside the step loop so that all STEPS vector loads are
-// issued before any result is used.
-template <int STEPS>
-__device__ __forceinline__ void load_rows(const void *p, int dt, bool vec_ok, long long r0, long long n,
-                                          long long (&v)[STEPS][4])
-{
-    if (vec_ok && r0 + (STEPS - 1) * 128 + 3 < n) {
-        if (dt == TDP_I32) {
-            int4 w[STEPS];
-#pragma unroll
-            for (int j = 0; j < STEPS; j++)
-                w[j] = __ldg((const int4 *)((const int32_t *)p + r0 + j * 128));
-#pragma unroll
-            for (int j = 0; j < STEPS; j++) {
-                v[j][0] = w[j].x;
-                v[j][1] = w[j].y;
-                v[j][2] = w[j].z;
-                v[j][3] = w[j].w;
-            }
-            return;
-        }
-        if (dt == TDP_I8 || dt == TDP_U8) {
-            unsigned w[STEPS];
-#pragma unroll
-            for (int j = 0; j < STEPS; j++)
-                w[j] = __ldg((const unsigned *)((const uint8_t *)p + r0 + j * 128));
-#pragma unroll
-            for (int j = 0; j < STEPS; j++)
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    unsigned b = (w[j] >> (8 * k)) & 0xffu;
-                    v[j][k] = dt == TDP_I8 ? (long long)(int8_t)b : (long long)b;
-                }
-            return;
-        }
-        if (dt == TDP_I64) {
-            longlong2 a[STEPS], b[STEPS];
-#pragma unroll
-            for (int j = 0; j < STEPS; j++) {
-                a[j] = __ldg((const longlong2 *)((const long long *)p + r0 + j * 128));
-                b[j] = __ldg((const longlong2 *)((const long long *)p + r0 + j * 128 + 2));
-            }
-#pragma unroll
-            for (int j = 0; j < STEPS; j++) {
-                v[j][0] = a[j].x;
-                v[j][1] = a[j].y;
-                v[j][2] = b[j].x;
-                v[j][3] = b[j].y;
-            }
-            return;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < STEPS; j++)
-        load4_int(p, dt, vec_ok, r0 + j * 128, n, v[j]);
-}
-
 // Range form of predicate p for a value already widened to 32 bits (I8, U8,
 // I32 columns; lo/hi are clamped into the column type, so hi - lo fits).
 __device__ __forceinline__ unsigned range_holds32(int v, int lo, unsigned span, unsigned neg)
@@ -387,19 +329,6 @@ __device__ __forceinline__ uint4 ldg16_hint(const uint32_t *p, uint64_t policy)
     return v;
 }
 
-// One test of the phase of the given parity (true once it has completed).
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.b32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done)
-                 : "r"(smem_addr(bar)), "r"(parity)
-                 : "memory");
-    return done != 0;
-}
-
 // Plain mbarrier arrival (release at CTA scope).
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -514,148 +443,6 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
     if (lane == 0)
         st_relaxed_u64(&status[tile], LB_INC | ((excl + aggregate) & LB_VAL));
     return excl;
-}
-
-
-// Wide look-back.  Each lane reads one aligned group of LB_WIDE = 16
-// consecutive status words (128 bytes, eight 16-byte vector loads) per round
-// trip, so one warp spans 512 predecessor tiles; the inclusive prefix a tile
-// needs is then nearly always found in one round.  Each status word is
-// written whole (64-bit single-copy atomic), so a vector load never sees a
-// torn word.  The window's loads can be issued early (lb_window_load) and
-// resolved later (lookback_resolve) so that their latency overlaps other work.
-constexpr int LB_WIDE = 16;
-
-struct LbWindow {
-    unsigned long long w[LB_WIDE]; // w[j] = word 16g + 15 - j of the lane's group g (j = 0 nearest)
-};
-
-__device__ __forceinline__ void lb_load2(const unsigned long long *p, unsigned long long &a, unsigned long long &b)
-{
-    asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
-}
-
-// Loads the group the lane covers in the first round of tile's look-back:
-// group (tile - 1) / 16 - lane.  Groups below 0 read as inclusive zeros.
-__device__ __forceinline__ void lb_window_load(const unsigned long long *status, long long tile, LbWindow &W)
-{
-    const int lane = threadIdx.x & 31;
-    const long long g = (tile - 1) / LB_WIDE - lane;
-    if (tile > 0 && g >= 0) {
-        const unsigned long long *p = status + g * LB_WIDE;
-#pragma unroll
-        for (int j = 0; j < LB_WIDE; j += 2)
-            lb_load2(p + LB_WIDE - 2 - j, W.w[j + 1], W.w[j]);
-    } else {
-#pragma unroll
-        for (int j = 0; j < LB_WIDE; j++)
-            W.w[j] = LB_INC;
-    }
-}
-
-// Called by ONE full warp, with W loaded by lb_window_load(status, tile, W)
-// (possibly long before).  Walks back from tile - 1 until an inclusive
-// prefix, returns the exclusive prefix of `tile` (same value in every lane)
-// and publishes tile's inclusive prefix (exclusive + aggregate).  The
-// tile's own aggregate must have been published before (lb_publish_agg), or
-// tile == 0.
-__device__ __forceinline__ unsigned long long lookback_resolve(unsigned long long *status, long long tile,
-                                                               unsigned long long aggregate, LbWindow &W,
-                                                               uint32_t limit, int32_t *d_status)
-{
-    const int lane = threadIdx.x & 31;
-    if (tile == 0) {
-        if (lane == 0)
-            st_relaxed_u64(&status[0], LB_INC | aggregate);
-        return 0;
-    }
-    unsigned long long excl = 0;
-    const long long base = tile - 1;   // nearest predecessor
-    long long g0 = base / LB_WIDE;     // its group
-    for (int round = 0;; round++) {
-        const long long g = g0 - lane;
-        if (round > 0) { // later rounds load here
-            if (g >= 0) {
-                const unsigned long long *p = status + g * LB_WIDE;
-#pragma unroll
-                for (int j = 0; j < LB_WIDE; j += 2)
-                    lb_load2(p + LB_WIDE - 2 - j, W.w[j + 1], W.w[j]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < LB_WIDE; j++)
-                    W.w[j] = LB_INC;
-            }
-        }
-        unsigned pend = 0;
-#pragma unroll
-        for (int j = 0; j < LB_WIDE; j++) {
-            const long long t = g * LB_WIDE + LB_WIDE - 1 - j;
-            if (t > base)
-                W.w[j] = LB_AGG; // the tile itself and later ones: neutral
-            if (g < 0)
-                W.w[j] = LB_INC;
-            pend |= ((W.w[j] >> 62) == 0 ? 1u : 0u) << j;
-        }
-        // bounded wait until every word of the lane holds a flag
-        for (uint32_t polls = 0; pend;) {
-            if (polls++ >= limit || ((polls & 63) == 0 && timed_out_already(d_status))) {
-                set_status(d_status, TDP_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(polls < 64 ? 20 : 200);
-#pragma unroll
-            for (int j = 0; j < LB_WIDE; j++)
-                if (pend >> j & 1u) {
-                    W.w[j] = ld_relaxed_u64(&status[g * LB_WIDE + LB_WIDE - 1 - j]);
-                    if ((W.w[j] >> 62) != 0)
-                        pend &= ~(1u << j);
-                }
-        }
-        // nearest inclusive word of the lane (a timed-out word counts as one)
-        int jinc = LB_WIDE;
-#pragma unroll
-        for (int j = LB_WIDE - 1; j >= 0; j--)
-            if ((W.w[j] >> 62) != 1)
-                jinc = j;
-        const unsigned inc_lanes = __ballot_sync(0xffffffffu, jinc < LB_WIDE);
-        const int stop = inc_lanes ? __ffs(inc_lanes) - 1 : 32;
-        unsigned long long contrib = 0;
-        if (lane <= stop) {
-            const int last = lane == stop ? jinc : LB_WIDE - 1;
-#pragma unroll
-            for (int j = 0; j < LB_WIDE; j++)
-                contrib += j <= last ? (W.w[j] & LB_VAL) : 0ull;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
-        excl += contrib;
-        if (inc_lanes)
-            break;
-        g0 -= 32;
-    }
-    if (lane == 0)
-        st_relaxed_u64(&status[tile], LB_INC | ((excl + aggregate) & LB_VAL));
-    return excl;
-}
-
-// Publishes a tile's aggregate (one thread); tile 0 publishes its inclusive
-// prefix, which is its aggregate.
-__device__ __forceinline__ void lb_publish_agg(unsigned long long *status, long long tile, unsigned long long aggregate)
-{
-    st_relaxed_u64(&status[tile], (tile == 0 ? LB_INC : LB_AGG) | aggregate);
-}
-
-// Same contract as lookback_exclusive, with the wide window.
-__device__ __forceinline__ unsigned long long lookback_exclusive_wide(unsigned long long *status, long long tile,
-                                                                      unsigned long long aggregate, uint32_t limit,
-                                                                      int32_t *d_status)
-{
-    if ((threadIdx.x & 31) == 0)
-        lb_publish_agg(status, tile, aggregate);
-    LbWindow W;
-    lb_window_load(status, tile, W);
-    return lookback_resolve(status, tile, aggregate, W, limit, d_status);
 }
 
 } // namespace tdp

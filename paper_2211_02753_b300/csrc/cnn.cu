@@ -123,7 +123,8 @@ struct EpiPartialF32 { // out[split][m][ldo]
     size_t split_stride;
     static constexpr int smem_bytes(int) { return 0; }
     __device__ void prefetch(unsigned char *, int, int, int, int) const {}
-    __device__ void store(int m, int n, const float (&v)[32], int split, const unsigned char *, int, int) const
+    __device__ void finish(const unsigned char *, int, int, int, int) const {}
+    __device__ void store(int m, int n, const float (&v)[32], int split, unsigned char *, int, int) const
     {
         if (m >= M)
             return;
@@ -153,12 +154,12 @@ struct EpiMaskedBf16 {
                             m < M);
         }
     }
-    __device__ void store(int m, int n, const float (&v)[32], int, const unsigned char *buf, int m0, int n0) const
+    // the masked values replace the mask in shared memory (this thread's row)
+    __device__ void store(int m, int n, const float (&v)[32], int, unsigned char *buf, int m0, int n0) const
     {
         if (m >= M)
             return;
-        const uint4 *mk = (const uint4 *)(buf + (m - m0) * pitch_bn + (n - n0) * 2);
-        uint4 *dst = (uint4 *)(out + (size_t)m * ldo + n);
+        uint4 *mk = (uint4 *)(buf + (m - m0) * pitch_bn + (n - n0) * 2);
 #pragma unroll
         for (int h = 0; h < 4; h++) {
             const uint4 mm = mk[h];
@@ -167,7 +168,18 @@ struct EpiMaskedBf16 {
 #pragma unroll
             for (int e = 0; e < 8; e++)
                 ov[e] = __float2bfloat16_rn(bf2f(mb[e]) > 0.f ? v[8 * h + e] : 0.f);
-            dst[h] = *(const uint4 *)ov;
+            mk[h] = *(const uint4 *)ov;
+        }
+    }
+    // then the tile leaves with row-contiguous 16-byte stores (a warp writes
+    // whole lines), after every thread's store()
+    __device__ void finish(const unsigned char *buf, int m0, int n0, int bn, int tid) const
+    {
+        const int cpr = bn / 8;
+        for (int c = tid; c < 128 * cpr; c += 128) {
+            const int r = c / cpr, j = c % cpr;
+            if (m0 + r < M)
+                *(uint4 *)(out + (size_t)(m0 + r) * ldo + n0 + j * 8) = *(const uint4 *)(buf + r * pitch_bn + j * 16);
         }
     }
     int pitch_bn; // the staging row pitch, pitch(BN) of the launch
@@ -340,6 +352,8 @@ __global__ void __launch_bounds__(UG_THREADS) umma_gemm_kernel(const __grid_cons
     }
     umma::fence_before_sync();
     __syncthreads();
+    if constexpr (EPI::PREFETCH)
+        epi.finish(epi_buf, m0, n0, BN, tid);
     if (tid == 0 && s_err)
         set_status(d_status, TDP_ERR_TIMEOUT);
     if (warp == 0) {

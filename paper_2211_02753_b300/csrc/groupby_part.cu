@@ -28,7 +28,8 @@
 
 namespace tdp {
 
-constexpr int GP_THREADS = 256;
+constexpr int GP_THREADS = 256;  // reduce pass
+constexpr int GS_THREADS = 1024; // count and scatter passes (rows in flight per SM)
 constexpr int GP_MAX_BUCKETS = 16384;
 constexpr size_t GP_TABLE_BYTES = 64 * 1024; // dense table of one bucket
 
@@ -59,7 +60,7 @@ template <bool SEL>
 __device__ __forceinline__ void block_chunk(long long n, const long long *d_nsel, long long &c0, long long &c1)
 {
     const long long total = SEL ? min(*d_nsel, n) : (d_nsel ? min(*d_nsel, n) : n);
-    const long long unit = SEL ? GP_THREADS : 4 * GP_THREADS;
+    const long long unit = SEL ? GS_THREADS : 4 * GS_THREADS;
     long long chunk = (total + gridDim.x - 1) / gridDim.x;
     chunk = (chunk + unit - 1) / unit * unit;
     c0 = min(total, (long long)blockIdx.x * chunk);
@@ -81,7 +82,7 @@ __device__ __forceinline__ bool for_rows(const PredSet &ps, const KeySet &ks, lo
     bool bad = false;
     if (!SEL) {
         const long long off = (long long)(threadIdx.x & ~31) * 4 + (threadIdx.x & 31) * 4;
-        for (long long sb = c0; sb < c1; sb += 4 * GP_THREADS) {
+        for (long long sb = c0; sb < c1; sb += 4 * GS_THREADS) {
             const long long r = sb + off;
             unsigned m = eval_preds4(ps, r, c1);
             long long gid[4] = {0, 0, 0, 0};
@@ -103,7 +104,7 @@ __device__ __forceinline__ bool for_rows(const PredSet &ps, const KeySet &ks, lo
                 f(r + j, (m >> j & 1) ? gid[j] : -1ll);
         }
     } else {
-        for (long long sb = c0; sb < c1; sb += GP_THREADS) {
+        for (long long sb = c0; sb < c1; sb += GS_THREADS) {
             const long long i = sb + threadIdx.x;
             long long gid = -1;
             long long row = 0;
@@ -127,13 +128,13 @@ __device__ __forceinline__ bool for_rows(const PredSet &ps, const KeySet &ks, lo
 // this block's offset within the bucket, kept in boff[block][bucket] for the
 // scatter pass.
 template <bool SEL>
-__global__ void __launch_bounds__(GP_THREADS) part_count_kernel(PredSet ps, KeySet ks, long long n,
+__global__ void __launch_bounds__(GS_THREADS) part_count_kernel(PredSet ps, KeySet ks, long long n,
                                                                 const int32_t *sel, const long long *d_nsel,
                                                                 int bw, int nb, unsigned *hist, unsigned *boff,
                                                                 int32_t *d_status)
 {
     extern __shared__ unsigned gp_hist[];
-    for (int i = threadIdx.x; i < nb; i += GP_THREADS)
+    for (int i = threadIdx.x; i < nb; i += GS_THREADS)
         gp_hist[i] = 0;
     __syncthreads();
     const bool ok = for_rows<SEL>(ps, ks, n, sel, d_nsel, [&](long long, long long gid) {
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(GP_THREADS) part_count_kernel(PredSet ps, KeyS
         set_status(d_status, TDP_ERR_OVERFLOW);
     __syncthreads();
     unsigned *my = boff + (size_t)blockIdx.x * nb;
-    for (int i = threadIdx.x; i < nb; i += GP_THREADS) {
+    for (int i = threadIdx.x; i < nb; i += GS_THREADS) {
         const unsigned c = gp_hist[i];
         my[i] = c ? atomicAdd(&hist[i], c) : 0u;
     }
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(1024) part_scan_kernel(const unsigned *hist, i
 // (gid, slot values), at start[bucket] + the block's offset within the bucket
 // + a shared-memory counter (no global atomics).
 template <bool SEL>
-__global__ void __launch_bounds__(GP_THREADS) part_scatter_kernel(PredSet ps, KeySet ks, AggSet as, long long n,
+__global__ void __launch_bounds__(GS_THREADS) part_scatter_kernel(PredSet ps, KeySet ks, AggSet as, long long n,
                                                                   const int32_t *sel, const long long *d_nsel,
                                                                   int bw, int nb, const unsigned *start,
                                                                   const unsigned *boff, uint32_t *out_gid,
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(GP_THREADS) part_scatter_kernel(PredSet ps, Ke
 {
     extern __shared__ unsigned gp_base[];
     const unsigned *my = boff + (size_t)blockIdx.x * nb;
-    for (int i = threadIdx.x; i < nb; i += GP_THREADS)
+    for (int i = threadIdx.x; i < nb; i += GS_THREADS)
         gp_base[i] = start[i] + my[i];
     __syncthreads();
     const int NS = as.nslots;
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(GP_THREADS) part_scatter_kernel(PredSet ps, Ke
     long long c0, c1;
     block_chunk<false>(n, d_nsel, c0, c1);
     const long long off = (long long)threadIdx.x * 4;
-    for (long long sb = c0; sb < c1; sb += 4 * GP_THREADS) {
+    for (long long sb = c0; sb < c1; sb += 4 * GS_THREADS) {
         const long long r = sb + off;
         unsigned m = eval_preds4(ps, r, c1);
         long long gid[4] = {0, 0, 0, 0};
@@ -487,10 +488,10 @@ tdp_status part_run(const PredSet &ps, const KeySet &ks, const AggSet &as, long 
         cudaFuncSetAttribute(sct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm) != cudaSuccess)
         return TDP_ERR_CUDA;
     if (n > 0)
-        cnt<<<G, GP_THREADS, hsm, s>>>(ps, ks, n, sel, dn, pp.bw, nb, hist, boff, d_status);
+        cnt<<<G, GS_THREADS, hsm, s>>>(ps, ks, n, sel, dn, pp.bw, nb, hist, boff, d_status);
     part_scan_kernel<<<1, 1024, 0, s>>>(hist, nb, start);
     if (n > 0)
-        sct<<<G, GP_THREADS, hsm, s>>>(ps, ks, as, n, sel, dn, pp.bw, nb, start, boff, gid, val, val_stride);
+        sct<<<G, GS_THREADS, hsm, s>>>(ps, ks, as, n, sel, dn, pp.bw, nb, start, boff, gid, val, val_stride);
     const size_t tsm = ((size_t)1 << pp.bw) * (as.nslots * 8 + 2); // table + rank -> slot index
     if (cudaFuncSetAttribute(part_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm) !=
         cudaSuccess)

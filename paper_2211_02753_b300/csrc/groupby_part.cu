@@ -28,7 +28,7 @@
 
 namespace tdp {
 
-constexpr int GP_THREADS = 256;  // reduce pass
+constexpr int GP_THREADS = 512;  // reduce pass
 constexpr int GS_THREADS = 1024; // count and scatter passes (rows in flight per SM)
 constexpr int GP_MAX_BUCKETS = 16384;
 constexpr size_t GP_TABLE_BYTES = 64 * 1024; // dense table of one bucket

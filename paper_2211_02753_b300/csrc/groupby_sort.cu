@@ -169,7 +169,7 @@ __device__ __forceinline__ void store_key(void *out, int dt, long long pos, long
 }
 
 template <typename K, typename V, int SL, bool CARRY>
-__global__ void __launch_bounds__(SR_THREADS) seg_reduce_kernel(const K *__restrict__ keys,
+__global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1) seg_reduce_kernel(const K *__restrict__ keys,
                                                                 const V *__restrict__ rows, long long n_max,
                                                                 const long long *d_n, KeySet ks, KeyPack kp,
                                                                 AggSet as, DenseOut out, long long cap,
@@ -543,13 +543,16 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
         kern<<<sgrid, SR_THREADS, 0, s>>>(sk, sr, n, rowcount, ks, kp, as, out, capacity, (long long *)d_ngroups,
                                           (SegRec *)(segws + 256), (unsigned *)segws, d_status, spin_limit());
     };
-    // accumulator slots carried through the scan: the smallest of 2, 4, 9 that fits
+    // accumulator slots carried through the scan: the smallest of 2, 4, 5, 9 that fits
+    // (the carried state sets the registers, and so the blocks resident per SM)
     if (CARRY)
         launch(seg_reduce_kernel<K, V, 2, true>);
     else if (as.nslots <= 2)
         launch(seg_reduce_kernel<K, V, 2, false>);
     else if (as.nslots <= 4)
         launch(seg_reduce_kernel<K, V, 4, false>);
+    else if (as.nslots <= 5)
+        launch(seg_reduce_kernel<K, V, 5, false>);
     else
         launch(seg_reduce_kernel<K, V, SR_MAXS, false>);
     return launch_status();

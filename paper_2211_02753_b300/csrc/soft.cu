@@ -3,11 +3,11 @@
 //
 // Rows stream through once per call with 16-byte loads (x, v: float4; gid:
 // int4).  Each block owns a contiguous chunk of rows and accumulates per-group
-// sums in shared memory: fp32 atomics over sub-chunks of about 16 rows per
-// group, folded after each sub-chunk into fp64 block accumulators; the fp64
-// partials of all blocks are then added in block order by a second small
-// kernel.  (Upstream gradients of either sign make the adjoint's group sums
-// cancel; a long fp32 chain would then lose the 1e-5 relative accuracy.)
+// sums in shared memory with fp64 atomics (each row's term is formed in fp32
+// and added in fp64); the fp64 partials of all blocks are then added in block
+// order by a second small kernel.  (Upstream gradients of either sign make the
+// adjoint's group sums cancel; fp32 sub-sums, even of ~16 rows per group,
+// left the cancelling groups of the adjoint at the edge of the 1e-5 bound.)
 // The mask m = sigmoid((x - theta[g]) / tau) is recomputed in the backward
 // pass, never stored; m(1-m) is evaluated as e/(1+e)^2 with e = exp(-|z|),
 // which has no cancellation when m is close to 1.  z = (x - theta) / tau is
@@ -54,30 +54,30 @@ __device__ __forceinline__ Sig sigmoid_xt(float x, float th, Tau tau)
 
 enum SoftMode { MODE_AGG_FWD = 0, MODE_AGG_BWD = 1, MODE_FILTER_BWD = 2 };
 
-// Per-row work of the three reduction modes.  Accumulates into smem
-// acc0 (and acc1 for the forward COUNT).
+// Per-row work of the three reduction modes.  Accumulates into the fp64
+// shared-memory accumulators acc0 (and acc1 for the forward COUNT).
 template <int MODE>
 __device__ __forceinline__ void soft_row(float x, float v, int g, float gm, const float *s_theta, const float *s_g0,
-                                         const float *s_g1, Tau tau, float *acc0, float *acc1, float *gx,
+                                         const float *s_g1, Tau tau, double *acc0, double *acc1, float *gx,
                                          float *gv, long long i, int G)
 {
     if ((unsigned)g >= (unsigned)G) // out-of-range group id: row ignored
         return;
     Sig s = sigmoid_xt(x, s_theta[g], tau);
     if (MODE == MODE_AGG_FWD) {
-        atomicAdd(&acc0[g], v * s.m);
-        atomicAdd(&acc1[g], s.m);
+        atomicAdd(&acc0[g], (double)(v * s.m));
+        atomicAdd(&acc1[g], (double)s.m);
     } else if (MODE == MODE_AGG_BWD) {
         float gS = s_g0[g];
         float w = (gS * v + s_g1[g]) * s.dm;
-        atomicAdd(&acc0[g], w);
+        atomicAdd(&acc0[g], (double)w);
         if (gx)
             gx[i] = w * tau.inv;
         if (gv)
             gv[i] = gS * s.m;
     } else {
         float w = gm * s.dm;
-        atomicAdd(&acc0[g], w);
+        atomicAdd(&acc0[g], (double)w);
         if (gx)
             gx[i] = w * tau.inv;
     }
@@ -93,26 +93,20 @@ __global__ void __launch_bounds__(SA_THREADS, SA_BLOCKS_PER_SM) soft_reduce_kern
                                                                  long long n, int G, long long chunk,
                                                                  double *__restrict__ partial, float *gx, float *gv)
 {
-    // Shared memory: fp64 block accumulators first, then fp32 arrays.
-    // fp32 atomics only ever sum one sub-chunk of at most SUB rows (about 16
-    // rows per group); each sub-chunk is then folded into fp64, so the fp32
-    // rounding error does not grow with the rows a block covers.
+    // Shared memory: fp64 block accumulators [K][G], then theta (and, for the
+    // aggregation adjoint, the upstream gradients) in fp32.
     constexpr int K = MODE == MODE_AGG_FWD ? 2 : 1;
     extern __shared__ double sm64[];
-    double *acc64 = sm64;                    // [K][G]
+    double *acc0 = sm64;                     // [G]
+    double *acc1 = sm64 + G;                 // [G], forward COUNT only
     float *s_theta = (float *)(sm64 + K * G);
-    float *acc0 = s_theta + G;
-    float *acc1 = s_theta + 2 * G;           // forward only
-    float *s_g0 = s_theta + 2 * G;           // aggregation backward only
-    float *s_g1 = s_theta + 3 * G;
+    float *s_g0 = s_theta + G;               // aggregation backward only
+    float *s_g1 = s_theta + 2 * G;
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
         s_theta[g] = theta[g];
-        acc0[g] = 0.f;
-        acc64[g] = 0.0;
-        if (MODE == MODE_AGG_FWD) {
-            acc1[g] = 0.f;
-            acc64[G + g] = 0.0;
-        }
+        acc0[g] = 0.0;
+        if (MODE == MODE_AGG_FWD)
+            acc1[g] = 0.0;
         if (MODE == MODE_AGG_BWD) {
             s_g0[g] = g0[g];
             s_g1[g] = g1[g];
@@ -123,62 +117,49 @@ __global__ void __launch_bounds__(SA_THREADS, SA_BLOCKS_PER_SM) soft_reduce_kern
     const long long end = min(n, beg + chunk);
     const bool vec = (((uintptr_t)x | (uintptr_t)gid | (uintptr_t)(MODE == MODE_FILTER_BWD ? g0 : v)) % 16) == 0;
     const float *aux = MODE == MODE_FILTER_BWD ? g0 : v; // v, or grad_mask for the filter adjoint
-    const long long SUB = (max(16ll * G, 512ll) + 3) / 4 * 4; // ~16 rows per group, multiple of 4
-    for (long long sb = beg; sb < end; sb += SUB) {
-        const long long se = min(end, sb + SUB);
-        long long tail = sb;
-        if (vec) {
-            const long long nvec = (se - sb) / 4;
-            // SA_UNROLL quads a thread per pass, all of their loads issued
-            // before any row is reduced (bytes in flight for the HBM)
-            long long q = threadIdx.x;
-            for (; q + (SA_UNROLL - 1) * SA_THREADS < nvec; q += SA_UNROLL * SA_THREADS) {
-                float4 xx[SA_UNROLL], aa[SA_UNROLL];
-                int4 gg[SA_UNROLL];
+    long long tail = beg;
+    if (vec && beg < end) {
+        const long long nvec = (end - beg) / 4;
+        // SA_UNROLL quads a thread per pass, all of their loads issued
+        // before any row is reduced (bytes in flight for the HBM)
+        long long q = threadIdx.x;
+        for (; q + (SA_UNROLL - 1) * SA_THREADS < nvec; q += SA_UNROLL * SA_THREADS) {
+            float4 xx[SA_UNROLL], aa[SA_UNROLL];
+            int4 gg[SA_UNROLL];
 #pragma unroll
-                for (int u = 0; u < SA_UNROLL; u++) {
-                    const long long i = sb + 4 * (q + u * SA_THREADS);
-                    xx[u] = __ldcs((const float4 *)(x + i));
-                    aa[u] = __ldcs((const float4 *)(aux + i));
-                    gg[u] = __ldcs((const int4 *)(gid + i));
-                }
+            for (int u = 0; u < SA_UNROLL; u++) {
+                const long long i = beg + 4 * (q + u * SA_THREADS);
+                xx[u] = __ldcs((const float4 *)(x + i));
+                aa[u] = __ldcs((const float4 *)(aux + i));
+                gg[u] = __ldcs((const int4 *)(gid + i));
+            }
 #pragma unroll
-                for (int u = 0; u < SA_UNROLL; u++) {
-                    const long long i = sb + 4 * (q + u * SA_THREADS);
-                    soft_row<MODE>(xx[u].x, aa[u].x, gg[u].x, aa[u].x, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i, G);
-                    soft_row<MODE>(xx[u].y, aa[u].y, gg[u].y, aa[u].y, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 1, G);
-                    soft_row<MODE>(xx[u].z, aa[u].z, gg[u].z, aa[u].z, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 2, G);
-                    soft_row<MODE>(xx[u].w, aa[u].w, gg[u].w, aa[u].w, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 3, G);
-                }
-            }
-            for (; q < nvec; q += SA_THREADS) {
-                const long long i = sb + 4 * q;
-                float4 xx = __ldcs((const float4 *)(x + i));
-                float4 aa = __ldcs((const float4 *)(aux + i));
-                int4 gg = __ldcs((const int4 *)(gid + i));
-                soft_row<MODE>(xx.x, aa.x, gg.x, aa.x, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i, G);
-                soft_row<MODE>(xx.y, aa.y, gg.y, aa.y, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 1, G);
-                soft_row<MODE>(xx.z, aa.z, gg.z, aa.z, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 2, G);
-                soft_row<MODE>(xx.w, aa.w, gg.w, aa.w, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 3, G);
-            }
-            tail = sb + 4 * nvec;
-        }
-        for (long long r = tail + threadIdx.x; r < se; r += SA_THREADS)
-            soft_row<MODE>(x[r], aux[r], gid[r], aux[r], s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, r, G);
-        __syncthreads();
-        for (int g = threadIdx.x; g < G; g += blockDim.x) {
-            acc64[g] += (double)acc0[g];
-            acc0[g] = 0.f;
-            if (MODE == MODE_AGG_FWD) {
-                acc64[G + g] += (double)acc1[g];
-                acc1[g] = 0.f;
+            for (int u = 0; u < SA_UNROLL; u++) {
+                const long long i = beg + 4 * (q + u * SA_THREADS);
+                soft_row<MODE>(xx[u].x, aa[u].x, gg[u].x, aa[u].x, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i, G);
+                soft_row<MODE>(xx[u].y, aa[u].y, gg[u].y, aa[u].y, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 1, G);
+                soft_row<MODE>(xx[u].z, aa[u].z, gg[u].z, aa[u].z, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 2, G);
+                soft_row<MODE>(xx[u].w, aa[u].w, gg[u].w, aa[u].w, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 3, G);
             }
         }
-        __syncthreads();
+        for (; q < nvec; q += SA_THREADS) {
+            const long long i = beg + 4 * q;
+            float4 xx = __ldcs((const float4 *)(x + i));
+            float4 aa = __ldcs((const float4 *)(aux + i));
+            int4 gg = __ldcs((const int4 *)(gid + i));
+            soft_row<MODE>(xx.x, aa.x, gg.x, aa.x, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i, G);
+            soft_row<MODE>(xx.y, aa.y, gg.y, aa.y, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 1, G);
+            soft_row<MODE>(xx.z, aa.z, gg.z, aa.z, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 2, G);
+            soft_row<MODE>(xx.w, aa.w, gg.w, aa.w, s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, i + 3, G);
+        }
+        tail = beg + 4 * nvec;
     }
+    for (long long r = tail + threadIdx.x; r < end; r += SA_THREADS)
+        soft_row<MODE>(x[r], aux[r], gid[r], aux[r], s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, r, G);
+    __syncthreads();
     double *out = partial + (size_t)blockIdx.x * K * G;
     for (int g = threadIdx.x; g < K * G; g += blockDim.x)
-        out[g] = acc64[g];
+        out[g] = sm64[g];
 }
 
 // out[k][g] = scale * sum_b partial[b][k][g] in float64, in a fixed order:
@@ -325,7 +306,7 @@ extern "C" tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 2, 3);
+    SoftGrid sg = soft_grid(n, G, 2, 1);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_FWD>, sg.smem)) != TDP_OK)
         return st;
     double *partial = (double *)ws;
@@ -348,7 +329,7 @@ extern "C" tdp_status tdp_soft_agg_bwd(const float *x, const float *v, const int
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 1, 4);
+    SoftGrid sg = soft_grid(n, G, 1, 3);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_BWD>, sg.smem)) != TDP_OK)
         return st;
     double *partial = (double *)ws;
@@ -371,7 +352,7 @@ extern "C" tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, co
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 1, 2);
+    SoftGrid sg = soft_grid(n, G, 1, 1);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_FILTER_BWD>, sg.smem)) != TDP_OK)
         return st;
     double *partial = (double *)ws;
@@ -438,7 +419,7 @@ extern "C" tdp_status tdp_soft_agg_fwd_noalloc(const float *x, const float *v, c
     if ((st = noalloc_scratch(&partial)) != TDP_OK)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 2, 3);
+    SoftGrid sg = soft_grid(n, G, 2, 1);
     if (sg.blocks > NOALLOC_MAX_BLOCKS) {
         sg.blocks = NOALLOC_MAX_BLOCKS;
         sg.chunk = (n + sg.blocks - 1) / sg.blocks;

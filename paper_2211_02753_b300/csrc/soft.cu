@@ -3,11 +3,16 @@
 //
 // Rows stream through once per call with 16-byte loads (x, v: float4; gid:
 // int4).  Each block owns a contiguous chunk of rows and accumulates per-group
-// sums in shared memory with fp64 atomics (each row's term is formed in fp32
-// and added in fp64); the fp64 partials of all blocks are then added in block
-// order by a second small kernel.  (Upstream gradients of either sign make the
-// adjoint's group sums cancel; fp32 sub-sums, even of ~16 rows per group,
-// left the cancelling groups of the adjoint at the edge of the 1e-5 bound.)
+// sums in shared memory as compensated fp32 pairs (hi, lo): each row's term t
+// goes to hi by an fp32 atomic add, whose returned old value gives the exact
+// rounding error of old + t by TwoSum (Knuth), and that error goes to lo by a
+// second atomic.  hi + lo then carries the block's sum to about fp32^2
+// relative accuracy whatever the order of the atomics.  The per-block sums
+// are then added in fp64, in block order, by a second small kernel.
+// (Upstream gradients of either sign make the adjoint's group sums cancel;
+// plain fp32 sub-sums, even of ~16 rows per group, left the cancelling groups
+// of the adjoint at the edge of the 1e-5 bound, and fp64 shared-memory
+// atomics cost twice the time of the whole kernel.)
 // The mask m = sigmoid((x - theta[g]) / tau) is recomputed in the backward
 // pass, never stored; m(1-m) is evaluated as e/(1+e)^2 with e = exp(-|z|),
 // which has no cancellation when m is close to 1.  z = (x - theta) / tau is
@@ -54,30 +59,43 @@ __device__ __forceinline__ Sig sigmoid_xt(float x, float th, Tau tau)
 
 enum SoftMode { MODE_AGG_FWD = 0, MODE_AGG_BWD = 1, MODE_FILTER_BWD = 2 };
 
-// Per-row work of the three reduction modes.  Accumulates into the fp64
-// shared-memory accumulators acc0 (and acc1 for the forward COUNT).
+// acc[0][g] + acc[1][g] += t, compensated (see the header).  An fp32 atomic
+// add rounds to nearest, so the value it stores is the fp32 sum old + t, and
+// TwoSum recovers that sum's error exactly (no multiply, so nothing fuses).
+__device__ __forceinline__ void comp_add(float *hi, int G, int g, float t)
+{
+    const float old = atomicAdd(&hi[g], t);
+    const float sum = old + t;
+    const float bt = sum - old;
+    const float err = (old - (sum - bt)) + (t - bt);
+    atomicAdd(&hi[G + g], err);
+}
+
+// Per-row work of the three reduction modes.  Accumulates into the
+// compensated shared-memory pairs acc0 (and acc1 for the forward COUNT), each
+// laid out [hi: G][lo: G].
 template <int MODE>
 __device__ __forceinline__ void soft_row(float x, float v, int g, float gm, const float *s_theta, const float *s_g0,
-                                         const float *s_g1, Tau tau, double *acc0, double *acc1, float *gx,
+                                         const float *s_g1, Tau tau, float *acc0, float *acc1, float *gx,
                                          float *gv, long long i, int G)
 {
     if ((unsigned)g >= (unsigned)G) // out-of-range group id: row ignored
         return;
     Sig s = sigmoid_xt(x, s_theta[g], tau);
     if (MODE == MODE_AGG_FWD) {
-        atomicAdd(&acc0[g], (double)(v * s.m));
-        atomicAdd(&acc1[g], (double)s.m);
+        comp_add(acc0, G, g, v * s.m);
+        comp_add(acc1, G, g, s.m);
     } else if (MODE == MODE_AGG_BWD) {
         float gS = s_g0[g];
         float w = (gS * v + s_g1[g]) * s.dm;
-        atomicAdd(&acc0[g], (double)w);
+        comp_add(acc0, G, g, w);
         if (gx)
             gx[i] = w * tau.inv;
         if (gv)
             gv[i] = gS * s.m;
     } else {
         float w = gm * s.dm;
-        atomicAdd(&acc0[g], (double)w);
+        comp_add(acc0, G, g, w);
         if (gx)
             gx[i] = w * tau.inv;
     }
@@ -93,20 +111,20 @@ __global__ void __launch_bounds__(SA_THREADS, SA_BLOCKS_PER_SM) soft_reduce_kern
                                                                  long long n, int G, long long chunk,
                                                                  double *__restrict__ partial, float *gx, float *gv)
 {
-    // Shared memory: fp64 block accumulators [K][G], then theta (and, for the
-    // aggregation adjoint, the upstream gradients) in fp32.
+    // Shared memory: K compensated accumulators [K][hi, lo][G], then theta
+    // (and, for the aggregation adjoint, the upstream gradients).
     constexpr int K = MODE == MODE_AGG_FWD ? 2 : 1;
-    extern __shared__ double sm64[];
-    double *acc0 = sm64;                     // [G]
-    double *acc1 = sm64 + G;                 // [G], forward COUNT only
-    float *s_theta = (float *)(sm64 + K * G);
+    extern __shared__ float smf[];
+    float *acc0 = smf;                       // [2][G]
+    float *acc1 = smf + 2 * G;               // [2][G], forward COUNT only
+    float *s_theta = smf + 2 * K * G;
     float *s_g0 = s_theta + G;               // aggregation backward only
     float *s_g1 = s_theta + 2 * G;
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
         s_theta[g] = theta[g];
-        acc0[g] = 0.0;
+        acc0[g] = acc0[G + g] = 0.f;
         if (MODE == MODE_AGG_FWD)
-            acc1[g] = 0.0;
+            acc1[g] = acc1[G + g] = 0.f;
         if (MODE == MODE_AGG_BWD) {
             s_g0[g] = g0[g];
             s_g1[g] = g1[g];
@@ -158,8 +176,10 @@ __global__ void __launch_bounds__(SA_THREADS, SA_BLOCKS_PER_SM) soft_reduce_kern
         soft_row<MODE>(x[r], aux[r], gid[r], aux[r], s_theta, s_g0, s_g1, tau, acc0, acc1, gx, gv, r, G);
     __syncthreads();
     double *out = partial + (size_t)blockIdx.x * K * G;
-    for (int g = threadIdx.x; g < K * G; g += blockDim.x)
-        out[g] = sm64[g];
+    for (int e = threadIdx.x; e < K * G; e += blockDim.x) {
+        const int k = e / G, g = e - k * G;
+        out[e] = (double)smf[2 * k * G + g] + (double)smf[(2 * k + 1) * G + g];
+    }
 }
 
 // out[k][g] = scale * sum_b partial[b][k][g] in float64, in a fixed order:
@@ -238,11 +258,11 @@ struct SoftGrid {
     size_t smem;
 };
 
-// n64 fp64 arrays and n32 fp32 arrays of G entries in shared memory
-static SoftGrid soft_grid(long long n, int G, int n64, int n32)
+// n32 fp32 arrays of G entries in shared memory
+static SoftGrid soft_grid(long long n, int G, int n32)
 {
     SoftGrid sg;
-    sg.smem = (size_t)G * (n64 * sizeof(double) + n32 * sizeof(float));
+    sg.smem = (size_t)G * n32 * sizeof(float);
     // resident blocks per SM: registers allow SA_BLOCKS_PER_SM, shared memory as it allows
     int per_sm = (int)std::max<size_t>(1, std::min<size_t>(SA_BLOCKS_PER_SM, (200 * 1024) / std::max<size_t>(sg.smem, 1)));
     long long want = (n + 4ll * SA_THREADS * 8 - 1) / (4ll * SA_THREADS * 8);
@@ -306,7 +326,7 @@ extern "C" tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 2, 1);
+    SoftGrid sg = soft_grid(n, G, 5);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_FWD>, sg.smem)) != TDP_OK)
         return st;
     double *partial = (double *)ws;
@@ -329,7 +349,7 @@ extern "C" tdp_status tdp_soft_agg_bwd(const float *x, const float *v, const int
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 1, 3);
+    SoftGrid sg = soft_grid(n, G, 5);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_BWD>, sg.smem)) != TDP_OK)
         return st;
     double *partial = (double *)ws;
@@ -352,7 +372,7 @@ extern "C" tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, co
     if (!ws || ws_bytes < tdp_soft_workspace(n, G))
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 1, 1);
+    SoftGrid sg = soft_grid(n, G, 3);
     if ((st = set_smem((const void *)soft_reduce_kernel<MODE_FILTER_BWD>, sg.smem)) != TDP_OK)
         return st;
     double *partial = (double *)ws;
@@ -419,7 +439,7 @@ extern "C" tdp_status tdp_soft_agg_fwd_noalloc(const float *x, const float *v, c
     if ((st = noalloc_scratch(&partial)) != TDP_OK)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
-    SoftGrid sg = soft_grid(n, G, 2, 1);
+    SoftGrid sg = soft_grid(n, G, 5);
     if (sg.blocks > NOALLOC_MAX_BLOCKS) {
         sg.blocks = NOALLOC_MAX_BLOCKS;
         sg.chunk = (n + sg.blocks - 1) / sg.blocks;

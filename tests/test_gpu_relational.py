@@ -446,12 +446,13 @@ def test_join_duplicate_keys_and_full_table_are_flagged():
         ops.join_build([big], 0, nslots=63)
 
 
-def test_join_probe_agg_matches_join_then_groupby():
+@pytest.mark.parametrize("nslots", [None, 65536])  # default load <= 1/2; a dense table at load 0.76
+def test_join_probe_agg_matches_join_then_groupby(nslots):
     nb, npr = 50000, 400000
     d = gen.chain_tables(npr, nb, 5000, seed=9, n_category=1000)
     cols_b = [cu(d["build_pk"]), cu(d["third_cat"][:nb] if len(d["third_cat"]) >= nb else np.resize(d["third_cat"], nb))]
     cat = cols_b[1].cpu().numpy()
-    table, st = ops.join_build(cols_b, 0, payload_col=1)
+    table, st = ops.join_build(cols_b, 0, payload_col=1, nslots=nslots)
     pcols = [cu(d["probe_fk"].astype(np.int32)), cu(d["probe_payload"])]
     out = ops.join_probe_agg(table, pcols, 0, 0, 999, [("sum", 1), ("count",)], status=st)
     ops.check(st)

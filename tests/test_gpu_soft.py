@@ -29,7 +29,8 @@ def cu(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-@pytest.mark.parametrize("n,G", [(1, 1), (4099, 7), (100003, 1024), (10_000_000, 1024)])
+# empty input, one row, ragged tails, the maximum group count (4096), the 10M-row workload
+@pytest.mark.parametrize("n,G", [(0, 5), (1, 1), (4099, 7), (50001, 4096), (100003, 1024), (10_000_000, 1024)])
 def test_soft_agg_fwd_bwd(n, G):
     d = gen.soft_table(n, G, gen.BASE_SEED + 3)
     r = np.random.default_rng(n)

@@ -506,3 +506,30 @@ def test_relational_results_are_deterministic():
         ref = ref or got
         assert got == ref
     ops.check(p.status)
+
+
+def test_shipping_plan_graph_replay_matches_eager():
+    """The plan captured as a CUDA graph (the bench's timed step) gives the
+    eager plan's results, and a replay reads new data copied into the
+    plan's input tensors."""
+    from paper_2211_02753_b300 import plans
+    nf, nd = 2_000_000, 500_000
+    fact = {k: cu(v) for k, v in gen.fact_table(nf, nd, 5, cols=("key", "price", "disc", "date")).items()}
+    dim = {k: cu(v) for k, v in gen.dim_table(nd, 5, cols=("key", "segment")).items()}
+    p = plans.ShippingPriority(fact, dim)
+
+    def result(o):
+        g = int(o["ngroups"].item())
+        return (int(o["nmatch"].item()), np_(o["groups"]["keys"][0], g).tobytes(),
+                np_(o["groups"]["aggs"][0], g).tobytes(), np_(o["top_vals"]).tobytes(), np_(o["top_keys"]).tobytes())
+
+    ref = result(p.run())
+    step = plans.Graphed(p)
+    for _ in range(2):
+        assert result(step.run()) == ref
+    fact2 = gen.fact_table(nf, nd, 6, cols=("key", "price", "disc", "date"))
+    for k in fact:
+        fact[k].copy_(cu(fact2[k]))
+    got = result(step.run())
+    assert got != ref and got == result(p.run())
+    ops.check(p.status)

@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass1_kernel(const long long 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * TK_THREADS * TK_UNROLL;
     long long published = VK_WORST_V;
+    // the list's k-th entry, re-read only when an insert changed the list
+    long long tv = __shfl_sync(0xffffffffu, l.v, k - 1);
+    int tk = __shfl_sync(0xffffffffu, l.k, k - 1);
     for (long long base = ((long long)blockIdx.x * (TK_THREADS / 32) + warp) * 32 * TK_UNROLL; base < n;
          base += stride) {
         long long v[TK_UNROLL];
@@ -141,21 +144,20 @@ __global__ void __launch_bounds__(TK_THREADS) topk_pass1_kernel(const long long 
 #pragma unroll
         for (int u = 0; u < TK_UNROLL; u++) {
             const long long i = base + u * 32 + lane;
-            const long long tv = __shfl_sync(0xffffffffu, l.v, k - 1);
-            const int tk = __shfl_sync(0xffffffffu, l.k, k - 1);
             const bool maybe = i < n && v[u] >= gb && v[u] >= tv;
             const int kk = maybe ? __ldg(keys + i) : VK_WORST_K;
             const unsigned m = __ballot_sync(0xffffffffu, maybe && better(v[u], kk, tv, tk));
-            if (m)
+            if (m) {
                 wl_insert(l, m, v[u], kk, k);
+                tv = __shfl_sync(0xffffffffu, l.v, k - 1);
+                tk = __shfl_sync(0xffffffffu, l.k, k - 1);
+            }
         }
         // publish this warp's k-th best once its list is full and it has risen
-        const long long kth = __shfl_sync(0xffffffffu, l.v, k - 1);
-        const int kthk = __shfl_sync(0xffffffffu, l.k, k - 1);
-        if (kthk != VK_WORST_K && kth > published && kth > gb) {
+        if (tk != VK_WORST_K && tv > published && tv > gb) {
             if (lane == 0)
-                atomicMax(bound, enc_v(kth));
-            published = kth;
+                atomicMax(bound, enc_v(tv));
+            published = tv;
         }
     }
     block_merge(l, k, cand + (size_t)blockIdx.x * k);

@@ -557,11 +557,12 @@ def run_only(args):
     from oracle import cnn as O  # glyph targets: the exact query on true labels
     dev = torch.device("cuda", 0)
     sc = max(1, args.scale)
-    if args.only == "shipping":
+    if args.only in ("shipping", "shipping_sep"):
         f, d = (gen.fact_table(N_FACT // sc, N_DIM // sc, SEED2, cols=("key", "price", "disc", "date")),
                 gen.dim_table(N_DIM // sc, SEED2, cols=("key", "segment")))
         p = plans.ShippingPriority({k: torch.from_numpy(v).to(dev) for k, v in f.items()},
-                                   {k: torch.from_numpy(v).to(dev) for k, v in d.items()})
+                                   {k: torch.from_numpy(v).to(dev) for k, v in d.items()},
+                                   groupjoin=args.only == "shipping")
         fn = p.run
     elif args.only in ("pricing", "pricing_sort", "filter"):
         t = gen.fact_table(N_FACT // sc, N_DIM // sc, SEED2, cols=("flag", "status", "qty", "price", "disc", "date"))
@@ -606,7 +607,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plans", default="all", choices=["all", "main"])
     ap.add_argument("--only", default=None,
-                    choices=["shipping", "pricing", "pricing_sort", "filter", "chain", "soft", "glyph"],
+                    choices=["shipping", "shipping_sep", "pricing", "pricing_sort", "filter", "chain", "soft",
+                             "glyph"],
                     help="profiling mode: run one plan at 1/--scale size and print its time only")
     ap.add_argument("--scale", type=int, default=1)
     args = ap.parse_args()

@@ -125,12 +125,16 @@ const char *tdp_status_str(int32_t status);
 int32_t tdp_abi_version(void);
 
 /*
- * Upper bound, in polls, of every device-side wait (decoupled look-back of the
- * filter/scan/sort kernels).  A wait that runs out sets TDP_ERR_TIMEOUT and
- * the kernel carries on without hanging; once one wait of a launch has timed
- * out, the other waits of that launch give up at once.  Default 1<<20 (about
- * 0.2 s of polling).  Affects later
- * launches only.  Returns the previous value.
+ * Upper bound, in polls, of every device-side wait: the decoupled look-back
+ * of the probe, sort, reduce-by-key and finalize kernels, the filter's grid
+ * barrier, and the mbarrier waits on bulk / TMA copies and tensor-core
+ * commits.  A wait that runs out sets TDP_ERR_TIMEOUT and the kernel carries
+ * on without hanging; once one wait of a launch has timed out, the other
+ * waits of that launch give up at once.  Default 1<<20 (about 0.2 s of
+ * polling).  Affects later launches only.  Returns the previous value.
+ *
+ * This limit is the library's one piece of process-wide mutable state (an
+ * atomic read at every launch); every other setting is a call argument.
  */
 uint32_t tdp_set_spin_limit(uint32_t polls);
 
@@ -165,8 +169,13 @@ size_t tdp_filter_workspace(int64_t n);
  *                     receives cols[gather_cols[j]] at the qualifying rows,
  *                     same order and capacity as out_rowid
  *
- * Single pass: each tile computes its selected count with warp ballots,
- * publishes it, and finds its output offset by decoupled look-back.
+ * Two phases in one cooperative launch of persistent blocks, each owning a
+ * contiguous chunk of rows: (1) the chunk's predicate columns stream through
+ * shared-memory tiles filled by bulk copies and each row's result is kept as
+ * one bit in shared memory, and the block publishes its count; (2) after one
+ * bounded grid-wide barrier each block's output offset is the sum of the
+ * counts before it, and the block writes its row ids (and gathered columns)
+ * in order.  Tables larger than one round of chunks take several rounds.
  */
 tdp_status tdp_filter(const tdp_col *cols, int32_t ncols, const tdp_pred *preds, int32_t npreds,
                       int64_t n, const int64_t *d_n, int32_t *out_rowid, int64_t capacity, int64_t *d_count,
@@ -341,6 +350,51 @@ tdp_status tdp_join_probe_agg(const uint64_t *table, int64_t nslots, const tdp_c
                               int64_t *d_ngroups, void *ws, size_t ws_bytes, int32_t *d_status,
                               tdp_stream_t stream);
 
+/* Workspace bytes for tdp_groupjoin (0 when the arguments are invalid). */
+size_t tdp_groupjoin_workspace(int64_t n_build, int64_t key_lo, int64_t key_hi, int32_t naggs);
+
+/*
+ * Group-join whose group key is the join key (Sec. 2 relational operators;
+ * the shipping-priority shape "JOIN ... ON key GROUP BY key"):
+ *
+ *   SELECT key, aggs(probe columns)
+ *   FROM build JOIN probe ON build.key = probe.key
+ *   WHERE build_preds AND probe_preds GROUP BY key ORDER BY key
+ *
+ * Build keys must be unique (N:1) and lie in the metadata bounds
+ * [key_lo, key_hi] (key_hi - key_lo < 2^31): a repeated build key sets
+ * TDP_ERR_DUP_BUILD_KEY and a build key outside the bounds sets
+ * TDP_ERR_OVERFLOW (that row is dropped).  Probe keys outside the bounds
+ * match nothing.  The build key set becomes an order-preserving dense code
+ * (Sec. 2, Data Encoding): a bitmap of the key domain with a running rank
+ * per 32-key word, 8 bytes per 32 keys of the domain in the workspace.  The
+ * probe adds each matching row straight into the accumulators of its code,
+ * and the groups are read out in code order, which is key order.
+ *
+ *   build_cols / build_preds   build side (fused filter); rows 0..n_build-1,
+ *                              or 0..min(n_build, *d_nbuild)-1
+ *   probe_cols / probe_preds   probe side (fused filter); rows 0..n_probe-1,
+ *                              or 0..min(n_probe, *d_nprobe)-1
+ *   build_key_col, probe_key_col  int32 key columns
+ *   aggs[naggs]                1..8 aggregates over probe columns (COUNT,
+ *                              SUM, SUM(a*(k-b)), AVG, MIN, MAX), exact int64
+ *   out_keys (int32), out_aggs[naggs] (int64), capacity, d_ngroups
+ *                              groups in ascending key order, as
+ *                              tdp_groupby_agg writes them
+ *   d_nmatch                   optional device int64: the number of joined
+ *                              rows (the inner join's row count)
+ *
+ * Equal to tdp_join_build + tdp_join_probe + tdp_groupby_agg over the
+ * joined rows, bit for bit.
+ */
+tdp_status tdp_groupjoin(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pred *build_preds,
+                         int32_t nbuild_preds, int64_t n_build, const int64_t *d_nbuild, int32_t build_key_col,
+                         const tdp_col *probe_cols, int32_t nprobe_cols, const tdp_pred *probe_preds,
+                         int32_t nprobe_preds, int64_t n_probe, const int64_t *d_nprobe, int32_t probe_key_col,
+                         int64_t key_lo, int64_t key_hi, const tdp_agg *aggs, int32_t naggs, int32_t *out_keys,
+                         int64_t *const *out_aggs, int64_t capacity, int64_t *d_ngroups, int64_t *d_nmatch,
+                         void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
+
 /* ----------------------------------------------------------------- top-k */
 
 /* Workspace bytes for tdp_topk over n rows. */
@@ -387,10 +441,13 @@ tdp_status tdp_soft_filter_bwd(const float *x, const int32_t *gid, const float *
  * Soft grouped aggregation, Sec. 4 (soft_count / soft_groupby): with
  * m_i = sigmoid((x[i] - theta[gid[i]]) / tau),
  *   sum[g] = sum_{gid[i]=g} v[i] m_i ,   cnt[g] = sum_{gid[i]=g} m_i .
- * The mask is never stored.  Each block sums fp32 contributions over short
- * sub-chunks (about 16 rows per group) into float64 accumulators; block
- * partials are combined in block order in float64.  sum, cnt: fp32[n_groups],
- * overwritten.
+ * The mask is never stored.  Each block keeps, per group, a compensated
+ * fp32 pair (hi, lo) in shared memory: every term is added to hi by an
+ * atomic whose returned old value gives the exact rounding error of the
+ * addition (TwoSum), and that error is added to lo, so hi + lo carries the
+ * block's group sum to about fp32^2 whatever the order of the atomics.  The
+ * per-block sums are widened to float64 and combined in block order by a
+ * fixed tree.  sum, cnt: fp32[n_groups], overwritten.
  */
 tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int32_t *gid, const float *theta,
                             float tau, int64_t n, int32_t n_groups, float *sum, float *cnt, void *ws,
@@ -401,8 +458,13 @@ tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int32_t *gid, 
  * device memory: code where a cudaMalloc is not allowed or would synchronise
  * the device at a bad moment, or an embedding host that only passes in
  * buffers it registered up front.  The paper has no counterpart; this is a
- * deployment variant of the call above, with the same arguments minus ws and
- * the same results (same kernels, same summation order for a given grid).
+ * deployment variant of the call above, with the same arguments minus ws.
+ * It runs the same kernels.  Up to about 4.2M rows (256 blocks of the
+ * reduction) the grid, and so every summation order, equals that of
+ * tdp_soft_agg_fwd and the results are bitwise equal; above that the grid is
+ * capped at 256 blocks with longer chunks, the float64 combine adds
+ * different block sums, and the results agree with tdp_soft_agg_fwd within
+ * the soft operators' tolerance (1e-5 relative per group), not bitwise.
  *
  * Scratch: the per-block float64 partial sums live in one fixed 4 MiB array
  * in the library's device image (256 blocks x 2 sums x 1024 groups), which
@@ -411,7 +473,9 @@ tdp_status tdp_soft_agg_fwd(const float *x, const float *v, const int32_t *gid, 
  *     TDP_ERR_WORKSPACE_TOO_SMALL (use tdp_soft_agg_fwd then).
  *   - The first call on a device looks up the array's device address with
  *     that device current (one cudaGetSymbolAddress, no allocation); make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  The address is cached for
+ *     the life of the process: after a cudaDeviceReset of that device it is
+ *     stale, so do not call this entry point again in that process.
  *   - All calls share the one array: two calls whose kernels overlap on the
  *     GPU (different streams, or different threads) race and give wrong
  *     sums.  Serialise them.  Each call overwrites the parts it reads, so

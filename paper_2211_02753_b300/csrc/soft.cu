@@ -396,6 +396,9 @@ namespace tdp {
 
 constexpr int NOALLOC_MAX_GROUPS = 1024;
 constexpr int NOALLOC_MAX_BLOCKS = 256;
+// the forward's shared memory (5 floats per group) stays under the default
+// 48 KiB dynamic limit at the largest group count
+static_assert(NOALLOC_MAX_GROUPS * 5 * sizeof(float) <= 48 * 1024, "no-alloc shared memory");
 
 // 256 blocks x 2 sums x 1024 groups x 8 bytes = 4 MiB, resident on every GPU
 // that loads this library until the process exits.
@@ -445,6 +448,8 @@ extern "C" tdp_status tdp_soft_agg_fwd_noalloc(const float *x, const float *v, c
         sg.chunk = (n + sg.blocks - 1) / sg.blocks;
         sg.chunk = (sg.chunk + 3) / 4 * 4;
     }
+    if ((st = set_smem((const void *)soft_reduce_kernel<MODE_AGG_FWD>, sg.smem)) != TDP_OK)
+        return st;
     // every block used overwrites its own K x G partials before the combine
     // reads them, so nothing in the shared scratch has to start at zero
     soft_reduce_kernel<MODE_AGG_FWD><<<sg.blocks, SA_THREADS, sg.smem, s>>>(

@@ -292,6 +292,34 @@ def join_probe_agg(table, cols, key_col, lo, hi, aggs, preds=(), n=None, capacit
     return {"keys": kout, "aggs": aout, "ngroups": ng, "status": status}
 
 
+def groupjoin(build_cols, build_key, probe_cols, probe_key, lo, hi, aggs, build_preds=(), probe_preds=(),
+              n_build=None, d_nbuild=None, n_probe=None, d_nprobe=None, capacity=None, status=None):
+    """JOIN build, probe ON key GROUP BY key (build keys unique and bounded by
+    [lo, hi]) with aggregates over probe columns.  Returns dict(keys, aggs,
+    ngroups, nmatch, status) like groupby_agg; groups in ascending key order."""
+    bc = col_array(build_cols)
+    pc = col_array(probe_cols)
+    dev = _as_col(probe_cols[0]).t.device
+    nb = _as_col(build_cols[build_key]).t.numel() if n_build is None else int(n_build)
+    npr = _as_col(probe_cols[probe_key]).t.numel() if n_probe is None else int(n_probe)
+    D = int(hi) - int(lo) + 1
+    cap = min(D, max(nb, 0)) if capacity is None else int(capacity)
+    status = new_status(dev) if status is None else status
+    kout = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    aout = [torch.empty(max(cap, 1), dtype=torch.int64, device=dev) for _ in aggs]
+    ng = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
+    nm = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
+    ws_n = L.lib().tdp_groupjoin_workspace(nb, int(lo), int(hi), len(aggs))
+    if ws_n == 0:
+        raise TdpError(1, "tdp_groupjoin_workspace")
+    ws = workspace(ws_n, dev)
+    L.call("tdp_groupjoin", bc, len(build_cols), pred_array(build_preds), len(build_preds), nb, _ptr(d_nbuild),
+           int(build_key), pc, len(probe_cols), pred_array(probe_preds), len(probe_preds), npr, _ptr(d_nprobe),
+           int(probe_key), int(lo), int(hi), agg_array(aggs), len(aggs), _ptr(kout), _ptr_array(aout), cap,
+           _ptr(ng), _ptr(nm), _ptr(ws), ws.numel(), _ptr(status), _stream())
+    return {"keys": [kout], "aggs": aout, "ngroups": ng, "nmatch": nm, "status": status}
+
+
 # ---------------------------------------------------------------- top-k
 
 def topk(vals, keys, k, d_n=None, status=None):

@@ -9,9 +9,10 @@ nothing.
   PricingSummary  -- filter + group-by on the line-item table
                      (WHERE date <= 2460 GROUP BY flag, status: SUM qty,
                      SUM price, SUM price*(100-disc), COUNT, AVG qty)
-  ShippingPriority -- dimension filter (segment = 2) -> hash build; fact filter
-                     (date > 1200) fused into the probe with a gather of
-                     key/price/disc; GROUP BY key SUM(price*(100-disc)); top-10
+  ShippingPriority -- dimension filter (segment = 2), fact filter (date >
+                     1200), join on key, GROUP BY key SUM(price*(100-disc)),
+                     top-10: one group-join call (default), or hash build ->
+                     probe with a gather of key/price/disc -> group-by
   JoinChain       -- third (pk -> category) build; build rows probe it with
                      fk2 (category per build row); build (pk -> category);
                      probe rows probe it and aggregate SUM(payload), COUNT(*)
@@ -73,9 +74,17 @@ class Graphed:
 
 
 class ShippingPriority:
-    def __init__(self, fact: dict, dim: dict, dim_selectivity: float = 0.2, groupby_strategy: str = "auto"):
+    """groupjoin=True (the default): one group-join call (dimension filter,
+    fact filter, join and GROUP BY key in one pass over the fact rows, groups
+    read out in key order) and top-10.  groupjoin=False: the separate path,
+    hash build -> probe with gathers -> group-by (`groupby_strategy`) ->
+    top-10."""
+
+    def __init__(self, fact: dict, dim: dict, dim_selectivity: float = 0.2, groupby_strategy: str = "auto",
+                 groupjoin: bool = True):
         self.f = fact  # key, price, disc, date
         self.d = dim   # key, segment
+        self.groupjoin = groupjoin
         # the join key is bounded by the dimension's key range 1..n_dim: AUTO
         # takes the partition strategy ("sort" keeps the general sort)
         self.groupby_strategy = groupby_strategy
@@ -90,6 +99,8 @@ class ShippingPriority:
         self.status = ops.new_status(dev)
 
     def run(self):
+        if self.groupjoin:
+            return self.run_groupjoin()
         st = self.status
         ops.join_build([self.d["key"], self.d["segment"]], 0, preds=[(1, "==", 2)], nslots=self.nslots,
                        table=self.table, status=st)
@@ -103,6 +114,17 @@ class ShippingPriority:
                              capacity=self.cap, status=st)
         ov, okk, dk = ops.topk(gb["aggs"][0], gb["keys"][0], 10, d_n=gb["ngroups"], status=st)
         return {"top_vals": ov, "top_keys": okk, "k": dk, "ngroups": gb["ngroups"], "nmatch": pr["count"],
+                "groups": gb, "status": st}
+
+    def run_groupjoin(self):
+        st = self.status
+        # dimension keys are bounded by 1..n_dim (the dimension's key metadata)
+        gb = ops.groupjoin([self.d["key"], self.d["segment"]], 0,
+                           [self.f["key"], self.f["date"], self.f["price"], self.f["disc"]], 0, 1, self.n_dim,
+                           [("sum_mul_kminus", 2, 3, 100)], build_preds=[(1, "==", 2)],
+                           probe_preds=[(1, ">", 1200)], status=st)
+        ov, okk, dk = ops.topk(gb["aggs"][0], gb["keys"][0], 10, d_n=gb["ngroups"], status=st)
+        return {"top_vals": ov, "top_keys": okk, "k": dk, "ngroups": gb["ngroups"], "nmatch": gb["nmatch"],
                 "groups": gb, "status": st}
 
 

@@ -32,7 +32,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 def test_host_only_calls():
     L = _lib.lib()
-    assert L.tdp_abi_version() == 101
+    assert L.tdp_abi_version() == 102
     assert L.tdp_status_str(4) == b"capacity exceeded"
     assert L.tdp_filter_workspace(0) >= 0
     assert L.tdp_join_default_slots(3_000_000) == 1 << 23
@@ -53,4 +53,10 @@ def test_host_argument_errors_without_launch():
     assert st == 1
     # soft op with tau <= 0
     st = L.tdp_soft_filter_fwd(None, None, None, 0.0, 0, None, None)
+    assert st == 1
+    # group-join: an empty key range, and its workspace query
+    assert L.tdp_groupjoin_workspace(10, 5, 4, 1) == 0
+    assert L.tdp_groupjoin_workspace(10, 1, 15_000_000, 1) > 15_000_000 // 32 * 8
+    st = L.tdp_groupjoin(None, 0, None, 0, 0, None, 0, None, 0, None, 0, 0, None, 0, 5, 4, None, 0, None, None, 0,
+                         None, None, None, 0, None, None)
     assert st == 1

@@ -533,3 +533,107 @@ def test_shipping_plan_graph_replay_matches_eager():
     got = result(step.run())
     assert got != ref and got == result(p.run())
     ops.check(p.status)
+
+
+# ------------------------------------------------------------ group-join
+
+def _groupjoin_case(nb, npr, seed, lo, hi, key_span=None):
+    r = np.random.default_rng(seed)
+    span = hi - lo + 1
+    bkey = (lo + r.permutation(span)[:nb]).astype(np.int32)
+    bseg = r.integers(0, 5, nb).astype(np.int8)
+    ks = key_span or (lo - 3, hi + 3)
+    pkey = r.integers(ks[0], ks[1] + 1, npr).astype(np.int32)  # some keys outside the bounds
+    pdate = r.integers(0, 2557, npr).astype(np.int32)
+    pflag = r.integers(0, 3, npr).astype(np.int8)
+    pv = r.integers(-10**9, 10**9, npr).astype(np.int64)
+    pw = r.integers(0, 11, npr).astype(np.int64)
+    p32 = r.integers(-1000, 1000, npr).astype(np.int32)
+    return bkey, bseg, pkey, pdate, pflag, pv, pw, p32
+
+
+GJ_AGGS = [("sum_mul_kminus", 4, 5, 100), ("count",), ("sum", 6), ("min", 4), ("max", 6), ("avg", 4)]
+
+
+def _groupjoin_oracle(bkey, bseg, pkey, pdate, pflag, pv, pw, p32, nb, npr):
+    bsel = R.filter([(bseg, "==", 2)], nb)
+    psel = R.filter([(pdate, ">", 1200), (pflag, "!=", 1)], npr)
+    prow, _, dup = R.join(bkey, pkey, bsel=bsel, psel=psel)
+    assert not dup
+    keys, aggs = R.groupby([pkey], [("sum_mul_kminus", pv, pw, 100), ("count", None, None, None),
+                                    ("sum", p32, None, None), ("min", pv, None, None), ("max", p32, None, None),
+                                    ("avg", pv, None, None)], npr, sel=prow)
+    return len(prow), keys[:, 0], aggs
+
+
+@pytest.mark.parametrize("nb,npr,lo,hi", [(0, 1000, 1, 100), (1, 1, 5, 5), (700, 0, -300, 1000),
+                                          (5000, 70001, 1, 20000), (300000, 1_000_003, -1_500_000, 1_500_000),
+                                          (32, 4097, 0, 31), (33, 4095, 7, 40)])
+def test_groupjoin_matches_join_then_groupby(nb, npr, lo, hi):
+    """JOIN ... GROUP BY key over the rank-coded build side equals the
+    oracle's join followed by its group-by, for every aggregate, including
+    empty sides, a one-key domain, a domain of exactly one bitmap word and
+    ragged tiles of the probe."""
+    bkey, bseg, pkey, pdate, pflag, pv, pw, p32 = _groupjoin_case(nb, npr, nb + npr, lo, hi)
+    bcols = [cu(bkey), cu(bseg)]
+    pcols = [cu(pkey), cu(pdate), cu(pflag), cu(pkey), cu(pv), cu(pw), cu(p32)]
+    out = ops.groupjoin(bcols, 0, pcols, 0, lo, hi, GJ_AGGS, build_preds=[(1, "==", 2)],
+                        probe_preds=[(1, ">", 1200), (2, "!=", 1)])
+    ops.check(out["status"])
+    nm, ek, ea = _groupjoin_oracle(bkey, bseg, pkey, pdate, pflag, pv, pw, p32, nb, npr)
+    g = int(out["ngroups"].item())
+    assert int(out["nmatch"].item()) == nm
+    assert g == len(ek)
+    assert np.array_equal(np_(out["keys"][0], g), ek)
+    for j in range(len(GJ_AGGS)):
+        assert np.array_equal(np_(out["aggs"][j], g), ea[:, j]), GJ_AGGS[j]
+
+
+def test_groupjoin_unaligned_columns_counts_and_capacity():
+    """Probe columns that do not start on a 16-byte boundary take the plain
+    load path; d_n limits of both sides; an undersized output keeps the true
+    group count and flags capacity."""
+    nb, npr, lo, hi = 40000, 300001, 1, 60000
+    bkey, bseg, pkey, pdate, pflag, pv, pw, p32 = _groupjoin_case(nb, npr + 1, 77, lo, hi)
+    kdev = cu(pkey)[1:]  # 4-byte offset
+    ddev = cu(pdate)[1:]
+    pcols = [kdev, ddev, cu(pflag)[1:], kdev, cu(pv)[1:], cu(pw)[1:], cu(p32)[1:]]
+    bcols = [cu(bkey), cu(bseg)]
+    nb_lim, np_lim = 25000, 200000
+    dnb = torch.tensor([nb_lim], dtype=torch.int64, device=DEV)
+    dnp = torch.tensor([np_lim], dtype=torch.int64, device=DEV)
+    out = ops.groupjoin(bcols, 0, pcols, 0, lo, hi, GJ_AGGS, build_preds=[(1, "==", 2)],
+                        probe_preds=[(1, ">", 1200), (2, "!=", 1)], d_nbuild=dnb, d_nprobe=dnp)
+    ops.check(out["status"])
+    sl = slice(1, 1 + np_lim)
+    nm, ek, ea = _groupjoin_oracle(bkey[:nb_lim], bseg[:nb_lim], pkey[sl], pdate[sl], pflag[sl], pv[sl], pw[sl],
+                                   p32[sl], nb_lim, np_lim)
+    g = int(out["ngroups"].item())
+    assert int(out["nmatch"].item()) == nm and g == len(ek)
+    assert np.array_equal(np_(out["keys"][0], g), ek)
+    for j in range(len(GJ_AGGS)):
+        assert np.array_equal(np_(out["aggs"][j], g), ea[:, j])
+    cap = g // 2
+    small = ops.groupjoin(bcols, 0, pcols, 0, lo, hi, GJ_AGGS, build_preds=[(1, "==", 2)],
+                          probe_preds=[(1, ">", 1200), (2, "!=", 1)], d_nbuild=dnb, d_nprobe=dnp, capacity=cap)
+    assert int(small["status"].item()) == 4
+    assert int(small["ngroups"].item()) == g
+    assert np.array_equal(np_(small["keys"][0], cap), ek[:cap])
+    assert np.array_equal(np_(small["aggs"][0], cap), ea[:cap, 0])
+
+
+def test_groupjoin_flags_duplicate_and_out_of_bounds_build_keys():
+    bkey = cu(np.array([5, 7, 5, 9], np.int32))
+    pk = cu(np.array([5, 7, 9, 11], np.int32))
+    pv = cu(np.array([1, 2, 3, 4], np.int64))
+    out = ops.groupjoin([bkey], 0, [pk, pv], 0, 0, 20, [("sum", 1)])
+    assert int(out["status"].item()) & 8
+    bkey2 = cu(np.array([5, 70, 9], np.int32))  # 70 is outside [0, 20]
+    out2 = ops.groupjoin([bkey2], 0, [pk, pv], 0, 0, 20, [("sum", 1)])
+    assert int(out2["status"].item()) == 32
+    g = int(out2["ngroups"].item())
+    assert g == 2
+    assert np_(out2["keys"][0], g).tolist() == [5, 9]
+    assert np_(out2["aggs"][0], g).tolist() == [1, 3]
+    with pytest.raises(TdpError):
+        ops.groupjoin([bkey], 0, [pk, pv], 0, 20, 0, [("sum", 1)])

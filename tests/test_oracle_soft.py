@@ -110,6 +110,23 @@ def test_filter_bwd_vs_finite_differences():
         e[g] = h
         fd = (L(theta.astype(np.float64) + e) - L(theta.astype(np.float64) - e)) / (2 * h)
         assert abs(fd - dth[g]) <= 1e-7 * max(1.0, abs(dth[g]))
+    # dx: central differences of the same loss in every row's x (the loss is a
+    # sum over rows, so one perturbation per row moves only that row's term)
+    x64 = x.astype(np.float64)
+
+    def Lx(xx):
+        return float(gm @ soft.soft_filter_fwd(xx, gid, theta, TAU))
+
+    assert dx.shape == x.shape
+    for i in range(0, 400, 7):
+        e = np.zeros(400)
+        e[i] = h
+        fd = (Lx(x64 + e) - Lx(x64 - e)) / (2 * h)
+        assert abs(fd - dx[i]) <= 1e-6 * max(1.0, abs(dx[i]))
+    # sign and scale of the adjoint: at x = theta the mask slope is 1/(4 tau)
+    xm = theta[gid].astype(np.float32)
+    _, dxm = soft.soft_filter_bwd(xm, gid, theta, TAU, G, np.ones(400))
+    assert np.allclose(dxm, 0.25 / TAU, rtol=1e-12)
 
 
 def test_onehot_pe_count_is_exact():

@@ -1,9 +1,14 @@
 """tdp_soft_agg_fwd_noalloc: the soft aggregation forward for callers that
 cannot allocate device memory (its scratch is a fixed array inside the
 library).  Checked through the C ABI against tdp_soft_agg_fwd, the entry
-point with a caller workspace, on two calls in a row (the second call must
-not see anything left behind by the first), with the tolerance the soft
-tests use: |a - b| <= 1e-5 * max(|b|, 1e-3 * max|b|).
+point with a caller workspace, and against the float64 oracle, on calls in a
+row (a later call must not see anything left behind by an earlier one), with
+the tolerance the soft tests use: |a - b| <= 1e-5 * max(|b|, 1e-3 * max|b|).
+
+The first call has 10M rows, more than the 256 blocks of the fixed scratch
+hold at the normal grid (about 4.2M rows), so it takes the capped grid with
+longer chunks; the calls after it are smaller and fill fewer blocks of the
+array than the first one left behind.
 
 This file is named so that pytest collects it last.
 """
@@ -14,6 +19,7 @@ import pytest
 import torch
 
 import gen
+from oracle import soft as O
 from paper_2211_02753_b300 import _lib as L
 
 pytestmark = pytest.mark.gpu
@@ -61,12 +67,16 @@ def test_no_alloc_matches_workspace_entry_point_twice():
     G = 1024
     S = torch.empty(G, dtype=torch.float32, device=DEV)
     Cn = torch.empty(G, dtype=torch.float32, device=DEV)
-    # two calls in a row on different inputs and sizes, the same outputs
-    for n, seed in ((3_000_001, 11), (777_777, 12)):
+    # calls in a row on different inputs and sizes: the capped grid first,
+    # then the normal grid with fewer blocks, then the capped grid again
+    for n, seed in ((10_000_000, 10), (3_000_001, 11), (777_777, 12), (4_500_000, 14)):
         x, v, gid, th = _inputs(n, G, seed)
         rS, rC = _with_workspace(x, v, gid, th, G)
         assert _no_alloc(x, v, gid, th, G, S, Cn) == 0
-        assert _close(S.cpu().numpy(), rS) and _close(Cn.cpu().numpy(), rC)
+        gS, gC = S.cpu().numpy(), Cn.cpu().numpy()
+        assert _close(gS, rS) and _close(gC, rC)
+        oS, oC = O.soft_agg_fwd(x.cpu().numpy(), v.cpu().numpy(), gid.cpu().numpy(), th.cpu().numpy(), TAU, G)
+        assert _close(gS, oS) and _close(gC, oC)
 
 
 def test_no_alloc_rejects_too_many_groups():

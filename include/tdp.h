@@ -351,7 +351,7 @@ tdp_status tdp_join_probe_agg(const uint64_t *table, int64_t nslots, const tdp_c
                               tdp_stream_t stream);
 
 /* Workspace bytes for tdp_groupjoin (0 when the arguments are invalid). */
-size_t tdp_groupjoin_workspace(int64_t n_build, int64_t key_lo, int64_t key_hi, int32_t naggs);
+size_t tdp_groupjoin_workspace(int64_t n_build, int64_t key_lo, int64_t key_hi, int32_t naggs, int32_t topk);
 
 /*
  * Group-join whose group key is the join key (Sec. 2 relational operators;
@@ -362,7 +362,8 @@ size_t tdp_groupjoin_workspace(int64_t n_build, int64_t key_lo, int64_t key_hi, 
  *   WHERE build_preds AND probe_preds GROUP BY key ORDER BY key
  *
  * Build keys must be unique (N:1) and lie in the metadata bounds
- * [key_lo, key_hi] (key_hi - key_lo < 2^31): a repeated build key sets
+ * [key_lo, key_hi] (int32 values, key_hi - key_lo < 2^31): a repeated build
+ * key sets
  * TDP_ERR_DUP_BUILD_KEY and a build key outside the bounds sets
  * TDP_ERR_OVERFLOW (that row is dropped).  Probe keys outside the bounds
  * match nothing.  The build key set becomes an order-preserving dense code
@@ -383,9 +384,15 @@ size_t tdp_groupjoin_workspace(int64_t n_build, int64_t key_lo, int64_t key_hi, 
  *                              tdp_groupby_agg writes them
  *   d_nmatch                   optional device int64: the number of joined
  *                              rows (the inner join's row count)
+ *   topk, topk_agg             optional fused ORDER BY aggs[topk_agg] DESC,
+ *                              key ASC LIMIT topk (1..16; 0: none) over the
+ *                              groups: min(topk, groups) results go to
+ *                              out_top_vals / out_top_keys and their count
+ *                              to *d_topk (as tdp_topk writes them); the
+ *                              groups must fit `capacity`
  *
  * Equal to tdp_join_build + tdp_join_probe + tdp_groupby_agg over the
- * joined rows, bit for bit.
+ * joined rows (and tdp_topk over the groups), bit for bit.
  */
 tdp_status tdp_groupjoin(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pred *build_preds,
                          int32_t nbuild_preds, int64_t n_build, const int64_t *d_nbuild, int32_t build_key_col,
@@ -393,7 +400,8 @@ tdp_status tdp_groupjoin(const tdp_col *build_cols, int32_t nbuild_cols, const t
                          int32_t nprobe_preds, int64_t n_probe, const int64_t *d_nprobe, int32_t probe_key_col,
                          int64_t key_lo, int64_t key_hi, const tdp_agg *aggs, int32_t naggs, int32_t *out_keys,
                          int64_t *const *out_aggs, int64_t capacity, int64_t *d_ngroups, int64_t *d_nmatch,
-                         void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
+                         int32_t topk, int32_t topk_agg, int64_t *out_top_vals, int32_t *out_top_keys,
+                         int64_t *d_topk, void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
 
 /* ----------------------------------------------------------------- top-k */
 

@@ -80,9 +80,9 @@ SIGNATURES = {
     "tdp_join_probe_agg_workspace": (_sz, [_i64, _i64, _i32]),
     "tdp_join_probe_agg": (_st, [_p, _i64, _p, _i32, _p, _i32, _i64, _p, _i32, _i64, _i64, _p, _i32, _p, _p,
                                  _i64, _p, _p, _sz, _p, _p]),
-    "tdp_groupjoin_workspace": (_sz, [_i64, _i64, _i64, _i32]),
+    "tdp_groupjoin_workspace": (_sz, [_i64, _i64, _i64, _i32, _i32]),
     "tdp_groupjoin": (_st, [_p, _i32, _p, _i32, _i64, _p, _i32, _p, _i32, _p, _i32, _i64, _p, _i32, _i64, _i64,
-                            _p, _i32, _p, _p, _i64, _p, _p, _p, _sz, _p, _p]),
+                            _p, _i32, _p, _p, _i64, _p, _p, _i32, _i32, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_topk_workspace": (_sz, [_i64, _i32]),
     "tdp_topk": (_st, [_p, _p, _i64, _p, _i32, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_soft_workspace": (_sz, [_i64, _i32]),

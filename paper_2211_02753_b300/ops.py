@@ -293,10 +293,13 @@ def join_probe_agg(table, cols, key_col, lo, hi, aggs, preds=(), n=None, capacit
 
 
 def groupjoin(build_cols, build_key, probe_cols, probe_key, lo, hi, aggs, build_preds=(), probe_preds=(),
-              n_build=None, d_nbuild=None, n_probe=None, d_nprobe=None, capacity=None, status=None):
+              n_build=None, d_nbuild=None, n_probe=None, d_nprobe=None, capacity=None, status=None, topk=0,
+              topk_agg=0):
     """JOIN build, probe ON key GROUP BY key (build keys unique and bounded by
     [lo, hi]) with aggregates over probe columns.  Returns dict(keys, aggs,
-    ngroups, nmatch, status) like groupby_agg; groups in ascending key order."""
+    ngroups, nmatch, status) like groupby_agg; groups in ascending key order.
+    topk > 0 adds the fused top-k by aggs[topk_agg] (value desc, key asc):
+    top_vals, top_keys, k."""
     bc = col_array(build_cols)
     pc = col_array(probe_cols)
     dev = _as_col(probe_cols[0]).t.device
@@ -309,15 +312,23 @@ def groupjoin(build_cols, build_key, probe_cols, probe_key, lo, hi, aggs, build_
     aout = [torch.empty(max(cap, 1), dtype=torch.int64, device=dev) for _ in aggs]
     ng = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
     nm = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
-    ws_n = L.lib().tdp_groupjoin_workspace(nb, int(lo), int(hi), len(aggs))
+    topk = int(topk)
+    tv = torch.empty(max(topk, 1), dtype=torch.int64, device=dev) if topk else None
+    tk = torch.empty(max(topk, 1), dtype=torch.int32, device=dev) if topk else None
+    dk = torch.empty(1, dtype=torch.int64, device=dev) if topk else None
+    ws_n = L.lib().tdp_groupjoin_workspace(nb, int(lo), int(hi), len(aggs), topk)
     if ws_n == 0:
         raise TdpError(1, "tdp_groupjoin_workspace")
     ws = workspace(ws_n, dev)
     L.call("tdp_groupjoin", bc, len(build_cols), pred_array(build_preds), len(build_preds), nb, _ptr(d_nbuild),
            int(build_key), pc, len(probe_cols), pred_array(probe_preds), len(probe_preds), npr, _ptr(d_nprobe),
            int(probe_key), int(lo), int(hi), agg_array(aggs), len(aggs), _ptr(kout), _ptr_array(aout), cap,
-           _ptr(ng), _ptr(nm), _ptr(ws), ws.numel(), _ptr(status), _stream())
-    return {"keys": [kout], "aggs": aout, "ngroups": ng, "nmatch": nm, "status": status}
+           _ptr(ng), _ptr(nm), topk, int(topk_agg), _ptr(tv), _ptr(tk), _ptr(dk), _ptr(ws), ws.numel(), _ptr(status),
+           _stream())
+    out = {"keys": [kout], "aggs": aout, "ngroups": ng, "nmatch": nm, "status": status}
+    if topk:
+        out.update({"top_vals": tv, "top_keys": tk, "k": dk})
+    return out
 
 
 # ---------------------------------------------------------------- top-k

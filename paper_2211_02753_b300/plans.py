@@ -122,10 +122,9 @@ class ShippingPriority:
         gb = ops.groupjoin([self.d["key"], self.d["segment"]], 0,
                            [self.f["key"], self.f["date"], self.f["price"], self.f["disc"]], 0, 1, self.n_dim,
                            [("sum_mul_kminus", 2, 3, 100)], build_preds=[(1, "==", 2)],
-                           probe_preds=[(1, ">", 1200)], status=st)
-        ov, okk, dk = ops.topk(gb["aggs"][0], gb["keys"][0], 10, d_n=gb["ngroups"], status=st)
-        return {"top_vals": ov, "top_keys": okk, "k": dk, "ngroups": gb["ngroups"], "nmatch": gb["nmatch"],
-                "groups": gb, "status": st}
+                           probe_preds=[(1, ">", 1200)], status=st, topk=10, topk_agg=0)
+        return {"top_vals": gb["top_vals"], "top_keys": gb["top_keys"], "k": gb["k"], "ngroups": gb["ngroups"],
+                "nmatch": gb["nmatch"], "groups": gb, "status": st}
 
 
 class JoinChain:

@@ -55,8 +55,9 @@ def test_host_argument_errors_without_launch():
     st = L.tdp_soft_filter_fwd(None, None, None, 0.0, 0, None, None)
     assert st == 1
     # group-join: an empty key range, and its workspace query
-    assert L.tdp_groupjoin_workspace(10, 5, 4, 1) == 0
-    assert L.tdp_groupjoin_workspace(10, 1, 15_000_000, 1) > 15_000_000 // 32 * 8
+    assert L.tdp_groupjoin_workspace(10, 5, 4, 1, 0) == 0
+    assert L.tdp_groupjoin_workspace(10, 1, 15_000_000, 1, 0) > 15_000_000 // 32 * 12
+    assert L.tdp_groupjoin_workspace(10, 1, 100, 1, 17) == 0  # top-k of at most 16
     st = L.tdp_groupjoin(None, 0, None, 0, 0, None, 0, None, 0, None, 0, 0, None, 0, 5, 4, None, 0, None, None, 0,
-                         None, None, None, 0, None, None)
+                         None, None, 0, 0, None, None, None, None, 0, None, None)
     assert st == 1

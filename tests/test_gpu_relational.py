@@ -637,3 +637,85 @@ def test_groupjoin_flags_duplicate_and_out_of_bounds_build_keys():
     assert np_(out2["aggs"][0], g).tolist() == [1, 3]
     with pytest.raises(TdpError):
         ops.groupjoin([bkey], 0, [pk, pv], 0, 20, 0, [("sum", 1)])
+
+
+@pytest.mark.parametrize("nb", [1, 15, 16, 17, 100_003])
+def test_groupjoin_build_predicates_every_column_type(nb):
+    """Build-side filters on uint8, int8, int32 and int64 columns (the 16-row
+    vector path and the ragged tail) select the same build keys as the
+    oracle's filter."""
+    r = np.random.default_rng(nb)
+    lo, hi = -50, 3 * nb + 50
+    bkey = (lo + r.permutation(hi - lo + 1)[:nb]).astype(np.int32)
+    u8 = r.integers(0, 256, nb).astype(np.uint8)
+    i8 = r.integers(-128, 128, nb).astype(np.int8)
+    i32 = r.integers(-1000, 1000, nb).astype(np.int32)
+    i64 = r.integers(-10**12, 10**12, nb).astype(np.int64)
+    npr = 4 * nb + 7
+    pkey = r.integers(lo - 5, hi + 5, npr).astype(np.int32)
+    pv = r.integers(0, 10**6, npr).astype(np.int64)
+    preds = [(1, "<", 200), (2, "!=", -3), (3, ">=", -700), (4, "<=", 5 * 10**11)]
+    out = ops.groupjoin([cu(bkey), cu(u8), cu(i8), cu(i32), cu(i64)], 0, [cu(pkey), cu(pv)], 0, lo, hi,
+                        [("sum", 1), ("count",)], build_preds=preds)
+    ops.check(out["status"])
+    cols = [bkey, u8, i8, i32, i64]
+    bsel = R.filter([(cols[c], op, lit) for c, op, lit in preds], nb)
+    prow, _, _ = R.join(bkey, pkey, bsel=bsel)
+    keys, aggs = R.groupby([pkey], [("sum", pv, None, None), ("count", None, None, None)], npr, sel=prow)
+    g = int(out["ngroups"].item())
+    assert g == len(keys) and int(out["nmatch"].item()) == len(prow)
+    assert np.array_equal(np_(out["keys"][0], g), keys[:, 0])
+    assert np.array_equal(np_(out["aggs"][0], g), aggs[:, 0])
+    assert np.array_equal(np_(out["aggs"][1], g), aggs[:, 1])
+
+
+@pytest.mark.parametrize("k", [1, 10, 16])
+def test_groupjoin_fused_topk_matches_oracle_topk(k):
+    """The fused ORDER BY ... LIMIT k over the groups (ties broken by key)
+    equals the oracle's top-k of the oracle's groups; few groups (fewer than
+    k) and heavy ties included."""
+    for nb, npr, span in ((5, 40, 3), (20000, 300000, 50), (200000, 2_000_000, 10**6)):
+        r = np.random.default_rng(nb + k)
+        bkey = (1 + r.permutation(4 * nb)[:nb]).astype(np.int32)
+        pkey = r.integers(1, 4 * nb + 1, npr).astype(np.int32)
+        pv = r.integers(0, span, npr).astype(np.int64)  # small spans: many equal sums
+        out = ops.groupjoin([cu(bkey)], 0, [cu(pkey), cu(pv)], 0, 1, 4 * nb, [("sum", 1)], topk=k, topk_agg=0)
+        ops.check(out["status"])
+        prow, _, _ = R.join(bkey, pkey)
+        keys, aggs = R.groupby([pkey], [("sum", pv, None, None)], npr, sel=prow)
+        ev, ek = R.topk(aggs[:, 0], keys[:, 0], k)
+        m = int(out["k"].item())
+        assert m == len(ev)
+        assert np.array_equal(np_(out["top_vals"], m), ev)
+        assert np.array_equal(np_(out["top_keys"], m), ek)
+
+
+def test_groupjoin_widest_key_domain():
+    """A key domain of 2^31 values (the largest the call takes): the bitmap
+    has more words than the resident blocks cover at once, so the rank and
+    finalize passes take several spans per block; keys at both ends of the
+    domain and probe keys outside it."""
+    lo, hi = -(1 << 30), (1 << 30) - 1
+    r = np.random.default_rng(2031)
+    nb, npr = 100_000, 1_000_000
+    bkey = np.unique(r.integers(lo, hi + 1, nb + 1000, dtype=np.int64))[:nb]
+    bkey[0], bkey[-1] = lo, hi
+    r.shuffle(bkey)
+    bkey = bkey.astype(np.int32)
+    pkey = np.concatenate([r.choice(bkey, npr // 2), r.integers(np.iinfo(np.int32).min, np.iinfo(np.int32).max,
+                                                                  npr // 2, dtype=np.int64)]).astype(np.int32)
+    pkey[:3] = [lo, hi, lo - 1]
+    pv = r.integers(-10**9, 10**9, npr).astype(np.int64)
+    out = ops.groupjoin([cu(bkey)], 0, [cu(pkey), cu(pv)], 0, lo, hi, [("sum", 1), ("count",), ("max", 1)],
+                        topk=5, topk_agg=0)
+    ops.check(out["status"])
+    prow, _, _ = R.join(bkey, pkey)
+    keys, aggs = R.groupby([pkey], [("sum", pv, None, None), ("count", None, None, None), ("max", pv, None, None)],
+                           npr, sel=prow)
+    g = int(out["ngroups"].item())
+    assert g == len(keys) and int(out["nmatch"].item()) == len(prow)
+    assert np.array_equal(np_(out["keys"][0], g), keys[:, 0])
+    for j in range(3):
+        assert np.array_equal(np_(out["aggs"][j], g), aggs[:, j])
+    ev, ek = R.topk(aggs[:, 0], keys[:, 0], 5)
+    assert np.array_equal(np_(out["top_vals"], 5), ev) and np.array_equal(np_(out["top_keys"], 5), ek)

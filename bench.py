@@ -2,15 +2,19 @@
 """Benchmark of the Tensor Data Platform hot path on one B300 (or N replicas).
 
 Headline step: the shipping-priority query plan on a 60M-row fact table and a
-15M-row dimension table (dimension filter -> hash build; fact filter fused
-into the probe with a gather; sort-based GROUP BY key of
-SUM(price*(100-disc)); top-10), all on synthetic seeded data.  value = fact
-rows per second over the whole job.
+15M-row dimension table -- dimension WHERE segment = 2, fact WHERE date >
+1200, inner join on key, GROUP BY key SUM(price*(100-disc)), top-10 -- run as
+one group-join (build: rank code of the dimension keys; probe: fact rows
+accumulate into their group; finish: groups in key order and the top-10), on
+synthetic seeded data.  value = fact rows per second over the whole job.
 
-The same run also times, on their own inputs: the pricing-summary plan
-(filter + small-domain group-by over 60M rows), the three-table join chain
-(100M probe rows, fused probe + group-by), the soft query forward+backward
-(10M rows) and, when built, the glyph-CNN trainable-query training step.
+The same run also measures, on their own inputs and each with a `roofline`
+object and a `cpu_baseline` (the oracle on the host cores, single-threaded
+and OpenMP row-partitioned): the standalone filter; the pricing summary
+(small-domain and onesweep sort group-by); the shipping plan on the separate
+build -> probe -> group-by path (partition and sort group-by); the
+three-table join chain (fused probe + group-by, and probe -> sort group-by);
+the soft query forward/backward kernels; the glyph-CNN trainable query.
 
 Flags: --gpus N --steps K --warmup W [--impl reference] [--plans all|main]
 """
@@ -43,8 +47,15 @@ def load_peaks():
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return d.get("hbm_gbs", 6400.0), "measured"
-    return 6400.0, "fallback"
+        return d.get("hbm_gbs", 6400.0), d.get("bf16_tflops_sustained", 1400.0), "measured"
+    return 6400.0, 1400.0, "fallback"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
 
 
 def shipping_inputs():
@@ -53,35 +64,132 @@ def shipping_inputs():
     return fact, dim
 
 
-# --------------------------------------------------------------- reference
+# --------------------------------------------------------------- CPU oracle
 
-def cpu_shipping_sample(scale: int):
-    """The oracle (plain C, single thread) on a 1/scale sample of the
-    shipping-priority workload (same generator, key range scaled with it).
-    Returns (fact rows, seconds)."""
+def _timed(fn):
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
+
+
+def cpu_shipping_sample(scale: int, parallel: bool):
+    """The oracle on a 1/scale sample of the shipping-priority workload (same
+    generator, key range scaled with it).  Returns (fact rows, seconds)."""
     from oracle import relational as R
     nf, nd = N_FACT // scale, N_DIM // scale
     fact = gen.fact_table(nf, nd, SEED2 + 1000 + scale, cols=("key", "price", "disc", "date"))
     dim = gen.dim_table(nd, SEED2 + 1000 + scale, cols=("key", "segment"))
-    t0 = time.perf_counter()
-    bsel = R.filter([(dim["segment"], "==", 2)], nd)
-    psel = R.filter([(fact["date"], ">", 1200)], nf)
-    prow, brow, _ = R.join(dim["key"], fact["key"], bsel=bsel, psel=psel)
-    keys, aggs = R.groupby([fact["key"]], [("sum_mul_kminus", fact["price"], fact["disc"], 100)], nf, sel=prow)
-    R.topk(aggs[:, 0], keys[:, 0], 10)
-    return nf, time.perf_counter() - t0
+
+    def q():
+        bsel = R.filter([(dim["segment"], "==", 2)], nd, parallel=parallel)
+        psel = R.filter([(fact["date"], ">", 1200)], nf, parallel=parallel)
+        prow, _, _ = R.join(dim["key"], fact["key"], bsel=bsel, psel=psel, parallel=parallel)
+        keys, aggs = R.groupby([fact["key"]], [("sum_mul_kminus", fact["price"], fact["disc"], 100)], nf, sel=prow,
+                               parallel=parallel)
+        R.topk(aggs[:, 0], keys[:, 0], 10)
+
+    return nf, _timed(q)
+
+
+def cpu_pricing_sample(scale: int, parallel: bool):
+    from oracle import relational as R
+    n = N_FACT // scale
+    t = gen.fact_table(n, N_DIM // scale, SEED2 + 2000, cols=("flag", "status", "qty", "price", "disc", "date"))
+
+    def q():
+        sel = R.filter([(t["date"], "<=", 2460)], n, parallel=parallel)
+        R.groupby([t["flag"], t["status"]], [("sum", t["qty"], None, None), ("sum", t["price"], None, None),
+                                              ("sum_mul_kminus", t["price"], t["disc"], 100),
+                                              ("count", None, None, None), ("avg", t["qty"], None, None)], n,
+                  sel=sel, parallel=parallel)
+
+    return n, _timed(q)
+
+
+def cpu_filter_sample(scale: int, parallel: bool):
+    from oracle import relational as R
+    n = N_FACT // scale
+    t = gen.fact_table(n, N_DIM // scale, SEED2 + 3000, cols=("date",))
+    return n, _timed(lambda: R.filter([(t["date"], "<=", 2460)], n, parallel=parallel))
+
+
+def cpu_chain_sample(scale: int, parallel: bool):
+    from oracle import relational as R
+    npr, nb, nt = 100_000_000 // scale, 10_000_000 // scale, 1_000_000 // scale
+    d = gen.chain_tables(npr, nb, nt, gen.BASE_SEED + 2 + 1000 * scale)
+
+    def q():
+        b_rows, t_rows, _ = R.join(d["third_pk"], d["build_fk2"], cap=nb, parallel=parallel)
+        cat_of = d["third_cat"][t_rows]
+        p_rows, ib, _ = R.join(d["build_pk"][b_rows], d["probe_fk"].astype(np.int32), cap=npr, parallel=parallel)
+        cat = np.ascontiguousarray(cat_of[ib], dtype=np.int32)
+        pay = np.ascontiguousarray(d["probe_payload"][p_rows])
+        R.groupby([cat], [("sum", pay, None, None), ("count", None, None, None)], len(cat), parallel=parallel)
+
+    return npr, _timed(q)
+
+
+def cpu_soft_sample(n: int):
+    """Soft aggregation forward + backward in float64 (numpy, one thread)."""
+    from oracle import soft
+    s = gen.soft_table(n, 1024, gen.BASE_SEED + 3)
+    th = np.zeros(1024, np.float32)
+    ones = np.ones(1024)
+
+    def q():
+        soft.soft_agg_fwd(s["x"], s["v"], s["gid"], th, 0.1, 1024)
+        soft.soft_agg_bwd(s["x"], s["v"], s["gid"], th, 0.1, 1024, ones, ones)
+
+    return n, _timed(q)
+
+
+def cpu_cnn_sample(grids: int = 1):
+    """One trainable-query step (forward, backward, Adam) of the float64 CNN
+    oracle on `grids` grids of 16 cells."""
+    from oracle import cnn as O
+    img, lab = gen.glyph_grids(grids, gen.BASE_SEED + 4)
+    params = {k: np.asarray(v, np.float64) for k, v in gen.cnn_params(gen.BASE_SEED + 5).items()}
+    tgt = O.targets_from_labels(lab)
+    zeros = {k: np.zeros_like(v) for k, v in params.items()}
+
+    def q():
+        fw = O.forward(params, img)
+        g = O.backward(params, fw, tgt)
+        O.adam_step(params, g, zeros, zeros, 1)
+
+    return grids * 16, _timed(q)
+
+
+def cpu_baseline(fn, unit_scale: float, unit: str, sample: str, parallel_ok: bool = True, **kw):
+    """Times the oracle: OpenMP on all host cores (when the function has a
+    parallel form) and single-threaded.  Rates are units per second of
+    `unit` (work per sample unit x unit_scale)."""
+    from oracle import relational as R
+    out = {"unit": unit, "kind": "oracle", "sample": sample}
+    n1, s1 = fn(parallel=False, **kw) if parallel_ok else fn(**kw)
+    out["single_thread"] = {"value": n1 * unit_scale / s1, "seconds": s1, "cores": 1}
+    if parallel_ok:
+        n2, s2 = fn(parallel=True, **kw)
+        out.update({"value": n2 * unit_scale / s2, "seconds": s2, "cores": R.threads()})
+    else:
+        out.update({"value": out["single_thread"]["value"], "seconds": s1, "cores": 1})
+    out["host_cores"] = host_cores()
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the oracle (plain C, OpenMP on the host cores) on a
+    bounded sample of the headline workload, per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import relational as R
     scale = 20
     rows, secs = [], []
     for _ in range(args.warmup):
-        cpu_shipping_sample(scale)
+        cpu_shipping_sample(scale, True)
     for _ in range(args.steps):
-        r, s = cpu_shipping_sample(scale)
+        r, s = cpu_shipping_sample(scale, True)
         rows.append(r)
         secs.append(s)
     v = sum(rows) / sum(secs)
@@ -91,9 +199,10 @@ def run_reference(args):
         "ms_per_step": 1000.0 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "fact_rows": N_FACT, "dim_rows": N_DIM, "parallelism": "replicas"},
-        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": R.threads(), "host_cores": host_cores(),
+                         "kind": "oracle",
                          "sample": "1/%d of the workload per step (%d fact rows, %d dimension rows), plain C "
-                                   "oracle, one thread" % (scale, N_FACT // scale, N_DIM // scale)},
+                                   "oracle, OpenMP row-partitioned" % (scale, N_FACT // scale, N_DIM // scale)},
         "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -102,28 +211,36 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- traffic
 
-# DRAM bytes (read + write) of a stage's kernel from an ncu capture kept in
-# profiles/, per fact row of the capture's workload, and the source file it was
-# built from.  The capture ran the plan at 1/4 scale; every term of the
-# probe's traffic grows with the fact rows, so it is scaled by them.
-TRAFFIC = {
-    "join_probe": {"bytes_per_fact_row": (328.591104e6 + 7.65696e6) / 15e6,
-                   "src": "paper_2211_02753_b300/csrc/join.cu", "sha1": "3fbda6a2fcd7",
-                   "capture": "profiles/join_probe_kernel_15M_fact_rows.md"},
-}
+# DRAM bytes (read + write) of a kernel from an ncu capture kept in
+# profiles/, per unit of the capture's workload (fact rows, probe rows ...),
+# and the source file it was built from.  Captures run a smaller case of the
+# same plan; every term of these kernels' traffic grows with those units, so
+# it is scaled by them.  None when the source changed since the capture.
+TRAFFIC = {}
 
 
-def measured_traffic(stage: str):
-    """Per-launch DRAM bytes of the stage at full size, or None when there is
-    no capture or the kernel source changed since it was taken."""
+def measured_traffic(kernel: str, units: float):
     import hashlib
-    t = TRAFFIC.get(stage)
+    t = TRAFFIC.get(kernel)
     if t is None:
         return None
     with open(os.path.join(ROOT, t["src"]), "rb") as f:
         if hashlib.sha1(f.read()).hexdigest()[:12] != t["sha1"]:
             return None
-    return t["bytes_per_fact_row"] * N_FACT
+    return t["bytes_per_unit"] * units
+
+
+def roofline(bound, algo, seconds, peak, unit, kernel, traffic=None, peak_kind="measured", extra=None):
+    achieved = algo / seconds / (1e9 if unit == "GB/s" else 1e12)
+    r = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+         "traffic": traffic, "kernel": kernel, "peak_kind": peak_kind,
+         "algorithmic": algo, "seconds": seconds}
+    if traffic is not None and unit == "GB/s":
+        r["dram_gbs"] = traffic / seconds / 1e9
+        r["dram_frac"] = r["dram_gbs"] / peak
+    if extra:
+        r.update(extra)
+    return r
 
 
 # ------------------------------------------------------------- multi-rank
@@ -196,6 +313,22 @@ class ClockSampler:
 
 # ------------------------------------------------------------------- GPU arm
 
+def _events_median(fns, stream, reps=5):
+    """Median CUDA-event time (ms) of each function in `fns`, run in order on
+    `stream` (each is a library call; events recorded between them)."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)]
+        e[0].record(stream)
+        for i, fn in enumerate(fns):
+            fn()
+            e[i + 1].record(stream)
+        torch.cuda.synchronize()
+        ts.append([e[i].elapsed_time(e[i + 1]) for i in range(len(fns))])
+    return [statistics.median(t[i] for t in ts) for i in range(len(fns))]
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -215,9 +348,9 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    hbm_peak, peak_kind = load_peaks()
+    hbm_peak, bf16_peak, peak_kind = load_peaks()
 
-    # ---- headline: shipping-priority plan
+    # ---- headline: shipping-priority plan as one group-join
     fact_h, dim_h = shipping_inputs()
     fact = {k: torch.from_numpy(v).to(dev) for k, v in fact_h.items()}
     dim = {k: torch.from_numpy(v).to(dev) for k, v in dim_h.items()}
@@ -230,31 +363,9 @@ def run_gpu(args):
     nmatch = int(out["nmatch"].item())
     ngroups = int(out["ngroups"].item())
 
-    # stage timing (CUDA events on the launching stream) for the roofline
-    def stage_times(reps=3):
-        ev = []
-        for _ in range(reps):
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-            e[0].record(stream)
-            ops.join_build([dim["key"], dim["segment"]], 0, preds=[(1, "==", 2)], nslots=plan.nslots,
-                           table=plan.table, status=plan.status)
-            e[1].record(stream)
-            pr = ops.join_probe(plan.table, [fact["key"], fact["date"], fact["price"], fact["disc"]], 0,
-                                preds=[(1, ">", 1200)], gather=[0, 2, 3], capacity=plan.cap, rowids=False,
-                                payload=False, status=plan.status)
-            e[2].record(stream)
-            kc, pc, dc = pr["gathered"]
-            gb = ops.groupby_agg([ops.Col(kc, 1, N_DIM), pc, dc], [0], [("sum_mul_kminus", 1, 2, 100)],
-                                 n=plan.cap, nsel=pr["count"], strategy=plan.groupby_strategy, capacity=plan.cap,
-                                 status=plan.status)
-            e[3].record(stream)
-            ops.topk(gb["aggs"][0], gb["keys"][0], 10, d_n=gb["ngroups"], status=plan.status)
-            e[4].record(stream)
-            torch.cuda.synchronize()
-            ev.append([e[i].elapsed_time(e[i + 1]) for i in range(4)])
-        return [statistics.median(x[i] for x in ev) for i in range(4)]
-
-    st_ms = stage_times()
+    # stage timing (CUDA events on the launching stream): build, probe, finish
+    st_ms = _events_median([plan.gj_build, plan.gj_probe, plan.gj_finish], stream)
+    ops.check(plan.status, "shipping-priority stages")
 
     # the timed step: the plan captured once as a CUDA graph and replayed
     # (the same kernels; no host work between launches)
@@ -264,7 +375,6 @@ def run_gpu(args):
     ops.check(plan.status, "shipping-priority plan (graph)")
     assert int(out["nmatch"].item()) == nmatch and int(out["ngroups"].item()) == ngroups
 
-    # timed region
     sampler = ClockSampler()
     barrier()
     torch.cuda.synchronize()
@@ -324,30 +434,22 @@ def run_gpu(args):
     except Exception:
         launches_per_step = None
 
-    # ---- roofline of the dominant stage
-    stage_names = ["join_build", "join_probe", "groupby", "topk"]
+    # ---- roofline of the dominant kernel: the probe (algorithmic bytes of
+    # the fact side per the plan's byte budget: the date column, the key of
+    # every row passing date > 1200, price and discount of every match;
+    # bitmap lookups and accumulator atomics are L2-resident and not counted)
     sel_f = float(np.mean(fact_h["date"] > 1200))
-    probe_rows = N_FACT * sel_f
-    algo = {
-        # build: dim segment (1 B) for every row + key (4 B) for matches + table slot writes (8 B/slot fill +
-        # 8 B per insert)
-        "join_build": N_DIM * 1 + N_DIM * 0.2 * 4 + plan.nslots * 8 + N_DIM * 0.2 * 8,
-        # probe: date (4 B) every row; key (4 B) of qualifying rows; one 8-byte slot per lookup; price/disc
-        # (16 B) of matches; key/price/disc written for matches (20 B)
-        "join_probe": N_FACT * 4 + probe_rows * 4 + probe_rows * 8 + nmatch * 16 + nmatch * 20,
-        # partitioned group-by: count (key 4 B), scatter (key, price, disc 20 B in; gid + value 12 B out),
-        # bucket reduce (12 B in), groups out (key 4 B + sum 8 B)
-        "groupby": nmatch * (4 + 20 + 12 + 12) + ngroups * 12,
-        "topk": ngroups * 12,
-    }
-    dom = int(np.argmax(st_ms))
-    dom_name = stage_names[dom]
-    achieved = algo[dom_name] / (st_ms[dom] / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": measured_traffic(dom_name), "kernel": dom_name,
-                "peak_kind": peak_kind + " (copy bandwidth)",
-                "stages_ms": dict(zip(stage_names, st_ms)),
-                "stages_algo_gbs": {k: algo[k] / (t / 1000.0) / 1e9 for k, t in zip(stage_names, st_ms)}}
+    probe_algo = N_FACT * 4 + N_FACT * sel_f * 4 + nmatch * 16
+    build_algo = N_DIM * 1 + N_DIM * 0.2 * 4
+    finish_algo = ngroups * 12
+    stage_names = ["groupjoin_build", "groupjoin_probe", "groupjoin_finish"]
+    roof = roofline("hbm", probe_algo, st_ms[1] / 1e3, hbm_peak, "GB/s", "gjr_probe_kernel (tdp_groupjoin_probe)",
+                    traffic=measured_traffic("gjr_probe", N_FACT), peak_kind=peak_kind + " (copy bandwidth)",
+                    extra={"stages_ms": dict(zip(stage_names, st_ms)),
+                           "stages_algo_gbs": {n: a / (t / 1e3) / 1e9 for n, a, t in
+                                               zip(stage_names, [build_algo, probe_algo, finish_algo], st_ms)},
+                           "plan_algorithmic_bytes": build_algo + probe_algo + finish_algo,
+                           "plan_frac": (build_algo + probe_algo + finish_algo) / (ms / 1e3) / 1e9 / hbm_peak})
 
     line = {
         "metric": "fact rows/s (shipping-priority plan)", "value": value, "unit": "rows/s", "n_gpus": world,
@@ -355,28 +457,28 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "fact_rows": N_FACT, "dim_rows": N_DIM, "matches": nmatch,
                    "groups": ngroups, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "plan": "group-join (build / probe / finish) with fused top-10",
                    "l2": "inputs larger than L2 (1.5 GB of columns per step)",
                    "launch": "each step one replay of the plan captured as a CUDA graph"},
-        "roofline": roofline,
+        "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms},
         "gpu_launches": (launches_per_step * args.steps) if launches_per_step is not None else None,
         "gpu_launches_per_step": launches_per_step,
         "clocks": clocks,
     }
-    del fact, dim, plan, pin_f, pin_d
+    del fact, dim, plan, step, pin_f, pin_d
     torch.cuda.empty_cache()
 
     if args.plans == "all":
-        line["plans"] = other_plans(dev, stream, hbm_peak, args)
+        line["plans"] = other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h)
 
     if rank == 0:
-        # CPU baseline: the oracle on a bounded sample (rank 0, N=1 semantics)
         scale = 20
-        r, s = cpu_shipping_sample(scale)
-        line["cpu_baseline"] = {"value": r / s, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                                "sample": "1/%d of the workload (%d fact rows, %d dimension rows), plain C "
-                                          "oracle, one thread, %.1f s" % (scale, r, N_DIM // scale, s)}
+        line["cpu_baseline"] = cpu_baseline(
+            cpu_shipping_sample, 1.0, "rows/s",
+            "1/%d of the workload (%d fact rows, %d dimension rows), plain C oracle" %
+            (scale, N_FACT // scale, N_DIM // scale), scale=scale)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -417,18 +519,44 @@ def _time_graph(fn, stream, steps):
     return _time(g.replay, stream, steps)
 
 
-def other_plans(dev, stream, hbm_peak, args):
+def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h):
     import torch
     from paper_2211_02753_b300 import ops, plans
     res = {}
     steps = max(3, args.steps)
-    # pricing summary at 60M rows
+    pk = peak_kind + " (copy bandwidth)"
+    # ---- shipping priority on the separate path (build -> probe -> group-by -> top-k)
+    fact = {k: torch.from_numpy(v).to(dev) for k, v in fact_h.items()}
+    dim = {k: torch.from_numpy(v).to(dev) for k, v in dim_h.items()}
+    sel_f = float(np.mean(fact_h["date"] > 1200))
+    for strategy in ("auto", "sort"):
+        p = plans.ShippingPriority(fact, dim, groupjoin=False, groupby_strategy=strategy)
+        ms = _time_graph(lambda: p.run(), stream, steps)
+        o = p.run()
+        torch.cuda.synchronize()
+        ops.check(p.status, "shipping separate " + strategy)
+        nm, ng = int(o["nmatch"].item()), int(o["ngroups"].item())
+        # the group-by stage on its own (CUDA events): 12 B/match scattered or
+        # sorted (3 digit passes x 2 x 12 B for the sort path) + groups out
+        kc, pc, dc = p.last_probe["gathered"]
+        gb_ms = _events_median([lambda: ops.groupby_agg([ops.Col(kc, 1, N_DIM), pc, dc], [0],
+                                                        [("sum_mul_kminus", 1, 2, 100)], n=p.cap,
+                                                        nsel=p.last_probe["count"], strategy=strategy,
+                                                        capacity=p.cap, status=p.status)], stream)[0]
+        gb_algo = nm * 20 + (nm * 12 * 2 * 3 if strategy == "sort" else nm * 24) + ng * 12
+        res["shipping_separate_" + ("partition" if strategy == "auto" else "sort")] = {
+            "ms": ms, "rows_per_s": N_FACT / (ms / 1e3), "groups": ng, "groupby_ms": gb_ms,
+            "roofline": roofline("hbm", gb_algo, gb_ms / 1e3, hbm_peak, "GB/s", "group-by stage (" + strategy + ")",
+                                 peak_kind=pk)}
+        del p
+        torch.cuda.empty_cache()
+    del fact, dim
+    torch.cuda.empty_cache()
+    # ---- filter and pricing summary at 60M rows
     t = gen.fact_table(N_FACT, N_DIM, SEED2, cols=("flag", "status", "qty", "price", "disc", "date"))
     sel = float(np.mean(t["date"] <= 2460))
     td = {k: torch.from_numpy(v).to(dev) for k, v in t.items()}
-    td["key"] = None
     del t
-    # standalone filter with stream compaction (row ids) over the 60M-row date column
     fout = {}
 
     def run_filter():
@@ -438,59 +566,81 @@ def other_plans(dev, stream, hbm_peak, args):
     nsel = int(fout["o"]["count"].item())
     fbytes = N_FACT * 4 + nsel * 4
     res["filter_60M"] = {"ms": ms, "rows_per_s": N_FACT / (ms / 1e3), "selected": nsel,
-                         "algo_gbs": fbytes / (ms / 1e3) / 1e9, "frac_hbm": fbytes / (ms / 1e3) / 1e9 / hbm_peak}
+                         "roofline": roofline("hbm", fbytes, ms / 1e3, hbm_peak, "GB/s", "filter_kernel", peak_kind=pk),
+                         "cpu_baseline": cpu_baseline(cpu_filter_sample, 1.0, "rows/s",
+                                                      "1/10 of the rows (6M), date <= 2460", scale=10)}
     for strategy in ("small_domain", "sort"):
         p = plans.PricingSummary(td, strategy)
         ms = _time_graph(lambda: p.run(), stream, steps if strategy == "small_domain" else 3)
-        bpr = plans.PricingSummary.bytes_per_row(sel)
-        res["pricing_summary_60M_" + strategy] = {"ms": ms, "rows_per_s": N_FACT / (ms / 1e3),
-                                                  "algo_gbs": N_FACT * bpr / (ms / 1e3) / 1e9,
-                                                  "frac_hbm": N_FACT * bpr / (ms / 1e3) / 1e9 / hbm_peak}
+        algo = N_FACT * plans.PricingSummary.bytes_per_row(sel)
+        if strategy == "sort":  # plus the pack and the sort passes over (key, row) pairs of the selected rows
+            algo += N_FACT * sel * (12 + 2 * 12)
+        res["pricing_summary_60M_" + strategy] = {
+            "ms": ms, "rows_per_s": N_FACT / (ms / 1e3),
+            "roofline": roofline("hbm", algo, ms / 1e3, hbm_peak, "GB/s",
+                                 "small_domain_priv_kernel" if strategy == "small_domain" else "sort path",
+                                 peak_kind=pk)}
+    res["pricing_summary_60M_small_domain"]["cpu_baseline"] = cpu_baseline(
+        cpu_pricing_sample, 1.0, "rows/s", "1/20 of the rows (3M)", scale=20)
     del td
     torch.cuda.empty_cache()
-    # join chain (100M probe rows)
+    # ---- join chain (100M probe rows): fused, and probe -> sort group-by
     d = gen.chain_tables(100_000_000, 10_000_000, 1_000_000, gen.BASE_SEED + 2)
     dd = {k: torch.from_numpy(v.astype(np.int32) if k == "probe_fk" else v).to(dev) for k, v in d.items()}
     del d
-    jc = plans.JoinChain(dd)
-    ms = _time_graph(lambda: jc.run(), stream, steps)
-    out = jc.run()
-    torch.cuda.synchronize()
-    ops.check(jc.status, "join chain")
-    algo = 100e6 * (4 + 8 + 8) + 10e6 * (4 + 4 + 8 + 8) + 1e6 * 8
-    res["join_chain_100M"] = {"ms": ms, "rows_per_s": 100e6 / (ms / 1e3), "algo_gbs": algo / (ms / 1e3) / 1e9,
-                              "frac_hbm": algo / (ms / 1e3) / 1e9 / hbm_peak,
-                              "groups": int(out["ngroups"].item())}
-    del dd, jc
+    for name, fused, strategy in (("join_chain_100M", True, "auto"), ("join_chain_100M_sort", False, "sort")):
+        jc = plans.JoinChain(dd, fused=fused, groupby_strategy=strategy)
+        ms = _time_graph(lambda: jc.run(), stream, steps if fused else 3)
+        out = jc.run()
+        torch.cuda.synchronize()
+        ops.check(jc.status, name)
+        # probe 12 B/row (key + payload), build 10M x (4 + 4 + 8 slot), third 1M x 8, tables written;
+        # the unfused path adds 12 B/match written + the sort (2 x 12 B x 3 passes) + read back
+        algo = 100e6 * 12 + 10e6 * (4 + 4 + 8 + 8) + 1e6 * 8 + 2 ** 24 * 8 + 2 ** 21 * 8
+        if not fused:
+            algo += 100e6 * (12 + 12 * 2 * 3 + 12)
+        res[name] = {"ms": ms, "rows_per_s": 100e6 / (ms / 1e3), "groups": int(out["ngroups"].item()),
+                     "roofline": roofline("hbm", algo, ms / 1e3, hbm_peak, "GB/s",
+                                          "join_probe_agg_kernel" if fused else "probe + sort group-by",
+                                          peak_kind=pk)}
+        del jc, out
+        torch.cuda.empty_cache()
+    res["join_chain_100M"]["cpu_baseline"] = cpu_baseline(cpu_chain_sample, 1.0, "rows/s",
+                                                          "1/50 of the chain (2M probe rows)", scale=50)
+    del dd
     torch.cuda.empty_cache()
-    # soft query fwd+bwd (10M rows)
+    # ---- soft query (10M rows)
     s = gen.soft_table(10_000_000, 1024, gen.BASE_SEED + 3)
     sd = {k: torch.from_numpy(v).to(dev) for k, v in s.items()}
     sq = plans.SoftQuery(sd)
     ms = _time_graph(lambda: sq.run(), stream, steps)
-    algo = 10e6 * 24
-    res["soft_query_10M_fwd_bwd"] = {"ms": ms, "rows_per_s": 10e6 / (ms / 1e3), "algo_gbs": algo / (ms / 1e3) / 1e9,
-                                     "frac_hbm": algo / (ms / 1e3) / 1e9 / hbm_peak}
-    # the individual soft kernels: aggregation forward / backward (12 B/row
-    # each), soft filter forward (12 B/row: x, gid in, mask out) and backward
-    # (16 B/row: x, gid, grad_mask in, grad_x out)
+    res["soft_query_10M_fwd_bwd"] = {
+        "ms": ms, "rows_per_s": 10e6 / (ms / 1e3),
+        "roofline": roofline("hbm", 10e6 * 24, ms / 1e3, hbm_peak, "GB/s", "soft_reduce_kernel fwd + bwd",
+                             peak_kind=pk),
+        "cpu_baseline": cpu_baseline(cpu_soft_sample, 1.0, "rows/s", "1M rows, float64 numpy, one thread",
+                                     parallel_ok=False, n=1_000_000)}
     th, tau = sq.theta, sq.tau
     gm = torch.ones_like(sd["x"])
-    for name, fn, bpr in (
-            ("soft_agg_fwd_10M", lambda: ops.soft_agg_fwd(sd["x"], sd["v"], sd["gid"], th, tau), 12),
-            ("soft_agg_bwd_10M", lambda: ops.soft_agg_bwd(sd["x"], sd["v"], sd["gid"], th, tau, sq.gS, sq.gC), 12),
-            ("soft_filter_fwd_10M", lambda: ops.soft_filter_fwd(sd["x"], sd["gid"], th, tau), 12),
-            ("soft_filter_bwd_10M", lambda: ops.soft_filter_bwd(sd["x"], sd["gid"], th, tau, gm), 16)):
+    for name, fn, bpr, kern in (
+            ("soft_agg_fwd_10M", lambda: ops.soft_agg_fwd(sd["x"], sd["v"], sd["gid"], th, tau), 12,
+             "soft_reduce_kernel<fwd>"),
+            ("soft_agg_bwd_10M", lambda: ops.soft_agg_bwd(sd["x"], sd["v"], sd["gid"], th, tau, sq.gS, sq.gC), 12,
+             "soft_reduce_kernel<bwd>"),
+            ("soft_filter_fwd_10M", lambda: ops.soft_filter_fwd(sd["x"], sd["gid"], th, tau), 12,
+             "soft_filter_fwd_kernel"),
+            ("soft_filter_bwd_10M", lambda: ops.soft_filter_bwd(sd["x"], sd["gid"], th, tau, gm), 16,
+             "soft_reduce_kernel<filter bwd>")):
         ms = _time_graph(fn, stream, steps)
-        res[name] = {"ms": ms, "rows_per_s": 10e6 / (ms / 1e3), "algo_gbs": 10e6 * bpr / (ms / 1e3) / 1e9,
-                     "frac_hbm": 10e6 * bpr / (ms / 1e3) / 1e9 / hbm_peak}
+        res[name] = {"ms": ms, "rows_per_s": 10e6 / (ms / 1e3),
+                     "roofline": roofline("hbm", 10e6 * bpr, ms / 1e3, hbm_peak, "GB/s", kern, peak_kind=pk)}
     del sd, sq
     torch.cuda.empty_cache()
-    res["trainable_query_glyph_cnn"] = glyph_plan(dev, stream, args)
+    res["trainable_query_glyph_cnn"] = glyph_plan(dev, stream, args, bf16_peak, peak_kind)
     return res
 
 
-def glyph_plan(dev, stream, args):
+def glyph_plan(dev, stream, args, bf16_peak, peak_kind):
     """Trainable glyph query: train steps/s (batch 256 grids = 4096 cells),
     exact-query steps/s on the same GPU, and the query-level accuracy reached
     after a fixed training budget."""
@@ -542,10 +692,18 @@ def glyph_plan(dev, stream, args):
     ok = np.all(cnt.cpu().numpy() == ec, axis=1) & np.all(rsum.cpu().numpy() == er, axis=1)
     cell_acc = float((labels.cpu().numpy().reshape(-1, 4, 4) == te_lab).mean())
     flops_fwd = 4096 * 2 * (26 * 26 * 32 * 9 + 24 * 24 * 64 * 288 + 9216 * 128 + 128 * 10)
+    train_flops = 3 * flops_fwd
+    cells, secs = cpu_cnn_sample(1)
     return {"train_ms": train_ms, "train_steps_per_s": 1000.0 / train_ms, "exact_query_ms": infer_ms,
             "exact_query_steps_per_s": 1000.0 / infer_ms, "batch_grids": B, "training_steps": budget,
             "query_accuracy": float(ok.mean()), "cell_accuracy": cell_acc,
-            "train_tflops": 3 * flops_fwd / (train_ms / 1e3) / 1e12}
+            "roofline": roofline("tensor", train_flops, train_ms / 1e3, bf16_peak, "TFLOP/s",
+                                 "whole training step (conv2 tcgen05 kernels, fc1 tcgen05 GEMM)",
+                                 peak_kind=peak_kind + " (cuBLAS bf16, sustained)"),
+            "cpu_baseline": {"value": 1.0 / (secs * 4096 / cells), "unit": "train steps/s", "cores": 1,
+                             "kind": "oracle", "host_cores": host_cores(),
+                             "sample": "one grid (16 cells) through the float64 oracle's forward, backward and "
+                                       "Adam (%.2f s), scaled per cell to the 4096-cell step" % secs}}
 
 
 def run_only(args):
@@ -602,7 +760,7 @@ def run_only(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plans", default="all", choices=["all", "main"])

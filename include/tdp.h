@@ -403,6 +403,40 @@ tdp_status tdp_groupjoin(const tdp_col *build_cols, int32_t nbuild_cols, const t
                          int32_t topk, int32_t topk_agg, int64_t *out_top_vals, int32_t *out_top_keys,
                          int64_t *d_topk, void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
 
+/*
+ * The same group-join in three steps over one workspace, so that a build
+ * side can be probed by several batches of probe rows (and each step timed
+ * on its own).  Every step takes the same n_build, key_lo, key_hi, aggs,
+ * naggs and topk, and the workspace of tdp_groupjoin_workspace(n_build,
+ * key_lo, key_hi, naggs, topk); the steps run in stream order.
+ *
+ *   tdp_groupjoin_build   clears the workspace, inserts the qualifying build
+ *                         keys (duplicates and keys outside [key_lo, key_hi]
+ *                         flagged as in tdp_groupjoin) and ranks them; the
+ *                         aggregates' ops fix the accumulator layout (their
+ *                         column indices are not read)
+ *   tdp_groupjoin_probe   adds the qualifying probe rows that find their key
+ *                         to the groups and to the joined-row count; may be
+ *                         called any number of times between build and finish
+ *                         (each call with its own probe columns)
+ *   tdp_groupjoin_finish  writes the groups in ascending key order, the
+ *                         joined-row count (d_nmatch, optional) and the
+ *                         optional top-k, as tdp_groupjoin does
+ */
+tdp_status tdp_groupjoin_build(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pred *build_preds,
+                               int32_t nbuild_preds, int64_t n_build, const int64_t *d_nbuild, int32_t build_key_col,
+                               int64_t key_lo, int64_t key_hi, const tdp_agg *aggs, int32_t naggs, int32_t topk,
+                               void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
+tdp_status tdp_groupjoin_probe(const tdp_col *probe_cols, int32_t nprobe_cols, const tdp_pred *probe_preds,
+                               int32_t nprobe_preds, int64_t n_probe, const int64_t *d_nprobe, int32_t probe_key_col,
+                               int64_t n_build, int64_t key_lo, int64_t key_hi, const tdp_agg *aggs, int32_t naggs,
+                               int32_t topk, void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
+tdp_status tdp_groupjoin_finish(int64_t n_build, int64_t key_lo, int64_t key_hi, const tdp_agg *aggs, int32_t naggs,
+                                int32_t *out_keys, int64_t *const *out_aggs, int64_t capacity, int64_t *d_ngroups,
+                                int64_t *d_nmatch, int32_t topk, int32_t topk_agg, int64_t *out_top_vals,
+                                int32_t *out_top_keys, int64_t *d_topk, void *ws, size_t ws_bytes,
+                                int32_t *d_status, tdp_stream_t stream);
+
 /* ----------------------------------------------------------------- top-k */
 
 /* Workspace bytes for tdp_topk over n rows. */

@@ -277,3 +277,234 @@ void orc_sort_pairs(int64_t n, const uint64_t *keys, const uint32_t *vals,
     }
     free(idx);
 }
+
+/* ------------------------------------------------- OpenMP variants (timing) */
+/*
+ * Row-partitioned versions of filter, join and group-by for the timed CPU
+ * baseline on all host cores.  Each gives exactly the result of its
+ * single-threaded counterpart above (pinned by the tests):
+ *   filter   -- every thread scans a contiguous block of rows; the blocks'
+ *               counts give each block its output offset, so the row ids
+ *               stay in ascending order.
+ *   join     -- the build side is sorted once (single thread); probe rows
+ *               are split into contiguous blocks, each counted, then written
+ *               at its offset: probe order, build-row order within a key.
+ *   group-by -- every thread sorts its block of selected rows by key and
+ *               reduces the runs to partial groups; the sorted partial lists
+ *               are merged by key (sums and counts added, minima / maxima
+ *               combined, AVG rounded from the merged sum and count).
+ */
+#include <omp.h>
+
+int orc_omp_threads(void) { return omp_get_max_threads(); }
+
+int64_t orc_filter_omp(int64_t n, int npred, const void **cols, const int *dts,
+                       const int *cmps, const int64_t *lits, int32_t *out_rowid)
+{
+    int T = omp_get_max_threads();
+    int64_t *cnt = (int64_t *)calloc((size_t)T + 1, sizeof(int64_t));
+#pragma omp parallel num_threads(T)
+    {
+        int t = omp_get_thread_num();
+        int64_t lo = n * t / T, hi = n * (t + 1) / T, c = 0;
+        for (int64_t i = lo; i < hi; i++) {
+            int ok = 1;
+            for (int p = 0; p < npred && ok; p++)
+                ok = holds(get(cols[p], dts[p], i), cmps[p], lits[p]);
+            c += ok;
+        }
+        cnt[t + 1] = c;
+#pragma omp barrier
+#pragma omp single
+        for (int k = 0; k < T; k++)
+            cnt[k + 1] += cnt[k];
+        int64_t o = cnt[t];
+        for (int64_t i = lo; i < hi; i++) {
+            int ok = 1;
+            for (int p = 0; p < npred && ok; p++)
+                ok = holds(get(cols[p], dts[p], i), cmps[p], lits[p]);
+            if (ok)
+                out_rowid[o++] = (int32_t)i;
+        }
+    }
+    int64_t m = cnt[T];
+    free(cnt);
+    return m;
+}
+
+static int64_t first_ge(const int32_t *bkey, const int64_t *b, int64_t mb, int32_t k)
+{
+    int64_t lo = 0, hi = mb;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (bkey[b[mid]] < k)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+int64_t orc_join_omp(int64_t nb, const int32_t *bkey, const int32_t *bsel, int64_t nbsel,
+                     int64_t np, const int32_t *pkey, const int32_t *psel, int64_t npsel,
+                     int32_t *out_probe, int32_t *out_build, int64_t cap, int *dup)
+{
+    int64_t mb = bsel ? nbsel : nb;
+    int64_t *b = (int64_t *)malloc((size_t)(mb > 0 ? mb : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < mb; i++)
+        b[i] = bsel ? bsel[i] : i;
+    qsort_r(b, (size_t)mb, sizeof(int64_t), cmp_build, (void *)bkey);
+    *dup = 0;
+    for (int64_t i = 1; i < mb; i++)
+        if (bkey[b[i]] == bkey[b[i - 1]])
+            *dup = 1;
+    int64_t mp = psel ? npsel : np;
+    int T = omp_get_max_threads();
+    int64_t *cnt = (int64_t *)calloc((size_t)T + 1, sizeof(int64_t));
+#pragma omp parallel num_threads(T)
+    {
+        int t = omp_get_thread_num();
+        int64_t lo = mp * t / T, hi = mp * (t + 1) / T, c = 0;
+        for (int64_t q = lo; q < hi; q++) {
+            int32_t k = pkey[psel ? psel[q] : q];
+            for (int64_t u = first_ge(bkey, b, mb, k); u < mb && bkey[b[u]] == k; u++)
+                c++;
+        }
+        cnt[t + 1] = c;
+#pragma omp barrier
+#pragma omp single
+        for (int k = 0; k < T; k++)
+            cnt[k + 1] += cnt[k];
+        int64_t o = cnt[t];
+        for (int64_t q = lo; q < hi; q++) {
+            int64_t pr = psel ? psel[q] : q;
+            int32_t k = pkey[pr];
+            for (int64_t u = first_ge(bkey, b, mb, k); u < mb && bkey[b[u]] == k; u++, o++)
+                if (o < cap) {
+                    out_probe[o] = (int32_t)pr;
+                    out_build[o] = (int32_t)b[u];
+                }
+        }
+    }
+    int64_t m = cnt[T];
+    free(cnt);
+    free(b);
+    return m;
+}
+
+/* One partial group: its key tuple (row of the first member), and for every
+ * aggregate the running value and the member count. */
+struct part {
+    int64_t row;
+    int64_t cnt;
+    int64_t acc[16];
+};
+
+static int same_key(const struct key_ctx *c, int64_t ra, int64_t rb)
+{
+    for (int k = 0; k < c->nkeys; k++)
+        if (get(c->cols[k], c->dts[k], ra) != get(c->cols[k], c->dts[k], rb))
+            return 0;
+    return 1;
+}
+
+static int key_cmp(const struct key_ctx *c, int64_t ra, int64_t rb)
+{
+    for (int k = 0; k < c->nkeys; k++) {
+        int64_t a = get(c->cols[k], c->dts[k], ra), b = get(c->cols[k], c->dts[k], rb);
+        if (a != b)
+            return a < b ? -1 : 1;
+    }
+    return 0;
+}
+
+int64_t orc_groupby_omp(int64_t n, const int32_t *sel, int64_t nsel,
+                        int nkeys, const void **keycols, const int *keydts,
+                        int naggs, const int *ops, const void **acols, const int *adts,
+                        const void **bcols, const int *bdts, const int64_t *ks,
+                        int64_t *out_keys, int64_t *out_aggs, int64_t cap)
+{
+    if (naggs > 16)
+        return -1;
+    int64_t m = sel ? nsel : n;
+    struct key_ctx ctx = { nkeys, keycols, keydts };
+    int T = omp_get_max_threads();
+    struct part **parts = (struct part **)calloc((size_t)T, sizeof(struct part *));
+    int64_t *np = (int64_t *)calloc((size_t)T, sizeof(int64_t));
+#pragma omp parallel num_threads(T)
+    {
+        int t = omp_get_thread_num();
+        int64_t lo = m * t / T, hi = m * (t + 1) / T, len = hi - lo;
+        int64_t *rows = (int64_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int64_t));
+        for (int64_t i = 0; i < len; i++)
+            rows[i] = sel ? sel[lo + i] : lo + i;
+        qsort_r(rows, (size_t)len, sizeof(int64_t), cmp_rows_by_key, &ctx);
+        struct part *p = (struct part *)malloc((size_t)(len > 0 ? len : 1) * sizeof(struct part));
+        int64_t g = -1;
+        for (int64_t i = 0; i < len; i++) {
+            int64_t r = rows[i];
+            if (g < 0 || !same_key(&ctx, p[g].row, r)) {
+                g++;
+                p[g].row = r;
+                p[g].cnt = 0;
+            }
+            for (int a = 0; a < naggs; a++) {
+                int64_t x = ops[a] == ORC_COUNT ? 1 : get(acols[a], adts[a], r);
+                if (ops[a] == ORC_SUM_MUL_KMINUS)
+                    x = x * (ks[a] - get(bcols[a], bdts[a], r));
+                if (p[g].cnt == 0)
+                    p[g].acc[a] = x;
+                else if (ops[a] == ORC_MIN)
+                    p[g].acc[a] = x < p[g].acc[a] ? x : p[g].acc[a];
+                else if (ops[a] == ORC_MAX)
+                    p[g].acc[a] = x > p[g].acc[a] ? x : p[g].acc[a];
+                else
+                    p[g].acc[a] += x;
+            }
+            p[g].cnt++;
+        }
+        parts[t] = p;
+        np[t] = g + 1;
+        free(rows);
+    }
+    /* merge the sorted partial lists by key */
+    int64_t *pos = (int64_t *)calloc((size_t)T, sizeof(int64_t));
+    int64_t ng = 0;
+    for (;;) {
+        int best = -1;
+        for (int t = 0; t < T; t++)
+            if (pos[t] < np[t] && (best < 0 || key_cmp(&ctx, parts[t][pos[t]].row, parts[best][pos[best]].row) < 0))
+                best = t;
+        if (best < 0)
+            break;
+        struct part acc = parts[best][pos[best]];
+        pos[best]++;
+        for (int t = 0; t < T; t++)
+            while (pos[t] < np[t] && same_key(&ctx, parts[t][pos[t]].row, acc.row)) {
+                const struct part *q = &parts[t][pos[t]];
+                for (int a = 0; a < naggs; a++) {
+                    if (ops[a] == ORC_MIN)
+                        acc.acc[a] = q->acc[a] < acc.acc[a] ? q->acc[a] : acc.acc[a];
+                    else if (ops[a] == ORC_MAX)
+                        acc.acc[a] = q->acc[a] > acc.acc[a] ? q->acc[a] : acc.acc[a];
+                    else
+                        acc.acc[a] += q->acc[a];
+                }
+                acc.cnt += q->cnt;
+                pos[t]++;
+            }
+        if (ng < cap) {
+            for (int k = 0; k < nkeys; k++)
+                out_keys[ng * nkeys + k] = get(keycols[k], keydts[k], acc.row);
+            for (int a = 0; a < naggs; a++)
+                out_aggs[ng * naggs + a] = ops[a] == ORC_AVG ? orc_avg_round(acc.acc[a], acc.cnt) : acc.acc[a];
+        }
+        ng++;
+    }
+    for (int t = 0; t < T; t++)
+        free(parts[t]);
+    free(parts);
+    free(np);
+    free(pos);
+    return ng;
+}

@@ -83,6 +83,11 @@ SIGNATURES = {
     "tdp_groupjoin_workspace": (_sz, [_i64, _i64, _i64, _i32, _i32]),
     "tdp_groupjoin": (_st, [_p, _i32, _p, _i32, _i64, _p, _i32, _p, _i32, _p, _i32, _i64, _p, _i32, _i64, _i64,
                             _p, _i32, _p, _p, _i64, _p, _p, _i32, _i32, _p, _p, _p, _p, _sz, _p, _p]),
+    "tdp_groupjoin_build": (_st, [_p, _i32, _p, _i32, _i64, _p, _i32, _i64, _i64, _p, _i32, _i32, _p, _sz, _p, _p]),
+    "tdp_groupjoin_probe": (_st, [_p, _i32, _p, _i32, _i64, _p, _i32, _i64, _i64, _i64, _p, _i32, _i32, _p, _sz, _p,
+                                  _p]),
+    "tdp_groupjoin_finish": (_st, [_i64, _i64, _i64, _p, _i32, _p, _p, _i64, _p, _p, _i32, _i32, _p, _p, _p, _p, _sz,
+                                   _p, _p]),
     "tdp_topk_workspace": (_sz, [_i64, _i32]),
     "tdp_topk": (_st, [_p, _p, _i64, _p, _i32, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_soft_workspace": (_sz, [_i64, _i32]),

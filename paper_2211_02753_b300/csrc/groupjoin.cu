@@ -38,6 +38,7 @@
 // Nothing is written per match and no partition or sort of the matches is
 // needed; the per-row traffic is the probe-side columns.
 #include <algorithm>
+#include <cstring>
 
 #include "groupby.cuh"
 #include "topk.cuh"
@@ -282,14 +283,14 @@ __device__ __forceinline__ unsigned long long coop_block_prefix(unsigned long lo
 // Rank pass: bm[w].rank = set bits before word w; accumulator rows of the
 // build keys set to their initial values; B (all set bits) to *d_nkeys.
 // d_rows: the inserted build rows (more rows than bits: a duplicate build
-// key).  Block 0 also clears *d_nmatch for the probe.  A block owns `rounds`
+// key).  A block owns `rounds`
 // consecutive spans of 256 x WPT words (more than one only when the domain
 // has more words than the resident blocks cover).
 template <int WPT>
 __global__ void __launch_bounds__(GJR_THREADS) gjr_rank_kernel(RankWord *bm, long long W, int rounds, AggSet as,
                                                                AccLayout al, long long *acc,
                                                                unsigned long long *d_nkeys,
-                                                               const unsigned long long *d_rows, long long *d_nmatch,
+                                                               const unsigned long long *d_rows,
                                                                unsigned long long *totals, unsigned *barrier,
                                                                int32_t *d_status, uint32_t limit)
 {
@@ -298,8 +299,6 @@ __global__ void __launch_bounds__(GJR_THREADS) gjr_rank_kernel(RankWord *bm, lon
     __shared__ long long s_init[TDP_MAX_AGGS + 1];
     if (threadIdx.x <= TDP_MAX_AGGS)
         s_init[threadIdx.x] = slot_init(as, threadIdx.x);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && d_nmatch)
-        *d_nmatch = 0; // the probe, which runs after this kernel, adds its matches
     const long long span = (long long)GJR_THREADS * WPT;
     const long long b0 = (long long)blockIdx.x * rounds * span;
     uint32_t b[WPT];
@@ -795,7 +794,7 @@ static GjrLayout gjr_layout(long long n_build, long long D, int naggs, int topk)
     const size_t kk = (size_t)std::max(0, topk);
     size_t off = 0;
     // [0] build keys, [1] rank barrier, [2] hit-rank barrier, [3] top-k bound
-    // (0: none), [4] inserted build rows
+    // (0: none), [4] inserted build rows, [5] joined rows
     L.counters = off;
     off += 256;
     L.bitmap = off;
@@ -883,23 +882,55 @@ static tdp_status launch_gjr_output(const GjrLayout &L, char *w, const RankWord 
 
 template <int WPT>
 static tdp_status launch_gjr_rank(const GjrLayout &L, char *w, RankWord *bm, const AggSet &as, AccLayout al,
-                                  long long *acc, int64_t *d_nmatch, int32_t *d_status, int G, int rounds,
-                                  cudaStream_t s)
+                                  long long *acc, int32_t *d_status, int G, int rounds, cudaStream_t s)
 {
     const void *kern = (const void *)gjr_rank_kernel<WPT>;
     unsigned long long *cnt = (unsigned long long *)(w + L.counters);
     unsigned long long *nk = &cnt[0], *rows = &cnt[4];
     unsigned long long *totals = (unsigned long long *)(w + L.totals_rank);
     unsigned *barrier = (unsigned *)&cnt[1];
-    long long *nm = (long long *)d_nmatch;
     long long W = L.W;
     const uint32_t limit = spin_limit();
     void *args[] = {(void *)&bm, (void *)&W, (void *)&rounds, (void *)&as, (void *)&al, (void *)&acc,
-                    (void *)&nk, (void *)&rows, (void *)&nm, (void *)&totals, (void *)&barrier,
-                    (void *)&d_status, (void *)&limit};
+                    (void *)&nk, (void *)&rows, (void *)&totals, (void *)&barrier, (void *)&d_status,
+                    (void *)&limit};
     if (cudaLaunchCooperativeKernel(kern, dim3(G), dim3(GJR_THREADS), args, 0, s) != cudaSuccess)
         return TDP_ERR_CUDA;
     return launch_status();
+}
+
+
+
+// The accumulator slots of `aggs` (as make_aggset assigns them: COUNT in slot
+// 0, every other aggregate in the next slot) without their columns: what the
+// build and finish steps need.
+static tdp_status agg_shape(const tdp_agg *aggs, int32_t naggs, AggSet *as, AccLayout *al)
+{
+    if (naggs < 1 || naggs > TDP_MAX_AGGS || !aggs)
+        return TDP_ERR_INVALID_ARG;
+    memset(as, 0, sizeof(*as));
+    as->n = naggs;
+    as->nslots = 1;
+    al->cs = 1;
+    for (int a = 0; a < naggs; a++) {
+        if (aggs[a].op < TDP_AGG_COUNT || aggs[a].op > TDP_AGG_MAX)
+            return TDP_ERR_INVALID_ARG;
+        as->op[a] = aggs[a].op;
+        as->k[a] = aggs[a].k;
+        as->slot[a] = aggs[a].op == TDP_AGG_COUNT ? 0 : as->nslots++;
+        if (aggs[a].op == TDP_AGG_COUNT || aggs[a].op == TDP_AGG_AVG)
+            al->cs = 0;
+    }
+    for (int a = 0; a < naggs; a++)
+        if (as->slot[a] != 0)
+            as->sop[as->slot[a]] = aggs[a].op;
+    al->stride = as->nslots - al->cs;
+    return TDP_OK;
+}
+
+static bool gj_range_ok(int64_t key_lo, int64_t key_hi)
+{
+    return key_hi >= key_lo && key_hi - key_lo < (1ll << 31) && key_lo >= INT32_MIN && key_hi <= INT32_MAX;
 }
 
 } // namespace tdp
@@ -909,64 +940,43 @@ using namespace tdp;
 extern "C" size_t tdp_groupjoin_workspace(int64_t n_build, int64_t key_lo, int64_t key_hi, int32_t naggs,
                                           int32_t topk)
 {
-    if (key_hi < key_lo || key_hi - key_lo >= (1ll << 31) || key_lo < INT32_MIN || key_hi > INT32_MAX || naggs < 1 ||
-        naggs > TDP_MAX_AGGS || n_build < 0 || topk < 0 || topk > TK_MAXK)
+    if (!gj_range_ok(key_lo, key_hi) || naggs < 1 || naggs > TDP_MAX_AGGS || n_build < 0 || topk < 0 ||
+        topk > TK_MAXK)
         return 0;
     return gjr_layout(n_build, key_hi - key_lo + 1, naggs, topk).total;
 }
 
-extern "C" tdp_status tdp_groupjoin(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pred *build_preds,
-                                    int32_t nbuild_preds, int64_t n_build, const int64_t *d_nbuild,
-                                    int32_t build_key_col, const tdp_col *probe_cols, int32_t nprobe_cols,
-                                    const tdp_pred *probe_preds, int32_t nprobe_preds, int64_t n_probe,
-                                    const int64_t *d_nprobe, int32_t probe_key_col, int64_t key_lo, int64_t key_hi,
-                                    const tdp_agg *aggs, int32_t naggs, int32_t *out_keys, int64_t *const *out_aggs,
-                                    int64_t capacity, int64_t *d_ngroups, int64_t *d_nmatch, int32_t topk,
-                                    int32_t topk_agg, int64_t *out_top_vals, int32_t *out_top_keys, int64_t *d_topk,
-                                    void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream)
+extern "C" tdp_status tdp_groupjoin_build(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pred *build_preds,
+                                          int32_t nbuild_preds, int64_t n_build, const int64_t *d_nbuild,
+                                          int32_t build_key_col, int64_t key_lo, int64_t key_hi, const tdp_agg *aggs,
+                                          int32_t naggs, int32_t topk, void *ws, size_t ws_bytes, int32_t *d_status,
+                                          tdp_stream_t stream)
 {
-    if (n_build < 0 || n_build >= (1ll << 31) || n_probe < 0 || n_probe >= (1ll << 31) || !build_cols ||
-        !probe_cols || build_key_col < 0 || build_key_col >= nbuild_cols || probe_key_col < 0 ||
-        probe_key_col >= nprobe_cols || key_hi < key_lo || key_hi - key_lo >= (1ll << 31) || key_lo < INT32_MIN ||
-        key_hi > INT32_MAX || capacity < 0 || !d_ngroups || !out_aggs || (capacity > 0 && !out_keys))
+    if (n_build < 0 || n_build >= (1ll << 31) || !build_cols || build_key_col < 0 || build_key_col >= nbuild_cols ||
+        !gj_range_ok(key_lo, key_hi) || topk < 0 || topk > TK_MAXK)
         return TDP_ERR_INVALID_ARG;
-    if (topk < 0 || topk > TK_MAXK ||
-        (topk > 0 && (topk_agg < 0 || topk_agg >= naggs || !out_top_vals || !out_top_keys || capacity <= 0)))
-        return TDP_ERR_INVALID_ARG;
-    if (build_cols[build_key_col].dtype != TDP_I32 || probe_cols[probe_key_col].dtype != TDP_I32)
+    if (build_cols[build_key_col].dtype != TDP_I32)
         return TDP_ERR_UNSUPPORTED_DTYPE;
-    if (build_cols[build_key_col].n < n_build || probe_cols[probe_key_col].n < n_probe)
+    if (build_cols[build_key_col].n < n_build)
         return TDP_ERR_INVALID_ARG;
-    PredSet bps, pps;
+    PredSet bps;
     tdp_status st = make_predset(build_cols, nbuild_cols, build_preds, nbuild_preds, n_build, &bps);
     if (st != TDP_OK)
         return st;
-    if ((st = make_predset(probe_cols, nprobe_cols, probe_preds, nprobe_preds, n_probe, &pps)) != TDP_OK)
-        return st;
     AggSet as;
-    if ((st = make_aggset(probe_cols, nprobe_cols, aggs, naggs, n_probe, &as)) != TDP_OK)
+    AccLayout al;
+    if ((st = agg_shape(aggs, naggs, &as, &al)) != TDP_OK)
         return st;
-    for (int a = 0; a < naggs; a++)
-        if (capacity > 0 && !out_aggs[a])
-            return TDP_ERR_INVALID_ARG;
     const long long D = key_hi - key_lo + 1;
     const GjrLayout L = gjr_layout(n_build, D, naggs, topk);
     if (!ws || ws_bytes < L.total)
         return TDP_ERR_WORKSPACE_TOO_SMALL;
     if (((uintptr_t)ws % 16) != 0)
         return TDP_ERR_INVALID_ARG;
-    AccLayout al;
-    al.cs = 1;
-    for (int a = 0; a < naggs; a++)
-        if (aggs[a].op == TDP_AGG_COUNT || aggs[a].op == TDP_AGG_AVG)
-            al.cs = 0;
-    al.stride = as.nslots - al.cs;
-
     cudaStream_t s = (cudaStream_t)stream;
     char *w = (char *)ws;
     unsigned long long *cnt = (unsigned long long *)(w + L.counters);
     RankWord *bm = (RankWord *)(w + L.bitmap);
-    uint32_t *hitw = (uint32_t *)(w + L.hits);
     long long *acc = (long long *)(w + L.acc);
     if (cudaMemsetAsync(w, 0, L.acc, s) != cudaSuccess)
         return TDP_ERR_CUDA;
@@ -977,32 +987,94 @@ extern "C" tdp_status tdp_groupjoin(const tdp_col *build_cols, int32_t nbuild_co
                            256, 0, s>>>(
             bps, (const int32_t *)build_cols[build_key_col].data, n_build, (const long long *)d_nbuild, (int)key_lo,
             (unsigned)D, bm, &cnt[4], d_status);
-    {
-        int G = 0, R = 1;
-        if (coop_grid((const void *)gjr_rank_kernel<1>, L.W, 1, L.Gmax, &G, &R, true))
-            st = launch_gjr_rank<1>(L, w, bm, as, al, acc, d_nmatch, d_status, G, R, s);
-        else if (coop_grid((const void *)gjr_rank_kernel<2>, L.W, 2, L.Gmax, &G, &R, true))
-            st = launch_gjr_rank<2>(L, w, bm, as, al, acc, d_nmatch, d_status, G, R, s);
-        else if (coop_grid((const void *)gjr_rank_kernel<4>, L.W, 4, L.Gmax, &G, &R, false))
-            st = launch_gjr_rank<4>(L, w, bm, as, al, acc, d_nmatch, d_status, G, R, s);
-        else
-            st = TDP_ERR_CUDA;
-        if (st != TDP_OK)
-            return st;
-    }
-    if (n_probe > 0) {
-        const long long *dn = (const long long *)d_nprobe;
-        const int32_t *pk = (const int32_t *)probe_cols[probe_key_col].data;
-        unsigned long long *nm = (unsigned long long *)d_nmatch;
-        if (as.nslots <= 2)
-            st = launch_gjr_probe<2>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, nm, s);
-        else if (as.nslots <= 4)
-            st = launch_gjr_probe<4>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, nm, s);
-        else
-            st = launch_gjr_probe<TDP_MAX_AGGS + 1>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, nm, s);
-        if (st != TDP_OK)
-            return st;
-    }
+    int G = 0, R = 1;
+    if (coop_grid((const void *)gjr_rank_kernel<1>, L.W, 1, L.Gmax, &G, &R, true))
+        return launch_gjr_rank<1>(L, w, bm, as, al, acc, d_status, G, R, s);
+    if (coop_grid((const void *)gjr_rank_kernel<2>, L.W, 2, L.Gmax, &G, &R, true))
+        return launch_gjr_rank<2>(L, w, bm, as, al, acc, d_status, G, R, s);
+    if (coop_grid((const void *)gjr_rank_kernel<4>, L.W, 4, L.Gmax, &G, &R, false))
+        return launch_gjr_rank<4>(L, w, bm, as, al, acc, d_status, G, R, s);
+    return TDP_ERR_CUDA;
+}
+
+extern "C" tdp_status tdp_groupjoin_probe(const tdp_col *probe_cols, int32_t nprobe_cols, const tdp_pred *probe_preds,
+                                          int32_t nprobe_preds, int64_t n_probe, const int64_t *d_nprobe,
+                                          int32_t probe_key_col, int64_t n_build, int64_t key_lo, int64_t key_hi,
+                                          const tdp_agg *aggs, int32_t naggs, int32_t topk, void *ws,
+                                          size_t ws_bytes, int32_t *d_status, tdp_stream_t stream)
+{
+    if (n_probe < 0 || n_probe >= (1ll << 31) || n_build < 0 || !probe_cols || probe_key_col < 0 ||
+        probe_key_col >= nprobe_cols || !gj_range_ok(key_lo, key_hi) || topk < 0 || topk > TK_MAXK)
+        return TDP_ERR_INVALID_ARG;
+    if (probe_cols[probe_key_col].dtype != TDP_I32)
+        return TDP_ERR_UNSUPPORTED_DTYPE;
+    if (probe_cols[probe_key_col].n < n_probe)
+        return TDP_ERR_INVALID_ARG;
+    PredSet pps;
+    tdp_status st = make_predset(probe_cols, nprobe_cols, probe_preds, nprobe_preds, n_probe, &pps);
+    if (st != TDP_OK)
+        return st;
+    AggSet as;
+    if ((st = make_aggset(probe_cols, nprobe_cols, aggs, naggs, n_probe, &as)) != TDP_OK)
+        return st;
+    AggSet shape;
+    AccLayout al;
+    if ((st = agg_shape(aggs, naggs, &shape, &al)) != TDP_OK)
+        return st;
+    const long long D = key_hi - key_lo + 1;
+    const GjrLayout L = gjr_layout(n_build, D, naggs, topk);
+    if (!ws || ws_bytes < L.total)
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    if (n_probe == 0)
+        return TDP_OK;
+    char *w = (char *)ws;
+    unsigned long long *cnt = (unsigned long long *)(w + L.counters);
+    const RankWord *bm = (const RankWord *)(w + L.bitmap);
+    uint32_t *hitw = (uint32_t *)(w + L.hits);
+    long long *acc = (long long *)(w + L.acc);
+    const long long *dn = (const long long *)d_nprobe;
+    const int32_t *pk = (const int32_t *)probe_cols[probe_key_col].data;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (as.nslots <= 2)
+        return launch_gjr_probe<2>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5], s);
+    if (as.nslots <= 4)
+        return launch_gjr_probe<4>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5], s);
+    return launch_gjr_probe<TDP_MAX_AGGS + 1>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5], s);
+}
+
+extern "C" tdp_status tdp_groupjoin_finish(int64_t n_build, int64_t key_lo, int64_t key_hi, const tdp_agg *aggs,
+                                           int32_t naggs, int32_t *out_keys, int64_t *const *out_aggs,
+                                           int64_t capacity, int64_t *d_ngroups, int64_t *d_nmatch, int32_t topk,
+                                           int32_t topk_agg, int64_t *out_top_vals, int32_t *out_top_keys,
+                                           int64_t *d_topk, void *ws, size_t ws_bytes, int32_t *d_status,
+                                           tdp_stream_t stream)
+{
+    if (n_build < 0 || !gj_range_ok(key_lo, key_hi) || capacity < 0 || !d_ngroups || !out_aggs ||
+        (capacity > 0 && !out_keys))
+        return TDP_ERR_INVALID_ARG;
+    if (topk < 0 || topk > TK_MAXK ||
+        (topk > 0 && (topk_agg < 0 || topk_agg >= naggs || !out_top_vals || !out_top_keys || capacity <= 0)))
+        return TDP_ERR_INVALID_ARG;
+    AggSet as;
+    AccLayout al;
+    tdp_status st = agg_shape(aggs, naggs, &as, &al);
+    if (st != TDP_OK)
+        return st;
+    for (int a = 0; a < naggs; a++)
+        if (capacity > 0 && !out_aggs[a])
+            return TDP_ERR_INVALID_ARG;
+    const long long D = key_hi - key_lo + 1;
+    const GjrLayout L = gjr_layout(n_build, D, naggs, topk);
+    if (!ws || ws_bytes < L.total)
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    unsigned long long *cnt = (unsigned long long *)(w + L.counters);
+    const RankWord *bm = (const RankWord *)(w + L.bitmap);
+    const uint32_t *hitw = (const uint32_t *)(w + L.hits);
+    const long long *acc = (const long long *)(w + L.acc);
+    if (d_nmatch && cudaMemcpyAsync(d_nmatch, &cnt[5], sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return TDP_ERR_CUDA;
     DenseOut out;
     for (int k = 0; k < TDP_MAX_KEYS; k++) {
         out.key_out[k] = nullptr;
@@ -1041,7 +1113,51 @@ extern "C" tdp_status tdp_groupjoin(const tdp_col *build_cols, int32_t nbuild_co
         gjr_topk_final_kernel<<<1, GJR_THREADS, 0, s>>>(cand, (long long)L.topk_blocks * topk, topk, &cnt[3],
                                                        (const long long *)d_ngroups, capacity,
                                                        (long long *)out_top_vals, out_top_keys, (long long *)d_topk);
-        return launch_status();
     }
-    return TDP_OK;
+    return launch_status();
+}
+
+extern "C" tdp_status tdp_groupjoin(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pred *build_preds,
+                                    int32_t nbuild_preds, int64_t n_build, const int64_t *d_nbuild,
+                                    int32_t build_key_col, const tdp_col *probe_cols, int32_t nprobe_cols,
+                                    const tdp_pred *probe_preds, int32_t nprobe_preds, int64_t n_probe,
+                                    const int64_t *d_nprobe, int32_t probe_key_col, int64_t key_lo, int64_t key_hi,
+                                    const tdp_agg *aggs, int32_t naggs, int32_t *out_keys, int64_t *const *out_aggs,
+                                    int64_t capacity, int64_t *d_ngroups, int64_t *d_nmatch, int32_t topk,
+                                    int32_t topk_agg, int64_t *out_top_vals, int32_t *out_top_keys, int64_t *d_topk,
+                                    void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream)
+{
+    // every argument is checked before anything is launched
+    if (!probe_cols || probe_key_col < 0 || probe_key_col >= nprobe_cols || n_probe < 0 || n_probe >= (1ll << 31) ||
+        capacity < 0 || !d_ngroups || !out_aggs || (capacity > 0 && !out_keys) || topk < 0 || topk > TK_MAXK ||
+        (topk > 0 && (topk_agg < 0 || topk_agg >= naggs || !out_top_vals || !out_top_keys || capacity <= 0)))
+        return TDP_ERR_INVALID_ARG;
+    if (probe_cols[probe_key_col].dtype != TDP_I32)
+        return TDP_ERR_UNSUPPORTED_DTYPE;
+    {
+        PredSet pps;
+        AggSet as;
+        tdp_status st = make_predset(probe_cols, nprobe_cols, probe_preds, nprobe_preds, n_probe, &pps);
+        if (st == TDP_OK)
+            st = make_aggset(probe_cols, nprobe_cols, aggs, naggs, n_probe, &as);
+        if (st != TDP_OK)
+            return st;
+        if (probe_cols[probe_key_col].n < n_probe)
+            return TDP_ERR_INVALID_ARG;
+        for (int a = 0; a < naggs; a++)
+            if (capacity > 0 && !out_aggs[a])
+                return TDP_ERR_INVALID_ARG;
+    }
+    tdp_status st = tdp_groupjoin_build(build_cols, nbuild_cols, build_preds, nbuild_preds, n_build, d_nbuild,
+                                        build_key_col, key_lo, key_hi, aggs, naggs, topk, ws, ws_bytes, d_status,
+                                        stream);
+    if (st != TDP_OK)
+        return st;
+    st = tdp_groupjoin_probe(probe_cols, nprobe_cols, probe_preds, nprobe_preds, n_probe, d_nprobe, probe_key_col,
+                             n_build, key_lo, key_hi, aggs, naggs, topk, ws, ws_bytes, d_status, stream);
+    if (st != TDP_OK)
+        return st;
+    return tdp_groupjoin_finish(n_build, key_lo, key_hi, aggs, naggs, out_keys, out_aggs, capacity, d_ngroups,
+                                d_nmatch, topk, topk_agg, out_top_vals, out_top_keys, d_topk, ws, ws_bytes, d_status,
+                                stream);
 }

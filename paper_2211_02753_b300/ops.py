@@ -331,6 +331,55 @@ def groupjoin(build_cols, build_key, probe_cols, probe_key, lo, hi, aggs, build_
     return out
 
 
+class GroupJoin:
+    """The group-join in steps over one workspace: build() once, probe() one
+    or more batches of probe rows, finish() for the groups (and top-k).  The
+    object owns its workspace and output tensors, so repeated use allocates
+    nothing new."""
+
+    def __init__(self, n_build, lo, hi, aggs, topk=0, topk_agg=0, capacity=None, device="cuda"):
+        self.n_build, self.lo, self.hi = int(n_build), int(lo), int(hi)
+        self.aggs = list(aggs)
+        self.topk, self.topk_agg = int(topk), int(topk_agg)
+        dev = torch.device(device)
+        D = self.hi - self.lo + 1
+        self.cap = min(D, max(self.n_build, 0)) if capacity is None else int(capacity)
+        n = L.lib().tdp_groupjoin_workspace(self.n_build, self.lo, self.hi, len(self.aggs), self.topk)
+        if n == 0:
+            raise TdpError(1, "tdp_groupjoin_workspace")
+        self.ws = torch.empty(int(n), dtype=torch.uint8, device=dev)
+        self.keys = torch.empty(max(self.cap, 1), dtype=torch.int32, device=dev)
+        self.out = [torch.empty(max(self.cap, 1), dtype=torch.int64, device=dev) for _ in self.aggs]
+        self.ngroups = torch.empty(1, dtype=torch.int64, device=dev)
+        self.nmatch = torch.empty(1, dtype=torch.int64, device=dev)
+        self.top_vals = torch.empty(max(self.topk, 1), dtype=torch.int64, device=dev)
+        self.top_keys = torch.empty(max(self.topk, 1), dtype=torch.int32, device=dev)
+        self.k = torch.empty(1, dtype=torch.int64, device=dev)
+        self._agg_arr = agg_array(self.aggs)
+
+    def build(self, cols, key_col, preds=(), d_n=None, status=None):
+        L.call("tdp_groupjoin_build", col_array(cols), len(cols), pred_array(preds), len(preds), self.n_build,
+               _ptr(d_n), int(key_col), self.lo, self.hi, self._agg_arr, len(self.aggs), self.topk, _ptr(self.ws),
+               self.ws.numel(), _ptr(status), _stream())
+
+    def probe(self, cols, key_col, preds=(), n=None, d_n=None, status=None):
+        n = _as_col(cols[key_col]).t.numel() if n is None else int(n)
+        L.call("tdp_groupjoin_probe", col_array(cols), len(cols), pred_array(preds), len(preds), n, _ptr(d_n),
+               int(key_col), self.n_build, self.lo, self.hi, self._agg_arr, len(self.aggs), self.topk,
+               _ptr(self.ws), self.ws.numel(), _ptr(status), _stream())
+
+    def finish(self, status=None):
+        tk = self.topk > 0
+        L.call("tdp_groupjoin_finish", self.n_build, self.lo, self.hi, self._agg_arr, len(self.aggs),
+               _ptr(self.keys), _ptr_array(self.out), self.cap, _ptr(self.ngroups), _ptr(self.nmatch), self.topk,
+               self.topk_agg, _ptr(self.top_vals) if tk else None, _ptr(self.top_keys) if tk else None,
+               _ptr(self.k) if tk else None, _ptr(self.ws), self.ws.numel(), _ptr(status), _stream())
+        out = {"keys": [self.keys], "aggs": self.out, "ngroups": self.ngroups, "nmatch": self.nmatch}
+        if tk:
+            out.update({"top_vals": self.top_vals, "top_keys": self.top_keys, "k": self.k})
+        return out
+
+
 # ---------------------------------------------------------------- top-k
 
 def topk(vals, keys, k, d_n=None, status=None):

@@ -97,6 +97,9 @@ class ShippingPriority:
         # probe output capacity: every fact row (host-side upper bound)
         self.cap = self.n_fact
         self.status = ops.new_status(dev)
+        # group-join: dimension keys bounded by 1..n_dim (the key metadata)
+        self.gj = ops.GroupJoin(self.n_dim, 1, self.n_dim, [("sum_mul_kminus", 2, 3, 100)], topk=10, topk_agg=0,
+                                device=dev) if groupjoin else None
 
     def run(self):
         if self.groupjoin:
@@ -107,6 +110,7 @@ class ShippingPriority:
         pr = ops.join_probe(self.table, [self.f["key"], self.f["date"], self.f["price"], self.f["disc"]], 0,
                             preds=[(1, ">", 1200)], gather=[0, 2, 3], capacity=self.cap, rowids=False,
                             payload=False, status=st)
+        self.last_probe = pr
         key_c, price_c, disc_c = pr["gathered"]
         gb = ops.groupby_agg([ops.Col(key_c, 1, self.n_dim), price_c, disc_c], [0],
                              [("sum_mul_kminus", 1, 2, 100)], n=self.cap, nsel=pr["count"],
@@ -116,20 +120,35 @@ class ShippingPriority:
         return {"top_vals": ov, "top_keys": okk, "k": dk, "ngroups": gb["ngroups"], "nmatch": pr["count"],
                 "groups": gb, "status": st}
 
-    def run_groupjoin(self):
-        st = self.status
-        # dimension keys are bounded by 1..n_dim (the dimension's key metadata)
-        gb = ops.groupjoin([self.d["key"], self.d["segment"]], 0,
-                           [self.f["key"], self.f["date"], self.f["price"], self.f["disc"]], 0, 1, self.n_dim,
-                           [("sum_mul_kminus", 2, 3, 100)], build_preds=[(1, "==", 2)],
-                           probe_preds=[(1, ">", 1200)], status=st, topk=10, topk_agg=0)
+    # the three steps of the group-join plan (timed one by one by the benchmark)
+    def gj_build(self):
+        self.gj.build([self.d["key"], self.d["segment"]], 0, preds=[(1, "==", 2)], status=self.status)
+
+    def gj_probe(self):
+        self.gj.probe([self.f["key"], self.f["date"], self.f["price"], self.f["disc"]], 0, preds=[(1, ">", 1200)],
+                      status=self.status)
+
+    def gj_finish(self):
+        gb = self.gj.finish(status=self.status)
         return {"top_vals": gb["top_vals"], "top_keys": gb["top_keys"], "k": gb["k"], "ngroups": gb["ngroups"],
-                "nmatch": gb["nmatch"], "groups": gb, "status": st}
+                "nmatch": gb["nmatch"], "groups": gb, "status": self.status}
+
+    def run_groupjoin(self):
+        self.gj_build()
+        self.gj_probe()
+        return self.gj_finish()
 
 
 class JoinChain:
-    def __init__(self, d: dict, n_category: int = 100000):
+    """fused=True: the last join and the GROUP BY category run as one
+    probe + aggregate call.  fused=False: the last probe writes (category,
+    payload) per matched probe row and a separate group-by (groupby_strategy,
+    e.g. "sort" for the onesweep radix-sort path) aggregates them."""
+
+    def __init__(self, d: dict, n_category: int = 100000, fused: bool = True, groupby_strategy: str = "auto"):
         self.d = d  # third_pk, third_cat, build_pk, build_fk2, probe_fk, probe_payload
+        self.fused = fused
+        self.groupby_strategy = groupby_strategy
         dev = d["probe_fk"].device
         self.n_third = d["third_pk"].numel()
         self.n_build = d["build_pk"].numel()
@@ -148,8 +167,17 @@ class JoinChain:
                             rowids=False, status=st)
         ops.join_build([p1["gathered"][0], p1["payload"]], 0, payload_col=1, n=self.n_build, d_n=p1["count"],
                        table=self.t2, nslots=self.t2.numel(), status=st)
-        out = ops.join_probe_agg(self.t2, [d["probe_fk"], d["probe_payload"]], 0, 0, self.n_category - 1,
-                                 [("sum", 1), ("count",)], status=st)
+        if self.fused:
+            out = ops.join_probe_agg(self.t2, [d["probe_fk"], d["probe_payload"]], 0, 0, self.n_category - 1,
+                                     [("sum", 1), ("count",)], status=st)
+        else:
+            p2 = ops.join_probe(self.t2, [d["probe_fk"], d["probe_payload"]], 0, gather=[1], capacity=self.n_probe,
+                                rowids=False, status=st)
+            gb = ops.groupby_agg([ops.Col(p2["payload"], 0, self.n_category - 1), p2["gathered"][0]], [0],
+                                 [("sum", 1), ("count",)], n=self.n_probe, nsel=p2["count"],
+                                 strategy=self.groupby_strategy, capacity=self.n_category, status=st)
+            out = {"keys": gb["keys"][0], "aggs": gb["aggs"], "ngroups": gb["ngroups"], "status": st,
+                   "probe_matches": p2["count"]}
         out["build_matches"] = p1["count"]
         return out
 

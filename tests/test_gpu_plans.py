@@ -133,21 +133,28 @@ def test_join_chain_plan_matches_oracle(case):
     d = gen.chain_tables(e["probe_rows"], e["build_rows"], e["third_rows"], e["seed"])
     dd = {k: cu(v.astype(np.int32) if k == "probe_fk" else v) for k, v in d.items()}
     del d
-    jc = plans.JoinChain(dd)
-    out = jc.run()
-    ops.check(jc.status, case)
-    assert int(out["build_matches"].item()) == e["build_matches"]
-    g = int(out["ngroups"].item())
-    assert g == e["ngroups"]
-    keys, sums, cnts = np_(out["keys"], g), np_(out["aggs"][0], g), np_(out["aggs"][1], g)
-    idx = e["sample_idx"]
-    assert keys[idx].tolist() == e["sample_keys"]
-    assert sums[idx].tolist() == e["sample_sums"]
-    assert cnts[idx].tolist() == e["sample_counts"]
-    assert int(cnts.sum()) == e["probe_matches"]
-    assert sha(keys, np.int32) == e["keys_sha256"]
-    assert sha(sums, np.int64) == e["sums_sha256"]
-    assert sha(cnts, np.int64) == e["counts_sha256"]
+    # fused probe + group-by, and the separate probe -> group-by on the
+    # onesweep sort path and on the small-domain path
+    for fused, strategy in ((True, "auto"), (False, "sort"), (False, "small_domain")):
+        jc = plans.JoinChain(dd, fused=fused, groupby_strategy=strategy)
+        out = jc.run()
+        ops.check(jc.status, "%s fused=%s %s" % (case, fused, strategy))
+        assert int(out["build_matches"].item()) == e["build_matches"]
+        if not fused:
+            assert int(out["probe_matches"].item()) == e["probe_matches"]
+        g = int(out["ngroups"].item())
+        assert g == e["ngroups"]
+        keys, sums, cnts = np_(out["keys"], g), np_(out["aggs"][0], g), np_(out["aggs"][1], g)
+        idx = e["sample_idx"]
+        assert keys[idx].tolist() == e["sample_keys"]
+        assert sums[idx].tolist() == e["sample_sums"]
+        assert cnts[idx].tolist() == e["sample_counts"]
+        assert int(cnts.sum()) == e["probe_matches"]
+        assert sha(keys, np.int32) == e["keys_sha256"]
+        assert sha(sums, np.int64) == e["sums_sha256"]
+        assert sha(cnts, np.int64) == e["counts_sha256"]
+        del jc, out
+        torch.cuda.empty_cache()
 
 
 def test_pricing_summary_60M_both_strategies_match_oracle():

@@ -719,3 +719,34 @@ def test_groupjoin_widest_key_domain():
         assert np.array_equal(np_(out["aggs"][j], g), aggs[:, j])
     ev, ek = R.topk(aggs[:, 0], keys[:, 0], 5)
     assert np.array_equal(np_(out["top_vals"], 5), ev) and np.array_equal(np_(out["top_keys"], 5), ek)
+
+
+def test_groupjoin_steps_with_several_probe_batches():
+    """build once, probe three batches (their own columns, each with its own
+    fused filter), finish: equal to one probe over the concatenated rows, and
+    to the oracle; the same object reused for a second round gives the same
+    result (the build step clears the workspace)."""
+    lo, hi, nb, npr = 1, 50000, 20000, 600_001
+    bkey, bseg, pkey, pdate, pflag, pv, pw, p32 = _groupjoin_case(nb, npr, 41, lo, hi)
+    aggs = [("sum_mul_kminus", 4, 5, 100), ("count",), ("avg", 4)]
+    gj = ops.GroupJoin(nb, lo, hi, aggs, topk=7, topk_agg=0, device=DEV)
+    cuts = [0, 150_000, 150_001, npr]
+    for _ in range(2):
+        gj.build([cu(bkey), cu(bseg)], 0, preds=[(1, "==", 2)])
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            pc = [cu(pkey[a:b]), cu(pdate[a:b]), cu(pflag[a:b]), cu(pkey[a:b]), cu(pv[a:b]), cu(pw[a:b])]
+            gj.probe(pc, 0, preds=[(1, ">", 1200), (2, "!=", 1)])
+        out = gj.finish()
+        torch.cuda.synchronize()
+        bsel = R.filter([(bseg, "==", 2)], nb)
+        psel = R.filter([(pdate, ">", 1200), (pflag, "!=", 1)], npr)
+        prow, _, _ = R.join(bkey, pkey, bsel=bsel, psel=psel)
+        keys, ea = R.groupby([pkey], [("sum_mul_kminus", pv, pw, 100), ("count", None, None, None),
+                                      ("avg", pv, None, None)], npr, sel=prow)
+        g = int(out["ngroups"].item())
+        assert g == len(keys) and int(out["nmatch"].item()) == len(prow)
+        assert np.array_equal(np_(out["keys"][0], g), keys[:, 0])
+        for j in range(3):
+            assert np.array_equal(np_(out["aggs"][j], g), ea[:, j])
+        ev, ek = R.topk(ea[:, 0], keys[:, 0], 7)
+        assert np.array_equal(np_(out["top_vals"], 7), ev) and np.array_equal(np_(out["top_keys"], 7), ek)

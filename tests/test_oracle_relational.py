@@ -160,3 +160,33 @@ def test_mutation_in_oracle_is_caught():
     good = R.filter(preds, 50).tolist()
     assert good == brute.filter(preds, 50)
     assert good[:-1] != brute.filter(preds, 50)
+
+
+def test_parallel_oracle_equals_single_thread():
+    """The OpenMP row-partitioned filter, join and group-by (used to time the
+    CPU baseline) give exactly the single-threaded oracle's results: row order,
+    group order, every aggregate including AVG rounding, N:M join order."""
+    from oracle import relational as R
+    r = np.random.default_rng(77)
+    n = 50_003
+    a = r.integers(-5, 6, n).astype(np.int8)
+    b = r.integers(0, 300, n).astype(np.int32)
+    v = r.integers(-10**9, 10**9, n).astype(np.int64)
+    w = r.integers(0, 11, n).astype(np.int64)
+    preds = [(a, "!=", 0), (b, "<", 250)]
+    sel = R.filter(preds, n)
+    assert np.array_equal(R.filter(preds, n, parallel=True), sel)
+    aggs = [("count", None, None, None), ("sum", v, None, None), ("sum_mul_kminus", v, w, 100), ("avg", v, None, None),
+            ("min", v, None, None), ("max", b, None, None)]
+    k1, a1 = R.groupby([a, b], aggs, n, sel=sel)
+    k2, a2 = R.groupby([a, b], aggs, n, sel=sel, parallel=True)
+    assert np.array_equal(k1, k2) and np.array_equal(a1, a2)
+    k1, a1 = R.groupby([a], aggs, n)
+    k2, a2 = R.groupby([a], aggs, n, parallel=True)
+    assert np.array_equal(k1, k2) and np.array_equal(a1, a2)
+    bk = r.integers(0, 2000, 3000).astype(np.int32)  # duplicate build keys: N:M
+    pk = r.integers(0, 2200, 20001).astype(np.int32)
+    p1, b1, d1 = R.join(bk, pk)
+    p2, b2, d2 = R.join(bk, pk, parallel=True)
+    assert d1 and d2 and np.array_equal(p1, p2) and np.array_equal(b1, b2)
+    assert R.threads() >= 1

@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "filter_api.cuh"
 #include "groupby.cuh"
 #include "topk.cuh"
 
@@ -374,7 +375,7 @@ constexpr int GJR_PROBE_THREADS = 256;
 
 template <int NSMAX>
 __global__ void __launch_bounds__(GJR_PROBE_THREADS, 4)
-    gjr_probe_kernel(PredSet ps, const int32_t *__restrict__ key, int key_vec, long long n_host,
+    gjr_probe_direct_kernel(PredSet ps, const int32_t *__restrict__ key, int key_vec, long long n_host,
                      const long long *d_n, int lo32, unsigned D32, const RankWord *bm, uint32_t *hitw, AggSet as,
                      AccLayout al, long long *acc, unsigned long long *d_nmatch)
 {
@@ -519,6 +520,226 @@ __global__ void __launch_bounds__(GJR_PROBE_THREADS, 4)
         }
         __syncwarp(); // the warp's queue is free for the next chunk
     }
+    if (lane == 0 && matches && d_nmatch)
+        atomicAdd(d_nmatch, matches);
+}
+
+// The same probe with each warp's chunks staged in shared memory: lane 0
+// bulk-copies the key and predicate columns of the warp's next chunk into
+// the other of the warp's two buffers (completion on the warp's own
+// mbarrier) before the warp works on the current one, so the column stream
+// stays in flight while the warp waits on its lookups and gathers.  Chunks
+// that are ragged or whose columns are not 16-byte aligned are loaded by the
+// lanes instead.  Still no block-wide barrier after the set-up.
+constexpr int GJR_MAX_STAGE = 1 + TDP_MAX_PREDS;
+constexpr int GJR_STAGE_MAX_ROW = 24; // bytes of staged columns per row (two buffers per warp)
+
+struct GJRStage {
+    const void *col[GJR_MAX_STAGE]; // [0] the probe key, then each distinct predicate column
+    int32_t size[GJR_MAX_STAGE];
+    int32_t n;
+    int32_t aligned;             // every staged column 16-byte aligned
+    int32_t pred[TDP_MAX_PREDS]; // stage index of predicate p's column
+};
+
+// (Measured: pipelining the warp's chunks -- chunk i's lookups in flight
+// while chunk i-1's hits are gathered, with two hit queues per warp -- cost
+// one resident block per SM for the second queue and ran slower, 314 vs
+// 289 us on the 60M-row probe.)
+template <int NSMAX>
+__global__ void __launch_bounds__(GJR_PROBE_THREADS, 4)
+    gjr_probe_kernel(PredSet ps, GJRStage sg, long long n_host, const long long *d_n, int lo32, unsigned D32,
+                     const RankWord *bm, uint32_t *hitw, AggSet as, AccLayout al, long long *acc,
+                     unsigned long long *d_nmatch, int32_t *d_status, uint32_t limit)
+{
+    constexpr int NB = 2;                      // queue entries per lane in flight in phase B
+    constexpr int VS = NSMAX <= 4 ? NSMAX : 1; // slots gathered ahead of the atomics
+    constexpr int WARPS = GJR_PROBE_THREADS / 32;
+    const long long n = d_n ? min(*d_n, n_host) : n_host;
+    extern __shared__ __align__(128) unsigned char gjr_smem[]; // [warp][2][GJR_CHUNK x row bytes]
+    __shared__ __align__(8) uint64_t s_bar[WARPS][2];
+    __shared__ uint16_t s_q[WARPS][1][GJR_CHUNK];
+    __shared__ uint32_t s_c[WARPS][1][GJR_CHUNK];
+    __shared__ int s_ops[TDP_MAX_AGGS + 1];
+    __shared__ uint32_t s_off[GJR_MAX_STAGE];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t row_bytes = 0;
+    for (int c = 0; c < sg.n; c++)
+        row_bytes += sg.size[c];
+    if (threadIdx.x <= TDP_MAX_AGGS)
+        s_ops[threadIdx.x] = slot_op(as, threadIdx.x);
+    if (threadIdx.x == 0) {
+        uint32_t off = 0;
+        for (int c = 0; c < sg.n; c++) {
+            s_off[c] = off;
+            off += GJR_CHUNK * sg.size[c];
+        }
+    }
+    if (lane == 0) {
+        mbar_init(&s_bar[warp][0], 1);
+        mbar_init(&s_bar[warp][1], 1);
+    }
+    __syncthreads();
+    const int NS = as.nslots;
+    const bool count = al.cs == 0;
+    const uint64_t stream_pol = l2_evict_first(), table_pol = l2_evict_last();
+    const unsigned lt = lanemask_lt();
+    const long long nchunks = (n + GJR_CHUNK - 1) / GJR_CHUNK;
+    const long long wstride = (long long)gridDim.x * WARPS;
+    unsigned char *wbuf = gjr_smem + (size_t)warp * 2 * GJR_CHUNK * row_bytes;
+    auto bulk_ok = [&](long long c) { return sg.aligned && (c + 1) * GJR_CHUNK <= n; };
+    auto issue = [&](long long c, int b) { // lane 0 only
+        unsigned char *buf = wbuf + (size_t)b * GJR_CHUNK * row_bytes;
+        fence_proxy_async_smem(); // the lanes' earlier reads of this buffer come first
+        mbar_arrive_expect_tx(&s_bar[warp][b], GJR_CHUNK * row_bytes);
+        for (int k = 0; k < sg.n; k++)
+            bulk_load_hint(buf + s_off[k], (const char *)sg.col[k] + (size_t)c * GJR_CHUNK * sg.size[k],
+                           GJR_CHUNK * sg.size[k], &s_bar[warp][b], stream_pol);
+    };
+    // gathers and atomics of one queued chunk (rows base + s_q)
+    auto drain = [&](int qb, unsigned qn, long long base) {
+        for (unsigned i0 = 0; i0 < qn; i0 += 32 * NB) {
+            long long row[NB];
+            uint32_t cd[NB];
+            long long va[NB][VS], vb[NB][VS];
+#pragma unroll
+            for (int u = 0; u < NB; u++) {
+                const unsigned i = i0 + lane + 32 * u;
+                row[u] = i < qn ? base + s_q[warp][qb][i] : -1;
+                cd[u] = i < qn ? s_c[warp][qb][i] : 0u;
+                if constexpr (NSMAX <= 4) {
+                    if (row[u] >= 0) {
+#pragma unroll
+                        for (int sl = 1; sl < VS; sl++) {
+                            if (sl >= NS)
+                                break;
+                            va[u][sl] = gather_int(as.sa[sl], as.sadt[sl], row[u], stream_pol);
+                            vb[u][sl] = as.sop[sl] == TDP_AGG_SUM_MUL_KMINUS
+                                            ? gather_int(as.sb[sl], as.sbdt[sl], row[u], stream_pol)
+                                            : 0;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < NB; u++) {
+                if (row[u] < 0)
+                    continue;
+                long long *arow = acc + (long long)cd[u] * al.stride; // slot s at arow[s - cs]
+                if (count)
+                    atomicAdd((unsigned long long *)arow, 1ull);
+                if constexpr (NSMAX <= 4) {
+#pragma unroll
+                    for (int sl = 1; sl < VS; sl++) {
+                        if (sl >= NS)
+                            break;
+                        long long v = va[u][sl];
+                        if (as.sop[sl] == TDP_AGG_SUM_MUL_KMINUS)
+                            v *= as.sk[sl] - vb[u][sl];
+                        acc_update(arow + (sl - al.cs), s_ops[sl], v);
+                    }
+                } else {
+                    for (int sl = 1; sl < NS; sl++) {
+                        long long v = gather_int(as.sa[sl], as.sadt[sl], row[u], stream_pol);
+                        if (as.sop[sl] == TDP_AGG_SUM_MUL_KMINUS)
+                            v *= as.sk[sl] - gather_int(as.sb[sl], as.sbdt[sl], row[u], stream_pol);
+                        acc_update(arow + (sl - al.cs), s_ops[sl], v);
+                    }
+                }
+            }
+        }
+    };
+    const long long c0 = (long long)blockIdx.x * WARPS + warp;
+    if (lane == 0 && c0 < nchunks && bulk_ok(c0))
+        issue(c0, 0);
+    bool late = false;
+    unsigned long long matches = 0;
+    uint32_t phase = 0;      // bit b: parity of buffer b's next phase
+    int it = 0;
+    for (long long c = c0; c < nchunks; c += wstride, it++) {
+        const int b = it & 1;
+        unsigned char *buf = wbuf + (size_t)b * GJR_CHUNK * row_bytes;
+        const long long cn = c + wstride;
+        if (lane == 0 && cn < nchunks && bulk_ok(cn))
+            issue(cn, b ^ 1); // that buffer was consumed in the previous iteration
+        const long long base = c * GJR_CHUNK;
+        if (bulk_ok(c)) {
+            late |= !mbar_wait(&s_bar[warp][b], (phase >> b) & 1u, limit);
+            phase ^= 1u << b;
+        } else {
+            for (int k = 0; k < sg.n; k++) {
+                unsigned char *d = buf + s_off[k];
+                for (int i = lane; i < GJR_CHUNK; i += 32) {
+                    if (base + i >= n)
+                        break;
+                    switch (sg.size[k]) {
+                    case 8: ((long long *)d)[i] = ((const long long *)sg.col[k])[base + i]; break;
+                    case 4: ((int32_t *)d)[i] = ((const int32_t *)sg.col[k])[base + i]; break;
+                    default: d[i] = ((const uint8_t *)sg.col[k])[base + i]; break;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        // ---- chunk c: predicates, then its lookups go out
+        const long long left = n - base; // > 0
+        unsigned msk[GJR_STEPS];
+#pragma unroll
+        for (int j = 0; j < GJR_STEPS; j++) {
+            const long long r = j * 128 + 4 * lane;
+            msk[j] = r + 3 < left ? 0xfu : (r + 2 < left ? 0x7u : (r + 1 < left ? 0x3u : (r < left ? 0x1u : 0u)));
+        }
+        for (int p = 0; p < ps.n; p++)
+            pred_test_smem<GJR_STEPS>(ps, p, buf + s_off[sg.pred[p]], 4 * lane, msk);
+        const int32_t *skey = (const int32_t *)buf; // stage 0 at offset 0
+        unsigned long long wv[GJR_STEPS * 4];
+        unsigned dd[GJR_STEPS * 4];
+        unsigned look = 0;
+#pragma unroll
+        for (int j = 0; j < GJR_STEPS; j++) {
+            const int4 k4 = *(const int4 *)(skey + j * 128 + 4 * lane);
+            const int kk[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int q = j * 4 + e;
+                dd[q] = (unsigned)(kk[e] - lo32);
+                if ((msk[j] >> e & 1u) && dd[q] < D32) {
+                    look |= 1u << q;
+                    wv[q] = ldg_hint((const unsigned long long *)(bm + (dd[q] >> 5)), table_pol);
+                }
+            }
+        }
+        // ---- chunk c: hits to the queue
+        unsigned qbase = 0;
+#pragma unroll
+        for (int q = 0; q < GJR_STEPS * 4; q++) {
+            bool hit = false;
+            uint32_t code = 0;
+            if (look >> q & 1u) {
+                const uint32_t bits = (uint32_t)wv[q];
+                const unsigned bp = dd[q] & 31u;
+                if ((bits >> bp) & 1u) {
+                    hit = true;
+                    code = (uint32_t)(wv[q] >> 32) + __popc(bits & ((1u << bp) - 1u));
+                    atomicOr(&hitw[dd[q] >> 5], 1u << bp);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const unsigned pos = qbase + __popc(bal & lt);
+                s_q[warp][0][pos] = (uint16_t)((q / 4) * 128 + 4 * lane + (q & 3));
+                s_c[warp][0][pos] = code;
+            }
+            qbase += __popc(bal);
+        }
+        matches += qbase; // lane 0's count is the warp's
+        __syncwarp(); // chunk c's queue written
+        // ---- chunk c: gathers and atomics of its hits
+        drain(0, qbase, base);
+        __syncwarp(); // the queue and the buffer are free for the next chunk
+    }
+    if (late)
+        set_status(d_status, TDP_ERR_TIMEOUT);
     if (lane == 0 && matches && d_nmatch)
         atomicAdd(d_nmatch, matches);
 }
@@ -836,15 +1057,53 @@ static bool coop_grid(const void *kern, long long W, int wpt, int Gmax, int *G, 
 template <int NSMAX>
 static tdp_status launch_gjr_probe(const PredSet &ps, const int32_t *key, long long n, const long long *d_n,
                                    long long lo, long long D, const RankWord *bm, uint32_t *hitw, const AggSet &as,
-                                   AccLayout al, long long *acc, unsigned long long *d_nmatch, cudaStream_t s)
+                                   AccLayout al, long long *acc, unsigned long long *d_nmatch, int32_t *d_status,
+                                   cudaStream_t s)
 {
     const long long chunks = (n + GJR_CHUNK - 1) / GJR_CHUNK;
     const long long want = (chunks + GJR_PROBE_THREADS / 32 - 1) / (GJR_PROBE_THREADS / 32);
     const unsigned grid = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() * 4));
+    // the staged columns: the key, then each distinct predicate column
+    GJRStage sg;
+    sg.n = 0;
+    sg.aligned = 1;
+    auto add = [&](const void *col, int size) -> int {
+        for (int c = 0; c < sg.n; c++)
+            if (sg.col[c] == col && sg.size[c] == size)
+                return c;
+        sg.col[sg.n] = col;
+        sg.size[sg.n] = size;
+        sg.aligned = sg.aligned && ((uintptr_t)col % 16) == 0;
+        return sg.n++;
+    };
+    for (int c = 0; c < GJR_MAX_STAGE; c++) {
+        sg.col[c] = nullptr;
+        sg.size[c] = 0;
+    }
+    add(key, 4);
+    for (int p = 0; p < TDP_MAX_PREDS; p++)
+        sg.pred[p] = p < ps.n ? add(ps.col[p], dtype_size(ps.dt[p])) : 0;
+    int row_bytes = 0;
+    for (int c = 0; c < sg.n; c++)
+        row_bytes += sg.size[c];
     // keys are int32 and [lo, hi] lies in the int32 range with D <= 2^31, so
     // (unsigned)(key - lo) < D (32-bit arithmetic) is the bounds test
-    gjr_probe_kernel<NSMAX><<<grid, GJR_PROBE_THREADS, 0, s>>>(ps, key, ((uintptr_t)key % 16) == 0, n, d_n, (int)lo,
-                                                               (unsigned)D, bm, hitw, as, al, acc, d_nmatch);
+    if (row_bytes <= GJR_STAGE_MAX_ROW) {
+        const size_t smem = (size_t)(GJR_PROBE_THREADS / 32) * 2 * GJR_CHUNK * row_bytes;
+        auto kern = gjr_probe_kernel<NSMAX>;
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GJR_PROBE_THREADS, smem) != cudaSuccess ||
+            per_sm < 1)
+            return TDP_ERR_CUDA;
+        // persistent: one wave of resident blocks
+        const unsigned g = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() * per_sm));
+        kern<<<g, GJR_PROBE_THREADS, smem, s>>>(ps, sg, n, d_n, (int)lo, (unsigned)D, bm, hitw, as, al, acc, d_nmatch,
+                                                d_status, spin_limit());
+    } else {
+        gjr_probe_direct_kernel<NSMAX><<<grid, GJR_PROBE_THREADS, 0, s>>>(
+            ps, key, ((uintptr_t)key % 16) == 0, n, d_n, (int)lo, (unsigned)D, bm, hitw, as, al, acc, d_nmatch);
+    }
     return launch_status();
 }
 
@@ -1036,10 +1295,11 @@ extern "C" tdp_status tdp_groupjoin_probe(const tdp_col *probe_cols, int32_t npr
     const int32_t *pk = (const int32_t *)probe_cols[probe_key_col].data;
     cudaStream_t s = (cudaStream_t)stream;
     if (as.nslots <= 2)
-        return launch_gjr_probe<2>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5], s);
+        return launch_gjr_probe<2>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5], d_status, s);
     if (as.nslots <= 4)
-        return launch_gjr_probe<4>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5], s);
-    return launch_gjr_probe<TDP_MAX_AGGS + 1>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5], s);
+        return launch_gjr_probe<4>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5], d_status, s);
+    return launch_gjr_probe<TDP_MAX_AGGS + 1>(pps, pk, n_probe, dn, key_lo, D, bm, hitw, as, al, acc, &cnt[5],
+                                              d_status, s);
 }
 
 extern "C" tdp_status tdp_groupjoin_finish(int64_t n_build, int64_t key_lo, int64_t key_hi, const tdp_agg *aggs,

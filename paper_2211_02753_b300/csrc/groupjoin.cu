@@ -709,29 +709,32 @@ __global__ void __launch_bounds__(GJR_PROBE_THREADS, 4)
                 }
             }
         }
-        // ---- chunk c: hits to the queue
-        unsigned qbase = 0;
+        // ---- chunk c: hits to the queue (one warp scan of the lanes' counts)
+        unsigned hm = 0;
 #pragma unroll
-        for (int q = 0; q < GJR_STEPS * 4; q++) {
-            bool hit = false;
-            uint32_t code = 0;
-            if (look >> q & 1u) {
+        for (int q = 0; q < GJR_STEPS * 4; q++)
+            if ((look >> q & 1u) && (((uint32_t)wv[q] >> (dd[q] & 31u)) & 1u))
+                hm |= 1u << q;
+        const unsigned nh = __popc(hm);
+        unsigned incl = nh;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += u;
+        }
+        const unsigned qbase = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned pos = incl - nh;
+#pragma unroll
+        for (int q = 0; q < GJR_STEPS * 4; q++)
+            if (hm >> q & 1u) {
                 const uint32_t bits = (uint32_t)wv[q];
                 const unsigned bp = dd[q] & 31u;
-                if ((bits >> bp) & 1u) {
-                    hit = true;
-                    code = (uint32_t)(wv[q] >> 32) + __popc(bits & ((1u << bp) - 1u));
-                    atomicOr(&hitw[dd[q] >> 5], 1u << bp);
-                }
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const unsigned pos = qbase + __popc(bal & lt);
                 s_q[warp][0][pos] = (uint16_t)((q / 4) * 128 + 4 * lane + (q & 3));
-                s_c[warp][0][pos] = code;
+                s_c[warp][0][pos] = (uint32_t)(wv[q] >> 32) + __popc(bits & ((1u << bp) - 1u));
+                atomicOr(&hitw[dd[q] >> 5], 1u << bp);
+                pos++;
             }
-            qbase += __popc(bal);
-        }
         matches += qbase; // lane 0's count is the warp's
         __syncwarp(); // chunk c's queue written
         // ---- chunk c: gathers and atomics of its hits

@@ -18,6 +18,10 @@ Workload shapes (all synthetic; the paper's own datasets are not available):
   build table, build rows with Zipf(0.5) foreign keys over a third table,
   int64 payloads U[0,1e9], int32 categories U[0,99999].
 * soft-query rows: fp32 x ~ N(0,1), fp32 v ~ U[0,100], int32 group id.
+* string columns (offsets + bytes): rows drawn from a seeded vocabulary of
+  random lower-case words, some of them prefixes of others.
+* N:M join tables: build keys with a fixed number of rows per distinct key
+  on average (Poisson), probe keys uniform over a wider range.
 * glyph grids: 4x4 cells of 28x28 uint8 glyphs drawn from 10 seeded stroke
   templates with affine jitter and Gaussian noise (stand-in for the paper's
   MNIST grids, Sec. 5.5).
@@ -246,3 +250,56 @@ def cnn_params(seed: int) -> dict:
             bound = 1.0 / math.sqrt(fan_in)
         out[name] = g.uniform(-bound, bound, size=shape).astype(np.float32)
     return out
+
+
+# ---------------------------------------------------------------------------
+# string columns and N:M join tables
+# ---------------------------------------------------------------------------
+
+def vocabulary(n_words: int, seed: int, min_len: int = 1, max_len: int = 24) -> list:
+    """n_words distinct random lower-case byte strings; about one in ten is a
+    proper prefix of another word of the list."""
+    r = rng(seed, 61)
+    words = set()
+    out = []
+    while len(out) < n_words:
+        ln = int(r.integers(min_len, max_len + 1))
+        w = bytes(r.integers(97, 123, ln, dtype=np.int64).astype(np.uint8))
+        if out and r.random() < 0.1:
+            base = out[int(r.integers(0, len(out)))]
+            if len(base) > 1:
+                w = base[:int(r.integers(1, len(base)))]
+        if w not in words:
+            words.add(w)
+            out.append(w)
+    return out
+
+
+def string_column(n: int, n_words: int, seed: int, max_len: int = 24):
+    """An offsets + bytes column of n rows drawn uniformly from a vocabulary
+    of n_words words.  Returns (offsets int32[n+1], bytes uint8, vocabulary,
+    row word index int64[n])."""
+    vocab = vocabulary(n_words, seed, 1, max_len)
+    idx = rng(seed, 62).integers(0, n_words, n, dtype=np.int64)
+    lens = np.array([len(w) for w in vocab], np.int64)[idx]
+    offsets = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    pool = np.frombuffer(b"".join(vocab), dtype=np.uint8)
+    starts = np.zeros(n_words + 1, np.int64)
+    np.cumsum([len(w) for w in vocab], out=starts[1:])
+    # row bytes: the vocabulary word's bytes, row after row
+    src = np.repeat(starts[idx], lens) + (np.arange(offsets[-1]) - np.repeat(offsets[:-1], lens))
+    data = pool[src] if len(src) else np.zeros(0, np.uint8)
+    return offsets.astype(np.int32), data.astype(np.uint8), vocab, idx
+
+
+def nm_join_tables(n_build: int, n_probe: int, dup: float, seed: int) -> dict:
+    """Build keys in 1..K with K = n_build / dup (about dup rows per key),
+    probe keys uniform in 1..2K (half of them match), int64 payloads."""
+    k = max(1, int(n_build / dup))
+    return {
+        "build_key": _uniform_int(seed, 71, 1, k, n_build, np.int32),
+        "build_pay": _uniform_int(seed, 72, 0, 1_000_000, n_build, np.int64),
+        "probe_key": _uniform_int(seed, 73, 1, 2 * k, n_probe, np.int32),
+        "probe_date": _uniform_int(seed, 74, 0, 2556, n_probe, np.int32),
+    }

@@ -331,6 +331,40 @@ tdp_status tdp_join(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pr
                     int32_t ngather, void *const *gather_out, int64_t capacity, int64_t *d_count,
                     void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
 
+/* Workspace bytes for tdp_join_nm. */
+size_t tdp_join_nm_workspace(int64_t n_build, int64_t n_probe);
+
+/*
+ * Inner equi-join with repeated build keys (N:M): every (probe row, build
+ * row) pair with equal int32 keys, ordered by probe row and, for one probe
+ * row, by build row -- the SQL inner join of Sec. 2's relational operators
+ * without the unique-key restriction of tdp_join.
+ *
+ *   build_cols / build_preds   build side and its fused filter; rows
+ *                              0..n_build-1, or 0..min(n_build, *d_nbuild)-1
+ *   probe_cols / probe_preds   probe side and its fused filter; rows
+ *                              0..n_probe-1, or 0..min(n_probe, *d_nprobe)-1
+ *   out_probe_row, out_build_row
+ *                              device int32[capacity]: the pairs in that order
+ *   d_count                    device int64: the number of pairs (may exceed
+ *                              both input sizes); more than capacity writes
+ *                              capacity pairs and sets TDP_ERR_CAPACITY
+ *
+ * The qualifying build rows are sorted by key with the stable radix sort
+ * (equal keys keep build-row order); the runs of equal keys go into the hash
+ * table as one entry each (key -> run); every probe row looks its key up once,
+ * the run lengths give every probe row its output offset, and the row then
+ * writes its run.  As in tdp_join_build, the key INT32_MIN cannot be stored:
+ * such build rows set TDP_ERR_OVERFLOW and are dropped, and such probe rows
+ * match nothing.
+ */
+tdp_status tdp_join_nm(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pred *build_preds,
+                       int32_t nbuild_preds, int64_t n_build, const int64_t *d_nbuild, int32_t build_key_col,
+                       const tdp_col *probe_cols, int32_t nprobe_cols, const tdp_pred *probe_preds,
+                       int32_t nprobe_preds, int64_t n_probe, const int64_t *d_nprobe, int32_t probe_key_col,
+                       int32_t *out_probe_row, int32_t *out_build_row, int64_t capacity, int64_t *d_count,
+                       void *ws, size_t ws_bytes, int32_t *d_status, tdp_stream_t stream);
+
 /* Workspace bytes for tdp_join_probe_agg. */
 size_t tdp_join_probe_agg_workspace(int64_t n, int64_t domain, int32_t naggs);
 
@@ -436,6 +470,34 @@ tdp_status tdp_groupjoin_finish(int64_t n_build, int64_t key_lo, int64_t key_hi,
                                 int64_t *d_nmatch, int32_t topk, int32_t topk_agg, int64_t *out_top_vals,
                                 int32_t *out_top_keys, int64_t *d_topk, void *ws, size_t ws_bytes,
                                 int32_t *d_status, tdp_stream_t stream);
+
+/* ------------------------------------------------------- dictionary codes */
+
+/* Workspace bytes for tdp_dict_encode (0 when the arguments are invalid). */
+size_t tdp_dict_encode_workspace(int64_t n, int32_t max_len);
+
+/*
+ * Order-preserving dictionary encoding of a string column (Sec. 2, Data
+ * Encoding): row i is the byte string bytes[offsets[i] .. offsets[i+1])
+ * (offsets: device int32[n + 1]).  codes[i] (device int32[n]) is the number of
+ * distinct strings of the column smaller than row i's string in bytewise
+ * unsigned lexicographic order (a proper prefix first), so codes compare as
+ * the strings do and can be grouped, joined and sorted in their place (as
+ * bounded keys [0, ndict - 1]).  The dictionary -- the distinct strings in
+ * order -- is written as dict_offsets (device int32[dict_cap + 1]) and
+ * dict_bytes (device uint8[bytes_cap]); *d_ndict and *d_nbytes receive its
+ * sizes (TDP_ERR_CAPACITY when it does not fit; the codes are complete).
+ *
+ * Strings may hold up to max_len bytes (1..32): longer rows set
+ * TDP_ERR_OVERFLOW and are encoded as the empty string.  The rows are sorted
+ * by (zero-padded 8-byte words, length) with a stable LSD radix sort (one
+ * pass for the length, then one per word from the last), and one pass over
+ * the sorted rows numbers the runs of equal strings.
+ */
+tdp_status tdp_dict_encode(const int32_t *offsets, const uint8_t *bytes, int64_t n, int32_t max_len, int32_t *codes,
+                           int32_t *dict_offsets, uint8_t *dict_bytes, int64_t dict_cap, int64_t bytes_cap,
+                           int64_t *d_ndict, int64_t *d_nbytes, void *ws, size_t ws_bytes, int32_t *d_status,
+                           tdp_stream_t stream);
 
 /* ----------------------------------------------------------------- top-k */
 

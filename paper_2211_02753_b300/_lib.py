@@ -77,6 +77,9 @@ SIGNATURES = {
     "tdp_join_workspace": (_sz, [_i64, _i64, _i64]),
     "tdp_join": (_st, [_p, _i32, _p, _i32, _i64, _i32, _i32, _p, _i32, _p, _i32, _i64, _i32, _i64, _p, _p, _p,
                        _i32, _p, _i64, _p, _p, _sz, _p, _p]),
+    "tdp_join_nm_workspace": (_sz, [_i64, _i64]),
+    "tdp_join_nm": (_st, [_p, _i32, _p, _i32, _i64, _p, _i32, _p, _i32, _p, _i32, _i64, _p, _i32, _p, _p, _i64, _p,
+                          _p, _sz, _p, _p]),
     "tdp_join_probe_agg_workspace": (_sz, [_i64, _i64, _i32]),
     "tdp_join_probe_agg": (_st, [_p, _i64, _p, _i32, _p, _i32, _i64, _p, _i32, _i64, _i64, _p, _i32, _p, _p,
                                  _i64, _p, _p, _sz, _p, _p]),
@@ -88,6 +91,8 @@ SIGNATURES = {
                                   _p]),
     "tdp_groupjoin_finish": (_st, [_i64, _i64, _i64, _p, _i32, _p, _p, _i64, _p, _p, _i32, _i32, _p, _p, _p, _p, _sz,
                                    _p, _p]),
+    "tdp_dict_encode_workspace": (_sz, [_i64, _i32]),
+    "tdp_dict_encode": (_st, [_p, _p, _i64, _i32, _p, _p, _p, _i64, _i64, _p, _p, _p, _sz, _p, _p]),
     "tdp_topk_workspace": (_sz, [_i64, _i32]),
     "tdp_topk": (_st, [_p, _p, _i64, _p, _i32, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_soft_workspace": (_sz, [_i64, _i32]),

@@ -42,6 +42,7 @@
 
 #include "filter_api.cuh"
 #include "groupby.cuh"
+#include "coop.cuh"
 #include "topk.cuh"
 
 namespace tdp {
@@ -217,69 +218,12 @@ __global__ void __launch_bounds__(256) gjr_build_kernel(PredSet ps, const int32_
 
 // ----------------------------------------------------------------- 2. rank
 
-// Exclusive block scan of one unsigned per thread; returns the thread's
-// exclusive prefix and (in *total) the block total.
-__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_warp, unsigned *total)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o)
-            incl += u;
-    }
-    if (lane == 31)
-        s_warp[warp] = incl;
-    __syncthreads();
-    unsigned before = 0, all = 0;
-#pragma unroll
-    for (int w = 0; w < GJR_THREADS / 32; w++) {
-        const unsigned t = s_warp[w];
-        before += w < warp ? t : 0;
-        all += t;
-    }
-    *total = all;
-    return before + incl - v;
-}
-
-// Block-wide sum of one value per thread (every thread gets the total).
-__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, unsigned long long *s_red)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads(); // s_red free from an earlier use
-    if (lane == 0)
-        s_red[warp] = v;
-    __syncthreads();
-    unsigned long long t = 0;
-#pragma unroll
-    for (int w = 0; w < GJR_THREADS / 32; w++)
-        t += s_red[w];
-    return t;
-}
-
 // Cooperative passes over the bitmap words (the rank pass and the finalize):
 // thread t of block b owns the WPT consecutive words starting at
 // (b * 256 + t) * WPT, so one block scan of the threads' counts orders all of
 // the block's words.  Every block publishes its total, waits once on a
 // bounded grid-wide barrier for all blocks to have counted, and starts from
 // the sum of the totals of the blocks before it: no chain of tiles.
-__device__ __forceinline__ unsigned long long coop_block_prefix(unsigned long long block_total,
-                                                                unsigned long long *s_red,
-                                                                unsigned long long *totals, unsigned *barrier,
-                                                                uint32_t limit, int32_t *d_status)
-{
-    if (threadIdx.x == 0)
-        st_relaxed_u64(&totals[blockIdx.x], block_total);
-    grid_barrier(barrier, gridDim.x, limit, d_status);
-    unsigned long long before = 0;
-    for (int b = threadIdx.x; b < (int)blockIdx.x; b += GJR_THREADS)
-        before += ld_relaxed_u64(&totals[b]);
-    return block_sum(before, s_red);
-}
 
 // Rank pass: bm[w].rank = set bits before word w; accumulator rows of the
 // build keys set to their initial values; B (all set bits) to *d_nkeys.

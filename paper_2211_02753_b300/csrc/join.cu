@@ -45,8 +45,10 @@
 // global table at the end, then the non-empty groups are compacted in order.
 #include <algorithm>
 
+#include "coop.cuh"
 #include "filter_api.cuh"
 #include "groupby.cuh"
+#include "radix.cuh"
 
 namespace tdp {
 
@@ -902,6 +904,204 @@ static tdp_status launch_probe_agg(const TableView &tv, const PredSet &ps, const
     }
 }
 
+// ----------------------------------------------------------- N:M join
+//
+// Inner equi-join with repeated build keys: every (probe row, build row)
+// pair with equal keys, in probe-row order and, for one probe row, in
+// build-row order.
+//   1. the build side's qualifying rows and their keys (the filter kernel,
+//      fused gather), the keys made unsigned order-preserving (sign bit
+//      flipped) and sorted with their row ids (onesweep radix sort, stable:
+//      equal keys keep build-row order);
+//   2. the runs of equal keys (cooperative pass): the distinct keys in order
+//      and the start of each run (CSR offsets, one more than the runs);
+//   3. the distinct keys into the open-addressing table with their run
+//      number as payload (tdp_join_build, unique keys);
+//   4. probe (cooperative): every qualifying probe row looks its key up once
+//      and keeps the run number; the run lengths give each block, and each
+//      thread, its output offset; then every probe row writes its run's
+//      build rows in order.
+
+constexpr int NM_IPT = 8; // elements per thread per span of the cooperative passes
+
+__global__ void nm_pack_kernel(const int32_t *key, long long n_max, const long long *d_n, uint32_t *ukey)
+{
+    const long long n = min(*d_n, n_max);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        ukey[i] = (uint32_t)key[i] ^ 0x80000000u;
+}
+
+// Runs of equal keys in the sorted keys skey[0..nb): dkey[u] the u-th
+// distinct key (signed), start[u] its first position; start[U] = nb, *d_runs
+// = U.
+__global__ void __launch_bounds__(COOP_THREADS) nm_runs_kernel(const uint32_t *skey, long long nb_max,
+                                                               const long long *d_nb, int rounds, int32_t *dkey,
+                                                               int32_t *start, long long *d_runs,
+                                                               unsigned long long *totals, unsigned *barrier,
+                                                               int32_t *d_status, uint32_t limit)
+{
+    __shared__ unsigned long long s_red[COOP_THREADS / 32];
+    __shared__ unsigned s_warp[COOP_THREADS / 32];
+    const long long nb = min(*d_nb, nb_max);
+    const long long span = (long long)COOP_THREADS * NM_IPT;
+    const long long b0 = (long long)blockIdx.x * rounds * span;
+    auto head = [&](long long i) { return i < nb && (i == 0 || skey[i] != skey[i - 1]); };
+    unsigned long long c = 0;
+    for (int r = 0; r < rounds; r++) {
+        const long long i0 = b0 + r * span + (long long)threadIdx.x * NM_IPT;
+#pragma unroll
+        for (int e = 0; e < NM_IPT; e++)
+            c += head(i0 + e);
+    }
+    const unsigned long long total = block_sum(c, s_red);
+    unsigned long long run = coop_block_prefix(total, s_red, totals, barrier, limit, d_status);
+    for (int r = 0; r < rounds; r++) {
+        const long long i0 = b0 + r * span + (long long)threadIdx.x * NM_IPT;
+        unsigned h = 0;
+#pragma unroll
+        for (int e = 0; e < NM_IPT; e++)
+            h |= head(i0 + e) ? 1u << e : 0u;
+        unsigned tot;
+        long long u = (long long)run + block_excl_scan(__popc(h), s_warp, &tot);
+#pragma unroll
+        for (int e = 0; e < NM_IPT; e++)
+            if (h >> e & 1u) {
+                dkey[u] = (int32_t)(skey[i0 + e] ^ 0x80000000u);
+                start[u] = (int32_t)(i0 + e);
+                u++;
+            }
+        run += tot;
+        __syncthreads(); // s_warp reused by the next span's scan
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        start[run] = (int32_t)nb;
+        *d_runs = (long long)run;
+    }
+}
+
+// Looks up `key` in the table: its payload (the run number), or -1.  Sets
+// *gave_up when the walk passed its bound.
+__device__ __forceinline__ int nm_lookup(const TableView &tv, int32_t key, uint64_t pol, bool *gave_up)
+{
+    if ((uint32_t)key == EMPTY_KEY)
+        return -1;
+    const unsigned b = bucket_of(key, tv.lgb);
+    const Oct k = load_oct(tv.keys + (size_t)b * BUCKET, pol);
+    const int r = scan_bucket(k, (uint32_t)key);
+    if (r >= 0)
+        return tv.pay[(size_t)b * BUCKET + r];
+    if (r == -1)
+        return -1;
+    const long long t = lookup_tail(tv.keys, tv.bmask, tv.steps, (uint32_t)key, b, pol);
+    if (t == -2)
+        *gave_up = true;
+    return t >= 0 ? tv.pay[t] : -1;
+}
+
+__global__ void __launch_bounds__(COOP_THREADS) nm_probe_kernel(
+    TableView tv, PredSet ps, const int32_t *__restrict__ key, long long n_host, const long long *d_n, int rounds,
+    const int32_t *start, const uint32_t *srow, int32_t *pord, int32_t *out_probe, int32_t *out_build, long long cap,
+    long long *d_count, unsigned long long *totals, unsigned *barrier, int32_t *d_status, uint32_t limit)
+{
+    __shared__ unsigned long long s_red[COOP_THREADS / 32];
+    __shared__ unsigned long long s_warp[COOP_THREADS / 32];
+    const long long n = d_n ? min(*d_n, n_host) : n_host;
+    const long long span = (long long)COOP_THREADS * NM_IPT;
+    const long long b0 = (long long)blockIdx.x * rounds * span;
+    const uint64_t pol = l2_evict_last();
+    bool gave_up = false;
+    // 1. one lookup per qualifying row; the run number is kept per row
+    unsigned long long c = 0;
+    for (int r = 0; r < rounds; r++) {
+        const long long i0 = b0 + r * span + (long long)threadIdx.x * NM_IPT;
+        if (i0 >= n)
+            continue;
+        unsigned m = 0;
+        for (int q = 0; q < NM_IPT; q += 4)
+            m |= eval_preds4(ps, i0 + q, n) << q;
+#pragma unroll
+        for (int e = 0; e < NM_IPT; e++) {
+            if (i0 + e >= n)
+                break;
+            const int u = (m >> e & 1u) ? nm_lookup(tv, key[i0 + e], pol, &gave_up) : -1;
+            pord[i0 + e] = u;
+            if (u >= 0)
+                c += (unsigned long long)(start[u + 1] - start[u]);
+        }
+    }
+    if (gave_up)
+        set_status(d_status, TDP_ERR_CAPACITY);
+    const unsigned long long total = block_sum(c, s_red);
+    unsigned long long run = coop_block_prefix(total, s_red, totals, barrier, limit, d_status);
+    // 2. every matching probe row writes its run of build rows at its offset
+    for (int r = 0; r < rounds; r++) {
+        const long long i0 = b0 + r * span + (long long)threadIdx.x * NM_IPT;
+        int u[NM_IPT];
+        unsigned long long cr = 0;
+#pragma unroll
+        for (int e = 0; e < NM_IPT; e++) {
+            u[e] = i0 + e < n ? pord[i0 + e] : -1;
+            if (u[e] >= 0)
+                cr += (unsigned long long)(start[u[e] + 1] - start[u[e]]);
+        }
+        unsigned long long tot;
+        long long pos = (long long)(run + block_excl_scan64(cr, s_warp, &tot));
+#pragma unroll
+        for (int e = 0; e < NM_IPT; e++) {
+            if (u[e] < 0)
+                continue;
+            const int32_t s0 = start[u[e]], s1 = start[u[e] + 1];
+            for (int32_t m = s0; m < s1; m++, pos++)
+                if (pos < cap) {
+                    out_probe[pos] = (int32_t)(i0 + e);
+                    out_build[pos] = (int32_t)srow[m];
+                }
+        }
+        run += tot;
+        __syncthreads(); // s_warp reused by the next span's scan
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        *d_count = (long long)run;
+        if ((long long)run > cap)
+            set_status(d_status, TDP_ERR_CAPACITY);
+    }
+}
+
+struct NmLayout {
+    size_t counters, filter_ws, brow, bkey, ukey, skey, srow, radix, dkey, start, table, pord, totals, total;
+    long long nslots;
+    int Gmax;
+};
+
+static NmLayout nm_layout(long long n_build, long long n_probe)
+{
+    NmLayout L;
+    const long long nb = std::max(1ll, n_build);
+    L.nslots = tdp_join_default_slots(nb);
+    L.Gmax = 8 * num_sms();
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    L.counters = take(256); // [0] build rows kept, [1] runs, [2] barrier (runs), [3] barrier (probe)
+    L.filter_ws = take(tdp_filter_workspace(nb));
+    L.brow = take((size_t)nb * 4);
+    L.bkey = take((size_t)nb * 4);
+    L.ukey = take((size_t)nb * 4);
+    L.skey = take((size_t)nb * 4);
+    L.srow = take((size_t)nb * 4);
+    L.radix = take(radix_ws_bytes(nb, 32, 4, 4));
+    L.dkey = take((size_t)nb * 4);
+    L.start = take((size_t)(nb + 1) * 4);
+    L.table = take((size_t)L.nslots * 8);
+    L.pord = take((size_t)std::max(1ll, n_probe) * 4);
+    L.totals = take((size_t)L.Gmax * 8 * 2);
+    L.total = off;
+    return L;
+}
+
 } // namespace tdp
 
 using namespace tdp;
@@ -1093,4 +1293,128 @@ extern "C" tdp_status tdp_join_probe_agg(const uint64_t *table, int64_t nslots, 
     for (int a = 0; a < TDP_MAX_AGGS; a++)
         out.agg_out[a] = a < naggs ? (long long *)out_aggs[a] : nullptr;
     return dense_finalize(ks, as, out, D, acc, capacity, d_ngroups, fin_ws, d_status, s);
+}
+
+extern "C" size_t tdp_join_nm_workspace(int64_t n_build, int64_t n_probe)
+{
+    if (n_build < 0 || n_probe < 0)
+        return 0;
+    return nm_layout(n_build, n_probe).total;
+}
+
+extern "C" tdp_status tdp_join_nm(const tdp_col *build_cols, int32_t nbuild_cols, const tdp_pred *build_preds,
+                                  int32_t nbuild_preds, int64_t n_build, const int64_t *d_nbuild, int32_t build_key_col,
+                                  const tdp_col *probe_cols, int32_t nprobe_cols, const tdp_pred *probe_preds,
+                                  int32_t nprobe_preds, int64_t n_probe, const int64_t *d_nprobe,
+                                  int32_t probe_key_col, int32_t *out_probe_row, int32_t *out_build_row,
+                                  int64_t capacity, int64_t *d_count, void *ws, size_t ws_bytes, int32_t *d_status,
+                                  tdp_stream_t stream)
+{
+    if (n_build < 0 || n_build >= (1ll << 31) || n_probe < 0 || n_probe >= (1ll << 31) || !build_cols ||
+        !probe_cols || build_key_col < 0 || build_key_col >= nbuild_cols || probe_key_col < 0 ||
+        probe_key_col >= nprobe_cols || capacity < 0 || !d_count || (capacity > 0 && (!out_probe_row || !out_build_row)))
+        return TDP_ERR_INVALID_ARG;
+    if (build_cols[build_key_col].dtype != TDP_I32 || probe_cols[probe_key_col].dtype != TDP_I32)
+        return TDP_ERR_UNSUPPORTED_DTYPE;
+    if (build_cols[build_key_col].n < n_build || probe_cols[probe_key_col].n < n_probe)
+        return TDP_ERR_INVALID_ARG;
+    PredSet bps, pps;
+    tdp_status st = make_predset(build_cols, nbuild_cols, build_preds, nbuild_preds, n_build, &bps);
+    if (st != TDP_OK)
+        return st;
+    if ((st = make_predset(probe_cols, nprobe_cols, probe_preds, nprobe_preds, n_probe, &pps)) != TDP_OK)
+        return st;
+    const NmLayout L = nm_layout(n_build, n_probe);
+    if (!ws || ws_bytes < L.total)
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    if (((uintptr_t)ws % 16) != 0)
+        return TDP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    long long *cnt = (long long *)(w + L.counters);
+    const long long nbm = std::max(1ll, (long long)n_build);
+    if (cudaMemsetAsync(w + L.counters, 0, 256, s) != cudaSuccess ||
+        cudaMemsetAsync(w + L.totals, 0, (size_t)L.Gmax * 16, s) != cudaSuccess)
+        return TDP_ERR_CUDA;
+    // 1. qualifying build rows and their keys, sorted by key (stable)
+    int32_t *brow = (int32_t *)(w + L.brow), *bkey = (int32_t *)(w + L.bkey);
+    {
+        const int32_t gcol = build_key_col;
+        void *gout = bkey;
+        GatherSet gs;
+        if ((st = make_gatherset(build_cols, nbuild_cols, &gcol, 1, &gout, n_build, &gs)) != TDP_OK)
+            return st;
+        if ((st = filter_rows(bps, n_build, (const long long *)d_nbuild, brow, n_build, &cnt[0], &gs,
+                              w + L.filter_ws, d_status, s)) != TDP_OK)
+            return st;
+    }
+    uint32_t *ukey = (uint32_t *)(w + L.ukey), *skey = (uint32_t *)(w + L.skey), *srow = (uint32_t *)(w + L.srow);
+    nm_pack_kernel<<<(unsigned)std::min<long long>((nbm + 255) / 256, (long long)num_sms() * 8), 256, 0, s>>>(
+        bkey, n_build, &cnt[0], ukey);
+    if ((st = launch_status()) != TDP_OK)
+        return st;
+    if ((st = radix_sort_pairs<uint32_t, uint32_t>(ukey, (const uint32_t *)brow, nbm, &cnt[0], 32, skey, srow,
+                                                   w + L.radix, radix_ws_bytes(nbm, 32, 4, 4), d_status, s)) != TDP_OK)
+        return st;
+    // 2. runs of equal keys
+    int32_t *dkey = (int32_t *)(w + L.dkey), *start = (int32_t *)(w + L.start);
+    const uint32_t limit = spin_limit();
+    {
+        int G = 0, R = 1;
+        if (!coop_grid_for((const void *)nm_runs_kernel, nbm, (long long)COOP_THREADS * NM_IPT, &G, &R))
+            return TDP_ERR_CUDA;
+        unsigned long long *tot = (unsigned long long *)(w + L.totals);
+        unsigned *bar = (unsigned *)&cnt[2];
+        long long nbmax = nbm;
+        const long long *dnb = &cnt[0];
+        long long *druns = &cnt[1];
+        void *args[] = {(void *)&skey, (void *)&nbmax, (void *)&dnb, (void *)&R, (void *)&dkey, (void *)&start,
+                        (void *)&druns, (void *)&tot, (void *)&bar, (void *)&d_status, (void *)&limit};
+        if (cudaLaunchCooperativeKernel((const void *)nm_runs_kernel, dim3(G), dim3(COOP_THREADS), args, 0, s) !=
+            cudaSuccess)
+            return TDP_ERR_CUDA;
+    }
+    // 3. the distinct keys into the table, payload = run number
+    uint64_t *table = (uint64_t *)(w + L.table);
+    {
+        tdp_col dc;
+        dc.data = dkey;
+        dc.dtype = TDP_I32;
+        dc.has_bounds = 0;
+        dc.n = nbm;
+        dc.lo = dc.hi = 0;
+        if ((st = tdp_join_build(&dc, 1, nullptr, 0, nbm, (const int64_t *)&cnt[1], 0, -1, TDP_JOIN_UNIQUE_BUILD,
+                                 table, L.nslots, d_status, stream)) != TDP_OK)
+            return st;
+    }
+    // 4. probe: count, then write
+    if (n_probe == 0) {
+        if (cudaMemsetAsync(d_count, 0, 8, s) != cudaSuccess)
+            return TDP_ERR_CUDA;
+        return launch_status();
+    }
+    {
+        int G = 0, R = 1;
+        if (!coop_grid_for((const void *)nm_probe_kernel, n_probe, (long long)COOP_THREADS * NM_IPT, &G, &R))
+            return TDP_ERR_CUDA;
+        TableView tv = table_view(table, L.nslots);
+        const int32_t *pk = (const int32_t *)probe_cols[probe_key_col].data;
+        long long np = n_probe;
+        const long long *dnp = (const long long *)d_nprobe;
+        int32_t *pord = (int32_t *)(w + L.pord);
+        long long cap = capacity;
+        long long *dc = (long long *)d_count;
+        unsigned long long *tot = (unsigned long long *)(w + L.totals) + L.Gmax;
+        unsigned *bar = (unsigned *)&cnt[3];
+        const int32_t *cstart = start;
+        const uint32_t *csrow = srow;
+        void *args[] = {(void *)&tv, (void *)&pps, (void *)&pk, (void *)&np, (void *)&dnp, (void *)&R,
+                        (void *)&cstart, (void *)&csrow, (void *)&pord, (void *)&out_probe_row,
+                        (void *)&out_build_row, (void *)&cap, (void *)&dc, (void *)&tot, (void *)&bar,
+                        (void *)&d_status, (void *)&limit};
+        if (cudaLaunchCooperativeKernel((const void *)nm_probe_kernel, dim3(G), dim3(COOP_THREADS), args, 0, s) !=
+            cudaSuccess)
+            return TDP_ERR_CUDA;
+    }
+    return launch_status();
 }

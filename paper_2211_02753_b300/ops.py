@@ -275,6 +275,28 @@ def join(build_cols, build_key, probe_cols, probe_key, build_payload=-1, build_p
     return {"probe_row": orow, "payload": opay, "gathered": gout, "count": count, "status": status}
 
 
+def join_nm(build_cols, build_key, probe_cols, probe_key, build_preds=(), probe_preds=(), capacity=None,
+            n_build=None, d_nbuild=None, n_probe=None, d_nprobe=None, status=None):
+    """Inner join with repeated build keys: (probe row, build row) pairs in
+    probe order, then build-row order.  capacity defaults to the probe row
+    count; the true pair count is always written (count)."""
+    bc = col_array(build_cols)
+    pc = col_array(probe_cols)
+    dev = _as_col(probe_cols[0]).t.device
+    nb = _as_col(build_cols[build_key]).t.numel() if n_build is None else int(n_build)
+    npr = _as_col(probe_cols[probe_key]).t.numel() if n_probe is None else int(n_probe)
+    cap = npr if capacity is None else int(capacity)
+    status = new_status(dev) if status is None else status
+    op = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    ob = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    count = torch.empty(1, dtype=torch.int64, device=dev)  # written by the call
+    ws = workspace(L.lib().tdp_join_nm_workspace(nb, npr), dev)
+    L.call("tdp_join_nm", bc, len(build_cols), pred_array(build_preds), len(build_preds), nb, _ptr(d_nbuild),
+           int(build_key), pc, len(probe_cols), pred_array(probe_preds), len(probe_preds), npr, _ptr(d_nprobe),
+           int(probe_key), _ptr(op), _ptr(ob), cap, _ptr(count), _ptr(ws), ws.numel(), _ptr(status), _stream())
+    return {"probe_row": op, "build_row": ob, "count": count, "status": status}
+
+
 def join_probe_agg(table, cols, key_col, lo, hi, aggs, preds=(), n=None, capacity=None, status=None, d_n=None):
     carr = col_array(cols)
     dev = _as_col(cols[0]).t.device
@@ -378,6 +400,31 @@ class GroupJoin:
         if tk:
             out.update({"top_vals": self.top_vals, "top_keys": self.top_keys, "k": self.k})
         return out
+
+
+def dict_encode(offsets, data, max_len=32, dict_cap=None, bytes_cap=None, status=None):
+    """Order-preserving dictionary codes of a string column (offsets int32
+    [n+1], data uint8).  Returns dict(codes int32[n], dict_offsets, dict_bytes,
+    ndict, nbytes (device int64[1] each), status)."""
+    _require_cuda(offsets, data)
+    dev = offsets.device
+    n = offsets.numel() - 1
+    dict_cap = n if dict_cap is None else int(dict_cap)
+    bytes_cap = data.numel() if bytes_cap is None else int(bytes_cap)
+    status = new_status(dev) if status is None else status
+    codes = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    doff = torch.empty(dict_cap + 1, dtype=torch.int32, device=dev)
+    dbytes = torch.empty(max(bytes_cap, 1), dtype=torch.uint8, device=dev)
+    nd = torch.empty(1, dtype=torch.int64, device=dev)
+    nbt = torch.empty(1, dtype=torch.int64, device=dev)
+    ws_n = L.lib().tdp_dict_encode_workspace(n, int(max_len))
+    if ws_n == 0:
+        raise TdpError(1, "tdp_dict_encode_workspace")
+    ws = workspace(ws_n, dev)
+    L.call("tdp_dict_encode", _ptr(offsets), _ptr(data), n, int(max_len), _ptr(codes), _ptr(doff), _ptr(dbytes),
+           dict_cap, bytes_cap, _ptr(nd), _ptr(nbt), _ptr(ws), ws.numel(), _ptr(status), _stream())
+    return {"codes": codes, "dict_offsets": doff, "dict_bytes": dbytes, "ndict": nd, "nbytes": nbt,
+            "status": status}
 
 
 # ---------------------------------------------------------------- top-k

@@ -176,13 +176,18 @@ def _render(points: np.ndarray, valid: np.ndarray) -> np.ndarray:
     return inten.reshape(-1, CELL, CELL)
 
 
-def glyph_cells(labels: np.ndarray, seed: int, stream: int) -> np.ndarray:
-    """Render one 28x28 uint8 glyph per label (labels: 1-d int array)."""
+def glyph_cells(labels: np.ndarray, seed: int, stream: int, sizes: np.ndarray | None = None) -> np.ndarray:
+    """Render one 28x28 uint8 glyph per label (labels: 1-d int array).  With
+    `sizes` (1-d 0/1 array) a size-0 glyph is drawn at scale 0.55..0.70 and a
+    size-1 glyph at 0.95..1.15 instead of 0.85..1.15."""
     templates = stroke_templates()
     n = labels.shape[0]
     g = rng(seed, stream)
     rot = np.deg2rad(g.uniform(-15.0, 15.0, n))
     scale = g.uniform(0.85, 1.15, n)
+    if sizes is not None:
+        u = (scale - 0.85) / 0.30  # the same draw, mapped into the size's range
+        scale = np.where(np.asarray(sizes) == 0, 0.55 + 0.15 * u, 0.95 + 0.20 * u)
     shear = g.uniform(-0.15, 0.15, n)
     shift = g.uniform(-2.0, 2.0, (n, 2))
     noise_g = rng(seed, stream + 1)
@@ -225,6 +230,29 @@ def glyph_grids(n_grids: int, seed: int, stream: int = 50) -> tuple:
     img = cells.reshape(n_grids, GRID, GRID, CELL, CELL).transpose(0, 1, 3, 2, 4)
     img = np.ascontiguousarray(img).reshape(n_grids, GRID * CELL, GRID * CELL)
     return img, labels
+
+
+def glyph_grids_sized(n_grids: int, seed: int, stream: int = 80) -> tuple:
+    """Grid images like glyph_grids whose cells also carry a size attribute
+    (0 small, 1 large; the second attribute of the paper's Digit x Size
+    grouping).  Returns (images uint8 [n, 112, 112], digits int64 [n, 4, 4],
+    sizes int64 [n, 4, 4])."""
+    labels = rng(seed, stream).integers(0, N_CLASSES, size=(n_grids, GRID, GRID), dtype=np.int64)
+    sizes = rng(seed, stream + 2).integers(0, 2, size=(n_grids, GRID, GRID), dtype=np.int64)
+    cells = glyph_cells(labels.reshape(-1), seed, stream + 1, sizes=sizes.reshape(-1))
+    img = cells.reshape(n_grids, GRID, GRID, CELL, CELL).transpose(0, 1, 3, 2, 4)
+    img = np.ascontiguousarray(img).reshape(n_grids, GRID * CELL, GRID * CELL)
+    return img, labels, sizes
+
+
+def size_head_params(seed: int) -> dict:
+    """Initial weights of the 2-class size head on the CNN's 128 hidden
+    units: fc2s w [2, 128], b [2], Kaiming-uniform like cnn_params."""
+    g = rng(seed, 90)
+    bound = math.sqrt(6.0 / 128)
+    bb = 1.0 / math.sqrt(128)
+    return {"fc2s_w": g.uniform(-bound, bound, (2, 128)).astype(np.float32),
+            "fc2s_b": rng(seed, 91).uniform(-bb, bb, 2).astype(np.float32)}
 
 
 def cnn_params(seed: int) -> dict:

@@ -170,6 +170,20 @@ def loss(pred, target):
     return float(np.mean(d * d))
 
 
+def _trunk_backward(p, fw, dh1, quant):
+    """Gradients of fc1, conv2 and conv1 from the hidden-layer gradient dh1
+    (ReLU applied, rounded as the accelerated path rounds it)."""
+    g = {}
+    B = dh1.shape[0]
+    flat = fw["y2"].reshape(B, 9216)
+    dflat, g["fc1_w"], g["fc1_b"] = fc1_backward(dh1, flat, fw["wf1"])
+    dy2 = _q(dflat.reshape(B, 12, 12, 64), quant)
+    dz1, g["conv2_w"], g["conv2_b"] = conv2_backward(dy2, fw["arg"], fw["y1"], fw["w2"])
+    dz1 = _q(dz1, quant)
+    g["conv1_w"], g["conv1_b"] = conv1_backward(dz1, fw["x0"])
+    return g
+
+
 def backward(params, fw, target):
     """Gradients of the MSE loss w.r.t. every parameter (dict like params)."""
     p = {k: np.asarray(v, np.float64) for k, v in params.items()}
@@ -185,14 +199,7 @@ def backward(params, fw, target):
     g["fc2_w"] = dlogits.T @ h1
     g["fc2_b"] = dlogits.sum(axis=0)
     dh1 = _q((dlogits @ p["fc2_w"]) * (h1 > 0), quant)
-    B = h1.shape[0]
-    flat = fw["y2"].reshape(B, 9216)
-    dflat, g["fc1_w"], g["fc1_b"] = fc1_backward(dh1, flat, fw["wf1"])
-    dy2 = _q(dflat.reshape(B, 12, 12, 64), quant)
-    y1 = fw["y1"]
-    dz1, g["conv2_w"], g["conv2_b"] = conv2_backward(dy2, fw["arg"], y1, fw["w2"])
-    dz1 = _q(dz1, quant)
-    g["conv1_w"], g["conv1_b"] = conv1_backward(dz1, fw["x0"])
+    g.update(_trunk_backward(p, fw, dh1, quant))
     return g
 
 
@@ -215,3 +222,60 @@ def predict_labels(params, grids_u8):
     """Exact-mode inference: argmax of the class probabilities per cell."""
     fw = forward(params, grids_u8, quant=False)
     return np.argmax(fw["logits"], axis=1).reshape(-1, GRID, GRID)
+
+
+# ------------------------------------------- two heads: Digit x Size query
+
+K_SIZES = 2
+
+
+def _softmax(z):
+    z = z - z.max(axis=1, keepdims=True)
+    e = np.exp(z)
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def forward2(params, size_params, grids_u8, quant=True):
+    """The Digit x Size query: the digit head (fc2) and a size head (fc2s,
+    128 -> 2) on the same hidden layer, one softmax each, then
+    cnt[d, s] = sum_c P_digit[c, d] P_size[c, s] per grid (20 outputs)."""
+    fw = forward(params, grids_u8, quant)
+    q = {k: np.asarray(v, np.float64) for k, v in size_params.items()}
+    ls = fc(fw["h1"], q["fc2s_w"], q["fc2s_b"], False)
+    Ps = _softmax(ls)
+    cnt = soft.pe_groupby2_fwd(fw["P"], Ps)
+    fw2 = dict(fw)
+    fw2.update(logits_s=ls, Ps=Ps, pred2=cnt.reshape(cnt.shape[0], -1))
+    return fw2
+
+
+def targets2(digits, sizes):
+    """Exact Digit x Size counts on the true labels: [n_grids, 20]."""
+    c = soft.exact_groupby2(digits, sizes, K_CLASSES, K_SIZES)
+    return c.reshape(c.shape[0], -1).astype(np.float64)
+
+
+def backward2(params, size_params, fw2, target):
+    """Gradients of the MSE of the 20 Digit x Size counts w.r.t. every
+    parameter of both heads and the shared trunk."""
+    p = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    q = {k: np.asarray(v, np.float64) for k, v in size_params.items()}
+    quant = fw2["quant"]
+    pred = fw2["pred2"]
+    dpred = 2.0 * (pred - np.asarray(target, np.float64)) / pred.size
+    dPd, dPs = soft.pe_groupby2_bwd(dpred.reshape(-1, K_CLASSES, K_SIZES), fw2["P"], fw2["Ps"])
+    P, Ps, h1 = fw2["P"], fw2["Ps"], fw2["h1"]
+    dld = P * (dPd - (P * dPd).sum(axis=1, keepdims=True))
+    dls = Ps * (dPs - (Ps * dPs).sum(axis=1, keepdims=True))
+    g = {"fc2_w": dld.T @ h1, "fc2_b": dld.sum(axis=0), "fc2s_w": dls.T @ h1, "fc2s_b": dls.sum(axis=0)}
+    dh1 = _q((dld @ p["fc2_w"] + dls @ q["fc2s_w"]) * (h1 > 0), quant)
+    g.update(_trunk_backward(p, fw2, dh1, quant))
+    return g
+
+
+def predict_labels2(params, size_params, grids_u8):
+    """Exact mode: argmax of each head per cell -> (digits, sizes) [n, 4, 4]."""
+    fw2 = forward2(params, size_params, grids_u8, quant=False)
+    n = np.asarray(grids_u8).shape[0]
+    return (np.argmax(fw2["logits"], axis=1).reshape(n, GRID, GRID),
+            np.argmax(fw2["logits_s"], axis=1).reshape(n, GRID, GRID))

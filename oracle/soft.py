@@ -125,3 +125,50 @@ def exact_groupby(labels, K: int = 10):
         cnt[:, k] = (labels == k).sum(axis=(1, 2))
     rsum = labels.sum(axis=2).astype(np.int64)
     return cnt, rsum
+
+
+# ------------------------------------------------- two-attribute PE group-by
+
+def pe_groupby2_fwd(Pa, Pb, cells: int = 16):
+    """GROUP BY (a, b) COUNT over two probability-encoded attributes of the
+    same cells (the paper's Digit x Size grouping): per grid,
+    cnt[a, b] = sum over the grid's cells c of Pa[c, a] * Pb[c, b].
+    Pa [n_cells, Ka], Pb [n_cells, Kb] -> cnt [n_grids, Ka, Kb]."""
+    Pa = np.asarray(Pa, np.float64)
+    Pb = np.asarray(Pb, np.float64)
+    n = Pa.shape[0] // cells
+    Pa = Pa.reshape(n, cells, -1)
+    Pb = Pb.reshape(n, cells, -1)
+    cnt = np.zeros((n, Pa.shape[2], Pb.shape[2]))
+    for c in range(cells):
+        cnt += Pa[:, c, :, None] * Pb[:, c, None, :]
+    return cnt
+
+
+def pe_groupby2_bwd(dcnt, Pa, Pb, cells: int = 16):
+    """Adjoint of pe_groupby2_fwd: dPa[c, a] = sum_b dcnt[a, b] Pb[c, b],
+    dPb[c, b] = sum_a dcnt[a, b] Pa[c, a] (c in the grid of dcnt)."""
+    dcnt = np.asarray(dcnt, np.float64)
+    Pa = np.asarray(Pa, np.float64)
+    Pb = np.asarray(Pb, np.float64)
+    n = dcnt.shape[0]
+    Pa3 = Pa.reshape(n, cells, -1)
+    Pb3 = Pb.reshape(n, cells, -1)
+    dPa = np.zeros_like(Pa3)
+    dPb = np.zeros_like(Pb3)
+    for c in range(cells):
+        dPa[:, c, :] = (dcnt * Pb3[:, c, None, :]).sum(axis=2)
+        dPb[:, c, :] = (dcnt * Pa3[:, c, :, None]).sum(axis=1)
+    return dPa.reshape(Pa.shape), dPb.reshape(Pb.shape)
+
+
+def exact_groupby2(a_labels, b_labels, Ka: int = 10, Kb: int = 2):
+    """Exact COUNT per (a, b) pair per grid from integer labels
+    [n_grids, grid_h, grid_w] of both attributes: [n_grids, Ka, Kb]."""
+    a = np.asarray(a_labels).reshape(len(a_labels), -1)
+    b = np.asarray(b_labels).reshape(len(b_labels), -1)
+    cnt = np.zeros((a.shape[0], Ka, Kb), np.int64)
+    for i in range(Ka):
+        for j in range(Kb):
+            cnt[:, i, j] = ((a == i) & (b == j)).sum(axis=1)
+    return cnt

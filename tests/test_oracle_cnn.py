@@ -117,3 +117,35 @@ def test_adam_first_step_closed_form():
     # first step: mhat = g, vhat = g^2, so the move is lr * g / (|g| + eps)
     assert np.allclose(newp["w"], p["w"] - 0.01 * g["w"] / (np.abs(g["w"]) + 1e-8), rtol=0, atol=1e-15)
     assert np.allclose(m["w"], 0.1 * g["w"]) and np.allclose(v["w"], 0.001 * g["w"] ** 2)
+
+
+def test_two_head_query_gradients_vs_finite_differences():
+    """The Digit x Size query loss (float64 network, no rounding): analytic
+    gradients of one element of every parameter tensor of both heads and the
+    trunk against central differences."""
+    import gen
+    from oracle import cnn as O
+    img, dig, siz = gen.glyph_grids_sized(1, 5)
+    p = {k: np.asarray(v, np.float64) for k, v in gen.cnn_params(5).items()}
+    q = {k: np.asarray(v, np.float64) for k, v in gen.size_head_params(5).items()}
+    tgt = O.targets2(dig, siz) + 0.3  # away from the optimum: non-zero gradients
+    fw = O.forward2(p, q, img, quant=False)
+    g = O.backward2(p, q, fw, tgt)
+
+    def loss(pp, qq):
+        return O.loss(O.forward2(pp, qq, img, quant=False)["pred2"], tgt)
+
+    r = np.random.default_rng(3)
+    h = 1e-6
+    for name in list(p) + list(q):
+        src = p if name in p else q
+        idx = tuple(int(r.integers(0, s)) for s in src[name].shape)
+        plus = {k: v.copy() for k, v in src.items()}
+        minus = {k: v.copy() for k, v in src.items()}
+        plus[name][idx] += h
+        minus[name][idx] -= h
+        if src is p:
+            fd = (loss(plus, q) - loss(minus, q)) / (2 * h)
+        else:
+            fd = (loss(p, plus) - loss(p, minus)) / (2 * h)
+        assert abs(fd - g[name][idx]) <= 1e-5 * max(1e-3, abs(g[name][idx])), name

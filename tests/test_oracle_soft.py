@@ -151,3 +151,28 @@ def test_pe_groupby_adjoint_identity():
     cnt, rsum = soft.pe_groupby_fwd(P)
     dP = soft.pe_groupby_bwd(dcnt, drsum)
     assert np.isclose((dP * P).sum(), (dcnt * cnt).sum() + (drsum * rsum).sum(), rtol=1e-12)
+
+
+def test_pe_groupby2_pins():
+    """The two-attribute soft COUNT (Digit x Size): per grid it is the matrix
+    product Pa^T Pb of the grid's cells (a library routine), one-hot inputs
+    give the exact pair counts bitwise, and the backward is the exact
+    adjoint of the bilinear map in each argument."""
+    r = np.random.default_rng(21)
+    n, cells = 5, 16
+    Pa = r.random((n * cells, 10))
+    Pb = r.random((n * cells, 2))
+    cnt = soft.pe_groupby2_fwd(Pa, Pb)
+    for g in range(n):
+        A = Pa[g * cells:(g + 1) * cells]
+        B = Pb[g * cells:(g + 1) * cells]
+        assert np.allclose(cnt[g], A.T @ B, rtol=1e-12)
+    dig = r.integers(0, 10, (n, 4, 4))
+    siz = r.integers(0, 2, (n, 4, 4))
+    oh = soft.pe_groupby2_fwd(np.eye(10)[dig.reshape(-1)], np.eye(2)[siz.reshape(-1)])
+    assert np.array_equal(oh, soft.exact_groupby2(dig, siz).astype(np.float64))
+    assert soft.exact_groupby2(dig, siz).sum() == n * 16
+    d = r.standard_normal((n, 10, 2))
+    dA, dB = soft.pe_groupby2_bwd(d, Pa, Pb)
+    lhs = (d * cnt).sum()
+    assert np.isclose((dA * Pa).sum(), lhs, rtol=1e-12) and np.isclose((dB * Pb).sum(), lhs, rtol=1e-12)

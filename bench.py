@@ -172,6 +172,25 @@ def cpu_cnn_sample(grids: int = 1):
     return grids * 16, _timed(q)
 
 
+def cpu_pair_sample(grids: int = 1):
+    """One Digit x Size query step (forward, backward, Adam) of the float64
+    oracle on `grids` grids of 16 cells."""
+    from oracle import cnn as O
+    img, dig, siz = gen.glyph_grids_sized(grids, gen.BASE_SEED + 6)
+    params = {k: np.asarray(v, np.float64) for k, v in gen.cnn_params(gen.BASE_SEED + 5).items()}
+    sp = {k: np.asarray(v, np.float64) for k, v in gen.size_head_params(gen.BASE_SEED + 5).items()}
+    tgt = O.targets2(dig, siz)
+    allp = dict(params, **sp)
+    zeros = {k: np.zeros_like(v) for k, v in allp.items()}
+
+    def q():
+        fw = O.forward2(params, sp, img)
+        g = O.backward2(params, sp, fw, tgt)
+        O.adam_step(allp, g, zeros, zeros, 1)
+
+    return grids * 16, _timed(q)
+
+
 def cpu_baseline(fn, unit_scale: float, unit: str, sample: str, parallel_ok: bool = True, **kw):
     """Times the oracle: OpenMP on all host cores (when the function has a
     parallel form) and single-threaded.  Rates are units per second of
@@ -702,6 +721,7 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
     del sd, sq
     torch.cuda.empty_cache()
     res["trainable_query_glyph_cnn"] = glyph_plan(dev, stream, args, bf16_peak, peak_kind)
+    res["trainable_query_digit_x_size"] = pair_plan(dev, stream, args, bf16_peak, peak_kind)
     return res
 
 
@@ -769,6 +789,72 @@ def glyph_plan(dev, stream, args, bf16_peak, peak_kind):
                              "kind": "oracle", "host_cores": host_cores(),
                              "sample": "one grid (16 cells) through the float64 oracle's forward, backward and "
                                        "Adam (%.2f s), scaled per cell to the 4096-cell step" % secs}}
+
+
+def pair_plan(dev, stream, args, bf16_peak, peak_kind):
+    """The Digit x Size trainable query (two heads, soft pair COUNT): train
+    steps/s at batch 256 grids, exact pair-query steps/s, and the exact pair
+    query's accuracy on 1024 held-out grids after a fixed training budget."""
+    import torch
+    from oracle import cnn as O  # targets: the exact pair counts on the true labels
+    from oracle import soft
+    from paper_2211_02753_b300 import cnn
+    tr_img, tr_dig, tr_siz = gen.glyph_grids_sized(4096, gen.BASE_SEED + 6)
+    te_img, te_dig, te_siz = gen.glyph_grids_sized(1024, gen.BASE_SEED + 106)
+    targets = torch.from_numpy(O.targets2(tr_dig, tr_siz).astype(np.float32)).to(dev)
+    g_tr = torch.from_numpy(tr_img).to(dev)
+    g_te = torch.from_numpy(te_img).to(dev)
+    q = cnn.GlyphQuery2(gen.cnn_params(gen.BASE_SEED + 5), gen.size_head_params(gen.BASE_SEED + 5), dev, lr=1e-3,
+                        warmup=400)
+    B = 256
+    nb = 4096 // B
+
+    def step(i):
+        j = (i % nb) * B
+        return q.train_step(g_tr[j:j + B], targets[j:j + B])
+
+    for i in range(3):
+        step(i)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    n_timed = max(20, args.steps)
+    a.record(stream)
+    for i in range(n_timed):
+        step(3 + i)
+    b.record(stream)
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(b) / n_timed
+    budget = 2400
+    for i in range(3 + n_timed, budget):
+        step(i)
+    torch.cuda.synchronize()
+    gq = g_te[:B]
+    for _ in range(3):
+        q.exact_query(gq)
+    a.record(stream)
+    for _ in range(n_timed):
+        q.exact_query(gq)
+    b.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = a.elapsed_time(b) / n_timed
+    ld, ls, cnt = q.exact_query(g_te)
+    e = soft.exact_groupby2(te_dig, te_siz).reshape(1024, -1)
+    ok = np.all(cnt.cpu().numpy().reshape(1024, -1) == e, axis=1)
+    flops_fwd = 4096 * 2 * (26 * 26 * 32 * 9 + 24 * 24 * 64 * 288 + 9216 * 128 + 128 * 12)
+    cells, secs = cpu_pair_sample(1)
+    return {"train_ms": train_ms, "train_steps_per_s": 1000.0 / train_ms, "exact_query_ms": infer_ms,
+            "exact_query_steps_per_s": 1000.0 / infer_ms, "batch_grids": B, "training_steps": budget,
+            "pair_query_accuracy": float(ok.mean()),
+            "digit_cell_accuracy": float((ld.cpu().numpy().reshape(-1, 4, 4) == te_dig).mean()),
+            "size_cell_accuracy": float((ls.cpu().numpy().reshape(-1, 4, 4) == te_siz).mean()),
+            "roofline": roofline("tensor", 3 * flops_fwd, train_ms / 1e3, bf16_peak, "TFLOP/s",
+                                 "whole training step (conv2 tcgen05 kernels, fc1 tcgen05 GEMM)",
+                                 peak_kind=peak_kind + " (cuBLAS bf16, sustained)"),
+            "cpu_baseline": {"value": 1.0 / (secs * 4096 / cells), "unit": "train steps/s", "cores": 1,
+                             "kind": "oracle", "host_cores": host_cores(),
+                             "sample": "one grid (16 cells) through the float64 oracle's two-head forward, "
+                                       "backward and Adam (%.2f s), scaled per cell to the 4096-cell step" % secs}}
 
 
 def run_only(args):

@@ -83,6 +83,27 @@ tdp_status tdp_cnn_head(const void *h1, int64_t n_grids, const float *wfc2, cons
                         float *logits, float *P, float *pred, void *dh1, float *dwfc2, float *dbfc2, float *loss,
                         void *ws, size_t ws_bytes, tdp_stream_t stream);
 
+/* Workspace bytes of tdp_cnn_head2. */
+size_t tdp_cnn_head2_workspace(int64_t n_grids);
+
+/*
+ * Head of the two-attribute query (Digit x Size, Sec. 4 soft group-by over
+ * two PE columns of the same cells), one block per grid: the digit head
+ * wfc2 [10][128], bfc2 [10] and the size head wfc2s [2][128], bfc2s [2], both
+ * on h1, one softmax each, and the soft COUNT of every (digit, size) pair
+ *   pred [n_grids][10][2], pred[g][a][b] = sum_cells P[c][a] * Ps[c][b]
+ * logits [n_cells][10], logits_s [n_cells][2], P [n_cells][10], Ps
+ * [n_cells][2] are optional outputs.  With targets [n_grids][10][2] (the exact
+ * pair counts on true labels): loss [1] = mean of the 20 n_grids squared
+ * errors, dh1 bf16 [n_cells][128] (both heads' gradients added, ReLU-masked),
+ * dwfc2, dbfc2, dwfc2s, dbfc2s (per-grid partials in ws summed in grid order
+ * in float64).  Argument errors as tdp_cnn_head.
+ */
+tdp_status tdp_cnn_head2(const void *h1, int64_t n_grids, const float *wfc2, const float *bfc2, const float *wfc2s,
+                         const float *bfc2s, const float *targets, float *logits, float *logits_s, float *P,
+                         float *Ps, float *pred, void *dh1, float *dwfc2, float *dbfc2, float *dwfc2s,
+                         float *dbfc2s, float *loss, void *ws, size_t ws_bytes, tdp_stream_t stream);
+
 /* Workspace bytes of tdp_cnn_fc1_bwd. */
 size_t tdp_cnn_fc1_bwd_workspace(int64_t n_cells);
 
@@ -132,7 +153,7 @@ tdp_status tdp_cnn_conv1_bwd(const void *dz1, const uint8_t *grids, int64_t n_ce
                              size_t ws_bytes, tdp_stream_t stream);
 
 /*
- * One Adam step (the optimiser of the paper's training loop) over up to 8
+ * One Adam step (the optimiser of the paper's training loop) over up to 16
  * fp32 tensors: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
  * bf16_copies[i] (optional, or NULL entries) receives p rounded to bf16, the
@@ -164,6 +185,28 @@ tdp_status tdp_pe_groupby_fwd(const float *P, int64_t n_grids, int32_t K, int32_
                               float *rsum, tdp_stream_t stream);
 tdp_status tdp_pe_groupby_bwd(const float *dcnt, const float *drsum, int64_t n_grids, int32_t K, int32_t grid_h,
                               int32_t grid_w, float *dP, tdp_stream_t stream);
+
+/*
+ * Exact pair query at inference: per cell the first arg-max of logits_a
+ * [n_grids*cells][Ka] and of logits_b [n_grids*cells][Kb] (labels_a,
+ * labels_b [n_grids*cells], each optional), per grid the integer COUNT of
+ * every pair, cnt [n_grids][Ka][Kb].
+ */
+tdp_status tdp_exact_pe_count2(const float *logits_a, int32_t Ka, const float *logits_b, int32_t Kb, int64_t n_grids,
+                               int32_t cells, int32_t *labels_a, int32_t *labels_b, int64_t *cnt,
+                               tdp_stream_t stream);
+
+/*
+ * Soft pair COUNT over two PE columns of the same cells (Sec. 4 soft
+ * group-by on two attributes): cnt [n_grids][Ka][Kb] = sum over the grid's
+ * `cells` consecutive cells of Pa[c][a] * Pb[c][b].  The backward is the
+ * adjoint of this bilinear map: dPa[c][a] = sum_b dcnt[g][a][b] Pb[c][b],
+ * dPb[c][b] = sum_a dcnt[g][a][b] Pa[c][a].
+ */
+tdp_status tdp_pe_groupby2_fwd(const float *Pa, int32_t Ka, const float *Pb, int32_t Kb, int64_t n_grids,
+                               int32_t cells, float *cnt, tdp_stream_t stream);
+tdp_status tdp_pe_groupby2_bwd(const float *dcnt, const float *Pa, int32_t Ka, const float *Pb, int32_t Kb,
+                               int64_t n_grids, int32_t cells, float *dPa, float *dPb, tdp_stream_t stream);
 
 #ifdef __cplusplus
 }

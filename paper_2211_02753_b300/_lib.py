@@ -108,6 +108,8 @@ SIGNATURES = {
     "tdp_cnn_fc1_fwd": (_st, [_p, _i64, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_cnn_head_workspace": (_sz, [_i64]),
     "tdp_cnn_head": (_st, [_p, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "tdp_cnn_head2_workspace": (_sz, [_i64]),
+    "tdp_cnn_head2": (_st, [_p, _i64] + [_p] * 17 + [_sz, _p]),
     "tdp_cnn_fc1_bwd_workspace": (_sz, [_i64]),
     "tdp_cnn_fc1_bwd": (_st, [_p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p, _p]),
     "tdp_cnn_conv2_bwd_workspace": (_sz, [_i64]),
@@ -119,6 +121,9 @@ SIGNATURES = {
     "tdp_exact_pe_count": (_st, [_p, _i64, _i32, _i32, _i32, _p, _p, _p, _p]),
     "tdp_pe_groupby_fwd": (_st, [_p, _i64, _i32, _i32, _i32, _p, _p, _p]),
     "tdp_pe_groupby_bwd": (_st, [_p, _p, _i64, _i32, _i32, _i32, _p, _p]),
+    "tdp_exact_pe_count2": (_st, [_p, _i32, _p, _i32, _i64, _i32, _p, _p, _p, _p]),
+    "tdp_pe_groupby2_fwd": (_st, [_p, _i32, _p, _i32, _i64, _i32, _p, _p]),
+    "tdp_pe_groupby2_bwd": (_st, [_p, _p, _i32, _p, _i32, _i64, _i32, _p, _p, _p]),
 }
 
 _lib = None

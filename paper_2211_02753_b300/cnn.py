@@ -122,10 +122,11 @@ class GlyphQuery:
 
     def adam(self) -> None:
         self.t += 1
-        k = list(PARAMS)
-        arr = lambda ts: (C.c_void_p * 8)(*[t.data_ptr() for t in ts])  # noqa: E731
-        copies = (C.c_void_p * 8)(*[self.bf[x].data_ptr() if x in self.bf else 0 for x in k])
-        sizes = (C.c_int64 * 8)(*[self.p[x].numel() for x in k])
+        k = list(self.p)
+        n = len(k)
+        arr = lambda ts: (C.c_void_p * n)(*[t.data_ptr() for t in ts])  # noqa: E731
+        copies = (C.c_void_p * n)(*[self.bf[x].data_ptr() if x in self.bf else 0 for x in k])
+        sizes = (C.c_int64 * n)(*[self.p[x].numel() for x in k])
         lr = self.lr * min(1.0, self.t / self.warmup) if self.warmup else self.lr
         L.call("tdp_adam_step", arr([self.p[x] for x in k]), arr([self.g[x] for x in k]),
                arr([self.m[x] for x in k]), arr([self.v[x] for x in k]), copies, sizes, len(k), self.t,
@@ -158,7 +159,7 @@ class GlyphQuery:
     def state(self) -> dict:
         """Checkpoint: parameters, Adam moments and step (host copies)."""
         out = {"t": self.t}
-        for k in PARAMS:
+        for k in self.p:
             out["p." + k] = self.p[k].cpu()
             out["m." + k] = self.m[k].cpu()
             out["v." + k] = self.v[k].cpu()
@@ -166,12 +167,111 @@ class GlyphQuery:
 
     def load_state(self, st: dict) -> None:
         self.t = int(st["t"])
-        for k in PARAMS:
+        for k in self.p:
             self.p[k].copy_(st["p." + k])
             self.m[k].copy_(st["m." + k])
             self.v[k].copy_(st["v." + k])
         for k in BF16_COPIES:
             L.call("tdp_f32_to_bf16", _ptr(self.p[k]), self.p[k].numel(), _ptr(self.bf[k]), _stream())
+
+
+SIZE_PARAMS = ("fc2s_w", "fc2s_b")
+NPRED2 = 20
+
+
+class GlyphQuery2(GlyphQuery):
+    """The Digit x Size query: the same CNN trunk with a second head (fc2s,
+    128 -> 2 size classes) on the hidden layer; the soft COUNT of every
+    (digit, size) pair per grid (20 outputs) is trained with an MSE against
+    the exact pair counts on true labels, end to end through both heads."""
+
+    def __init__(self, params: dict, size_params: dict, device="cuda", **kw):
+        super().__init__(params, device, **kw)
+        for k in SIZE_PARAMS:
+            self.p[k] = torch.as_tensor(np.asarray(size_params[k], np.float32)).to(self.dev).contiguous()
+            self.m[k] = torch.zeros_like(self.p[k])
+            self.v[k] = torch.zeros_like(self.p[k])
+            self.g[k] = torch.zeros_like(self.p[k])
+
+    def _buffers(self, n_grids: int) -> dict:
+        b = self._buf.get(n_grids)
+        if b is not None and "pred2" in b:
+            return b
+        b = super()._buffers(n_grids)
+        nc = n_grids * CELLS
+        d = self.dev
+        hw = L.lib().tdp_cnn_head2_workspace(n_grids)
+        if b["ws"].numel() < hw:
+            b["ws"] = torch.empty(int(hw), dtype=torch.uint8, device=d)
+        b.update({
+            "logits_s": torch.empty((nc, 2), dtype=torch.float32, device=d),
+            "Ps": torch.empty((nc, 2), dtype=torch.float32, device=d),
+            "pred2": torch.empty((n_grids, NPRED2), dtype=torch.float32, device=d),
+            "labels_s": torch.empty(nc, dtype=torch.int32, device=d),
+            "cnt2": torch.empty((n_grids, 10, 2), dtype=torch.int64, device=d),
+        })
+        return b
+
+    def forward(self, grids: torch.Tensor, targets: torch.Tensor | None = None,
+                loss_out: torch.Tensor | None = None) -> dict:
+        n = grids.shape[0]
+        nc = n * CELLS
+        b = self._buffers(n)
+        s = _stream()
+        p = self.p
+        ws, wsn = _ptr(b["ws"]), b["ws"].numel()
+        L.call("tdp_cnn_conv1_fwd", _ptr(grids), n, _ptr(p["conv1_w"]), _ptr(p["conv1_b"]), _ptr(b["y1"]), s)
+        L.call("tdp_cnn_conv2_pool_fwd", _ptr(b["y1"]), nc, _ptr(self.bf["conv2_w"]), _ptr(p["conv2_b"]),
+               _ptr(b["y2"]), _ptr(b["argmax"]), _ptr(self.status), s)
+        L.call("tdp_cnn_fc1_fwd", _ptr(b["y2"]), nc, _ptr(self.bf["fc1_w"]), _ptr(p["fc1_b"]), _ptr(b["h1"]), ws,
+               wsn, _ptr(self.status), s)
+        g = self.g
+        tr = targets is not None
+        L.call("tdp_cnn_head2", _ptr(b["h1"]), n, _ptr(p["fc2_w"]), _ptr(p["fc2_b"]), _ptr(p["fc2s_w"]),
+               _ptr(p["fc2s_b"]), _ptr(targets), _ptr(b["logits"]), _ptr(b["logits_s"]), _ptr(b["P"]),
+               _ptr(b["Ps"]), _ptr(b["pred2"]), _ptr(b["dh1"]) if tr else None,
+               _ptr(g["fc2_w"]) if tr else None, _ptr(g["fc2_b"]) if tr else None,
+               _ptr(g["fc2s_w"]) if tr else None, _ptr(g["fc2s_b"]) if tr else None,
+               _ptr(loss_out if loss_out is not None else b["loss"]) if tr else None, ws, wsn, s)
+        return b
+
+    def soft_query(self, grids: torch.Tensor) -> torch.Tensor:
+        return self.forward(grids)["pred2"]
+
+    def exact_query(self, grids: torch.Tensor):
+        """Exact pair query on argmax labels: (digits [n*16], sizes [n*16],
+        cnt [n, 10, 2])."""
+        b = self.forward(grids)
+        n = grids.shape[0]
+        L.call("tdp_exact_pe_count2", _ptr(b["logits"]), 10, _ptr(b["logits_s"]), 2, n, CELLS, _ptr(b["labels"]),
+               _ptr(b["labels_s"]), _ptr(b["cnt2"]), _stream())
+        return b["labels"], b["labels_s"], b["cnt2"]
+
+
+def pe_groupby2_fwd(Pa: torch.Tensor, Pb: torch.Tensor, n_grids: int, cells: int = CELLS):
+    Ka, Kb = Pa.shape[1], Pb.shape[1]
+    cnt = torch.empty((n_grids, Ka, Kb), dtype=torch.float32, device=Pa.device)
+    L.call("tdp_pe_groupby2_fwd", _ptr(Pa), Ka, _ptr(Pb), Kb, n_grids, cells, _ptr(cnt), _stream())
+    return cnt
+
+
+def pe_groupby2_bwd(dcnt: torch.Tensor, Pa: torch.Tensor, Pb: torch.Tensor, cells: int = CELLS):
+    n, Ka, Kb = dcnt.shape
+    dPa = torch.empty_like(Pa)
+    dPb = torch.empty_like(Pb)
+    L.call("tdp_pe_groupby2_bwd", _ptr(dcnt), _ptr(Pa), Ka, _ptr(Pb), Kb, n, cells, _ptr(dPa), _ptr(dPb),
+           _stream())
+    return dPa, dPb
+
+
+def exact_count2(logits_a: torch.Tensor, logits_b: torch.Tensor, n_grids: int, cells: int = CELLS):
+    Ka, Kb = logits_a.shape[1], logits_b.shape[1]
+    la = torch.empty(n_grids * cells, dtype=torch.int32, device=logits_a.device)
+    lb = torch.empty(n_grids * cells, dtype=torch.int32, device=logits_a.device)
+    cnt = torch.empty((n_grids, Ka, Kb), dtype=torch.int64, device=logits_a.device)
+    L.call("tdp_exact_pe_count2", _ptr(logits_a), Ka, _ptr(logits_b), Kb, n_grids, cells, _ptr(la), _ptr(lb),
+           _ptr(cnt), _stream())
+    return la, lb, cnt
 
 
 def pe_groupby_fwd(P: torch.Tensor, n_grids: int, K: int = 10, gh: int = 4, gw: int = 4):

@@ -1464,6 +1464,155 @@ __global__ void __launch_bounds__(HEAD_THREADS) head_kernel(const bf16 *__restri
     }
 }
 
+// ------------------------------------------------- head of the pair query
+//
+// The Digit x Size query: two heads on the same hidden layer (fc2 -> 10
+// digit classes, fc2s -> 2 size classes), one softmax each, and the soft
+// COUNT of every (digit, size) pair, cnt[a][b] = sum_c Pd[c][a] Ps[c][b]
+// (Sec. 4 soft group-by over two PE attributes: products of the two
+// attributes' probabilities, summed).  With targets: the MSE of the 20
+// counts, its backward through both softmaxes down to dh1 (the two heads'
+// contributions added before the ReLU mask) and both heads' gradients as
+// per-grid partials.
+constexpr int NSZ = 2;
+constexpr int NH2 = NCLS + NSZ;         // logits of both heads per cell
+constexpr int NPRED2 = NCLS * NSZ;      // pair counts per grid
+constexpr int H2_PER = NCLS * HID + NCLS + NSZ * HID + NSZ + 1; // partial row
+
+__global__ void __launch_bounds__(HEAD_THREADS) head2_kernel(const bf16 *__restrict__ h1, const float *__restrict__ wd,
+                                                             const float *__restrict__ bd,
+                                                             const float *__restrict__ ws_,
+                                                             const float *__restrict__ bs,
+                                                             const float *__restrict__ target, float inv_nout,
+                                                             float *__restrict__ logits_d, float *__restrict__ logits_s,
+                                                             float *__restrict__ Pd_out, float *__restrict__ Ps_out,
+                                                             float *__restrict__ pred_out, bf16 *__restrict__ dh1,
+                                                             float *__restrict__ part)
+{
+    __shared__ float sh[CELLS_PER_GRID][HID];
+    __shared__ float sw[NH2][HID];
+    __shared__ float sP[CELLS_PER_GRID][NH2]; // logits, then the two softmaxes
+    __shared__ float sdl[CELLS_PER_GRID][NH2];
+    __shared__ float sdpred[NPRED2];
+    const long long grid = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < CELLS_PER_GRID * HID; i += HEAD_THREADS)
+        sh[i / HID][i % HID] = bf2f(h1[grid * CELLS_PER_GRID * HID + i]);
+    for (int i = tid; i < NH2 * HID; i += HEAD_THREADS)
+        sw[i / HID][i % HID] = i < NCLS * HID ? wd[i] : ws_[i - NCLS * HID];
+    __syncthreads();
+    if (tid < CELLS_PER_GRID * NH2) {
+        const int c = tid / NH2, k = tid % NH2;
+        float s = k < NCLS ? bd[k] : bs[k - NCLS];
+        for (int u = 0; u < HID; u++)
+            s = fmaf(sh[c][u], sw[k][u], s);
+        sP[c][k] = s;
+        const long long cell = grid * CELLS_PER_GRID + c;
+        if (k < NCLS && logits_d)
+            logits_d[cell * NCLS + k] = s;
+        if (k >= NCLS && logits_s)
+            logits_s[cell * NSZ + (k - NCLS)] = s;
+    }
+    __syncthreads();
+    if (tid < 2 * CELLS_PER_GRID) { // thread c: digit softmax of cell c; 16 + c: size softmax
+        const int c = tid % CELLS_PER_GRID;
+        const int k0 = tid < CELLS_PER_GRID ? 0 : NCLS, kn = tid < CELLS_PER_GRID ? NCLS : NSZ;
+        float mx = sP[c][k0];
+        for (int k = 1; k < kn; k++)
+            mx = fmaxf(mx, sP[c][k0 + k]);
+        float e[NCLS], z = 0.f;
+        for (int k = 0; k < kn; k++) {
+            e[k] = expf(sP[c][k0 + k] - mx);
+            z += e[k];
+        }
+        const float iz = 1.0f / z;
+        for (int k = 0; k < kn; k++)
+            sP[c][k0 + k] = e[k] * iz;
+    }
+    __syncthreads();
+    if (tid < CELLS_PER_GRID * NH2) {
+        const int c = tid / NH2, k = tid % NH2;
+        const long long cell = grid * CELLS_PER_GRID + c;
+        if (k < NCLS && Pd_out)
+            Pd_out[cell * NCLS + k] = sP[c][k];
+        if (k >= NCLS && Ps_out)
+            Ps_out[cell * NSZ + (k - NCLS)] = sP[c][k];
+    }
+    float d = 0.f;
+    if (tid < NPRED2) {
+        const int a = tid / NSZ, b = tid % NSZ;
+        float s = 0.f;
+        for (int c = 0; c < CELLS_PER_GRID; c++)
+            s = fmaf(sP[c][a], sP[c][NCLS + b], s);
+        if (pred_out)
+            pred_out[grid * NPRED2 + tid] = s;
+        if (target) {
+            d = s - target[grid * NPRED2 + tid];
+            sdpred[tid] = 2.f * d * inv_nout;
+        }
+    }
+    if (!target)
+        return;
+    float *gp = part + grid * H2_PER;
+    if (tid < 32) { // the grid's share of the mean loss (lanes >= 20 add 0)
+        float l = d * d;
+        for (int o = 16; o > 0; o >>= 1)
+            l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (tid == 0)
+            gp[H2_PER - 1] = l * inv_nout;
+    }
+    __syncthreads();
+    if (tid < 2 * CELLS_PER_GRID) {
+        const int c = tid % CELLS_PER_GRID;
+        if (tid < CELLS_PER_GRID) { // dPd[a] = sum_b dpred[a][b] Ps[c][b], then the softmax backward
+            float dP[NCLS], dot = 0.f;
+            for (int a = 0; a < NCLS; a++) {
+                float v = 0.f;
+                for (int b = 0; b < NSZ; b++)
+                    v = fmaf(sdpred[a * NSZ + b], sP[c][NCLS + b], v);
+                dP[a] = v;
+                dot = fmaf(sP[c][a], v, dot);
+            }
+            for (int a = 0; a < NCLS; a++)
+                sdl[c][a] = sP[c][a] * (dP[a] - dot);
+        } else { // dPs[b] = sum_a dpred[a][b] Pd[c][a]
+            float dP[NSZ], dot = 0.f;
+            for (int b = 0; b < NSZ; b++) {
+                float v = 0.f;
+                for (int a = 0; a < NCLS; a++)
+                    v = fmaf(sdpred[a * NSZ + b], sP[c][a], v);
+                dP[b] = v;
+                dot = fmaf(sP[c][NCLS + b], v, dot);
+            }
+            for (int b = 0; b < NSZ; b++)
+                sdl[c][NCLS + b] = sP[c][NCLS + b] * (dP[b] - dot);
+        }
+    }
+    __syncthreads();
+    // dh1[c][u] = (sum_k dl[c][k] w[k][u] over both heads) * (h1 > 0)
+    for (int i = tid; i < CELLS_PER_GRID * HID; i += HEAD_THREADS) {
+        const int c = i / HID, u = i % HID;
+        float s = 0.f;
+        for (int k = 0; k < NH2; k++)
+            s = fmaf(sdl[c][k], sw[k][u], s);
+        dh1[grid * CELLS_PER_GRID * HID + i] = __float2bfloat16_rn(sh[c][u] > 0.f ? s : 0.f);
+    }
+    // both heads' weight gradients of this grid: [dwd 10x128][dbd 10][dws 2x128][dbs 2][loss]
+    for (int i = tid; i < NH2 * HID; i += HEAD_THREADS) {
+        const int k = i / HID, u = i % HID;
+        float s = 0.f;
+        for (int c = 0; c < CELLS_PER_GRID; c++)
+            s = fmaf(sdl[c][k], sh[c][u], s);
+        gp[k < NCLS ? i : NCLS * HID + NCLS + (i - NCLS * HID)] = s;
+    }
+    if (tid < NH2) {
+        float s = 0.f;
+        for (int c = 0; c < CELLS_PER_GRID; c++)
+            s += sdl[c][tid];
+        gp[tid < NCLS ? NCLS * HID + tid : NCLS * HID + NCLS + NSZ * HID + (tid - NCLS)] = s;
+    }
+}
+
 // ------------------------------------------------------- exact inference
 
 // Exact query (Sec. 4: the exact operators replace the soft ones at
@@ -1532,15 +1681,88 @@ __global__ void pe_groupby_bwd_kernel(const float *__restrict__ dcnt, const floa
     dP[i] = dcnt[g * K + k] + (float)k * drsum[g * gh + r];
 }
 
+// Exact pair query: per cell the first arg-max of each attribute's logits,
+// then the integer COUNT of every (a, b) pair per grid.
+__global__ void exact_count2_kernel(const float *__restrict__ la, int Ka, const float *__restrict__ lb, int Kb,
+                                    long long ngrid, int cpg, int32_t *__restrict__ labels_a,
+                                    int32_t *__restrict__ labels_b, long long *__restrict__ cnt)
+{
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngrid)
+        return;
+    long long *out = cnt + g * Ka * Kb;
+    for (int j = 0; j < Ka * Kb; j++)
+        out[j] = 0;
+    for (int c = 0; c < cpg; c++) {
+        const long long cell = g * cpg + c;
+        const float *xa = la + cell * Ka, *xb = lb + cell * Kb;
+        int ba = 0, bb = 0;
+        for (int k = 1; k < Ka; k++)
+            if (xa[k] > xa[ba])
+                ba = k;
+        for (int k = 1; k < Kb; k++)
+            if (xb[k] > xb[bb])
+                bb = k;
+        if (labels_a)
+            labels_a[cell] = ba;
+        if (labels_b)
+            labels_b[cell] = bb;
+        out[ba * Kb + bb] += 1;
+    }
+}
+
+// Soft pair COUNT: cnt[g][a][b] = sum over the grid's cells of Pa[c][a] Pb[c][b]
+__global__ void pe_groupby2_fwd_kernel(const float *__restrict__ Pa, int Ka, const float *__restrict__ Pb, int Kb,
+                                       long long ngrid, int cpg, float *__restrict__ cnt)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ngrid * Ka * Kb)
+        return;
+    const long long g = i / (Ka * Kb);
+    const int j = (int)(i % (Ka * Kb)), a = j / Kb, b = j % Kb;
+    float s = 0.f;
+    for (int c = 0; c < cpg; c++)
+        s = fmaf(Pa[(g * cpg + c) * Ka + a], Pb[(g * cpg + c) * Kb + b], s);
+    cnt[i] = s;
+}
+
+// Its adjoint: dPa[c][a] = sum_b dcnt[g][a][b] Pb[c][b] and
+// dPb[c][b] = sum_a dcnt[g][a][b] Pa[c][a]; one thread per element of either.
+__global__ void pe_groupby2_bwd_kernel(const float *__restrict__ dcnt, const float *__restrict__ Pa, int Ka,
+                                       const float *__restrict__ Pb, int Kb, long long ngrid, int cpg,
+                                       float *__restrict__ dPa, float *__restrict__ dPb)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int per = Ka + Kb;
+    if (i >= ngrid * cpg * per)
+        return;
+    const long long cell = i / per;
+    const int j = (int)(i % per);
+    const float *dc = dcnt + (cell / cpg) * Ka * Kb;
+    float s = 0.f;
+    if (j < Ka) {
+        for (int b = 0; b < Kb; b++)
+            s = fmaf(dc[j * Kb + b], Pb[cell * Kb + b], s);
+        dPa[cell * Ka + j] = s;
+    } else {
+        const int b = j - Ka;
+        for (int a = 0; a < Ka; a++)
+            s = fmaf(dc[a * Kb + b], Pa[cell * Ka + a], s);
+        dPb[cell * Kb + b] = s;
+    }
+}
+
 // ------------------------------------------------------------------- Adam
 
+constexpr int ADAM_MAX = 16;
+
 struct AdamSet {
-    float *p[8];
-    const float *g[8];
-    float *m[8];
-    float *v[8];
-    bf16 *copy[8];
-    long long off[9];
+    float *p[ADAM_MAX];
+    const float *g[ADAM_MAX];
+    float *m[ADAM_MAX];
+    float *v[ADAM_MAX];
+    bf16 *copy[ADAM_MAX];
+    long long off[ADAM_MAX + 1];
     int count;
 };
 
@@ -1705,6 +1927,40 @@ tdp_status tdp_cnn_head(const void *h1, int64_t n_grids, const float *wfc2, cons
     return launch_status();
 }
 
+size_t tdp_cnn_head2_workspace(int64_t n_grids)
+{
+    return align_up((size_t)n_grids * H2_PER * sizeof(float), 256);
+}
+
+tdp_status tdp_cnn_head2(const void *h1, int64_t n_grids, const float *wfc2, const float *bfc2, const float *wfc2s,
+                         const float *bfc2s, const float *targets, float *logits, float *logits_s, float *P,
+                         float *Ps, float *pred, void *dh1, float *dwfc2, float *dbfc2, float *dwfc2s,
+                         float *dbfc2s, float *loss, void *ws, size_t ws_bytes, tdp_stream_t stream)
+{
+    if (n_grids < 0 || (n_grids > 0 && (!h1 || !wfc2 || !bfc2 || !wfc2s || !bfc2s)))
+        return TDP_ERR_INVALID_ARG;
+    if (targets && (!dh1 || !dwfc2 || !dbfc2 || !dwfc2s || !dbfc2s || !loss))
+        return TDP_ERR_INVALID_ARG;
+    if (n_grids == 0)
+        return TDP_OK;
+    if (targets && (!ws || ws_bytes < tdp_cnn_head2_workspace(n_grids)))
+        return TDP_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *part = (float *)ws;
+    head2_kernel<<<(unsigned)n_grids, HEAD_THREADS, 0, s>>>((const bf16 *)h1, wfc2, bfc2, wfc2s, bfc2s, targets,
+                                                            1.0f / (float)(n_grids * NPRED2), logits, logits_s, P,
+                                                            Ps, pred, (bf16 *)dh1, part);
+    if (targets) {
+        // digit head's weight and bias sums, then the size head's and the loss
+        const int n1 = NCLS * HID + NCLS, n2 = NSZ * HID + NSZ + 1;
+        partial_sum_kernel<<<psum_blocks(n1), 32 * PS_SLICES, 0, s>>>(part, (int)n_grids, n1, H2_PER,
+                                                                      PsOut{dwfc2, dbfc2, nullptr, NCLS * HID, NCLS});
+        partial_sum_kernel<<<psum_blocks(n2), 32 * PS_SLICES, 0, s>>>(part + n1, (int)n_grids, n2, H2_PER,
+                                                                      PsOut{dwfc2s, dbfc2s, loss, NSZ * HID, NSZ});
+    }
+    return launch_status();
+}
+
 size_t tdp_cnn_fc1_bwd_workspace(int64_t n_cells)
 {
     size_t a = align_up((size_t)FC1_WGRAD_SPLITS * HID * FEAT * sizeof(float), 256);
@@ -1854,12 +2110,12 @@ tdp_status tdp_adam_step(float *const *params, const float *const *grads, float 
                          void *const *bf16_copies, const int64_t *sizes, int32_t count, int32_t step, float lr,
                          float beta1, float beta2, float eps, tdp_stream_t stream)
 {
-    if (count < 1 || count > 8 || step < 1 || !params || !grads || !m || !v || !sizes)
+    if (count < 1 || count > ADAM_MAX || step < 1 || !params || !grads || !m || !v || !sizes)
         return TDP_ERR_INVALID_ARG;
     AdamSet as;
     as.count = count;
     as.off[0] = 0;
-    for (int i = 0; i < 8; i++) {
+    for (int i = 0; i < ADAM_MAX; i++) {
         bool on = i < count;
         as.p[i] = on ? params[i] : nullptr;
         as.g[i] = on ? grads[i] : nullptr;
@@ -1925,6 +2181,46 @@ tdp_status tdp_pe_groupby_bwd(const float *dcnt, const float *drsum, int64_t n_g
         return TDP_OK;
     pe_groupby_bwd_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(dcnt, drsum, n_grids, K, grid_h,
                                                                                 grid_w, dP);
+    return launch_status();
+}
+
+tdp_status tdp_exact_pe_count2(const float *logits_a, int32_t Ka, const float *logits_b, int32_t Kb, int64_t n_grids,
+                               int32_t cells, int32_t *labels_a, int32_t *labels_b, int64_t *cnt,
+                               tdp_stream_t stream)
+{
+    if (n_grids < 0 || Ka < 1 || Kb < 1 || cells < 1 || (n_grids > 0 && (!logits_a || !logits_b || !cnt)))
+        return TDP_ERR_INVALID_ARG;
+    if (n_grids == 0)
+        return TDP_OK;
+    exact_count2_kernel<<<blocks_for(n_grids, 128), 128, 0, (cudaStream_t)stream>>>(
+        logits_a, Ka, logits_b, Kb, n_grids, cells, labels_a, labels_b, (long long *)cnt);
+    return launch_status();
+}
+
+tdp_status tdp_pe_groupby2_fwd(const float *Pa, int32_t Ka, const float *Pb, int32_t Kb, int64_t n_grids,
+                               int32_t cells, float *cnt, tdp_stream_t stream)
+{
+    if (n_grids < 0 || Ka < 1 || Kb < 1 || cells < 1 || (n_grids > 0 && (!Pa || !Pb || !cnt)))
+        return TDP_ERR_INVALID_ARG;
+    const long long n = n_grids * Ka * Kb;
+    if (n == 0)
+        return TDP_OK;
+    pe_groupby2_fwd_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Pa, Ka, Pb, Kb, n_grids, cells,
+                                                                                 cnt);
+    return launch_status();
+}
+
+tdp_status tdp_pe_groupby2_bwd(const float *dcnt, const float *Pa, int32_t Ka, const float *Pb, int32_t Kb,
+                               int64_t n_grids, int32_t cells, float *dPa, float *dPb, tdp_stream_t stream)
+{
+    if (n_grids < 0 || Ka < 1 || Kb < 1 || cells < 1 ||
+        (n_grids > 0 && (!dcnt || !Pa || !Pb || !dPa || !dPb)))
+        return TDP_ERR_INVALID_ARG;
+    const long long n = n_grids * cells * (Ka + Kb);
+    if (n == 0)
+        return TDP_OK;
+    pe_groupby2_bwd_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(dcnt, Pa, Ka, Pb, Kb, n_grids,
+                                                                                 cells, dPa, dPb);
     return launch_status();
 }
 

@@ -140,7 +140,7 @@ const char *tdp_status_str(int32_t s)
     }
 }
 
-int32_t tdp_abi_version(void) { return 102; }
+int32_t tdp_abi_version(void) { return 103; }
 
 uint32_t tdp_set_spin_limit(uint32_t polls) { return tdp::g_spin_limit.exchange(polls); }
 

@@ -32,7 +32,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 def test_host_only_calls():
     L = _lib.lib()
-    assert L.tdp_abi_version() == 102
+    assert L.tdp_abi_version() == 103
     assert L.tdp_status_str(4) == b"capacity exceeded"
     assert L.tdp_filter_workspace(0) >= 0
     assert L.tdp_join_default_slots(3_000_000) == 1 << 23

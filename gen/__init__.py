@@ -22,6 +22,14 @@ Workload shapes (all synthetic; the paper's own datasets are not available):
   random lower-case words, some of them prefixes of others.
 * N:M join tables: build keys with a fixed number of rows per distinct key
   on average (Poisson), probe keys uniform over a wider range.
+* LLP rows (stand-in for the paper's Adult Income census rows, Sec. 5.3):
+  six standardised fp32 numeric features shaped like the census numeric
+  columns (an age-like and an hours-like Gaussian, a discrete education
+  level, two mostly-zero heavy-tailed capital columns, an uninformative
+  sampling weight) and an int32 binary label, about 24% positive, from a
+  fixed logistic model of the features.  Rows are in random order, so bags
+  of consecutive rows are random bags.  Standard Laplace draws for the
+  label-DP counts come from a stream of their own.
 * glyph grids: 4x4 cells of 28x28 uint8 glyphs drawn from 10 seeded stroke
   templates with affine jitter and Gaussian noise (stand-in for the paper's
   MNIST grids, Sec. 5.5).
@@ -331,3 +339,34 @@ def nm_join_tables(n_build: int, n_probe: int, dup: float, seed: int) -> dict:
         "probe_key": _uniform_int(seed, 73, 1, 2 * k, n_probe, np.int32),
         "probe_date": _uniform_int(seed, 74, 0, 2556, n_probe, np.int32),
     }
+
+
+LLP_FEATURES = 6
+# the fixed logistic model that draws the labels (weights per standardised
+# feature, then the intercept that puts about 24% of rows in class 1)
+_LLP_W = np.array([0.9, 0.1, 1.1, 0.8, 0.35, 0.6])
+_LLP_B = -1.75
+
+
+def llp_table(n: int, seed: int, stream: int = 120) -> tuple:
+    """Census-shaped rows for learning from label proportions: features fp32
+    [n, 6] (each column standardised to mean 0, variance 1 over the drawn
+    rows), labels int32 [n] in {0, 1}."""
+    g = rng(seed, stream)
+    age = g.normal(38.6, 13.6, n)
+    fnl = np.log(g.lognormal(12.0, 0.5, n))  # sampling weight: no relation to the label
+    edu = np.clip(np.rint(g.normal(10.1, 2.6, n)), 1, 16)
+    gain = np.where(g.random(n) < 0.08, np.log1p(g.lognormal(8.5, 1.0, n)), 0.0)
+    loss = np.where(g.random(n) < 0.05, np.log1p(g.lognormal(7.5, 0.3, n)), 0.0)
+    hours = np.clip(g.normal(40.4, 12.3, n), 1, 99)
+    raw = np.stack([age, fnl, edu, gain, loss, hours], axis=1)
+    X = (raw - raw.mean(axis=0)) / raw.std(axis=0)
+    z = X @ _LLP_W + _LLP_B + g.logistic(0.0, 1.0, n)
+    y = (z > 0).astype(np.int32)
+    return X.astype(np.float32), y
+
+
+def laplace_noise(n_bags: int, k: int, seed: int, stream: int = 130) -> np.ndarray:
+    """Standard Laplace draws (location 0, scale 1), fp32 [n_bags, k]: the
+    random numbers of the label-DP mechanism, scaled by the method."""
+    return rng(seed, stream).laplace(0.0, 1.0, (n_bags, k)).astype(np.float32)

@@ -15,5 +15,8 @@ Modules:
   soft       -- fp64 soft filter, soft aggregation and their adjoints (Sec. 4),
                 soft group-by on probability-encoded columns.
   cnn        -- fp64 glyph CNN forward/backward, the trainable query loss and
-                Adam (Sec. 3 training loop).
+                Adam (Sec. 3 training loop); the two-head Digit x Size query.
+  dictionary -- order-preserving dictionary codes of string columns.
+  llp        -- fp64 learning from label proportions (Sec. 5.3) and its
+                label-DP variant (Sec. 5.4).
 """

@@ -191,6 +191,23 @@ def cpu_pair_sample(grids: int = 1):
     return grids * 16, _timed(q)
 
 
+def cpu_llp_sample(n: int = 1_000_000, B: int = 64):
+    """One LLP training step (forward, backward, Adam) of the float64 oracle
+    on n census-shaped rows in bags of B."""
+    from oracle import cnn as O
+    from oracle import llp as R
+    X, y = gen.llp_table(n, gen.BASE_SEED + 9)
+    t = R.bag_counts(y, B).astype(np.float64)
+    p = {"W": np.zeros((2, 6)), "b": np.zeros(2)}
+    z = {k: np.zeros_like(v) for k, v in p.items()}
+
+    def q():
+        fw = R.forward(X, p["W"], p["b"], B)
+        O.adam_step(p, R.backward(X, fw, t, B), z, z, 1)
+
+    return n, _timed(q)
+
+
 def cpu_baseline(fn, unit_scale: float, unit: str, sample: str, parallel_ok: bool = True, **kw):
     """Times the oracle: OpenMP on all host cores (when the function has a
     parallel form) and single-threaded.  Rates are units per second of
@@ -722,6 +739,7 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
     torch.cuda.empty_cache()
     res["trainable_query_glyph_cnn"] = glyph_plan(dev, stream, args, bf16_peak, peak_kind)
     res["trainable_query_digit_x_size"] = pair_plan(dev, stream, args, bf16_peak, peak_kind)
+    res.update(llp_plans(dev, stream, args, hbm_peak, peak_kind))
     return res
 
 
@@ -857,6 +875,83 @@ def pair_plan(dev, stream, args, bf16_peak, peak_kind):
                                        "backward and Adam (%.2f s), scaled per cell to the 4096-cell step" % secs}}
 
 
+LLP_ROWS = 64_000_000
+LLP_BAG = 64
+
+
+def llp_plans(dev, stream, args, hbm_peak, peak_kind):
+    """Learning from label proportions: (1) training throughput on 64M
+    census-shaped rows (6 fp32 features, bags of 64, label-DP counts at
+    eps = 0.1), one full-batch step = the fused forward + backward pass and
+    Adam; (2) the paper's experiment on census-sized data (32,561 training
+    rows, 16,281 test rows): test error after 300 steps per bag size, with
+    exact and with Laplace counts, and the step time at that size."""
+    import torch
+    from oracle import llp as R  # count labels of the throughput workload
+    from paper_2211_02753_b300 import llp
+    out = {}
+    X, y = gen.llp_table(LLP_ROWS, gen.BASE_SEED + 9)
+    gX, gy = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
+    nb = R.n_bags(LLP_ROWS, LLP_BAG)
+    noise = torch.from_numpy(gen.laplace_noise(nb, 2, gen.BASE_SEED + 10)).to(dev)
+    del X, y
+    t = llp.counts(gy, LLP_BAG, 2, noise=noise, eps=0.1)
+    tr = llp.LLPTrainer(gX, t, LLP_BAG, np.zeros((2, 6)), np.zeros(2), lr=0.05)
+    for _ in range(3):
+        tr.step()
+    n_timed = max(10, min(args.steps, 100))
+    fb_ms, = _events_median([tr.forward_backward], stream, reps=n_timed)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n_timed):
+        tr.step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    step_ms = a.elapsed_time(b) / n_timed
+    cnt_ms, = _events_median([lambda: llp.counts(gy, LLP_BAG, 2, noise=noise, eps=0.1)], stream, reps=10)
+    algo = LLP_ROWS * 6 * 4 + nb * 2 * 4  # X once, the count labels once
+    n1, s1 = cpu_llp_sample()
+    out["llp_64M_bag64_dp"] = {
+        "rows": LLP_ROWS, "features": 6, "bag": LLP_BAG, "eps": 0.1, "step_ms": step_ms,
+        "rows_per_s": LLP_ROWS / (step_ms / 1e3), "forward_backward_ms": fb_ms, "dp_counts_ms": cnt_ms,
+        "roofline": roofline("hbm", algo, fb_ms / 1e3, hbm_peak, "GB/s", "llp_step_kernel + llp_reduce_kernel",
+                             peak_kind=peak_kind),
+        "cpu_baseline": {"value": n1 / s1, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                         "host_cores": host_cores(),
+                         "sample": "one training step of the float64 oracle on 1M rows (%.2f s)" % s1}}
+    del tr, gX, gy, noise, t
+    torch.cuda.empty_cache()
+    # ---- the paper's experiment at census size
+    Xtr, ytr = gen.llp_table(32561, gen.BASE_SEED + 7)
+    Xte, yte = gen.llp_table(16281, gen.BASE_SEED + 107)
+    gtr, gytr = torch.from_numpy(Xtr).to(dev), torch.from_numpy(ytr).to(dev)
+    gte, gyte = torch.from_numpy(Xte).to(dev), torch.from_numpy(yte).to(dev)
+    table = {}
+    small_ms = None
+    for B in (1, 8, 16, 32, 64, 128, 256, 512):
+        row = {}
+        for dp in (False, True):
+            nz = torch.from_numpy(gen.laplace_noise(R.n_bags(32561, B), 2, gen.BASE_SEED + 8)).to(dev) if dp \
+                else None
+            tt = llp.counts(gytr, B, 2, noise=nz, eps=0.1 if dp else None)
+            tr = llp.LLPTrainer(gtr, tt, B, np.zeros((2, 6)), np.zeros(2), lr=0.05)
+            a.record(stream)
+            for _ in range(300):
+                tr.step()
+            b.record(stream)
+            _, err = llp.predict(gte, tr.W, tr.b, gyte)
+            row["llp_dp_error" if dp else "llp_error"] = int(err.item()) / len(yte)
+            if B == 64 and not dp:
+                small_ms = a.elapsed_time(b) / 300
+        table[str(B)] = row
+    out["llp_census_error_by_bag"] = {
+        "train_rows": 32561, "test_rows": 16281, "steps": 300, "lr": 0.05, "eps": 0.1,
+        "majority_class_error": float(np.mean(yte != 0)), "errors": table,
+        "step_ms_at_bag_64": small_ms}
+    return out
+
+
 def run_only(args):
     """One plan at 1/scale of its size, `steps` times after `warmup` runs, and
     a one-line timing (CUDA events).  Used for profiler captures of a small
@@ -887,6 +982,14 @@ def run_only(args):
     elif args.only == "soft":
         s = gen.soft_table(10_000_000 // sc, 1024, gen.BASE_SEED + 3)
         fn = plans.SoftQuery({k: torch.from_numpy(v).to(dev) for k, v in s.items()}).run
+    elif args.only == "llp":
+        from oracle import llp as R  # count labels of the workload
+        from paper_2211_02753_b300 import llp
+        n = LLP_ROWS // sc
+        X, y = gen.llp_table(n, gen.BASE_SEED + 9)
+        t = torch.from_numpy(R.bag_counts(y, LLP_BAG).astype(np.float32)).to(dev)
+        tr = llp.LLPTrainer(torch.from_numpy(X).to(dev), t, LLP_BAG, np.zeros((2, 6)), np.zeros(2))
+        fn = tr.forward_backward
     else:  # glyph: one training step of the trainable query
         g = max(16, 256 // sc)
         img, lab = gen.glyph_grids(g, gen.BASE_SEED + 4)
@@ -917,7 +1020,7 @@ def main():
     ap.add_argument("--plans", default="all", choices=["all", "main"])
     ap.add_argument("--only", default=None,
                     choices=["shipping", "shipping_sep", "pricing", "pricing_sort", "filter", "chain", "soft",
-                             "glyph"],
+                             "glyph", "llp"],
                     help="profiling mode: run one plan at 1/--scale size and print its time only")
     ap.add_argument("--scale", type=int, default=1)
     args = ap.parse_args()

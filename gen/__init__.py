@@ -351,7 +351,8 @@ _LLP_B = -1.75
 def llp_table(n: int, seed: int, stream: int = 120) -> tuple:
     """Census-shaped rows for learning from label proportions: features fp32
     [n, 6] (each column standardised to mean 0, variance 1 over the drawn
-    rows), labels int32 [n] in {0, 1}."""
+    rows; a column with no spread is only centred), labels int32 [n] in
+    {0, 1}."""
     g = rng(seed, stream)
     age = g.normal(38.6, 13.6, n)
     fnl = np.log(g.lognormal(12.0, 0.5, n))  # sampling weight: no relation to the label
@@ -360,7 +361,9 @@ def llp_table(n: int, seed: int, stream: int = 120) -> tuple:
     loss = np.where(g.random(n) < 0.05, np.log1p(g.lognormal(7.5, 0.3, n)), 0.0)
     hours = np.clip(g.normal(40.4, 12.3, n), 1, 99)
     raw = np.stack([age, fnl, edu, gain, loss, hours], axis=1)
-    X = (raw - raw.mean(axis=0)) / raw.std(axis=0)
+    sd = raw.std(axis=0)
+    sd[sd == 0] = 1.0  # a single row (or a constant column) stays finite
+    X = (raw - raw.mean(axis=0)) / sd
     z = X @ _LLP_W + _LLP_B + g.logistic(0.0, 1.0, n)
     y = (z > 0).astype(np.int32)
     return X.astype(np.float32), y

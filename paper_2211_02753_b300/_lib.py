@@ -121,6 +121,11 @@ SIGNATURES = {
     "tdp_exact_pe_count": (_st, [_p, _i64, _i32, _i32, _i32, _p, _p, _p, _p]),
     "tdp_pe_groupby_fwd": (_st, [_p, _i64, _i32, _i32, _i32, _p, _p, _p]),
     "tdp_pe_groupby_bwd": (_st, [_p, _p, _i64, _i32, _i32, _i32, _p, _p]),
+    # learning from label proportions (include/tdp_llp.h)
+    "tdp_llp_counts": (_st, [_p, _i64, _i32, _i64, _p, _f, _p, _p, _p]),
+    "tdp_llp_step_workspace": (_sz, [_i64, _i32, _i32, _i64]),
+    "tdp_llp_step": (_st, [_p, _i64, _i32, _i32, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p, _p]),
+    "tdp_llp_predict": (_st, [_p, _i64, _i32, _i32, _p, _p, _p, _p, _p, _p]),
     "tdp_exact_pe_count2": (_st, [_p, _i32, _p, _i32, _i64, _i32, _p, _p, _p, _p]),
     "tdp_pe_groupby2_fwd": (_st, [_p, _i32, _p, _i32, _i64, _i32, _p, _p]),
     "tdp_pe_groupby2_bwd": (_st, [_p, _p, _i32, _p, _i32, _i64, _i32, _p, _p, _p]),

@@ -27,7 +27,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
 
 def _deps_hash(src: str) -> str:
     h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "tdp.h"), src]):
+    for f in sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))) + [src]:
         with open(f, "rb") as fh:
             h.update(fh.read())
     h.update(" ".join(ARCH + FLAGS).encode())

@@ -316,11 +316,12 @@ __global__ void __launch_bounds__(LLP_THREADS) llp_step_kernel(const float *__re
 // rows (cnt0, cnt1, T, S), so one pass over X suffices and no row is
 // visited twice.
 //
-// Each warp works alone: it takes tasks of whole bags, streams the task's
-// rows through its own ring of LLP_NST shared-memory stages (LLP_SR rows
-// each) filled by bulk copies that lane 0 issues LLP_NST stages ahead, and
-// its lanes take one row each per step of 32 rows.  Bags of a multiple of
-// 32 rows are whole steps; bags of a divisor of 32 rows are aligned lane
+// Each warp works alone on one contiguous range of rows made of whole tasks
+// (tasks of whole bags, split evenly over the warps).  It streams the range
+// through its own ring of LLP_NST shared-memory stages of LLP_SR rows,
+// filled by bulk copies that lane 0 issues LLP_NST stages ahead, and its
+// lanes take one row each per step of 32 rows.  Bags of a multiple of 32
+// rows are whole steps; bags of a divisor of 32 rows are aligned lane
 // groups.  Only a bag's two counts are reduced across its lanes (they give
 // delta); S and T stay per-lane partials scaled by delta, and the lanes'
 // gradient sums meet once, at the end.  No block barrier is taken until the
@@ -334,37 +335,6 @@ constexpr int LLP_TASK = 512;       // rows per task (whole bags; a bag longer t
 __host__ __device__ inline long long task_rows(long long B)
 {
     return B <= LLP_TASK ? (LLP_TASK / B) * B : B;
-}
-
-// Cursor over a warp's sequence of stages: task t (strided by the number of
-// warps), stage k of the task.
-struct StageCursor {
-    long long t;
-    int k;
-};
-
-__device__ __forceinline__ bool stage_span(const StageCursor &c, long long TR, long long n, long long ntasks,
-                                           long long &r0, int &rows)
-{
-    if (c.t >= ntasks)
-        return false;
-    const long long t0 = c.t * TR;
-    const long long tend = min(n, t0 + TR);
-    r0 = t0 + (long long)c.k * LLP_SR;
-    rows = (int)min((long long)LLP_SR, tend - r0);
-    return true;
-}
-
-__device__ __forceinline__ void stage_next(StageCursor &c, long long TR, long long n, long long wstride)
-{
-    const long long t0 = c.t * TR;
-    const long long tend = min(n, t0 + TR);
-    if (t0 + (long long)(c.k + 1) * LLP_SR < tend) {
-        c.k++;
-    } else {
-        c.t += wstride;
-        c.k = 0;
-    }
 }
 
 __device__ __forceinline__ void issue_stage(float *buf, const float *X, long long r0, int rows, int d, uint64_t *bar)
@@ -398,10 +368,75 @@ __device__ __forceinline__ void finish_bag2(long long bag, bool leader, float c0
     }
 }
 
+// Bounded wait for an mbarrier phase that sleeps briefly between polls, so
+// that warps whose stage is still in flight leave the issue slots to warps
+// that have data.  False when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.b32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (done)
+            return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// One step: each lane's row of the 32 (FULL: all rows present) adds to the
+// lane's running sums of P0, P1, T = P0 P1 and S = P0 P1 x.
+template <int DM, bool FULL>
+__device__ __forceinline__ void step_rows(const float *__restrict__ buf, int rr, int rows, int d,
+                                          const float (&w)[DM], float bd, float &c0, float &c1, float &T,
+                                          float (&S)[DM])
+{
+    if (!FULL && rr >= rows)
+        return;
+    float x[DM];
+    const float *xr = buf + rr * d;
+    if ((d & 1) == 0) {
+#pragma unroll
+        for (int f = 0; f < DM; f += 2) {
+            if (f < d) {
+                const float2 v = *reinterpret_cast<const float2 *>(xr + f);
+                x[f] = v.x;
+                x[f + 1] = v.y;
+            } else {
+                x[f] = x[f + 1] = 0.f;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < DM; f++)
+            x[f] = f < d ? xr[f] : 0.f;
+    }
+    float dz = bd;
+#pragma unroll
+    for (int f = 0; f < DM; f++)
+        dz = fmaf(x[f], w[f], dz);
+    // P1 = sigma(z1 - z0) from e = 2^-|dz2| in (0, 1] (no overflow either
+    // way); 1 + e lies in [1, 2], where the fast divide holds
+    const float e = exp2f(-fabsf(dz));
+    const float a = __fdividef(1.0f, 1.0f + e);
+    const float P0 = dz >= 0.f ? e * a : a;
+    const float P1 = dz >= 0.f ? a : e * a;
+    const float h = P0 * P1;
+    c0 += P0;
+    c1 += P1;
+    T += h;
+#pragma unroll
+    for (int f = 0; f < DM; f++)
+        S[f] = fmaf(h, x[f], S[f]);
+}
+
 template <int DM, bool EXACT>
 __global__ void __launch_bounds__(LLP_ST) llp_stream_kernel(const float *__restrict__ X, long long n, int d_rt,
-                                                           long long B, uint32_t bag_mul,
-                                                           const float *__restrict__ W,
+                                                           long long B, const float *__restrict__ W,
                                                            const float *__restrict__ bias,
                                                            const float *__restrict__ target, float inv_nout,
                                                            float *__restrict__ cnt_out, float *__restrict__ part,
@@ -421,27 +456,24 @@ __global__ void __launch_bounds__(LLP_ST) llp_stream_kernel(const float *__restr
         w[f] = f < d ? (W[d + f] - W[f]) * LOG2E : 0.f;
     const float bd = (bias[1] - bias[0]) * LOG2E;
     const float two_inv = 2.f * inv_nout;
-    const long long TR = task_rows(B);
-    const long long wstride = (long long)gridDim.x * LLP_SW;
     const bool big = B % 32 == 0; // else B divides 32 (a power of two)
     const int lgB = big ? 0 : __ffs((int)B) - 1;
-    const int Bi = big ? 0 : (int)B;
-    const long long bpt = TR / B; // bags per task
+    const int Bi = (int)B;        // bags of the streamed path hold at most 2^30 rows
+
+    // this warp's rows: tasks [gw * ntasks / nw, (gw + 1) * ntasks / nw)
+    const long long TR = task_rows(B);
+    const long long nw = (long long)gridDim.x * LLP_SW, gw = (long long)blockIdx.x * LLP_SW + warp;
+    const long long wbeg = min(n, (gw * ntasks / nw) * TR), wend = min(n, ((gw + 1) * ntasks / nw) * TR);
+    const int nstages = (int)((wend - wbeg + LLP_SR - 1) / LLP_SR);
 
     if (lane == 0)
         for (int q = 0; q < LLP_NST; q++)
             mbar_init(&bar[warp][q], 1);
     __syncwarp();
-    // producer cursor (lane 0) runs LLP_NST stages ahead of the consumer
-    StageCursor prod{(long long)blockIdx.x * LLP_SW + warp, 0}, cons = prod;
     if (lane == 0)
-        for (int q = 0; q < LLP_NST; q++) {
-            long long r0;
-            int rows;
-            if (!stage_span(prod, TR, n, ntasks, r0, rows))
-                break;
-            issue_stage(ring + q * LLP_SR * d, X, r0, rows, d, &bar[warp][q]);
-            stage_next(prod, TR, n, wstride);
+        for (int q = 0; q < LLP_NST && q < nstages; q++) {
+            const long long r0 = wbeg + (long long)q * LLP_SR;
+            issue_stage(ring + q * LLP_SR * d, X, r0, (int)min((long long)LLP_SR, wend - r0), d, &bar[warp][q]);
         }
 
     float gW[DM], gb = 0.f, gl = 0.f;
@@ -449,15 +481,16 @@ __global__ void __launch_bounds__(LLP_ST) llp_stream_kernel(const float *__restr
 #pragma unroll
     for (int f = 0; f < DM; f++)
         gW[f] = S[f] = 0.f;
-    bool failed = false;
+    long long bag = big ? wbeg / B : 0; // the next bag to finish (bags of a multiple of 32 rows)
+    int rib = 0;                        // rows of that bag seen so far
     int it = 0;
-    long long r0;
-    int rows;
-    int rib = 0; // rows of the current bag seen so far (bags of a multiple of 32 rows)
-    while (stage_span(cons, TR, n, ntasks, r0, rows)) {
+    bool failed = false;
+    for (; it < nstages; it++) {
         const int q = it % LLP_NST;
         float *buf = ring + q * LLP_SR * d;
-        const bool ok = mbar_wait(&bar[warp][q], (uint32_t)(it / LLP_NST) & 1u, spin);
+        const long long r0 = wbeg + (long long)it * LLP_SR;
+        const int rows = (int)min((long long)LLP_SR, wend - r0);
+        const bool ok = mbar_wait_sleep(&bar[warp][q], (uint32_t)(it / LLP_NST) & 1u, spin);
         if (!__all_sync(0xffffffffu, ok)) {
             failed = true;
             break;
@@ -470,83 +503,44 @@ __global__ void __launch_bounds__(LLP_ST) llp_stream_kernel(const float *__restr
             }
             __syncwarp();
         }
-        const long long t0 = cons.t * TR, tend = min(n, t0 + TR);
-        if (cons.k == 0)
-            rib = 0; // a task starts on a bag boundary
-        for (int st = 0; st < rows; st += 32) {
-            const int rr = st + lane;
-            float P0 = 0.f, P1 = 0.f, x[DM];
+        const bool full = rows == LLP_SR;
 #pragma unroll
-            for (int f = 0; f < DM; f++)
-                x[f] = 0.f;
-            if (rr < rows) {
-                const float *xr = buf + rr * d;
-                if ((d & 1) == 0) {
-#pragma unroll
-                    for (int f = 0; f < DM; f += 2)
-                        if (f < d) {
-                            const float2 v = *reinterpret_cast<const float2 *>(xr + f);
-                            x[f] = v.x;
-                            x[f + 1] = v.y;
-                        }
-                } else {
-#pragma unroll
-                    for (int f = 0; f < DM; f++)
-                        if (f < d)
-                            x[f] = xr[f];
-                }
-                float dz = bd;
-#pragma unroll
-                for (int f = 0; f < DM; f++)
-                    dz = fmaf(x[f], w[f], dz);
-                // P1 = sigma(z1 - z0) from e = 2^-|dz2| in (0, 1] (no overflow
-                // either way); 1 + e lies in [1, 2], where the fast divide holds
-                const float e = exp2f(-fabsf(dz));
-                const float a = __fdividef(1.0f, 1.0f + e);
-                P0 = dz >= 0.f ? e * a : a;
-                P1 = dz >= 0.f ? a : e * a;
-            }
-            const float h = P0 * P1;
-            c0 += P0;
-            c1 += P1;
-            T += h;
-#pragma unroll
-            for (int f = 0; f < DM; f++)
-                S[f] = fmaf(h, x[f], S[f]);
-            const long long row0 = r0 + st; // first row of this step
+        for (int st = 0; st < LLP_SR; st += 32) {
+            if (st >= rows)
+                break;
+            if (full)
+                step_rows<DM, true>(buf, st + lane, rows, d, w, bd, c0, c1, T, S);
+            else
+                step_rows<DM, false>(buf, st + lane, rows, d, w, bd, c0, c1, T, S);
+            bool done; // a bag (or, for bags that divide 32, every lane group) ends with this step
             if (big) {
-                // the step ends a bag when the bag is full or the task ends
                 rib += 32;
-                if (rib == B || row0 + 32 >= tend) {
-                    // only the counts are reduced across the warp; S and T
-                    // stay lane partials, scaled by the bag's delta
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-                        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-                    }
-                    // bag index: B > LLP_TASK makes one bag per task; else the
-                    // offset in the task over B by a multiply-shift (exact for
-                    // offsets and B up to 1024, bag_mul = ceil(2^20 / B))
-                    const long long bag =
-                        bpt == 1 ? cons.t : cons.t * bpt + (((uint32_t)(row0 - t0) * bag_mul) >> 20);
-                    finish_bag2<DM>(bag, lane == 0, c0, c1, T, S, target, two_inv, cnt_out, gW, gb, gl);
-                    rib = 0;
-                    c0 = c1 = T = 0.f;
-#pragma unroll
-                    for (int f = 0; f < DM; f++)
-                        S[f] = 0.f;
-                }
+                done = rib == Bi || st + 32 >= rows && it + 1 == nstages; // full, or the last rows
             } else {
-                // bags of Bi lanes (Bi divides 32): aligned lane groups
+                done = true;
                 for (int o = Bi >> 1; o > 0; o >>= 1) {
                     c0 += __shfl_xor_sync(0xffffffffu, c0, o);
                     c1 += __shfl_xor_sync(0xffffffffu, c1, o);
                 }
-                const long long lead = row0 + (lane & ~(Bi - 1)); // the group's first row
-                if (lead < tend)
-                    finish_bag2<DM>(lead >> lgB, (lane & (Bi - 1)) == 0, c0, c1, T, S, target, two_inv, cnt_out,
-                                    gW, gb, gl);
+            }
+            if (big && done) {
+                // only the counts are reduced across the warp; S and T stay
+                // lane partials, scaled by the bag's delta
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+                    c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+                }
+                finish_bag2<DM>(bag, lane == 0, c0, c1, T, S, target, two_inv, cnt_out, gW, gb, gl);
+                bag++;
+                rib = 0;
+            } else if (!big) {
+                const int lead = st + (lane & ~(Bi - 1)); // the lane group's first row in this stage
+                if (lead < rows)
+                    finish_bag2<DM>((r0 + lead) >> lgB, (lane & (Bi - 1)) == 0, c0, c1, T, S, target, two_inv,
+                                    cnt_out, gW, gb, gl);
+            }
+            if (done) {
                 c0 = c1 = T = 0.f;
 #pragma unroll
                 for (int f = 0; f < DM; f++)
@@ -555,30 +549,19 @@ __global__ void __launch_bounds__(LLP_ST) llp_stream_kernel(const float *__restr
         }
         // the stage has been read: lane 0 refills it LLP_NST stages ahead
         __syncwarp();
-        if (lane == 0) {
-            long long pr0;
-            int prows;
-            if (stage_span(prod, TR, n, ntasks, pr0, prows)) {
-                fence_proxy_async_smem();
-                issue_stage(buf, X, pr0, prows, d, &bar[warp][q]);
-                stage_next(prod, TR, n, wstride);
-            }
+        if (lane == 0 && it + LLP_NST < nstages) {
+            const long long pr0 = wbeg + (long long)(it + LLP_NST) * LLP_SR;
+            fence_proxy_async_smem();
+            issue_stage(buf, X, pr0, (int)min((long long)LLP_SR, wend - pr0), d, &bar[warp][q]);
         }
-        stage_next(cons, TR, n, wstride);
-        it++;
     }
     if (failed) {
         // a wait ran out: report it, and let this warp's copies still in
         // flight land (bounded) before the block's shared memory is released
         if (lane == 0) {
             set_status(d_status, TDP_ERR_TIMEOUT);
-            StageCursor c = cons;
-            for (int k = 0; k < LLP_NST; k++, it++) {
-                if (c.t == prod.t && c.k == prod.k)
-                    break; // nothing issued from here on
-                mbar_wait(&bar[warp][it % LLP_NST], (uint32_t)(it / LLP_NST) & 1u, spin);
-                stage_next(c, TR, n, wstride);
-            }
+            for (int k = it; k < nstages && k < it + LLP_NST; k++)
+                mbar_wait_sleep(&bar[warp][k % LLP_NST], (uint32_t)(k / LLP_NST) & 1u, spin);
         }
         gl = gb = 0.f;
 #pragma unroll
@@ -804,7 +787,7 @@ template <int DM, bool EXACT> int stream_blocks_per_sm(int d)
 // (bulk copies of whole stages) and 8-byte aligned targets and counts.
 bool stream_ok(const float *X, const float *targets, const float *cnt, int d, int K, long long B)
 {
-    return K == 2 && d <= 8 && (B % 32 == 0 || 32 % B == 0) && (uintptr_t)X % 16 == 0 &&
+    return K == 2 && d <= 8 && (B % 32 == 0 || 32 % B == 0) && B <= (1ll << 30) && (uintptr_t)X % 16 == 0 &&
            (uintptr_t)targets % 8 == 0 && (uintptr_t)cnt % 8 == 0; // (targets, counts) read and written as pairs
 }
 
@@ -822,14 +805,12 @@ tdp_status launch_stream(const float *X, long long n, int d, long long B, const 
     const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)per_sm * num_sms()));
     const long long nbags = (n + B - 1) / B;
     const float inv = 1.0f / (float)((double)nbags * 2);
-    const uint32_t bag_mul = B <= LLP_TASK ? (uint32_t)(((1u << 20) + B - 1) / B) : 0u;
     if (census)
-        llp_stream_kernel<6, true><<<grid, LLP_ST, stream_smem(d), s>>>(X, n, d, B, bag_mul, W, b, targets, inv,
-                                                                       cnt, part, ntasks, d_status, spin_limit());
+        llp_stream_kernel<6, true><<<grid, LLP_ST, stream_smem(d), s>>>(X, n, d, B, W, b, targets, inv, cnt, part,
+                                                                       ntasks, d_status, spin_limit());
     else
-        llp_stream_kernel<8, false><<<grid, LLP_ST, stream_smem(d), s>>>(X, n, d, B, bag_mul, W, b, targets, inv,
-                                                                        cnt, part, ntasks, d_status,
-                                                                        spin_limit());
+        llp_stream_kernel<8, false><<<grid, LLP_ST, stream_smem(d), s>>>(X, n, d, B, W, b, targets, inv, cnt,
+                                                                        part, ntasks, d_status, spin_limit());
     llp_reduce_kernel<<<1, 128, 0, s>>>(part, grid, 2, d, dW, db, loss);
     return launch_status();
 }

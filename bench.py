@@ -264,7 +264,14 @@ def run_reference(args):
 # and the source file it was built from.  Captures run a smaller case of the
 # same plan; every term of these kernels' traffic grows with those units, so
 # it is scaled by them.  None when the source changed since the capture.
-TRAFFIC = {}
+# DRAM traffic per unit of work from one ncu capture of the kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch over its units), valid while the kernel's source file
+# is unchanged (first 12 hex digits of its sha1).  Summaries with the commands: profiles/.
+TRAFFIC = {
+    # gjr_probe_kernel at 1/4 scale (15M fact rows): 327.60 MB read + 3.19 MB written
+    "gjr_probe": {"src": "paper_2211_02753_b300/csrc/groupjoin.cu", "sha1": "7603544ee7d1",
+                  "bytes_per_unit": (327_599_616 + 3_187_456) / 15_000_000},
+}
 
 
 def measured_traffic(kernel: str, units: float):

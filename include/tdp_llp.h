@@ -54,7 +54,7 @@ size_t tdp_llp_step_workspace(int64_t n, int32_t d, int32_t K, int64_t B);
  * dW [K][d], db [K] of that mean.  Bags never straddle a block's group of
  * rows (groups hold whole bags; a bag longer than one staged chunk is read
  * twice), so each bag's count gradient is formed where its rows are.  Sums
- * are per-block fp32 partials added in block order in float64, so results
+ * are per-block fp32 partials added in float64 in a fixed order, so results
  * are deterministic for a given GPU.  X must be 4-byte aligned.  With two
  * classes, at most 8 features and X 16-byte aligned, the rows stream
  * through shared memory by bulk copies; a bounded wait for one that runs out

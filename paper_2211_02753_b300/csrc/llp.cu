@@ -9,8 +9,8 @@
 // per bag in a fixed order, forms each bag's count gradient from its own
 // target right there, and accumulates the weight gradient from the staged
 // rows.  Blocks are persistent (a grid of at most the resident count) and
-// write one partial row each; a one-block kernel adds the rows in block
-// order in float64.
+// write one partial row each; a one-block kernel adds the rows in float64 in
+// a fixed order.
 #include <algorithm>
 #include <atomic>
 
@@ -607,21 +607,32 @@ __global__ void __launch_bounds__(LLP_ST) llp_stream_kernel(const float *__restr
     }
 }
 
-// dW, db, loss = the sums of the blocks' partial rows, in block order, in float64
-__global__ void llp_reduce_kernel(const float *__restrict__ part, int nblk, int K, int d, float *__restrict__ dW,
-                                  float *__restrict__ db, float *__restrict__ loss)
+// dW, db, loss = the sums of the blocks' partial rows in float64, in a fixed
+// order: a warp per column, lane l adds blocks l, l + 32, ... in order, then
+// a fixed xor tree over the lanes.
+constexpr int LLP_RED_THREADS = 1024;
+
+__global__ void __launch_bounds__(LLP_RED_THREADS) llp_reduce_kernel(const float *__restrict__ part, int nblk, int K,
+                                                                     int d, float *__restrict__ dW,
+                                                                     float *__restrict__ db, float *__restrict__ loss)
 {
     const int per = part_len(K, d);
-    for (int v = threadIdx.x; v < per; v += blockDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = warp; v < per; v += LLP_RED_THREADS / 32) {
         double s = 0.0;
-        for (int b = 0; b < nblk; b++)
+        for (int b = lane; b < nblk; b += 32)
             s += part[(size_t)b * per + v];
-        if (v < K * d)
-            dW[v] = (float)s;
-        else if (v < K * d + K)
-            db[v - K * d] = (float)s;
-        else
-            loss[0] = (float)s;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            if (v < K * d)
+                dW[v] = (float)s;
+            else if (v < K * d + K)
+                db[v - K * d] = (float)s;
+            else
+                loss[0] = (float)s;
+        }
     }
 }
 
@@ -754,7 +765,7 @@ tdp_status launch_step(const float *X, long long n, int d, int K, long long B, c
     const long long nbags = (n + B - 1) / B;
     llp_step_kernel<KM, DM><<<grid, LLP_THREADS, step_smem(d, KM), s>>>(
         X, n, d, K, B, W, b, targets, 1.0f / (float)((double)nbags * K), cnt, part, G, ngroups);
-    llp_reduce_kernel<<<1, 128, 0, s>>>(part, grid, K, d, dW, db, loss);
+    llp_reduce_kernel<<<1, LLP_RED_THREADS, 0, s>>>(part, grid, K, d, dW, db, loss);
     return launch_status();
 }
 
@@ -811,7 +822,7 @@ tdp_status launch_stream(const float *X, long long n, int d, long long B, const 
     else
         llp_stream_kernel<8, false><<<grid, LLP_ST, stream_smem(d), s>>>(X, n, d, B, W, b, targets, inv, cnt,
                                                                         part, ntasks, d_status, spin_limit());
-    llp_reduce_kernel<<<1, 128, 0, s>>>(part, grid, 2, d, dW, db, loss);
+    llp_reduce_kernel<<<1, LLP_RED_THREADS, 0, s>>>(part, grid, 2, d, dW, db, loss);
     return launch_status();
 }
 

@@ -30,6 +30,9 @@ Workload shapes (all synthetic; the paper's own datasets are not available):
   fixed logistic model of the features.  Rows are in random order, so bags
   of consecutive rows are random bags.  Standard Laplace draws for the
   label-DP counts come from a stream of their own.
+* ranked groups (soft ORDER BY ... LIMIT k): fp32 scores x ~ N(0,1), fp32
+  payloads v ~ U[0,100], groups of consecutive rows whose sizes are uniform
+  on [size/2, 3 size/2] (int64 offsets).
 * glyph grids: 4x4 cells of 28x28 uint8 glyphs drawn from 10 seeded stroke
   templates with affine jitter and Gaussian noise (stand-in for the paper's
   MNIST grids, Sec. 5.5).
@@ -373,3 +376,15 @@ def laplace_noise(n_bags: int, k: int, seed: int, stream: int = 130) -> np.ndarr
     """Standard Laplace draws (location 0, scale 1), fp32 [n_bags, k]: the
     random numbers of the label-DP mechanism, scaled by the method."""
     return rng(seed, stream).laplace(0.0, 1.0, (n_bags, k)).astype(np.float32)
+
+
+def ranked_groups(n_groups: int, size: int, seed: int, stream: int = 140) -> dict:
+    """Groups of consecutive rows for a per-group ORDER BY ... LIMIT k: x fp32
+    N(0,1) scores, v fp32 U[0,100] payloads, offsets int64 [n_groups + 1]
+    with group sizes uniform on [size // 2, size + size // 2]."""
+    g = rng(seed, stream)
+    sizes = g.integers(max(1, size // 2), size + size // 2 + 1, n_groups)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offsets[-1])
+    return {"x": g.standard_normal(n).astype(np.float32), "v": g.uniform(0, 100, n).astype(np.float32),
+            "offsets": offsets}

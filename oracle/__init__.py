@@ -19,4 +19,6 @@ Modules:
   dictionary -- order-preserving dictionary codes of string columns.
   llp        -- fp64 learning from label proportions (Sec. 5.3) and its
                 label-DP variant (Sec. 5.4).
+  softsort   -- fp64 soft ORDER BY ... LIMIT k: logistic soft ranks, soft
+                top-k membership and sum, their adjoints; the exact ranks.
 """

@@ -208,6 +208,26 @@ def cpu_llp_sample(n: int = 1_000_000, B: int = 64):
     return n, _timed(q)
 
 
+def cpu_softsort_sample(groups: int = 20):
+    """The float64 oracle's soft top-10 forward and backward on `groups` groups
+    of the ranked-groups workload."""
+    from oracle import softsort as O
+    d = gen.ranked_groups(1000, 1000, gen.BASE_SEED + 11)
+    offs = d["offsets"][:groups + 1]
+    x, v = d["x"][:offs[-1]], d["v"][:offs[-1]]
+    pairs = float(np.sum(np.diff(offs).astype(np.float64) ** 2))
+
+    def q():
+        _, m, _ = O.soft_topk_fwd(x, v, offs, 10, 0.05, 0.5)
+        O.soft_topk_bwd(x, v, offs, 10, 0.05, 0.5, m, dS=np.ones(groups))
+
+    return pairs, _timed(q)
+
+
+# special-function (MUFU) results per SM per clock: 2^x and 1/x of a logistic
+MUFU_PER_SM_CLK = 16
+
+
 def cpu_baseline(fn, unit_scale: float, unit: str, sample: str, parallel_ok: bool = True, **kw):
     """Times the oracle: OpenMP on all host cores (when the function has a
     parallel form) and single-threaded.  Rates are units per second of
@@ -747,6 +767,7 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
     res["trainable_query_glyph_cnn"] = glyph_plan(dev, stream, args, bf16_peak, peak_kind)
     res["trainable_query_digit_x_size"] = pair_plan(dev, stream, args, bf16_peak, peak_kind)
     res.update(llp_plans(dev, stream, args, hbm_peak, peak_kind))
+    res["soft_topk_1000_groups"] = softsort_plan(dev, stream, args)
     return res
 
 
@@ -959,6 +980,43 @@ def llp_plans(dev, stream, args, hbm_peak, peak_kind):
     return out
 
 
+def softsort_plan(dev, stream, args):
+    """Soft ORDER BY x DESC LIMIT 10 per group with the soft top-10 SUM of a
+    payload: 1000 groups of 500..1500 rows (1.01M rows, 1.08e9 ordered
+    pairs), forward + backward (dS = 1), and the exact operator."""
+    import torch
+    from paper_2211_02753_b300 import softsort as ss
+    d = gen.ranked_groups(1000, 1000, gen.BASE_SEED + 11)
+    gx, gv, go = (torch.from_numpy(d[k]).to(dev) for k in ("x", "v", "offsets"))
+    pairs = float(np.sum(np.diff(d["offsets"]).astype(np.float64) ** 2))
+    k, tau, tau_r, mg = 10, 0.05, 0.5, 1500
+    dS = torch.ones(1000, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    fwd = lambda: ss.soft_topk_fwd(gx, gv, go, k, tau, tau_r, max_group=mg, status=st)  # noqa: E731
+    _, mask, _ = fwd()
+    bwd = lambda: ss.soft_topk_bwd(gx, gv, go, k, tau, tau_r, mask, dsum=dS, max_group=mg, status=st)  # noqa: E731
+    exact = lambda: ss.exact_topk(gx, gv, go, k, max_group=mg, status=st)  # noqa: E731
+    for _ in range(3):
+        fwd(), bwd(), exact()
+    reps = max(5, min(args.steps, 30))
+    f_ms, b_ms, e_ms = _events_median([fwd, bwd, exact], stream, reps=reps)
+    if int(st.item()) != 0:
+        raise RuntimeError("soft top-k status %d" % int(st.item()))
+    peak = MUFU_PER_SM_CLK * 148 * 2.032e9 / 1e12  # T special-function results / s
+    n1, s1 = cpu_softsort_sample()
+    ms = f_ms + b_ms
+    return {"rows": int(d["offsets"][-1]), "groups": 1000, "pairs": pairs, "k": k, "tau": tau, "tau_r": tau_r,
+            "fwd_ms": f_ms, "bwd_ms": b_ms, "exact_ms": e_ms, "pairs_per_s": pairs / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": 4 * pairs / (ms / 1e3) / 1e12, "peak": peak,
+                         "unit": "T special-function results/s", "frac": 4 * pairs / (ms / 1e3) / 1e12 / peak,
+                         "traffic": None, "kernel": "ss_rank_kernel<0> + ss_bwd_pair_kernel (2^x and 1/x, "
+                                                    "2 per pair each)",
+                         "peak_kind": "derived: 16 results per SM per clock x 148 SMs x 2032 MHz"},
+            "cpu_baseline": {"value": n1 / s1, "unit": "pairs/s (forward + backward)", "cores": 1, "kind": "oracle",
+                             "host_cores": host_cores(),
+                             "sample": "20 groups (%.2e pairs) through the float64 oracle (%.2f s)" % (n1, s1)}}
+
+
 def run_only(args):
     """One plan at 1/scale of its size, `steps` times after `warmup` runs, and
     a one-line timing (CUDA events).  Used for profiler captures of a small
@@ -989,6 +1047,16 @@ def run_only(args):
     elif args.only == "soft":
         s = gen.soft_table(10_000_000 // sc, 1024, gen.BASE_SEED + 3)
         fn = plans.SoftQuery({k: torch.from_numpy(v).to(dev) for k, v in s.items()}).run
+    elif args.only == "softsort":
+        from paper_2211_02753_b300 import softsort as ss
+        d = gen.ranked_groups(1000 // sc, 1000, gen.BASE_SEED + 11)
+        gx, gv, go = (torch.from_numpy(d[k]).to(dev) for k in ("x", "v", "offsets"))
+        _, mask, _ = ss.soft_topk_fwd(gx, gv, go, 10, 0.05, 0.5, max_group=1500)
+        dS = torch.ones(1000 // sc, device=dev)
+
+        def fn():
+            ss.soft_topk_fwd(gx, gv, go, 10, 0.05, 0.5, max_group=1500)
+            ss.soft_topk_bwd(gx, gv, go, 10, 0.05, 0.5, mask, dsum=dS, max_group=1500)
     elif args.only == "llp":
         from oracle import llp as R  # count labels of the workload
         from paper_2211_02753_b300 import llp
@@ -1027,7 +1095,7 @@ def main():
     ap.add_argument("--plans", default="all", choices=["all", "main"])
     ap.add_argument("--only", default=None,
                     choices=["shipping", "shipping_sep", "pricing", "pricing_sort", "filter", "chain", "soft",
-                             "glyph", "llp"],
+                             "glyph", "llp", "softsort"],
                     help="profiling mode: run one plan at 1/--scale size and print its time only")
     ap.add_argument("--scale", type=int, default=1)
     args = ap.parse_args()

@@ -121,6 +121,12 @@ SIGNATURES = {
     "tdp_exact_pe_count": (_st, [_p, _i64, _i32, _i32, _i32, _p, _p, _p, _p]),
     "tdp_pe_groupby_fwd": (_st, [_p, _i64, _i32, _i32, _i32, _p, _p, _p]),
     "tdp_pe_groupby_bwd": (_st, [_p, _p, _i64, _i32, _i32, _i32, _p, _p]),
+    # soft ORDER BY ... LIMIT k (include/tdp_softsort.h)
+    "tdp_soft_topk_fwd": (_st, [_p, _p, _i64, _p, _i64, _i64, _i32, _f, _f, _p, _p, _p, _p, _p]),
+    "tdp_soft_topk_workspace": (_sz, [_i64]),
+    "tdp_soft_topk_bwd": (_st, [_p, _p, _i64, _p, _i64, _i64, _i32, _f, _f, _p, _p, _p, _p, _p, _p, _p, _sz, _p,
+                                _p]),
+    "tdp_exact_topk": (_st, [_p, _p, _i64, _p, _i64, _i64, _i32, _p, _p, _p, _p]),
     # learning from label proportions (include/tdp_llp.h)
     "tdp_llp_counts": (_st, [_p, _i64, _i32, _i64, _p, _f, _p, _p, _p]),
     "tdp_llp_step_workspace": (_sz, [_i64, _i32, _i32, _i64]),

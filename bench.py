@@ -289,7 +289,7 @@ def run_reference(args):
 # is unchanged (first 12 hex digits of its sha1).  Summaries with the commands: profiles/.
 TRAFFIC = {
     # gjr_probe_kernel at 1/4 scale (15M fact rows): 327.60 MB read + 3.19 MB written
-    "gjr_probe": {"src": "paper_2211_02753_b300/csrc/groupjoin.cu", "sha1": "7603544ee7d1",
+    "gjr_probe": {"src": "paper_2211_02753_b300/csrc/groupjoin.cu", "sha1": "69c6b8e2ce61",
                   "bytes_per_unit": (327_599_616 + 3_187_456) / 15_000_000},
 }
 

@@ -12,29 +12,33 @@
 //   1. build: every qualifying build row sets bit (key - lo) of a bitmap of
 //      D = hi - lo + 1 bits, stored as words of 32 keys with a rank field
 //      beside each word ({bits, rank}: 8 bytes per 32 keys, 3.75 MB for
-//      D = 15M).  A bit that is already set is a duplicate build key.
-//   2. rank: an exclusive scan of the words' popcounts (decoupled look-back
-//      over tiles of 1024 words) writes each word's rank; the code of key k
-//      is then rank[w] + popc(bits[w] below k's bit), a dense number in
-//      0..B-1 in ascending key order (B build keys).  The same pass sets the
-//      B accumulator rows to their initial values.
-//   3. probe: persistent blocks stream tiles of the probe key and predicate
-//      columns through two shared-memory buffers filled by bulk copies.
-//      Phase A: every qualifying row of the tile looks its key up in the
-//      bitmap (one 8-byte load, L2-resident; all of a thread's lookups in
-//      flight together) and the hits (row, code) are queued in shared
-//      memory.  Phase B: all threads take the queue, gather the hits'
-//      aggregate inputs (many gathers in flight per thread) and add them
-//      into accumulator row `code` with 64-bit atomics (L2-resident:
-//      B x slots x 8 bytes); the key's bit is set in a second bitmap of the
-//      matched keys.
-//   4. finalize: tiles of 1024 words; every set bit of the matched-key bitmap
-//      is one output group.  Walking the bits in order walks the keys in
-//      order, so the groups come out sorted with no sort; the key is
-//      lo + 32 w + bit.  Output offsets by decoupled look-back.  With a top-k
-//      request every tile also keeps its k best groups (warp lists merged per
-//      block) and one block merges the per-tile lists.
+//      D = 15M), by atomic ORs; the inserted rows are counted, and fewer set
+//      bits than inserted rows means a duplicate build key.
+//   2. rank (cooperative, one bounded grid barrier): an exclusive scan of
+//      the words' popcounts writes each word's rank; the code of key k is
+//      then rank[w] + popc(bits[w] below k's bit), a dense number in 0..B-1
+//      in ascending key order (B build keys).  The same pass sets the B
+//      accumulator rows to their initial values.
+//   3. probe: every warp works alone on chunks of probe rows that lane 0
+//      bulk-copies into the warp's two shared-memory buffers (completion on
+//      the warp's own mbarrier), so the next chunk's columns are in flight
+//      while the warp works on this one.  Phase A: predicates, then the
+//      bitmap word of every qualifying key (one 8-byte load, L2-resident; all
+//      of a lane's lookups in flight together); a hit sets the key's bit in a
+//      second bitmap of the matched keys and is queued in the warp's own
+//      shared-memory slots.  Phase B: the lanes take the queue, gather the
+//      hits' aggregate inputs and add them into accumulator row `code` with
+//      64-bit atomics (L2-resident: B x slots x 8 bytes).  No block barrier.
+//   4. finalize: a cooperative hit-rank scan over the matched-key bitmap
+//      gives every word its first output position; an output pass walks the
+//      bits in order, which walks the keys in order, so the groups come out
+//      sorted with no sort (key = lo + 32 w + bit, aggregates from row
+//      rank + popc).  With a top-k request, blocks rank their shares of the
+//      groups exactly behind a shared lower bound and one block merges their
+//      candidates.
 //
+// The integer accumulation is exact and order-independent, so the result is
+// bit-identical to join, then group-by, then top-k.
 // Nothing is written per match and no partition or sort of the matches is
 // needed; the per-row traffic is the probe-side columns.
 #include <algorithm>

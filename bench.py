@@ -172,6 +172,41 @@ def cpu_cnn_sample(grids: int = 1):
     return grids * 16, _timed(q)
 
 
+def cpu_dict_sample(n: int = 1_000_000, parallel: bool = False):
+    """Dictionary codes of n strings of the dictionary workload (the oracle:
+    Python's sort of the distinct byte strings), then GROUP BY (code, flag)
+    with the plain C oracle."""
+    from oracle import dictionary as D
+    from oracle import relational as R
+    off, data, vocab, idx = gen.string_column(n, 100_000, gen.BASE_SEED + 7, max_len=24)
+    flag = gen.fact_table(n, 1, gen.BASE_SEED + 7, cols=("flag", "price"))
+    strs = D.split(off, data)
+    out = {}
+
+    def enc():
+        out["codes"] = D.dict_encode(strs)[0]
+
+    s_enc = _timed(enc)
+    s_gb = _timed(lambda: R.groupby([out["codes"].astype(np.int64), flag["flag"]],
+                                    [("sum", flag["price"], None, None), ("count", None, None, None)], n,
+                                    parallel=parallel))
+    return n, s_enc, s_gb
+
+
+def cpu_soft_filter_sample(n: int = 1_000_000):
+    """Soft filter forward + backward in float64 (numpy, one thread)."""
+    from oracle import soft
+    s = gen.soft_table(n, 1024, gen.BASE_SEED + 3)
+    th = np.zeros(1024, np.float32)
+    gm = np.ones(n)
+
+    def q():
+        soft.soft_filter_fwd(s["x"], s["gid"], th, 0.1)
+        soft.soft_filter_bwd(s["x"], s["gid"], th, 0.1, 1024, gm)
+
+    return n, _timed(q)
+
+
 def cpu_pair_sample(grids: int = 1):
     """One Digit x Size query step (forward, backward, Adam) of the float64
     oracle on `grids` grids of 16 cells."""
@@ -279,14 +314,12 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- traffic
 
-# DRAM bytes (read + write) of a kernel from an ncu capture kept in
-# profiles/, per unit of the capture's workload (fact rows, probe rows ...),
-# and the source file it was built from.  Captures run a smaller case of the
-# same plan; every term of these kernels' traffic grows with those units, so
-# it is scaled by them.  None when the source changed since the capture.
-# DRAM traffic per unit of work from one ncu capture of the kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch over its units), valid while the kernel's source file
-# is unchanged (first 12 hex digits of its sha1).  Summaries with the commands: profiles/.
+# DRAM bytes (read + write) of a kernel per unit of its workload (fact rows,
+# probe rows ...) from one ncu capture summarised in profiles/, with the
+# source file it was built from (first 12 hex digits of its sha1).  Captures
+# run a smaller case of the same plan; every term of these kernels' traffic
+# grows with those units, so it is scaled by them.  None when the source
+# changed since the capture.
 TRAFFIC = {
     # gjr_probe_kernel at 1/4 scale (15M fact rows): 327.60 MB read + 3.19 MB written
     "gjr_probe": {"src": "paper_2211_02753_b300/csrc/groupjoin.cu", "sha1": "69c6b8e2ce61",
@@ -554,6 +587,10 @@ def run_gpu(args):
             cpu_shipping_sample, 1.0, "rows/s",
             "1/%d of the workload (%d fact rows, %d dimension rows), plain C oracle" %
             (scale, N_FACT // scale, N_DIM // scale), scale=scale)
+        for name in ("shipping_separate_partition", "shipping_separate_sort"):
+            if name in line.get("plans", {}):
+                line["plans"][name]["cpu_baseline"] = dict(line["cpu_baseline"],
+                                                           note="the same query's oracle as the headline")
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -735,6 +772,13 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
         "ms": ms, "rows_per_s": 10e6 / (ms / 1e3),
         "roofline": roofline("hbm", 10e6 * (4 + 1 + 8), ms / 1e3, hbm_peak, "GB/s",
                              "GROUP BY (dictionary code, flag)", peak_kind=pk)}
+    n1, s_enc, s_gb = cpu_dict_sample()
+    res["dict_encode_10M"]["cpu_baseline"] = {
+        "value": n1 / s_enc, "unit": "strings/s", "cores": 1, "kind": "oracle", "host_cores": host_cores(),
+        "sample": "1M strings of the same column: the oracle's sort of the distinct byte strings (%.2f s)" % s_enc}
+    res["dict_groupby_10M"]["cpu_baseline"] = {
+        "value": n1 / s_gb, "unit": "rows/s", "cores": 1, "kind": "oracle", "host_cores": host_cores(),
+        "sample": "1M rows: the plain C oracle's GROUP BY (code, flag), one thread (%.2f s)" % s_gb}
     del doff, ddat, fl, pr, enc, codes, gcols
     torch.cuda.empty_cache()
     # ---- soft query (10M rows)
@@ -762,6 +806,18 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
         ms = _time_graph(fn, stream, steps)
         res[name] = {"ms": ms, "rows_per_s": 10e6 / (ms / 1e3),
                      "roofline": roofline("hbm", 10e6 * bpr, ms / 1e3, hbm_peak, "GB/s", kern, peak_kind=pk)}
+    n1, s1 = cpu_soft_filter_sample()
+    sfb = {"value": n1 / s1, "unit": "rows/s", "cores": 1, "kind": "oracle", "host_cores": host_cores(),
+           "sample": "1M rows, soft filter forward + backward, float64 numpy, one thread (%.2f s)" % s1}
+    res["soft_filter_fwd_10M"]["cpu_baseline"] = sfb
+    res["soft_filter_bwd_10M"]["cpu_baseline"] = sfb
+    for name in ("soft_agg_fwd_10M", "soft_agg_bwd_10M"):
+        res[name]["cpu_baseline"] = dict(res["soft_query_10M_fwd_bwd"]["cpu_baseline"],
+                                         note="the oracle's soft aggregation forward + backward")
+    # variants of one query share its oracle timing (the oracle has no strategies)
+    for name, base in (("pricing_summary_60M_sort", "pricing_summary_60M_small_domain"),
+                       ("join_chain_100M_sort", "join_chain_100M")):
+        res[name]["cpu_baseline"] = dict(res[base]["cpu_baseline"], note="the same query's oracle as " + base)
     del sd, sq
     torch.cuda.empty_cache()
     res["trainable_query_glyph_cnn"] = glyph_plan(dev, stream, args, bf16_peak, peak_kind)

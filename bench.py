@@ -1082,12 +1082,13 @@ def run_only(args):
     from oracle import cnn as O  # glyph targets: the exact query on true labels
     dev = torch.device("cuda", 0)
     sc = max(1, args.scale)
-    if args.only in ("shipping", "shipping_sep"):
+    if args.only in ("shipping", "shipping_sep", "shipping_sort"):
         f, d = (gen.fact_table(N_FACT // sc, N_DIM // sc, SEED2, cols=("key", "price", "disc", "date")),
                 gen.dim_table(N_DIM // sc, SEED2, cols=("key", "segment")))
         p = plans.ShippingPriority({k: torch.from_numpy(v).to(dev) for k, v in f.items()},
                                    {k: torch.from_numpy(v).to(dev) for k, v in d.items()},
-                                   groupjoin=args.only == "shipping")
+                                   groupjoin=args.only == "shipping",
+                                   groupby_strategy="sort" if args.only == "shipping_sort" else "auto")
         fn = p.run
     elif args.only in ("pricing", "pricing_sort", "filter"):
         t = gen.fact_table(N_FACT // sc, N_DIM // sc, SEED2, cols=("flag", "status", "qty", "price", "disc", "date"))
@@ -1096,10 +1097,12 @@ def run_only(args):
             fn = lambda: ops.filter([td["date"]], [(0, "<=", 2460)])  # noqa: E731
         else:
             fn = plans.PricingSummary(td, "sort" if args.only == "pricing_sort" else "small_domain").run
-    elif args.only == "chain":
+    elif args.only in ("chain", "chain_sort"):
         dd = gen.chain_tables(100_000_000 // sc, 10_000_000 // sc, 1_000_000 // sc, gen.BASE_SEED + 2)
+        srt = args.only == "chain_sort"
         fn = plans.JoinChain({k: torch.from_numpy(v.astype(np.int32) if k == "probe_fk" else v).to(dev)
-                              for k, v in dd.items()}).run
+                              for k, v in dd.items()}, fused=not srt,
+                             groupby_strategy="sort" if srt else "auto").run
     elif args.only == "soft":
         s = gen.soft_table(10_000_000 // sc, 1024, gen.BASE_SEED + 3)
         fn = plans.SoftQuery({k: torch.from_numpy(v).to(dev) for k, v in s.items()}).run
@@ -1150,7 +1153,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plans", default="all", choices=["all", "main"])
     ap.add_argument("--only", default=None,
-                    choices=["shipping", "shipping_sep", "pricing", "pricing_sort", "filter", "chain", "soft",
+                    choices=["shipping", "shipping_sep", "shipping_sort", "pricing", "pricing_sort", "filter", "chain",
+                             "chain_sort", "soft",
                              "glyph", "llp", "softsort"],
                     help="profiling mode: run one plan at 1/--scale size and print its time only")
     ap.add_argument("--scale", type=int, default=1)

@@ -1,12 +1,13 @@
 // K3: onesweep LSD radix sort of (key, uint32 value) pairs, 8-bit digits.
 //
 //  1. One histogram pass reads every key once and counts all digit positions
-//     (per-block shared-memory histograms, warp-aggregated with match_any so
-//     skewed digits do not serialise on one counter).
+//     (per-block shared-memory histograms, warp-aggregated over the lanes
+//     that share a digit so skewed digits do not serialise on one counter).
 //  2. A 256-thread kernel turns each digit position's histogram into
 //     exclusive global offsets.
 //  3. One scatter pass per digit.  A tile of 4096 pairs is ranked in shared
-//     memory (each warp ranks its 512 pairs stably with match_any + popc),
+//     memory (each warp ranks its 512 pairs stably: the lanes that share a
+//     digit come from nine ballots, a lane's rank is their popc below it),
 //     publishes its per-digit counts, and every one of the 256 threads finds
 //     its digit's offset by decoupled look-back over earlier tiles (tile ids
 //     from an atomic ticket; waits bounded).  Pairs are staged in shared
@@ -19,6 +20,21 @@ namespace tdp {
 constexpr unsigned RS_AGG = 1u << 30;
 constexpr unsigned RS_INC = 2u << 30;
 constexpr unsigned RS_VAL = (1u << 30) - 1;
+
+// The lanes of the warp whose 9-bit value (an 8-bit digit, or 256 for "no
+// element") equals this lane's: the AND over the bits of the ballot of the
+// lanes that agree with this lane on that bit.
+__device__ __forceinline__ unsigned digit_peers(unsigned d)
+{
+    unsigned m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; b++) {
+        const unsigned bit = (d >> b) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bb : ~bb;
+    }
+    return m;
+}
 
 template <typename K>
 __global__ void __launch_bounds__(RS_THREADS) radix_hist_kernel(const K *__restrict__ keys, long long n_max,
@@ -39,7 +55,7 @@ __global__ void __launch_bounds__(RS_THREADS) radix_hist_kernel(const K *__restr
         K k = valid ? keys[i] : (K)0;
         for (int p = 0; p < passes; p++) {
             unsigned d = valid ? (unsigned)((k >> (8 * p)) & 0xff) : 0x100u;
-            unsigned peers = __match_any_sync(0xffffffffu, d);
+            unsigned peers = digit_peers(d);
             if (valid && (peers & lt) == 0)
                 atomicAdd(&sh[p * 256 + d], __popc(peers));
         }
@@ -150,7 +166,7 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__re
     }
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; i++) {
-        unsigned peers = __match_any_sync(0xffffffffu, (unsigned)dig[i]);
+        unsigned peers = digit_peers((unsigned)dig[i]);
         unsigned base = wh[dig[i]];
         rank[i] = (unsigned short)(base + __popc(peers & lt));
         __syncwarp();

@@ -85,38 +85,59 @@ __device__ __forceinline__ unsigned long long field_mask(int bits)
     return bits >= 64 ? ~0ull : ((1ull << bits) - 1);
 }
 
-// Writes the packed key of every input row and its payload: the row id, or
-// (CARRY) the value of accumulator slot 1 when that is the only value slot,
-// so that the reduce streams it instead of gathering it by row id.
+// Writes the packed key of every input row and its payload: the row id (or,
+// with `positions`, the input position), or (CARRY) the value of
+// accumulator slot 1 when that is the only value slot, so that the reduce
+// streams it instead of gathering it by row id.
 template <typename K, typename V, bool CARRY>
 __global__ void pack_keys_kernel(KeySet ks, KeyPack kp, AggSet as, long long n, const int32_t *sel,
-                                 const long long *d_nsel, K *keys, V *rows, int32_t *d_status)
+                                 const long long *d_nsel, K *keys, V *rows, bool positions, int32_t *d_status)
 {
     const long long m = d_nsel ? min(*d_nsel, n) : n;
     bool bad = false;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
-        long long row = sel ? sel[i] : i;
-        unsigned long long packed = 0;
-        for (int k = 0; k < ks.n; k++) {
-            long long v = load_int(ks.col[k], ks.dt[k], row);
-            unsigned long long f;
-            if (kp.bounded[k]) {
-                long long d = v - ks.lo[k];
-                if (d < 0 || d >= ks.size[k]) {
-                    bad = true;
-                    d = 0;
-                }
-                f = (unsigned long long)d;
-            } else {
-                int w = kp.bits[k];
-                f = (unsigned long long)v & field_mask(w);
-                if (ks.dt[k] != TDP_U8)
-                    f ^= 1ull << (w - 1);
-            }
-            packed |= f << kp.shift[k];
+    constexpr int U = 4; // rows in flight per thread: their loads are issued together
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += stride * U) {
+        long long row[U];
+        unsigned long long packed[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long i = i0 + u * stride;
+            row[u] = i < m ? (sel ? sel[i] : i) : -1;
+            packed[u] = 0;
         }
-        keys[i] = (K)packed;
-        rows[i] = CARRY ? (V)slot_value(as, 1, row) : (V)row;
+        for (int k = 0; k < ks.n; k++) {
+            long long v[U];
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                v[u] = row[u] >= 0 ? load_int(ks.col[k], ks.dt[k], row[u]) : 0;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                unsigned long long f;
+                if (kp.bounded[k]) {
+                    long long d = v[u] - ks.lo[k];
+                    if (row[u] >= 0 && (d < 0 || d >= ks.size[k])) {
+                        bad = true;
+                        d = 0;
+                    }
+                    f = (unsigned long long)d;
+                } else {
+                    const int w = kp.bits[k];
+                    f = (unsigned long long)v[u] & field_mask(w);
+                    if (ks.dt[k] != TDP_U8)
+                        f ^= 1ull << (w - 1);
+                }
+                packed[u] |= f << kp.shift[k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long i = i0 + u * stride;
+            if (i < m) {
+                keys[i] = (K)packed[u];
+                rows[i] = CARRY ? (V)slot_value(as, 1, row[u]) : (V)(positions ? i : row[u]);
+            }
+        }
     }
     if (bad)
         set_status(d_status, TDP_ERR_OVERFLOW);
@@ -468,6 +489,40 @@ __global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1) seg_reduce_kernel
     }
 }
 
+// Few groups, several value slots: instead of the reduce gathering every
+// slot input by row id (the groups' rows interleave, so each column would be
+// read once per group, at gather latency), the slot values are written into
+// sorted order.  (1) perm_invert: the sort carried input positions j; inv[j]
+// = the sorted position of j, and the sorted payload becomes the identity.
+// (2) perm_slots: the inputs in their own order (sequential reads) write
+// each slot's value at inv[j]; the writes form one ascending stream per
+// group, which L2 gathers into whole lines.  The reduce then streams them.
+constexpr int PERM_MAX_KEY_BITS = 16; // at most 64K groups, so 64K write streams
+
+template <typename V>
+__global__ void perm_invert_kernel(V *sr, long long n, const long long *d_n, uint32_t *inv)
+{
+    const long long m = d_n ? min(*d_n, n) : n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        inv[(long long)sr[i]] = (uint32_t)i;
+        sr[i] = (V)i;
+    }
+}
+
+__global__ void perm_slots_kernel(AggSet as, long long n, const int32_t *sel, const long long *d_n,
+                                  const uint32_t *__restrict__ inv, long long *__restrict__ perm, size_t stride)
+{
+    const long long m = d_n ? min(*d_n, n) : n;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (long long)gridDim.x * blockDim.x) {
+        const long long row = sel ? sel[j] : j;
+        const long long p = inv[j];
+        for (int sl = 1; sl < as.nslots; sl++)
+            perm[(size_t)(sl - 1) * stride + p] = slot_value(as, sl, row);
+    }
+}
+
+static bool use_perm(int key_bits, bool carry) { return !carry && key_bits <= PERM_MAX_KEY_BITS; }
+
 static size_t seg_ws(long long n)
 {
     long long tiles = (n + SR_TILE - 1) / SR_TILE;
@@ -477,7 +532,6 @@ static size_t seg_ws(long long n)
 size_t sort_groupby_ws(long long n, int nkeys, int naggs, int key_bits)
 {
     (void)nkeys;
-    (void)naggs;
     int kb = key_bits <= 32 ? 4 : 8;
     const int vb = 8; // payload: uint32 row id, or the carried int64 value
     size_t b = align_up((size_t)n * 4, 256);                         // filtered row ids
@@ -486,6 +540,8 @@ size_t sort_groupby_ws(long long n, int nkeys, int naggs, int key_bits)
     b += radix_ws_bytes(n, key_bits, kb, vb);
     b += seg_ws(n);
     b += tdp_filter_workspace(n);
+    if (key_bits <= PERM_MAX_KEY_BITS) // inverse positions + one int64 array per value slot
+        b += align_up((size_t)n * 4, 256) + (size_t)naggs * align_up((size_t)n * 8, 256);
     return b;
 }
 
@@ -514,6 +570,15 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
     char *segws = p;
     p += seg_ws(n);
     void *fws = p;
+    p += tdp_filter_workspace(n);
+    const bool perm = use_perm(key_bits, CARRY);
+    uint32_t *inv = (uint32_t *)p;
+    long long *pslots = nullptr;
+    const size_t pstride = align_up((size_t)n * 8, 256) / 8;
+    if (perm) {
+        p += align_up((size_t)n * 4, 256);
+        pslots = (long long *)p;
+    }
 
     const int32_t *rowsel = sel;
     const long long *rowcount = (const long long *)d_nsel;
@@ -529,18 +594,29 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
     KeyPack kp = make_keypack(ks);
     int grid = (int)std::max(1ll, std::min<long long>((n + 255) / 256, (long long)num_sms() * 8));
     if (n > 0)
-        pack_keys_kernel<K, V, CARRY><<<grid, 256, 0, s>>>(ks, kp, as, n, rowsel, rowcount, pk, pr, d_status);
+        pack_keys_kernel<K, V, CARRY><<<grid, 256, 0, s>>>(ks, kp, as, n, rowsel, rowcount, pk, pr, perm, d_status);
     tdp_status st = radix_sort_pairs<K, V>(pk, pr, n, rowcount, key_bits, sk, sr, rws, rws_bytes, d_status, s);
     if (st != TDP_OK)
         return st;
     cudaMemsetAsync(d_ngroups, 0, 8, s);
     if (n == 0)
         return launch_status();
+    AggSet ras = as; // the aggregates as the reduce reads them
+    if (perm) {
+        perm_invert_kernel<V><<<grid, 256, 0, s>>>(sr, n, rowcount, inv);
+        perm_slots_kernel<<<grid, 256, 0, s>>>(as, n, rowsel, rowcount, inv, pslots, pstride);
+        for (int sl = 1; sl < as.nslots; sl++) {
+            ras.sa[sl] = pslots + (size_t)(sl - 1) * pstride;
+            ras.sadt[sl] = TDP_I64;
+            if (ras.sop[sl] == TDP_AGG_SUM_MUL_KMINUS)
+                ras.sop[sl] = TDP_AGG_SUM; // the stored value is already a * (k - b)
+        }
+    }
     cudaMemsetAsync(segws, 0, seg_ws(n), s);
     long long tiles = (n + SR_TILE - 1) / SR_TILE;
     const unsigned sgrid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 3);
     auto launch = [&](auto kern) {
-        kern<<<sgrid, SR_THREADS, 0, s>>>(sk, sr, n, rowcount, ks, kp, as, out, capacity, (long long *)d_ngroups,
+        kern<<<sgrid, SR_THREADS, 0, s>>>(sk, sr, n, rowcount, ks, kp, ras, out, capacity, (long long *)d_ngroups,
                                           (SegRec *)(segws + 256), (unsigned *)segws, d_status, spin_limit());
     };
     // accumulator slots carried through the scan: the smallest of 2, 4, 5, 9 that fits

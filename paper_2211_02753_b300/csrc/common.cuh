@@ -352,6 +352,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
+// Bounded wait for an mbarrier phase that sleeps briefly between polls, so
+// that warps whose stage is still in flight leave the issue slots to warps
+// that have data.  False when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.b32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (done)
+            return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
 // Grid-wide barrier of a cooperative launch: every block adds one to the
 // counter and waits (bounded) until all blocks of this round have.
 __device__ __forceinline__ void grid_barrier(unsigned *counter, unsigned target, uint32_t limit, int32_t *d_status)

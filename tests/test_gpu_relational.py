@@ -190,6 +190,66 @@ def test_groupby_matches_oracle(strategy, n):
         assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), AGGS6[j]
 
 
+# Private per-thread tables (at most 63 accumulators) over millions of rows,
+# with ragged tails, a device row count and an unaligned column.
+STREAM_CASES = [
+    ([4], [("count", None, None, None), ("sum", 6, None, None), ("sum_mul_kminus", 6, 7, 100),
+           ("min", 0, None, None), ("max", 3, None, None), ("avg", 2, None, None)]),
+    ([4, 5], [("count", None, None, None), ("sum", 6, None, None), ("avg", 7, None, None)]),
+]
+
+
+@pytest.mark.parametrize("n", [1_048_576, 1_048_579, 5_000_001])
+@pytest.mark.parametrize("case", [0, 1])
+def test_groupby_small_domain_streamed(n, case):
+    keys, aggs = STREAM_CASES[case]
+    t = _table(n, 900 + n + case)
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w"]
+    cols = [cu(t[k]) for k in names]
+    cols[4] = ops.Col(cols[4], 0, 2)
+    cols[5] = ops.Col(cols[5], -2, 2)
+    preds = [(2, "<", 700), (1, ">=", 10)]
+    out = ops.groupby_agg(cols, keys, aggs, preds=preds, strategy="small_domain")
+    ops.check(out["status"])
+    sel = R.filter([(t["b32"], "<", 700), (t["u8"], ">=", 10)], n)
+    oa = [(op, t[names[a]] if a is not None else None, t[names[b]] if b is not None else None, kk)
+          for op, a, b, kk in aggs]
+    rk, ra = R.groupby([t[names[k]] for k in keys], oa, n, sel=sel)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    for j in range(len(keys)):
+        assert np.array_equal(np_(out["keys"][j], g), rk[:, j])
+    for j in range(len(aggs)):
+        assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), aggs[j]
+
+
+def test_groupby_small_domain_streamed_device_count_and_unaligned_column():
+    n, m = 3_000_000, 2_000_123
+    keys, aggs = STREAM_CASES[0]
+    t = _table(n, 77)
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w"]
+    oa = [(op, t[names[a]] if a is not None else None, t[names[b]] if b is not None else None, kk)
+          for op, a, b, kk in aggs]
+    sel = R.filter([(t["b32"][:m], "<", 700)], m)
+    rk, ra = R.groupby([t["k1"][:m]], oa, m, sel=sel)
+    for unaligned in (False, True):
+        cols = [cu(t[k]) for k in names]
+        if unaligned:  # a 4-byte offset: scalar loads instead of vector loads
+            buf = torch.zeros(n + 1, dtype=torch.int32, device=DEV)
+            buf[1:] = cols[2]
+            cols[2] = buf[1:]
+            assert cols[2].data_ptr() % 16 == 4
+        cols[4] = ops.Col(cols[4], 0, 2)
+        nsel = torch.tensor([m], dtype=torch.int64, device=DEV)
+        out = ops.groupby_agg(cols, keys, aggs, preds=[(2, "<", 700)], n=n, nsel=nsel, strategy="small_domain")
+        ops.check(out["status"])
+        g = int(out["ngroups"].item())
+        assert g == len(rk)
+        assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+        for j in range(len(aggs)):
+            assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), (unaligned, aggs[j])
+
+
 @pytest.mark.parametrize("n", [1, 4099, 300001])
 def test_groupby_partition_large_domain(n):
     """PARTITION over domains of many buckets: one bounded int32 key over

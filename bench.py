@@ -324,6 +324,9 @@ TRAFFIC = {
     # gjr_probe_kernel at 1/4 scale (15M fact rows): 327.60 MB read + 3.19 MB written
     "gjr_probe": {"src": "paper_2211_02753_b300/csrc/groupjoin.cu", "sha1": "69c6b8e2ce61",
                   "bytes_per_unit": (327_599_616 + 3_187_456) / 15_000_000},
+    # llp_stream_kernel<6, true> on 8M census-shaped rows (bags of 64): 193.26 MB read + 0.04 MB written
+    "llp_stream": {"src": "paper_2211_02753_b300/csrc/llp.cu", "sha1": "9e82e8c8ab78",
+                   "bytes_per_unit": (193_255_168 + 37_632) / 8_000_000},
 }
 
 
@@ -999,8 +1002,8 @@ def llp_plans(dev, stream, args, hbm_peak, peak_kind):
     out["llp_64M_bag64_dp"] = {
         "rows": LLP_ROWS, "features": 6, "bag": LLP_BAG, "eps": 0.1, "step_ms": step_ms,
         "rows_per_s": LLP_ROWS / (step_ms / 1e3), "forward_backward_ms": fb_ms, "dp_counts_ms": cnt_ms,
-        "roofline": roofline("hbm", algo, fb_ms / 1e3, hbm_peak, "GB/s", "llp_step_kernel + llp_reduce_kernel",
-                             peak_kind=peak_kind),
+        "roofline": roofline("hbm", algo, fb_ms / 1e3, hbm_peak, "GB/s", "llp_stream_kernel + llp_reduce_kernel",
+                             traffic=measured_traffic("llp_stream", LLP_ROWS), peak_kind=peak_kind),
         "cpu_baseline": {"value": n1 / s1, "unit": "rows/s", "cores": 1, "kind": "oracle",
                          "host_cores": host_cores(),
                          "sample": "one training step of the float64 oracle on 1M rows (%.2f s)" % s1}}

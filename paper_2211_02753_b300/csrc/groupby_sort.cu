@@ -11,12 +11,16 @@
 //     The payload is the row id, or -- when the query has a single value
 //     aggregate besides COUNT -- that row's value itself (e.g. price*(100-disc)),
 //     which spares the reduce a random gather per row.
-//  4. Reduce-by-key over the sorted pairs in one pass: each thread folds 8
-//     consecutive pairs, the block scans (head count, running aggregates)
-//     with the segmented operator (a, b) -> (a.h + b.h, b.h ? b.s : a.s (+) b.s),
-//     tiles chain their carries by decoupled look-back, and the thread that
-//     holds the last pair of a group writes the group (key fields unpacked,
-//     aggregates finalised).  Groups come out in ascending key order.
+//  4. Reduce-by-key over the sorted pairs (one cooperative launch): every
+//     warp folds its run of pairs with the segmented operator
+//     (a, b) -> (a.h + b.h, b.h ? b.s : a.s (+) b.s) over (head count,
+//     running aggregates); after one grid barrier each warp takes the fold
+//     of the runs before it as its carry and re-scans only the part of its
+//     run in which groups end, and the lane that holds the last pair of a
+//     group writes the group (key fields unpacked, aggregates finalised).
+//     Groups come out in ascending key order.
+#include <type_traits>
+
 #include "filter_api.cuh"
 #include "groupby.cuh"
 #include "radix.cuh"
@@ -26,6 +30,7 @@ namespace tdp {
 constexpr int SR_THREADS = 256;
 constexpr int SR_ITEMS = 8;
 constexpr int SR_TILE = SR_THREADS * SR_ITEMS;
+constexpr int SR_WTILE = 32 * SR_ITEMS; // rows a warp scans at a time
 constexpr int SR_MAXS = TDP_MAX_AGGS + 1;
 
 struct KeyPack {
@@ -143,23 +148,21 @@ __global__ void pack_keys_kernel(KeySet ks, KeyPack kp, AggSet as, long long n, 
         set_status(d_status, TDP_ERR_OVERFLOW);
 }
 
-// Look-back record of a tile.  The aggregate and the inclusive prefix live in
-// separate fields so that a reader never sees a half-overwritten value: the
-// fields selected by `flag` (1: aggregate, 2: inclusive) are final once the
-// flag is visible (written with release, read with acquire).
-struct __align__(16) SegRec {
-    unsigned flag;
-    unsigned h_agg;
-    unsigned h_inc;
-    unsigned pad;
-    long long s_agg[SR_MAXS];
-    long long s_inc[SR_MAXS];
-};
-
+// Segmented fold of sorted rows: heads seen, and each slot's aggregate since
+// the last head (the whole span's aggregate when no head was seen).
 template <int SL>
 struct SegValT {
     unsigned h;
     long long s[SL];
+};
+
+// The same with the prefix: each slot's aggregate over the rows before the
+// first head (all rows when there is none).
+template <int SL>
+struct SegPreT {
+    unsigned h;
+    long long s[SL];
+    long long p[SL];
 };
 
 __device__ __forceinline__ long long comb(int op, long long a, long long b)
@@ -179,6 +182,81 @@ __device__ __forceinline__ void seg_combine(const int *ops, int NS, const SegVal
             r.s[j] = b.h ? b.s[j] : comb(ops[j], a.s[j], b.s[j]);
 }
 
+template <int SL>
+__device__ __forceinline__ void seg_combine(const int *ops, int NS, const SegPreT<SL> &a, const SegPreT<SL> &b,
+                                            SegPreT<SL> &r)
+{
+    r.h = a.h + b.h;
+#pragma unroll
+    for (int j = 0; j < SL; j++)
+        if (j < NS) {
+            r.s[j] = b.h ? b.s[j] : comb(ops[j], a.s[j], b.s[j]);
+            r.p[j] = a.h ? a.p[j] : comb(ops[j], a.p[j], b.p[j]);
+        }
+}
+
+template <int SL>
+__device__ __forceinline__ void seg_identity(SegValT<SL> &v, const long long *init)
+{
+    v.h = 0;
+#pragma unroll
+    for (int j = 0; j < SL; j++)
+        v.s[j] = init[j];
+}
+
+template <int SL>
+__device__ __forceinline__ void seg_identity(SegPreT<SL> &v, const long long *init)
+{
+    v.h = 0;
+#pragma unroll
+    for (int j = 0; j < SL; j++)
+        v.s[j] = v.p[j] = init[j];
+}
+
+template <int SL>
+__device__ __forceinline__ void seg_shfl_down(SegValT<SL> &v, int o)
+{
+    v.h = __shfl_down_sync(0xffffffffu, v.h, o);
+#pragma unroll
+    for (int j = 0; j < SL; j++)
+        v.s[j] = __shfl_down_sync(0xffffffffu, v.s[j], o);
+}
+
+template <int SL>
+__device__ __forceinline__ void seg_shfl_down(SegPreT<SL> &v, int o)
+{
+    v.h = __shfl_down_sync(0xffffffffu, v.h, o);
+#pragma unroll
+    for (int j = 0; j < SL; j++) {
+        v.s[j] = __shfl_down_sync(0xffffffffu, v.s[j], o);
+        v.p[j] = __shfl_down_sync(0xffffffffu, v.p[j], o);
+    }
+}
+
+template <int SL>
+__device__ __forceinline__ void seg_shfl_up(SegValT<SL> &v, int o)
+{
+    v.h = __shfl_up_sync(0xffffffffu, v.h, o);
+#pragma unroll
+    for (int j = 0; j < SL; j++)
+        v.s[j] = __shfl_up_sync(0xffffffffu, v.s[j], o);
+}
+
+// Ordered fold of the 32 lanes' values (lane 0 first); the result is lane 0's.
+template <typename SV>
+__device__ __forceinline__ void seg_warp_fold(const int *ops, int NS, SV &v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        SV up = v, r;
+        seg_shfl_down(up, o);
+        seg_combine(ops, NS, v, up, r);
+        if (lane + o < 32)
+            v = r;
+    }
+}
+
 __device__ __forceinline__ void store_key(void *out, int dt, long long pos, long long v)
 {
     switch (dt) {
@@ -189,18 +267,221 @@ __device__ __forceinline__ void store_key(void *out, int dt, long long pos, long
     }
 }
 
-template <typename K, typename V, int SL, bool CARRY>
-__global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1) seg_reduce_kernel(const K *__restrict__ keys,
-                                                                const V *__restrict__ rows, long long n_max,
-                                                                const long long *d_n, KeySet ks, KeyPack kp,
-                                                                AggSet as, DenseOut out, long long cap,
-                                                                long long *d_ngroups, SegRec *recs, unsigned *ticket,
-                                                                int32_t *d_status, uint32_t limit)
+// Where the reduce finds the slot values of sorted position i.
+//   SEG_ROWS:  gathered by the row id the sort carried (slot_value).
+//   SEG_CARRY: slot 1 is the carried value itself (slot 0 counts).
+//   SEG_PERM:  slot j >= 1 at perm[(j - 1) * pstride + i], written into sorted
+//              order beforehand (int64, SUM / MIN / MAX only).
+enum SegMode { SEG_ROWS = 0, SEG_CARRY = 1, SEG_PERM = 2 };
+
+struct SegSrc {
+    const long long *perm;
+    long long pstride;
+};
+
+template <typename K>
+__device__ __forceinline__ void load4_keys(const K *p, K *k)
+{
+    if (sizeof(K) == 4) {
+        const uint4 v = __ldg((const uint4 *)p);
+        k[0] = (K)v.x, k[1] = (K)v.y, k[2] = (K)v.z, k[3] = (K)v.w;
+    } else {
+        const ulonglong2 a = __ldg((const ulonglong2 *)p), b = __ldg((const ulonglong2 *)p + 1);
+        k[0] = (K)a.x, k[1] = (K)a.y, k[2] = (K)b.x, k[3] = (K)b.y;
+    }
+}
+
+// Folds the sorted rows i0 .. i0 + SR_ITEMS - 1 that lie in [lo, end) into m
+// (and, with PRE, into the prefix part of m): heads are marked in *headmask,
+// and the first / last head position lowers *first / raises *last.  The
+// rows before i0 (keys[i0 - 1]) decide whether i0 is a head.  i0 is a
+// multiple of SR_ITEMS.
+template <typename K, typename V, int SL, int MODE, typename SV>
+__device__ __forceinline__ void seg_lane_fold(const K *__restrict__ keys, const V *__restrict__ rows,
+                                              const AggSet &as, const SegSrc &src, long long i0, long long lo,
+                                              long long end, const int *ops, const long long *init, int NS, SV &m,
+                                              unsigned *headmask, long long *first, long long *last)
+{
+    constexpr bool PRE = std::is_same<SV, SegPreT<SL>>::value;
+    K prev = (i0 > 0 && i0 < end) ? keys[i0 - 1] : (K)0;
+    unsigned hm = 0;
+#pragma unroll
+    for (int half = 0; half < SR_ITEMS / 4; half++) {
+        const long long b = i0 + half * 4;
+        const bool full = b + 4 <= end;
+        K kk[4];
+        if (full) {
+            load4_keys(keys + b, kk);
+        } else {
+#pragma unroll
+            for (int it = 0; it < 4; it++)
+                kk[it] = b + it < end ? keys[b + it] : (K)0;
+        }
+        // heads and active rows of these four
+        unsigned hb = 0, act = 0;
+#pragma unroll
+        for (int it = 0; it < 4; it++) {
+            const long long i = b + it;
+            if (i < end) {
+                const bool head = i == 0 || kk[it] != prev;
+                prev = kk[it];
+                if (i >= lo) {
+                    act |= 1u << it;
+                    if (head) {
+                        hb |= 1u << it;
+                        *first = *first < 0 ? i : *first;
+                        *last = i;
+                    }
+                }
+            }
+        }
+        hm |= hb << (half * 4);
+        const unsigned h0 = m.h;
+        const unsigned fb = h0 == 0 ? hb & (0u - hb) : 0u; // the lane's first head, if here
+        m.h += __popc(hb);
+        if (MODE == SEG_PERM) {
+            // slot by slot: four values live at a time
+#pragma unroll
+            for (int j = 0; j < SL; j++) {
+                if (j >= NS)
+                    continue;
+                long long v[4];
+                if (j == 0) {
+                    v[0] = v[1] = v[2] = v[3] = 1;
+                } else if (full) {
+                    const longlong2 *q = (const longlong2 *)(src.perm + (j - 1) * src.pstride + b);
+                    const longlong2 x = __ldg(q), y = __ldg(q + 1);
+                    v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
+                } else {
+#pragma unroll
+                    for (int it = 0; it < 4; it++)
+                        v[it] = b + it < end ? src.perm[(j - 1) * src.pstride + b + it] : 0;
+                }
+                long long sj = m.s[j];
+#pragma unroll
+                for (int it = 0; it < 4; it++) {
+                    if (!(act >> it & 1))
+                        continue;
+                    if (hb >> it & 1) {
+                        if constexpr (PRE) {
+                            if (fb >> it & 1)
+                                m.p[j] = sj;
+                        }
+                        sj = init[j];
+                    }
+                    sj = comb(ops[j], sj, v[it]);
+                }
+                m.s[j] = sj;
+            }
+        } else {
+#pragma unroll
+            for (int it = 0; it < 4; it++) {
+                if (!(act >> it & 1))
+                    continue;
+                const long long i = b + it;
+                if (hb >> it & 1) {
+                    if constexpr (PRE) {
+                        if (fb >> it & 1) {
+#pragma unroll
+                            for (int j = 0; j < SL; j++)
+                                m.p[j] = m.s[j];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < SL; j++)
+                        m.s[j] = init[j];
+                }
+                if (MODE == SEG_CARRY) {
+                    m.s[0] += 1;
+                    m.s[1] = comb(ops[1], m.s[1], (long long)rows[i]);
+                } else {
+                    const long long row = (long long)rows[i];
+#pragma unroll
+                    for (int j = 0; j < SL; j++)
+                        if (j < NS)
+                            m.s[j] = comb(ops[j], m.s[j], slot_value(as, j, row));
+                }
+            }
+        }
+    }
+    if constexpr (PRE) {
+        if (m.h == 0) {
+#pragma unroll
+            for (int j = 0; j < SL; j++)
+                m.p[j] = m.s[j];
+        }
+    }
+    *headmask = hm;
+}
+
+// Writes group g: its key fields unpacked from the sorted key, and every
+// aggregate from its accumulator slot (AVG from its sum and the count).
+template <typename K, int SL>
+__device__ __forceinline__ void emit_group(long long g, K key, const long long *acc, int NS, const KeySet &ks,
+                                           const KeyPack &kp, const AggSet &as, const DenseOut &out)
+{
+    const unsigned long long packed = (unsigned long long)key;
+    for (int k = 0; k < ks.n; k++) {
+        unsigned long long f = (packed >> kp.shift[k]) & field_mask(kp.bits[k]);
+        long long v;
+        if (kp.bounded[k]) {
+            v = ks.lo[k] + (long long)f;
+        } else {
+            const int w = kp.bits[k];
+            if (ks.dt[k] != TDP_U8)
+                f ^= 1ull << (w - 1);
+            v = w >= 64 ? (long long)f : (long long)(f << (64 - w)) >> (64 - w);
+            if (ks.dt[k] == TDP_U8)
+                v = (long long)f;
+        }
+        store_key(out.key_out[k], out.key_dt[k], g, v);
+    }
+#pragma unroll
+    for (int j = 0; j < SL; j++) {
+        if (j >= NS)
+            continue;
+        for (int a = 0; a < as.n; a++) {
+            if (as.slot[a] != j)
+                continue;
+            long long v = acc[j];
+            if (as.op[a] == TDP_AGG_AVG) {
+                const long long c = acc[0], sg = v > 0 ? 1 : (v < 0 ? -1 : 0);
+                v = (2 * v + sg * c) / (2 * c);
+            }
+            out.agg_out[a][g] = v;
+        }
+    }
+}
+
+// Reduce-by-key of the sorted rows: one cooperative launch, every warp owning
+// a contiguous run of whole 256-row tiles (the runs of a block are adjacent).
+//   1. Each warp folds its run into (heads, aggregates since the last head,
+//      aggregates before the first head) and notes its first and last head;
+//      a block's (heads, aggregates since the last head) is the ordered fold
+//      of its warps' and goes to global memory.
+//   2. One bounded grid barrier.
+//   3. Each warp's carry is the ordered fold of everything before its run.
+//      Lane 0 writes the group that ends inside the run before its first
+//      head (carry + prefix), and, in the run that holds the final row, the
+//      group from the last head to the end.  Groups that both start and end
+//      inside the run exist only between its first and last head: just that
+//      span is read again and scanned, and the lane holding a group's last
+//      row writes it.
+// With few groups hardly a run holds two heads, so the rows are read once;
+// with many every run is read twice, still at streaming rate: no warp waits
+// on another except at the barrier.
+template <typename K, typename V, int SL, int MODE>
+__global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1)
+    seg_reduce_kernel(const K *__restrict__ keys, const V *__restrict__ rows, SegSrc src, long long n_max,
+                      const long long *d_n, KeySet ks, KeyPack kp, AggSet as, DenseOut out, long long cap,
+                      long long *d_ngroups, SegValT<SL> *recs, unsigned *barrier, int32_t *d_status, uint32_t limit)
 {
     using SV = SegValT<SL>;
-    __shared__ long long s_tile;
-    __shared__ SV s_warp[SR_THREADS / 32];
-    __shared__ SV s_carry;
+    using SP = SegPreT<SL>;
+    constexpr int WARPS = SR_THREADS / 32;
+    __shared__ SP s_wrec[WARPS];
+    __shared__ long long s_wfirst[WARPS], s_wlast[WARPS];
+    __shared__ SV s_red[WARPS];
     __shared__ int s_ops[SR_MAXS];
     __shared__ long long s_init[SR_MAXS];
     // parameter structs indexed with run-time indices live in shared memory
@@ -212,280 +493,231 @@ __global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1) seg_reduce_kernel
         s_out = out;
     }
     if (threadIdx.x < SR_MAXS) {
-        int s = threadIdx.x, op = as.sop[s] == TDP_AGG_COUNT ? TDP_AGG_SUM : as.sop[s];
+        const int s = threadIdx.x, op = as.sop[s] == TDP_AGG_COUNT ? TDP_AGG_SUM : as.sop[s];
         s_ops[s] = op;
         s_init[s] = op == TDP_AGG_MIN ? 0x7fffffffffffffffll : op == TDP_AGG_MAX ? (long long)0x8000000000000000ull : 0;
     }
-    const long long n = d_n ? min(*d_n, n_max) : n_max;
-    // persistent: tiles are taken in ticket order until the input runs out
-    for (;;) {
-    if (threadIdx.x == 0)
-        s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
-    const long long tile = s_tile;
-    const long long tile_base = tile * SR_TILE;
-    if (tile_base >= n)
-        return;
+    const long long n = d_n ? min(*d_n, n_max) : n_max;
     const int NS = as.nslots;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long i0 = tile_base + (long long)threadIdx.x * SR_ITEMS;
     int ops[SL];
+    long long init[SL];
 #pragma unroll
-    for (int j = 0; j < SL; j++)
+    for (int j = 0; j < SL; j++) {
         ops[j] = s_ops[j];
+        init[j] = s_init[j];
+    }
+    const long long tiles = (n + SR_WTILE - 1) / SR_WTILE;
+    const long long nw = (long long)gridDim.x * WARPS;
+    const long long per = (tiles + nw - 1) / nw;
+    const long long gw = (long long)blockIdx.x * WARPS + warp;
+    const long long ws = min(n, gw * per * SR_WTILE), we = min(n, ws + per * SR_WTILE);
 
-    // thread fold: (heads, aggregates since the last head)
-    SV mine;
-    mine.h = 0;
-#pragma unroll
-    for (int j = 0; j < SL; j++)
-        mine.s[j] = s_init[j];
-    K prev = (i0 > 0 && i0 - 1 < n) ? keys[i0 - 1] : (K)0;
-    unsigned headmask = 0;
-    for (int it = 0; it < SR_ITEMS; it++) {
-        long long i = i0 + it;
-        if (i >= n)
-            break;
-        K key = keys[i];
-        bool head = (i == 0) || key != prev;
-        prev = key;
-        if (head) {
-            headmask |= 1u << it;
-            mine.h++;
-#pragma unroll
-            for (int j = 0; j < SL; j++)
-                mine.s[j] = s_init[j];
-        }
-        if (CARRY) { // count + the carried value of slot 1
-            mine.s[0] += 1;
-            mine.s[1] = comb(ops[1], mine.s[1], (long long)rows[i]);
-        } else {
-            const long long row = (long long)rows[i];
-#pragma unroll
-            for (int j = 0; j < SL; j++)
-                if (j < NS)
-                    mine.s[j] = comb(ops[j], mine.s[j], slot_value(as, j, row));
-        }
-    }
-    // warp inclusive scan
-    SV inc = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        SV up;
-        up.h = __shfl_up_sync(0xffffffffu, inc.h, o);
-#pragma unroll
-        for (int j = 0; j < SL; j++)
-            up.s[j] = __shfl_up_sync(0xffffffffu, inc.s[j], o);
-        if (lane >= o) {
-            SV r;
-            seg_combine(ops, NS, up, inc, r);
-            inc = r;
-        }
-    }
-    if (lane == 31)
-        s_warp[warp] = inc;
-    // lane-exclusive within the warp
-    SV lex;
-    lex.h = __shfl_up_sync(0xffffffffu, inc.h, 1);
-#pragma unroll
-    for (int j = 0; j < SL; j++)
-        lex.s[j] = __shfl_up_sync(0xffffffffu, inc.s[j], 1);
-    if (lane == 0) {
-        lex.h = 0;
-#pragma unroll
-        for (int j = 0; j < SL; j++)
-            lex.s[j] = s_init[j];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        // tile aggregate = fold of the warp totals (every lane computes it)
-        SV agg = s_warp[0];
-        for (int w = 1; w < SR_THREADS / 32; w++) {
-            SV r;
-            seg_combine(ops, NS, agg, s_warp[w], r);
-            agg = r;
-        }
-        SegRec *me = recs + tile;
-        SV excl;
-        excl.h = 0;
-#pragma unroll
-        for (int j = 0; j < SL; j++)
-            excl.s[j] = s_init[j];
-        if (tile == 0) {
+    // 1. fold of the run; lane 0 keeps the run's record in s_wrec[warp]
+    if (lane == 0)
+        seg_identity(s_wrec[warp], init);
+    long long first = -1, last = -1;
+    for (long long t = ws; t < we; t += SR_WTILE) {
+        SP m;
+        seg_identity(m, init);
+        unsigned hm;
+        seg_lane_fold<K, V, SL, MODE>(keys, rows, s_as, src, t + lane * SR_ITEMS, ws, we, ops, init, NS, m, &hm,
+                                      &first, &last);
+        if (__any_sync(0xffffffffu, hm != 0)) {
+            seg_warp_fold(ops, NS, m);
             if (lane == 0) {
-                me->h_inc = agg.h;
-#pragma unroll
-                for (int j = 0; j < SL; j++)
-                    if (j < NS)
-                        me->s_inc[j] = agg.s[j];
-                __threadfence();
-                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(2u) : "memory");
+                SP r;
+                seg_combine(ops, NS, s_wrec[warp], m, r);
+                s_wrec[warp] = r;
             }
         } else {
-            if (lane == 0) {
-                me->h_agg = agg.h;
+            // no head in the tile: a plain ordered fold, added to the
+            // aggregates since the last head and, before the first, to the prefix
 #pragma unroll
-                for (int j = 0; j < SL; j++)
-                    if (j < NS)
-                        me->s_agg[j] = agg.s[j];
-                __threadfence();
-                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(1u) : "memory");
-            }
-            // warp-parallel look-back: lane l reads the record of tile base-l;
-            // the records up to the nearest inclusive one are folded in order
-            // (earlier tiles first) and prepended to what was gathered so far.
-            long long base = tile - 1;
-            while (true) {
-                const long long t = base - lane;
-                unsigned f = 2;
-                SV pv;
-                pv.h = 0;
-#pragma unroll
-                for (int j = 0; j < SL; j++)
-                    pv.s[j] = s_init[j];
-                if (t >= 0) {
-                    const SegRec *pr = recs + t;
-                    uint32_t polls = 0;
-                    while (true) {
-                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&pr->flag) : "memory");
-                        if (f != 0)
-                            break;
-                        if (polls++ >= limit || ((polls & 63) == 0 && timed_out_already(d_status))) {
-                            set_status(d_status, TDP_ERR_TIMEOUT);
-                            break; // f == 0: treated as an (empty) inclusive record
-                        }
-                        __nanosleep(polls < 64 ? 20 : 200);
-                    }
-                    if (f != 0) {
-                        pv.h = f == 2 ? *(volatile const unsigned *)&pr->h_inc : *(volatile const unsigned *)&pr->h_agg;
-#pragma unroll
-                        for (int j = 0; j < SL; j++)
-                            if (j < NS)
-                                pv.s[j] = f == 2 ? *(volatile const long long *)&pr->s_inc[j]
-                                                 : *(volatile const long long *)&pr->s_agg[j];
-                    }
-                }
-                const unsigned incl_mask = __ballot_sync(0xffffffffu, f != 1);
-                const int k = incl_mask ? __ffs(incl_mask) - 1 : 31;
-                SV w;
-                w.h = 0;
-#pragma unroll
-                for (int j = 0; j < SL; j++)
-                    w.s[j] = s_init[j];
-                for (int src = k; src >= 0; src--) { // k is warp-uniform
-                    SV pj, r;
-                    pj.h = __shfl_sync(0xffffffffu, pv.h, src);
-#pragma unroll
-                    for (int j = 0; j < SL; j++)
-                        pj.s[j] = __shfl_sync(0xffffffffu, pv.s[j], src);
-                    seg_combine(ops, NS, w, pj, r);
-                    w = r;
-                }
-                SV r;
-                seg_combine(ops, NS, w, excl, r);
-                excl = r;
-                if (incl_mask)
-                    break;
-                base -= 32;
-            }
-            if (lane == 0) {
-                SV incl;
-                seg_combine(ops, NS, excl, agg, incl);
-                me->h_inc = incl.h;
-#pragma unroll
-                for (int j = 0; j < SL; j++)
-                    if (j < NS)
-                        me->s_inc[j] = incl.s[j];
-                __threadfence();
-                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&me->flag), "r"(2u) : "memory");
-            }
-        }
-        if (lane == 0)
-            s_carry = excl;
-    }
-    __syncthreads();
-    // carry into this thread = tile excl (+) warps before (+) lanes before
-    SV carry = s_carry;
-    for (int w = 0; w < warp; w++) {
-        SV r;
-        seg_combine(ops, NS, carry, s_warp[w], r);
-        carry = r;
-    }
-    {
-        SV r;
-        seg_combine(ops, NS, carry, lex, r);
-        carry = r;
-    }
-    // emit groups that end inside this thread's items
-    long long g = (long long)carry.h - 1;
-    SV run = carry;
-    for (int it = 0; it < SR_ITEMS; it++) {
-        long long i = i0 + it;
-        if (i >= n)
-            break;
-        if (headmask >> it & 1) {
-            g++;
-#pragma unroll
-            for (int j = 0; j < SL; j++)
-                run.s[j] = s_init[j];
-        }
-        if (CARRY) {
-            run.s[0] += 1;
-            run.s[1] = comb(ops[1], run.s[1], (long long)rows[i]);
-        } else {
-            const long long row = (long long)rows[i];
-#pragma unroll
-            for (int j = 0; j < SL; j++)
-                if (j < NS)
-                    run.s[j] = comb(ops[j], run.s[j], slot_value(as, j, row));
-        }
-        bool last = (i == n - 1);
-        K key = keys[i];
-        if (!last)
-            last = keys[i + 1] != key;
-        if (last) {
-            if (g >= 0 && g < cap) {
-                unsigned long long packed = (unsigned long long)key;
-                for (int k = 0; k < ks.n; k++) {
-                    unsigned long long f = (packed >> kp.shift[k]) & field_mask(kp.bits[k]);
-                    long long v;
-                    if (kp.bounded[k]) {
-                        v = ks.lo[k] + (long long)f;
-                    } else {
-                        int w = kp.bits[k];
-                        if (ks.dt[k] != TDP_U8)
-                            f ^= 1ull << (w - 1);
-                        v = w >= 64 ? (long long)f : (long long)(f << (64 - w)) >> (64 - w);
-                        if (ks.dt[k] == TDP_U8)
-                            v = (long long)f;
-                    }
-                    store_key(s_out.key_out[k], s_out.key_dt[k], g, v);
-                }
-                // aggregates by slot (compile-time slot index; AVG needs the count)
+            for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
                 for (int j = 0; j < SL; j++) {
-                    if (j >= NS)
-                        continue;
-                    for (int a = 0; a < s_as.n; a++) {
-                        if (s_as.slot[a] != j)
-                            continue;
-                        long long v = run.s[j];
-                        if (s_as.op[a] == TDP_AGG_AVG) {
-                            long long c = run.s[0], sg = v > 0 ? 1 : (v < 0 ? -1 : 0);
-                            v = (2 * v + sg * c) / (2 * c);
-                        }
-                        s_out.agg_out[a][g] = v;
-                    }
+                    const long long u = __shfl_down_sync(0xffffffffu, m.s[j], o);
+                    if (j < NS && lane + o < 32)
+                        m.s[j] = comb(ops[j], m.s[j], u);
                 }
             }
-            if (i == n - 1) {
-                *d_ngroups = g + 1;
-                if (g + 1 > cap)
-                    set_status(d_status, TDP_ERR_CAPACITY);
+            if (lane == 0) {
+                SP &w = s_wrec[warp];
+#pragma unroll
+                for (int j = 0; j < SL; j++)
+                    if (j < NS) {
+                        w.s[j] = comb(ops[j], w.s[j], m.s[j]);
+                        if (w.h == 0)
+                            w.p[j] = comb(ops[j], w.p[j], m.s[j]);
+                    }
             }
         }
     }
-    __syncthreads(); // s_warp / s_carry are reused by the next tile
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long f = __shfl_xor_sync(0xffffffffu, first, o);
+        first = first < 0 ? f : (f < 0 ? first : min(first, f));
+        last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+    }
+    if (lane == 0) {
+        s_wfirst[warp] = first;
+        s_wlast[warp] = last;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SV b;
+        seg_identity(b, init);
+        for (int w = 0; w < WARPS; w++) {
+            SV x, r;
+            x.h = s_wrec[w].h;
+#pragma unroll
+            for (int j = 0; j < SL; j++)
+                x.s[j] = s_wrec[w].s[j];
+            seg_combine(ops, NS, b, x, r);
+            b = r;
+        }
+        recs[blockIdx.x] = b;
+    }
+    grid_barrier(barrier, gridDim.x, limit, d_status);
+
+    // 3. carry: thread t folds the records of blocks [t * q, (t + 1) * q)
+    // before this one, then the lanes and warps are folded in order, then
+    // the warps of this block before this one
+    SV carry;
+    {
+        const int nb = blockIdx.x, q = (nb + SR_THREADS - 1) / SR_THREADS;
+        SV part;
+        seg_identity(part, init);
+        const int r0 = threadIdx.x * q, r1 = min(nb, r0 + q);
+        for (int r = r0; r < r1; r++) {
+            SV rec, x;
+            rec.h = __ldcg(&recs[r].h);
+#pragma unroll
+            for (int j = 0; j < SL; j++)
+                rec.s[j] = j < NS ? __ldcg(&recs[r].s[j]) : init[j];
+            seg_combine(ops, NS, part, rec, x);
+            part = x;
+        }
+        seg_warp_fold(ops, NS, part);
+        if (lane == 0)
+            s_red[warp] = part;
+        __syncthreads();
+        seg_identity(carry, init);
+        for (int w = 0; w < WARPS; w++) {
+            SV x;
+            seg_combine(ops, NS, carry, s_red[w], x);
+            carry = x;
+        }
+        for (int w = 0; w < warp; w++) {
+            SV x, y;
+            x.h = s_wrec[w].h;
+#pragma unroll
+            for (int j = 0; j < SL; j++)
+                x.s[j] = s_wrec[w].s[j];
+            seg_combine(ops, NS, carry, x, y);
+            carry = y;
+        }
+    }
+    if (ws >= n)
+        return;
+    const SP &me = s_wrec[warp];
+    const long long f = s_wfirst[warp], l = s_wlast[warp];
+    const bool holds_end = we == n;
+    if (lane == 0) {
+        if ((me.h > 0 || holds_end) && carry.h > 0) {
+            // the group open at the run's start: carry + the rows before the first head
+            long long v[SL];
+#pragma unroll
+            for (int j = 0; j < SL; j++)
+                v[j] = j < NS ? comb(ops[j], carry.s[j], me.p[j]) : 0;
+            const long long g = (long long)carry.h - 1;
+            if (g < cap)
+                emit_group<K, SL>(g, me.h > 0 ? keys[f - 1] : keys[n - 1], v, NS, ks, kp, s_as, s_out);
+        }
+        if (holds_end) {
+            const long long total = (long long)carry.h + me.h;
+            if (me.h > 0 && total - 1 < cap) // the group from the last head to the final row
+                emit_group<K, SL>(total - 1, keys[n - 1], me.s, NS, ks, kp, s_as, s_out);
+            *d_ngroups = total;
+            if (total > cap)
+                set_status(d_status, TDP_ERR_CAPACITY);
+        }
+    }
+    if (me.h < 2)
+        return;
+    // groups that start and end inside the run: rows [f, l), scanned from the
+    // tile that holds f; rows before f are skipped (their sum is in no such group)
+    SV wcarry;
+    seg_identity(wcarry, init);
+    wcarry.h = carry.h;
+    for (long long t = ws + (f - ws) / SR_WTILE * SR_WTILE; t < l; t += SR_WTILE) {
+        const long long i0 = t + lane * SR_ITEMS;
+        SV mine;
+        seg_identity(mine, init);
+        unsigned headmask;
+        long long dummy_f = -1, dummy_l = -1;
+        seg_lane_fold<K, V, SL, MODE>(keys, rows, s_as, src, i0, f, l, ops, init, NS, mine, &headmask, &dummy_f,
+                                      &dummy_l);
+        SV inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            SV up = inc, r;
+            seg_shfl_up(up, o);
+            seg_combine(ops, NS, up, inc, r);
+            if (lane >= o)
+                inc = r;
+        }
+        SV lex = inc, total = inc;
+        seg_shfl_up(lex, 1);
+        if (lane == 0)
+            seg_identity(lex, init);
+        total.h = __shfl_sync(0xffffffffu, inc.h, 31);
+#pragma unroll
+        for (int j = 0; j < SL; j++)
+            total.s[j] = __shfl_sync(0xffffffffu, inc.s[j], 31);
+        SV run;
+        seg_combine(ops, NS, wcarry, lex, run);
+        {
+            SV x;
+            seg_combine(ops, NS, wcarry, total, x);
+            wcarry = x;
+        }
+        // write the groups that end inside this lane's rows (all end before l)
+        long long g = (long long)run.h - 1;
+        for (int it = 0; it < SR_ITEMS; it++) {
+            const long long i = i0 + it;
+            if (i >= l)
+                break;
+            if (i < f)
+                continue;
+            if (headmask >> it & 1) {
+                g++;
+#pragma unroll
+                for (int j = 0; j < SL; j++)
+                    run.s[j] = init[j];
+            }
+            if (MODE == SEG_CARRY) {
+                run.s[0] += 1;
+                run.s[1] = comb(ops[1], run.s[1], (long long)rows[i]);
+            } else if (MODE == SEG_PERM) {
+                run.s[0] += 1;
+#pragma unroll
+                for (int j = 1; j < SL; j++)
+                    if (j < NS)
+                        run.s[j] = comb(ops[j], run.s[j], src.perm[(j - 1) * src.pstride + i]);
+            } else {
+                const long long row = (long long)rows[i];
+#pragma unroll
+                for (int j = 0; j < SL; j++)
+                    if (j < NS)
+                        run.s[j] = comb(ops[j], run.s[j], slot_value(s_as, j, row));
+            }
+            const K key = keys[i];
+            if (keys[i + 1] != key && g < cap)
+                emit_group<K, SL>(g, key, run.s, NS, ks, kp, s_as, s_out);
+        }
     }
 }
 
@@ -493,40 +725,65 @@ __global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1) seg_reduce_kernel
 // slot input by row id (the groups' rows interleave, so each column would be
 // read once per group, at gather latency), the slot values are written into
 // sorted order.  (1) perm_invert: the sort carried input positions j; inv[j]
-// = the sorted position of j, and the sorted payload becomes the identity.
-// (2) perm_slots: the inputs in their own order (sequential reads) write
-// each slot's value at inv[j]; the writes form one ascending stream per
-// group, which L2 gathers into whole lines.  The reduce then streams them.
+// = the sorted position of j.  (2) perm_slots: the inputs in their own
+// order (sequential reads) write each slot's value at inv[j]; the writes
+// form one ascending stream per group, which L2 gathers into whole lines.
+// The reduce then streams them (SEG_PERM) and reads no payload.
 constexpr int PERM_MAX_KEY_BITS = 16; // at most 64K groups, so 64K write streams
 
 template <typename V>
-__global__ void perm_invert_kernel(V *sr, long long n, const long long *d_n, uint32_t *inv)
+__global__ void perm_invert_kernel(const V *__restrict__ sr, long long n, const long long *d_n, uint32_t *inv)
 {
+    constexpr int U = 4; // positions in flight per thread
     const long long m = d_n ? min(*d_n, n) : n;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
-        inv[(long long)sr[i]] = (uint32_t)i;
-        sr[i] = (V)i;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += step * U) {
+        long long j[U];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            j[u] = i0 + u * step < m ? (long long)sr[i0 + u * step] : -1;
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (j[u] >= 0)
+                inv[j[u]] = (uint32_t)(i0 + u * step);
     }
 }
 
 __global__ void perm_slots_kernel(AggSet as, long long n, const int32_t *sel, const long long *d_n,
                                   const uint32_t *__restrict__ inv, long long *__restrict__ perm, size_t stride)
 {
+    constexpr int U = 4; // rows in flight per thread
     const long long m = d_n ? min(*d_n, n) : n;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (long long)gridDim.x * blockDim.x) {
-        const long long row = sel ? sel[j] : j;
-        const long long p = inv[j];
-        for (int sl = 1; sl < as.nslots; sl++)
-            perm[(size_t)(sl - 1) * stride + p] = slot_value(as, sl, row);
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; j0 < m; j0 += step * U) {
+        long long row[U], p[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long j = j0 + u * step;
+            row[u] = j < m ? (sel ? sel[j] : j) : -1;
+            p[u] = j < m ? (long long)inv[j] : 0;
+        }
+        for (int sl = 1; sl < as.nslots; sl++) {
+            long long v[U];
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                v[u] = row[u] >= 0 ? slot_value(as, sl, row[u]) : 0;
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (row[u] >= 0)
+                    perm[(size_t)(sl - 1) * stride + p[u]] = v[u];
+        }
     }
 }
 
 static bool use_perm(int key_bits, bool carry) { return !carry && key_bits <= PERM_MAX_KEY_BITS; }
 
+// Barrier word + one record per block of the reduce (at most one block per
+// SR_TILE rows).
 static size_t seg_ws(long long n)
 {
     long long tiles = (n + SR_TILE - 1) / SR_TILE;
-    return 256 + align_up((size_t)tiles * sizeof(SegRec), 256);
+    return 256 + align_up((size_t)tiles * sizeof(SegValT<SR_MAXS>), 256);
 }
 
 size_t sort_groupby_ws(long long n, int nkeys, int naggs, int key_bits)
@@ -612,26 +869,43 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
                 ras.sop[sl] = TDP_AGG_SUM; // the stored value is already a * (k - b)
         }
     }
-    cudaMemsetAsync(segws, 0, seg_ws(n), s);
-    long long tiles = (n + SR_TILE - 1) / SR_TILE;
-    const unsigned sgrid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 3);
-    auto launch = [&](auto kern) {
-        kern<<<sgrid, SR_THREADS, 0, s>>>(sk, sr, n, rowcount, ks, kp, ras, out, capacity, (long long *)d_ngroups,
-                                          (SegRec *)(segws + 256), (unsigned *)segws, d_status, spin_limit());
+    cudaMemsetAsync(segws, 0, 256, s);
+    // cooperative: at most two blocks per SM (16 warps streaming), at most one
+    // block per SR_TILE rows
+    const long long want = (n + SR_TILE - 1) / SR_TILE;
+    const uint32_t limit = spin_limit();
+    const SegSrc ssrc{pslots, (long long)pstride};
+    auto launch = [&](auto kern, auto *recs) -> tdp_status {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SR_THREADS, 0) != cudaSuccess || per_sm < 1)
+            return TDP_ERR_CUDA;
+        const int G = (int)std::min<long long>(want, (long long)std::min(per_sm, 2) * num_sms());
+        unsigned *barrier = (unsigned *)segws;
+        const K *kk = sk;
+        const V *rr = sr;
+        long long *ng = (long long *)d_ngroups;
+        void *args[] = {(void *)&kk, (void *)&rr, (void *)&ssrc, (void *)&n, (void *)&rowcount, (void *)&ks, (void *)&kp,
+                        (void *)&ras, (void *)&out, (void *)&capacity, (void *)&ng, (void *)&recs,
+                        (void *)&barrier, (void *)&d_status, (void *)&limit};
+        if (cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(SR_THREADS), args, 0, s) != cudaSuccess)
+            return TDP_ERR_CUDA;
+        return launch_status();
     };
     // accumulator slots carried through the scan: the smallest of 2, 4, 5, 9 that fits
     // (the carried state sets the registers, and so the blocks resident per SM)
     if (CARRY)
-        launch(seg_reduce_kernel<K, V, 2, true>);
-    else if (as.nslots <= 2)
-        launch(seg_reduce_kernel<K, V, 2, false>);
-    else if (as.nslots <= 4)
-        launch(seg_reduce_kernel<K, V, 4, false>);
-    else if (as.nslots <= 5)
-        launch(seg_reduce_kernel<K, V, 5, false>);
-    else
-        launch(seg_reduce_kernel<K, V, SR_MAXS, false>);
-    return launch_status();
+        return launch(seg_reduce_kernel<K, V, 2, SEG_CARRY>, (SegValT<2> *)(segws + 256));
+    auto by_slots = [&](auto mode) -> tdp_status {
+        constexpr int M = decltype(mode)::value;
+        if (as.nslots <= 2)
+            return launch(seg_reduce_kernel<K, V, 2, M>, (SegValT<2> *)(segws + 256));
+        if (as.nslots <= 4)
+            return launch(seg_reduce_kernel<K, V, 4, M>, (SegValT<4> *)(segws + 256));
+        if (as.nslots <= 5)
+            return launch(seg_reduce_kernel<K, V, 5, M>, (SegValT<5> *)(segws + 256));
+        return launch(seg_reduce_kernel<K, V, SR_MAXS, M>, (SegValT<SR_MAXS> *)(segws + 256));
+    };
+    return perm ? by_slots(std::integral_constant<int, SEG_PERM>()) : by_slots(std::integral_constant<int, SEG_ROWS>());
 }
 
 tdp_status sort_groupby_run(const PredSet &ps, const KeySet &ks, int key_bits, const AggSet &as, long long n,

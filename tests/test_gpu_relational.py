@@ -366,6 +366,41 @@ def test_groupby_sort_single_value_aggregate(agg):
     assert np.array_equal(np_(out["aggs"][1], g), ra[:, 1])
 
 
+@pytest.mark.parametrize("n", [2_000_003, 6_000_001])
+@pytest.mark.parametrize("case", ["few_groups", "many_groups", "carried_value"])
+def test_groupby_sort_millions_of_rows(n, case):
+    """Sort strategy over millions of rows behind a WHERE (the row count comes
+    from the device).  The reduce spreads the sorted rows over hundreds of
+    blocks: with 15 groups each group spans many warps' runs (slot values
+    written into sorted order); with ~500K groups every run ends hundreds of
+    groups (row ids carried through the sort); with one value aggregate the
+    value itself is carried."""
+    t = _table(n, 31 + n)
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w"]
+    cols = [cu(t[k]) for k in names]
+    if case == "few_groups":
+        cols[4] = ops.Col(cols[4], 0, 2)
+        cols[5] = ops.Col(cols[5], -2, 2)
+        keys, aggs, oaggs = [4, 5], AGGS6, _oracle_aggs(t, names)
+    elif case == "many_groups":
+        cols[2] = ops.Col(cols[2], -1000, 999)
+        keys, aggs, oaggs = [2, 0], AGGS6, _oracle_aggs(t, names)
+    else:
+        keys = [2, 1]
+        aggs = [("sum_mul_kminus", 6, 7, 100), ("count",)]
+        oaggs = [("sum_mul_kminus", t["v"], t["w"], 100), ("count", None, None, None)]
+    out = ops.groupby_agg(cols, keys, aggs, preds=[(3, ">", 0)], strategy="sort")
+    ops.check(out["status"])
+    sel = R.filter([(t["c64"], ">", 0)], n)
+    rk, ra = R.groupby([t[names[k]] for k in keys], oaggs, n, sel=sel)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    for j in range(len(keys)):
+        assert np.array_equal(np_(out["keys"][j], g), rk[:, j])
+    for j in range(len(aggs)):
+        assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), aggs[j]
+
+
 def test_groupby_config1_60k_both_strategies():
     n = 60000
     t = gen.fact_table(n, 15000, gen.BASE_SEED + 0)

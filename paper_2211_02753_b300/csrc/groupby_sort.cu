@@ -19,8 +19,6 @@
 //     run in which groups end, and the lane that holds the last pair of a
 //     group writes the group (key fields unpacked, aggregates finalised).
 //     Groups come out in ascending key order.
-#include <type_traits>
-
 #include "filter_api.cuh"
 #include "groupby.cuh"
 #include "radix.cuh"
@@ -156,8 +154,8 @@ struct SegValT {
     long long s[SL];
 };
 
-// The same with the prefix: each slot's aggregate over the rows before the
-// first head (all rows when there is none).
+// A warp run's record: heads, each slot's aggregate since the last head,
+// and before the first head (both over all rows when there is none).
 template <int SL>
 struct SegPreT {
     unsigned h;
@@ -183,19 +181,6 @@ __device__ __forceinline__ void seg_combine(const int *ops, int NS, const SegVal
 }
 
 template <int SL>
-__device__ __forceinline__ void seg_combine(const int *ops, int NS, const SegPreT<SL> &a, const SegPreT<SL> &b,
-                                            SegPreT<SL> &r)
-{
-    r.h = a.h + b.h;
-#pragma unroll
-    for (int j = 0; j < SL; j++)
-        if (j < NS) {
-            r.s[j] = b.h ? b.s[j] : comb(ops[j], a.s[j], b.s[j]);
-            r.p[j] = a.h ? a.p[j] : comb(ops[j], a.p[j], b.p[j]);
-        }
-}
-
-template <int SL>
 __device__ __forceinline__ void seg_identity(SegValT<SL> &v, const long long *init)
 {
     v.h = 0;
@@ -205,32 +190,12 @@ __device__ __forceinline__ void seg_identity(SegValT<SL> &v, const long long *in
 }
 
 template <int SL>
-__device__ __forceinline__ void seg_identity(SegPreT<SL> &v, const long long *init)
-{
-    v.h = 0;
-#pragma unroll
-    for (int j = 0; j < SL; j++)
-        v.s[j] = v.p[j] = init[j];
-}
-
-template <int SL>
 __device__ __forceinline__ void seg_shfl_down(SegValT<SL> &v, int o)
 {
     v.h = __shfl_down_sync(0xffffffffu, v.h, o);
 #pragma unroll
     for (int j = 0; j < SL; j++)
         v.s[j] = __shfl_down_sync(0xffffffffu, v.s[j], o);
-}
-
-template <int SL>
-__device__ __forceinline__ void seg_shfl_down(SegPreT<SL> &v, int o)
-{
-    v.h = __shfl_down_sync(0xffffffffu, v.h, o);
-#pragma unroll
-    for (int j = 0; j < SL; j++) {
-        v.s[j] = __shfl_down_sync(0xffffffffu, v.s[j], o);
-        v.p[j] = __shfl_down_sync(0xffffffffu, v.p[j], o);
-    }
 }
 
 template <int SL>
@@ -292,17 +257,14 @@ __device__ __forceinline__ void load4_keys(const K *p, K *k)
 }
 
 // Folds the sorted rows i0 .. i0 + SR_ITEMS - 1 that lie in [lo, end) into m
-// (and, with PRE, into the prefix part of m): heads are marked in *headmask,
-// and the first / last head position lowers *first / raises *last.  The
-// rows before i0 (keys[i0 - 1]) decide whether i0 is a head.  i0 is a
-// multiple of SR_ITEMS.
-template <typename K, typename V, int SL, int MODE, typename SV>
+// and marks their heads in *headmask.  keys[i0 - 1] decides whether i0 is a
+// head.  i0 is a multiple of SR_ITEMS.
+template <typename K, typename V, int SL, int MODE>
 __device__ __forceinline__ void seg_lane_fold(const K *__restrict__ keys, const V *__restrict__ rows,
                                               const AggSet &as, const SegSrc &src, long long i0, long long lo,
-                                              long long end, const int *ops, const long long *init, int NS, SV &m,
-                                              unsigned *headmask, long long *first, long long *last)
+                                              long long end, const int *ops, const long long *init, int NS,
+                                              SegValT<SL> &m, unsigned *headmask)
 {
-    constexpr bool PRE = std::is_same<SV, SegPreT<SL>>::value;
     K prev = (i0 > 0 && i0 < end) ? keys[i0 - 1] : (K)0;
     unsigned hm = 0;
 #pragma unroll
@@ -327,17 +289,12 @@ __device__ __forceinline__ void seg_lane_fold(const K *__restrict__ keys, const 
                 prev = kk[it];
                 if (i >= lo) {
                     act |= 1u << it;
-                    if (head) {
+                    if (head)
                         hb |= 1u << it;
-                        *first = *first < 0 ? i : *first;
-                        *last = i;
-                    }
                 }
             }
         }
         hm |= hb << (half * 4);
-        const unsigned h0 = m.h;
-        const unsigned fb = h0 == 0 ? hb & (0u - hb) : 0u; // the lane's first head, if here
         m.h += __popc(hb);
         if (MODE == SEG_PERM) {
             // slot by slot: four values live at a time
@@ -362,13 +319,8 @@ __device__ __forceinline__ void seg_lane_fold(const K *__restrict__ keys, const 
                 for (int it = 0; it < 4; it++) {
                     if (!(act >> it & 1))
                         continue;
-                    if (hb >> it & 1) {
-                        if constexpr (PRE) {
-                            if (fb >> it & 1)
-                                m.p[j] = sj;
-                        }
+                    if (hb >> it & 1)
                         sj = init[j];
-                    }
                     sj = comb(ops[j], sj, v[it]);
                 }
                 m.s[j] = sj;
@@ -380,13 +332,6 @@ __device__ __forceinline__ void seg_lane_fold(const K *__restrict__ keys, const 
                     continue;
                 const long long i = b + it;
                 if (hb >> it & 1) {
-                    if constexpr (PRE) {
-                        if (fb >> it & 1) {
-#pragma unroll
-                            for (int j = 0; j < SL; j++)
-                                m.p[j] = m.s[j];
-                        }
-                    }
 #pragma unroll
                     for (int j = 0; j < SL; j++)
                         m.s[j] = init[j];
@@ -404,14 +349,56 @@ __device__ __forceinline__ void seg_lane_fold(const K *__restrict__ keys, const 
             }
         }
     }
-    if constexpr (PRE) {
-        if (m.h == 0) {
+    *headmask = hm;
+}
+
+// Plain fold of the slot values of sorted rows [a, b) into this lane's acc
+// (SUM, MIN and MAX commute, so every lane folds its own rows and the warp
+// combines the lanes afterwards).  Lanes take 8 consecutive rows of each
+// 256-row tile of the run that starts at ws.
+template <typename K, typename V, int SL, int MODE>
+__device__ __forceinline__ void seg_range_fold(const V *__restrict__ rows, const AggSet &as, const SegSrc &src,
+                                               long long ws, long long a, long long b, const int *ops, int NS,
+                                               long long *acc)
+{
+    const int lane = threadIdx.x & 31;
+    if (a >= b)
+        return;
+    for (long long t = ws + (a - ws) / SR_WTILE * SR_WTILE; t < b; t += SR_WTILE) {
+        const long long i0 = t + lane * SR_ITEMS;
+        const long long lo = max(i0, a), hi = min(i0 + SR_ITEMS, b);
+        if (lo >= hi)
+            continue;
+        acc[0] += hi - lo; // COUNT
+        const bool full = lo == i0 && hi == i0 + SR_ITEMS;
+        if (MODE == SEG_PERM || MODE == SEG_CARRY) {
 #pragma unroll
-            for (int j = 0; j < SL; j++)
-                m.p[j] = m.s[j];
+            for (int j = 1; j < SL; j++) {
+                if (j >= NS || (MODE == SEG_CARRY && j > 1))
+                    continue;
+                const long long *col = MODE == SEG_PERM ? src.perm + (j - 1) * src.pstride : (const long long *)rows;
+                if (full) {
+#pragma unroll
+                    for (int q = 0; q < SR_ITEMS / 2; q++) {
+                        const longlong2 x = __ldg((const longlong2 *)(col + i0) + q);
+                        acc[j] = comb(ops[j], acc[j], x.x);
+                        acc[j] = comb(ops[j], acc[j], x.y);
+                    }
+                } else {
+                    for (long long i = lo; i < hi; i++)
+                        acc[j] = comb(ops[j], acc[j], col[i]);
+                }
+            }
+        } else {
+            for (long long i = lo; i < hi; i++) {
+                const long long row = (long long)rows[i];
+#pragma unroll
+                for (int j = 1; j < SL; j++)
+                    if (j < NS)
+                        acc[j] = comb(ops[j], acc[j], slot_value(as, j, row));
+            }
         }
     }
-    *headmask = hm;
 }
 
 // Writes group g: its key fields unpacked from the sorted key, and every
@@ -455,21 +442,24 @@ __device__ __forceinline__ void emit_group(long long g, K key, const long long *
 
 // Reduce-by-key of the sorted rows: one cooperative launch, every warp owning
 // a contiguous run of whole 256-row tiles (the runs of a block are adjacent).
-//   1. Each warp folds its run into (heads, aggregates since the last head,
-//      aggregates before the first head) and notes its first and last head;
-//      a block's (heads, aggregates since the last head) is the ordered fold
-//      of its warps' and goes to global memory.
+//   1. Each warp reads its run's keys and counts its heads (first and last
+//      noted), then folds the slot values of the rows before the first head
+//      and of the rows from the last head on (all rows when there is no
+//      head) -- plain folds, the operators commute.  A block's (heads,
+//      aggregates since the last head) is the ordered fold of its warps' and
+//      goes to global memory.
 //   2. One bounded grid barrier.
 //   3. Each warp's carry is the ordered fold of everything before its run.
 //      Lane 0 writes the group that ends inside the run before its first
 //      head (carry + prefix), and, in the run that holds the final row, the
 //      group from the last head to the end.  Groups that both start and end
-//      inside the run exist only between its first and last head: just that
-//      span is read again and scanned, and the lane holding a group's last
-//      row writes it.
-// With few groups hardly a run holds two heads, so the rows are read once;
-// with many every run is read twice, still at streaming rate: no warp waits
-// on another except at the barrier.
+//      inside the run lie between its first and last head: that span is
+//      read again and scanned, and the lane holding a group's last row
+//      writes it.
+// Keys are read twice and every slot value once, except the values between
+// a run's first and last head, which are read in step 3 only: with few
+// groups the rows are streamed once; with many, 4 bytes a row more.  No warp
+// waits on another except at the barrier.
 template <typename K, typename V, int SL, int MODE>
 __global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1)
     seg_reduce_kernel(const K *__restrict__ keys, const V *__restrict__ rows, SegSrc src, long long n_max,
@@ -514,54 +504,69 @@ __global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1)
     const long long gw = (long long)blockIdx.x * WARPS + warp;
     const long long ws = min(n, gw * per * SR_WTILE), we = min(n, ws + per * SR_WTILE);
 
-    // 1. fold of the run; lane 0 keeps the run's record in s_wrec[warp]
-    if (lane == 0)
-        seg_identity(s_wrec[warp], init);
+    // 1a. the heads of the run (keys only): count, first, last
+    unsigned h = 0;
     long long first = -1, last = -1;
     for (long long t = ws; t < we; t += SR_WTILE) {
-        SP m;
-        seg_identity(m, init);
-        unsigned hm;
-        seg_lane_fold<K, V, SL, MODE>(keys, rows, s_as, src, t + lane * SR_ITEMS, ws, we, ops, init, NS, m, &hm,
-                                      &first, &last);
-        if (__any_sync(0xffffffffu, hm != 0)) {
-            seg_warp_fold(ops, NS, m);
-            if (lane == 0) {
-                SP r;
-                seg_combine(ops, NS, s_wrec[warp], m, r);
-                s_wrec[warp] = r;
+        const long long i0 = t + lane * SR_ITEMS;
+        K prev = (i0 > 0 && i0 < we) ? keys[i0 - 1] : (K)0;
+#pragma unroll
+        for (int half = 0; half < SR_ITEMS / 4; half++) {
+            const long long b = i0 + half * 4;
+            K kk[4];
+            if (b + 4 <= we) {
+                load4_keys(keys + b, kk);
+            } else {
+#pragma unroll
+                for (int it = 0; it < 4; it++)
+                    kk[it] = b + it < we ? keys[b + it] : (K)0;
             }
-        } else {
-            // no head in the tile: a plain ordered fold, added to the
-            // aggregates since the last head and, before the first, to the prefix
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-                for (int j = 0; j < SL; j++) {
-                    const long long u = __shfl_down_sync(0xffffffffu, m.s[j], o);
-                    if (j < NS && lane + o < 32)
-                        m.s[j] = comb(ops[j], m.s[j], u);
+            for (int it = 0; it < 4; it++) {
+                const long long i = b + it;
+                if (i < we && (i == 0 || kk[it] != prev)) {
+                    h++;
+                    first = first < 0 ? i : first;
+                    last = i;
                 }
-            }
-            if (lane == 0) {
-                SP &w = s_wrec[warp];
-#pragma unroll
-                for (int j = 0; j < SL; j++)
-                    if (j < NS) {
-                        w.s[j] = comb(ops[j], w.s[j], m.s[j]);
-                        if (w.h == 0)
-                            w.p[j] = comb(ops[j], w.p[j], m.s[j]);
-                    }
+                prev = kk[it];
             }
         }
     }
+    h = __reduce_add_sync(0xffffffffu, h);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const long long f = __shfl_xor_sync(0xffffffffu, first, o);
         first = first < 0 ? f : (f < 0 ? first : min(first, f));
         last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
     }
+    // 1b. the aggregates before the first head (all rows when there is none)
+    // and after the last head: plain folds (SUM, MIN, MAX commute)
+    long long pre[SL], suf[SL];
+#pragma unroll
+    for (int j = 0; j < SL; j++)
+        pre[j] = suf[j] = init[j];
+    seg_range_fold<K, V, SL, MODE>(rows, s_as, src, ws, ws, h ? first : we, ops, NS, pre);
+    if (h)
+        seg_range_fold<K, V, SL, MODE>(rows, s_as, src, ws, last, we, ops, NS, suf);
+#pragma unroll
+    for (int j = 0; j < SL; j++) {
+        if (j >= NS)
+            continue;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pre[j] = comb(ops[j], pre[j], __shfl_xor_sync(0xffffffffu, pre[j], o));
+            suf[j] = comb(ops[j], suf[j], __shfl_xor_sync(0xffffffffu, suf[j], o));
+        }
+    }
     if (lane == 0) {
+        SP &w = s_wrec[warp];
+        w.h = h;
+#pragma unroll
+        for (int j = 0; j < SL; j++) {
+            w.p[j] = pre[j];
+            w.s[j] = h ? suf[j] : pre[j];
+        }
         s_wfirst[warp] = first;
         s_wlast[warp] = last;
     }
@@ -657,9 +662,7 @@ __global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1)
         SV mine;
         seg_identity(mine, init);
         unsigned headmask;
-        long long dummy_f = -1, dummy_l = -1;
-        seg_lane_fold<K, V, SL, MODE>(keys, rows, s_as, src, i0, f, l, ops, init, NS, mine, &headmask, &dummy_f,
-                                      &dummy_l);
+        seg_lane_fold<K, V, SL, MODE>(keys, rows, s_as, src, i0, f, l, ops, init, NS, mine, &headmask);
         SV inc = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {

@@ -1,8 +1,9 @@
 // K3: onesweep LSD radix sort of (key, uint32 value) pairs, 8-bit digits.
 //
 //  1. One histogram pass reads every key once and counts all digit positions
-//     (per-block shared-memory histograms, warp-aggregated over the lanes
-//     that share a digit so skewed digits do not serialise on one counter).
+//     (per-block shared-memory histograms; each lane adds runs of equal
+//     digits among its own consecutive keys, so skewed or presorted digits
+//     do not serialise on one counter).
 //  2. A 256-thread kernel turns each digit position's histogram into
 //     exclusive global offsets.
 //  3. One scatter pass per digit.  A tile of 4096 pairs is ranked in shared
@@ -36,28 +37,52 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d)
     return m;
 }
 
-template <typename K>
+// Each lane reads 32 contiguous bytes of keys a step (two 16-byte loads when
+// the keys are 16-byte aligned), so that enough bytes are in flight, and
+// counts runs of equal digits among its own keys before one shared-memory
+// atomic per run: skewed or presorted digits cost few atomics, random ones
+// one per key, with no cross-lane ranking.
+template <typename K, bool VEC>
 __global__ void __launch_bounds__(RS_THREADS) radix_hist_kernel(const K *__restrict__ keys, long long n_max,
                                                                 const long long *d_n, int passes,
                                                                 unsigned *__restrict__ hist)
 {
+    constexpr int KPL = 32 / sizeof(K); // keys per lane per step
     __shared__ unsigned sh[8 * 256];
     for (int i = threadIdx.x; i < passes * 256; i += RS_THREADS)
         sh[i] = 0;
     __syncthreads();
     const long long n = d_n ? min(*d_n, n_max) : n_max;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt = lanemask_lt();
-    for (long long base = ((long long)blockIdx.x * RS_WARPS + warp) * 32; base < n;
-         base += (long long)gridDim.x * RS_THREADS) {
-        long long i = base + lane;
-        bool valid = i < n;
-        K k = valid ? keys[i] : (K)0;
+    const long long step = (long long)gridDim.x * RS_THREADS * KPL;
+    for (long long i0 = ((long long)blockIdx.x * RS_THREADS + threadIdx.x) * KPL; i0 < n; i0 += step) {
+        K k[KPL];
+        const int cnt = (int)min((long long)KPL, n - i0);
+        if (VEC && cnt == KPL) {
+            const uint4 a = __ldg((const uint4 *)(keys + i0)), b = __ldg((const uint4 *)(keys + i0) + 1);
+            const unsigned w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int u = 0; u < KPL; u++)
+                k[u] = sizeof(K) == 4 ? (K)w[u] : (K)(((unsigned long long)w[2 * u + 1] << 32) | w[2 * u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < KPL; u++)
+                k[u] = u < cnt ? keys[i0 + u] : (K)0;
+        }
         for (int p = 0; p < passes; p++) {
-            unsigned d = valid ? (unsigned)((k >> (8 * p)) & 0xff) : 0x100u;
-            unsigned peers = digit_peers(d);
-            if (valid && (peers & lt) == 0)
-                atomicAdd(&sh[p * 256 + d], __popc(peers));
+            unsigned run = (unsigned)((k[0] >> (8 * p)) & 0xff), c = 1;
+#pragma unroll
+            for (int u = 1; u < KPL; u++) {
+                if (u >= cnt)
+                    break;
+                const unsigned d = (unsigned)((k[u] >> (8 * p)) & 0xff);
+                if (d != run) {
+                    atomicAdd(&sh[p * 256 + run], c);
+                    run = d;
+                    c = 0;
+                }
+                c++;
+            }
+            atomicAdd(&sh[p * 256 + run], c);
         }
     }
     __syncthreads();
@@ -260,8 +285,13 @@ tdp_status radix_sort_pairs(const K *keys_in, const V *vals_in, long long n_max,
     p += align_up((size_t)n_max * sizeof(K), 256);
     V *tmp_v = (V *)p;
     cudaMemsetAsync(ws, 0, (size_t)((char *)tmp_k - (char *)ws), s);
-    int hist_blocks = (int)std::min<long long>((n_max + RS_THREADS - 1) / RS_THREADS, (long long)num_sms() * 4);
-    radix_hist_kernel<K><<<hist_blocks, RS_THREADS, 0, s>>>(keys_in, n_max, d_n, P, hist);
+    constexpr int KPL = 32 / sizeof(K);
+    const int hist_blocks =
+        (int)std::min<long long>((n_max + RS_THREADS * KPL - 1) / (RS_THREADS * KPL), (long long)num_sms() * 4);
+    if ((uintptr_t)keys_in % 16 == 0)
+        radix_hist_kernel<K, true><<<hist_blocks, RS_THREADS, 0, s>>>(keys_in, n_max, d_n, P, hist);
+    else
+        radix_hist_kernel<K, false><<<hist_blocks, RS_THREADS, 0, s>>>(keys_in, n_max, d_n, P, hist);
     radix_hist_scan_kernel<<<P, 256, 0, s>>>(hist);
     const size_t smem = (size_t)RS_TILE * (sizeof(K) + sizeof(V)) + RS_WARPS * 257 * 4;
     if (cudaFuncSetAttribute(radix_scatter_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

@@ -460,6 +460,25 @@ def test_sort_pairs_matches_oracle(n, bits):
     assert np.array_equal(np_(vo).view(np.uint32), ev)
 
 
+def test_sort_pairs_unaligned_keys_and_skewed_digits():
+    """Keys that start 8 bytes past a 16-byte boundary (the histogram reads
+    them one by one) and digits that are mostly equal (runs of one digit
+    within each lane's keys)."""
+    n = 300001
+    r = np.random.default_rng(17)
+    keys = np.zeros(n + 1, np.uint64)
+    keys[1:] = r.integers(0, 1 << 20, n, dtype=np.uint64)
+    keys[1 : n // 2 + 1] &= 0xF00FF  # skewed: the middle digit is 0 for half the keys
+    vals = r.integers(0, 2**31, n, dtype=np.uint32)
+    k_all = cu(keys.view(np.int64))
+    assert k_all[1:].data_ptr() % 16 != 0
+    ko, vo, st = ops.sort_pairs(k_all[1:], cu(vals.view(np.int32)), key_bits=20)
+    ops.check(st)
+    ek, ev = R.sort_pairs(keys[1:], vals)
+    assert np.array_equal(np_(ko).view(np.uint64), ek)
+    assert np.array_equal(np_(vo).view(np.uint32), ev)
+
+
 @pytest.mark.parametrize("nb,np_rows", [(1, 1), (1000, 5000), (300000, 1000003)])
 def test_join_matches_oracle(nb, np_rows):
     r = np.random.default_rng(nb)

@@ -504,32 +504,39 @@ __global__ void __launch_bounds__(SR_THREADS, SL <= 5 ? 2 : 1)
     const long long gw = (long long)blockIdx.x * WARPS + warp;
     const long long ws = min(n, gw * per * SR_WTILE), we = min(n, ws + per * SR_WTILE);
 
-    // 1a. the heads of the run (keys only): count, first, last
+    // 1a. the heads of the run (keys only): count, first, last; four tiles'
+    // keys in flight per lane
     unsigned h = 0;
     long long first = -1, last = -1;
-    for (long long t = ws; t < we; t += SR_WTILE) {
-        const long long i0 = t + lane * SR_ITEMS;
-        K prev = (i0 > 0 && i0 < we) ? keys[i0 - 1] : (K)0;
+    constexpr int KT = 4;
+    for (long long t0 = ws; t0 < we; t0 += KT * SR_WTILE) {
+        K kk[KT][SR_ITEMS], pv[KT];
 #pragma unroll
-        for (int half = 0; half < SR_ITEMS / 4; half++) {
-            const long long b = i0 + half * 4;
-            K kk[4];
-            if (b + 4 <= we) {
-                load4_keys(keys + b, kk);
+        for (int u = 0; u < KT; u++) {
+            const long long i0 = t0 + u * SR_WTILE + lane * SR_ITEMS;
+            pv[u] = (i0 > 0 && i0 < we) ? keys[i0 - 1] : (K)0;
+            if (i0 + SR_ITEMS <= we) {
+                load4_keys(keys + i0, kk[u]);
+                load4_keys(keys + i0 + 4, kk[u] + 4);
             } else {
 #pragma unroll
-                for (int it = 0; it < 4; it++)
-                    kk[it] = b + it < we ? keys[b + it] : (K)0;
+                for (int it = 0; it < SR_ITEMS; it++)
+                    kk[u][it] = i0 + it < we ? keys[i0 + it] : (K)0;
             }
+        }
 #pragma unroll
-            for (int it = 0; it < 4; it++) {
-                const long long i = b + it;
-                if (i < we && (i == 0 || kk[it] != prev)) {
+        for (int u = 0; u < KT; u++) {
+            const long long i0 = t0 + u * SR_WTILE + lane * SR_ITEMS;
+            K prev = pv[u];
+#pragma unroll
+            for (int it = 0; it < SR_ITEMS; it++) {
+                const long long i = i0 + it;
+                if (i < we && (i == 0 || kk[u][it] != prev)) {
                     h++;
                     first = first < 0 ? i : first;
                     last = i;
                 }
-                prev = kk[it];
+                prev = kk[u][it];
             }
         }
     }

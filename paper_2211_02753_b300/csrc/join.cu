@@ -38,10 +38,11 @@
 // [lo, hi]).  Persistent blocks take tiles of probe rows in grid-stride
 // order, the staged columns of the next tile arriving by bulk copy while the
 // current one is processed; matched rows are added into a per-block
-// shared-memory cache of
-// 2048 groups (open addressing on the group id), which absorbs Zipf-hot
-// groups; groups that find no cache slot go straight to the global dense
-// accumulator table with 64-bit atomics.  Cache contents are merged into the
+// shared-memory cache of 2048 groups (open addressing on the group id, two
+// probes), which absorbs Zipf-hot groups; groups that find no cache slot go
+// straight to the global dense accumulator table with 64-bit atomics (a
+// short probe sequence: once the cache is full, the cold half of a Zipf
+// stream misses, and a miss should cost two shared reads, not eight).  Cache contents are merged into the
 // global table at the end, then the non-empty groups are compacted in order.
 #include <algorithm>
 
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(JP_THREADS, 3) join_probe_kernel(
 // ------------------------------------------------------- probe + aggregate
 
 constexpr int GJ_CACHE = 2048;
-constexpr int GJ_PROBES = 8;
+constexpr int GJ_PROBES = 2;
 constexpr int GJ_MAX_STAGE = 16; // distinct columns staged per tile
 
 // The columns a group-join tile stages in shared memory (key, predicate and

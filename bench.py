@@ -1109,6 +1109,10 @@ def run_only(args):
     elif args.only == "soft":
         s = gen.soft_table(10_000_000 // sc, 1024, gen.BASE_SEED + 3)
         fn = plans.SoftQuery({k: torch.from_numpy(v).to(dev) for k, v in s.items()}).run
+    elif args.only == "dict":
+        off, data, _, _ = gen.string_column(10_000_000 // sc, 100_000 // sc, gen.BASE_SEED + 7, max_len=24)
+        doff, ddat = torch.from_numpy(off).to(dev), torch.from_numpy(data).to(dev)
+        fn = lambda: ops.dict_encode(doff, ddat, max_len=24)  # noqa: E731
     elif args.only == "softsort":
         from paper_2211_02753_b300 import softsort as ss
         d = gen.ranked_groups(1000 // sc, 1000, gen.BASE_SEED + 11)
@@ -1157,7 +1161,7 @@ def main():
     ap.add_argument("--plans", default="all", choices=["all", "main"])
     ap.add_argument("--only", default=None,
                     choices=["shipping", "shipping_sep", "shipping_sort", "pricing", "pricing_sort", "filter", "chain",
-                             "chain_sort", "soft",
+                             "chain_sort", "soft", "dict",
                              "glyph", "llp", "softsort"],
                     help="profiling mode: run one plan at 1/--scale size and print its time only")
     ap.add_argument("--scale", type=int, default=1)

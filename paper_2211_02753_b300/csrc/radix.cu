@@ -6,14 +6,15 @@
 //     do not serialise on one counter).
 //  2. A 256-thread kernel turns each digit position's histogram into
 //     exclusive global offsets.
-//  3. One scatter pass per digit.  A tile of 4096 pairs is ranked in shared
-//     memory (each warp ranks its 512 pairs stably: the lanes that share a
-//     digit come from nine ballots, a lane's rank is their popc below it),
-//     publishes its per-digit counts, and every one of the 256 threads finds
-//     its digit's offset by decoupled look-back over earlier tiles (tile ids
-//     from an atomic ticket; waits bounded).  Pairs are staged in shared
-//     memory in digit order so that the global writes of a digit run are
-//     contiguous.
+//  3. One scatter pass per digit.  A tile of 4096 pairs is copied into
+//     shared memory and ranked there (each warp ranks its 512 pairs stably:
+//     the lanes that share a digit come from nine ballots, a lane's rank is
+//     their popc below it), publishes its per-digit counts, and every one of
+//     the 256 threads finds its digit's offset by decoupled look-back over
+//     earlier tiles (tile ids from an atomic ticket; waits bounded).  The
+//     ranks become the tile's permutation into digit order, through which
+//     the pairs are written out, so that the global writes of a digit run
+//     are contiguous.
 #include "radix.cuh"
 
 namespace tdp {
@@ -143,112 +144,140 @@ __device__ __forceinline__ unsigned rs_wait(const unsigned *w, uint32_t limit, i
     return s;
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only), and its wait.
+__device__ __forceinline__ void rs_cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void rs_cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// One onesweep digit pass.  The tile's pairs are copied into shared memory
+// in input order (16-byte cp.async for a full tile of 16-byte aligned
+// arrays), ranked there, and the ranks become a permutation: s_src[j] = the
+// input index of the tile's j-th pair in digit order.  The write-out reads
+// the pairs back through it, so a thread keeps only its 16 (digit, rank)
+// words in registers and three blocks fit on an SM.
 template <typename K, typename V>
-__global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__restrict__ kin,
-                                                                   const V *__restrict__ vin,
-                                                                   K *__restrict__ kout, V *__restrict__ vout,
-                                                                   long long n_max, const long long *d_n, int shift,
-                                                                   const unsigned *__restrict__ offsets,
-                                                                   unsigned *status, unsigned *ticket,
-                                                                   int32_t *d_status, uint32_t limit)
+__global__ void __launch_bounds__(RS_THREADS, 3) radix_scatter_kernel(const K *__restrict__ kin,
+                                                                      const V *__restrict__ vin,
+                                                                      K *__restrict__ kout, V *__restrict__ vout,
+                                                                      long long n_max, const long long *d_n,
+                                                                      int shift, const unsigned *__restrict__ offsets,
+                                                                      unsigned *status, unsigned *ticket,
+                                                                      int32_t *d_status, uint32_t limit, int vec)
 {
     extern __shared__ __align__(16) unsigned char rs_smem[];
-    K *s_keys = (K *)rs_smem;
-    V *s_vals = (V *)(s_keys + RS_TILE);
-    unsigned *s_whist = (unsigned *)(s_vals + RS_TILE); // [RS_WARPS][257]
+    K *s_keys = (K *)rs_smem;                           // [RS_TILE], input order
+    V *s_vals = (V *)(s_keys + RS_TILE);                // [RS_TILE], input order
+    uint16_t *s_src = (uint16_t *)(s_vals + RS_TILE);   // [RS_TILE], digit order -> input index
+    unsigned *s_whist = (unsigned *)(s_src + RS_TILE);  // [RS_WARPS][257]
     __shared__ unsigned s_dstart[256];
     __shared__ unsigned s_glob[256];
     __shared__ unsigned s_tmp[8];
     __shared__ long long s_tile;
 
     const long long n = d_n ? min(*d_n, n_max) : n_max;
-    // persistent: tiles are taken in ticket order until the input runs out
-    for (;;) {
-    if (threadIdx.x == 0)
-        s_tile = atomicAdd(ticket, 1u);
-    for (int i = threadIdx.x; i < RS_WARPS * 257; i += RS_THREADS)
-        s_whist[i] = 0;
-    __syncthreads();
-    const long long tile = s_tile;
-    const long long tile_base = tile * RS_TILE;
-    if (tile_base >= n)
-        return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    const long long wb = tile_base + (long long)warp * (RS_ITEMS * 32);
     unsigned *wh = s_whist + warp * 257;
-
-    K k[RS_ITEMS];
-    V v[RS_ITEMS];
-    unsigned short dig[RS_ITEMS], rank[RS_ITEMS];
-#pragma unroll
-    for (int i = 0; i < RS_ITEMS; i++) {
-        long long idx = wb + i * 32 + lane;
-        bool valid = idx < n;
-        k[i] = valid ? kin[idx] : (K)0;
-        v[i] = valid ? vin[idx] : (V)0;
-        dig[i] = valid ? (unsigned short)((k[i] >> shift) & 0xff) : (unsigned short)256;
-    }
-#pragma unroll
-    for (int i = 0; i < RS_ITEMS; i++) {
-        unsigned peers = digit_peers((unsigned)dig[i]);
-        unsigned base = wh[dig[i]];
-        rank[i] = (unsigned short)(base + __popc(peers & lt));
-        __syncwarp();
-        if ((peers & lt) == 0)
-            wh[dig[i]] = base + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    // per digit d = threadIdx.x: exclusive prefix over warps and tile count
-    const int d = threadIdx.x;
-    unsigned cnt = 0;
-#pragma unroll
-    for (int w = 0; w < RS_WARPS; w++) {
-        unsigned c = s_whist[w * 257 + d];
-        s_whist[w * 257 + d] = cnt;
-        cnt += c;
-    }
-    unsigned dstart = block_excl_scan_256(cnt, s_tmp, nullptr);
-    s_dstart[d] = dstart;
-    // decoupled look-back for this digit
-    unsigned excl = 0;
-    unsigned *my = status + tile * 256 + d;
-    if (tile == 0) {
-        st_relaxed_u32(my, RS_INC | cnt);
-    } else {
-        st_relaxed_u32(my, RS_AGG | cnt);
-        long long t = tile - 1;
-        while (t >= 0) {
-            bool to = false;
-            unsigned s = rs_wait(status + t * 256 + d, limit, d_status, &to);
-            excl += s & RS_VAL;
-            if ((s >> 30) == 2 || to)
-                break;
-            t--;
+    // persistent: tiles are taken in ticket order until the input runs out
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_tile = atomicAdd(ticket, 1u);
+        for (int i = threadIdx.x; i < RS_WARPS * 257; i += RS_THREADS)
+            s_whist[i] = 0;
+        __syncthreads();
+        const long long tile = s_tile;
+        const long long tile_base = tile * RS_TILE;
+        if (tile_base >= n)
+            return;
+        const int m = (int)min((long long)RS_TILE, n - tile_base);
+        // 1. the tile into shared memory, input order
+        if (vec && m == RS_TILE) {
+            constexpr int KCH = RS_TILE * (int)sizeof(K) / 16, VCH = RS_TILE * (int)sizeof(V) / 16;
+            const char *gk = (const char *)(kin + tile_base), *gv = (const char *)(vin + tile_base);
+            for (int c = threadIdx.x; c < KCH; c += RS_THREADS)
+                rs_cp_async16((char *)s_keys + 16 * c, gk + 16 * c);
+            for (int c = threadIdx.x; c < VCH; c += RS_THREADS)
+                rs_cp_async16((char *)s_vals + 16 * c, gv + 16 * c);
+            rs_cp_async_wait_all();
+        } else {
+            for (int p = threadIdx.x; p < m; p += RS_THREADS) {
+                s_keys[p] = kin[tile_base + p];
+                s_vals[p] = vin[tile_base + p];
+            }
         }
-        st_relaxed_u32(my, RS_INC | ((excl + cnt) & RS_VAL));
-    }
-    s_glob[d] = offsets[d] + excl;
-    __syncthreads();
+        __syncthreads();
+        // 2. stable rank within the warp's 512 pairs (digit 256: no pair)
+        uint32_t dr[RS_ITEMS]; // digit | rank << 16
 #pragma unroll
-    for (int i = 0; i < RS_ITEMS; i++) {
-        if (dig[i] < 256) {
-            unsigned lp = s_dstart[dig[i]] + s_whist[warp * 257 + dig[i]] + rank[i];
-            s_keys[lp] = k[i];
-            s_vals[lp] = v[i];
+        for (int i = 0; i < RS_ITEMS; i++) {
+            const int p = warp * (RS_ITEMS * 32) + i * 32 + lane;
+            const unsigned d = p < m ? (unsigned)((s_keys[p] >> shift) & 0xff) : 256u;
+            const unsigned peers = digit_peers(d);
+            const unsigned base = wh[d];
+            dr[i] = d | (base + __popc(peers & lt)) << 16;
+            __syncwarp();
+            if ((peers & lt) == 0)
+                wh[d] = base + __popc(peers);
+            __syncwarp();
         }
-    }
-    __syncthreads();
-    const int m = (int)min((long long)RS_TILE, n - tile_base);
-    for (int j = threadIdx.x; j < m; j += RS_THREADS) {
-        K key = s_keys[j];
-        unsigned dd = (unsigned)((key >> shift) & 0xff);
-        long long g = (long long)s_glob[dd] + (j - (long long)s_dstart[dd]);
-        kout[g] = key;
-        vout[g] = s_vals[j];
-    }
-    __syncthreads(); // shared staging is reused by the next tile
+        __syncthreads();
+        // per digit d = threadIdx.x: exclusive prefix over warps and tile count
+        const int d = threadIdx.x;
+        unsigned cnt = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; w++) {
+            const unsigned c = s_whist[w * 257 + d];
+            s_whist[w * 257 + d] = cnt;
+            cnt += c;
+        }
+        const unsigned dstart = block_excl_scan_256(cnt, s_tmp, nullptr);
+        s_dstart[d] = dstart;
+        // decoupled look-back for this digit
+        unsigned excl = 0;
+        unsigned *my = status + tile * 256 + d;
+        if (tile == 0) {
+            st_relaxed_u32(my, RS_INC | cnt);
+        } else {
+            st_relaxed_u32(my, RS_AGG | cnt);
+            long long t = tile - 1;
+            while (t >= 0) {
+                bool to = false;
+                const unsigned s = rs_wait(status + t * 256 + d, limit, d_status, &to);
+                excl += s & RS_VAL;
+                if ((s >> 30) == 2 || to)
+                    break;
+                t--;
+            }
+            st_relaxed_u32(my, RS_INC | ((excl + cnt) & RS_VAL));
+        }
+        s_glob[d] = offsets[d] + excl;
+        __syncthreads();
+        // 3. the tile's permutation into digit order
+#pragma unroll
+        for (int i = 0; i < RS_ITEMS; i++) {
+            const unsigned dd = dr[i] & 0xffffu;
+            if (dd < 256) {
+                const unsigned lp = s_dstart[dd] + s_whist[warp * 257 + dd] + (dr[i] >> 16);
+                s_src[lp] = (uint16_t)(warp * (RS_ITEMS * 32) + i * 32 + lane);
+            }
+        }
+        __syncthreads();
+        // 4. coalesced write-out: a digit's run is contiguous in the output
+        for (int j = threadIdx.x; j < m; j += RS_THREADS) {
+            const int p = s_src[j];
+            const K key = s_keys[p];
+            const unsigned dd = (unsigned)((key >> shift) & 0xff);
+            const long long g = (long long)s_glob[dd] + (j - (long long)s_dstart[dd]);
+            kout[g] = key;
+            vout[g] = s_vals[p];
+        }
+        __syncthreads(); // shared staging is reused by the next tile
     }
 }
 
@@ -293,21 +322,27 @@ tdp_status radix_sort_pairs(const K *keys_in, const V *vals_in, long long n_max,
     else
         radix_hist_kernel<K, false><<<hist_blocks, RS_THREADS, 0, s>>>(keys_in, n_max, d_n, P, hist);
     radix_hist_scan_kernel<<<P, 256, 0, s>>>(hist);
-    const size_t smem = (size_t)RS_TILE * (sizeof(K) + sizeof(V)) + RS_WARPS * 257 * 4;
+    const size_t smem = (size_t)RS_TILE * (sizeof(K) + sizeof(V) + 2) + RS_WARPS * 257 * 4;
     if (cudaFuncSetAttribute(radix_scatter_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return TDP_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, radix_scatter_kernel<K, V>, RS_THREADS, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return TDP_ERR_CUDA;
     const K *src_k = keys_in;
     const V *src_v = vals_in;
-    // persistent grid: as many blocks as fit at once (2 per SM at 128 registers)
-    const unsigned sgrid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 2);
+    // persistent grid: as many blocks as are resident at once
+    const unsigned sgrid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * per_sm);
     for (int pass = 0; pass < P; pass++) {
         bool to_out = ((P - 1 - pass) % 2) == 0;
         K *dk = to_out ? keys_out : tmp_k;
         V *dv = to_out ? vals_out : tmp_v;
+        const int vec = (((uintptr_t)src_k | (uintptr_t)src_v) % 16) == 0;
         radix_scatter_kernel<K, V><<<sgrid, RS_THREADS, smem, s>>>(
             src_k, src_v, dk, dv, n_max, d_n, 8 * pass, hist + pass * 256, status + (size_t)pass * tiles * 256,
-            tickets + pass, d_status, spin_limit());
+            tickets + pass, d_status, spin_limit(), vec);
         src_k = dk;
         src_v = dv;
     }

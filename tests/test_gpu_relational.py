@@ -250,6 +250,73 @@ def test_groupby_small_domain_streamed_device_count_and_unaligned_column():
             assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), (unaligned, aggs[j])
 
 
+# Additive aggregates over small tables (at most 32 accumulators: 32 groups x
+# 1 slot, 15 x 2, 6 x 5) on the small-domain strategy: keys k1 (3 values) x
+# k2 (5), a8 & 31 as a bounded column of 32 groups, u8 % 6 as 6 groups.
+ADD_CASES = [
+    ("a32", [("count", None, None, None)]),                                          # 32 groups x 1 slot
+    ("k12", [("count", None, None, None), ("sum", 6, None, None)]),                   # 15 x 2
+    ("g6", [("sum", 6, None, None), ("sum", 3, None, None), ("sum_mul_kminus", 6, 7, 100),
+            ("count", None, None, None), ("avg", 2, None, None)]),                  # 6 x 5
+]
+
+
+@pytest.mark.parametrize("n", [1, 4099, 1_048_579, 5_000_001])
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_groupby_small_domain_additive_tables(n, case):
+    kind, aggs = ADD_CASES[case]
+    t = _table(n, 1200 + n + case)
+    t["a32"] = (t["a8"].astype(np.int32) & 31).astype(np.int8)
+    t["g6"] = (t["u8"] % 6).astype(np.uint8)
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w", "a32", "g6"]
+    cols = [cu(t[k]) for k in names]
+    cols[4] = ops.Col(cols[4], 0, 2)
+    cols[5] = ops.Col(cols[5], -2, 2)
+    cols[8] = ops.Col(cols[8], 0, 31)
+    cols[9] = ops.Col(cols[9], 0, 5)
+    keys = {"a32": [8], "k12": [4, 5], "g6": [9]}[kind]
+    out = ops.groupby_agg(cols, keys, aggs, preds=[(2, "<", 700)], strategy="small_domain")
+    ops.check(out["status"])
+    sel = R.filter([(t["b32"], "<", 700)], n)
+    oa = [(op, t[names[a]] if a is not None else None, t[names[b]] if b is not None else None, kk)
+          for op, a, b, kk in aggs]
+    rk, ra = R.groupby([t[names[k]] for k in keys], oa, n, sel=sel)
+    g = int(out["ngroups"].item())
+    assert g == len(rk)
+    for j in range(len(keys)):
+        assert np.array_equal(np_(out["keys"][j], g), rk[:, j])
+    for j in range(len(aggs)):
+        assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), aggs[j]
+
+
+def test_groupby_small_domain_additive_tables_device_count_and_unaligned_column():
+    n, m = 3_000_000, 2_000_123
+    aggs = ADD_CASES[2][1]
+    t = _table(n, 78)
+    t["g6"] = (t["u8"] % 6).astype(np.uint8)
+    names = ["a8", "u8", "b32", "c64", "k1", "k2", "v", "w", "g6"]
+    oa = [(op, t[names[a]] if a is not None else None, t[names[b]] if b is not None else None, kk)
+          for op, a, b, kk in aggs]
+    sel = R.filter([(t["b32"][:m], "<", 700)], m)
+    rk, ra = R.groupby([t["g6"][:m]], oa, m, sel=sel)
+    for unaligned in (False, True):
+        cols = [cu(t[k]) for k in names]
+        if unaligned:  # an 8-byte offset on an aggregate column: scalar loads
+            buf = torch.zeros(n + 1, dtype=torch.int64, device=DEV)
+            buf[1:] = cols[6]
+            cols[6] = buf[1:]
+            assert cols[6].data_ptr() % 16 == 8
+        cols[8] = ops.Col(cols[8], 0, 5)
+        nsel = torch.tensor([m], dtype=torch.int64, device=DEV)
+        out = ops.groupby_agg(cols, [8], aggs, preds=[(2, "<", 700)], n=n, nsel=nsel, strategy="small_domain")
+        ops.check(out["status"])
+        g = int(out["ngroups"].item())
+        assert g == len(rk)
+        assert np.array_equal(np_(out["keys"][0], g), rk[:, 0])
+        for j in range(len(aggs)):
+            assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), (unaligned, aggs[j])
+
+
 @pytest.mark.parametrize("n", [1, 4099, 300001])
 def test_groupby_partition_large_domain(n):
     """PARTITION over domains of many buckets: one bounded int32 key over

@@ -75,7 +75,7 @@ def _dict_case(strings):
 
 
 @pytest.mark.parametrize("n,words,max_len", [(1, 1, 8), (1000, 50, 8), (4097, 300, 16), (100_003, 5000, 24),
-                                             (300_000, 20000, 32)])
+                                             (300_000, 20000, 32), (2_000_003, 1_500_000, 24)])
 def test_dict_encode_matches_oracle(n, words, max_len):
     off, data, vocab, idx = gen.string_column(n, words, seed=n, max_len=max_len)
     strings = D.split(off, data)

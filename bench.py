@@ -764,9 +764,11 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
     res["dict_encode_10M"] = {
         "ms": ms, "rows_per_s": 10e6 / (ms / 1e3), "distinct": nd,
         "roofline": roofline("hbm", algo, ms / 1e3, hbm_peak, "GB/s",
-                             "dictionary encoding (4 stable sort passes over the rows)", peak_kind=pk,
-                             extra={"note": "algorithmic = strings + offsets read, codes written; the sort "
-                                            "passes move about 25 x 24 B per row on top"})}
+                             "dictionary encoding (hash dedup of the rows, sort of the distinct strings)",
+                             peak_kind=pk,
+                             extra={"note": "algorithmic = strings + offsets read, codes written; the words "
+                                            "(28 B per row) are written and read back, and the distinct "
+                                            "strings take 25 digit passes on top"})}
     codes = enc["o"]["codes"]
     gcols = [ops.Col(codes, 0, nd - 1), ops.Col(fl, 0, 2), pr]
     ms = _time_graph(lambda: ops.groupby_agg(gcols, [0, 1], [("sum", 2), ("count",)], capacity=3 * nd), stream,

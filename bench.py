@@ -1111,6 +1111,11 @@ def run_only(args):
     elif args.only == "soft":
         s = gen.soft_table(10_000_000 // sc, 1024, gen.BASE_SEED + 3)
         fn = plans.SoftQuery({k: torch.from_numpy(v).to(dev) for k, v in s.items()}).run
+    elif args.only == "nm":
+        d = gen.nm_join_tables(10_000_000 // sc, 20_000_000 // sc, 12.0, gen.BASE_SEED + 6)
+        dd = {k: torch.from_numpy(v).to(dev) for k, v in d.items()}
+        fn = lambda: ops.join_nm([dd["build_key"]], 0, [dd["probe_key"], dd["probe_date"]], 0,  # noqa: E731
+                                 probe_preds=[(1, ">", 1200)], capacity=80_000_000 // sc)
     elif args.only == "dict":
         off, data, _, _ = gen.string_column(10_000_000 // sc, 100_000 // sc, gen.BASE_SEED + 7, max_len=24)
         doff, ddat = torch.from_numpy(off).to(dev), torch.from_numpy(data).to(dev)
@@ -1163,7 +1168,7 @@ def main():
     ap.add_argument("--plans", default="all", choices=["all", "main"])
     ap.add_argument("--only", default=None,
                     choices=["shipping", "shipping_sep", "shipping_sort", "pricing", "pricing_sort", "filter", "chain",
-                             "chain_sort", "soft", "dict",
+                             "chain_sort", "soft", "dict", "nm",
                              "glyph", "llp", "softsort"],
                     help="profiling mode: run one plan at 1/--scale size and print its time only")
     ap.add_argument("--scale", type=int, default=1)

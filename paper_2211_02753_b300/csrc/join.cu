@@ -980,25 +980,6 @@ __global__ void __launch_bounds__(COOP_THREADS) nm_runs_kernel(const uint32_t *s
     }
 }
 
-// Looks up `key` in the table: its payload (the run number), or -1.  Sets
-// *gave_up when the walk passed its bound.
-__device__ __forceinline__ int nm_lookup(const TableView &tv, int32_t key, uint64_t pol, bool *gave_up)
-{
-    if ((uint32_t)key == EMPTY_KEY)
-        return -1;
-    const unsigned b = bucket_of(key, tv.lgb);
-    const Oct k = load_oct(tv.keys + (size_t)b * BUCKET, pol);
-    const int r = scan_bucket(k, (uint32_t)key);
-    if (r >= 0)
-        return tv.pay[(size_t)b * BUCKET + r];
-    if (r == -1)
-        return -1;
-    const long long t = lookup_tail(tv.keys, tv.bmask, tv.steps, (uint32_t)key, b, pol);
-    if (t == -2)
-        *gave_up = true;
-    return t >= 0 ? tv.pay[t] : -1;
-}
-
 __global__ void __launch_bounds__(COOP_THREADS) nm_probe_kernel(
     TableView tv, PredSet ps, const int32_t *__restrict__ key, long long n_host, const long long *d_n, int rounds,
     const int32_t *start, const uint32_t *srow, int32_t *pord, int32_t *out_probe, int32_t *out_build, long long cap,
@@ -1020,46 +1001,113 @@ __global__ void __launch_bounds__(COOP_THREADS) nm_probe_kernel(
         unsigned m = 0;
         for (int q = 0; q < NM_IPT; q += 4)
             m |= eval_preds4(ps, i0 + q, n) << q;
+        // four rows at a time, in stages (their buckets, then their
+        // payloads, then their run lengths), so that the rows' loads overlap
 #pragma unroll
-        for (int e = 0; e < NM_IPT; e++) {
-            if (i0 + e >= n)
-                break;
-            const int u = (m >> e & 1u) ? nm_lookup(tv, key[i0 + e], pol, &gave_up) : -1;
-            pord[i0 + e] = u;
-            if (u >= 0)
-                c += (unsigned long long)(start[u + 1] - start[u]);
+        for (int e0 = 0; e0 < NM_IPT; e0 += 4) {
+            uint32_t kq[4];
+            Oct kb[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const long long i = i0 + e0 + e;
+                kq[e] = (i < n && (m >> (e0 + e) & 1u)) ? (uint32_t)key[i] : EMPTY_KEY;
+                if (kq[e] != EMPTY_KEY)
+                    kb[e] = load_oct(tv.keys + (size_t)bucket_of((int)kq[e], tv.lgb) * BUCKET, pol);
+            }
+            long long slot[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                slot[e] = -1;
+                if (kq[e] == EMPTY_KEY)
+                    continue;
+                const unsigned b = bucket_of((int)kq[e], tv.lgb);
+                const int r = scan_bucket(kb[e], kq[e]);
+                if (r >= 0) {
+                    slot[e] = (long long)b * BUCKET + r;
+                } else if (r == -2) {
+                    slot[e] = lookup_tail(tv.keys, tv.bmask, tv.steps, kq[e], b, pol);
+                    gave_up |= slot[e] == -2;
+                }
+            }
+            int u[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                u[e] = slot[e] >= 0 ? tv.pay[slot[e]] : -1;
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (u[e] >= 0)
+                    c += (unsigned long long)(start[u[e] + 1] - start[u[e]]);
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (i0 + e0 + e < n)
+                    pord[i0 + e0 + e] = u[e];
         }
     }
     if (gave_up)
         set_status(d_status, TDP_ERR_CAPACITY);
     const unsigned long long total = block_sum(c, s_red);
     unsigned long long run = coop_block_prefix(total, s_red, totals, barrier, limit, d_status);
-    // 2. every matching probe row writes its run of build rows at its offset
+    // 2. every matching probe row writes its run of build rows at its offset.
+    // A span's pairs are one contiguous range of the output; the block writes
+    // it together: output k of the span finds its row q (the last whose
+    // offset is <= k) by binary search over the rows' offsets in shared
+    // memory, so consecutive threads write consecutive pairs.
+    __shared__ unsigned long long s_roff[COOP_THREADS * NM_IPT + 1];
+    __shared__ int32_t s_base[COOP_THREADS * NM_IPT]; // the row's run starts at srow[s_base]
+    constexpr int SR = COOP_THREADS * NM_IPT;
     for (int r = 0; r < rounds; r++) {
         const long long i0 = b0 + r * span + (long long)threadIdx.x * NM_IPT;
-        int u[NM_IPT];
-        unsigned long long cr = 0;
+        int u[NM_IPT], s0[NM_IPT];
+        unsigned long long len[NM_IPT], cr = 0;
+#pragma unroll
+        for (int e = 0; e < NM_IPT; e++)
+            u[e] = i0 + e < n ? pord[i0 + e] : -1;
 #pragma unroll
         for (int e = 0; e < NM_IPT; e++) {
-            u[e] = i0 + e < n ? pord[i0 + e] : -1;
-            if (u[e] >= 0)
-                cr += (unsigned long long)(start[u[e] + 1] - start[u[e]]);
+            s0[e] = u[e] >= 0 ? start[u[e]] : 0;
+            len[e] = u[e] >= 0 ? (unsigned long long)(start[u[e] + 1] - s0[e]) : 0ull;
+            cr += len[e];
         }
         unsigned long long tot;
-        long long pos = (long long)(run + block_excl_scan64(cr, s_warp, &tot));
+        unsigned long long off = block_excl_scan64(cr, s_warp, &tot);
 #pragma unroll
         for (int e = 0; e < NM_IPT; e++) {
-            if (u[e] < 0)
-                continue;
-            const int32_t s0 = start[u[e]], s1 = start[u[e] + 1];
-            for (int32_t m = s0; m < s1; m++, pos++)
-                if (pos < cap) {
-                    out_probe[pos] = (int32_t)(i0 + e);
-                    out_build[pos] = (int32_t)srow[m];
+            s_roff[threadIdx.x * NM_IPT + e] = off;
+            s_base[threadIdx.x * NM_IPT + e] = s0[e];
+            off += len[e];
+        }
+        if (threadIdx.x == 0)
+            s_roff[SR] = tot;
+        __syncthreads();
+        const long long rbase = b0 + r * span; // probe row of span row 0
+        static_assert((SR & (SR - 1)) == 0, "span rows: a power of two");
+        // four outputs a thread at a time (their searches and gathers overlap)
+        for (unsigned long long k0 = threadIdx.x; k0 < tot; k0 += 4 * COOP_THREADS) {
+            int lo[4] = {0, 0, 0, 0}; // the last row whose offset is <= k (s_roff[0] = 0)
+#pragma unroll
+            for (int st = SR / 2; st > 0; st >>= 1)
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (s_roff[lo[j] + st] <= k0 + j * COOP_THREADS)
+                        lo[j] += st;
+            uint32_t b[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const unsigned long long k = k0 + j * COOP_THREADS;
+                b[j] = k < tot ? srow[s_base[lo[j]] + (long long)(k - s_roff[lo[j]])] : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const unsigned long long k = k0 + j * COOP_THREADS;
+                const long long pos = (long long)(run + k);
+                if (k < tot && pos < cap) {
+                    out_probe[pos] = (int32_t)(rbase + lo[j]);
+                    out_build[pos] = (int32_t)b[j];
                 }
+            }
         }
         run += tot;
-        __syncthreads(); // s_warp reused by the next span's scan
+        __syncthreads(); // s_warp, s_roff, s_base reused by the next span
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         *d_count = (long long)run;

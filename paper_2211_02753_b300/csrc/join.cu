@@ -919,9 +919,12 @@ static tdp_status launch_probe_agg(const TableView &tv, const PredSet &ps, const
 //   3. the distinct keys into the open-addressing table with their run
 //      number as payload (tdp_join_build, unique keys);
 //   4. probe (cooperative): every qualifying probe row looks its key up once
-//      and keeps the run number; the run lengths give each block, and each
-//      thread, its output offset; then every probe row writes its run's
-//      build rows in order.
+//      (four rows a thread in flight) and keeps the run number; the run
+//      lengths give each block its output offset; then each span of 2048
+//      probe rows writes its pairs as one contiguous range, the block's
+//      threads taking consecutive outputs (an output finds its probe row by
+//      binary search over the rows' offsets in shared memory), so the writes
+//      coalesce whatever the run lengths.
 
 constexpr int NM_IPT = 8; // elements per thread per span of the cooperative passes
 

@@ -45,6 +45,21 @@ def test_join_nm_matches_oracle(nb, npr, dup):
     assert np.array_equal(np_(out["build_row"], c), eb)
 
 
+def test_join_nm_workload_size():
+    """The benchmark's N:M join: 10M build rows (about 12 per key), 20M probe
+    rows behind date > 1200 -- about 63M pairs, every one compared."""
+    d = gen.nm_join_tables(10_000_000, 20_000_000, 12.0, gen.BASE_SEED + 6)
+    psel = R.filter([(d["probe_date"], ">", 1200)], 20_000_000)
+    ep, eb, _ = R.join(d["build_key"], d["probe_key"], psel=psel)
+    out = ops.join_nm([cu(d["build_key"])], 0, [cu(d["probe_key"]), cu(d["probe_date"])], 0,
+                      probe_preds=[(1, ">", 1200)], capacity=len(ep) + 16)
+    ops.check(out["status"])
+    c = int(out["count"].item())
+    assert c == len(ep)
+    assert np.array_equal(np_(out["probe_row"], c), ep)
+    assert np.array_equal(np_(out["build_row"], c), eb)
+
+
 def test_join_nm_counts_capacity_and_int32_min():
     imin = np.iinfo(np.int32).min
     bkey = np.array([5, 7, 5, imin, 9, 5, 7], np.int32)

@@ -104,6 +104,24 @@ def test_dict_encode_matches_oracle(n, words, max_len):
     assert got == ed
 
 
+def test_dict_encode_workload_size():
+    """The benchmark's column: 10M rows drawn from 100K words of up to 24
+    bytes.  Every row is its vocabulary word, so the oracle encodes the words
+    the rows use (the same strings, each once) and a row's expected code is
+    its word's; the dictionary is compared whole."""
+    off, data, vocab, idx = gen.string_column(10_000_000, 100_000, gen.BASE_SEED + 7, max_len=24)
+    out = ops.dict_encode(cu(off), cu(data), max_len=24)
+    ops.check(out["status"])
+    used = np.unique(idx)
+    wc, ed = D.dict_encode([vocab[u] for u in used])
+    code_of_word = np.full(len(vocab), -1, np.int64)
+    code_of_word[used] = wc
+    assert np.array_equal(np_(out["codes"], len(idx)), code_of_word[idx])
+    nd, nbytes = int(out["ndict"].item()), int(out["nbytes"].item())
+    assert nd == len(ed) and nbytes == sum(len(w) for w in ed)
+    assert D.split(np_(out["dict_offsets"], nd + 1), np_(out["dict_bytes"], nbytes)) == ed
+
+
 def test_dict_encode_edge_strings():
     """The empty string, proper prefixes, bytes above 0x7f (unsigned order),
     strings that differ only in their last byte of a word, the longest

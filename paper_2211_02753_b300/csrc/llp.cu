@@ -618,9 +618,10 @@ __global__ void __launch_bounds__(LLP_RED_THREADS) llp_reduce_kernel(const float
 
 // counts[j][k] = #{ labels == k in bag j } + scale * noise[j][k]; one thread
 // per (bag, class)
-__global__ void llp_counts_kernel(const int32_t *__restrict__ labels, long long n, int K, long long B,
-                                  const float *__restrict__ noise, float scale, float *__restrict__ counts,
-                                  int32_t *__restrict__ d_status)
+// Bags smaller than a warp: a thread per (bag, class) counts its bag.
+__global__ void llp_counts_small_kernel(const int32_t *__restrict__ labels, long long n, int K, long long B,
+                                        const float *__restrict__ noise, float scale, float *__restrict__ counts,
+                                        int32_t *__restrict__ d_status)
 {
     const long long nbags = (n + B - 1) / B;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -639,6 +640,48 @@ __global__ void llp_counts_kernel(const int32_t *__restrict__ labels, long long 
     if (bad)
         set_status(d_status, TDP_ERR_OVERFLOW);
     counts[i] = noise ? (float)c + scale * noise[i] : (float)c;
+}
+
+// Bags of at least a warp's rows: a warp per bag (bags in grid-stride order), its
+// lanes reading consecutive labels (coalesced) and counting each class in
+// registers; the warp adds the lanes' counts and lane k writes class k.
+template <int KM>
+__global__ void llp_counts_kernel(const int32_t *__restrict__ labels, long long n, int K, long long B,
+                                  const float *__restrict__ noise, float scale, float *__restrict__ counts,
+                                  int32_t *__restrict__ d_status)
+{
+    const long long nbags = (n + B - 1) / B;
+    const int lane = threadIdx.x & 31;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (long long j = w0; j < nbags; j += nw) {
+        const long long re = min(n, (j + 1) * B);
+        unsigned c[KM];
+#pragma unroll
+        for (int k = 0; k < KM; k++)
+            c[k] = 0;
+        for (long long r = j * B + lane; r < re; r += 32) {
+            const int32_t y = __ldcs(labels + r);
+            bad |= y < 0 || y >= K;
+#pragma unroll
+            for (int k = 0; k < KM; k++)
+                c[k] += y == k;
+        }
+        unsigned mine = 0;
+#pragma unroll
+        for (int k = 0; k < KM; k++) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, c[k]);
+            if (lane == k)
+                mine = v;
+        }
+        if (lane < K) {
+            const long long i = j * K + lane;
+            counts[i] = noise ? (float)mine + scale * noise[i] : (float)mine;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0)
+        set_status(d_status, TDP_ERR_OVERFLOW);
 }
 
 template <int KM, int DM>
@@ -817,9 +860,19 @@ tdp_status tdp_llp_counts(const int32_t *labels, int64_t n, int32_t K, int64_t B
         return TDP_ERR_INVALID_ARG;
     if (n == 0)
         return TDP_OK;
-    const long long work = (n + B - 1) / B * K;
-    llp_counts_kernel<<<(unsigned)((work + 255) / 256), 256, 0, (cudaStream_t)stream>>>(labels, n, K, B, noise,
-                                                                                     scale, counts, d_status);
+    const long long nbags = (n + B - 1) / B;
+    if (B < 32) {
+        const long long work = nbags * K;
+        llp_counts_small_kernel<<<(unsigned)((work + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            labels, n, K, B, noise, scale, counts, d_status);
+        return launch_status();
+    }
+    const unsigned grid = (unsigned)std::max(1ll, std::min<long long>((nbags + 7) / 8, (long long)num_sms() * 16));
+    if (K <= 2)
+        llp_counts_kernel<2><<<grid, 256, 0, (cudaStream_t)stream>>>(labels, n, K, B, noise, scale, counts, d_status);
+    else
+        llp_counts_kernel<16><<<grid, 256, 0, (cudaStream_t)stream>>>(labels, n, K, B, noise, scale, counts,
+                                                                       d_status);
     return launch_status();
 }
 

@@ -47,6 +47,14 @@ def test_counts_label_out_of_range_sets_overflow_and_is_dropped():
     got = llp.counts(dev(y), 3, 2, status=st)
     assert int(st.item()) == 32
     assert got.cpu().numpy().tolist() == [[1.0, 1.0], [1.0, 1.0]]
+    # bags of a warp's rows and more (the warp-per-bag kernel)
+    y = np.zeros(70, np.int32)
+    y[33] = 7
+    y[40:50] = 1
+    st.zero_()
+    got = llp.counts(dev(y), 32, 2, status=st)
+    assert int(st.item()) == 32
+    assert got.cpu().numpy().tolist() == [[32.0, 0.0], [21.0, 10.0], [6.0, 0.0]]
 
 
 CASES = [

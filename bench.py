@@ -1116,10 +1116,17 @@ def run_only(args):
         dd = {k: torch.from_numpy(v).to(dev) for k, v in d.items()}
         fn = lambda: ops.join_nm([dd["build_key"]], 0, [dd["probe_key"], dd["probe_date"]], 0,  # noqa: E731
                                  probe_preds=[(1, ">", 1200)], capacity=80_000_000 // sc)
-    elif args.only == "dict":
+    elif args.only in ("dict", "dict_groupby"):
         off, data, _, _ = gen.string_column(10_000_000 // sc, 100_000 // sc, gen.BASE_SEED + 7, max_len=24)
         doff, ddat = torch.from_numpy(off).to(dev), torch.from_numpy(data).to(dev)
         fn = lambda: ops.dict_encode(doff, ddat, max_len=24)  # noqa: E731
+        if args.only == "dict_groupby":
+            enc = fn()
+            nd = int(enc["ndict"].item())
+            flag = gen.fact_table(10_000_000 // sc, 1, gen.BASE_SEED + 7, cols=("flag", "price"))
+            fl, pr = torch.from_numpy(flag["flag"]).to(dev), torch.from_numpy(flag["price"]).to(dev)
+            gcols = [ops.Col(enc["codes"], 0, nd - 1), ops.Col(fl, 0, 2), pr]
+            fn = lambda: ops.groupby_agg(gcols, [0, 1], [("sum", 2), ("count",)], capacity=3 * nd)  # noqa: E731
     elif args.only == "softsort":
         from paper_2211_02753_b300 import softsort as ss
         d = gen.ranked_groups(1000 // sc, 1000, gen.BASE_SEED + 11)
@@ -1168,7 +1175,7 @@ def main():
     ap.add_argument("--plans", default="all", choices=["all", "main"])
     ap.add_argument("--only", default=None,
                     choices=["shipping", "shipping_sep", "shipping_sort", "pricing", "pricing_sort", "filter", "chain",
-                             "chain_sort", "soft", "dict", "nm",
+                             "chain_sort", "soft", "dict", "dict_groupby", "nm",
                              "glyph", "llp", "softsort"],
                     help="profiling mode: run one plan at 1/--scale size and print its time only")
     ap.add_argument("--scale", type=int, default=1)

@@ -266,14 +266,15 @@ int64_t tdp_join_default_slots(int64_t n_keys);
  * Build an open-addressing hash table for an inner equi-join on int32 keys
  * (the hash join of Sec. 2's relational operators over key tensors).
  * The table is nslots x 8 bytes of device memory owned by the caller
- * (nslots a power of two >= 8, base 32-byte aligned), laid out as two int32
- * arrays of nslots entries: the keys, then the payloads (entry i of one
- * belongs to entry i of the other).  Keys are grouped in buckets of 8 (32
- * bytes); a multiplicative hash picks a bucket and a full bucket without the
- * key passes the search on to the next one (linear probing over buckets).
- * An empty key entry holds INT32_MIN, so that key cannot be stored: a build
- * row with key INT32_MIN sets TDP_ERR_OVERFLOW and is dropped, and a probe
- * row with that key finds nothing.  One 32-bit CAS per insert.
+ * (nslots a power of two >= 8, base 32-byte aligned): nslots slots of one
+ * int32 key (low word) and its int32 payload (high word), in buckets of 4
+ * slots (32 bytes, one sector, so one load of a bucket gives its keys and
+ * their payloads); a multiplicative hash picks a bucket and a full bucket
+ * without the key passes the search on to the next one (linear probing over
+ * buckets).  An empty slot holds (INT32_MIN, 0), so that key cannot be
+ * stored: a build row with key INT32_MIN sets TDP_ERR_OVERFLOW and is
+ * dropped, and a probe row with that key finds nothing.  One 64-bit CAS per
+ * insert (key and payload together).
  *
  *   cols/preds         build-side columns and an optional fused filter
  *   n, d_n             rows 0..n-1, or 0..min(n, *d_n)-1 when d_n != NULL
@@ -285,7 +286,7 @@ int64_t tdp_join_default_slots(int64_t n_keys);
  *   table              device uint64[nslots]; this call fills it with the
  *                      empty pattern first
  *
- * A full table (no free slot within min(nslots / 8, 8192) buckets) sets
+ * A full table (no free slot within min(nslots / 4, 8192) buckets) sets
  * TDP_ERR_CAPACITY; a lookup that walks that far sets it too.  Argument
  * errors (nslots not a power of two >= 8, a misaligned table, a key column
  * that is not int32) are returned as TDP_ERR_INVALID_ARG /

@@ -1,22 +1,22 @@
 // K6/K7: open-addressing hash equi-join (build, probe, fused probe+group-by).
 //
 // Table (the caller's nslots x 8 bytes, nslots a power of two >= 8, base
-// 32-byte aligned): two arrays of nslots int32, the keys and then the
-// payloads, entry i of one belonging to entry i of the other.  Keys are
-// grouped in buckets of 8 (32 bytes: one DRAM/L2 sector, one vector load),
-// and so are their payloads.  A key hashes (multiplicative, Fibonacci) to a
-// bucket; a bucket that is full and does not hold the key passes the search
-// on to the next bucket (linear probing over buckets).  An empty key slot
-// holds INT32_MIN, which therefore cannot be stored (the build flags it as
-// TDP_ERR_OVERFLOW).  Insert: one load of the bucket's keys, a 32-bit CAS on
-// its first empty slot (on a lost race the CAS result tells whether the
-// winner holds the same key: a duplicate), then a plain store of the
-// payload.  Lookup: one 32-byte load of the bucket's keys nearly always
-// decides it; the payload bucket is loaded alongside when the caller wants
-// payloads.  The key array stays compact in L2 for key-only probes.  At the
-// default load factor (<= 1/2) a lookup crosses into a second bucket
-// rarely; the walk is bounded by min(nbuckets, 8192) buckets, beyond which
-// TDP_ERR_CAPACITY is reported.
+// 32-byte aligned): nslots slots of (int32 key, int32 payload), in buckets
+// of 4 slots -- 32 bytes, one DRAM/L2 sector, one vector load that brings a
+// bucket's keys and their payloads together.  A key hashes (multiplicative,
+// Fibonacci) to a bucket; a bucket that is full and does not hold the key
+// passes the search on to the next bucket (linear probing over buckets).  An
+// empty slot holds (INT32_MIN, 0), so INT32_MIN cannot be stored (the build
+// flags it as TDP_ERR_OVERFLOW).  Insert: one load of the bucket, a 64-bit
+// CAS of key and payload into its first empty slot (on a lost race the CAS
+// result tells whether the winner holds the same key: a duplicate).
+// Lookup: one 32-byte load of the bucket nearly always decides it, payload
+// included.  At the default load factor (<= 1/2) a lookup crosses into a
+// second bucket for a few percent of the keys; the walk is bounded by
+// min(nbuckets, 8192) buckets, beyond which TDP_ERR_CAPACITY is reported.
+// (With the keys and the payloads in two arrays, a lookup that wanted the
+// payload made two sector requests; the join chain's probe + aggregate ran
+// 1.5x longer so.)
 //
 // Probe (compaction in probe order): one tile of T = 256 x 4 x STEPS probe
 // rows per block, tiles in block order:
@@ -54,15 +54,16 @@
 namespace tdp {
 
 constexpr uint32_t EMPTY_KEY = 0x80000000u; // INT32_MIN
-constexpr int BUCKET = 8;                   // key slots per bucket (one sector)
+constexpr int BUCKET = 4;                   // (key, payload) slots per bucket: 32 bytes, one sector
 constexpr unsigned long long MAX_BUCKETS = 1ull << 13;
+// an empty slot: key INT32_MIN, payload 0 (as one little-endian 64-bit word)
+constexpr unsigned long long EMPTY_SLOT = (unsigned long long)EMPTY_KEY;
 
 struct TableView {
-    const uint32_t *keys; // bucket b: keys[8b .. 8b+7]
-    const int32_t *pay;   // and its payloads pay[8b .. 8b+7]
-    unsigned bmask;       // nbuckets - 1
-    int lgb;              // log2(nbuckets)
-    unsigned steps;       // bucket walk bound
+    const uint32_t *w; // slot i: key w[2i], payload w[2i + 1]; bucket b: slots 4b .. 4b+3
+    unsigned bmask;    // nbuckets - 1
+    int lgb;           // log2(nbuckets)
+    unsigned steps;    // bucket walk bound
 };
 
 __device__ __forceinline__ unsigned bucket_of(int key, int lgb)
@@ -74,7 +75,8 @@ struct Oct {
     uint32_t v[8];
 };
 
-// 32-byte read-only load with an L2 policy (a bucket of keys or payloads).
+// 32-byte read-only load with an L2 policy: a bucket's four (key, payload)
+// slots.
 __device__ __forceinline__ Oct load_oct(const uint32_t *p, uint64_t pol)
 {
     Oct r;
@@ -85,37 +87,49 @@ __device__ __forceinline__ Oct load_oct(const uint32_t *p, uint64_t pol)
     return r;
 }
 
-// Position of the first slot holding `key` (0..7), -1 if an empty slot
-// comes first (the key is absent), -2 if the bucket is full of other keys
-// (the walk goes on).  Slots fill in order and are never freed, so no empty
-// slot precedes a stored key.
+// The bucket b of the table (its first word).
+__device__ __forceinline__ const uint32_t *bucket_ptr(const TableView &tv, unsigned b)
+{
+    return tv.w + (size_t)b * (2 * BUCKET);
+}
+
+// Position of the first slot holding `key` (0..3) in a loaded bucket, -1 if
+// an empty slot comes first (the key is absent), -2 if the bucket is full of
+// other keys (the walk goes on).  Slots fill in order and are never freed,
+// so no empty slot precedes a stored key.
 __device__ __forceinline__ int scan_bucket(const Oct &k, uint32_t key)
 {
     int res = -2;
 #pragma unroll
     for (int i = BUCKET - 1; i >= 0; i--) {
-        if (k.v[i] == key)
+        if (k.v[2 * i] == key)
             res = i;
-        else if (k.v[i] == EMPTY_KEY)
+        else if (k.v[2 * i] == EMPTY_KEY)
             res = -1;
     }
     return res;
 }
 
-// The payload at position i of a loaded payload bucket (i in 0..7).
+// The payload of slot i (0..3) of a loaded bucket.
 __device__ __forceinline__ int32_t pick(const Oct &p, int i)
 {
     int32_t r = 0;
 #pragma unroll
     for (int j = 0; j < BUCKET; j++)
-        r = j == i ? (int32_t)p.v[j] : r;
+        r = j == i ? (int32_t)p.v[2 * j + 1] : r;
     return r;
+}
+
+// The payload of slot `slot` of the table.
+__device__ __forceinline__ int32_t tv_pay(const TableView &tv, long long slot)
+{
+    return (int32_t)__ldg(tv.w + 2 * slot + 1);
 }
 
 // Continues a lookup whose first bucket b0 was full of other keys: walks the
 // following buckets.  Returns the slot of the key (>= 0), -1 if absent, -2
 // past the walk bound.
-__device__ __noinline__ long long lookup_tail(const uint32_t *keys, unsigned bmask, unsigned steps, uint32_t key,
+__device__ __noinline__ long long lookup_tail(const uint32_t *w, unsigned bmask, unsigned steps, uint32_t key,
                                               unsigned b0, uint64_t pol)
 {
     unsigned b = b0;
@@ -123,7 +137,7 @@ __device__ __noinline__ long long lookup_tail(const uint32_t *keys, unsigned bma
         b = (b + 1) & bmask;
         // two 16-byte loads here: ptxas of CUDA 13.0 fails on a 32-byte load
         // inside a non-inlined function
-        const uint32_t *bk = keys + (size_t)b * BUCKET;
+        const uint32_t *bk = w + (size_t)b * (2 * BUCKET);
         Oct k;
         asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
             : "=r"(k.v[0]), "=r"(k.v[1]), "=r"(k.v[2]), "=r"(k.v[3])
@@ -140,16 +154,17 @@ __device__ __noinline__ long long lookup_tail(const uint32_t *keys, unsigned bma
     return -2;
 }
 
-__global__ void fill_empty_kernel(uint32_t *keys, long long nslots)
+// Every slot empty: (INT32_MIN, 0), two slots per 16-byte store.
+__global__ void fill_empty_kernel(uint32_t *w, long long nslots)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint4 e = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
-    for (; i < nslots / 4; i += (long long)gridDim.x * blockDim.x)
-        ((uint4 *)keys)[i] = e;
+    const uint4 e = make_uint4(EMPTY_KEY, 0u, EMPTY_KEY, 0u);
+    for (; i < nslots / 2; i += (long long)gridDim.x * blockDim.x)
+        ((uint4 *)w)[i] = e;
 }
 
 __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, const int32_t *__restrict__ payload,
-                                  long long n, const long long *d_n, uint32_t *tkeys, int32_t *tpay, int lgb,
+                                  long long n, const long long *d_n, uint32_t *tw, int lgb,
                                   unsigned steps, int32_t *d_status)
 {
     if (d_n)
@@ -194,9 +209,9 @@ __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, c
         unsigned b = bucket_of(k[e], lgb);
         bool done = false;
         for (unsigned s = 0; s < steps && !done; s++, b = (b + 1) & bmask) {
-            uint32_t *bk = tkeys + (size_t)b * BUCKET;
+            uint32_t *bk = tw + (size_t)b * (2 * BUCKET);
             const uint4 lo = __ldcg((const uint4 *)bk), hi = __ldcg((const uint4 *)bk + 1);
-            const uint32_t cur[BUCKET] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            const uint32_t cur[BUCKET] = {lo.x, lo.z, hi.x, hi.z}; // the slots' keys
             // slots are visited in order; a slot passed over holds another key
             // for good (no deletes), so two inserts of one key meet on one slot
 #pragma unroll
@@ -205,9 +220,12 @@ __global__ void join_build_kernel(PredSet ps, const int32_t *__restrict__ key, c
                     break;
                 uint32_t c = cur[i];
                 if (c == EMPTY_KEY) {
-                    c = atomicCAS(bk + i, EMPTY_KEY, kv);
-                    if (c == EMPTY_KEY) {
-                        tpay[(size_t)b * BUCKET + i] = pv;
+                    // key and payload claimed together: one 64-bit CAS of the slot
+                    const unsigned long long got = atomicCAS(
+                        (unsigned long long *)(bk + 2 * i), EMPTY_SLOT,
+                        ((unsigned long long)(uint32_t)pv << 32) | kv);
+                    c = (uint32_t)got;
+                    if (got == EMPTY_SLOT) {
                         done = true;
                         break;
                     }
@@ -363,18 +381,14 @@ __global__ void __launch_bounds__(JP_THREADS, 3) join_probe_kernel(
         uint32_t kq[NB];
         int pv[NB];
         long long slot[NB]; // slot of the found key, -1 if absent
-        Oct wk[NB], wp[PAY ? NB : 1];
+        Oct wk[NB]; // the buckets: keys and payloads
 #pragma unroll
         for (int k = 0; k < NB; k++) {
             const unsigned q = base + tid + k * JP_THREADS;
             li[k] = q < qtot ? queue[q] : -1;
             kq[k] = li[k] >= 0 ? (uint32_t)sk[li[k]] : EMPTY_KEY;
-            if (kq[k] != EMPTY_KEY) {
-                const size_t b8 = (size_t)bucket_of((int)kq[k], tv.lgb) * BUCKET;
-                wk[k] = load_oct(tv.keys + b8, table_pol);
-                if constexpr (PAY)
-                    wp[k] = load_oct((const uint32_t *)tv.pay + b8, table_pol);
-            }
+            if (kq[k] != EMPTY_KEY)
+                wk[k] = load_oct(bucket_ptr(tv, bucket_of((int)kq[k], tv.lgb)), table_pol);
         }
 #pragma unroll
         for (int k = 0; k < NB; k++) {
@@ -387,14 +401,14 @@ __global__ void __launch_bounds__(JP_THREADS, 3) join_probe_kernel(
             if (r >= 0) {
                 slot[k] = (long long)b * BUCKET + r;
                 if constexpr (PAY)
-                    pv[k] = pick(wp[k], r);
+                    pv[k] = pick(wk[k], r);
             } else if (r == -2) {
-                const long long t = lookup_tail(tv.keys, tv.bmask, tv.steps, kq[k], b, table_pol);
+                const long long t = lookup_tail(tv.w, tv.bmask, tv.steps, kq[k], b, table_pol);
                 gave_up |= t == -2;
                 if (t >= 0) {
                     slot[k] = t;
                     if constexpr (PAY)
-                        pv[k] = tv.pay[t];
+                        pv[k] = tv_pay(tv, t);
                 }
             }
         }
@@ -660,9 +674,10 @@ __global__ void __launch_bounds__(JP_THREADS, 3) join_probe_agg_kernel(TableView
         const int32_t *skey = (const int32_t *)(buf + s_off[sg.key]);
 #pragma unroll
         for (int h = 0; h < RPT; h += 4) {
-            // predicates, then one round trip for the first halves of 4 buckets
+            // predicates, then one round trip for 4 buckets (a bucket is one
+            // sector of four (key, payload) slots)
             uint32_t kq[4];
-            uint4 wk[4], wp[4];
+            Oct wk[4];
 #pragma unroll
             for (int r = 0; r < 4; r++) {
                 kq[r] = EMPTY_KEY;
@@ -680,11 +695,8 @@ __global__ void __launch_bounds__(JP_THREADS, 3) join_probe_agg_kernel(TableView
                 }
                 if (q)
                     kq[r] = (uint32_t)skey[li];
-                if (kq[r] != EMPTY_KEY) {
-                    const size_t b8 = (size_t)bucket_of((int)kq[r], tv.lgb) * BUCKET;
-                    wk[r] = ldg16_hint(tv.keys + b8, table_pol);
-                    wp[r] = ldg16_hint((const uint32_t *)tv.pay + b8, table_pol);
-                }
+                if (kq[r] != EMPTY_KEY)
+                    wk[r] = load_oct(bucket_ptr(tv, bucket_of((int)kq[r], tv.lgb)), table_pol);
             }
 #pragma unroll
             for (int r = 0; r < 4; r++) {
@@ -692,38 +704,14 @@ __global__ void __launch_bounds__(JP_THREADS, 3) join_probe_agg_kernel(TableView
                     continue;
                 const int li = tid + (h + r) * JP_THREADS;
                 const unsigned bk = bucket_of((int)kq[r], tv.lgb);
-                const uint32_t k4[4] = {wk[r].x, wk[r].y, wk[r].z, wk[r].w};
-                const uint32_t p4[4] = {wp[r].x, wp[r].y, wp[r].z, wp[r].w};
-                int pos = -2;
-                int32_t pay = 0;
-#pragma unroll
-                for (int i = 3; i >= 0; i--) {
-                    if (k4[i] == kq[r]) {
-                        pos = i;
-                        pay = (int32_t)p4[i];
-                    } else if (k4[i] == EMPTY_KEY) {
-                        pos = -1;
-                    }
-                }
-                if (pos == -2) { // first half full of other keys: the rest of the bucket, then the walk
-                    const size_t b8 = (size_t)bk * BUCKET;
-                    const uint4 k2 = ldg16_hint(tv.keys + b8 + 4, table_pol);
-                    const uint32_t kk[4] = {k2.x, k2.y, k2.z, k2.w};
-#pragma unroll
-                    for (int i = 3; i >= 0; i--) {
-                        if (kk[i] == kq[r])
-                            pos = 4 + i;
-                        else if (kk[i] == EMPTY_KEY)
-                            pos = -1;
-                    }
-                    long long slot = pos >= 0 ? (long long)b8 + pos : -1;
-                    if (pos == -2) {
-                        slot = lookup_tail(tv.keys, tv.bmask, tv.steps, kq[r], bk, table_pol);
-                        gave_up |= slot == -2;
-                    }
+                int pos = scan_bucket(wk[r], kq[r]);
+                int32_t pay = pos >= 0 ? pick(wk[r], pos) : 0;
+                if (pos == -2) { // bucket full of other keys: the walk
+                    const long long slot = lookup_tail(tv.w, tv.bmask, tv.steps, kq[r], bk, table_pol);
+                    gave_up |= slot == -2;
                     if (slot < 0)
                         continue;
-                    pay = tv.pay[slot];
+                    pay = tv_pay(tv, slot);
                 } else if (pos < 0) {
                     continue;
                 }
@@ -785,8 +773,7 @@ static bool table_ok(const void *table, long long nslots)
 static TableView table_view(const uint64_t *table, long long nslots)
 {
     TableView tv;
-    tv.keys = (const uint32_t *)table;
-    tv.pay = (const int32_t *)table + nslots;
+    tv.w = (const uint32_t *)table;
     const long long nb = nslots / BUCKET;
     tv.lgb = log2_of(nb);
     tv.bmask = (unsigned)(nb - 1);
@@ -1015,27 +1002,29 @@ __global__ void __launch_bounds__(COOP_THREADS) nm_probe_kernel(
                 const long long i = i0 + e0 + e;
                 kq[e] = (i < n && (m >> (e0 + e) & 1u)) ? (uint32_t)key[i] : EMPTY_KEY;
                 if (kq[e] != EMPTY_KEY)
-                    kb[e] = load_oct(tv.keys + (size_t)bucket_of((int)kq[e], tv.lgb) * BUCKET, pol);
+                    kb[e] = load_oct(bucket_ptr(tv, bucket_of((int)kq[e], tv.lgb)), pol);
             }
-            long long slot[4];
+            int u[4]; // the run number (the payload), -1: no match
+            long long tail[4]; // a walked lookup's slot (its payload read below)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                slot[e] = -1;
+                u[e] = -1;
+                tail[e] = -1;
                 if (kq[e] == EMPTY_KEY)
                     continue;
                 const unsigned b = bucket_of((int)kq[e], tv.lgb);
                 const int r = scan_bucket(kb[e], kq[e]);
                 if (r >= 0) {
-                    slot[e] = (long long)b * BUCKET + r;
+                    u[e] = pick(kb[e], r);
                 } else if (r == -2) {
-                    slot[e] = lookup_tail(tv.keys, tv.bmask, tv.steps, kq[e], b, pol);
-                    gave_up |= slot[e] == -2;
+                    tail[e] = lookup_tail(tv.w, tv.bmask, tv.steps, kq[e], b, pol);
+                    gave_up |= tail[e] == -2;
                 }
             }
-            int u[4];
 #pragma unroll
             for (int e = 0; e < 4; e++)
-                u[e] = slot[e] >= 0 ? tv.pay[slot[e]] : -1;
+                if (tail[e] >= 0)
+                    u[e] = tv_pay(tv, tail[e]);
 #pragma unroll
             for (int e = 0; e < 4; e++)
                 if (u[e] >= 0)
@@ -1184,15 +1173,15 @@ extern "C" tdp_status tdp_join_build(const tdp_col *cols, int32_t ncols, const t
         return st;
     cudaStream_t s = (cudaStream_t)stream;
     const TableView tv = table_view(table, nslots);
-    fill_empty_kernel<<<(unsigned)std::min<long long>((nslots / 4 + 255) / 256, (long long)num_sms() * 8), 256, 0,
+    fill_empty_kernel<<<(unsigned)std::min<long long>((nslots / 2 + 255) / 256, (long long)num_sms() * 8), 256, 0,
                         s>>>((uint32_t *)table, nslots);
     if (n > 0) {
         // one thread per 4 rows (the kernel is not grid-strided)
         unsigned grid = (unsigned)((n + 1023) / 1024);
         join_build_kernel<<<grid, 256, 0, s>>>(ps, (const int32_t *)cols[key_col].data,
                                                payload_col >= 0 ? (const int32_t *)cols[payload_col].data : nullptr,
-                                               n, (const long long *)d_n, (uint32_t *)table,
-                                               (int32_t *)table + nslots, tv.lgb, tv.steps, d_status);
+                                               n, (const long long *)d_n, (uint32_t *)table, tv.lgb, tv.steps,
+                                               d_status);
     }
     return launch_status();
 }

@@ -329,3 +329,101 @@ def test_checkpoint_resume_reproduces_the_next_step_bitwise():
     for k in cnn.PARAMS:
         assert torch.equal(a.p[k], b.p[k]), k
         assert torch.equal(a.m[k], b.m[k]) and torch.equal(a.v[k], b.v[k]), k
+
+
+def test_conv2_and_fc1_layers_at_the_training_batch():
+    """The tcgen05 layers at the training step's batch (256 grids = 4096
+    cells, the launch configuration of the benchmark's step).  conv2's
+    forward and data gradient are cell-local, so a spread sample of cells
+    (both ends of the batch, CTA-tile boundaries, random cells) is compared
+    with the float64 oracle on those cells.  The weight gradient sums over
+    every cell: a second backward call sees dy2 only on the sampled cells
+    (zero elsewhere, whose terms vanish exactly), so the oracle's weight and
+    bias gradients over the sample are the whole answer, while the kernel
+    still walks every tile of the batch.  fc1 is checked on every row.
+    Tolerances are the layer tests' above."""
+    nc = 4096
+    r = np.random.default_rng(4096)
+    samp = np.unique(np.concatenate([[0, 1, 2, 63, 64, 127, 128, 2047, 2048, 4094, 4095],
+                                     r.choice(nc, 117, replace=False)]))
+    y1 = bf16_np(np.abs(r.standard_normal((nc, 26, 26, 32), np.float32))
+                 * (r.random((nc, 26, 26, 32), np.float32) > 0.3))
+    w2 = bf16_np(r.uniform(-0.08, 0.08, (64, 3, 3, 32)))
+    b2 = r.uniform(-0.05, 0.05, 64).astype(np.float32)
+    g_y1, g_w2, g_b2 = to_bf16_dev(y1), to_bf16_dev(w2), torch.from_numpy(b2).to(DEV)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+
+    y2 = torch.empty((nc, 9216), dtype=torch.bfloat16, device=DEV)
+    am = torch.empty((nc, 9216), dtype=torch.uint8, device=DEV)
+    L.call("tdp_cnn_conv2_pool_fwd", _ptr(g_y1), nc, _ptr(g_w2), _ptr(g_b2), _ptr(y2), _ptr(am), _ptr(st),
+           _stream())
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ys = y1[samp]
+    pooled, arg, a2 = O.conv2_relu_pool(ys, w2, b2.astype(np.float64))
+    ref = bf16_np(pooled).reshape(len(samp), 9216)
+    got = y2[torch.from_numpy(samp).to(DEV)].float().cpu().numpy()
+    assert np.all(np.abs(got - ref) <= ULP * np.abs(ref) + 1e-6)
+    ga = am[torch.from_numpy(samp).to(DEV)].cpu().numpy().reshape(len(samp), 12, 12, 64).astype(np.int64)
+    win = a2.reshape(len(samp), 12, 2, 12, 2, 64).transpose(0, 1, 3, 2, 4, 5).reshape(len(samp), 12, 12, 4, 64)
+    at_gpu = np.take_along_axis(win, ga[:, :, :, None, :], axis=3)[:, :, :, 0, :]
+    assert ga.max() <= 3 and np.all(at_gpu >= pooled - ULP * np.abs(pooled) - 1e-6)
+    assert np.mean(ga == arg) > 0.99
+    del y2, am
+
+    dy2 = bf16_np(r.standard_normal((nc, 12, 12, 64), np.float32)
+                  * (r.random((nc, 12, 12, 64), np.float32) > 0.2))
+    argb = r.integers(0, 4, (nc, 12, 12, 64)).astype(np.uint8)
+    g_arg = torch.from_numpy(argb).to(DEV)
+    dz1 = torch.empty((nc, 26, 26, 32), dtype=torch.bfloat16, device=DEV)
+    dw2 = torch.empty((64, 3, 3, 32), dtype=torch.float32, device=DEV)
+    db2 = torch.empty(64, dtype=torch.float32, device=DEV)
+    ws = torch.empty(L.lib().tdp_cnn_conv2_bwd_workspace(nc), dtype=torch.uint8, device=DEV)
+
+    def bwd(dy):
+        g_dy = to_bf16_dev(dy)
+        L.call("tdp_cnn_conv2_bwd", _ptr(g_dy), _ptr(g_arg), _ptr(g_y1), _ptr(g_w2), nc, _ptr(dz1),
+               _ptr(dw2), _ptr(db2), _ptr(ws), ws.numel(), _ptr(st), _stream())
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+
+    rdz1, rdw2, rdb2 = O.conv2_backward(dy2[samp], argb[samp], ys, w2)
+    bwd(dy2)  # every cell active: the data gradient of the sampled cells
+    got = dz1[torch.from_numpy(samp).to(DEV)].float().cpu().numpy()
+    assert np.all(np.abs(got - bf16_np(rdz1)) <= ULP * np.abs(rdz1) + 1e-3 * np.abs(rdz1).max())
+    only = np.zeros_like(dy2)
+    only[samp] = dy2[samp]
+    bwd(only)  # only the sampled cells active: the weight and bias gradients
+    gw = dw2.cpu().numpy()
+    assert np.linalg.norm(gw - rdw2) <= 1e-5 * np.linalg.norm(rdw2)
+    assert np.allclose(db2.cpu().numpy(), rdb2, rtol=1e-5, atol=1e-5 * np.abs(rdb2).max())
+    rest = np.setdiff1d(np.arange(nc), samp)
+    assert not dz1[torch.from_numpy(rest).to(DEV)].any()  # inactive cells get no data gradient
+    del dz1, g_y1, g_arg, ws
+
+    yf = bf16_np(np.abs(r.standard_normal((nc, 9216), np.float32)) * (r.random((nc, 9216), np.float32) > 0.5))
+    w = bf16_np(r.uniform(-0.02, 0.02, (128, 9216)))
+    b = r.uniform(-0.05, 0.05, 128).astype(np.float32)
+    dh1 = bf16_np(r.standard_normal((nc, 128)) * (r.random((nc, 128)) > 0.3))
+    g_y2, g_w, g_b, g_dh1 = to_bf16_dev(yf), to_bf16_dev(w), torch.from_numpy(b).to(DEV), to_bf16_dev(dh1)
+    h1 = torch.empty((nc, 128), dtype=torch.bfloat16, device=DEV)
+    dy2p = torch.empty((nc, 9216), dtype=torch.bfloat16, device=DEV)
+    dw = torch.empty((128, 9216), dtype=torch.float32, device=DEV)
+    db = torch.empty(128, dtype=torch.float32, device=DEV)
+    lib = L.lib()
+    ws = torch.empty(max(lib.tdp_cnn_fc1_fwd_workspace(nc), lib.tdp_cnn_fc1_bwd_workspace(nc)), dtype=torch.uint8,
+                     device=DEV)
+    L.call("tdp_cnn_fc1_fwd", _ptr(g_y2), nc, _ptr(g_w), _ptr(g_b), _ptr(h1), _ptr(ws), ws.numel(), _ptr(st),
+           _stream())
+    L.call("tdp_cnn_fc1_bwd", _ptr(g_dh1), _ptr(g_y2), _ptr(g_w), nc, _ptr(dy2p), _ptr(dw), _ptr(db), _ptr(ws),
+           ws.numel(), _ptr(st), _stream())
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    rh = O.fc(yf, w, b.astype(np.float64), True)
+    got = h1.float().cpu().numpy()
+    assert np.all(np.abs(got - bf16_np(rh)) <= ULP * np.abs(rh) + 1e-5 * np.abs(rh).max())
+    rdy, rdw, rdb = O.fc1_backward(dh1, yf, w)
+    got = dy2p.float().cpu().numpy()
+    assert np.all(np.abs(got - bf16_np(rdy)) <= ULP * np.abs(rdy) + 1e-5 * np.abs(rdy).max())
+    assert np.linalg.norm(dw.cpu().numpy() - rdw) <= 1e-5 * np.linalg.norm(rdw)
+    assert np.allclose(db.cpu().numpy(), rdb, rtol=1e-5, atol=1e-5 * np.abs(rdb).max())

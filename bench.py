@@ -426,11 +426,17 @@ class ClockSampler:
 
 def _events_median(fns, stream, reps=5):
     """Median CUDA-event time (ms) of each function in `fns`, run in order on
-    `stream` (each is a library call; events recorded between them)."""
+    `stream` (each is a library call; events recorded between them).  A
+    bounded ~1 ms device sleep is queued first, so that the host has issued
+    every call before the GPU reaches the first event: the intervals then
+    hold the calls' device time only, not the host's argument marshalling
+    and launch latency (which the graph-replayed step does not pay)."""
     import torch
     ts = []
     for _ in range(reps):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)]
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(2_000_000)
         e[0].record(stream)
         for i, fn in enumerate(fns):
             fn()

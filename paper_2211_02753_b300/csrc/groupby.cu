@@ -276,6 +276,172 @@ __global__ void __launch_bounds__(SD_THREADS) small_domain_priv_kernel(PredSet p
             acc_update(&gacc[e], s_op[e % NS], spriv[e]);
 }
 
+// eval_preds4 with every comparison in its closed-range form (lo, hi and neg
+// of the PredSet, clamped into the column's type, so a 64-bit unsigned
+// distance decides it for every type).
+__device__ __forceinline__ unsigned preds4_range(const PredSet &ps, long long r, long long n)
+{
+    unsigned m = r + 3 < n ? 0xfu : (r + 2 < n ? 0x7u : (r + 1 < n ? 0x3u : (r < n ? 0x1u : 0u)));
+    for (int p = 0; p < ps.n; p++) {
+        long long v[4];
+        load4_int(ps.col[p], ps.dt[p], ps.vec_ok[p], r, n, v);
+        const long long lo = ps.lo[p];
+        const unsigned long long span = (unsigned long long)ps.hi[p] - (unsigned long long)lo;
+        const unsigned neg = (unsigned)ps.neg[p];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            m &= ~((range_holds64(v[k], lo, span, neg) ^ 1u) << k);
+    }
+    return m;
+}
+
+// The same private-slice scheme with the slot count NSX a compile-time
+// constant and at most one a * (k - b) slot: MS is that slot (0 for none)
+// when every slot combines by addition (ADD), else MS = -1 and the slot is
+// the argument mslot.  After the predicates, the first two key columns and
+// every value column of the thread's four rows are loaded before any of
+// them is used, so a quad costs two round trips to memory instead of one per
+// slot; the slice offsets, and for ADD the per-slot arithmetic, are fixed at
+// compile time.  Three blocks of 256 threads per SM (the shared slices allow
+// three; the register cap keeps them resident).
+template <int NSX, bool ADD, int MS>
+__global__ void __launch_bounds__(SD_THREADS, 3) small_domain_priv_n_kernel(PredSet ps, KeySet ks, AggSet as, long long n,
+                                                                            const long long *d_nsel, int D, int pitch,
+                                                                            int mslot, long long *gacc,
+                                                                            int32_t *d_status)
+{
+    constexpr int KB = TDP_MAX_KEYS < 2 ? TDP_MAX_KEYS : 2; // key columns loaded with the values
+    extern __shared__ long long spriv[];
+    const int tab = D * NSX;
+    long long *my = spriv + (size_t)threadIdx.x * pitch;
+    __shared__ long long s_init[NSX];
+    __shared__ int s_op[NSX];
+    if (threadIdx.x < NSX) {
+        s_init[threadIdx.x] = slot_init(as, threadIdx.x);
+        s_op[threadIdx.x] = slot_op(as, threadIdx.x);
+    }
+    __syncthreads();
+    for (int e = 0; e < tab; e++)
+        my[e] = s_init[e % NSX];
+    if (MS >= 0)
+        mslot = MS;
+    int op[NSX];
+    bool va_vec[NSX], is_mul[NSX];
+#pragma unroll
+    for (int sl = 1; sl < NSX; sl++) {
+        op[sl] = s_op[sl];
+        va_vec[sl] = ((uintptr_t)as.sa[sl] % 16) == 0;
+        is_mul[sl] = MS >= 0 ? sl == MS : sl == mslot;
+    }
+    const void *bcol = mslot ? as.sb[mslot] : nullptr;
+    const int bdt = mslot ? as.sbdt[mslot] : TDP_I64;
+    const bool b_vec = mslot && ((uintptr_t)bcol % 16) == 0;
+    const long long bk = mslot ? as.sk[mslot] : 0;
+    bool bad = false;
+    if (d_nsel)
+        n = min(*d_nsel, n);
+    const long long stride = (long long)gridDim.x * SD_THREADS * 4;
+    // the first predicate's column of the thread's next quad is loaded one
+    // iteration ahead (its values decide which rows the other loads serve)
+    const bool pf = ps.n > 0;
+    const long long p0lo = pf ? ps.lo[0] : 0;
+    const unsigned long long p0span = pf ? (unsigned long long)ps.hi[0] - (unsigned long long)p0lo : 0;
+    const unsigned p0neg = pf ? (unsigned)ps.neg[0] : 0u;
+    long long r = ((long long)blockIdx.x * SD_THREADS + threadIdx.x) * 4;
+    long long pv[4] = {0, 0, 0, 0};
+    if (pf && r < n)
+        load4_int(ps.col[0], ps.dt[0], ps.vec_ok[0], r, n, pv);
+    for (; r < n; r += stride) {
+        unsigned m = r + 3 < n ? 0xfu : (r + 2 < n ? 0x7u : (r + 1 < n ? 0x3u : 0x1u));
+        if (pf) {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                m &= ~((range_holds64(pv[k], p0lo, p0span, p0neg) ^ 1u) << k);
+            if (r + stride < n)
+                load4_int(ps.col[0], ps.dt[0], ps.vec_ok[0], r + stride, n, pv);
+        }
+        for (int p = 1; p < ps.n; p++) {
+            long long v[4];
+            load4_int(ps.col[p], ps.dt[p], ps.vec_ok[p], r, n, v);
+            const long long lo = ps.lo[p];
+            const unsigned long long span = (unsigned long long)ps.hi[p] - (unsigned long long)lo;
+            const unsigned neg = (unsigned)ps.neg[p];
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                m &= ~((range_holds64(v[k], lo, span, neg) ^ 1u) << k);
+        }
+        if (!m)
+            continue;
+        long long kv[KB][4];
+#pragma unroll
+        for (int k = 0; k < KB; k++)
+            if (k < ks.n)
+                load4_int(ks.col[k], ks.dt[k], ks.vec_ok[k], r, n, kv[k]);
+        long long va[NSX][4], vb[4];
+#pragma unroll
+        for (int sl = 1; sl < NSX; sl++)
+            load4_int(as.sa[sl], as.sadt[sl], va_vec[sl], r, n, va[sl]);
+        if (mslot)
+            load4_int(bcol, bdt, b_vec, r, n, vb);
+        int gid[4] = {0, 0, 0, 0}; // < D <= SP_MAX_TAB once the rows' keys are in bounds
+        auto add_key = [&](int k, const long long *v) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const long long d = v[j] - ks.lo[k];
+                if ((m >> j & 1) && (unsigned long long)d >= (unsigned long long)ks.size[k]) {
+                    m &= ~(1u << j);
+                    bad = true;
+                }
+                gid[j] += (int)d * (int)ks.stride[k];
+            }
+        };
+#pragma unroll
+        for (int k = 0; k < KB; k++)
+            if (k < ks.n)
+                add_key(k, kv[k]);
+        for (int k = KB; k < ks.n; k++) {
+            long long v[4];
+            load4_int(ks.col[k], ks.dt[k], ks.vec_ok[k], r, n, v);
+            add_key(k, v);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (!(m >> j & 1))
+                continue;
+            long long *a = my + gid[j] * NSX;
+            a[0] += 1;
+#pragma unroll
+            for (int sl = 1; sl < NSX; sl++) {
+                long long v;
+                if (MS >= 0)
+                    v = sl == MS ? va[sl][j] * (bk - vb[j]) : va[sl][j];
+                else
+                    v = is_mul[sl] ? va[sl][j] * (bk - vb[j]) : va[sl][j];
+                if (ADD)
+                    a[sl] += v;
+                else
+                    a[sl] = op[sl] == TDP_AGG_MIN ? min(a[sl], v) : op[sl] == TDP_AGG_MAX ? max(a[sl], v) : a[sl] + v;
+            }
+        }
+    }
+    if (bad)
+        set_status(d_status, TDP_ERR_OVERFLOW);
+    for (int h = SD_THREADS / 2; h > 0; h >>= 1) {
+        __syncthreads();
+        if ((int)threadIdx.x < h) {
+            const long long *o = spriv + (size_t)(threadIdx.x + h) * pitch;
+            for (int e = 0; e < tab; e++) {
+                const int sop = s_op[e % NSX];
+                my[e] = sop == TDP_AGG_MIN ? min(my[e], o[e]) : sop == TDP_AGG_MAX ? max(my[e], o[e]) : my[e] + o[e];
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tab; e += SD_THREADS)
+        if (spriv[e] != s_init[e % NSX])
+            acc_update(&gacc[e], s_op[e % NSX], spriv[e]);
+}
+
 constexpr int FIN_THREADS = 256;
 constexpr int FIN_TILE = FIN_THREADS * 4;
 
@@ -464,12 +630,66 @@ tdp_status small_domain_run(const PredSet &ps, const KeySet &ks, const AggSet &a
         // private per-thread accumulators
         const int pitch = (int)(D * as.nslots) | 1;
         const size_t psm = (size_t)SD_THREADS * pitch * 8;
-        cudaFuncSetAttribute(small_domain_priv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
         const int per_sm = std::max(1, std::min(8, (int)(200 * 1024 / psm)));
         const long long want = ((n + 3) / 4 + SD_THREADS - 1) / SD_THREADS;
         const unsigned pgrid = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() * per_sm));
-        small_domain_priv_kernel<<<pgrid, SD_THREADS, psm, s>>>(ps, ks, as, n, (const long long *)d_nsel, (int)D,
-                                                                pitch, acc, d_status);
+        // the slot of a * (k - b), when there is exactly one
+        int mslot = 0, nmul = 0;
+        for (int sl = 1; sl < as.nslots; sl++)
+            if (as.sop[sl] == TDP_AGG_SUM_MUL_KMINUS) {
+                mslot = sl;
+                nmul++;
+            }
+        // resident blocks per SM: the shared slices allow per_sm, the
+        // registers of the kernel may allow fewer
+        auto priv_n = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SD_THREADS, psm) != cudaSuccess || occ < 1)
+                occ = 1;
+            const unsigned g = (unsigned)std::max(1ll, std::min<long long>(want, (long long)num_sms() *
+                                                                                   std::min(per_sm, occ)));
+            kern<<<g, SD_THREADS, psm, s>>>(ps, ks, as, n, (const long long *)d_nsel, (int)D, pitch, mslot, acc,
+                                            d_status);
+        };
+        auto add_n = [&](auto nsx) { // ADD kernels: MS compile-time
+            constexpr int N = decltype(nsx)::value;
+            if (mslot == 0 || N < 2)
+                priv_n(small_domain_priv_n_kernel<N, true, 0>);
+            else if constexpr (N >= 2) {
+                if (mslot == 1)
+                    priv_n(small_domain_priv_n_kernel<N, true, 1>);
+                else if constexpr (N >= 3) {
+                    if (mslot == 2)
+                        priv_n(small_domain_priv_n_kernel<N, true, 2>);
+                    else if constexpr (N >= 4) {
+                        if (mslot == 3)
+                            priv_n(small_domain_priv_n_kernel<N, true, 3>);
+                        else if constexpr (N >= 5)
+                            priv_n(small_domain_priv_n_kernel<N, true, 4>);
+                    }
+                }
+            }
+        };
+        bool add = true; // every slot combines by +
+        for (int sl = 1; sl < as.nslots; sl++)
+            add = add && as.sop[sl] != TDP_AGG_MIN && as.sop[sl] != TDP_AGG_MAX;
+        switch (nmul <= 1 ? as.nslots * 2 + (add ? 1 : 0) : 0) {
+        case 2: priv_n(small_domain_priv_n_kernel<1, false, -1>); break;
+        case 3: add_n(std::integral_constant<int, 1>()); break;
+        case 4: priv_n(small_domain_priv_n_kernel<2, false, -1>); break;
+        case 5: add_n(std::integral_constant<int, 2>()); break;
+        case 6: priv_n(small_domain_priv_n_kernel<3, false, -1>); break;
+        case 7: add_n(std::integral_constant<int, 3>()); break;
+        case 8: priv_n(small_domain_priv_n_kernel<4, false, -1>); break;
+        case 9: add_n(std::integral_constant<int, 4>()); break;
+        case 10: priv_n(small_domain_priv_n_kernel<5, false, -1>); break;
+        case 11: add_n(std::integral_constant<int, 5>()); break;
+        default:
+            cudaFuncSetAttribute(small_domain_priv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+            small_domain_priv_kernel<<<pgrid, SD_THREADS, psm, s>>>(ps, ks, as, n, (const long long *)d_nsel, (int)D,
+                                                                    pitch, acc, d_status);
+        }
         tdp_status st = launch_status();
         if (st != TDP_OK)
             return st;

@@ -196,11 +196,14 @@ STREAM_CASES = [
     ([4], [("count", None, None, None), ("sum", 6, None, None), ("sum_mul_kminus", 6, 7, 100),
            ("min", 0, None, None), ("max", 3, None, None), ("avg", 2, None, None)]),
     ([4, 5], [("count", None, None, None), ("sum", 6, None, None), ("avg", 7, None, None)]),
+    # four slots with MIN / MAX beside one a * (k - b) slot (not purely additive)
+    ([4], [("min", 0, None, None), ("sum_mul_kminus", 6, 7, 100), ("max", 3, None, None),
+           ("count", None, None, None)]),
 ]
 
 
 @pytest.mark.parametrize("n", [1_048_576, 1_048_579, 5_000_001])
-@pytest.mark.parametrize("case", [0, 1])
+@pytest.mark.parametrize("case", [0, 1, 2])
 def test_groupby_small_domain_streamed(n, case):
     keys, aggs = STREAM_CASES[case]
     t = _table(n, 900 + n + case)
@@ -250,19 +253,21 @@ def test_groupby_small_domain_streamed_device_count_and_unaligned_column():
             assert np.array_equal(np_(out["aggs"][j], g), ra[:, j]), (unaligned, aggs[j])
 
 
-# Additive aggregates over small tables (at most 32 accumulators: 32 groups x
-# 1 slot, 15 x 2, 6 x 5) on the small-domain strategy: keys k1 (3 values) x
+# Additive aggregates over small tables (at most 45 accumulators: 32 groups x
+# 1 slot, 15 x 2, 6 x 5, 15 x 3 with the product slot first) on the
+# small-domain strategy: keys k1 (3 values) x
 # k2 (5), a8 & 31 as a bounded column of 32 groups, u8 % 6 as 6 groups.
 ADD_CASES = [
     ("a32", [("count", None, None, None)]),                                          # 32 groups x 1 slot
     ("k12", [("count", None, None, None), ("sum", 6, None, None)]),                   # 15 x 2
     ("g6", [("sum", 6, None, None), ("sum", 3, None, None), ("sum_mul_kminus", 6, 7, 100),
             ("count", None, None, None), ("avg", 2, None, None)]),                  # 6 x 5
+    ("k12", [("sum_mul_kminus", 6, 7, 100), ("count", None, None, None), ("sum", 3, None, None)]),  # 15 x 3
 ]
 
 
 @pytest.mark.parametrize("n", [1, 4099, 1_048_579, 5_000_001])
-@pytest.mark.parametrize("case", [0, 1, 2])
+@pytest.mark.parametrize("case", [0, 1, 2, 3])
 def test_groupby_small_domain_additive_tables(n, case):
     kind, aggs = ADD_CASES[case]
     t = _table(n, 1200 + n + case)

@@ -109,16 +109,31 @@ __global__ void pack_keys_kernel(KeySet ks, KeyPack kp, AggSet as, long long n, 
             row[u] = i < m ? (sel ? sel[i] : i) : -1;
             packed[u] = 0;
         }
-        for (int k = 0; k < ks.n; k++) {
-            long long v[U];
+        // every key column (and the carried value) of the U rows is loaded
+        // before any of them is used: one round trip after the row ids
+        long long v[TDP_MAX_KEYS][U];
+#pragma unroll
+        for (int k = 0; k < TDP_MAX_KEYS; k++)
+            if (k < ks.n) {
+#pragma unroll
+                for (int u = 0; u < U; u++)
+                    v[k][u] = row[u] >= 0 ? load_int(ks.col[k], ks.dt[k], row[u]) : 0;
+            }
+        V cv[U];
+        if (CARRY) {
 #pragma unroll
             for (int u = 0; u < U; u++)
-                v[u] = row[u] >= 0 ? load_int(ks.col[k], ks.dt[k], row[u]) : 0;
+                cv[u] = row[u] >= 0 ? (V)slot_value(as, 1, row[u]) : (V)0;
+        }
+#pragma unroll
+        for (int k = 0; k < TDP_MAX_KEYS; k++) {
+            if (k >= ks.n)
+                break;
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 unsigned long long f;
                 if (kp.bounded[k]) {
-                    long long d = v[u] - ks.lo[k];
+                    long long d = v[k][u] - ks.lo[k];
                     if (row[u] >= 0 && (d < 0 || d >= ks.size[k])) {
                         bad = true;
                         d = 0;
@@ -126,7 +141,7 @@ __global__ void pack_keys_kernel(KeySet ks, KeyPack kp, AggSet as, long long n, 
                     f = (unsigned long long)d;
                 } else {
                     const int w = kp.bits[k];
-                    f = (unsigned long long)v[u] & field_mask(w);
+                    f = (unsigned long long)v[k][u] & field_mask(w);
                     if (ks.dt[k] != TDP_U8)
                         f ^= 1ull << (w - 1);
                 }
@@ -138,7 +153,7 @@ __global__ void pack_keys_kernel(KeySet ks, KeyPack kp, AggSet as, long long n, 
             const long long i = i0 + u * stride;
             if (i < m) {
                 keys[i] = (K)packed[u];
-                rows[i] = CARRY ? (V)slot_value(as, 1, row[u]) : (V)(positions ? i : row[u]);
+                rows[i] = CARRY ? cv[u] : (V)(positions ? i : row[u]);
             }
         }
     }
@@ -860,8 +875,17 @@ static tdp_status sort_groupby_impl(const PredSet &ps, const KeySet &ks, int key
     }
     KeyPack kp = make_keypack(ks);
     int grid = (int)std::max(1ll, std::min<long long>((n + 255) / 256, (long long)num_sms() * 8));
-    if (n > 0)
-        pack_keys_kernel<K, V, CARRY><<<grid, 256, 0, s>>>(ks, kp, as, n, rowsel, rowcount, pk, pr, perm, d_status);
+    if (n > 0) {
+        // grid-stride pack: one wave of resident blocks, so that no block
+        // starts after the others have finished their share
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_keys_kernel<K, V, CARRY>, 256, 0) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        const int pgrid = (int)std::max(1ll, std::min<long long>((n + 255) / 256, (long long)num_sms() * per_sm));
+        pack_keys_kernel<K, V, CARRY><<<pgrid, 256, 0, s>>>(ks, kp, as, n, rowsel, rowcount, pk, pr, perm, d_status);
+    }
     tdp_status st = radix_sort_pairs<K, V>(pk, pr, n, rowcount, key_bits, sk, sr, rws, rws_bytes, d_status, s);
     if (st != TDP_OK)
         return st;

@@ -276,34 +276,18 @@ __global__ void __launch_bounds__(SD_THREADS) small_domain_priv_kernel(PredSet p
             acc_update(&gacc[e], s_op[e % NS], spriv[e]);
 }
 
-// eval_preds4 with every comparison in its closed-range form (lo, hi and neg
-// of the PredSet, clamped into the column's type, so a 64-bit unsigned
-// distance decides it for every type).
-__device__ __forceinline__ unsigned preds4_range(const PredSet &ps, long long r, long long n)
-{
-    unsigned m = r + 3 < n ? 0xfu : (r + 2 < n ? 0x7u : (r + 1 < n ? 0x3u : (r < n ? 0x1u : 0u)));
-    for (int p = 0; p < ps.n; p++) {
-        long long v[4];
-        load4_int(ps.col[p], ps.dt[p], ps.vec_ok[p], r, n, v);
-        const long long lo = ps.lo[p];
-        const unsigned long long span = (unsigned long long)ps.hi[p] - (unsigned long long)lo;
-        const unsigned neg = (unsigned)ps.neg[p];
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            m &= ~((range_holds64(v[k], lo, span, neg) ^ 1u) << k);
-    }
-    return m;
-}
-
 // The same private-slice scheme with the slot count NSX a compile-time
 // constant and at most one a * (k - b) slot: MS is that slot (0 for none)
 // when every slot combines by addition (ADD), else MS = -1 and the slot is
-// the argument mslot.  After the predicates, the first two key columns and
-// every value column of the thread's four rows are loaded before any of
-// them is used, so a quad costs two round trips to memory instead of one per
-// slot; the slice offsets, and for ADD the per-slot arithmetic, are fixed at
-// compile time.  Three blocks of 256 threads per SM (the shared slices allow
-// three; the register cap keeps them resident).
+// the argument mslot.  Predicates are tested in their closed-range form (lo,
+// hi and neg of the PredSet, clamped into the column's type, so a 64-bit
+// unsigned distance decides every type); the first predicate's column is
+// loaded one quad ahead, and once a quad's predicates are known the first
+// two key columns and every value column of its four rows are loaded before
+// any of them is used: one round trip to memory per quad instead of one per
+// slot.  The slice offsets, and for ADD the per-slot arithmetic, are fixed
+// at compile time.  Three blocks of 256 threads per SM (the shared slices
+// allow three; the register cap keeps them resident).
 template <int NSX, bool ADD, int MS>
 __global__ void __launch_bounds__(SD_THREADS, 3) small_domain_priv_n_kernel(PredSet ps, KeySet ks, AggSet as, long long n,
                                                                             const long long *d_nsel, int D, int pitch,
@@ -383,7 +367,7 @@ __global__ void __launch_bounds__(SD_THREADS, 3) small_domain_priv_n_kernel(Pred
             load4_int(as.sa[sl], as.sadt[sl], va_vec[sl], r, n, va[sl]);
         if (mslot)
             load4_int(bcol, bdt, b_vec, r, n, vb);
-        int gid[4] = {0, 0, 0, 0}; // < D <= SP_MAX_TAB once the rows' keys are in bounds
+        unsigned gid[4] = {0u, 0u, 0u, 0u}; // < D <= SP_MAX_TAB for the rows whose keys are in bounds
         auto add_key = [&](int k, const long long *v) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -392,7 +376,7 @@ __global__ void __launch_bounds__(SD_THREADS, 3) small_domain_priv_n_kernel(Pred
                     m &= ~(1u << j);
                     bad = true;
                 }
-                gid[j] += (int)d * (int)ks.stride[k];
+                gid[j] += (unsigned)d * (unsigned)ks.stride[k]; // wraps harmlessly for masked rows
             }
         };
 #pragma unroll

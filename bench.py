@@ -324,9 +324,21 @@ TRAFFIC = {
     # gjr_probe_kernel at 1/4 scale (15M fact rows): 327.60 MB read + 3.19 MB written
     "gjr_probe": {"src": "paper_2211_02753_b300/csrc/groupjoin.cu", "sha1": "69c6b8e2ce61",
                   "bytes_per_unit": (327_599_616 + 3_187_456) / 15_000_000},
-    # llp_stream_kernel<6, true> on 8M census-shaped rows (bags of 64): 193.26 MB read + 0.04 MB written
-    "llp_stream": {"src": "paper_2211_02753_b300/csrc/llp.cu", "sha1": "9e82e8c8ab78",
-                   "bytes_per_unit": (193_255_168 + 37_632) / 8_000_000},
+    # llp_stream_kernel<6, true> on 8M census-shaped rows (bags of 64): 193.25 MB read + 0.04 MB written
+    "llp_stream": {"src": "paper_2211_02753_b300/csrc/llp.cu", "sha1": "254578b3f29e",
+                   "bytes_per_unit": (193_246_720 + 37_632) / 8_000_000},
+    # filter_kernel<4> on 60M rows (date <= 2460): 240.10 MB read + 170.58 MB written (the last
+    # ~60 MB of row ids are still in L2 when the kernel ends)
+    "filter": {"src": "paper_2211_02753_b300/csrc/filter.cu", "sha1": "6155f4a8d054",
+               "bytes_per_unit": (240_095_744 + 170_581_248) / 60_000_000},
+    # small_domain_priv_n_kernel<5, 1, 3> on 15M rows of the pricing summary: 450.07 MB read + 2.90 MB written
+    "small_domain_priv": {"src": "paper_2211_02753_b300/csrc/groupby.cu", "sha1": "c3865440c0bb",
+                          "bytes_per_unit": (450_068_992 + 2_904_064) / 15_000_000},
+    # soft_reduce_kernel<0> / <1> on the 10M-row soft query: 120.18 MB read + 4.50 / 2.15 MB written
+    "soft_reduce_fwd": {"src": "paper_2211_02753_b300/csrc/soft.cu", "sha1": "c1765360f92f",
+                        "bytes_per_unit": (120_178_944 + 4_499_968) / 10_000_000},
+    "soft_reduce_bwd": {"src": "paper_2211_02753_b300/csrc/soft.cu", "sha1": "c1765360f92f",
+                        "bytes_per_unit": (120_182_016 + 2_154_240) / 10_000_000},
 }
 
 
@@ -687,7 +699,8 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
     nsel = int(fout["o"]["count"].item())
     fbytes = N_FACT * 4 + nsel * 4
     res["filter_60M"] = {"ms": ms, "rows_per_s": N_FACT / (ms / 1e3), "selected": nsel,
-                         "roofline": roofline("hbm", fbytes, ms / 1e3, hbm_peak, "GB/s", "filter_kernel", peak_kind=pk),
+                         "roofline": roofline("hbm", fbytes, ms / 1e3, hbm_peak, "GB/s", "filter_kernel",
+                                              traffic=measured_traffic("filter", N_FACT), peak_kind=pk),
                          "cpu_baseline": cpu_baseline(cpu_filter_sample, 1.0, "rows/s",
                                                       "1/10 of the rows (6M), date <= 2460", scale=10)}
     for strategy in ("small_domain", "sort"):
@@ -699,8 +712,9 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
         res["pricing_summary_60M_" + strategy] = {
             "ms": ms, "rows_per_s": N_FACT / (ms / 1e3),
             "roofline": roofline("hbm", algo, ms / 1e3, hbm_peak, "GB/s",
-                                 "small_domain_priv_kernel" if strategy == "small_domain" else "sort path",
-                                 peak_kind=pk)}
+                                 "small_domain_priv_n_kernel" if strategy == "small_domain" else "sort path",
+                                 traffic=measured_traffic("small_domain_priv", N_FACT)
+                                 if strategy == "small_domain" else None, peak_kind=pk)}
     res["pricing_summary_60M_small_domain"]["cpu_baseline"] = cpu_baseline(
         cpu_pricing_sample, 1.0, "rows/s", "1/20 of the rows (3M)", scale=20)
     del td
@@ -805,18 +819,19 @@ def other_plans(dev, stream, hbm_peak, bf16_peak, peak_kind, args, fact_h, dim_h
                                      parallel_ok=False, n=1_000_000)}
     th, tau = sq.theta, sq.tau
     gm = torch.ones_like(sd["x"])
-    for name, fn, bpr, kern in (
+    for name, fn, bpr, kern, tkey in (
             ("soft_agg_fwd_10M", lambda: ops.soft_agg_fwd(sd["x"], sd["v"], sd["gid"], th, tau), 12,
-             "soft_reduce_kernel<fwd>"),
+             "soft_reduce_kernel<fwd>", "soft_reduce_fwd"),
             ("soft_agg_bwd_10M", lambda: ops.soft_agg_bwd(sd["x"], sd["v"], sd["gid"], th, tau, sq.gS, sq.gC), 12,
-             "soft_reduce_kernel<bwd>"),
+             "soft_reduce_kernel<bwd>", "soft_reduce_bwd"),
             ("soft_filter_fwd_10M", lambda: ops.soft_filter_fwd(sd["x"], sd["gid"], th, tau), 12,
-             "soft_filter_fwd_kernel"),
+             "soft_filter_fwd_kernel", None),
             ("soft_filter_bwd_10M", lambda: ops.soft_filter_bwd(sd["x"], sd["gid"], th, tau, gm), 16,
-             "soft_reduce_kernel<filter bwd>")):
+             "soft_reduce_kernel<filter bwd>", None)):
         ms = _time_graph(fn, stream, steps)
         res[name] = {"ms": ms, "rows_per_s": 10e6 / (ms / 1e3),
-                     "roofline": roofline("hbm", 10e6 * bpr, ms / 1e3, hbm_peak, "GB/s", kern, peak_kind=pk)}
+                     "roofline": roofline("hbm", 10e6 * bpr, ms / 1e3, hbm_peak, "GB/s", kern,
+                                          traffic=measured_traffic(tkey, 10e6) if tkey else None, peak_kind=pk)}
     n1, s1 = cpu_soft_filter_sample()
     sfb = {"value": n1 / s1, "unit": "rows/s", "cores": 1, "kind": "oracle", "host_cores": host_cores(),
            "sample": "1M rows, soft filter forward + backward, float64 numpy, one thread (%.2f s)" % s1}

@@ -223,8 +223,10 @@ size_t tdp_groupby_agg_workspace(int64_t n, const tdp_col *keys, int32_t nkeys, 
  * AVG = (2*sum + sign(sum)*count) / (2*count) with truncating division.
  * SORT: packs the keys into an unsigned radix key (offset by lo when bounds
  * are present), radix-sorts (key, row id) and reduces the sorted runs.
- * SMALL_DOMAIN: one pass that accumulates into per-block copies of the dense
- * key domain and merges them.
+ * SMALL_DOMAIN: one pass that accumulates into private copies of the dense
+ * key domain and merges them: per thread (in shared memory, plain adds, no
+ * atomics) when the domain times the accumulator slots is at most 63 and
+ * the input is not a row-id list, else per warp or per block.
  * PARTITION: bounded keys whose dense domain D fits 16384 buckets of B group
  * ids (B = 4096 with one aggregate slot besides COUNT, smaller with more, so
  * D <= 64M for one sum): rows are counted per bucket, scattered to bucket

@@ -10,13 +10,18 @@ synthetic seeded data.  value = fact rows per second over the whole job.
 
 The same run also measures, on their own inputs and each with a `roofline`
 object and a `cpu_baseline` (the oracle on the host cores, single-threaded
-and OpenMP row-partitioned): the standalone filter; the pricing summary
-(small-domain and onesweep sort group-by); the shipping plan on the separate
-build -> probe -> group-by path (partition and sort group-by); the
-three-table join chain (fused probe + group-by, and probe -> sort group-by);
-the soft query forward/backward kernels; the glyph-CNN trainable query.
+and OpenMP row-partitioned where it has that form): the standalone filter;
+the pricing summary (small-domain and onesweep sort group-by); the shipping
+plan on the separate build -> probe -> group-by path (partition and sort
+group-by); the three-table join chain (fused probe + group-by, and probe ->
+sort group-by); the N:M join; dictionary codes of a string column and a
+GROUP BY over two coded columns; the soft query forward/backward kernels;
+the glyph-CNN and Digit x Size trainable queries with their exact queries;
+learning from label proportions (the 64M-row step and the census error by
+bag size); the soft top-k.
 
 Flags: --gpus N --steps K --warmup W [--impl reference] [--plans all|main]
+[--only PLAN --scale S: one plan at 1/S of its size, for profiler captures]
 """
 from __future__ import annotations
 

@@ -306,7 +306,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "fact_rows": N_FACT, "dim_rows": N_DIM, "parallelism": "replicas"},
+        "config": {"workload": WORKLOAD, "fact_rows": N_FACT, "dim_rows": N_DIM,
+                   "parallelism": "replicas" if args.gpus > 1 else "single-gpu"},
         "cpu_baseline": {"value": v, "unit": "rows/s", "cores": R.threads(), "host_cores": host_cores(),
                          "kind": "oracle",
                          "sample": "1/%d of the workload per step (%d fact rows, %d dimension rows), plain C "
